@@ -1,0 +1,343 @@
+"""Benchmark of the ADASAP hot path on B300 (one JSON line on rank 0).
+
+A step is one full ADASAP iteration (Alg. 2: sample, Step I block residual,
+Step II sketch, Alg. 4 Nystrom core, Alg. 5 stepsize, Step IV direction and
+Alg. 6 update) on the regression workload: n = 2^20, d = 11, X ~ U[0,1]^11,
+Matern-3/2, ell = 0.3, lambda = 1e-3, b = 10^4, r = 100, one right-hand side
+(synthetic stand-in for the paper's regression datasets).
+
+value: kernel entries k(x_i, x_j) evaluated per second over whole iterations
+  (b n for Step I, b^2 for the sketch, N b^2 for the N powering products).
+roofline: the fused kernel-row product (Step I's kernel) timed alone with CUDA
+  events; its peak is the MUFU bound (16 MUFU results/clk/SM, 148 SMs, max SM
+  clock; Matern needs rsqrt + ex2 per entry, RBF ex2 only).
+e2e: the same entries through the C-ABI with host buffers (create + solve +
+  copy-back inside the timed region).
+cpu_baseline / --impl reference: the FP64 oracle's block-row product on a
+  bounded row sample of the same workload, on the host.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torchrun each rank runs an independent replica ("replicas only": every box has
+one GPU per call) and rank 0 reports the aggregate.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ADASAP s to rel-resid 1e-3 (mixed vs FP32); kernel-row Gentries/s, % roofline"
+UNIT = "Gentries/s"
+MUFU_PER_CLK_SM = 16
+SMS = 148
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-tol-run", action="store_true")
+    p.add_argument("--n", type=int, default=1 << 20, help="rows of the workload (default: full size)")
+    p.add_argument("--kernel-launches", type=int, default=10, help="timed launches of the Step I kernel alone")
+    return p.parse_args()
+
+
+def workload(n):
+    from paper_2505_13723_b300 import synth
+    return synth.regress(n=n, b=min(10000, n // 4))
+
+
+def entries_per_step(P, power_iters=10):
+    n, b = P.X.shape[0], P.b
+    return b * n + b * b + power_iters * b * b
+
+
+def mufu_per_entry(kernel):
+    return 1 if kernel == 0 else 2
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_rows_rate(P, target_s=10.0, max_rows=None):
+    """Entries/s of the oracle's block-row product (FP64 NumPy, one thread) on sampled rows."""
+    from threadpoolctl import threadpool_limits
+
+    from oracle import kernels as OK
+    X = P.X.astype(np.float64)
+    W = P.Y.astype(np.float64)
+    g = np.random.default_rng(0)
+    with threadpool_limits(limits=1):
+        rows = g.choice(X.shape[0], size=2, replace=False)
+        t0 = time.perf_counter()
+        OK.kernel_rows(X, rows, W, P.kernel, P.ell, P.sigma2)
+        per_row = (time.perf_counter() - t0) / 2
+        k = max(1, int(target_s / max(per_row, 1e-6)))
+        if max_rows:
+            k = min(k, max_rows)
+        rows = g.choice(X.shape[0], size=k, replace=False)
+        t0 = time.perf_counter()
+        OK.kernel_rows(X, rows, W, P.kernel, P.ell, P.sigma2)
+        dt = time.perf_counter() - t0
+    return k * X.shape[0] / dt, k, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    P = workload(args.n)
+    n = P.X.shape[0]
+    for _ in range(args.warmup):
+        oracle_rows_rate(P, target_s=0.5, max_rows=2)
+    rates, tot_rows, tot_t = [], 0, 0.0
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        rate, k, dt = oracle_rows_rate(P, target_s=5.0)
+        rates.append(rate)
+        tot_rows += k
+        tot_t += dt
+    value = tot_rows * n / tot_t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(P),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "FP64 NumPy block-row product K(X_B, X) w on %d sampled rows x n=%d per "
+                                       "step (%.1f s of host work per step)" % (tot_rows // args.steps, n,
+                                                                                 tot_t / args.steps)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t_all}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(P):
+    return {"workload": "regress: n=%d, d=11, X~U[0,1]^11, Matern-3/2 ell=0.3, lambda=1e-3, b=%d, r=100, s=1"
+                        % (P.X.shape[0], P.b),
+            "n": int(P.X.shape[0]), "d": 11, "kernel": "matern32", "b": int(P.b), "r": 100, "s": 1,
+            "power_iters": 10, "precision": "fp32", "l2": "flushed between timed steps",
+            "parallelism": "replicas"}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_ours(args, rank, world, dist):
+    import torch
+
+    from paper_2505_13723_b300 import binding as lib
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P = workload(args.n)
+    n, b, r = P.X.shape[0], P.b, P.r
+    stream = torch.cuda.current_stream()
+    Xd = torch.from_numpy(P.X).to(dev)
+    Yd = torch.from_numpy(P.Y).to(dev)
+    ctx = lib.Context(Xd, P.kernel, P.ell, P.sigma2, P.lam)
+    opts = lib.default_opts(n, b=b, r=r, seed=1, check_every=0, max_iters=args.steps)
+    sol = lib.Solver(ctx, Yd, opts=opts)
+    kernels_per_iter = sol.graph_kernels()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 126 MB L2
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sol.step(args.warmup)
+    barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            sol.step(1)
+            ends[i].record(stream)
+        barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_local = sum(step_ms) / 1e3
+    rel = sol.residual()
+    eta, rho, status = sol.scalars()
+    sol.close()
+    t_max = t_local
+    if dist is not None:
+        tt = torch.tensor([t_local], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    ent = entries_per_step(P)
+    value = ent * args.steps * world / t_max / 1e9
+
+    # ---- the dominant kernel alone: Step I block-row product, same launch shape
+    g = np.random.default_rng(5)
+    B = torch.from_numpy(g.choice(n, size=b, replace=False)).to(dev)
+    Wv = torch.from_numpy(g.standard_normal((n, 1)).astype(np.float32)).to(dev)
+    for _ in range(3):
+        ctx.kernel_rows(B, Wv)
+    ks = [torch.cuda.Event(enable_timing=True) for _ in range(args.kernel_launches)]
+    ke = [torch.cuda.Event(enable_timing=True) for _ in range(args.kernel_launches)]
+    with ClockSampler(local) as kclk:
+        torch.cuda.synchronize()
+        for i in range(args.kernel_launches):
+            flush.zero_()
+            ks[i].record(stream)
+            ctx.kernel_rows(B, Wv)
+            ke[i].record(stream)
+        torch.cuda.synchronize()
+    k_ms = statistics.mean(s.elapsed_time(e) for s, e in zip(ks, ke))
+    k_rate = b * n / (k_ms * 1e-3)
+    pk, pk_src = peaks()
+    mhz = float(pk.get("sm_max_mhz", 2032.0))
+    peak_entries = SMS * MUFU_PER_CLK_SM * mhz * 1e6 / mufu_per_entry(P.kernel)
+
+    # ---- time to relative residual 1e-3 (FP32), bounded
+    tol_run = None
+    if not args.no_tol_run and rank == 0:
+        topts = lib.default_opts(n, b=b, r=r, seed=2, tol=1e-3, max_iters=300, check_every=25,
+                                 check_rows=20000)
+        W, st, stc = ctx.solve(Yd, opts=topts)
+        tol_run = {"fp32": {"seconds": st["seconds"], "iters": st["iters"], "rel_resid": st["rel_resid"],
+                            "reached": bool(st["rel_resid"] <= 1e-3), "resid_rows_sampled": 20000},
+                   "mixed": None}
+
+    # ---- end to end through the C-ABI with host buffers
+    e2e = None
+    if rank == 0:
+        Xh, Yh = P.X, P.Y
+        Wh = np.zeros_like(Yh)
+        eopts = lib.default_opts(n, b=b, r=r, seed=3, check_every=0, max_iters=args.steps)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c2 = lib.Context(Xh, P.kernel, P.ell, P.sigma2, P.lam)
+        Wout, st2, _ = c2.solve(Yh, opts=eopts, W=Wh)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        c2.close()
+        e2e = {"value": ent * args.steps / te / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int((Xh.nbytes + Yh.nbytes + Wh.nbytes) / args.steps),
+               "d2h_bytes_per_step": int(Wh.nbytes / args.steps),
+               "includes": "create (H2D of X, centring) + solve (H2D of Y, W0; %d iterations; final residual) + "
+                           "D2H of W" % args.steps}
+
+    ctx.close()
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, k, dt = oracle_rows_rate(P, target_s=12.0)
+        cpu = {"value": rate / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "FP64 NumPy block-row product K(X_B, X) w, %d sampled rows x n=%d (%.1f s), one thread"
+                         % (k, n, dt)}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(P),
+            "roofline": {"bound": "alu", "achieved": k_rate / 1e9, "peak": peak_entries / 1e9,
+                         "unit": "Gentries/s", "frac": k_rate / peak_entries, "traffic": None,
+                         "kernel": "k_rows_narrow (Step I block-row product, b=%d rows x n=%d)" % (b, n),
+                         "ms_per_launch": k_ms,
+                         "peak_basis": "MUFU: %d/clk/SM x %d SMs x %.0f MHz / %d MUFU per entry (sm_max_mhz %s)"
+                                       % (MUFU_PER_CLK_SM, SMS, mhz, mufu_per_entry(P.kernel), pk_src)},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": kernels_per_iter * args.steps,
+            "clocks": clk.summary(), "kernel_clocks": kclk.summary(),
+            "time_to_tol": tol_run,
+            "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+            "solver_state": {"rel_resid_after": rel, "eta": eta, "rho": rho, "status": status}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        if args.impl == "reference":
+            tdist = None
+        else:
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            tdist.init_process_group("nccl")
+        dist = tdist
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, dist)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

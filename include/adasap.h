@@ -1,0 +1,171 @@
+/*
+ * adasap.h -- C-ABI of the B300-native (sm_103a) ADASAP hot path.
+ *
+ * ADASAP ("Turbocharging Gaussian Process Inference with Approximate
+ * Sketch-and-Project", Rathore et al., NeurIPS 2025, Alg. 2) solves
+ *
+ *     (K(X, X) + lambda I) W = Y,      K_ij = k(x_i, x_j),
+ *
+ * for a stationary kernel k, by sampling a block B of b rows per iteration,
+ * forming the block residual K(X_B, X) W + lambda W_B - Y_B on the fly,
+ * preconditioning it with a rank-r randomized Nystrom approximation of K_BB
+ * (Alg. 4, App. C.2), choosing the step by randomized powering (Alg. 5) and
+ * updating three Nesterov sequences (Alg. 6).
+ *
+ * Conventions for every entry point below
+ *   - Matrices are dense, row-major, float32 unless stated; an (n x s) matrix
+ *     has row j at offset j*s.  Index arrays are int64.
+ *   - Pointers are CUDA device pointers unless the entry says "host or
+ *     device": those are probed with cudaPointerGetAttributes and copied.
+ *   - The caller owns every pointer it passes; the context owns its own
+ *     device copies and workspaces and frees them in adasap_destroy.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     ordered after everything already queued on it.  adasap_solve* and
+ *     adasap_hypergrad return after the work completed (they read results
+ *     back); the other calls are asynchronous with respect to the host.
+ *   - Every function returns a status and never aborts the process.
+ *     Invalid sizes or pointers give ADASAP_EINVAL before any GPU work.
+ *   - A context is not thread-safe; use one context per host thread/stream.
+ *
+ * Kernels (the paper uses them without printing the formulas; standard forms),
+ * r = ||x - x'||:
+ *   ADASAP_RBF       k = sigma2 * exp(-r^2 / (2 ell^2))
+ *   ADASAP_MATERN32  k = sigma2 * (1 + a) exp(-a),           a = sqrt(3) r / ell
+ *   ADASAP_MATERN52  k = sigma2 * (1 + a + a^2/3) exp(-a),   a = sqrt(5) r / ell
+ */
+#ifndef ADASAP_H
+#define ADASAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct adasap_ctx adasap_ctx;
+
+typedef enum {
+  ADASAP_OK = 0,
+  ADASAP_EINVAL = 1,        /* invalid argument (shape, range, null pointer) */
+  ADASAP_ENOMEM = 2,        /* device allocation failed */
+  ADASAP_ECUDA = 3,         /* a CUDA runtime call failed (see adasap_last_error) */
+  ADASAP_ENUMERIC = 4,      /* Cholesky of an r x r core failed after retries */
+  ADASAP_EDIVERGED = 5,     /* residual became non-finite or exploded */
+  ADASAP_ETIMEOUT = 6,      /* a bounded device wait gave up */
+  ADASAP_ENOTCONVERGED = 7  /* max_iters reached before tol (W still returned) */
+} adasap_status;
+
+typedef enum { ADASAP_RBF = 0, ADASAP_MATERN32 = 1, ADASAP_MATERN52 = 2 } adasap_kernel;
+
+/* Options of adasap_solve.  adasap_default_opts fills the paper's defaults. */
+typedef struct {
+  int64_t b;           /* block size (Alg. 2); 0 < b <= n.  Default n/100 (App. D.2). */
+  int r;               /* Nystrom rank (Alg. 4); 1 <= r <= min(b, 128).  Default 100 (App. D.2). */
+  int max_iters;       /* iteration cap T_max (Alg. 2). */
+  double tol;          /* stop when the relative residual estimate <= tol (0: never). */
+  int power_iters;     /* randomized-powering iterations N of Alg. 5.  Default 10 (App. C.3). */
+  double mu, nu;       /* acceleration parameters (Alg. 2); 0 => mu = lambda, nu = n/b (Sec. 4.2). */
+  int precond;         /* 0 = Nystrom (ADASAP), 1 = identity (ADASAP-I, Sec. 5). */
+  int literal;         /* 0: residual at Z_t and Z_{t+1} from V_{t+1} (standard accelerated
+                          sketch-and-project); 1: residual at W_t and Z_{t+1} from V_t, as
+                          Alg. 2 / Alg. 6 print. */
+  uint64_t seed;       /* Philox4x32-10 key for B, Omega, v0. */
+  int check_every;     /* evaluate the residual every this many iterations (0: only at the end). */
+  int64_t check_rows;  /* residual on all rows if n <= check_rows, else on this many sampled rows. */
+  double eps;          /* eps of Alg. 4's shift Delta = eps * Tr(Omega^T M Omega); 0 => 2^-23. */
+} adasap_opts;
+
+typedef struct {
+  int iters;           /* iterations run */
+  double rel_resid;    /* last relative residual ||(K + lambda I) W - Y||_F / ||Y||_F (exact or sampled) */
+  int resid_exact;     /* 1 if rel_resid used all n rows */
+  double seconds;      /* device time of the iteration loop incl. residual checks (CUDA events) */
+  double last_eta;     /* stepsize eta_B of the last iteration */
+  double last_rho;     /* damping rho = S_rr + lambda of the last iteration */
+} adasap_stats;
+
+void adasap_default_opts(adasap_opts* opts, int64_t n);
+const char* adasap_status_string(adasap_status s);
+/* Text of the last CUDA error seen by this host thread (empty if none). */
+const char* adasap_last_error(void);
+
+/* Create a context for the training inputs X (n x d, host or device).
+ * X is centred and scaled by 1/ell into a device copy (the kernel is
+ * translation invariant), so the caller may free X afterwards.
+ * Requires n >= 1, 1 <= d <= 64, ell > 0, sigma2 > 0, lambda > 0. */
+adasap_status adasap_create(const float* X, int64_t n, int d, int kernel, float ell,
+                            float sigma2, float lambda, void* stream, adasap_ctx** out);
+void adasap_destroy(adasap_ctx* ctx);
+
+/* Block-row kernel product (Alg. 2 Step I; App. C.1 ColDistMatMat as one kernel):
+ *   out (b x s) = K(X_B, X) W,  B (b) int64 row indices into X, W (n x s).
+ * Rows whose index is outside [0, n) are written as NaN (no fault). */
+adasap_status adasap_kernel_rows(adasap_ctx* ctx, const int64_t* B, int64_t b, const float* W,
+                                 int s, float* out, void* stream);
+
+/* ADASAP (Alg. 2 with Alg. 4, 5, 6 and the stabilised Woodbury apply of App. C.2).
+ * Y (n x s) and W (n x s) are host or device.  W holds W_0 on entry and the
+ * returned iterate W_T on exit.  1 <= s <= 128.  Randomness (B, Omega, v0) is
+ * drawn on the device from Philox4x32-10 keyed by opts->seed. */
+adasap_status adasap_solve(adasap_ctx* ctx, const float* Y, int s, const adasap_opts* opts,
+                           float* W, adasap_stats* stats, void* stream);
+
+/* As adasap_solve, but iteration t < T uses the caller's randomness:
+ * B_sched (T x b) int64 distinct rows, Omega_sched (T x b x r), v0_sched (T x b),
+ * all device.  Runs exactly T iterations (opts->max_iters and tol are ignored).
+ * trace (device, T x 2 float64, may be NULL) receives (eta_t, rho_t). */
+adasap_status adasap_solve_scheduled(adasap_ctx* ctx, const float* Y, int s,
+                                     const adasap_opts* opts, const int64_t* B_sched,
+                                     const float* Omega_sched, const float* v0_sched, int T,
+                                     float* W, double* trace, adasap_stats* stats, void* stream);
+
+/* Incremental form of adasap_solve (same arithmetic), for callers that step
+ * the solver themselves or time it.  One active solver per context: the
+ * solver uses the context's streams and device scalars.
+ *   begin:    allocate the solver state (W0 host or device, NULL = zeros), copy
+ *             Y and W0, and capture one iteration of Alg. 2 as a CUDA graph.
+ *   step:     enqueue `iters` iterations on `stream` (no host synchronisation).
+ *   residual: ||(K + lambda I) W - Y||_F / ||Y||_F on all rows when
+ *             n <= opts->check_rows, else on check_rows rows drawn afresh
+ *             (scaled by sqrt(n / check_rows)); synchronises.  Returns the
+ *             device status (ENUMERIC / EDIVERGED) if an iteration failed.
+ *   get_w:    copy the current iterate W_t (n x s) to W (host or device).
+ *   scalars:  eta, rho and the device status of the last iteration (synchronises).
+ *   end:      free everything. */
+typedef struct adasap_solver adasap_solver;
+adasap_status adasap_solver_begin(adasap_ctx* ctx, const float* Y, int s, const adasap_opts* opts,
+                                  const float* W0, void* stream, adasap_solver** out);
+adasap_status adasap_solver_step(adasap_solver* sol, int iters, void* stream);
+adasap_status adasap_solver_residual(adasap_solver* sol, double* rel_resid, void* stream);
+adasap_status adasap_solver_get_w(adasap_solver* sol, float* W, void* stream);
+adasap_status adasap_solver_scalars(adasap_solver* sol, double* eta, double* rho, int* status, void* stream);
+void adasap_solver_end(adasap_solver* sol);
+/* Number of kernel launches in one captured iteration (for launch accounting). */
+adasap_status adasap_solver_graph_kernels(adasap_solver* sol, int* count);
+
+/* Posterior mean with zero prior mean (Sec. 2, eq. post_eqns):
+ *   out (m x s) = K(Xtest, X) W,  Xtest (m x d) device, W (n x s) device. */
+adasap_status adasap_predict(adasap_ctx* ctx, const float* Xtest, int64_t m, const float* W, int s,
+                             float* out, void* stream);
+
+/* Kernel adjoint for hyperparameter fitting (App. D.1):
+ *   d_ell    = sum_c G[:,c]^T (dK/dell)    W[:,c]
+ *   d_sigma2 = sum_c G[:,c]^T (dK/dsigma2) W[:,c]
+ * over the full n x n kernel, recomputing tiles.  W, G (n x s) device;
+ * d_ell, d_sigma2 host.  With W = G = (K + lambda I)^{-1} y this gives
+ * -d(y^T (K + lambda I)^{-1} y)/dtheta. */
+adasap_status adasap_hypergrad(adasap_ctx* ctx, const float* W, const float* G, int s,
+                               double* d_ell, double* d_sigma2, void* stream);
+
+/* The device sampler of adasap_solve at iteration t (for tests and for
+ * callers that want the same randomness): B (b) int64 distinct rows of [n],
+ * Omega (b x r) with N(0, 1/b) entries, v0 (b) N(0, 1); any output may be NULL.
+ * Definitions: Philox4x32-10 (Salmon et al., SC'11) keyed by seed, a 4-round
+ * Feistel permutation of [n] with cycle walking for B, Box-Muller normals. */
+adasap_status adasap_sample(uint64_t seed, int64_t t, int64_t n, int64_t b, int r, int64_t* B,
+                            float* Omega, float* v0, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADASAP_H */

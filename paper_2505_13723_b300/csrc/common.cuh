@@ -1,0 +1,118 @@
+// Shared device helpers of the ADASAP CUDA path (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "adasap.h"
+
+namespace adasap {
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+// ---- PTX one-instruction approximations (MUFU) and packed FP32 -------------
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// d = a * b + c on two lanes at once (sm_100+ packed FP32 FMA)
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  unsigned long long ra = *reinterpret_cast<unsigned long long*>(&a);
+  unsigned long long rb = *reinterpret_cast<unsigned long long*>(&b);
+  unsigned long long rc = *reinterpret_cast<unsigned long long*>(&c);
+  unsigned long long rd;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
+  return *reinterpret_cast<float2*>(&rd);
+}
+
+// ---- kernel epilogues --------------------------------------------------------
+// Columns and rows are stored pre-scaled: x' = kappa (x - mean) / ell with
+//   RBF  kappa^2 = log2(e)/2   -> u = kappa^2 r~^2,  k = sigma2 * 2^(-u)
+//   M32  kappa^2 = 3           -> u = a^2,           k = sigma2 (1 + a) e^(-a)
+//   M52  kappa^2 = 5           -> u = a^2,           k = sigma2 (1 + a + a^2/3) e^(-a)
+// where r~ = r / ell and u = ||x'_i - x'_j||^2 >= 0.  kval returns k / sigma2.
+template <int KERN>
+__device__ __forceinline__ float kval(float u) {
+  if (KERN == ADASAP_RBF) return ex2_approx(-u);
+  float a = u * rsqrt_approx(fmaxf(u, 1e-30f));
+  float e = ex2_approx(-kLog2e * a);
+  if (KERN == ADASAP_MATERN32) return fmaf(a, e, e);
+  float p = fmaf(a, fmaf(a, 1.0f / 3.0f, 1.0f), 1.0f);
+  return p * e;
+}
+// k / sigma2 and g = ell * (dk/dell) / sigma2 together (adjoint):
+//   RBF  g = r~^2 e^(-r~^2/2) = 2 ln2 u 2^(-u)
+//   M32  g = a^2 e^(-a)
+//   M52  g = a^2 (1 + a) e^(-a) / 3
+template <int KERN>
+__device__ __forceinline__ void kval_grad(float u, float& kv, float& gv) {
+  if (KERN == ADASAP_RBF) {
+    float e = ex2_approx(-u);
+    kv = e;
+    gv = (2.0f * kLn2) * u * e;
+    return;
+  }
+  float a = u * rsqrt_approx(fmaxf(u, 1e-30f));
+  float e = ex2_approx(-kLog2e * a);
+  if (KERN == ADASAP_MATERN32) {
+    kv = fmaf(a, e, e);
+    gv = u * e;
+  } else {
+    kv = fmaf(a, fmaf(a, 1.0f / 3.0f, 1.0f), 1.0f) * e;
+    gv = u * fmaf(a, e, e) * (1.0f / 3.0f);
+  }
+}
+
+// ---- reductions ------------------------------------------------------------
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+// Block-wide double sum; every thread gets the result.  blockDim.x <= 1024.
+__device__ __forceinline__ double block_sum(double v, double* red /* >= 33 doubles */) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double w = (lane < (int)((blockDim.x + 31) >> 5)) ? red[lane] : 0.0;
+    w = warp_sum(w);
+    if (lane == 0) red[32] = w;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// ---- device status -----------------------------------------------------------
+// Scalars shared by the kernels of one solve (device memory).
+struct DevScalars {
+  double delta;      // Nystrom shift Delta (Alg. 4)
+  double rho;        // damping rho = S_rr + lambda
+  double eta;        // stepsize eta_B (Alg. 5)
+  double lam_hat;    // Rayleigh quotient of the power iteration
+  double ysq;        // ||Y||_F^2
+  double resid_sq;   // sum of squares of the sampled residual
+  double dot;        // scratch dot product (power iteration)
+  int status;        // first error (adasap_status), 0 if none
+  int chol_retries;  // number of Delta increases in the last iteration
+  long long t;       // iteration counter
+};
+
+__device__ __forceinline__ void set_status(DevScalars* sc, int code) {
+  atomicCAS(&sc->status, 0, code);
+}
+
+}  // namespace adasap

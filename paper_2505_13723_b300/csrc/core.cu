@@ -1,0 +1,773 @@
+// Step III and IV of Alg. 2 on the GPU:
+//   - Gram matrices of b x r panels (FP32 products, FP64 accumulation)
+//   - the randomized Nystrom factorisation of Alg. 4 on its r x r core
+//     (FP64 Cholesky and triangular solves; eigenvectors by FP32 cyclic
+//     Jacobi with FP64 Rayleigh-quotient eigenvalues)
+//   - the Woodbury applies of App. C.2: (P + rho I)^{-1/2} v
+//     (eq. inv_sqrt_nys_woodbury) and the Cholesky-stabilised
+//     (P + rho I)^{-1} g
+//   - the stepsize of Alg. 5 and the NesterovAcc update of Alg. 6.
+//
+// The thin SVD of B = Y_nu C^{-1} (Alg. 4) is computed through the r x r
+// matrix B^T B = C^{-T} (Y_nu^T Y_nu) C^{-1}: its eigenvectors are B's right
+// singular vectors V and its eigenvalues Sigma^2, and U = Y_nu (C^{-1} V Sigma^{-1}).
+// Y_nu^T Y_nu comes from the Gram of [Omega | M Omega] without forming Y_nu.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace adasap {
+
+// ---------------------------------------------------------------------------
+// Gram matrix of the row-concatenation [A1 | A2] (m x (c1 + c2), c <= 256):
+// per chunk of rows FP32 products over 32-row slices, folded into FP64; only
+// upper 32 x 32 tiles are computed, the reduce mirrors them.
+// ---------------------------------------------------------------------------
+int gram_chunks_for(int64_t b) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, (b + 255) / 256)); }
+
+__device__ __forceinline__ float cat_get(const float* A1, int64_t ld1, int c1, const float* A2, int64_t ld2,
+                                         int c2, int64_t row, int col) {
+  if (col < c1) return A1[row * ld1 + col];
+  if (col < c1 + c2) return A2[row * ld2 + (col - c1)];
+  return 0.0f;
+}
+
+__global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1, int64_t ld1, int c1,
+                                                   const float* __restrict__ A2, int64_t ld2, int c2,
+                                                   int64_t m, int64_t chunk_rows, double* __restrict__ part) {
+  const int ti = blockIdx.y, tj = blockIdx.z;
+  if (ti > tj) return;
+  const int c = c1 + c2;
+  __shared__ float sa[32][33];
+  __shared__ float sb[32][33];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk_rows;
+  const int64_t r1 = min(m, r0 + chunk_rows);
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int64_t s0 = r0; s0 < r1; s0 += 32) {
+    __syncthreads();
+    for (int e = tid; e < 32 * 32; e += 256) {
+      const int rr = e >> 5, cc = e & 31;
+      const int64_t row = s0 + rr;
+      const bool ok = row < r1;
+      sa[rr][cc] = ok ? cat_get(A1, ld1, c1, A2, ld2, c2, row, ti * 32 + cc) : 0.0f;
+      sb[rr][cc] = ok ? cat_get(A1, ld1, c1, A2, ld2, c2, row, tj * 32 + cc) : 0.0f;
+    }
+    __syncthreads();
+    float f[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 8
+    for (int rr = 0; rr < 32; ++rr) {
+      const float a0 = sa[rr][2 * ty], a1 = sa[rr][2 * ty + 1];
+      const float b0 = sb[rr][2 * tx], b1 = sb[rr][2 * tx + 1];
+      f[0][0] = fmaf(a0, b0, f[0][0]);
+      f[0][1] = fmaf(a0, b1, f[0][1]);
+      f[1][0] = fmaf(a1, b0, f[1][0]);
+      f[1][1] = fmaf(a1, b1, f[1][1]);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int v = 0; v < 2; ++v) acc[u][v] += (double)f[u][v];
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int i = ti * 32 + 2 * ty + u, j = tj * 32 + 2 * tx + v;
+      if (i < c && j < c) part[((int64_t)blockIdx.x * c + i) * c + j] = acc[u][v];
+    }
+}
+
+__global__ void k_gram_reduce(const double* __restrict__ part, int chunks, int c, double* __restrict__ G) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < c * c; e += gridDim.x * blockDim.x) {
+    int i = e / c, j = e % c;
+    if ((i >> 5) > (j >> 5)) { const int t = i; i = j; j = t; }
+    double acc = 0.0;
+    for (int ch = 0; ch < chunks; ++ch) acc += part[((int64_t)ch * c + i) * c + j];
+    G[e] = acc;
+  }
+}
+
+cudaError_t launch_gram(const float* A1, int64_t ld1, int c1, const float* A2, int64_t ld2, int c2,
+                        int64_t m, double* part, int chunks, double* G, cudaStream_t st) {
+  const int c = c1 + c2;
+  const int nt = (c + 31) / 32;
+  const int64_t chunk_rows = (m + chunks - 1) / chunks;
+  k_gram_part<<<dim3(chunks, nt, nt), 256, 0, st>>>(A1, ld1, c1, A2, ld2, c2, m, chunk_rows, part);
+  k_gram_reduce<<<std::min(148, (c * c + 255) / 256), 256, 0, st>>>(part, chunks, c, G);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// One-CTA FP64 Cholesky (lower, in place) of an r x r matrix in shared memory
+// with leading dimension ld (r + 1 keeps column reads conflict free).
+// Returns false, uniformly over the block, if a pivot is not positive.
+// ---------------------------------------------------------------------------
+__device__ bool chol_lower_smem(double* A, int r, int ld, int* flag) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = 0; k < r; ++k) {
+    if (threadIdx.x == 0) {
+      const double d = A[k * ld + k];
+      *flag = (d > 0.0 && isfinite(d)) ? 0 : 1;
+      if (!*flag) A[k * ld + k] = sqrt(d);
+    }
+    __syncthreads();
+    if (*flag) return false;
+    const double dk = A[k * ld + k];
+    for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) A[i * ld + k] /= dk;
+    __syncthreads();
+    for (int i = k + 1 + warp; i < r; i += nw) {
+      const double lik = A[i * ld + k];
+      for (int j = k + 1 + lane; j <= i; j += 32) A[i * ld + j] -= lik * A[j * ld + k];
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// Alg. 4, first half: Delta, C = chol(Omega^T M Omega + Delta Omega^T Omega)
+// (stored as the lower factor L = C^T), and Y_nu^T Y_nu.
+__global__ void __launch_bounds__(512) k_nys_chol(const double* __restrict__ G, int r, double eps,
+                                                  double* __restrict__ Lout, double* __restrict__ Gnu,
+                                                  DevScalars* sc) {
+  extern __shared__ double sh[];
+  __shared__ double red[33];
+  __shared__ int flag;
+  const int ld = r + 1, c = 2 * r;
+  double tr = 0.0;
+  for (int i = threadIdx.x; i < r; i += blockDim.x) tr += G[(int64_t)i * c + r + i];
+  tr = block_sum(tr, red);
+  double delta = eps * tr;
+  bool ok = false;
+  int attempt = 0;
+  for (; attempt < 4; ++attempt) {
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+      const int i = e / r, j = e % r;
+      const double oty = 0.5 * (G[(int64_t)i * c + r + j] + G[(int64_t)j * c + r + i]);
+      sh[i * ld + j] = oty + delta * G[(int64_t)i * c + j];
+    }
+    __syncthreads();
+    ok = chol_lower_smem(sh, r, ld, &flag);
+    __syncthreads();
+    if (ok) break;
+    delta *= 10.0;
+  }
+  if (!ok) {
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) sh[(e / r) * ld + e % r] = (e / r == e % r) ? 1.0 : 0.0;
+    if (threadIdx.x == 0) set_status(sc, ADASAP_ENUMERIC);
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e / r, j = e % r;
+    Lout[e] = (j <= i) ? sh[i * ld + j] : 0.0;
+    const double yty = G[(int64_t)(r + i) * c + r + j];
+    const double cross = G[(int64_t)i * c + r + j] + G[(int64_t)j * c + r + i];
+    Gnu[e] = yty + delta * cross + delta * delta * G[(int64_t)i * c + j];
+  }
+  if (threadIdx.x == 0) {
+    sc->delta = delta;
+    sc->chol_retries = attempt;
+  }
+}
+
+// Column-wise triangular solves with the lower factor L (r x r, row-major):
+//   upper == 0:  L X = R'     upper == 1:  L^T X = R'
+// where R' = trans ? R^T : R.  One warp per right-hand side column.
+__global__ void k_trsm(const double* __restrict__ L, int r, const double* __restrict__ R, int trans, int upper,
+                       double* __restrict__ X) {
+  extern __shared__ double xs[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (col >= r) return;
+  double* x = xs + warp * r;
+  for (int step = 0; step < r; ++step) {
+    const int i = upper ? r - 1 - step : step;
+    double part = 0.0;
+    if (!upper) {
+      for (int k = lane; k < i; k += 32) part += L[(int64_t)i * r + k] * x[k];
+    } else {
+      for (int k = i + 1 + lane; k < r; k += 32) part += L[(int64_t)k * r + i] * x[k];
+    }
+    part = warp_sum(part);
+    if (lane == 0) {
+      const double rhs = trans ? R[(int64_t)col * r + i] : R[(int64_t)i * r + col];
+      x[i] = (rhs - part) / L[(int64_t)i * r + i];
+    }
+    __syncwarp();
+  }
+  for (int i = lane; i < r; i += 32) X[(int64_t)i * r + col] = x[i];
+}
+
+static cudaError_t trsm(const double* L, int r, const double* R, int trans, int upper, double* X, cudaStream_t st) {
+  const int wpb = 2;
+  k_trsm<<<(r + wpb - 1) / wpb, 32 * wpb, wpb * r * sizeof(double), st>>>(L, r, R, trans, upper, X);
+  return cudaGetLastError();
+}
+
+// Cyclic Jacobi (parallel round-robin ordering) on the symmetric r x r matrix
+// A / max(diag A) in FP32, accumulating the rotations in V.  A rotation is
+// skipped when |a_pq| <= 1e-7 sqrt(|a_pp a_qq|); the sweeps stop when a sweep
+// skips all of them (at most 30 sweeps).
+__global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ A, int r, float* __restrict__ Vout) {
+  extern __shared__ float shf[];
+  const int r2 = r + (r & 1), ld = r2 + 1;
+  float* a = shf;
+  float* v = shf + r2 * ld;
+  __shared__ int pp[64], qq[64];
+  __shared__ float cc[64], ss[64];
+  __shared__ double red[33];
+  __shared__ int nrot;
+  double mx = 0.0;
+  for (int i = threadIdx.x; i < r; i += blockDim.x) mx = fmax(mx, fabs(A[(int64_t)i * r + i]));
+  // block max via shared memory
+  __shared__ double mxs[32];
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) mxs[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, mxs[w]);
+    red[0] = m > 0.0 ? m : 1.0;
+  }
+  __syncthreads();
+  const double scale = 1.0 / red[0];
+  for (int e = threadIdx.x; e < r2 * r2; e += blockDim.x) {
+    const int i = e / r2, j = e % r2;
+    a[i * ld + j] = (i < r && j < r) ? (float)(A[(int64_t)i * r + j] * scale) : 0.0f;
+    v[i * ld + j] = (i == j) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+  const int half = r2 / 2;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    if (threadIdx.x == 0) nrot = 0;
+    __syncthreads();
+    for (int round = 0; round < r2 - 1; ++round) {
+      if (threadIdx.x < half) {
+        const int m = threadIdx.x;
+        int p, q;
+        if (m == 0) { p = round; q = r2 - 1; }
+        else { p = (round + m) % (r2 - 1); q = (round - m + r2 - 1) % (r2 - 1); }
+        if (p > q) { const int t = p; p = q; q = t; }
+        const float apq = a[p * ld + q], app = a[p * ld + p], aqq = a[q * ld + q];
+        float c = 1.0f, s = 0.0f;
+        if (fabsf(apq) > 1e-7f * sqrtf(fabsf(app * aqq)) && fabsf(apq) > 1e-35f) {
+          const float tau = (aqq - app) / (2.0f * apq);
+          const float t = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+          c = 1.0f / sqrtf(1.0f + t * t);
+          s = t * c;
+          atomicAdd(&nrot, 1);
+        }
+        pp[m] = p; qq[m] = q; cc[m] = c; ss[m] = s;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < half * r2; e += blockDim.x) {
+        const int m = e / r2, k = e % r2;
+        const float c = cc[m], s = ss[m];
+        if (s == 0.0f) continue;
+        const int p = pp[m], q = qq[m];
+        const float akp = a[k * ld + p], akq = a[k * ld + q];
+        a[k * ld + p] = c * akp - s * akq;
+        a[k * ld + q] = s * akp + c * akq;
+        const float vkp = v[k * ld + p], vkq = v[k * ld + q];
+        v[k * ld + p] = c * vkp - s * vkq;
+        v[k * ld + q] = s * vkp + c * vkq;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < half * r2; e += blockDim.x) {
+        const int m = e / r2, k = e % r2;
+        const float c = cc[m], s = ss[m];
+        if (s == 0.0f) continue;
+        const int p = pp[m], q = qq[m];
+        const float apk = a[p * ld + k], aqk = a[q * ld + k];
+        a[p * ld + k] = c * apk - s * aqk;
+        a[q * ld + k] = s * apk + c * aqk;
+      }
+      __syncthreads();
+    }
+    if (nrot == 0) break;
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) Vout[e] = v[(e / r) * ld + (e % r)];
+}
+
+// lambda_i = v_i^T A v_i / v_i^T v_i in FP64 (one block per eigenvector)
+__global__ void k_rayleigh(const double* __restrict__ A, const float* __restrict__ V, int r, double* __restrict__ lam) {
+  __shared__ double red[33];
+  const int i = blockIdx.x;
+  double num = 0.0, den = 0.0;
+  for (int k = threadIdx.x; k < r; k += blockDim.x) {
+    double w = 0.0;
+    for (int j = 0; j < r; ++j) w += A[(int64_t)k * r + j] * (double)V[(int64_t)j * r + i];
+    const double vk = (double)V[(int64_t)k * r + i];
+    num += vk * w;
+    den += vk * vk;
+  }
+  num = block_sum(num, red);
+  den = block_sum(den, red);
+  if (threadIdx.x == 0) lam[i] = num / den;
+}
+
+// Sort eigenpairs (descending), S = max(0, Sigma^2 - Delta), rho = S_r + lambda,
+// and T' = V Sigma^{-1} (columns normalised) for U = Y_nu L^{-T} T'.
+__global__ void k_nys_finalize(const double* __restrict__ lam, const float* __restrict__ V, int r, double lam_reg,
+                               DevScalars* sc, double* __restrict__ S, double* __restrict__ keep,
+                               double* __restrict__ Tp) {
+  __shared__ int perm[kMaxRank];
+  __shared__ double sig[kMaxRank];
+  __shared__ double nrm[kMaxRank];
+  const double delta = sc->delta;
+  for (int i = threadIdx.x; i < r; i += blockDim.x) perm[i] = i;  // stays a valid index even if ranks collide (NaN)
+  __syncthreads();
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    const double li = lam[i];
+    int rank = 0;
+    for (int j = 0; j < r; ++j) {
+      const double lj = lam[j];
+      rank += (lj > li) || (lj == li && j < i);
+    }
+    if (rank < r) perm[rank] = i;
+    double n2 = 0.0;
+    for (int k = 0; k < r; ++k) n2 += (double)V[(int64_t)k * r + i] * (double)V[(int64_t)k * r + i];
+    nrm[i] = sqrt(n2);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < r; q += blockDim.x) {
+    const double li = lam[perm[q]];
+    const double sq = fmax(0.0, li - delta);
+    S[q] = sq;
+    keep[q] = sq > 0.0 ? 1.0 : 0.0;
+    sig[q] = li > 0.0 ? sqrt(li) : 0.0;
+    if (!isfinite(li)) set_status(sc, ADASAP_ENUMERIC);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sc->rho = S[r - 1] + lam_reg;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int k = e / r, q = e % r;
+    const int i = perm[q];
+    Tp[e] = sig[q] > 0.0 ? (double)V[(int64_t)k * r + i] / (nrm[i] * sig[q]) : 0.0;
+  }
+}
+
+// U = (Y + Delta Omega) T  (b x r): rows in blocks of 32, T in shared memory (FP32)
+__global__ void __launch_bounds__(256) k_make_u(const float* __restrict__ Om, const float* __restrict__ Ysk, int64_t b,
+                                                int r, const double* __restrict__ T, const DevScalars* sc,
+                                                float* __restrict__ U) {
+  extern __shared__ float shm[];
+  float* sT = shm;                  // r x r
+  float* sY = shm + r * r;          // 32 x r
+  const double delta = sc->delta;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) sT[e] = (float)T[e];
+  const int64_t row0 = (int64_t)blockIdx.x * 32;
+  for (int e = threadIdx.x; e < 32 * r; e += blockDim.x) {
+    const int rr = e / r, k = e % r;
+    const int64_t row = row0 + rr;
+    sY[e] = row < b ? (float)((double)Ysk[row * r + k] + delta * (double)Om[row * r + k]) : 0.0f;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int CQ = kMaxRank / 32;
+  float acc[4][CQ];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int q = 0; q < CQ; ++q) acc[u][q] = 0.0f;
+  for (int k = 0; k < r; ++k) {
+    float yv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) yv[u] = sY[(warp * 4 + u) * r + k];
+#pragma unroll
+    for (int q = 0; q < CQ; ++q) {
+      const int c = lane + 32 * q;
+      const float tv = c < r ? sT[k * r + c] : 0.0f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u][q] = fmaf(yv[u], tv, acc[u][q]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t row = row0 + warp * 4 + u;
+    if (row >= b) continue;
+#pragma unroll
+    for (int q = 0; q < CQ; ++q) {
+      const int c = lane + 32 * q;
+      if (c < r) U[row * r + c] = acc[u][q];
+    }
+  }
+}
+
+cudaError_t launch_nystrom_core(CoreBufs& cb, double eps, double lam, DevScalars* sc, const float* Om,
+                                const float* Ysk, cudaStream_t st) {
+  const int r = cb.r;
+  cudaError_t e;
+  // Gram of [Omega | M Omega] -> (Omega^T Omega, Omega^T Y, Y^T Y)
+  if ((e = launch_gram(Om, r, r, Ysk, r, r, cb.b, cb.gram_part, cb.gram_chunks, cb.G, st))) return e;
+  const size_t sm_chol = (size_t)r * (r + 1) * sizeof(double);
+  k_nys_chol<<<1, 512, sm_chol, st>>>(cb.G, r, eps, cb.Lc, cb.Gnu, sc);
+  // A = L^{-1} Gnu L^{-T}  (= C^{-T} Y_nu^T Y_nu C^{-1} = B^T B)
+  if ((e = trsm(cb.Lc, r, cb.Gnu, 0, 0, cb.X1, st))) return e;
+  if ((e = trsm(cb.Lc, r, cb.X1, 1, 0, cb.A, st))) return e;
+  const int r2 = r + (r & 1);
+  k_jacobi<<<1, 1024, (size_t)2 * r2 * (r2 + 1) * sizeof(float), st>>>(cb.A, r, cb.V32);
+  k_rayleigh<<<r, 128, 0, st>>>(cb.A, cb.V32, r, cb.lam);
+  k_nys_finalize<<<1, 256, 0, st>>>(cb.lam, cb.V32, r, lam, sc, cb.S, cb.keep, cb.X1);
+  // T = L^{-T} T'
+  if ((e = trsm(cb.Lc, r, cb.X1, 0, 1, cb.T, st))) return e;
+  k_make_u<<<(unsigned)((cb.b + 31) / 32), 256, (size_t)(r * r + 32 * r) * sizeof(float), st>>>(Om, Ysk, cb.b, r,
+                                                                                               cb.T, sc, cb.U);
+  return cudaGetLastError();
+}
+
+// L_w L_w^T = rho S^{-1} + U^T U on the kept eigenpairs (App. C.2, stabilised form)
+__global__ void __launch_bounds__(512) k_wchol(const double* __restrict__ UtU, int r, const double* __restrict__ S,
+                                               const double* __restrict__ keep, DevScalars* sc,
+                                               double* __restrict__ Lw) {
+  extern __shared__ double sh[];
+  __shared__ int flag;
+  const int ld = r + 1;
+  const double rho = sc->rho;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e / r, j = e % r;
+    double v = keep[i] * keep[j] * UtU[e];
+    if (i == j) v += keep[i] > 0.0 ? rho / S[i] : 1.0;
+    sh[i * ld + j] = v;
+  }
+  __syncthreads();
+  const bool ok = chol_lower_smem(sh, r, ld, &flag);
+  __syncthreads();
+  if (!ok && threadIdx.x == 0) set_status(sc, ADASAP_ENUMERIC);
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e / r, j = e % r;
+    Lw[e] = ok ? ((j <= i) ? sh[i * ld + j] : 0.0) : (i == j ? 1.0 : 0.0);
+  }
+}
+
+cudaError_t launch_woodbury_factor(CoreBufs& cb, double lam, DevScalars* sc, cudaStream_t st) {
+  (void)lam;
+  const int r = cb.r;
+  cudaError_t e;
+  if ((e = launch_gram(cb.U, r, r, nullptr, 0, 0, cb.b, cb.gram_part, cb.gram_chunks, cb.X1, st))) return e;
+  k_wchol<<<1, 512, (size_t)r * (r + 1) * sizeof(double), st>>>(cb.X1, r, cb.S, cb.keep, sc, cb.Lw);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Woodbury applies.
+// ---------------------------------------------------------------------------
+int utv_chunks_for(int64_t b) { return (int)std::max<int64_t>(1, std::min<int64_t>(148, (b + 127) / 128)); }
+
+// part[ch][o], o = k*s + c: sum over the rows i of chunk ch of U[i][k] v[i][c].
+// blockIdx.y selects a group of 2048 outputs (8 per thread).
+constexpr int kUtvOut = 8;
+__global__ void __launch_bounds__(256) k_utv(const float* __restrict__ U, int64_t b, int r, const float* __restrict__ v,
+                                             int s, int64_t ldv, int64_t chunk_rows, double* __restrict__ part) {
+  extern __shared__ float shm[];
+  float* su = shm;           // 32 x r
+  float* sv = shm + 32 * r;  // 32 x s
+  const int64_t r0 = (int64_t)blockIdx.x * chunk_rows;
+  const int64_t r1 = min(b, r0 + chunk_rows);
+  const int nout = r * s;
+  const int obase = blockIdx.y * 256 * kUtvOut;
+  double acc[kUtvOut];
+#pragma unroll
+  for (int q = 0; q < kUtvOut; ++q) acc[q] = 0.0;
+  for (int64_t s0 = r0; s0 < r1; s0 += 32) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * r; e += blockDim.x) {
+      const int64_t row = s0 + e / r;
+      su[e] = row < r1 ? U[row * r + e % r] : 0.0f;
+    }
+    for (int e = threadIdx.x; e < 32 * s; e += blockDim.x) {
+      const int64_t row = s0 + e / s;
+      sv[e] = row < r1 ? v[row * ldv + e % s] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kUtvOut; ++q) {
+      const int o = obase + threadIdx.x + 256 * q;
+      if (o < nout) {
+        const int k = o / s, c = o % s;
+        float f = 0.0f;
+        for (int rr = 0; rr < 32; ++rr) f = fmaf(su[rr * r + k], sv[rr * s + c], f);
+        acc[q] += (double)f;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kUtvOut; ++q) {
+    const int o = obase + threadIdx.x + 256 * q;
+    if (o < nout) part[(int64_t)blockIdx.x * nout + o] = acc[q];
+  }
+}
+
+// Small FP64 step between U^T v and the apply.  alpha[0] = coefficient of v,
+// alpha[1] = 1/||v|| of the input (normalised mode).
+__global__ void __launch_bounds__(256) k_wcoef(int mode, const double* __restrict__ part, int chunks, int r, int s,
+                                               const double* __restrict__ S, const double* __restrict__ keep,
+                                               const double* __restrict__ Lw, const double* __restrict__ sq_part,
+                                               DevScalars* sc, float* __restrict__ coef, double* __restrict__ alpha) {
+  extern __shared__ double q[];  // r x s
+  __shared__ double red[33];
+  const double rho = sc->rho;
+  double scale = 1.0;
+  if (mode == kInvSqrtNormalised) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i < kReduceBlocks; i += blockDim.x) t += sq_part[i];
+    t = block_sum(t, red);
+    scale = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+  }
+  const int nout = r * s;
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    double acc = 0.0;
+    for (int ch = 0; ch < chunks; ++ch) acc += part[(int64_t)ch * nout + o];
+    q[o] = acc;
+  }
+  __syncthreads();
+  if (mode == kInv) {
+    // y = L^{-T} L^{-1} (keep . q), one thread per column
+    for (int c = threadIdx.x; c < s; c += blockDim.x) {
+      for (int i = 0; i < r; ++i) {
+        double acc = keep[i] * q[i * s + c];
+        for (int k = 0; k < i; ++k) acc -= Lw[i * r + k] * q[k * s + c];
+        q[i * s + c] = acc / Lw[i * r + i];
+      }
+      for (int i = r - 1; i >= 0; --i) {
+        double acc = q[i * s + c];
+        for (int k = i + 1; k < r; ++k) acc -= Lw[k * r + i] * q[k * s + c];
+        q[i * s + c] = acc / Lw[i * r + i];
+      }
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) coef[o] = (float)(-keep[o / s] * q[o] / rho);
+    if (threadIdx.x == 0) alpha[0] = 1.0 / rho;
+  } else {
+    const double irs = 1.0 / sqrt(rho);
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+      const int k = o / s;
+      coef[o] = (float)(scale * q[o] * (1.0 / sqrt(S[k] + rho) - irs));
+    }
+    if (threadIdx.x == 0) {
+      alpha[0] = scale * irs;
+      if (mode == kInvSqrtNormalised) alpha[1] = scale;
+    }
+  }
+}
+
+// out[i][c] = alpha v[i][c] + sum_k U[i][k] coef[k][c]; optional per-block
+// partials of sum(out^2) and sum(out * dotv) (s == 1).
+__global__ void __launch_bounds__(256) k_wapply(const float* __restrict__ U, int64_t b, int r, const float* __restrict__ v,
+                                                int s, const float* __restrict__ coef, const double* __restrict__ alpha,
+                                                float* __restrict__ out, double* sq_part, double* dot_part,
+                                                const float* __restrict__ dotv) {
+  extern __shared__ float scoef[];  // r x s
+  __shared__ double red[33];
+  for (int e = threadIdx.x; e < r * s; e += blockDim.x) scoef[e] = coef[e];
+  __syncthreads();
+  const float al = (float)alpha[0];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+  double sq = 0.0, dt = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; i < b; i += wstride) {
+    if (s == 1) {
+      float acc = 0.0f;
+      for (int k = lane; k < r; k += 32) acc = fmaf(U[i * r + k], scoef[k], acc);
+      acc = warp_sum(acc);
+      const float o = fmaf(al, v[i], acc);
+      if (lane == 0) {
+        out[i] = o;
+        sq += (double)o * (double)o;
+        if (dotv) dt += (double)o * (double)dotv[i];
+      }
+    } else {
+      for (int c = lane; c < s; c += 32) {
+        float acc = 0.0f;
+        for (int k = 0; k < r; ++k) acc = fmaf(U[i * r + k], scoef[k * s + c], acc);
+        out[i * s + c] = fmaf(al, v[i * s + c], acc);
+      }
+    }
+  }
+  if (sq_part) {
+    const double t = block_sum(sq, red);
+    if (threadIdx.x == 0) sq_part[blockIdx.x] = t;
+  }
+  if (dot_part) {
+    const double t = block_sum(dt, red);
+    if (threadIdx.x == 0) dot_part[blockIdx.x] = t;
+  }
+}
+
+// identity preconditioner (ADASAP-I): out = alpha v with alpha = 1 or 1/||v||
+__global__ void k_iapply(int normalised, const float* __restrict__ v, int64_t count, const double* __restrict__ sq_in,
+                         float* __restrict__ out, double* __restrict__ alpha, double* sq_part, double* dot_part,
+                         const float* __restrict__ dotv) {
+  __shared__ double red[33];
+  __shared__ double sscale;
+  if (threadIdx.x == 0) sscale = 1.0;
+  __syncthreads();
+  if (normalised) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i < kReduceBlocks; i += blockDim.x) t += sq_in[i];
+    t = block_sum(t, red);
+    if (threadIdx.x == 0) sscale = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+    __syncthreads();
+  }
+  const double scale = sscale;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    alpha[0] = scale;
+    if (normalised) alpha[1] = scale;
+  }
+  double sq = 0.0, dt = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const float o = (float)(scale * (double)v[i]);
+    out[i] = o;
+    sq += (double)o * (double)o;
+    if (dotv) dt += (double)o * (double)dotv[i];
+  }
+  if (sq_part) {
+    const double t = block_sum(sq, red);
+    if (threadIdx.x == 0) sq_part[blockIdx.x] = t;
+  }
+  if (dot_part) {
+    const double t = block_sum(dt, red);
+    if (threadIdx.x == 0) dot_part[blockIdx.x] = t;
+  }
+}
+
+cudaError_t launch_woodbury_apply(CoreBufs& cb, int mode, const float* v, int s, float* out, bool want_sq,
+                                  bool want_dot, const float* dotv, DevScalars* sc, cudaStream_t st) {
+  double* sqp = want_sq ? cb.sq_part : nullptr;
+  double* dtp = want_dot ? cb.dot_part : nullptr;
+  if (cb.r == 0) {  // identity preconditioner
+    k_iapply<<<kReduceBlocks, 256, 0, st>>>(mode == kInvSqrtNormalised, v, cb.b * s, cb.sq_part, out, cb.alpha, sqp,
+                                            dtp, dotv);
+    return cudaGetLastError();
+  }
+  const int r = cb.r;
+  const int64_t chunk_rows = (cb.b + cb.utv_chunks - 1) / cb.utv_chunks;
+  const int ogroups = (r * s + 256 * kUtvOut - 1) / (256 * kUtvOut);
+  k_utv<<<dim3(cb.utv_chunks, ogroups), 256, (size_t)(32 * r + 32 * s) * sizeof(float), st>>>(cb.U, cb.b, r, v, s, s,
+                                                                                               chunk_rows, cb.utv_part);
+  k_wcoef<<<1, 256, (size_t)r * s * sizeof(double), st>>>(mode, cb.utv_part, cb.utv_chunks, r, s, cb.S, cb.keep,
+                                                          cb.Lw, cb.sq_part, sc, cb.coef, cb.alpha);
+  k_wapply<<<kReduceBlocks, 256, (size_t)r * s * sizeof(float), st>>>(cb.U, cb.b, r, v, s, cb.coef, cb.alpha, out,
+                                                                       sqp, dtp, dotv);
+  return cudaGetLastError();
+}
+
+// eta = 1 / lambda_hat, lambda_hat = (1/||v_{N-1}||) * sum(w_N . v_{N-1}) (Alg. 5,
+// Rayleigh-quotient reading).  A failed factorisation (status != 0) gives eta = 0.
+__global__ void k_set_eta(const double* __restrict__ dot_part, const double* __restrict__ alpha, DevScalars* sc) {
+  __shared__ double red[33];
+  double t = 0.0;
+  for (int i = threadIdx.x; i < kReduceBlocks; i += blockDim.x) t += dot_part[i];
+  t = block_sum(t, red);
+  if (threadIdx.x == 0) {
+    const double lam_hat = alpha[1] * t;
+    sc->lam_hat = lam_hat;
+    double eta = (lam_hat > 0.0 && isfinite(lam_hat)) ? 1.0 / lam_hat : 0.0;
+    if (!(lam_hat > 0.0 && isfinite(lam_hat))) set_status(sc, ADASAP_ENUMERIC);
+    if (sc->status != 0) eta = 0.0;
+    sc->eta = eta;
+  }
+}
+
+cudaError_t launch_set_eta(CoreBufs& cb, DevScalars* sc, int identity, cudaStream_t st) {
+  (void)identity;
+  k_set_eta<<<1, 256, 0, st>>>(cb.dot_part, cb.alpha, sc);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// NesterovAcc (Alg. 6) as a dense pass over all n x s entries followed by the
+// correction of the b rows of the block (the direction is zero elsewhere):
+//   dense:   W' = Z;  V' = beta V + (1 - beta) Z;  Z' = alpha V'' + (1 - alpha) W'
+//            with V'' = V' (standard) or V (literal)
+//   scatter: W' -= eta D;  V' -= gamma eta D;
+//            Z' -= (alpha gamma eta + (1 - alpha) eta) D   (standard)
+//            Z' -= (1 - alpha) eta D                       (literal)
+// ---------------------------------------------------------------------------
+__global__ void k_nesterov(float* __restrict__ W, float* __restrict__ V, float* __restrict__ Z, int64_t count,
+                           float beta, float alpha, int literal) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    const float z = Z[e], v = V[e];
+    const float v1 = fmaf(beta, v, (1.0f - beta) * z);
+    const float vz = literal ? v : v1;
+    W[e] = z;
+    V[e] = v1;
+    Z[e] = fmaf(alpha, vz, (1.0f - alpha) * z);
+  }
+}
+
+cudaError_t launch_nesterov(float* W, float* V, float* Z, int64_t count, float beta, float alpha, int literal,
+                            cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((count + 255) / 256, 148 * 16);
+  k_nesterov<<<blocks, 256, 0, st>>>(W, V, Z, count, beta, alpha, literal);
+  return cudaGetLastError();
+}
+
+__global__ void k_scatter(float* __restrict__ W, float* __restrict__ V, float* __restrict__ Z, const int* __restrict__ B,
+                          int64_t b, int s, const float* __restrict__ D, float gamma, float alpha, int literal,
+                          const DevScalars* sc) {
+  const double eta = sc->eta;
+  const float fw = (float)eta;
+  const float fv = (float)(gamma * eta);
+  const float fz = literal ? (float)((1.0 - alpha) * eta) : (float)(alpha * gamma * eta + (1.0 - alpha) * eta);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < b * s; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / s;
+    const int c = (int)(e - i * s);
+    const int64_t j = (int64_t)B[i] * s + c;
+    const float d = D[e];
+    W[j] = fmaf(-fw, d, W[j]);
+    V[j] = fmaf(-fv, d, V[j]);
+    Z[j] = fmaf(-fz, d, Z[j]);
+  }
+}
+
+cudaError_t launch_scatter(float* W, float* V, float* Z, const int* B, int64_t b, int s, const float* D, float gamma,
+                           float alpha, int literal, DevScalars* sc, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((b * s + 255) / 256, 148 * 8);
+  k_scatter<<<std::max(blocks, 1), 256, 0, st>>>(W, V, Z, B, b, s, D, gamma, alpha, literal, sc);
+  return cudaGetLastError();
+}
+
+__global__ void k_sum_blocks(const double* __restrict__ parts, int count, double* dst) {
+  __shared__ double red[33];
+  double t = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) t += parts[i];
+  t = block_sum(t, red);
+  if (threadIdx.x == 0) *dst = t;
+}
+
+cudaError_t launch_sum_blocks(const double* parts, int count, double* dst, cudaStream_t st) {
+  k_sum_blocks<<<1, 256, 0, st>>>(parts, count, dst);
+  return cudaGetLastError();
+}
+
+__global__ void k_trace(DevScalars* sc, double* trace) {
+  const long long t = sc->t;
+  trace[2 * t] = sc->eta;
+  trace[2 * t + 1] = sc->rho;
+}
+cudaError_t launch_trace(DevScalars* sc, double* trace, cudaStream_t st) {
+  k_trace<<<1, 1, 0, st>>>(sc, trace);
+  return cudaGetLastError();
+}
+
+__global__ void k_tick(DevScalars* sc) { sc->t += 1; }
+cudaError_t launch_tick(DevScalars* sc, cudaStream_t st) {
+  k_tick<<<1, 1, 0, st>>>(sc);
+  return cudaGetLastError();
+}
+
+cudaError_t core_init() {
+  const int big = 200 * 1024;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_nys_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_make_u, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_wchol, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_wcoef, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_wapply, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  return cudaSuccess;
+}
+
+}  // namespace adasap

@@ -1,0 +1,127 @@
+// Internal launchers of the ADASAP CUDA path.  Host code in solver.cu composes
+// them; each launcher is defined next to its kernels.
+#pragma once
+#include "common.cuh"
+
+namespace adasap {
+
+constexpr int kMaxRank = 128;   // r <= 128 (one CTA holds r x r FP64 in shared memory)
+constexpr int kMaxRhs = 128;    // s <= 128
+constexpr int kMaxDim = 64;     // d <= 64
+
+// Padded feature width used for the device copy of X (multiple of 4).
+int padded_dim(int d);
+// kappa of the pre-scaling x' = kappa (x - mean) / ell (see common.cuh).
+double kernel_kappa(int kern);
+
+// Operand description of one kernel-times-matrix product
+//   part[p][i][:] = sigma2 * sum_{j in split p} k(x'_{row i}, x'_j) * w[j][:]
+// Rows: row i has data xr[src*DP .. +DP) and squared norm qr[src] with
+// src = ridx ? ridx[i] : i (ridx[i] < 0 marks an invalid row: NaN output).
+// Columns: xc (ncols x DP), qc (ncols).  W rows are indexed like columns.
+struct RowsArgs {
+  const float* xr;
+  const float* qr;
+  const int* ridx;
+  int64_t m;
+  const float* xc;
+  const float* qc;
+  int64_t ncols;
+  const float* w;
+  int64_t ldw;
+  float* part;
+  int64_t cps;  // columns per split
+  float sigma2;
+};
+
+// Number of column splits for an m-row product (fills the GPU without a tail).
+int rows_nsplit(int64_t m, int64_t ncols, int s, int dp, bool adjoint);
+// Launch the fused distance + kernel epilogue + contraction (K1/K2 engine).
+// s <= 4 (or adjoint): register-blocked narrow kernel; otherwise the
+// tiled kernel with a shared-memory kernel tile.  part: nsplit x m x s
+// (x 2s for the adjoint: [k-sums | g-sums]).
+cudaError_t launch_rows(int kern, int dp, const RowsArgs& a, int s, int nsplit, bool adjoint,
+                        cudaStream_t st);
+// out[i*ldo + c] = sum_p part[(p*m + i)*na + coff + c] + beta*A[ai*lda + c] + gamma*B[bi*ldb + c]
+// (ai = aidx ? aidx[i] : i, same for bi); FP64 sums.  If blocksq != NULL each of
+// kReduceBlocks blocks writes its sum of out^2 there.
+constexpr int kReduceBlocks = 296;
+cudaError_t launch_reduce(const float* part, int nsplit, int64_t m, int na, int coff, int s,
+                          float* out, int64_t ldo, float beta, const float* A, const int* aidx,
+                          int64_t lda, float gamma, const float* B, const int* bidx, int64_t ldb,
+                          double* blocksq, cudaStream_t st);
+// out rows i < m: x'[idx[i]] (DP floats) and q[idx[i]]
+cudaError_t launch_gather(const float* X, const float* q, const int* idx, int64_t m, int dp,
+                          float* out, float* qout, cudaStream_t st);
+// Column sums (FP64) of raw X (n x d): per-block partials [nb][d].
+constexpr int kColsumBlocks = 148;
+cudaError_t launch_colsum(const float* X, int64_t n, int d, double* partials, cudaStream_t st);
+// x' = kappa (x - mean) / ell, padded to dp; q = ||x'||^2 (FP64 then rounded).
+cudaError_t launch_transform(const float* X, int64_t n, int d, int dp, const double* mean_dev,
+                             double scale, float* out, float* q, cudaStream_t st);
+// int64 indices -> int32, entries outside [0, n) become -1.
+cudaError_t launch_index32(const int64_t* in, int64_t m, int64_t n, int* out, cudaStream_t st);
+
+// ---- sampler (Philox4x32-10; definitions in sampler.cu) -------------------------
+cudaError_t launch_sample_block(uint64_t seed, const long long* t_dev, int64_t t_host, int64_t n,
+                                int64_t b, int stream_tag, int* B32, int64_t* B64, cudaStream_t st);
+cudaError_t launch_normals(uint64_t seed, const long long* t_dev, int64_t t_host, int64_t count,
+                           int stream_tag, float scale, float* out, cudaStream_t st);
+// Copy iteration t (read from t_dev) of a schedule into the working buffers.
+cudaError_t launch_copy_schedule(const int64_t* Bs, const float* Om_s, const float* v0s,
+                                 const long long* t_dev, int64_t n, int64_t b, int r, int* B32,
+                                 float* Om, float* v0, DevScalars* sc, cudaStream_t st);
+
+// ---- Nystrom core, Woodbury, Nesterov (core.cu) ---------------------------------
+struct CoreBufs {
+  int r, s;
+  int64_t b;
+  // Gram workspace
+  double* gram_part;  // [gram_chunks][2r][2r]
+  int gram_chunks;
+  double* G;          // 2r x 2r
+  double* Lc;         // r x r lower Cholesky of the Nystrom core
+  double* Gnu;        // r x r  Y_nu^T Y_nu
+  double* X1;         // r x r  scratch
+  double* A;          // r x r  B^T B
+  float* V32;         // r x r  eigenvectors (FP32 Jacobi)
+  double* lam;        // r      Rayleigh quotients
+  double* T;          // r x r  U = Y_nu T
+  double* S;          // r      Nystrom eigenvalues (descending)
+  double* keep;       // r      1 if S_i > 0 else 0
+  double* Lw;         // r x r  Cholesky of rho S^-1 + U^T U
+  float* U;           // b x r
+  double* utv_part;   // [utv_chunks][r][s]
+  int utv_chunks;
+  float* coef;        // r x s
+  double* sq_part;    // [kReduceBlocks] sums of squares / dots
+  double* dot_part;   // [kReduceBlocks]
+  double* alpha;      // scalar apply coefficient
+};
+int gram_chunks_for(int64_t b);
+int utv_chunks_for(int64_t b);
+cudaError_t launch_gram(const float* A1, int64_t ld1, int c1, const float* A2, int64_t ld2, int c2,
+                        int64_t m, double* part, int chunks, double* G, cudaStream_t st);
+cudaError_t launch_nystrom_core(CoreBufs& cb, double eps, double lam, DevScalars* sc,
+                                const float* Om, const float* Ysk, cudaStream_t st);
+cudaError_t launch_woodbury_factor(CoreBufs& cb, double lam, DevScalars* sc, cudaStream_t st);
+// P^{-1/2}-type or P^{-1}-type apply of App. C.2 in three launches:
+//   utv: part = U^T v (per chunk); coef: small FP64 work; apply: out = alpha v + U coef.
+enum ApplyMode { kInvSqrt = 0, kInvSqrtNormalised = 1, kInv = 2 };
+cudaError_t launch_woodbury_apply(CoreBufs& cb, int mode, const float* v, int s, float* out,
+                                  bool want_sq, bool want_dot, const float* dotv, DevScalars* sc,
+                                  cudaStream_t st);
+cudaError_t launch_set_eta(CoreBufs& cb, DevScalars* sc, int identity, cudaStream_t st);
+cudaError_t launch_nesterov(float* W, float* V, float* Z, int64_t count, float beta, float alpha,
+                            int literal, cudaStream_t st);
+cudaError_t launch_scatter(float* W, float* V, float* Z, const int* B, int64_t b, int s,
+                           const float* D, float gamma, float alpha, int literal, DevScalars* sc,
+                           cudaStream_t st);
+cudaError_t launch_sum_blocks(const double* parts, int count, double* dst, cudaStream_t st);
+cudaError_t launch_trace(DevScalars* sc, double* trace, cudaStream_t st);
+cudaError_t launch_tick(DevScalars* sc, cudaStream_t st);
+cudaError_t launch_scale_copy(const float* src, float* dst, int64_t count, cudaStream_t st);
+cudaError_t launch_adj_reduce(const float* part, int nsplit, int64_t m, int s, const float* G,
+                              int64_t ldg, int coff, double* blockacc, cudaStream_t st);
+
+}  // namespace adasap

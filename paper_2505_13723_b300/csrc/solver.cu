@@ -1,0 +1,730 @@
+// C-ABI entry points (include/adasap.h): context set-up, the block-row product,
+// the ADASAP iteration (Alg. 2) captured once as a CUDA graph and replayed,
+// the posterior mean, the hyperparameter adjoint and the device sampler.
+//
+// One iteration is a two-branch graph:
+//   sample B, Omega, v0 -> gather X_B
+//   branch 1 (high-priority stream): sketch K_BB Omega (Step II), Nystrom core
+//            (Alg. 4), Woodbury factor, randomized powering (Alg. 5) -> eta
+//   branch 2: block residual K_Bn Z + lambda Z_B - Y_B (Step I)
+//   join -> direction P^{-1} R (App. C.2) -> NesterovAcc (Alg. 6) -> t += 1
+// The branches are independent given B and Omega, so the latency-bound FP64
+// core runs in the shadow of the throughput-bound Step I.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace adasap;
+
+namespace adasap {
+cudaError_t core_init();
+}
+
+static thread_local std::string g_last_error;
+
+static void note_error(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+}
+
+#define CT(x)                      \
+  do {                             \
+    cudaError_t e_ = (x);          \
+    if (e_ != cudaSuccess) {       \
+      note_error(e_, #x);          \
+      return ADASAP_ECUDA;         \
+    }                              \
+  } while (0)
+
+struct adasap_ctx {
+  int device = 0;
+  int64_t n = 0;
+  int d = 0, dp = 0, kern = 0;
+  float ell = 1.f, sigma2 = 1.f, lambda = 1.f;
+  double kappa = 1.0;
+  float* Xc = nullptr;      // n x dp, x' = kappa (x - mean) / ell
+  float* qc = nullptr;      // n, ||x'||^2
+  double* mean_dev = nullptr;
+  cudaStream_t s0 = nullptr, s1 = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_fork = nullptr, ev_join = nullptr, ev_out = nullptr;
+  cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
+  DevScalars* sc = nullptr;
+  DevScalars* sc_host = nullptr;  // pinned
+  void* ws = nullptr;             // kernel_rows workspace
+  size_t ws_bytes = 0;
+};
+
+namespace {
+
+// Device allocations of one call, freed together.
+struct Arena {
+  std::vector<void*> ptrs;
+  cudaError_t err = cudaSuccess;
+  template <class T>
+  T* get(size_t count) {
+    if (count == 0) count = 1;
+    void* p = nullptr;
+    const cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      if (err == cudaSuccess) err = e;
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    return static_cast<T*>(p);
+  }
+  ~Arena() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+};
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes attr;
+  const cudaError_t e = cudaPointerGetAttributes(&attr, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+adasap_status order_after(cudaStream_t user, cudaEvent_t ev, cudaStream_t mine) {
+  CT(cudaEventRecord(ev, user));
+  CT(cudaStreamWaitEvent(mine, ev, 0));
+  return ADASAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void adasap_default_opts(adasap_opts* o, int64_t n) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->b = n >= 100 ? n / 100 : (n > 0 ? n : 1);
+  o->r = (int)std::min<int64_t>(std::min<int64_t>(100, o->b), kMaxRank);
+  o->max_iters = 1000;
+  o->tol = 0.0;
+  o->power_iters = 10;
+  o->mu = 0.0;
+  o->nu = 0.0;
+  o->precond = 0;
+  o->literal = 0;
+  o->seed = 0;
+  o->check_every = 10;
+  o->check_rows = 65536;
+  o->eps = 0.0;
+}
+
+const char* adasap_status_string(adasap_status s) {
+  switch (s) {
+    case ADASAP_OK: return "ok";
+    case ADASAP_EINVAL: return "invalid argument";
+    case ADASAP_ENOMEM: return "device allocation failed";
+    case ADASAP_ECUDA: return "CUDA runtime error";
+    case ADASAP_ENUMERIC: return "Cholesky of an r x r core failed";
+    case ADASAP_EDIVERGED: return "residual diverged";
+    case ADASAP_ETIMEOUT: return "bounded device wait timed out";
+    case ADASAP_ENOTCONVERGED: return "tolerance not reached within max_iters";
+  }
+  return "unknown status";
+}
+
+const char* adasap_last_error(void) { return g_last_error.c_str(); }
+
+adasap_status adasap_create(const float* X, int64_t n, int d, int kernel, float ell, float sigma2, float lambda,
+                            void* stream, adasap_ctx** out) {
+  if (!out || !X || n < 1 || n >= (1LL << 31) || d < 1 || d > kMaxDim || kernel < 0 || kernel > 2 ||
+      !(ell > 0.f) || !(sigma2 > 0.f) || !(lambda > 0.f))
+    return ADASAP_EINVAL;
+  *out = nullptr;
+  adasap_ctx* c = new (std::nothrow) adasap_ctx();
+  if (!c) return ADASAP_ENOMEM;
+  auto fail = [&](adasap_status s) {
+    adasap_destroy(c);
+    return s;
+  };
+  cudaStream_t us = (cudaStream_t)stream;
+  if (cudaGetDevice(&c->device) != cudaSuccess) return fail(ADASAP_ECUDA);
+  if (core_init() != cudaSuccess) { note_error(cudaGetLastError(), "core_init"); return fail(ADASAP_ECUDA); }
+  c->n = n;
+  c->d = d;
+  c->dp = padded_dim(d);
+  c->kern = kernel;
+  c->ell = ell;
+  c->sigma2 = sigma2;
+  c->lambda = lambda;
+  c->kappa = kernel_kappa(kernel);
+  int lo = 0, hi = 0;
+  if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) return fail(ADASAP_ECUDA);
+  if (cudaStreamCreateWithPriority(&c->s0, cudaStreamNonBlocking, lo) != cudaSuccess) return fail(ADASAP_ECUDA);
+  if (cudaStreamCreateWithPriority(&c->s1, cudaStreamNonBlocking, hi) != cudaSuccess) return fail(ADASAP_ECUDA);
+  cudaEvent_t* evs[] = {&c->ev_in, &c->ev_fork, &c->ev_join, &c->ev_out};
+  for (cudaEvent_t* e : evs)
+    if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return fail(ADASAP_ECUDA);
+  if (cudaEventCreate(&c->ev_t0) != cudaSuccess || cudaEventCreate(&c->ev_t1) != cudaSuccess)
+    return fail(ADASAP_ECUDA);
+  if (cudaMalloc(&c->Xc, (size_t)n * c->dp * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&c->qc, (size_t)n * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&c->mean_dev, (size_t)d * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->sc, sizeof(DevScalars)) != cudaSuccess ||
+      cudaMallocHost(&c->sc_host, sizeof(DevScalars)) != cudaSuccess)
+    return fail(ADASAP_ENOMEM);
+  if (order_after(us, c->ev_in, c->s0) != ADASAP_OK) return fail(ADASAP_ECUDA);
+  {
+    Arena ar;
+    const float* Xd = X;
+    if (!is_device_ptr(X)) {
+      float* tmp = ar.get<float>((size_t)n * d);
+      if (!tmp) return fail(ADASAP_ENOMEM);
+      if (cudaMemcpyAsync(tmp, X, (size_t)n * d * sizeof(float), cudaMemcpyHostToDevice, c->s0) != cudaSuccess)
+        return fail(ADASAP_ECUDA);
+      Xd = tmp;
+    }
+    double* parts = ar.get<double>((size_t)kColsumBlocks * d);
+    if (!parts) return fail(ADASAP_ENOMEM);
+    if (launch_colsum(Xd, n, d, parts, c->s0) != cudaSuccess) return fail(ADASAP_ECUDA);
+    std::vector<double> hp((size_t)kColsumBlocks * d), mean(d, 0.0);
+    if (cudaMemcpyAsync(hp.data(), parts, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s0) != cudaSuccess ||
+        cudaStreamSynchronize(c->s0) != cudaSuccess)
+      return fail(ADASAP_ECUDA);
+    for (int b = 0; b < kColsumBlocks; ++b)
+      for (int k = 0; k < d; ++k) mean[k] += hp[(size_t)b * d + k];
+    for (int k = 0; k < d; ++k) mean[k] /= (double)n;
+    if (cudaMemcpyAsync(c->mean_dev, mean.data(), d * sizeof(double), cudaMemcpyHostToDevice, c->s0) != cudaSuccess)
+      return fail(ADASAP_ECUDA);
+    if (launch_transform(Xd, n, d, c->dp, c->mean_dev, c->kappa / (double)ell, c->Xc, c->qc, c->s0) != cudaSuccess)
+      return fail(ADASAP_ECUDA);
+    if (cudaStreamSynchronize(c->s0) != cudaSuccess) return fail(ADASAP_ECUDA);
+  }
+  *out = c;
+  return ADASAP_OK;
+}
+
+void adasap_destroy(adasap_ctx* c) {
+  if (!c) return;
+  if (c->s0) cudaStreamSynchronize(c->s0);
+  if (c->s1) cudaStreamSynchronize(c->s1);
+  cudaFree(c->Xc);
+  cudaFree(c->qc);
+  cudaFree(c->mean_dev);
+  cudaFree(c->sc);
+  cudaFree(c->ws);
+  if (c->sc_host) cudaFreeHost(c->sc_host);
+  cudaEvent_t evs[] = {c->ev_in, c->ev_fork, c->ev_join, c->ev_out, c->ev_t0, c->ev_t1};
+  for (cudaEvent_t e : evs)
+    if (e) cudaEventDestroy(e);
+  if (c->s0) cudaStreamDestroy(c->s0);
+  if (c->s1) cudaStreamDestroy(c->s1);
+  delete c;
+}
+
+}  // extern "C"
+
+namespace {
+
+RowsArgs rows_over_x(const adasap_ctx* c, const float* xr, const float* qr, const int* ridx, int64_t m,
+                     const float* w, int64_t ldw, float* part) {
+  RowsArgs a;
+  a.xr = xr;
+  a.qr = qr;
+  a.ridx = ridx;
+  a.m = m;
+  a.xc = c->Xc;
+  a.qc = c->qc;
+  a.ncols = c->n;
+  a.w = w;
+  a.ldw = ldw;
+  a.part = part;
+  a.cps = 0;
+  a.sigma2 = c->sigma2;
+  return a;
+}
+
+adasap_status grow_ws(adasap_ctx* c, size_t bytes) {
+  if (bytes <= c->ws_bytes) return ADASAP_OK;
+  cudaFree(c->ws);
+  c->ws = nullptr;
+  c->ws_bytes = 0;
+  if (cudaMalloc(&c->ws, bytes) != cudaSuccess) return ADASAP_ENOMEM;
+  c->ws_bytes = bytes;
+  return ADASAP_OK;
+}
+
+}  // namespace
+
+extern "C" adasap_status adasap_kernel_rows(adasap_ctx* c, const int64_t* B, int64_t b, const float* W, int s,
+                                            float* out, void* stream) {
+  if (!c || !B || !W || !out || b < 1 || b >= (1LL << 31) || s < 1 || s > kMaxRhs) return ADASAP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nsplit = rows_nsplit(b, c->n, s, c->dp, false);
+  const size_t idx_bytes = ((size_t)b * sizeof(int) + 255) & ~(size_t)255;
+  const size_t part_bytes = (size_t)nsplit * b * s * sizeof(float);
+  const adasap_status g = grow_ws(c, idx_bytes + part_bytes);
+  if (g != ADASAP_OK) return g;
+  int* idx = (int*)c->ws;
+  float* part = (float*)((char*)c->ws + idx_bytes);
+  CT(launch_index32(B, b, c->n, idx, st));
+  CT(launch_rows(c->kern, c->dp, rows_over_x(c, c->Xc, c->qc, idx, b, W, s, part), s, nsplit, false, st));
+  CT(launch_reduce(part, nsplit, b, s, 0, s, out, s, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, nullptr, st));
+  return ADASAP_OK;
+}
+
+extern "C" adasap_status adasap_predict(adasap_ctx* c, const float* Xtest, int64_t m, const float* W, int s,
+                                        float* out, void* stream) {
+  if (!c || !Xtest || !W || !out || m < 1 || m >= (1LL << 31) || s < 1 || s > kMaxRhs) return ADASAP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Arena ar;
+  const int nsplit = rows_nsplit(m, c->n, s, c->dp, false);
+  float* xt = ar.get<float>((size_t)m * c->dp);
+  float* qt = ar.get<float>((size_t)m);
+  float* part = ar.get<float>((size_t)nsplit * m * s);
+  if (ar.err != cudaSuccess) return ADASAP_ENOMEM;
+  CT(launch_transform(Xtest, m, c->d, c->dp, c->mean_dev, c->kappa / (double)c->ell, xt, qt, st));
+  CT(launch_rows(c->kern, c->dp, rows_over_x(c, xt, qt, nullptr, m, W, s, part), s, nsplit, false, st));
+  CT(launch_reduce(part, nsplit, m, s, 0, s, out, s, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, nullptr, st));
+  CT(cudaStreamSynchronize(st));  // the arena frees its buffers on return
+  return ADASAP_OK;
+}
+
+extern "C" adasap_status adasap_hypergrad(adasap_ctx* c, const float* W, const float* G, int s, double* d_ell,
+                                          double* d_sigma2, void* stream) {
+  if (!c || !W || !G || !d_ell || !d_sigma2 || s < 1 || s > kMaxRhs) return ADASAP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Arena ar;
+  // the partials of a 1-column group may use more splits than a 2-column group
+  const size_t part_elems = std::max((size_t)rows_nsplit(c->n, c->n, 2, c->dp, true) * 4,
+                                     (size_t)rows_nsplit(c->n, c->n, 1, c->dp, true) * 2) * (size_t)c->n;
+  float* part = ar.get<float>(part_elems);
+  double* acc = ar.get<double>(2 * kReduceBlocks);
+  if (ar.err != cudaSuccess) return ADASAP_ENOMEM;
+  CT(cudaMemsetAsync(acc, 0, 2 * kReduceBlocks * sizeof(double), st));
+  for (int c0 = 0; c0 < s; c0 += 2) {
+    const int g = std::min(2, s - c0);
+    const int ns = rows_nsplit(c->n, c->n, g, c->dp, true);
+    CT(launch_rows(c->kern, c->dp, rows_over_x(c, c->Xc, c->qc, nullptr, c->n, W + c0, s, part), g, ns, true, st));
+    CT(launch_adj_reduce(part, ns, c->n, g, G, s, c0, acc, st));
+  }
+  std::vector<double> h(2 * kReduceBlocks);
+  CT(cudaMemcpyAsync(h.data(), acc, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CT(cudaStreamSynchronize(st));
+  double sk = 0.0, sg = 0.0;
+  for (int i = 0; i < kReduceBlocks; ++i) {
+    sk += h[2 * i];
+    sg += h[2 * i + 1];
+  }
+  *d_sigma2 = sk / (double)c->sigma2;
+  *d_ell = sg / (double)c->ell;
+  return ADASAP_OK;
+}
+
+extern "C" adasap_status adasap_sample(uint64_t seed, int64_t t, int64_t n, int64_t b, int r, int64_t* B,
+                                       float* Omega, float* v0, void* stream) {
+  if (n < 1 || n >= (1LL << 31) || b < 1 || b > n || r < 0 || t < 0 || t >= (1LL << 32)) return ADASAP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (B) CT(launch_sample_block(seed, nullptr, t, n, b, 1, nullptr, B, st));
+  if (Omega && r > 0) CT(launch_normals(seed, nullptr, t, b * (int64_t)r, 2, (float)(1.0 / std::sqrt((double)b)), Omega, st));
+  if (v0) CT(launch_normals(seed, nullptr, t, b, 3, 1.0f, v0, st));
+  return ADASAP_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// ADASAP solver handle: device state, the captured iteration graph, residuals.
+// ---------------------------------------------------------------------------
+struct adasap_solver {
+  adasap_ctx* c = nullptr;
+  int s = 1;
+  adasap_opts o{};
+  bool sched = false;
+  bool identity = false;
+  int r = 0;
+  int64_t b = 0, mc = 0;
+  int ns1 = 1, ns_sk = 1, ns_pw = 1, ns_c = 1;
+  double beta = 0, gamma = 0, alpha = 0, eps = 0;
+  int literal = 0;
+  int64_t iters = 0;
+  Arena ar;
+  float *Y = nullptr, *W = nullptr, *V = nullptr, *Z = nullptr;
+  int* B32 = nullptr;
+  float *Om = nullptr, *v0 = nullptr, *XB = nullptr, *qB = nullptr, *R = nullptr, *D = nullptr;
+  float *part1 = nullptr, *part2 = nullptr, *Ysk = nullptr, *a = nullptr, *h = nullptr, *vA = nullptr, *vB = nullptr;
+  int* Cidx = nullptr;
+  float *Rc = nullptr, *cpart = nullptr;
+  double* sqb = nullptr;
+  CoreBufs cb{};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ~adasap_solver() {
+    if (c && c->s0) cudaStreamSynchronize(c->s0);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
+
+namespace {
+
+adasap_status alloc_solver(adasap_solver* S) {
+  adasap_ctx* c = S->c;
+  Arena& ar = S->ar;
+  const int64_t n = c->n, b = S->b;
+  const int s = S->s, r = S->r, rr = std::max(r, 1);
+  const size_t ns_ = (size_t)n * s;
+  S->Y = ar.get<float>(ns_);
+  S->W = ar.get<float>(ns_);
+  S->V = ar.get<float>(ns_);
+  S->Z = ar.get<float>(ns_);
+  S->B32 = ar.get<int>(b);
+  S->Om = ar.get<float>((size_t)b * rr);
+  S->v0 = ar.get<float>(b);
+  S->XB = ar.get<float>((size_t)b * c->dp);
+  S->qB = ar.get<float>(b);
+  S->R = ar.get<float>((size_t)b * s);
+  S->D = ar.get<float>((size_t)b * s);
+  S->part1 = ar.get<float>((size_t)S->ns1 * b * s);
+  S->part2 = ar.get<float>(std::max((size_t)S->ns_sk * b * rr, (size_t)S->ns_pw * b));
+  S->Ysk = ar.get<float>((size_t)b * rr);
+  S->a = ar.get<float>(b);
+  S->h = ar.get<float>(b);
+  S->vA = ar.get<float>(b);
+  S->vB = ar.get<float>(b);
+  S->Cidx = ar.get<int>(S->mc);
+  S->Rc = ar.get<float>((size_t)S->mc * s);
+  S->cpart = ar.get<float>((size_t)S->ns_c * S->mc * s);
+  S->sqb = ar.get<double>(kReduceBlocks);
+  CoreBufs& cb = S->cb;
+  cb.r = r;
+  cb.s = s;
+  cb.b = b;
+  cb.gram_chunks = gram_chunks_for(b);
+  cb.gram_part = ar.get<double>((size_t)cb.gram_chunks * 4 * rr * rr);
+  cb.G = ar.get<double>((size_t)4 * rr * rr);
+  cb.Lc = ar.get<double>((size_t)rr * rr);
+  cb.Gnu = ar.get<double>((size_t)rr * rr);
+  cb.X1 = ar.get<double>((size_t)rr * rr);
+  cb.A = ar.get<double>((size_t)rr * rr);
+  cb.V32 = ar.get<float>((size_t)rr * rr);
+  cb.lam = ar.get<double>(rr);
+  cb.T = ar.get<double>((size_t)rr * rr);
+  cb.S = ar.get<double>(rr);
+  cb.keep = ar.get<double>(rr);
+  cb.Lw = ar.get<double>((size_t)rr * rr);
+  cb.U = ar.get<float>((size_t)b * rr);
+  cb.utv_chunks = utv_chunks_for(b);
+  cb.utv_part = ar.get<double>((size_t)cb.utv_chunks * rr * s);
+  cb.coef = ar.get<float>((size_t)rr * s);
+  cb.sq_part = ar.get<double>(kReduceBlocks);
+  cb.dot_part = ar.get<double>(kReduceBlocks);
+  cb.alpha = ar.get<double>(2);
+  return ar.err == cudaSuccess ? ADASAP_OK : ADASAP_ENOMEM;
+}
+
+// Record one ADASAP iteration on s0 (forking to s1) into S->graph.
+cudaError_t capture_iteration(adasap_solver* S, const int64_t* Bs, const float* Oms, const float* v0s, double* trace) {
+  adasap_ctx* c = S->c;
+  cudaStream_t s0 = c->s0, s1 = c->s1;
+  const int64_t n = c->n, b = S->b;
+  const int s = S->s, r = S->r;
+  const double lam = c->lambda;
+  CoreBufs& cb = S->cb;
+  cudaError_t e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t ce = cudaSuccess;
+  auto K = [&](cudaError_t x) {
+    if (ce == cudaSuccess && x != cudaSuccess) ce = x;
+  };
+  const long long* tdev = &c->sc->t;
+  // sample B, Omega, v0 (Alg. 2; Alg. 5)
+  if (S->sched) {
+    K(launch_copy_schedule(Bs, Oms, v0s, tdev, n, b, r, S->B32, S->Om, S->v0, c->sc, s0));
+  } else {
+    K(launch_sample_block(S->o.seed, tdev, 0, n, b, 1, S->B32, nullptr, s0));
+    if (!S->identity)
+      K(launch_normals(S->o.seed, tdev, 0, b * (int64_t)r, 2, (float)(1.0 / std::sqrt((double)b)), S->Om, s0));
+    K(launch_normals(S->o.seed, tdev, 0, b, 3, 1.0f, S->v0, s0));
+  }
+  K(launch_gather(c->Xc, c->qc, S->B32, b, c->dp, S->XB, S->qB, s0));
+  K(cudaEventRecord(c->ev_fork, s0));
+  K(cudaStreamWaitEvent(s1, c->ev_fork, 0));
+  // branch 1: Step II sketch, Step III Nystrom + preconditioner + stepsize
+  RowsArgs kb;
+  kb.xr = S->XB; kb.qr = S->qB; kb.ridx = nullptr; kb.m = b;
+  kb.xc = S->XB; kb.qc = S->qB; kb.ncols = b;
+  kb.part = S->part2; kb.cps = 0; kb.sigma2 = c->sigma2;
+  if (!S->identity) {
+    kb.w = S->Om; kb.ldw = r;
+    K(launch_rows(c->kern, c->dp, kb, r, S->ns_sk, false, s1));
+    K(launch_reduce(S->part2, S->ns_sk, b, r, 0, r, S->Ysk, r, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0,
+                    nullptr, s1));
+    K(launch_nystrom_core(cb, S->eps, lam, c->sc, S->Om, S->Ysk, s1));
+    K(launch_woodbury_factor(cb, lam, c->sc, s1));
+  }
+  // v0 copy and ||v0||^2 partials
+  K(launch_reduce(S->v0, 1, b, 1, 0, 1, S->vA, 1, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, cb.sq_part, s1));
+  float* vcur = S->vA;
+  float* vnext = S->vB;
+  for (int i = 0; i < S->o.power_iters; ++i) {
+    const bool last = i == S->o.power_iters - 1;
+    K(launch_woodbury_apply(cb, kInvSqrtNormalised, vcur, 1, S->a, false, false, nullptr, c->sc, s1));
+    kb.w = S->a; kb.ldw = 1;
+    K(launch_rows(c->kern, c->dp, kb, 1, S->ns_pw, false, s1));
+    K(launch_reduce(S->part2, S->ns_pw, b, 1, 0, 1, S->h, 1, (float)lam, S->a, nullptr, 1, 0.f, nullptr, nullptr, 0,
+                    nullptr, s1));
+    K(launch_woodbury_apply(cb, kInvSqrt, S->h, 1, vnext, true, last, last ? vcur : nullptr, c->sc, s1));
+    std::swap(vcur, vnext);
+  }
+  K(launch_set_eta(cb, c->sc, S->identity, s1));
+  K(cudaEventRecord(c->ev_join, s1));
+  // branch 2: Step I block residual at the reading's point
+  float* P = S->literal ? S->W : S->Z;
+  K(launch_rows(c->kern, c->dp, rows_over_x(c, c->Xc, c->qc, S->B32, b, P, s, S->part1), s, S->ns1, false, s0));
+  K(launch_reduce(S->part1, S->ns1, b, s, 0, s, S->R, s, (float)lam, P, S->B32, s, -1.f, S->Y, S->B32, s, nullptr,
+                  s0));
+  K(cudaStreamWaitEvent(s0, c->ev_join, 0));
+  // Step IV: direction and NesterovAcc
+  K(launch_woodbury_apply(cb, kInv, S->R, s, S->D, false, false, nullptr, c->sc, s0));
+  K(launch_nesterov(S->W, S->V, S->Z, n * (int64_t)s, (float)S->beta, (float)S->alpha, S->literal, s0));
+  K(launch_scatter(S->W, S->V, S->Z, S->B32, b, s, S->D, (float)S->gamma, (float)S->alpha, S->literal, c->sc, s0));
+  if (trace) K(launch_trace(c->sc, trace, s0));
+  K(launch_tick(c->sc, s0));
+  e = cudaStreamEndCapture(s0, &S->graph);
+  if (ce != cudaSuccess) return ce;
+  if (e != cudaSuccess) return e;
+  return cudaGraphInstantiateWithFlags(&S->exec, S->graph, cudaGraphInstantiateFlagUseNodePriority);
+}
+
+adasap_status solver_begin(adasap_ctx* c, const float* Y, int s, const adasap_opts* o, const int64_t* Bs,
+                           const float* Oms, const float* v0s, const float* W0, double* trace, cudaStream_t us,
+                           adasap_solver** out) {
+  if (!c || !Y || !o || !out || s < 1 || s > kMaxRhs) return ADASAP_EINVAL;
+  *out = nullptr;
+  const int64_t n = c->n, b = o->b;
+  const bool identity = o->precond == 1;
+  const int r = identity ? 0 : o->r;
+  if (b < 1 || b > n || o->power_iters < 1 || (o->precond != 0 && o->precond != 1)) return ADASAP_EINVAL;
+  if (!identity && (r < 1 || r > kMaxRank || r > b)) return ADASAP_EINVAL;
+  if (Bs && (!v0s || (!identity && !Oms))) return ADASAP_EINVAL;
+  adasap_solver* S = new (std::nothrow) adasap_solver();
+  if (!S) return ADASAP_ENOMEM;
+  S->c = c;
+  S->s = s;
+  S->o = *o;
+  S->sched = Bs != nullptr;
+  S->identity = identity;
+  S->r = r;
+  S->b = b;
+  const double lam = c->lambda;
+  const double mu = o->mu > 0 ? o->mu : lam;
+  const double nu = o->nu > 0 ? o->nu : (double)n / (double)b;
+  S->beta = 1.0 - std::sqrt(mu / nu);
+  S->gamma = 1.0 / std::sqrt(mu * nu);
+  S->alpha = 1.0 / (1.0 + S->gamma * nu);
+  S->eps = o->eps > 0 ? o->eps : std::ldexp(1.0, -23);
+  S->literal = o->literal ? 1 : 0;
+  S->mc = std::min<int64_t>(n, std::max<int64_t>(1, o->check_rows));
+  S->ns1 = rows_nsplit(b, n, s, c->dp, false);
+  S->ns_sk = identity ? 1 : rows_nsplit(b, b, r, c->dp, false);
+  S->ns_pw = rows_nsplit(b, b, 1, c->dp, false);
+  S->ns_c = rows_nsplit(S->mc, n, s, c->dp, false);
+  adasap_status st = alloc_solver(S);
+  if (st != ADASAP_OK) { delete S; return st; }
+  auto fail = [&](cudaError_t e, const char* what) {
+    note_error(e, what);
+    delete S;
+    return ADASAP_ECUDA;
+  };
+  cudaError_t e;
+  const size_t bytes = (size_t)n * s * sizeof(float);
+  if ((e = cudaEventRecord(c->ev_in, us)) || (e = cudaStreamWaitEvent(c->s0, c->ev_in, 0))) return fail(e, "order");
+  if ((e = cudaMemcpyAsync(S->Y, Y, bytes, cudaMemcpyDefault, c->s0))) return fail(e, "copy Y");
+  if (W0) e = cudaMemcpyAsync(S->W, W0, bytes, cudaMemcpyDefault, c->s0);
+  else e = cudaMemsetAsync(S->W, 0, bytes, c->s0);
+  if (e) return fail(e, "copy W0");
+  if ((e = cudaMemsetAsync(c->sc, 0, sizeof(DevScalars), c->s0))) return fail(e, "memset");
+  // ||Y||_F^2 (the reduce copies Y into V, overwritten just below)
+  if ((e = launch_reduce(S->Y, 1, n, s, 0, s, S->V, s, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, S->sqb,
+                         c->s0)))
+    return fail(e, "ysq");
+  if ((e = launch_sum_blocks(S->sqb, kReduceBlocks, &c->sc->ysq, c->s0))) return fail(e, "ysq");
+  if ((e = cudaMemcpyAsync(S->V, S->W, bytes, cudaMemcpyDeviceToDevice, c->s0))) return fail(e, "V0");
+  if ((e = cudaMemcpyAsync(S->Z, S->W, bytes, cudaMemcpyDeviceToDevice, c->s0))) return fail(e, "Z0");
+  if ((e = cudaStreamSynchronize(c->s0))) return fail(e, "sync");
+  if ((e = capture_iteration(S, Bs, Oms, v0s, trace))) return fail(e, "graph capture");
+  *out = S;
+  return ADASAP_OK;
+}
+
+adasap_status solver_residual(adasap_solver* S, double* rel, cudaStream_t us) {
+  adasap_ctx* c = S->c;
+  const int s = S->s;
+  const int64_t mc = S->mc;
+  CT(cudaEventRecord(c->ev_in, us));
+  CT(cudaStreamWaitEvent(c->s0, c->ev_in, 0));
+  const int* cidx = nullptr;
+  if (mc < c->n) {
+    CT(launch_sample_block(S->o.seed, nullptr, S->iters, c->n, mc, 4, S->Cidx, nullptr, c->s0));
+    cidx = S->Cidx;
+  }
+  CT(launch_rows(c->kern, c->dp, rows_over_x(c, c->Xc, c->qc, cidx, mc, S->W, s, S->cpart), s, S->ns_c, false,
+                 c->s0));
+  CT(launch_reduce(S->cpart, S->ns_c, mc, s, 0, s, S->Rc, s, c->lambda, S->W, cidx, s, -1.f, S->Y, cidx, s, S->sqb,
+                   c->s0));
+  CT(launch_sum_blocks(S->sqb, kReduceBlocks, &c->sc->resid_sq, c->s0));
+  CT(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->s0));
+  CT(cudaStreamSynchronize(c->s0));
+  const DevScalars& hs = *c->sc_host;
+  *rel = std::sqrt(hs.resid_sq * ((double)c->n / (double)mc) / hs.ysq);
+  if (hs.status != 0) return (adasap_status)hs.status;
+  if (!std::isfinite(*rel) || *rel > 1e8) return ADASAP_EDIVERGED;
+  return ADASAP_OK;
+}
+
+}  // namespace
+
+extern "C" adasap_status adasap_solver_begin(adasap_ctx* c, const float* Y, int s, const adasap_opts* o,
+                                             const float* W0, void* stream, adasap_solver** out) {
+  try {
+    return solver_begin(c, Y, s, o, nullptr, nullptr, nullptr, W0, nullptr, (cudaStream_t)stream, out);
+  } catch (...) {
+    return ADASAP_ENOMEM;
+  }
+}
+
+extern "C" adasap_status adasap_solver_step(adasap_solver* S, int iters, void* stream) {
+  if (!S || iters < 0) return ADASAP_EINVAL;
+  for (int i = 0; i < iters; ++i) CT(cudaGraphLaunch(S->exec, (cudaStream_t)stream));
+  S->iters += iters;
+  return ADASAP_OK;
+}
+
+extern "C" adasap_status adasap_solver_residual(adasap_solver* S, double* rel, void* stream) {
+  if (!S || !rel) return ADASAP_EINVAL;
+  return solver_residual(S, rel, (cudaStream_t)stream);
+}
+
+extern "C" adasap_status adasap_solver_get_w(adasap_solver* S, float* W, void* stream) {
+  if (!S || !W) return ADASAP_EINVAL;
+  CT(cudaMemcpyAsync(W, S->W, (size_t)S->c->n * S->s * sizeof(float), cudaMemcpyDefault, (cudaStream_t)stream));
+  return ADASAP_OK;
+}
+
+extern "C" adasap_status adasap_solver_scalars(adasap_solver* S, double* eta, double* rho, int* status,
+                                               void* stream) {
+  if (!S) return ADASAP_EINVAL;
+  adasap_ctx* c = S->c;
+  CT(cudaEventRecord(c->ev_in, (cudaStream_t)stream));
+  CT(cudaStreamWaitEvent(c->s0, c->ev_in, 0));
+  CT(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->s0));
+  CT(cudaStreamSynchronize(c->s0));
+  if (eta) *eta = c->sc_host->eta;
+  if (rho) *rho = c->sc_host->rho;
+  if (status) *status = c->sc_host->status;
+  return ADASAP_OK;
+}
+
+extern "C" void adasap_solver_end(adasap_solver* S) { delete S; }
+
+namespace {
+
+adasap_status solve_loop(adasap_solver* S, float* W, adasap_stats* stats, int T_run, cudaStream_t us) {
+  adasap_ctx* c = S->c;
+  const adasap_opts& o = S->o;
+  adasap_status st = ADASAP_OK;
+  double rel = NAN;
+  bool converged = false, checked_last = false;
+  int it = 0;
+  CT(cudaEventRecord(c->ev_t0, c->s0));
+  while (it < T_run) {
+    int k = T_run - it;
+    if (!S->sched && o.check_every > 0) k = std::min(k, o.check_every - (it % o.check_every));
+    for (int i = 0; i < k; ++i) CT(cudaGraphLaunch(S->exec, c->s0));
+    it += k;
+    S->iters = it;
+    checked_last = false;
+    if (!S->sched && o.check_every > 0 && it % o.check_every == 0) {
+      st = solver_residual(S, &rel, c->s0);
+      checked_last = true;
+      if (st != ADASAP_OK) break;
+      if (o.tol > 0 && rel <= o.tol) {
+        converged = true;
+        break;
+      }
+    }
+  }
+  CT(cudaEventRecord(c->ev_t1, c->s0));
+  CT(cudaStreamSynchronize(c->s0));
+  float ms = 0.f;
+  CT(cudaEventElapsedTime(&ms, c->ev_t0, c->ev_t1));
+  if (st == ADASAP_OK && !checked_last && !S->sched) {
+    st = solver_residual(S, &rel, c->s0);
+    if (st == ADASAP_OK && o.tol > 0 && rel <= o.tol) converged = true;
+  }
+  CT(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->s0));
+  CT(cudaMemcpyAsync(W, S->W, (size_t)c->n * S->s * sizeof(float), cudaMemcpyDefault, c->s0));
+  CT(cudaStreamSynchronize(c->s0));
+  if (st == ADASAP_OK && c->sc_host->status != 0) st = (adasap_status)c->sc_host->status;
+  if (stats) {
+    stats->iters = it;
+    stats->rel_resid = rel;
+    stats->resid_exact = S->mc == c->n ? 1 : 0;
+    stats->seconds = ms * 1e-3;
+    stats->last_eta = c->sc_host->eta;
+    stats->last_rho = c->sc_host->rho;
+  }
+  if (st == ADASAP_OK && !S->sched && o.tol > 0 && !converged) st = ADASAP_ENOTCONVERGED;
+  CT(cudaEventRecord(c->ev_out, c->s0));
+  CT(cudaStreamWaitEvent(us, c->ev_out, 0));
+  return st;
+}
+
+}  // namespace
+
+extern "C" adasap_status adasap_solve(adasap_ctx* c, const float* Y, int s, const adasap_opts* o, float* W,
+                                      adasap_stats* stats, void* stream) {
+  if (!W || !o || o->max_iters < 0) return ADASAP_EINVAL;
+  try {
+    adasap_solver* S = nullptr;
+    adasap_status st = solver_begin(c, Y, s, o, nullptr, nullptr, nullptr, W, nullptr, (cudaStream_t)stream, &S);
+    if (st != ADASAP_OK) return st;
+    st = solve_loop(S, W, stats, o->max_iters, (cudaStream_t)stream);
+    delete S;
+    return st;
+  } catch (...) {
+    return ADASAP_ENOMEM;
+  }
+}
+
+extern "C" adasap_status adasap_solve_scheduled(adasap_ctx* c, const float* Y, int s, const adasap_opts* o,
+                                                const int64_t* B_sched, const float* Omega_sched,
+                                                const float* v0_sched, int T, float* W, double* trace,
+                                                adasap_stats* stats, void* stream) {
+  if (!B_sched || !W || !o || T < 0) return ADASAP_EINVAL;
+  try {
+    adasap_solver* S = nullptr;
+    adasap_status st = solver_begin(c, Y, s, o, B_sched, Omega_sched, v0_sched, W, trace, (cudaStream_t)stream, &S);
+    if (st != ADASAP_OK) return st;
+    st = solve_loop(S, W, stats, T, (cudaStream_t)stream);
+    delete S;
+    return st;
+  } catch (...) {
+    return ADASAP_ENOMEM;
+  }
+}
+
+extern "C" adasap_status adasap_solver_graph_kernels(adasap_solver* S, int* count) {
+  if (!S || !count || !S->graph) return ADASAP_EINVAL;
+  size_t nn = 0;
+  CT(cudaGraphGetNodes(S->graph, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  CT(cudaGraphGetNodes(S->graph, nodes.data(), &nn));
+  int k = 0;
+  for (size_t i = 0; i < nn; ++i) {
+    cudaGraphNodeType t;
+    CT(cudaGraphNodeGetType(nodes[i], &t));
+    k += t == cudaGraphNodeTypeKernel;
+  }
+  *count = k;
+  return ADASAP_OK;
+}

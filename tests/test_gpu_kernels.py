@@ -1,0 +1,167 @@
+"""GPU parity of the kernel-row engine, sampler, posterior mean and adjoint
+against the FP64 oracle (through the C-ABI)."""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import gp
+from oracle import kernels as OK
+from oracle import rng as OR
+from paper_2505_13723_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+# Tolerance of an FP32 kernel-row product (spec: <= 1e-5 relative):
+#   |out_i - ref_i| <= 1e-5 * sum_j |k_ij| |w_ij|
+# i.e. relative to the sum of absolute terms, the scale at which FP32
+# rounding of distances, exponentials and partial sums acts.
+RTOL_ROWS = 1e-5
+
+
+def _data(n, d, s, seed, dist="normal"):
+    g = np.random.default_rng(seed)
+    X = (g.standard_normal((n, d)) if dist == "normal" else g.random((n, d))).astype(np.float32)
+    W = g.standard_normal((n, s)).astype(np.float32)
+    return X, W
+
+
+def _check_rows(got, X, rows, W, kern, ell, s2, rtol=RTOL_ROWS):
+    Xd = X.astype(np.float64)
+    ref = OK.kernel_apply(Xd[rows], Xd, W.astype(np.float64), kern, ell, s2)
+    scale = OK.kernel_apply(Xd[rows], Xd, np.abs(W.astype(np.float64)), kern, ell, s2)
+    err = np.abs(got - ref)
+    bad = err > rtol * scale + 1e-30
+    assert not bad.any(), "max err/scale %.3e" % (err / np.maximum(scale, 1e-300)).max()
+
+
+@pytest.mark.parametrize("kern", [0, 1, 2])
+@pytest.mark.parametrize("d", [1, 8, 11, 20, 40])
+@pytest.mark.parametrize("s", [1, 3, 4, 17, 64])
+def test_kernel_rows_matches_oracle(lib, kern, d, s):
+    n, b = 3001, 157                      # ragged against every tile size
+    X, W = _data(n, d, s, seed=d * 10 + s)
+    ell = 0.9 * np.sqrt(d)
+    ctx = lib.Context(X, kern, ell, 1.3, 1e-2)
+    g = np.random.default_rng(kern)
+    rows = g.choice(n, size=b, replace=False)
+    out = ctx.kernel_rows(torch.from_numpy(rows).cuda(), torch.from_numpy(W).cuda()).cpu().numpy()
+    _check_rows(out.astype(np.float64), X, rows, W, kern, ell, 1.3)
+
+
+@pytest.mark.parametrize("s", [1, 100])
+def test_kernel_rows_edge_sizes(lib, s):
+    # n = 1, b = 1; a block of all rows; repeated rows
+    X, W = _data(1, 3, s, seed=1)
+    ctx = lib.Context(X, 1, 1.0, 1.0, 1.0)
+    out = ctx.kernel_rows(torch.zeros(1, dtype=torch.int64, device="cuda"), torch.from_numpy(W).cuda())
+    np.testing.assert_allclose(out.cpu().numpy(), W, rtol=1e-6)      # k(x, x) = sigma2 = 1
+    X, W = _data(700, 5, s, seed=2)
+    ctx = lib.Context(X, 2, 1.5, 0.7, 1.0)
+    rows = np.concatenate([np.arange(700), [3, 3, 699]])
+    out = ctx.kernel_rows(torch.from_numpy(rows).cuda(), torch.from_numpy(W).cuda()).cpu().numpy()
+    _check_rows(out.astype(np.float64), X, rows, W, 2, 1.5, 0.7)
+
+
+def test_kernel_rows_invalid_index_gives_nan_row(lib):
+    X, W = _data(500, 4, 2, seed=3)
+    ctx = lib.Context(X, 0, 1.0, 1.0, 1.0)
+    rows = torch.tensor([0, -1, 499, 500, 7], device="cuda")
+    out = ctx.kernel_rows(rows, torch.from_numpy(W).cuda()).cpu().numpy()
+    assert np.isnan(out[1]).all() and np.isnan(out[3]).all()
+    assert np.isfinite(out[[0, 2, 4]]).all()
+    _check_rows(out[[0, 2, 4]].astype(np.float64), X, np.array([0, 499, 7]), W, 0, 1.0, 1.0)
+
+
+def test_kernel_rows_regress_workload_full_size_sampled(lib):
+    """n = 2^20, d = 11, Matern-3/2, b = 10^4 (the benchmark's launch); 48 rows checked."""
+    P = synth.regress()
+    ctx = lib.Context(P.X, P.kernel, P.ell, P.sigma2, P.lam)
+    g = np.random.default_rng(11)
+    rows = g.choice(P.X.shape[0], size=P.b, replace=False)
+    W = g.standard_normal((P.X.shape[0], 1)).astype(np.float32)
+    out = ctx.kernel_rows(torch.from_numpy(rows).cuda(), torch.from_numpy(W).cuda()).cpu().numpy()
+    pick = g.choice(P.b, size=48, replace=False)
+    _check_rows(out[pick].astype(np.float64), P.X, rows[pick], W, P.kernel, P.ell, P.sigma2)
+
+
+def test_sampler_matches_oracle_generator(lib):
+    for (n, b, r, t, seed) in [(2000, 200, 32, 0, 0), (2000, 200, 32, 7, 0), (1 << 20, 10000, 100, 3, 99),
+                               (5, 5, 2, 1, 1), (1, 1, 1, 0, 2)]:
+        B, Om, v0 = lib.sample(seed, t, n, b, r)
+        np.testing.assert_array_equal(B.cpu().numpy(), OR.sample_block(n, b, seed, t))
+        np.testing.assert_allclose(Om.cpu().numpy(), OR.sample_omega(b, r, seed, t), rtol=2e-5, atol=2e-6)
+        np.testing.assert_allclose(v0.cpu().numpy(), OR.sample_v0(b, seed, t), rtol=2e-5, atol=2e-6)
+
+
+@pytest.mark.parametrize("kern", [0, 1, 2])
+def test_predict_matches_oracle(lib, kern):
+    X, W = _data(2500, 6, 2, seed=5)
+    Xt = np.random.default_rng(6).standard_normal((333, 6)).astype(np.float32)
+    ctx = lib.Context(X, kern, 1.1, 0.8, 1e-2)
+    out = ctx.predict(torch.from_numpy(Xt).cuda(), torch.from_numpy(W).cuda()).cpu().numpy()
+    ref = gp.posterior_mean(Xt.astype(np.float64), X.astype(np.float64), W.astype(np.float64), kern, 1.1, 0.8)
+    scale = gp.posterior_mean(Xt.astype(np.float64), X.astype(np.float64), np.abs(W.astype(np.float64)), kern, 1.1, 0.8)
+    assert (np.abs(out - ref) <= RTOL_ROWS * scale).all()
+
+
+@pytest.mark.parametrize("kern", [0, 1, 2])
+@pytest.mark.parametrize("s", [1, 3])
+def test_hypergrad_matches_oracle(lib, kern, s):
+    X, W = _data(1500, 5, s, seed=7)
+    G = np.random.default_rng(8).standard_normal(W.shape).astype(np.float32)
+    ctx = lib.Context(X, kern, 0.9, 1.4, 1e-2)
+    d_ell, d_s2 = ctx.hypergrad(torch.from_numpy(W).cuda(), torch.from_numpy(G).cuda())
+    r_ell, r_s2 = gp.hypergrad(X.astype(np.float64), W.astype(np.float64), G.astype(np.float64), kern, 0.9, 1.4)
+    # scale: the same sums with absolute values (cancellation-aware bound)
+    Xd = X.astype(np.float64)
+    a_ell = np.sum(np.abs(G) * OK.kernel_apply(Xd, Xd, np.abs(W.astype(np.float64)), kern, 0.9, 1.4, deriv=True))
+    a_s2 = np.sum(np.abs(G) * OK.kernel_apply(Xd, Xd, np.abs(W.astype(np.float64)), kern, 0.9, 1.4)) / 1.4
+    assert abs(d_ell - r_ell) <= 1e-5 * a_ell
+    assert abs(d_s2 - r_s2) <= 1e-5 * a_s2
+
+
+def test_hypergrad_at_16384_against_finite_differences(lib):
+    """The adjoint at n = 16,384 (BO-shaped data, Matern-5/2) against central differences of
+    the kernel-row product itself: f(theta) = sum G * (K(theta) W)."""
+    P = synth.bo_systems(count=1)[0]
+    g = np.random.default_rng(9)
+    n = 16384
+    X = g.uniform(-1, 1, (n, 8)).astype(np.float32)
+    W = g.standard_normal((n, 1)).astype(np.float32)
+    G = g.standard_normal((n, 1)).astype(np.float32)
+    ell, s2 = 0.6, 1.0
+    Wt, Gt = torch.from_numpy(W).cuda(), torch.from_numpy(G).cuda()
+    rows = torch.arange(n, device="cuda")
+
+    def f(e, s):
+        c = lib.Context(X, P.kernel, e, s, 1e-3)
+        return float((c.kernel_rows(rows, Wt).double() * Gt.double()).sum())
+
+    ctx = lib.Context(X, P.kernel, ell, s2, 1e-3)
+    d_ell, d_s2 = ctx.hypergrad(Wt, Gt)
+    h = 1e-2 * ell
+    fd_ell = (f(ell + h, s2) - f(ell - h, s2)) / (2 * h)
+    fd_s2 = (f(ell, s2 + 0.1) - f(ell, s2 - 0.1)) / 0.2
+    assert abs(d_ell - fd_ell) <= 2e-3 * abs(fd_ell)
+    assert abs(d_s2 - fd_s2) <= 1e-4 * abs(fd_s2)
+
+
+def test_autograd_function_gradients(lib):
+    X, W = _data(800, 4, 2, seed=10)
+    ctx = lib.Context(X, 1, 0.7, 1.2, 1e-2)
+    Wt = torch.from_numpy(W).cuda().requires_grad_(True)
+    ell = torch.tensor(0.7, device="cuda", requires_grad=True)
+    s2 = torch.tensor(1.2, device="cuda", requires_grad=True)
+    G = torch.randn(800, 2, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    y = lib.KernelMatmul.apply(ctx, Wt, ell, s2)
+    (y * G).sum().backward()
+    Xd = X.astype(np.float64)
+    Kd = OK.kernel_matrix(Xd, Xd, 1, 0.7, 1.2)
+    np.testing.assert_allclose(y.detach().cpu().numpy(), Kd @ W, rtol=0, atol=1e-5 * (np.abs(Kd) @ np.abs(W)).max())
+    Gn = G.cpu().numpy().astype(np.float64)
+    gW_ref = Kd @ Gn
+    assert np.abs(Wt.grad.cpu().numpy() - gW_ref).max() <= 1e-5 * (np.abs(Kd) @ np.abs(Gn)).max()
+    r_ell, r_s2 = gp.hypergrad(Xd, W.astype(np.float64), Gn, 1, 0.7, 1.2)
+    assert abs(ell.grad.item() - r_ell) <= 1e-4 * abs(r_ell) + 1e-3
+    assert abs(s2.grad.item() - r_s2) <= 1e-4 * abs(r_s2) + 1e-3
