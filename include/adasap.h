@@ -82,6 +82,10 @@ typedef struct {
   double seconds;      /* device time of the iteration loop incl. residual checks (CUDA events) */
   double last_eta;     /* stepsize eta_B of the last iteration */
   double last_rho;     /* damping rho = S_rr + lambda of the last iteration */
+  int status_detail;   /* stage of a device-side failure: 1 Nystrom core Cholesky (after 3
+                          shift increases), 2 non-finite eigenvalue, 3 Woodbury Cholesky,
+                          4 non-positive stepsize estimate, 5 schedule row out of range,
+                          6 Cholesky of the test matrix's Gram (thin QR of Omega) */
 } adasap_stats;
 
 void adasap_default_opts(adasap_opts* opts, int64_t n);

@@ -19,10 +19,12 @@ a keyword argument here so that tests can discriminate between them):
       (default) forms Z_{t+1} from V_{t+1}; nesterov='literal' uses V_t as
       Alg. 6 prints.  With mu = nu = 1 the standard pair reduces exactly to
       plain SAP with stepsize eta (W = V = Z every step).
-  Omega                Gaussian test matrix with N(0, 1/b) entries, no explicit
-      orthonormalisation: the Nystrom approximation is invariant under
-      Omega -> Omega R for invertible R, and Alg. 4 keeps the general
-      Delta * Omega^T Omega term for exactly this case.
+  Omega                Gaussian test matrix, orthonormalised by a thin QR
+      (Q with a positive-diagonal R), as the commented-out first lines of
+      Alg. 4 do.  The Nystrom approximation itself is invariant under
+      Omega -> Omega R, but the shift Delta * Omega^T Omega only dominates the
+      rounding of a single-precision sketch in every direction when Omega has
+      orthonormal columns.
   Alg. 4, line "B <- Y C^{-1}"   Y is the shifted sketch Y_nu = M Omega + Delta Omega.
       "S <- max{0, diag(S^2 - Delta I)}" reads S = max(0, Sigma^2 - Delta).
   eps                  eps of the precision the sketch M Omega is computed in
@@ -85,6 +87,14 @@ def nystrom(Y, Omega, eps=EPS_FP32, retries=3):
     U, Sigma, _ = np.linalg.svd(B, full_matrices=False)   # thin SVD
     S = np.maximum(0.0, Sigma ** 2 - Delta)    # remove the shift
     return U, S, Delta
+
+
+def orthonormalize(Omega):
+    """Thin QR of the test matrix: Q with orthonormal columns, R with positive diagonal."""
+    Q, R = np.linalg.qr(np.asarray(Omega, dtype=np.float64))
+    sgn = np.sign(np.diag(R))
+    sgn[sgn == 0] = 1.0
+    return Q * sgn
 
 
 def damping(S, lam):
@@ -188,7 +198,8 @@ def adasap(X, Y, kernel, ell, sigma2, lam, b, r, T, schedule, W0=None,
         KBB = K.kernel_matrix(XB, XB, kernel, ell, sigma2)
         H_mv = lambda v: KBB @ v + lam * v
         if precond == "nystrom":
-            # Step II: Nystrom sketch K_BB Omega
+            # Step II: Nystrom sketch K_BB Omega (Omega orthonormalised)
+            Omega = orthonormalize(Omega)
             MOmega = KBB @ Omega
             # Step III: Nystrom approximation, preconditioner, stepsize
             U, S, Delta = nystrom(MOmega, Omega, eps=eps)

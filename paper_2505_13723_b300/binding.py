@@ -46,7 +46,8 @@ class Opts(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("rel_resid", ctypes.c_double),
                 ("resid_exact", ctypes.c_int), ("seconds", ctypes.c_double),
-                ("last_eta", ctypes.c_double), ("last_rho", ctypes.c_double)]
+                ("last_eta", ctypes.c_double), ("last_rho", ctypes.c_double),
+                ("status_detail", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -185,7 +186,7 @@ class Context:
         st = Stats()
         status = _lib.adasap_solve(self.h, _ptr_any(Y, "Y"), s, ctypes.byref(o), _ptr_any(W, "W"),
                                    ctypes.byref(st), _stream(stream))
-        _check(status, "adasap_solve", allow=(7,))
+        _check(status, "adasap_solve (stage %d)" % st.status_detail, allow=(7,))
         return W, st.as_dict(), status
 
     def solve_scheduled(self, Y, B, Omega, v0, opts=None, W=None, trace=True, stream=None, **kw):
@@ -200,12 +201,13 @@ class Context:
             W = torch.zeros(self.n, s, device="cuda", dtype=torch.float32)
         tr = torch.zeros(T, 2, device="cuda", dtype=torch.float64) if trace else None
         st = Stats()
-        _check(_lib.adasap_solve_scheduled(
+        status = _lib.adasap_solve_scheduled(
             self.h, _ptr_any(Y, "Y"), s, ctypes.byref(o), ctypes.c_void_p(B.data_ptr()),
             ctypes.c_void_p(Omega.data_ptr()) if Omega is not None else None,
             ctypes.c_void_p(v0.data_ptr()), T, _ptr_any(W, "W"),
             ctypes.c_void_p(tr.data_ptr()) if tr is not None else None, ctypes.byref(st),
-            _stream(stream)), "adasap_solve_scheduled")
+            _stream(stream))
+        _check(status, "adasap_solve_scheduled (stage %d)" % st.status_detail)
         return W, tr, st.as_dict()
 
     def predict(self, Xtest, W, stream=None):

@@ -107,12 +107,15 @@ struct DevScalars {
   double resid_sq;   // sum of squares of the sampled residual
   double dot;        // scratch dot product (power iteration)
   int status;        // first error (adasap_status), 0 if none
+  int detail;        // stage of the first error: 1 Nystrom core Cholesky, 2 non-finite
+                     // eigenvalue, 3 Woodbury Cholesky, 4 non-positive stepsize estimate,
+                     // 5 schedule row out of range, 6 test-matrix QR Cholesky
   int chol_retries;  // number of Delta increases in the last iteration
   long long t;       // iteration counter
 };
 
-__device__ __forceinline__ void set_status(DevScalars* sc, int code) {
-  atomicCAS(&sc->status, 0, code);
+__device__ __forceinline__ void set_status(DevScalars* sc, int code, int detail = 0) {
+  if (atomicCAS(&sc->status, 0, code) == 0) sc->detail = detail;
 }
 
 }  // namespace adasap

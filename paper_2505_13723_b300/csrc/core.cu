@@ -19,9 +19,12 @@
 namespace adasap {
 
 // ---------------------------------------------------------------------------
-// Gram matrix of the row-concatenation [A1 | A2] (m x (c1 + c2), c <= 256):
-// per chunk of rows FP32 products over 32-row slices, folded into FP64; only
-// upper 32 x 32 tiles are computed, the reduce mirrors them.
+// Gram matrix of the row-concatenation [A1 | A2] (m x (c1 + c2), c <= 256) in
+// FP64: the products of the FP32 entries are exact in FP64 (24 + 24 bits) and
+// are accumulated in FP64.  Exactness matters: B^T B = C^{-T} (Y_nu^T Y_nu) C^{-1}
+// multiplies the Gram's absolute error by cond(C)^2, so FP32 products would
+// swamp the small Nystrom eigenvalues.  Only upper 32 x 32 tiles are computed;
+// the reduce mirrors them.
 // ---------------------------------------------------------------------------
 int gram_chunks_for(int64_t b) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, (b + 255) / 256)); }
 
@@ -54,20 +57,15 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1,
       sb[rr][cc] = ok ? cat_get(A1, ld1, c1, A2, ld2, c2, row, tj * 32 + cc) : 0.0f;
     }
     __syncthreads();
-    float f[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll 8
     for (int rr = 0; rr < 32; ++rr) {
-      const float a0 = sa[rr][2 * ty], a1 = sa[rr][2 * ty + 1];
-      const float b0 = sb[rr][2 * tx], b1 = sb[rr][2 * tx + 1];
-      f[0][0] = fmaf(a0, b0, f[0][0]);
-      f[0][1] = fmaf(a0, b1, f[0][1]);
-      f[1][0] = fmaf(a1, b0, f[1][0]);
-      f[1][1] = fmaf(a1, b1, f[1][1]);
+      const double a0 = sa[rr][2 * ty], a1 = sa[rr][2 * ty + 1];
+      const double b0 = sb[rr][2 * tx], b1 = sb[rr][2 * tx + 1];
+      acc[0][0] = fma(a0, b0, acc[0][0]);
+      acc[0][1] = fma(a0, b1, acc[0][1]);
+      acc[1][0] = fma(a1, b0, acc[1][0]);
+      acc[1][1] = fma(a1, b1, acc[1][1]);
     }
-#pragma unroll
-    for (int u = 0; u < 2; ++u)
-#pragma unroll
-      for (int v = 0; v < 2; ++v) acc[u][v] += (double)f[u][v];
   }
 #pragma unroll
   for (int u = 0; u < 2; ++u)
@@ -154,7 +152,7 @@ __global__ void __launch_bounds__(512) k_nys_chol(const double* __restrict__ G, 
   }
   if (!ok) {
     for (int e = threadIdx.x; e < r * r; e += blockDim.x) sh[(e / r) * ld + e % r] = (e / r == e % r) ? 1.0 : 0.0;
-    if (threadIdx.x == 0) set_status(sc, ADASAP_ENUMERIC);
+    if (threadIdx.x == 0) set_status(sc, ADASAP_ENUMERIC, 1);
     __syncthreads();
   }
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
@@ -337,31 +335,40 @@ __global__ void k_nys_finalize(const double* __restrict__ lam, const float* __re
     S[q] = sq;
     keep[q] = sq > 0.0 ? 1.0 : 0.0;
     sig[q] = li > 0.0 ? sqrt(li) : 0.0;
-    if (!isfinite(li)) set_status(sc, ADASAP_ENUMERIC);
+    if (!isfinite(li)) set_status(sc, ADASAP_ENUMERIC, 2);
   }
   __syncthreads();
   if (threadIdx.x == 0) sc->rho = S[r - 1] + lam_reg;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int k = e / r, q = e % r;
     const int i = perm[q];
-    Tp[e] = sig[q] > 0.0 ? (double)V[(int64_t)k * r + i] / (nrm[i] * sig[q]) : 0.0;
+    // a dropped eigenpair (S_q = 0) contributes exactly nothing to either Woodbury form
+    // (eqs. inv_nys_woodbury and inv_sqrt_nys_woodbury), so its U column is set to 0
+    // instead of V / sigma with sigma ~ 0
+    Tp[e] = (S[q] > 0.0 && sig[q] > 0.0) ? (double)V[(int64_t)k * r + i] / (nrm[i] * sig[q]) : 0.0;
   }
 }
 
-// U = (Y + Delta Omega) T  (b x r): rows in blocks of 32, T in shared memory (FP32)
-__global__ void __launch_bounds__(256) k_make_u(const float* __restrict__ Om, const float* __restrict__ Ysk, int64_t b,
-                                                int r, const double* __restrict__ T, const DevScalars* sc,
+// U = (A1 + delta A2) T'  (b x r), T' = T or T^T (r x r FP64, staged as FP32 in
+// shared memory), delta = sc->delta or 0 when A2 is NULL.  Rows in blocks of 32.
+//   Nystrom: A1 = M Omega, A2 = Omega, T' = T      (U = Y_nu T)
+//   QR:      A1 = Omega,   A2 = NULL,  T' = L^{-T} (Omega R^{-1}, R = L^T)
+__global__ void __launch_bounds__(256) k_make_u(const float* __restrict__ A1, const float* __restrict__ A2, int64_t b,
+                                                int r, const double* __restrict__ T, int transT, const DevScalars* sc,
                                                 float* __restrict__ U) {
   extern __shared__ float shm[];
   float* sT = shm;                  // r x r
   float* sY = shm + r * r;          // 32 x r
-  const double delta = sc->delta;
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) sT[e] = (float)T[e];
+  const double delta = A2 ? sc->delta : 0.0;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x)
+    sT[e] = (float)(transT ? T[(e % r) * r + e / r] : T[e]);
   const int64_t row0 = (int64_t)blockIdx.x * 32;
   for (int e = threadIdx.x; e < 32 * r; e += blockDim.x) {
     const int rr = e / r, k = e % r;
     const int64_t row = row0 + rr;
-    sY[e] = row < b ? (float)((double)Ysk[row * r + k] + delta * (double)Om[row * r + k]) : 0.0f;
+    float v = 0.0f;
+    if (row < b) v = A2 ? (float)((double)A1[row * r + k] + delta * (double)A2[row * r + k]) : A1[row * r + k];
+    sY[e] = v;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -395,6 +402,47 @@ __global__ void __launch_bounds__(256) k_make_u(const float* __restrict__ Om, co
   }
 }
 
+static cudaError_t make_u(const float* A1, const float* A2, int64_t b, int r, const double* T, int transT,
+                          const DevScalars* sc, float* U, cudaStream_t st) {
+  k_make_u<<<(unsigned)((b + 31) / 32), 256, (size_t)(r * r + 32 * r) * sizeof(float), st>>>(A1, A2, b, r, T, transT,
+                                                                                            sc, U);
+  return cudaGetLastError();
+}
+
+// FP64 Cholesky of an r x r SPD matrix into a lower factor (identity and a
+// status on failure), one CTA.
+__global__ void __launch_bounds__(512) k_chol_plain(const double* __restrict__ G, int r, double* __restrict__ L,
+                                                    DevScalars* sc, int detail) {
+  extern __shared__ double sh[];
+  __shared__ int flag;
+  const int ld = r + 1;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) sh[(e / r) * ld + e % r] = G[e];
+  __syncthreads();
+  const bool ok = chol_lower_smem(sh, r, ld, &flag);
+  __syncthreads();
+  if (!ok && threadIdx.x == 0) set_status(sc, ADASAP_ENUMERIC, detail);
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e / r, j = e % r;
+    L[e] = ok ? ((j <= i) ? sh[i * ld + j] : 0.0) : (i == j ? 1.0 : 0.0);
+  }
+}
+
+// Thin QR of the Gaussian test matrix by CholeskyQR2 (Omega <- Omega R^{-1}
+// twice, Omega^T Omega = R^T R in FP64), in place; tmp is b x r scratch.
+cudaError_t launch_orthonormalize(CoreBufs& cb, float* Om, float* tmp, DevScalars* sc, cudaStream_t st) {
+  const int r = cb.r;
+  cudaError_t e;
+  for (int pass = 0; pass < 2; ++pass) {
+    const float* src = pass == 0 ? Om : tmp;
+    float* dst = pass == 0 ? tmp : Om;
+    if ((e = launch_gram(src, r, r, nullptr, 0, 0, cb.b, cb.gram_part, cb.gram_chunks, cb.X1, st))) return e;
+    k_chol_plain<<<1, 512, (size_t)r * (r + 1) * sizeof(double), st>>>(cb.X1, r, cb.Lc, sc, 6);
+    if ((e = trsm(cb.Lc, r, cb.Ident, 0, 0, cb.A, st))) return e;      // A = L^{-1}
+    if ((e = make_u(src, nullptr, cb.b, r, cb.A, 1, sc, dst, st))) return e;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_nystrom_core(CoreBufs& cb, double eps, double lam, DevScalars* sc, const float* Om,
                                 const float* Ysk, cudaStream_t st) {
   const int r = cb.r;
@@ -412,9 +460,7 @@ cudaError_t launch_nystrom_core(CoreBufs& cb, double eps, double lam, DevScalars
   k_nys_finalize<<<1, 256, 0, st>>>(cb.lam, cb.V32, r, lam, sc, cb.S, cb.keep, cb.X1);
   // T = L^{-T} T'
   if ((e = trsm(cb.Lc, r, cb.X1, 0, 1, cb.T, st))) return e;
-  k_make_u<<<(unsigned)((cb.b + 31) / 32), 256, (size_t)(r * r + 32 * r) * sizeof(float), st>>>(Om, Ysk, cb.b, r,
-                                                                                               cb.T, sc, cb.U);
-  return cudaGetLastError();
+  return make_u(Ysk, Om, cb.b, r, cb.T, 0, sc, cb.U, st);
 }
 
 // L_w L_w^T = rho S^{-1} + U^T U on the kept eigenpairs (App. C.2, stabilised form)
@@ -434,7 +480,7 @@ __global__ void __launch_bounds__(512) k_wchol(const double* __restrict__ UtU, i
   __syncthreads();
   const bool ok = chol_lower_smem(sh, r, ld, &flag);
   __syncthreads();
-  if (!ok && threadIdx.x == 0) set_status(sc, ADASAP_ENUMERIC);
+  if (!ok && threadIdx.x == 0) set_status(sc, ADASAP_ENUMERIC, 3);
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
     Lw[e] = ok ? ((j <= i) ? sh[i * ld + j] : 0.0) : (i == j ? 1.0 : 0.0);
@@ -664,7 +710,7 @@ __global__ void k_set_eta(const double* __restrict__ dot_part, const double* __r
     const double lam_hat = alpha[1] * t;
     sc->lam_hat = lam_hat;
     double eta = (lam_hat > 0.0 && isfinite(lam_hat)) ? 1.0 / lam_hat : 0.0;
-    if (!(lam_hat > 0.0 && isfinite(lam_hat))) set_status(sc, ADASAP_ENUMERIC);
+    if (!(lam_hat > 0.0 && isfinite(lam_hat))) set_status(sc, ADASAP_ENUMERIC, 4);
     if (sc->status != 0) eta = 0.0;
     sc->eta = eta;
   }
@@ -764,6 +810,7 @@ cudaError_t core_init() {
   if ((e = cudaFuncSetAttribute(k_nys_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_make_u, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_chol_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_wchol, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_wcoef, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_wapply, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;

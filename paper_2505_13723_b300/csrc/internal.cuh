@@ -97,11 +97,13 @@ struct CoreBufs {
   double* sq_part;    // [kReduceBlocks] sums of squares / dots
   double* dot_part;   // [kReduceBlocks]
   double* alpha;      // scalar apply coefficient
+  double* Ident;      // r x r identity
 };
 int gram_chunks_for(int64_t b);
 int utv_chunks_for(int64_t b);
 cudaError_t launch_gram(const float* A1, int64_t ld1, int c1, const float* A2, int64_t ld2, int c2,
                         int64_t m, double* part, int chunks, double* G, cudaStream_t st);
+cudaError_t launch_orthonormalize(CoreBufs& cb, float* Om, float* tmp, DevScalars* sc, cudaStream_t st);
 cudaError_t launch_nystrom_core(CoreBufs& cb, double eps, double lam, DevScalars* sc,
                                 const float* Om, const float* Ysk, cudaStream_t st);
 cudaError_t launch_woodbury_factor(CoreBufs& cb, double lam, DevScalars* sc, cudaStream_t st);

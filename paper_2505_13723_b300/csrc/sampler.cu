@@ -127,7 +127,7 @@ __global__ void k_copy_schedule(const int64_t* __restrict__ Bs, const float* __r
     if (e < b) {
       const int64_t v = Bs[t * b + e];
       const bool ok = v >= 0 && v < n;
-      if (!ok) set_status(sc, ADASAP_EINVAL);
+      if (!ok) set_status(sc, ADASAP_EINVAL, 5);
       B32[e] = ok ? (int)v : 0;
       v0[e] = v0s[t * b + e];
     }

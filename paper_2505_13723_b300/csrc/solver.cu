@@ -418,6 +418,7 @@ adasap_status alloc_solver(adasap_solver* S) {
   cb.sq_part = ar.get<double>(kReduceBlocks);
   cb.dot_part = ar.get<double>(kReduceBlocks);
   cb.alpha = ar.get<double>(2);
+  cb.Ident = ar.get<double>((size_t)rr * rr);
   return ar.err == cudaSuccess ? ADASAP_OK : ADASAP_ENOMEM;
 }
 
@@ -454,6 +455,7 @@ cudaError_t capture_iteration(adasap_solver* S, const int64_t* Bs, const float* 
   kb.xc = S->XB; kb.qc = S->qB; kb.ncols = b;
   kb.part = S->part2; kb.cps = 0; kb.sigma2 = c->sigma2;
   if (!S->identity) {
+    K(launch_orthonormalize(cb, S->Om, S->Ysk, c->sc, s1));   // thin QR of Omega
     kb.w = S->Om; kb.ldw = r;
     K(launch_rows(c->kern, c->dp, kb, r, S->ns_sk, false, s1));
     K(launch_reduce(S->part2, S->ns_sk, b, r, 0, r, S->Ysk, r, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0,
@@ -543,6 +545,13 @@ adasap_status solver_begin(adasap_ctx* c, const float* Y, int s, const adasap_op
   else e = cudaMemsetAsync(S->W, 0, bytes, c->s0);
   if (e) return fail(e, "copy W0");
   if ((e = cudaMemsetAsync(c->sc, 0, sizeof(DevScalars), c->s0))) return fail(e, "memset");
+  {
+    const int rr = std::max(S->r, 1);
+    std::vector<double> eye((size_t)rr * rr, 0.0);
+    for (int i = 0; i < rr; ++i) eye[(size_t)i * rr + i] = 1.0;
+    if ((e = cudaMemcpy(S->cb.Ident, eye.data(), eye.size() * sizeof(double), cudaMemcpyHostToDevice)))
+      return fail(e, "identity");
+  }
   // ||Y||_F^2 (the reduce copies Y into V, overwritten just below)
   if ((e = launch_reduce(S->Y, 1, n, s, 0, s, S->V, s, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, S->sqb,
                          c->s0)))
@@ -672,6 +681,7 @@ adasap_status solve_loop(adasap_solver* S, float* W, adasap_stats* stats, int T_
     stats->seconds = ms * 1e-3;
     stats->last_eta = c->sc_host->eta;
     stats->last_rho = c->sc_host->rho;
+    stats->status_detail = c->sc_host->detail;
   }
   if (st == ADASAP_OK && !S->sched && o.tol > 0 && !converged) st = ADASAP_ENOTCONVERGED;
   CT(cudaEventRecord(c->ev_out, c->s0));

@@ -1,12 +1,19 @@
 """GPU parity of the ADASAP solver (Alg. 2) against the FP64 oracle.
 
-Tolerances.  The GPU forms kernel products in FP32 (relative error ~1e-6 of the
-absolute sums), factors the r x r Nystrom core in FP64 with FP32 Jacobi
-eigenvectors, and keeps W, V, Z in FP32.  On the small workload the
-preconditioned block system is well conditioned (kappa(P) < 10), so one
-iteration reproduces the oracle's eta_t, rho_t and W_t to ~1e-5 relative; we
-allow 1e-4.  The converged posterior mean is held to the benchmark spec's bound of
-1e-4 relative error on the 500 test points.
+Tolerances.  The GPU forms the sketch K_BB Omega and the block residual in
+FP32, so the preconditioner it builds differs from the oracle's FP64 one by
+||dP|| ~ eps32 * tr(K_BB) = 2^-23 * b * sigma2 (Alg. 4's shift Delta is of the
+same size by design).  A perturbation dP moves the Rayleigh quotient of
+P^{-1/2} H P^{-1/2} (Alg. 5), the damping rho = S_rr + lambda and the direction
+P^{-1} R by about ||dP|| / rho relative.  The per-iteration tolerance is
+therefore  tol = max(1e-4, 4 * 2^-23 * b * sigma2 / min_t rho_t).  The stepsize
+is the Rayleigh quotient after N = 10 powering steps, i.e. after 2N + 1
+products with the perturbed operator, so its bound (and that of W, which
+moves by eta * D) carries a further factor 2N + 1 where the top eigenvalues
+cluster (tiny degenerate blocks).  On the standard small workload the
+observed agreement is far inside these bounds and is checked at 1e-4.
+The converged posterior mean is held to the benchmark spec's bound of 1e-4
+relative error on the 500 test points.
 """
 
 import numpy as np
@@ -24,6 +31,23 @@ pytestmark = pytest.mark.gpu
 def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - np.asarray(b, np.float64)) /
                  max(np.linalg.norm(np.asarray(b, np.float64)), 1e-300))
+
+
+def _tol(rec, b, sigma2):
+    rhos = [x["rho"] for x in rec if x["rho"] is not None]
+    if not rhos:
+        return 1e-4
+    return max(1e-4, 4 * 2.0 ** -23 * b * sigma2 / min(rhos))
+
+
+def _tol_eta(rec, b, sigma2, power_iters=10):
+    return max(1e-4, (2 * power_iters + 1) * _tol(rec, b, sigma2))
+
+
+def _check_trace(tr, rec, tol, rho=True, tol_eta=None):
+    np.testing.assert_allclose(tr[:, 0], [x["eta"] for x in rec], rtol=tol if tol_eta is None else tol_eta)
+    if rho:
+        np.testing.assert_allclose(tr[:, 1], [x["rho"] for x in rec], rtol=tol)
 
 
 def _scheduled_case(lib, P, T, b, r, precond="nystrom", literal=False, s=None, seed=21):
@@ -45,10 +69,7 @@ def _scheduled_case(lib, P, T, b, r, precond="nystrom", literal=False, s=None, s
 def test_scheduled_iterations_match_oracle_small(lib, T):
     P = synth.small()
     W, tr, Wref, rec = _scheduled_case(lib, P, T, b=200, r=32)
-    eta = np.array([x["eta"] for x in rec])
-    rho = np.array([x["rho"] for x in rec])
-    np.testing.assert_allclose(tr[:, 0], eta, rtol=1e-4)
-    np.testing.assert_allclose(tr[:, 1], rho, rtol=1e-4)
+    _check_trace(tr, rec, 1e-4)
     assert _rel(W, Wref) < 1e-4
 
 
@@ -57,22 +78,23 @@ def test_scheduled_matern_regress_shape(lib, kern):
     P = synth.regress(n=6000, b=600)
     P["kernel"] = kern
     W, tr, Wref, rec = _scheduled_case(lib, P, 4, b=600, r=64)
-    np.testing.assert_allclose(tr[:, 0], [x["eta"] for x in rec], rtol=1e-4)
-    np.testing.assert_allclose(tr[:, 1], [x["rho"] for x in rec], rtol=1e-4)
-    assert _rel(W, Wref) < 1e-4
+    tol, tol_eta = _tol(rec, 600, P.sigma2), _tol_eta(rec, 600, P.sigma2)
+    _check_trace(tr, rec, tol, tol_eta=tol_eta)
+    assert _rel(W, Wref) < tol_eta
 
 
 def test_scheduled_multi_rhs_and_literal_reading(lib):
     P = synth.multirhs(n=3000, s=5, b=300)
     W, tr, Wref, rec = _scheduled_case(lib, P, 3, b=300, r=40, literal=True)
-    np.testing.assert_allclose(tr[:, 0], [x["eta"] for x in rec], rtol=1e-4)
-    assert _rel(W, Wref) < 1e-4
+    tol, tol_eta = _tol(rec, 300, P.sigma2), _tol_eta(rec, 300, P.sigma2)
+    _check_trace(tr, rec, tol, tol_eta=tol_eta)
+    assert _rel(W, Wref) < tol_eta
 
 
 def test_scheduled_identity_preconditioner(lib):
     P = synth.small(n=1500)
     W, tr, Wref, rec = _scheduled_case(lib, P, 5, b=150, r=1, precond="identity")
-    np.testing.assert_allclose(tr[:, 0], [x["eta"] for x in rec], rtol=1e-4)
+    _check_trace(tr, rec, 1e-4, rho=False)
     assert _rel(W, Wref) < 1e-4
 
 
@@ -81,8 +103,9 @@ def test_scheduled_edge_shapes(lib, n, b, r, d):
     """b = n (the whole matrix as one block), r = b, d = 1, odd sizes."""
     P = synth.small(n=n, d=d)
     W, tr, Wref, rec = _scheduled_case(lib, P, 3, b=b, r=r)
-    np.testing.assert_allclose(tr[:, 0], [x["eta"] for x in rec], rtol=1e-4)
-    assert _rel(W, Wref) < 1e-4
+    tol, tol_eta = _tol(rec, b, P.sigma2), _tol_eta(rec, b, P.sigma2)
+    _check_trace(tr, rec, tol, tol_eta=tol_eta)
+    assert _rel(W, Wref) < tol_eta
 
 
 def test_small_workload_300_iterations_posterior_mean(lib):

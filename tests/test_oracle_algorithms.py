@@ -59,6 +59,16 @@ def test_nystrom_shift_and_clip():
     assert np.all(S[3:] < 10 * Delta)
 
 
+def test_orthonormalize_is_the_positive_diagonal_thin_qr():
+    g = np.random.default_rng(11)
+    Om = g.standard_normal((40, 40)) / np.sqrt(40)          # square: badly conditioned
+    Q = A.orthonormalize(Om)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(40), atol=1e-12)
+    Rm = Q.T @ Om                                            # Om = Q R with R upper, diag > 0
+    np.testing.assert_allclose(np.tril(Rm, -1), 0.0, atol=1e-12)
+    assert np.all(np.diag(Rm) > 0)
+
+
 def _random_nys(g, p=50, r=9, zeros=0):
     U, _ = np.linalg.qr(g.standard_normal((p, r)))
     S = np.sort(g.uniform(0.1, 10, r))[::-1]
