@@ -13,18 +13,20 @@
 // singular vectors V and its eigenvalues Sigma^2, and U = Y_nu (C^{-1} V Sigma^{-1}).
 // Y_nu^T Y_nu comes from the Gram of [Omega | M Omega] without forming Y_nu.
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.cuh"
 
 namespace adasap {
 
 // ---------------------------------------------------------------------------
-// Gram matrix of the row-concatenation [A1 | A2] (m x (c1 + c2), c <= 256) in
-// FP64: the products of the FP32 entries are exact in FP64 (24 + 24 bits) and
-// are accumulated in FP64.  Exactness matters: B^T B = C^{-T} (Y_nu^T Y_nu) C^{-1}
-// multiplies the Gram's absolute error by cond(C)^2, so FP32 products would
-// swamp the small Nystrom eigenvalues.  Only upper 32 x 32 tiles are computed;
-// the reduce mirrors them.
+// Gram matrix of the row-concatenation [A1 | A2] (m x (c1 + c2), c <= 256),
+// accumulated in FP64.  With `exact` the products of the FP32 entries are
+// formed in FP64 (exact: 24 + 24 bits).  Exactness matters for Y_nu^T Y_nu:
+// B^T B = C^{-T} (Y_nu^T Y_nu) C^{-1} multiplies its absolute error by cond(C)^2,
+// so FP32 products would swamp the small Nystrom eigenvalues; everywhere else
+// an FP32 product error of eps * |a| |b| is below the data's own rounding.
+// Only upper 64 x 64 tiles are computed; the reduce mirrors them.
 // ---------------------------------------------------------------------------
 int gram_chunks_for(int64_t b) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, (b + 255) / 256)); }
 
@@ -35,43 +37,66 @@ __device__ __forceinline__ float cat_get(const float* A1, int64_t ld1, int c1, c
   return 0.0f;
 }
 
+// 64 x 64 output tiles, 256 threads x (4 x 4) outputs, 16-row slices.
+// EXACT: products and sums in FP64 (exact products of FP32 entries);
+// otherwise FP32 products summed in FP32 over a 16-row slice, then in FP64.
+template <bool EXACT>
 __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1, int64_t ld1, int c1,
                                                    const float* __restrict__ A2, int64_t ld2, int c2,
                                                    int64_t m, int64_t chunk_rows, double* __restrict__ part) {
+  constexpr int TS = 64, KR = 16;
+  using T = typename std::conditional<EXACT, double, float>::type;
   const int ti = blockIdx.y, tj = blockIdx.z;
   if (ti > tj) return;
   const int c = c1 + c2;
-  __shared__ float sa[32][33];
-  __shared__ float sb[32][33];
+  __shared__ T sa[KR][TS + 1];
+  __shared__ T sb[KR][TS + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int64_t r0 = (int64_t)blockIdx.x * chunk_rows;
   const int64_t r1 = min(m, r0 + chunk_rows);
-  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
-  for (int64_t s0 = r0; s0 < r1; s0 += 32) {
+  double acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+  for (int64_t s0 = r0; s0 < r1; s0 += KR) {
     __syncthreads();
-    for (int e = tid; e < 32 * 32; e += 256) {
-      const int rr = e >> 5, cc = e & 31;
+    for (int e = tid; e < KR * TS; e += 256) {
+      const int rr = e / TS, cc = e % TS;
       const int64_t row = s0 + rr;
       const bool ok = row < r1;
-      sa[rr][cc] = ok ? cat_get(A1, ld1, c1, A2, ld2, c2, row, ti * 32 + cc) : 0.0f;
-      sb[rr][cc] = ok ? cat_get(A1, ld1, c1, A2, ld2, c2, row, tj * 32 + cc) : 0.0f;
+      sa[rr][cc] = ok ? (T)cat_get(A1, ld1, c1, A2, ld2, c2, row, ti * TS + cc) : (T)0;
+      sb[rr][cc] = ok ? (T)cat_get(A1, ld1, c1, A2, ld2, c2, row, tj * TS + cc) : (T)0;
     }
     __syncthreads();
-#pragma unroll 8
-    for (int rr = 0; rr < 32; ++rr) {
-      const double a0 = sa[rr][2 * ty], a1 = sa[rr][2 * ty + 1];
-      const double b0 = sb[rr][2 * tx], b1 = sb[rr][2 * tx + 1];
-      acc[0][0] = fma(a0, b0, acc[0][0]);
-      acc[0][1] = fma(a0, b1, acc[0][1]);
-      acc[1][0] = fma(a1, b0, acc[1][0]);
-      acc[1][1] = fma(a1, b1, acc[1][1]);
+    T f[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) f[u][v] = (T)0;
+#pragma unroll 4
+    for (int rr = 0; rr < KR; ++rr) {
+      T a[4], bb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = sa[rr][ty + 16 * u];
+        bb[u] = sb[rr][tx + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) f[u][v] = fma(a[u], bb[v], f[u][v]);
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] += (double)f[u][v];
   }
 #pragma unroll
-  for (int u = 0; u < 2; ++u)
+  for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 2; ++v) {
-      const int i = ti * 32 + 2 * ty + u, j = tj * 32 + 2 * tx + v;
+    for (int v = 0; v < 4; ++v) {
+      const int i = ti * TS + ty + 16 * u, j = tj * TS + tx + 16 * v;
       if (i < c && j < c) part[((int64_t)blockIdx.x * c + i) * c + j] = acc[u][v];
     }
 }
@@ -79,7 +104,7 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1,
 __global__ void k_gram_reduce(const double* __restrict__ part, int chunks, int c, double* __restrict__ G) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < c * c; e += gridDim.x * blockDim.x) {
     int i = e / c, j = e % c;
-    if ((i >> 5) > (j >> 5)) { const int t = i; i = j; j = t; }
+    if ((i >> 6) > (j >> 6)) { const int t = i; i = j; j = t; }
     double acc = 0.0;
     for (int ch = 0; ch < chunks; ++ch) acc += part[((int64_t)ch * c + i) * c + j];
     G[e] = acc;
@@ -87,11 +112,14 @@ __global__ void k_gram_reduce(const double* __restrict__ part, int chunks, int c
 }
 
 cudaError_t launch_gram(const float* A1, int64_t ld1, int c1, const float* A2, int64_t ld2, int c2,
-                        int64_t m, double* part, int chunks, double* G, cudaStream_t st) {
+                        int64_t m, double* part, int chunks, double* G, bool exact, cudaStream_t st) {
   const int c = c1 + c2;
-  const int nt = (c + 31) / 32;
+  const int nt = (c + 63) / 64;
   const int64_t chunk_rows = (m + chunks - 1) / chunks;
-  k_gram_part<<<dim3(chunks, nt, nt), 256, 0, st>>>(A1, ld1, c1, A2, ld2, c2, m, chunk_rows, part);
+  if (exact)
+    k_gram_part<true><<<dim3(chunks, nt, nt), 256, 0, st>>>(A1, ld1, c1, A2, ld2, c2, m, chunk_rows, part);
+  else
+    k_gram_part<false><<<dim3(chunks, nt, nt), 256, 0, st>>>(A1, ld1, c1, A2, ld2, c2, m, chunk_rows, part);
   k_gram_reduce<<<std::min(148, (c * c + 255) / 256), 256, 0, st>>>(part, chunks, c, G);
   return cudaGetLastError();
 }
@@ -125,7 +153,8 @@ __device__ bool chol_lower_smem(double* A, int r, int ld, int* flag) {
 
 // Alg. 4, first half: Delta, C = chol(Omega^T M Omega + Delta Omega^T Omega)
 // (stored as the lower factor L = C^T), and Y_nu^T Y_nu.
-__global__ void __launch_bounds__(512) k_nys_chol(const double* __restrict__ G, int r, double eps,
+__global__ void __launch_bounds__(512) k_nys_chol(const double* __restrict__ G, const double* __restrict__ Gyy,
+                                                  int r, double eps,
                                                   double* __restrict__ Lout, double* __restrict__ Gnu,
                                                   DevScalars* sc) {
   extern __shared__ double sh[];
@@ -158,7 +187,7 @@ __global__ void __launch_bounds__(512) k_nys_chol(const double* __restrict__ G, 
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
     Lout[e] = (j <= i) ? sh[i * ld + j] : 0.0;
-    const double yty = G[(int64_t)(r + i) * c + r + j];
+    const double yty = Gyy[(int64_t)i * r + j];
     const double cross = G[(int64_t)i * c + r + j] + G[(int64_t)j * c + r + i];
     Gnu[e] = yty + delta * cross + delta * delta * G[(int64_t)i * c + j];
   }
@@ -170,26 +199,37 @@ __global__ void __launch_bounds__(512) k_nys_chol(const double* __restrict__ G, 
 
 // Column-wise triangular solves with the lower factor L (r x r, row-major):
 //   upper == 0:  L X = R'     upper == 1:  L^T X = R'
-// where R' = trans ? R^T : R.  One warp per right-hand side column.
-__global__ void k_trsm(const double* __restrict__ L, int r, const double* __restrict__ R, int trans, int upper,
-                       double* __restrict__ X) {
-  extern __shared__ double xs[];
+// where R' = trans ? R^T : R.  L and the reciprocals of its diagonal are
+// staged in shared memory; one warp per right-hand side column.
+constexpr int kTrsmWarps = 4;
+__global__ void __launch_bounds__(32 * kTrsmWarps) k_trsm(const double* __restrict__ L, int r,
+                                                          const double* __restrict__ R, int trans, int upper,
+                                                          double* __restrict__ X) {
+  extern __shared__ double shd[];
+  const int ld = r + 1;
+  double* sL = shd;                       // r x (r + 1)
+  double* rinv = shd + r * ld;            // r
+  double* xs = rinv + r;                  // kTrsmWarps x r
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) sL[(e / r) * ld + e % r] = L[e];
+  __syncthreads();
+  for (int i = threadIdx.x; i < r; i += blockDim.x) rinv[i] = 1.0 / sL[i * ld + i];
+  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int col = blockIdx.x * (blockDim.x >> 5) + warp;
+  const int col = blockIdx.x * kTrsmWarps + warp;
   if (col >= r) return;
   double* x = xs + warp * r;
   for (int step = 0; step < r; ++step) {
     const int i = upper ? r - 1 - step : step;
     double part = 0.0;
     if (!upper) {
-      for (int k = lane; k < i; k += 32) part += L[(int64_t)i * r + k] * x[k];
+      for (int k = lane; k < i; k += 32) part += sL[i * ld + k] * x[k];
     } else {
-      for (int k = i + 1 + lane; k < r; k += 32) part += L[(int64_t)k * r + i] * x[k];
+      for (int k = i + 1 + lane; k < r; k += 32) part += sL[k * ld + i] * x[k];
     }
     part = warp_sum(part);
     if (lane == 0) {
       const double rhs = trans ? R[(int64_t)col * r + i] : R[(int64_t)i * r + col];
-      x[i] = (rhs - part) / L[(int64_t)i * r + i];
+      x[i] = (rhs - part) * rinv[i];
     }
     __syncwarp();
   }
@@ -197,15 +237,15 @@ __global__ void k_trsm(const double* __restrict__ L, int r, const double* __rest
 }
 
 static cudaError_t trsm(const double* L, int r, const double* R, int trans, int upper, double* X, cudaStream_t st) {
-  const int wpb = 2;
-  k_trsm<<<(r + wpb - 1) / wpb, 32 * wpb, wpb * r * sizeof(double), st>>>(L, r, R, trans, upper, X);
+  const size_t smem = ((size_t)r * (r + 1) + r + (size_t)kTrsmWarps * r) * sizeof(double);
+  k_trsm<<<(r + kTrsmWarps - 1) / kTrsmWarps, 32 * kTrsmWarps, smem, st>>>(L, r, R, trans, upper, X);
   return cudaGetLastError();
 }
 
 // Cyclic Jacobi (parallel round-robin ordering) on the symmetric r x r matrix
 // A / max(diag A) in FP32, accumulating the rotations in V.  A rotation is
-// skipped when |a_pq| <= 1e-7 sqrt(|a_pp a_qq|); the sweeps stop when a sweep
-// skips all of them (at most 30 sweeps).
+// skipped when |a_pq| <= 1e-7 sqrt(|a_pp a_qq|) or |a_pq| <= 1e-9 (below FP32
+// resolution); the sweeps stop when a sweep skips all of them (at most 30).
 __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ A, int r, float* __restrict__ Vout) {
   extern __shared__ float shf[];
   const int r2 = r + (r & 1), ld = r2 + 1;
@@ -248,7 +288,9 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ A, i
         if (p > q) { const int t = p; p = q; q = t; }
         const float apq = a[p * ld + q], app = a[p * ld + p], aqq = a[q * ld + q];
         float c = 1.0f, s = 0.0f;
-        if (fabsf(apq) > 1e-7f * sqrtf(fabsf(app * aqq)) && fabsf(apq) > 1e-35f) {
+        // skip entries already below the FP32 resolution of their diagonal pair or of
+        // the matrix (scaled so that max diag = 1)
+        if (fabsf(apq) > 1e-7f * sqrtf(fabsf(app * aqq)) && fabsf(apq) > 1e-9f) {
           const float tau = (aqq - app) / (2.0f * apq);
           const float t = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
           c = 1.0f / sqrtf(1.0f + t * t);
@@ -435,7 +477,9 @@ cudaError_t launch_orthonormalize(CoreBufs& cb, float* Om, float* tmp, DevScalar
   for (int pass = 0; pass < 2; ++pass) {
     const float* src = pass == 0 ? Om : tmp;
     float* dst = pass == 0 ? tmp : Om;
-    if ((e = launch_gram(src, r, r, nullptr, 0, 0, cb.b, cb.gram_part, cb.gram_chunks, cb.X1, st))) return e;
+    // pass 1 exact (a near-square Omega has cond^2 beyond FP32); pass 2 sees cond ~ 1
+    if ((e = launch_gram(src, r, r, nullptr, 0, 0, cb.b, cb.gram_part, cb.gram_chunks, cb.X1, pass == 0, st)))
+      return e;
     k_chol_plain<<<1, 512, (size_t)r * (r + 1) * sizeof(double), st>>>(cb.X1, r, cb.Lc, sc, 6);
     if ((e = trsm(cb.Lc, r, cb.Ident, 0, 0, cb.A, st))) return e;      // A = L^{-1}
     if ((e = make_u(src, nullptr, cb.b, r, cb.A, 1, sc, dst, st))) return e;
@@ -448,9 +492,10 @@ cudaError_t launch_nystrom_core(CoreBufs& cb, double eps, double lam, DevScalars
   const int r = cb.r;
   cudaError_t e;
   // Gram of [Omega | M Omega] -> (Omega^T Omega, Omega^T Y, Y^T Y)
-  if ((e = launch_gram(Om, r, r, Ysk, r, r, cb.b, cb.gram_part, cb.gram_chunks, cb.G, st))) return e;
+  if ((e = launch_gram(Om, r, r, Ysk, r, r, cb.b, cb.gram_part, cb.gram_chunks, cb.G, false, st))) return e;
+  if ((e = launch_gram(Ysk, r, r, nullptr, 0, 0, cb.b, cb.gram_part, cb.gram_chunks, cb.Gyy, true, st))) return e;
   const size_t sm_chol = (size_t)r * (r + 1) * sizeof(double);
-  k_nys_chol<<<1, 512, sm_chol, st>>>(cb.G, r, eps, cb.Lc, cb.Gnu, sc);
+  k_nys_chol<<<1, 512, sm_chol, st>>>(cb.G, cb.Gyy, r, eps, cb.Lc, cb.Gnu, sc);
   // A = L^{-1} Gnu L^{-T}  (= C^{-T} Y_nu^T Y_nu C^{-1} = B^T B)
   if ((e = trsm(cb.Lc, r, cb.Gnu, 0, 0, cb.X1, st))) return e;
   if ((e = trsm(cb.Lc, r, cb.X1, 1, 0, cb.A, st))) return e;
@@ -491,7 +536,7 @@ cudaError_t launch_woodbury_factor(CoreBufs& cb, double lam, DevScalars* sc, cud
   (void)lam;
   const int r = cb.r;
   cudaError_t e;
-  if ((e = launch_gram(cb.U, r, r, nullptr, 0, 0, cb.b, cb.gram_part, cb.gram_chunks, cb.X1, st))) return e;
+  if ((e = launch_gram(cb.U, r, r, nullptr, 0, 0, cb.b, cb.gram_part, cb.gram_chunks, cb.X1, false, st))) return e;
   k_wchol<<<1, 512, (size_t)r * (r + 1) * sizeof(double), st>>>(cb.X1, r, cb.S, cb.keep, sc, cb.Lw);
   return cudaGetLastError();
 }
@@ -569,17 +614,22 @@ __global__ void __launch_bounds__(256) k_wcoef(int mode, const double* __restric
   }
   __syncthreads();
   if (mode == kInv) {
-    // y = L^{-T} L^{-1} (keep . q), one thread per column
-    for (int c = threadIdx.x; c < s; c += blockDim.x) {
+    // y = L^{-T} L^{-1} (keep . q): one warp per column, lanes split each dot product
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = warp; c < s; c += nw) {
       for (int i = 0; i < r; ++i) {
-        double acc = keep[i] * q[i * s + c];
-        for (int k = 0; k < i; ++k) acc -= Lw[i * r + k] * q[k * s + c];
-        q[i * s + c] = acc / Lw[i * r + i];
+        double part = 0.0;
+        for (int k = lane; k < i; k += 32) part += Lw[i * r + k] * q[k * s + c];
+        part = warp_sum(part);
+        if (lane == 0) q[i * s + c] = (keep[i] * q[i * s + c] - part) / Lw[i * r + i];
+        __syncwarp();
       }
       for (int i = r - 1; i >= 0; --i) {
-        double acc = q[i * s + c];
-        for (int k = i + 1; k < r; ++k) acc -= Lw[k * r + i] * q[k * s + c];
-        q[i * s + c] = acc / Lw[i * r + i];
+        double part = 0.0;
+        for (int k = i + 1 + lane; k < r; k += 32) part += Lw[k * r + i] * q[k * s + c];
+        part = warp_sum(part);
+        if (lane == 0) q[i * s + c] = (q[i * s + c] - part) / Lw[i * r + i];
+        __syncwarp();
       }
     }
     __syncthreads();
@@ -811,6 +861,7 @@ cudaError_t core_init() {
   if ((e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_make_u, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_chol_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_wchol, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_wcoef, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_wapply, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;

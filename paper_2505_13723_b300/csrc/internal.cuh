@@ -82,6 +82,7 @@ struct CoreBufs {
   double* G;          // 2r x 2r
   double* Lc;         // r x r lower Cholesky of the Nystrom core
   double* Gnu;        // r x r  Y_nu^T Y_nu
+  double* Gyy;        // r x r  Y^T Y with exact products
   double* X1;         // r x r  scratch
   double* A;          // r x r  B^T B
   float* V32;         // r x r  eigenvectors (FP32 Jacobi)
@@ -102,7 +103,7 @@ struct CoreBufs {
 int gram_chunks_for(int64_t b);
 int utv_chunks_for(int64_t b);
 cudaError_t launch_gram(const float* A1, int64_t ld1, int c1, const float* A2, int64_t ld2, int c2,
-                        int64_t m, double* part, int chunks, double* G, cudaStream_t st);
+                        int64_t m, double* part, int chunks, double* G, bool exact, cudaStream_t st);
 cudaError_t launch_orthonormalize(CoreBufs& cb, float* Om, float* tmp, DevScalars* sc, cudaStream_t st);
 cudaError_t launch_nystrom_core(CoreBufs& cb, double eps, double lam, DevScalars* sc,
                                 const float* Om, const float* Ysk, cudaStream_t st);

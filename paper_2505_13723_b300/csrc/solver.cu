@@ -403,6 +403,7 @@ adasap_status alloc_solver(adasap_solver* S) {
   cb.G = ar.get<double>((size_t)4 * rr * rr);
   cb.Lc = ar.get<double>((size_t)rr * rr);
   cb.Gnu = ar.get<double>((size_t)rr * rr);
+  cb.Gyy = ar.get<double>((size_t)rr * rr);
   cb.X1 = ar.get<double>((size_t)rr * rr);
   cb.A = ar.get<double>((size_t)rr * rr);
   cb.V32 = ar.get<float>((size_t)rr * rr);
