@@ -187,7 +187,7 @@ def config_dict(P):
     return {"workload": "regress: n=%d, d=11, X~U[0,1]^11, Matern-3/2 ell=0.3, lambda=1e-3, b=%d, r=100, s=1"
                         % (P.X.shape[0], P.b),
             "n": int(P.X.shape[0]), "d": 11, "kernel": "matern32", "b": int(P.b), "r": 100, "s": 1,
-            "power_iters": 10, "precision": "fp32", "l2": "flushed between timed steps",
+            "power_iters": 10, "l2": "flushed between timed steps",
             "parallelism": "replicas"}
 
 
@@ -250,6 +250,7 @@ def run_ours(args, rank, world, dist):
     t_local = sum(step_ms) / 1e3
     rel = sol.residual()
     eta, rho, status = sol.scalars()
+    diag = sol.diag()
     sol.close()
     t_max = t_local
     if dist is not None:
@@ -263,19 +264,26 @@ def run_ours(args, rank, world, dist):
     g = np.random.default_rng(5)
     B = torch.from_numpy(g.choice(n, size=b, replace=False)).to(dev)
     Wv = torch.from_numpy(g.standard_normal((n, 1)).astype(np.float32)).to(dev)
-    for _ in range(3):
-        ctx.kernel_rows(B, Wv)
-    ks = [torch.cuda.Event(enable_timing=True) for _ in range(args.kernel_launches)]
-    ke = [torch.cuda.Event(enable_timing=True) for _ in range(args.kernel_launches)]
-    with ClockSampler(local) as kclk:
-        torch.cuda.synchronize()
-        for i in range(args.kernel_launches):
-            flush.zero_()
-            ks[i].record(stream)
+
+    def time_kernel(prec):
+        ctx.set_precision(prec)
+        for _ in range(3):
             ctx.kernel_rows(B, Wv)
-            ke[i].record(stream)
-        torch.cuda.synchronize()
-    k_ms = statistics.mean(s.elapsed_time(e) for s, e in zip(ks, ke))
+        ks = [torch.cuda.Event(enable_timing=True) for _ in range(args.kernel_launches)]
+        ke = [torch.cuda.Event(enable_timing=True) for _ in range(args.kernel_launches)]
+        with ClockSampler(local) as kc:
+            torch.cuda.synchronize()
+            for i in range(args.kernel_launches):
+                flush.zero_()
+                ks[i].record(stream)
+                ctx.kernel_rows(B, Wv)
+                ke[i].record(stream)
+            torch.cuda.synchronize()
+        return statistics.mean(s.elapsed_time(e) for s, e in zip(ks, ke)), kc
+
+    default_prec = ctx.prec if hasattr(ctx, "prec") else lib.PREC_TF32X3
+    fp32_ms, _ = time_kernel(lib.PREC_FP32)
+    k_ms, kclk = time_kernel(default_prec)
     k_rate = b * n / (k_ms * 1e-3)
     pk, pk_src = peaks()
     mhz = float(pk.get("sm_max_mhz", 2032.0))
@@ -284,12 +292,15 @@ def run_ours(args, rank, world, dist):
     # ---- time to relative residual 1e-3 (FP32), bounded
     tol_run = None
     if not args.no_tol_run and rank == 0:
-        topts = lib.default_opts(n, b=b, r=r, seed=2, tol=1e-3, max_iters=300, check_every=25,
-                                 check_rows=20000)
-        W, st, stc = ctx.solve(Yd, opts=topts)
-        tol_run = {"fp32": {"seconds": st["seconds"], "iters": st["iters"], "rel_resid": st["rel_resid"],
-                            "reached": bool(st["rel_resid"] <= 1e-3), "resid_rows_sampled": 20000},
-                   "mixed": None}
+        tol_run = {}
+        for name, prec in (("fp32", lib.PREC_FP32), ("mixed", lib.PREC_TF32X3)):
+            ctx.set_precision(prec)
+            topts = lib.default_opts(n, b=b, r=r, seed=2, tol=1e-3, max_iters=300, check_every=25,
+                                     check_rows=20000)
+            W, st, stc = ctx.solve(Yd, opts=topts)
+            tol_run[name] = {"seconds": st["seconds"], "iters": st["iters"], "rel_resid": st["rel_resid"],
+                             "reached": bool(st["rel_resid"] <= 1e-3), "resid_rows_sampled": 20000}
+        ctx.set_precision(default_prec)
 
     # ---- end to end through the C-ABI with host buffers
     e2e = None
@@ -324,19 +335,26 @@ def run_ours(args, rank, world, dist):
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": repr(ex)}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "tf32x3+f32" if default_prec == lib.PREC_TF32X3 else "f32", "data": "synthetic",
             "config": config_dict(P),
             "roofline": {"bound": "alu", "achieved": k_rate / 1e9, "peak": peak_entries / 1e9,
                          "unit": "Gentries/s", "frac": k_rate / peak_entries, "traffic": None,
-                         "kernel": "k_rows_narrow (Step I block-row product, b=%d rows x n=%d)" % (b, n),
+                         "kernel": ("k_rows_tc (tcgen05 TF32x3 distances)" if default_prec == lib.PREC_TF32X3
+                                    else "k_rows_narrow (FP32)")
+                                   + " Step I block-row product, b=%d rows x n=%d" % (b, n),
                          "ms_per_launch": k_ms,
+                         "fp32_cuda_core_kernel": {"ms_per_launch": fp32_ms,
+                                                   "achieved": b * n / (fp32_ms * 1e-3) / 1e9},
                          "peak_basis": "MUFU: %d/clk/SM x %d SMs x %.0f MHz / %d MUFU per entry (sm_max_mhz %s)"
                                        % (MUFU_PER_CLK_SM, SMS, mhz, mufu_per_entry(P.kernel), pk_src)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": kernels_per_iter * args.steps,
             "clocks": clk.summary(), "kernel_clocks": kclk.summary(),
             "time_to_tol": tol_run,
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
-            "solver_state": {"rel_resid_after": rel, "eta": eta, "rho": rho, "status": status}}
+            "solver_state": {"rel_resid_after": rel, "eta": eta, "rho": rho, "status": status,
+                             "jacobi_sweeps": diag["jacobi_sweeps"], "chol_retries": diag["chol_retries"],
+                             "delta": diag["delta"]}}
     print(json.dumps(line), flush=True)
 
 

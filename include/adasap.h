@@ -57,6 +57,14 @@ typedef enum {
 
 typedef enum { ADASAP_RBF = 0, ADASAP_MATERN32 = 1, ADASAP_MATERN52 = 2 } adasap_kernel;
 
+/* Arithmetic of the single-right-hand-side kernel-row products (Step I, the
+ * K_BB v products of Alg. 5, predict, residual checks):
+ *   ADASAP_PREC_FP32    FP32 CUDA-core distances and epilogue
+ *   ADASAP_PREC_TF32X3  distances on the tensor cores (tcgen05, TF32 hi/lo split
+ *                       with three products; FP32 epilogue); needs d <= 30.
+ * Products with more than one right-hand side use the FP32 CUDA-core kernels. */
+typedef enum { ADASAP_PREC_FP32 = 0, ADASAP_PREC_TF32X3 = 1 } adasap_precision;
+
 /* Options of adasap_solve.  adasap_default_opts fills the paper's defaults. */
 typedef struct {
   int64_t b;           /* block size (Alg. 2); 0 < b <= n.  Default n/100 (App. D.2). */
@@ -100,6 +108,9 @@ const char* adasap_last_error(void);
 adasap_status adasap_create(const float* X, int64_t n, int d, int kernel, float ell,
                             float sigma2, float lambda, void* stream, adasap_ctx** out);
 void adasap_destroy(adasap_ctx* ctx);
+/* Select the arithmetic of later calls on this context (default: ADASAP_PREC_TF32X3
+ * when d <= 30, else ADASAP_PREC_FP32).  EINVAL if unavailable. */
+adasap_status adasap_set_precision(adasap_ctx* ctx, int precision);
 
 /* Block-row kernel product (Alg. 2 Step I; App. C.1 ColDistMatMat as one kernel):
  *   out (b x s) = K(X_B, X) W,  B (b) int64 row indices into X, W (n x s).
@@ -144,6 +155,10 @@ adasap_status adasap_solver_residual(adasap_solver* sol, double* rel_resid, void
 adasap_status adasap_solver_get_w(adasap_solver* sol, float* W, void* stream);
 adasap_status adasap_solver_scalars(adasap_solver* sol, double* eta, double* rho, int* status, void* stream);
 void adasap_solver_end(adasap_solver* sol);
+/* Diagnostics of the last iteration (synchronises): out[0..8] = Delta, rho, eta,
+ * lambda_hat, Cholesky shift increases, Jacobi sweeps, status, status detail,
+ * iteration counter; the first `count` are written. */
+adasap_status adasap_solver_diag(adasap_solver* sol, double* out, int count, void* stream);
 /* Number of kernel launches in one captured iteration (for launch accounting). */
 adasap_status adasap_solver_graph_kernels(adasap_solver* sol, int* count);
 

@@ -21,6 +21,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 RBF, MATERN32, MATERN52 = 0, 1, 2
+PREC_FP32, PREC_TF32X3 = 0, 1
 KERNELS = {"rbf": RBF, "matern32": MATERN32, "matern52": MATERN52}
 
 STATUS = {0: "ADASAP_OK", 1: "ADASAP_EINVAL", 2: "ADASAP_ENOMEM", 3: "ADASAP_ECUDA",
@@ -32,7 +33,8 @@ SYMBOLS = ["adasap_default_opts", "adasap_status_string", "adasap_last_error", "
            "adasap_destroy", "adasap_kernel_rows", "adasap_solve", "adasap_solve_scheduled",
            "adasap_predict", "adasap_hypergrad", "adasap_sample", "adasap_solver_begin",
            "adasap_solver_step", "adasap_solver_residual", "adasap_solver_get_w",
-           "adasap_solver_scalars", "adasap_solver_end", "adasap_solver_graph_kernels"]
+           "adasap_solver_scalars", "adasap_solver_end", "adasap_solver_graph_kernels",
+           "adasap_solver_diag", "adasap_set_precision"]
 
 
 class Opts(ctypes.Structure):
@@ -65,6 +67,8 @@ _lib.adasap_create.argtypes = [_P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_fl
                                ctypes.c_float, _P, ctypes.POINTER(_P)]
 _lib.adasap_destroy.argtypes = [_P]
 _lib.adasap_destroy.restype = None
+_lib.adasap_set_precision.argtypes = [_P, ctypes.c_int]
+_lib.adasap_set_precision.restype = ctypes.c_int
 _lib.adasap_kernel_rows.argtypes = [_P, _P, _I64, _P, ctypes.c_int, _P, _P]
 _lib.adasap_solve.argtypes = [_P, _P, ctypes.c_int, ctypes.POINTER(Opts), _P, ctypes.POINTER(Stats), _P]
 _lib.adasap_solve_scheduled.argtypes = [_P, _P, ctypes.c_int, ctypes.POINTER(Opts), _P, _P, _P,
@@ -81,6 +85,8 @@ _lib.adasap_solver_scalars.argtypes = [_P, ctypes.POINTER(ctypes.c_double), ctyp
                                        ctypes.POINTER(ctypes.c_int), _P]
 _lib.adasap_solver_graph_kernels.argtypes = [_P, ctypes.POINTER(ctypes.c_int)]
 _lib.adasap_solver_graph_kernels.restype = ctypes.c_int
+_lib.adasap_solver_diag.argtypes = [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int, _P]
+_lib.adasap_solver_diag.restype = ctypes.c_int
 _lib.adasap_solver_end.argtypes = [_P]
 _lib.adasap_solver_end.restype = None
 for _f in ["adasap_solver_begin", "adasap_solver_step", "adasap_solver_residual", "adasap_solver_get_w",
@@ -143,7 +149,7 @@ def default_opts(n, **kw):
 class Context:
     """adasap_create / adasap_destroy around the training inputs X (n x d)."""
 
-    def __init__(self, X, kernel, ell, sigma2, lam, stream=None):
+    def __init__(self, X, kernel, ell, sigma2, lam, stream=None, precision=None):
         kernel = KERNELS.get(kernel, kernel)
         n, d = X.shape
         h = ctypes.c_void_p()
@@ -152,6 +158,13 @@ class Context:
         self.h = h
         self.n, self.d, self.kernel = n, d, int(kernel)
         self.ell, self.sigma2, self.lam = float(ell), float(sigma2), float(lam)
+        if precision is not None:
+            self.set_precision(precision)
+
+    def set_precision(self, prec):
+        """PREC_FP32 (CUDA-core FP32) or PREC_TF32X3 (tensor-core split distances)."""
+        _check(_lib.adasap_set_precision(self.h, int(prec)), "adasap_set_precision")
+        self.prec = int(prec)
 
     def close(self):
         if getattr(self, "h", None):
@@ -259,6 +272,13 @@ class Solver:
         _check(_lib.adasap_solver_scalars(self.h, ctypes.byref(eta), ctypes.byref(rho), ctypes.byref(st),
                                           _stream(stream)), "adasap_solver_scalars")
         return eta.value, rho.value, st.value
+
+    DIAG = ["delta", "rho", "eta", "lam_hat", "chol_retries", "jacobi_sweeps", "status", "detail", "t"]
+
+    def diag(self, stream=None):
+        out = (ctypes.c_double * len(self.DIAG))()
+        _check(_lib.adasap_solver_diag(self.h, out, len(self.DIAG), _stream(stream)), "adasap_solver_diag")
+        return dict(zip(self.DIAG, list(out)))
 
     def graph_kernels(self):
         k = ctypes.c_int()

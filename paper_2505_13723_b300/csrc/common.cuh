@@ -111,6 +111,7 @@ struct DevScalars {
                      // eigenvalue, 3 Woodbury Cholesky, 4 non-positive stepsize estimate,
                      // 5 schedule row out of range, 6 test-matrix QR Cholesky
   int chol_retries;  // number of Delta increases in the last iteration
+  int jacobi_sweeps; // sweeps of the last eigen-solve
   long long t;       // iteration counter
 };
 

@@ -242,92 +242,106 @@ static cudaError_t trsm(const double* L, int r, const double* R, int trans, int 
   return cudaGetLastError();
 }
 
-// Cyclic Jacobi (parallel round-robin ordering) on the symmetric r x r matrix
-// A / max(diag A) in FP32, accumulating the rotations in V.  A rotation is
-// skipped when |a_pq| <= 1e-7 sqrt(|a_pp a_qq|) or |a_pq| <= 1e-9 (below FP32
-// resolution); the sweeps stop when a sweep skips all of them (at most 30).
-__global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ A, int r, float* __restrict__ Vout) {
+// Eigenvectors of the symmetric PSD r x r matrix A by one-sided (Hestenes)
+// Jacobi in FP32: W = A V is rotated column pair by column pair until its
+// columns are orthogonal; then A V = W and, A being PSD, V holds A's
+// eigenvectors (the eigenvalues are refined in FP64 by k_rayleigh).
+// Parallel round-robin ordering: in each of the r2 - 1 rounds of a sweep the
+// r2/2 disjoint pairs are rotated concurrently, one warp per pair, so a round
+// needs one barrier.  W and V are stored column-major in shared memory.  A
+// pair is skipped when |w_p . w_q| <= 1e-6 |w_p| |w_q| or when it is below what
+// the columns' absolute FP32 noise can produce; sweeps stop when one rotates
+// nothing (at most kJacobiSweeps; Jacobi converges quadratically).
+constexpr int kJacobiSweeps = 12;
+__global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ A, int r, float* __restrict__ Vout,
+                                                 DevScalars* sc) {
   extern __shared__ float shf[];
-  const int r2 = r + (r & 1), ld = r2 + 1;
-  float* a = shf;
-  float* v = shf + r2 * ld;
-  __shared__ int pp[64], qq[64];
-  __shared__ float cc[64], ss[64];
-  __shared__ double red[33];
+  const int r2 = r + (r & 1);
+  float* w = shf;               // r2 columns x r2 rows (column-major)
+  float* v = shf + r2 * r2;
+  __shared__ float mxs[32];
   __shared__ int nrot;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double mx = 0.0;
   for (int i = threadIdx.x; i < r; i += blockDim.x) mx = fmax(mx, fabs(A[(int64_t)i * r + i]));
-  // block max via shared memory
-  __shared__ double mxs[32];
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) mxs[threadIdx.x >> 5] = mx;
+  if (lane == 0) mxs[warp] = (float)mx;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double m = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, mxs[w]);
-    red[0] = m > 0.0 ? m : 1.0;
-  }
-  __syncthreads();
-  const double scale = 1.0 / red[0];
+  float amax = 0.f;
+  for (int k = 0; k < nw; ++k) amax = fmaxf(amax, mxs[k]);
+  const double scale = amax > 0.f ? 1.0 / (double)amax : 1.0;
   for (int e = threadIdx.x; e < r2 * r2; e += blockDim.x) {
-    const int i = e / r2, j = e % r2;
-    a[i * ld + j] = (i < r && j < r) ? (float)(A[(int64_t)i * r + j] * scale) : 0.0f;
-    v[i * ld + j] = (i == j) ? 1.0f : 0.0f;
+    const int col = e / r2, row = e % r2;
+    w[e] = (row < r && col < r) ? (float)(A[(int64_t)row * r + col] * scale) : 0.0f;
+    v[e] = (row == col) ? 1.0f : 0.0f;
   }
   __syncthreads();
+  // largest column norm^2 (scaled) for the absolute floor
+  float cmax = 0.f;
+  for (int col = warp; col < r; col += nw) {
+    float t = 0.f;
+    for (int k = lane; k < r2; k += 32) t = fmaf(w[col * r2 + k], w[col * r2 + k], t);
+    t = warp_sum(t);
+    cmax = fmaxf(cmax, t);
+  }
+  if (lane == 0) mxs[warp] = cmax;
+  __syncthreads();
+  float nmax = 0.f;
+  for (int k = 0; k < nw; ++k) nmax = fmaxf(nmax, mxs[k]);
+  // absolute FP32 noise carried by every column after rotations against the
+  // largest one: a dot product below noise * (|w_p| + |w_q|) cannot be reduced
+  const float noise = 4.0f * 1.1920929e-7f * sqrtf(nmax);
   const int half = r2 / 2;
-  for (int sweep = 0; sweep < 30; ++sweep) {
+  int sweep = 0;
+  for (; sweep < kJacobiSweeps; ++sweep) {
     if (threadIdx.x == 0) nrot = 0;
     __syncthreads();
     for (int round = 0; round < r2 - 1; ++round) {
-      if (threadIdx.x < half) {
-        const int m = threadIdx.x;
+      for (int m = warp; m < half; m += nw) {
         int p, q;
         if (m == 0) { p = round; q = r2 - 1; }
         else { p = (round + m) % (r2 - 1); q = (round - m + r2 - 1) % (r2 - 1); }
-        if (p > q) { const int t = p; p = q; q = t; }
-        const float apq = a[p * ld + q], app = a[p * ld + p], aqq = a[q * ld + q];
-        float c = 1.0f, s = 0.0f;
-        // skip entries already below the FP32 resolution of their diagonal pair or of
-        // the matrix (scaled so that max diag = 1)
-        if (fabsf(apq) > 1e-7f * sqrtf(fabsf(app * aqq)) && fabsf(apq) > 1e-9f) {
-          const float tau = (aqq - app) / (2.0f * apq);
-          const float t = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
-          c = 1.0f / sqrtf(1.0f + t * t);
-          s = t * c;
-          atomicAdd(&nrot, 1);
+        float* wp = w + p * r2;
+        float* wq = w + q * r2;
+        float al = 0.f, be = 0.f, ga = 0.f;
+        for (int k = lane; k < r2; k += 32) {
+          const float a = wp[k], b = wq[k];
+          al = fmaf(a, a, al);
+          be = fmaf(b, b, be);
+          ga = fmaf(a, b, ga);
         }
-        pp[m] = p; qq[m] = q; cc[m] = c; ss[m] = s;
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < half * r2; e += blockDim.x) {
-        const int m = e / r2, k = e % r2;
-        const float c = cc[m], s = ss[m];
-        if (s == 0.0f) continue;
-        const int p = pp[m], q = qq[m];
-        const float akp = a[k * ld + p], akq = a[k * ld + q];
-        a[k * ld + p] = c * akp - s * akq;
-        a[k * ld + q] = s * akp + c * akq;
-        const float vkp = v[k * ld + p], vkq = v[k * ld + q];
-        v[k * ld + p] = c * vkp - s * vkq;
-        v[k * ld + q] = s * vkp + c * vkq;
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < half * r2; e += blockDim.x) {
-        const int m = e / r2, k = e % r2;
-        const float c = cc[m], s = ss[m];
-        if (s == 0.0f) continue;
-        const int p = pp[m], q = qq[m];
-        const float apk = a[p * ld + k], aqk = a[q * ld + k];
-        a[p * ld + k] = c * apk - s * aqk;
-        a[q * ld + k] = s * apk + c * aqk;
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (fabsf(ga) > 1e-6f * sqrtf(al * be) && fabsf(ga) > noise * (sqrtf(al) + sqrtf(be))) {
+          const float zeta = (be - al) / (2.0f * ga);
+          const float t = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+          const float c = rsqrtf(1.0f + t * t);
+          const float s = c * t;
+          float* vp = v + p * r2;
+          float* vq = v + q * r2;
+          for (int k = lane; k < r2; k += 32) {
+            const float a = wp[k], b = wq[k];
+            wp[k] = c * a - s * b;
+            wq[k] = s * a + c * b;
+            const float x = vp[k], y = vq[k];
+            vp[k] = c * x - s * y;
+            vq[k] = s * x + c * y;
+          }
+          if (lane == 0) atomicAdd(&nrot, 1);
+        }
       }
       __syncthreads();
     }
     if (nrot == 0) break;
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) Vout[e] = v[(e / r) * ld + (e % r)];
+  if (threadIdx.x == 0) sc->jacobi_sweeps = sweep;
+  // Vout row-major: Vout[k * r + i] = component k of eigenvector i
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int k = e / r, i = e % r;
+    Vout[e] = v[i * r2 + k];
+  }
 }
 
 // lambda_i = v_i^T A v_i / v_i^T v_i in FP64 (one block per eigenvector)
@@ -500,7 +514,7 @@ cudaError_t launch_nystrom_core(CoreBufs& cb, double eps, double lam, DevScalars
   if ((e = trsm(cb.Lc, r, cb.Gnu, 0, 0, cb.X1, st))) return e;
   if ((e = trsm(cb.Lc, r, cb.X1, 1, 0, cb.A, st))) return e;
   const int r2 = r + (r & 1);
-  k_jacobi<<<1, 1024, (size_t)2 * r2 * (r2 + 1) * sizeof(float), st>>>(cb.A, r, cb.V32);
+  k_jacobi<<<1, 1024, (size_t)2 * r2 * r2 * sizeof(float), st>>>(cb.A, r, cb.V32, sc);
   k_rayleigh<<<r, 128, 0, st>>>(cb.A, cb.V32, r, cb.lam);
   k_nys_finalize<<<1, 256, 0, st>>>(cb.lam, cb.V32, r, lam, sc, cb.S, cb.keep, cb.X1);
   // T = L^{-T} T'

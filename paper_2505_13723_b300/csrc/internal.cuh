@@ -62,6 +62,20 @@ cudaError_t launch_transform(const float* X, int64_t n, int d, int dp, const dou
 // int64 indices -> int32, entries outside [0, n) become -1.
 cudaError_t launch_index32(const int64_t* in, int64_t m, int64_t n, int* out, cudaStream_t st);
 
+// ---- tensor-core block-row product (rows_tc.cu) ------------------------------------
+// K of the augmented MMA operands (16 or 32; 0 if d + 2 > 32) and padded row count.
+int tc_kp(int d);
+int64_t tc_npad(int64_t n);
+cudaError_t tc_init();
+int tc_nsplit(int64_t m, int64_t ncols);
+// Split (hi, lo) column operands in the MMA layout for X' (or rows gidx of X').
+cudaError_t launch_build_tc(const float* X, const float* q, const int* gidx, int64_t n, int d, int dp, float* hi,
+                            float* lo, cudaStream_t st);
+// part[p][i] = sigma2 * sum_{j in split p} k(x'_{row i}, x'_j) w[j] (s = 1).
+cudaError_t launch_rows_tc(int kern, int d, const float* xr, const float* qr, const int* ridx, int64_t m, int dp,
+                           const float* bhi, const float* blo, int64_t ncols, int self_mode, const float* w,
+                           int64_t ldw, float* part, int nsplit, float sigma2, int* err, cudaStream_t st);
+
 // ---- sampler (Philox4x32-10; definitions in sampler.cu) -------------------------
 cudaError_t launch_sample_block(uint64_t seed, const long long* t_dev, int64_t t_host, int64_t n,
                                 int64_t b, int stream_tag, int* B32, int64_t* B64, cudaStream_t st);

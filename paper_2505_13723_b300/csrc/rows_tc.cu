@@ -1,0 +1,504 @@
+// Block-row kernel product on the 5th-generation tensor cores (tcgen05 + TMEM).
+//
+// The same product as k_rows_narrow (Alg. 2 Step I, K_Bn w; the K_BB v products
+// of Alg. 5; the posterior mean), with the squared distances formed by MMAs:
+//   a_i = [-2 x'_i, q_i, 1, 0...],  b_j = [x'_j, 1, q_j, 0...]   (K = KP >= d + 2)
+//   u_ij = a_i . b_j = q_i + q_j - 2 x'_i . x'_j = ||x'_i - x'_j||^2
+// FP32 accuracy is recovered with a TF32 hi/lo split of both operands and three
+// MMAs, hi.hi + hi.lo + lo.hi (the dropped lo.lo term is 2^-22 relative); a
+// row paired with its own column (the diagonal of K_BB / K_Bn) gets u = 0.
+//
+// CTA = 128 rows x a column range, 384 threads:
+//   warp 0       producer: bulk copies (cp.async.bulk, the TMA engine) of
+//                128-column operand tiles into a 2-stage shared-memory ring
+//   warp 1       owns the TMEM allocation (2 x 128 FP32 accumulator columns)
+//                and issues the MMAs from one thread (tcgen05.mma kind::tf32,
+//                M = 128, N = 128, K = 8 per instruction)
+//   warps 4..11  epilogue: two warpgroups, each tcgen05.ld-ing 64 columns of
+//                its 128 TMEM lanes (one row per thread), applying the RBF /
+//                Matern epilogue and contracting with w in registers
+// Operands live in shared memory in the no-swizzle K-major canonical layout:
+// 8-row core groups of 16-byte K chunks (LBO = 128 B between K chunks,
+// SBO = 32 * KP B between 8-row groups).  The column operands are prebuilt in
+// that layout in global memory (padded to a multiple of 128 rows), so a tile
+// is one contiguous copy.  Every mbarrier wait is bounded: on timeout the CTA
+// raises an error flag, drains its own copies and MMAs, frees TMEM and writes
+// NaN partials.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace adasap {
+
+constexpr int kTcM = 128, kTcN = 128, kTcThreads = 384;
+constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kWaitPolls = 1u << 20;  // a legitimate wait is one pipeline stage
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred P;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, P;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on an mbarrier phase; false on timeout or when another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  for (uint32_t it = 0; it < kWaitPolls; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u && *abort_flag) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                   smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Shared-memory matrix descriptor: start address, leading (K) byte offset,
+// stride (8-row group) byte offset, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46);
+}
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, N = 128, M = 128.
+constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+                                ((uint32_t)(kTcM >> 4) << 24);
+
+#define TMEM_LD32(taddr, r)                                                                                        \
+  asm volatile(                                                                                                    \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18," \
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                                               \
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),          \
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),    \
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),  \
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])   \
+      : "r"(taddr))
+
+// tcgen05.wait::ld with the loaded registers as operands, so that no use of
+// them can be scheduled before the wait.
+#define TMEM_WAIT32(r)                                                                                             \
+  asm volatile("tcgen05.wait::ld.sync.aligned;"                                                                    \
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),  \
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),          \
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),        \
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),        \
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])                                                             \
+               :                                                                                                   \
+               : "memory")
+
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t y;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+  return __uint_as_float(y);
+}
+
+// float offset of element (row, k) in the no-swizzle K-major layout
+template <int KP>
+__host__ __device__ __forceinline__ int64_t tc_off(int64_t row, int k) {
+  return (row >> 3) * (8 * KP) + (k >> 2) * 32 + (row & 7) * 4 + (k & 3);
+}
+
+template <int KP>
+struct TcSmem {
+  static constexpr int OPF = kTcM * KP;  // floats per 128-row operand tile
+  static constexpr size_t ops_bytes = (size_t)6 * OPF * sizeof(float);
+  static constexpr size_t bytes = ops_bytes + 16 * sizeof(uint64_t) + 16 + 128 * sizeof(float) + 16 + 1024;
+};
+
+struct TcArgs {
+  const float* xr;   // rows, x' form (m rows of stride dp), or gathered block
+  const float* qr;
+  const int* ridx;   // row -> source row (NULL: identity); < 0 marks an invalid row
+  int64_t m;
+  int dp, d;
+  const float* bhi;  // columns: split operands in the canonical layout (npad rows)
+  const float* blo;
+  int64_t ncols;
+  int self_mode;     // 1: column j is the same point as the row's source index
+  const float* w;
+  int64_t ldw;
+  int wvec;          // w is 16-byte aligned with ldw == 1: float4 loads allowed
+  float* part;       // nsplit x m
+  int64_t cps;       // columns per split (multiple of 128)
+  float sigma2;
+  int* err;          // set to 1 on a wait timeout
+};
+
+template <int KERN, int KP>
+__global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(TcArgs a) {
+  using L = TcSmem<KP>;
+  constexpr int OPF = L::OPF;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+  float* sAhi = reinterpret_cast<float*>(base);
+  float* sAlo = sAhi + OPF;
+  float* sB = sAlo + OPF;  // [stage][hi, lo][OPF]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + L::ops_bytes);
+  uint64_t* full = bars;        // [2]
+  uint64_t* empty = bars + 2;   // [2]
+  uint64_t* tfull = bars + 4;   // [2]
+  uint64_t* tempty = bars + 6;  // [2]
+  uint64_t* drain = bars + 8;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 16);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  float* red = reinterpret_cast<float*>(tslot + 4);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t row0 = (int64_t)blockIdx.x * kTcM;
+  const int64_t c0 = (int64_t)blockIdx.y * a.cps;
+  const int64_t c1 = min(a.ncols, c0 + a.cps);
+  const int ntiles = c1 > c0 ? (int)((c1 - c0 + kTcN - 1) / kTcN) : 0;
+
+  // ---- set-up: barriers, row operands (hi/lo split), TMEM ------------------
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 8);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (tid < kTcM) {
+    const int64_t ri = row0 + tid;
+    float av[KP];
+#pragma unroll
+    for (int k = 0; k < KP; ++k) av[k] = 0.0f;
+    bool ok = ri < a.m;
+    int64_t src = ri;
+    if (ok && a.ridx) {
+      const int id = a.ridx[ri];
+      ok = id >= 0;
+      src = id;
+    }
+    if (ok) {
+      for (int k = 0; k < a.d; ++k) av[k] = -2.0f * a.xr[src * a.dp + k];
+      av[a.d] = a.qr[src];
+    } else {
+      av[a.d] = 1e20f;  // padded or invalid row: u is huge, the kernel value 0
+    }
+    av[a.d + 1] = 1.0f;
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      const float hi = tf32_round(av[k]);
+      const float lo = tf32_round(av[k] - hi);
+      sAhi[tc_off<KP>(tid, k)] = hi;
+      sAlo[tc_off<KP>(tid, k)] = lo;
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+
+  if (warp == 0) {
+    // ---- producer --------------------------------------------------------------
+    if (lane == 0) {
+      int issued = 0;
+      for (int t = 0; t < ntiles; ++t) {
+        const int st = t & 1;
+        const uint32_t ph = (uint32_t)(t >> 1) & 1u;
+        if (!mbar_wait(&empty[st], ph ^ 1u, abort_flag)) {
+          *abort_flag = 1;
+          break;
+        }
+        mbar_arrive_expect_tx(&full[st], 2u * OPF * sizeof(float));
+        const int64_t off = (c0 + (int64_t)t * kTcN) * KP;
+        bulk_g2s(sB + (st * 2 + 0) * OPF, a.bhi + off, OPF * sizeof(float), &full[st]);
+        bulk_g2s(sB + (st * 2 + 1) * OPF, a.blo + off, OPF * sizeof(float), &full[st]);
+        issued = t + 1;
+      }
+      if (*abort_flag) {
+        // our copies still write shared memory: wait (bounded) for the last ones
+        for (int t = max(0, issued - 2); t < issued; ++t) {
+          const int st = t & 1;
+          const uint32_t ph = (uint32_t)(t >> 1) & 1u;
+          for (uint32_t it = 0; it < kWaitPolls && !mbar_try_wait(&full[st], ph); ++it) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer -------------------------------------------------------------
+    if (lane == 0) {
+      int issued = 0;
+      for (int t = 0; t < ntiles; ++t) {
+        const int st = t & 1, buf = t & 1;
+        const uint32_t ph = (uint32_t)(t >> 1) & 1u;
+        if (!mbar_wait(&full[st], ph, abort_flag) || !mbar_wait(&tempty[buf], ph ^ 1u, abort_flag)) {
+          *abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dt = tbase + (uint32_t)(buf * kTcN);
+        const uint32_t a_hi = smem_u32(sAhi), a_lo = smem_u32(sAlo);
+        const uint32_t b_hi = smem_u32(sB + (st * 2 + 0) * OPF), b_lo = smem_u32(sB + (st * 2 + 1) * OPF);
+        uint32_t acc = 0;
+#pragma unroll
+        for (int pass = 0; pass < 3; ++pass) {
+          const uint32_t A = pass == 2 ? a_lo : a_hi;
+          const uint32_t B = pass == 1 ? b_lo : b_hi;
+#pragma unroll
+          for (int ks = 0; ks < KP / 8; ++ks) {
+            tc_mma_tf32(dt, smem_desc(A + 256u * ks, 128u, 32u * KP), smem_desc(B + 256u * ks, 128u, 32u * KP),
+                        kIdescTf32, acc);
+            acc = 1;
+          }
+        }
+        tc_commit(&empty[st]);
+        tc_commit(&tfull[buf]);
+        issued = t + 1;
+      }
+      if (issued > 0) {
+        // all MMAs of this thread complete before TMEM is released
+        tc_commit(drain);
+        for (uint32_t it = 0; it < kWaitPolls && !mbar_try_wait(drain, 0); ++it) {
+        }
+      }
+    }
+  } else if (warp >= 4) {
+    // ---- epilogue ------------------------------------------------------------------
+    const int g = (warp - 4) >> 2, qd = warp & 3;
+    const int rl = qd * 32 + lane;
+    const int64_t ri = row0 + rl;
+    int64_t gi = -1;
+    bool bad = false;
+    if (ri < a.m) {
+      const int64_t src = a.ridx ? (int64_t)a.ridx[ri] : ri;
+      bad = src < 0;
+      if (a.self_mode) gi = src;
+    }
+    float acc = 0.0f, cmp = 0.0f;
+    for (int t = 0; t < ntiles; ++t) {
+      const int buf = t & 1;
+      const uint32_t ph = (uint32_t)(t >> 1) & 1u;
+      if (!mbar_wait(&tfull[buf], ph, abort_flag)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      uint32_t u0[32], u1[32];
+      const uint32_t taddr = tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)(buf * kTcN + g * 64);
+      TMEM_LD32(taddr, u0);
+      TMEM_LD32(taddr + 32u, u1);
+      TMEM_WAIT32(u0);
+      TMEM_WAIT32(u1);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
+      const int64_t jb = c0 + (int64_t)t * kTcN + g * 64;
+      float wv[64];
+      if (jb + 64 <= c1 && a.wvec) {
+        const float4* w4 = reinterpret_cast<const float4*>(a.w + jb);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const float4 x = __ldg(w4 + i);
+          wv[4 * i] = x.x; wv[4 * i + 1] = x.y; wv[4 * i + 2] = x.z; wv[4 * i + 3] = x.w;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 64; ++i) wv[i] = (jb + i < c1) ? __ldg(a.w + (jb + i) * a.ldw) : 0.0f;
+      }
+      const bool self_here = gi >= jb && gi < jb + 64;
+      float tacc = 0.0f;
+      if (__any_sync(0xffffffffu, self_here)) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float ua = (jb + i == gi) ? 0.0f : fmaxf(__uint_as_float(u0[i]), 0.0f);
+          const float ub = (jb + 32 + i == gi) ? 0.0f : fmaxf(__uint_as_float(u1[i]), 0.0f);
+          tacc = fmaf(kval<KERN>(ua), wv[i], tacc);
+          tacc = fmaf(kval<KERN>(ub), wv[32 + i], tacc);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          tacc = fmaf(kval<KERN>(fmaxf(__uint_as_float(u0[i]), 0.0f)), wv[i], tacc);
+          tacc = fmaf(kval<KERN>(fmaxf(__uint_as_float(u1[i]), 0.0f)), wv[32 + i], tacc);
+        }
+      }
+      const float y = tacc - cmp;
+      const float tt = acc + y;
+      cmp = (tt - acc) - y;
+      acc = tt;
+    }
+    // combine the two warpgroups' column halves
+    if (g == 1) red[rl] = acc - cmp;
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+    if (g == 0 && ri < a.m) {
+      const float tot = (acc - cmp) + red[rl];
+      a.part[(int64_t)blockIdx.y * a.m + ri] =
+          (bad || *abort_flag) ? __int_as_float(0x7fc00000) : a.sigma2 * tot;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0 && lane == 0 && *abort_flag && a.err) atomicExch(a.err, 1);
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Split column operands in the canonical layout, npad = multiple of 128 rows:
+//   b_j = [x'_j (d), 1, q_j, 0...] for j < n; padding rows [0, 1, 1e20, 0...].
+// With gidx, row j takes the point gidx[j] (a gathered block).
+template <int KP>
+__global__ void k_build_tc(const float* __restrict__ X, const float* __restrict__ q, const int* __restrict__ gidx,
+                           int64_t n, int64_t npad, int d, int dp, float* __restrict__ hi, float* __restrict__ lo) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < npad; j += (int64_t)gridDim.x * blockDim.x) {
+    float bv[KP];
+#pragma unroll
+    for (int k = 0; k < KP; ++k) bv[k] = 0.0f;
+    if (j < n) {
+      const int64_t src = gidx ? (int64_t)max(gidx[j], 0) : j;
+      for (int k = 0; k < d; ++k) bv[k] = X[src * dp + k];
+      bv[d + 1] = q[src];
+    } else {
+      bv[d + 1] = 1e20f;
+    }
+    bv[d] = 1.0f;
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      const float h = tf32_round(bv[k]);
+      hi[tc_off<KP>(j, k)] = h;
+      lo[tc_off<KP>(j, k)] = tf32_round(bv[k] - h);
+    }
+  }
+}
+
+int tc_kp(int d) { return d + 2 <= 16 ? 16 : (d + 2 <= 32 ? 32 : 0); }
+int64_t tc_npad(int64_t n) { return (n + kTcN - 1) / kTcN * kTcN; }
+
+cudaError_t launch_build_tc(const float* X, const float* q, const int* gidx, int64_t n, int d, int dp, float* hi,
+                            float* lo, cudaStream_t st) {
+  const int kp = tc_kp(d);
+  const int64_t npad = tc_npad(n);
+  const int blocks = (int)std::min<int64_t>((npad + 255) / 256, 148 * 8);
+  if (kp == 16) k_build_tc<16><<<blocks, 256, 0, st>>>(X, q, gidx, n, npad, d, dp, hi, lo);
+  else if (kp == 32) k_build_tc<32><<<blocks, 256, 0, st>>>(X, q, gidx, n, npad, d, dp, hi, lo);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+static int g_tc_slots = 0;  // resident CTAs of k_rows_tc per SM x SMs
+
+template <int KERN, int KP>
+static cudaError_t tc_setup() {
+  return cudaFuncSetAttribute(k_rows_tc<KERN, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)std::max<size_t>(TcSmem<KP>::bytes, 80 * 1024));
+}
+
+cudaError_t tc_init() {
+  cudaError_t e;
+  if ((e = tc_setup<0, 16>()) || (e = tc_setup<1, 16>()) || (e = tc_setup<2, 16>()) || (e = tc_setup<0, 32>()) ||
+      (e = tc_setup<1, 32>()) || (e = tc_setup<2, 32>()))
+    return e;
+  int per_sm = 0, dev = 0, sms = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_tc<1, 16>, kTcThreads,
+                                                         std::max<size_t>(TcSmem<16>::bytes, 80 * 1024))))
+    return e;
+  if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
+  g_tc_slots = std::max(1, per_sm) * sms;
+  return cudaSuccess;
+}
+
+// Column splits: whole 128-column tiles, and a CTA count close to a whole
+// number of waves of the resident slots.
+int tc_nsplit(int64_t m, int64_t ncols) {
+  const int64_t rt = (m + kTcM - 1) / kTcM;
+  const int64_t tiles = (ncols + kTcN - 1) / kTcN;
+  const int64_t slots = g_tc_slots > 0 ? g_tc_slots : 148;
+  int64_t best = 1;
+  double best_eff = -1.0;
+  for (int64_t ns = 1; ns <= std::min<int64_t>(tiles, 4096); ++ns) {
+    const int64_t tot = rt * ns;
+    const int64_t waves = (tot + slots - 1) / slots;
+    if (waves > 64) break;
+    // tiles per split is a ceiling, so the effective work per CTA is rounded up
+    const int64_t tps = (tiles + ns - 1) / ns;
+    const double eff = (double)(rt * tiles) / (double)(waves * slots * tps);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = ns;
+    }
+  }
+  return (int)best;
+}
+
+template <int KERN, int KP>
+static cudaError_t launch_tc_k(const TcArgs& a, int nsplit, cudaStream_t st) {
+  const dim3 grid((unsigned)((a.m + kTcM - 1) / kTcM), (unsigned)nsplit);
+  k_rows_tc<KERN, KP><<<grid, kTcThreads, std::max<size_t>(TcSmem<KP>::bytes, 80 * 1024), st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rows_tc(int kern, int d, const float* xr, const float* qr, const int* ridx, int64_t m, int dp,
+                           const float* bhi, const float* blo, int64_t ncols, int self_mode, const float* w,
+                           int64_t ldw, float* part, int nsplit, float sigma2, int* err, cudaStream_t st) {
+  if (m <= 0 || ncols <= 0) return cudaSuccess;
+  TcArgs a;
+  a.xr = xr; a.qr = qr; a.ridx = ridx; a.m = m; a.dp = dp; a.d = d;
+  a.bhi = bhi; a.blo = blo; a.ncols = ncols; a.self_mode = self_mode;
+  a.w = w; a.ldw = ldw; a.part = part; a.sigma2 = sigma2; a.err = err;
+  a.wvec = (ldw == 1 && (reinterpret_cast<uintptr_t>(w) & 15u) == 0) ? 1 : 0;
+  const int64_t tiles = (ncols + kTcN - 1) / kTcN;
+  a.cps = (tiles + nsplit - 1) / nsplit * kTcN;
+  const int kp = tc_kp(d);
+  if (kp == 16) {
+    if (kern == 0) return launch_tc_k<0, 16>(a, nsplit, st);
+    if (kern == 1) return launch_tc_k<1, 16>(a, nsplit, st);
+    return launch_tc_k<2, 16>(a, nsplit, st);
+  }
+  if (kp == 32) {
+    if (kern == 0) return launch_tc_k<0, 32>(a, nsplit, st);
+    if (kern == 1) return launch_tc_k<1, 32>(a, nsplit, st);
+    return launch_tc_k<2, 32>(a, nsplit, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace adasap

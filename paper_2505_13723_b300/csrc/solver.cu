@@ -24,6 +24,13 @@ namespace adasap {
 cudaError_t core_init();
 }
 
+// A product y = K(rows, X') w dispatched to the tensor-core kernel (s = 1,
+// split precision) or to the FP32 SIMT kernels.
+struct RowsPlan {
+  bool tc;
+  int nsplit;
+};
+
 static thread_local std::string g_last_error;
 
 static void note_error(cudaError_t e, const char* what) {
@@ -55,6 +62,12 @@ struct adasap_ctx {
   DevScalars* sc_host = nullptr;  // pinned
   void* ws = nullptr;             // kernel_rows workspace
   size_t ws_bytes = 0;
+  int prec = 0;                   // ADASAP_PREC_FP32 or ADASAP_PREC_TF32X3
+  int kp = 0;                     // K of the tensor-core operands (0: unavailable)
+  int64_t npad = 0;
+  float* tc_hi = nullptr;         // split column operands of X' (npad x kp, MMA layout)
+  float* tc_lo = nullptr;
+  int* err_dev = nullptr;         // device error flag of the tensor-core kernel
 };
 
 namespace {
@@ -149,6 +162,7 @@ adasap_status adasap_create(const float* X, int64_t n, int d, int kernel, float 
   cudaStream_t us = (cudaStream_t)stream;
   if (cudaGetDevice(&c->device) != cudaSuccess) return fail(ADASAP_ECUDA);
   if (core_init() != cudaSuccess) { note_error(cudaGetLastError(), "core_init"); return fail(ADASAP_ECUDA); }
+  if (tc_init() != cudaSuccess) { note_error(cudaGetLastError(), "tc_init"); return fail(ADASAP_ECUDA); }
   c->n = n;
   c->d = d;
   c->dp = padded_dim(d);
@@ -197,6 +211,19 @@ adasap_status adasap_create(const float* X, int64_t n, int d, int kernel, float 
       return fail(ADASAP_ECUDA);
     if (launch_transform(Xd, n, d, c->dp, c->mean_dev, c->kappa / (double)ell, c->Xc, c->qc, c->s0) != cudaSuccess)
       return fail(ADASAP_ECUDA);
+    c->kp = tc_kp(d);
+    if (cudaMalloc(&c->err_dev, sizeof(int)) != cudaSuccess ||
+        cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->s0) != cudaSuccess)
+      return fail(ADASAP_ENOMEM);
+    if (c->kp > 0) {
+      c->npad = tc_npad(n);
+      if (cudaMalloc(&c->tc_hi, (size_t)c->npad * c->kp * sizeof(float)) != cudaSuccess ||
+          cudaMalloc(&c->tc_lo, (size_t)c->npad * c->kp * sizeof(float)) != cudaSuccess)
+        return fail(ADASAP_ENOMEM);
+      if (launch_build_tc(c->Xc, c->qc, nullptr, n, d, c->dp, c->tc_hi, c->tc_lo, c->s0) != cudaSuccess)
+        return fail(ADASAP_ECUDA);
+      c->prec = ADASAP_PREC_TF32X3;
+    }
     if (cudaStreamSynchronize(c->s0) != cudaSuccess) return fail(ADASAP_ECUDA);
   }
   *out = c;
@@ -212,6 +239,9 @@ void adasap_destroy(adasap_ctx* c) {
   cudaFree(c->mean_dev);
   cudaFree(c->sc);
   cudaFree(c->ws);
+  cudaFree(c->tc_hi);
+  cudaFree(c->tc_lo);
+  cudaFree(c->err_dev);
   if (c->sc_host) cudaFreeHost(c->sc_host);
   cudaEvent_t evs[] = {c->ev_in, c->ev_fork, c->ev_join, c->ev_out, c->ev_t0, c->ev_t1};
   for (cudaEvent_t e : evs)
@@ -253,22 +283,46 @@ adasap_status grow_ws(adasap_ctx* c, size_t bytes) {
   return ADASAP_OK;
 }
 
+RowsPlan plan_rows(const adasap_ctx* c, int64_t m, int64_t ncols, int s) {
+  RowsPlan p;
+  p.tc = c->prec == ADASAP_PREC_TF32X3 && c->kp > 0 && s == 1;
+  p.nsplit = p.tc ? tc_nsplit(m, ncols) : rows_nsplit(m, ncols, s, c->dp, false);
+  return p;
+}
+
+// y-partials of K(rows, X') W over all n columns of the context
+cudaError_t run_rows_over_x(const adasap_ctx* c, const RowsPlan& p, const float* xr, const float* qr, const int* ridx,
+                            int64_t m, const float* w, int s, float* part, int self_mode, cudaStream_t st) {
+  if (p.tc)
+    return launch_rows_tc(c->kern, c->d, xr, qr, ridx, m, c->dp, c->tc_hi, c->tc_lo, c->n, self_mode, w, s, part,
+                          p.nsplit, c->sigma2, c->err_dev, st);
+  return launch_rows(c->kern, c->dp, rows_over_x(c, xr, qr, ridx, m, w, s, part), s, p.nsplit, false, st);
+}
+
 }  // namespace
+
+extern "C" adasap_status adasap_set_precision(adasap_ctx* c, int prec) {
+  if (!c || (prec != ADASAP_PREC_FP32 && prec != ADASAP_PREC_TF32X3)) return ADASAP_EINVAL;
+  if (prec == ADASAP_PREC_TF32X3 && c->kp == 0) return ADASAP_EINVAL;
+  c->prec = prec;
+  return ADASAP_OK;
+}
 
 extern "C" adasap_status adasap_kernel_rows(adasap_ctx* c, const int64_t* B, int64_t b, const float* W, int s,
                                             float* out, void* stream) {
   if (!c || !B || !W || !out || b < 1 || b >= (1LL << 31) || s < 1 || s > kMaxRhs) return ADASAP_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  const int nsplit = rows_nsplit(b, c->n, s, c->dp, false);
+  const RowsPlan p = plan_rows(c, b, c->n, s);
   const size_t idx_bytes = ((size_t)b * sizeof(int) + 255) & ~(size_t)255;
-  const size_t part_bytes = (size_t)nsplit * b * s * sizeof(float);
+  const size_t part_bytes = (size_t)p.nsplit * b * s * sizeof(float);
   const adasap_status g = grow_ws(c, idx_bytes + part_bytes);
   if (g != ADASAP_OK) return g;
   int* idx = (int*)c->ws;
   float* part = (float*)((char*)c->ws + idx_bytes);
   CT(launch_index32(B, b, c->n, idx, st));
-  CT(launch_rows(c->kern, c->dp, rows_over_x(c, c->Xc, c->qc, idx, b, W, s, part), s, nsplit, false, st));
-  CT(launch_reduce(part, nsplit, b, s, 0, s, out, s, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, nullptr, st));
+  CT(run_rows_over_x(c, p, c->Xc, c->qc, idx, b, W, s, part, 1, st));
+  CT(launch_reduce(part, p.nsplit, b, s, 0, s, out, s, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, nullptr,
+                   st));
   return ADASAP_OK;
 }
 
@@ -277,14 +331,15 @@ extern "C" adasap_status adasap_predict(adasap_ctx* c, const float* Xtest, int64
   if (!c || !Xtest || !W || !out || m < 1 || m >= (1LL << 31) || s < 1 || s > kMaxRhs) return ADASAP_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   Arena ar;
-  const int nsplit = rows_nsplit(m, c->n, s, c->dp, false);
+  const RowsPlan p = plan_rows(c, m, c->n, s);
   float* xt = ar.get<float>((size_t)m * c->dp);
   float* qt = ar.get<float>((size_t)m);
-  float* part = ar.get<float>((size_t)nsplit * m * s);
+  float* part = ar.get<float>((size_t)p.nsplit * m * s);
   if (ar.err != cudaSuccess) return ADASAP_ENOMEM;
   CT(launch_transform(Xtest, m, c->d, c->dp, c->mean_dev, c->kappa / (double)c->ell, xt, qt, st));
-  CT(launch_rows(c->kern, c->dp, rows_over_x(c, xt, qt, nullptr, m, W, s, part), s, nsplit, false, st));
-  CT(launch_reduce(part, nsplit, m, s, 0, s, out, s, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, nullptr, st));
+  CT(run_rows_over_x(c, p, xt, qt, nullptr, m, W, s, part, 0, st));
+  CT(launch_reduce(part, p.nsplit, m, s, 0, s, out, s, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, nullptr,
+                   st));
   CT(cudaStreamSynchronize(st));  // the arena frees its buffers on return
   return ADASAP_OK;
 }
@@ -343,6 +398,9 @@ struct adasap_solver {
   int r = 0;
   int64_t b = 0, mc = 0;
   int ns1 = 1, ns_sk = 1, ns_pw = 1, ns_c = 1;
+  RowsPlan plan1{}, plan_c{};
+  bool tc_pw = false;              // K_BB v products on the tensor cores
+  float *XBhi = nullptr, *XBlo = nullptr;
   double beta = 0, gamma = 0, alpha = 0, eps = 0;
   int literal = 0;
   int64_t iters = 0;
@@ -384,6 +442,10 @@ adasap_status alloc_solver(adasap_solver* S) {
   S->R = ar.get<float>((size_t)b * s);
   S->D = ar.get<float>((size_t)b * s);
   S->part1 = ar.get<float>((size_t)S->ns1 * b * s);
+  if (S->tc_pw) {
+    S->XBhi = ar.get<float>((size_t)tc_npad(b) * c->kp);
+    S->XBlo = ar.get<float>((size_t)tc_npad(b) * c->kp);
+  }
   S->part2 = ar.get<float>(std::max((size_t)S->ns_sk * b * rr, (size_t)S->ns_pw * b));
   S->Ysk = ar.get<float>((size_t)b * rr);
   S->a = ar.get<float>(b);
@@ -465,6 +527,7 @@ cudaError_t capture_iteration(adasap_solver* S, const int64_t* Bs, const float* 
     K(launch_woodbury_factor(cb, lam, c->sc, s1));
   }
   // v0 copy and ||v0||^2 partials
+  if (S->tc_pw) K(launch_build_tc(c->Xc, c->qc, S->B32, b, c->d, c->dp, S->XBhi, S->XBlo, s1));
   K(launch_reduce(S->v0, 1, b, 1, 0, 1, S->vA, 1, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, cb.sq_part, s1));
   float* vcur = S->vA;
   float* vnext = S->vB;
@@ -472,7 +535,11 @@ cudaError_t capture_iteration(adasap_solver* S, const int64_t* Bs, const float* 
     const bool last = i == S->o.power_iters - 1;
     K(launch_woodbury_apply(cb, kInvSqrtNormalised, vcur, 1, S->a, false, false, nullptr, c->sc, s1));
     kb.w = S->a; kb.ldw = 1;
-    K(launch_rows(c->kern, c->dp, kb, 1, S->ns_pw, false, s1));
+    if (S->tc_pw)
+      K(launch_rows_tc(c->kern, c->d, S->XB, S->qB, nullptr, b, c->dp, S->XBhi, S->XBlo, b, 1, S->a, 1, S->part2,
+                       S->ns_pw, c->sigma2, c->err_dev, s1));
+    else
+      K(launch_rows(c->kern, c->dp, kb, 1, S->ns_pw, false, s1));
     K(launch_reduce(S->part2, S->ns_pw, b, 1, 0, 1, S->h, 1, (float)lam, S->a, nullptr, 1, 0.f, nullptr, nullptr, 0,
                     nullptr, s1));
     K(launch_woodbury_apply(cb, kInvSqrt, S->h, 1, vnext, true, last, last ? vcur : nullptr, c->sc, s1));
@@ -482,7 +549,7 @@ cudaError_t capture_iteration(adasap_solver* S, const int64_t* Bs, const float* 
   K(cudaEventRecord(c->ev_join, s1));
   // branch 2: Step I block residual at the reading's point
   float* P = S->literal ? S->W : S->Z;
-  K(launch_rows(c->kern, c->dp, rows_over_x(c, c->Xc, c->qc, S->B32, b, P, s, S->part1), s, S->ns1, false, s0));
+  K(run_rows_over_x(c, S->plan1, c->Xc, c->qc, S->B32, b, P, s, S->part1, 1, s0));
   K(launch_reduce(S->part1, S->ns1, b, s, 0, s, S->R, s, (float)lam, P, S->B32, s, -1.f, S->Y, S->B32, s, nullptr,
                   s0));
   K(cudaStreamWaitEvent(s0, c->ev_join, 0));
@@ -527,10 +594,13 @@ adasap_status solver_begin(adasap_ctx* c, const float* Y, int s, const adasap_op
   S->eps = o->eps > 0 ? o->eps : std::ldexp(1.0, -23);
   S->literal = o->literal ? 1 : 0;
   S->mc = std::min<int64_t>(n, std::max<int64_t>(1, o->check_rows));
-  S->ns1 = rows_nsplit(b, n, s, c->dp, false);
+  S->plan1 = plan_rows(c, b, n, s);
+  S->plan_c = plan_rows(c, S->mc, n, s);
+  S->tc_pw = c->prec == ADASAP_PREC_TF32X3 && c->kp > 0;
+  S->ns1 = S->plan1.nsplit;
   S->ns_sk = identity ? 1 : rows_nsplit(b, b, r, c->dp, false);
-  S->ns_pw = rows_nsplit(b, b, 1, c->dp, false);
-  S->ns_c = rows_nsplit(S->mc, n, s, c->dp, false);
+  S->ns_pw = S->tc_pw ? tc_nsplit(b, b) : rows_nsplit(b, b, 1, c->dp, false);
+  S->ns_c = S->plan_c.nsplit;
   adasap_status st = alloc_solver(S);
   if (st != ADASAP_OK) { delete S; return st; }
   auto fail = [&](cudaError_t e, const char* what) {
@@ -577,8 +647,7 @@ adasap_status solver_residual(adasap_solver* S, double* rel, cudaStream_t us) {
     CT(launch_sample_block(S->o.seed, nullptr, S->iters, c->n, mc, 4, S->Cidx, nullptr, c->s0));
     cidx = S->Cidx;
   }
-  CT(launch_rows(c->kern, c->dp, rows_over_x(c, c->Xc, c->qc, cidx, mc, S->W, s, S->cpart), s, S->ns_c, false,
-                 c->s0));
+  CT(run_rows_over_x(c, S->plan_c, c->Xc, c->qc, cidx, mc, S->W, s, S->cpart, 1, c->s0));
   CT(launch_reduce(S->cpart, S->ns_c, mc, s, 0, s, S->Rc, s, c->lambda, S->W, cidx, s, -1.f, S->Y, cidx, s, S->sqb,
                    c->s0));
   CT(launch_sum_blocks(S->sqb, kReduceBlocks, &c->sc->resid_sq, c->s0));
@@ -737,5 +806,19 @@ extern "C" adasap_status adasap_solver_graph_kernels(adasap_solver* S, int* coun
     k += t == cudaGraphNodeTypeKernel;
   }
   *count = k;
+  return ADASAP_OK;
+}
+
+extern "C" adasap_status adasap_solver_diag(adasap_solver* S, double* out, int count, void* stream) {
+  if (!S || !out || count < 1) return ADASAP_EINVAL;
+  adasap_ctx* c = S->c;
+  CT(cudaEventRecord(c->ev_in, (cudaStream_t)stream));
+  CT(cudaStreamWaitEvent(c->s0, c->ev_in, 0));
+  CT(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->s0));
+  CT(cudaStreamSynchronize(c->s0));
+  const DevScalars& h = *c->sc_host;
+  const double vals[] = {h.delta, h.rho, h.eta, h.lam_hat, (double)h.chol_retries, (double)h.jacobi_sweeps,
+                         (double)h.status, (double)h.detail, (double)h.t};
+  for (int i = 0; i < count && i < (int)(sizeof(vals) / sizeof(vals[0])); ++i) out[i] = vals[i];
   return ADASAP_OK;
 }

@@ -35,37 +35,48 @@ def _check_rows(got, X, rows, W, kern, ell, s2, rtol=RTOL_ROWS):
     assert not bad.any(), "max err/scale %.3e" % (err / np.maximum(scale, 1e-300)).max()
 
 
+def _ctx(lib, X, kern, ell, s2, lam, prec):
+    ctx = lib.Context(X, kern, ell, s2, lam)
+    if prec == lib.PREC_TF32X3 and X.shape[1] + 2 > 32:
+        pytest.skip("tensor-core path needs d <= 30")
+    ctx.set_precision(prec)
+    return ctx
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("kern", [0, 1, 2])
 @pytest.mark.parametrize("d", [1, 8, 11, 20, 40])
 @pytest.mark.parametrize("s", [1, 3, 4, 17, 64])
-def test_kernel_rows_matches_oracle(lib, kern, d, s):
+def test_kernel_rows_matches_oracle(lib, kern, d, s, prec):
     n, b = 3001, 157                      # ragged against every tile size
     X, W = _data(n, d, s, seed=d * 10 + s)
     ell = 0.9 * np.sqrt(d)
-    ctx = lib.Context(X, kern, ell, 1.3, 1e-2)
+    ctx = _ctx(lib, X, kern, ell, 1.3, 1e-2, prec)
     g = np.random.default_rng(kern)
     rows = g.choice(n, size=b, replace=False)
     out = ctx.kernel_rows(torch.from_numpy(rows).cuda(), torch.from_numpy(W).cuda()).cpu().numpy()
     _check_rows(out.astype(np.float64), X, rows, W, kern, ell, 1.3)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("s", [1, 100])
-def test_kernel_rows_edge_sizes(lib, s):
+def test_kernel_rows_edge_sizes(lib, s, prec):
     # n = 1, b = 1; a block of all rows; repeated rows
     X, W = _data(1, 3, s, seed=1)
-    ctx = lib.Context(X, 1, 1.0, 1.0, 1.0)
+    ctx = _ctx(lib, X, 1, 1.0, 1.0, 1.0, prec)
     out = ctx.kernel_rows(torch.zeros(1, dtype=torch.int64, device="cuda"), torch.from_numpy(W).cuda())
     np.testing.assert_allclose(out.cpu().numpy(), W, rtol=1e-6)      # k(x, x) = sigma2 = 1
     X, W = _data(700, 5, s, seed=2)
-    ctx = lib.Context(X, 2, 1.5, 0.7, 1.0)
+    ctx = _ctx(lib, X, 2, 1.5, 0.7, 1.0, prec)
     rows = np.concatenate([np.arange(700), [3, 3, 699]])
     out = ctx.kernel_rows(torch.from_numpy(rows).cuda(), torch.from_numpy(W).cuda()).cpu().numpy()
     _check_rows(out.astype(np.float64), X, rows, W, 2, 1.5, 0.7)
 
 
-def test_kernel_rows_invalid_index_gives_nan_row(lib):
-    X, W = _data(500, 4, 2, seed=3)
-    ctx = lib.Context(X, 0, 1.0, 1.0, 1.0)
+@pytest.mark.parametrize("prec,s", [(0, 2), (1, 1)])
+def test_kernel_rows_invalid_index_gives_nan_row(lib, prec, s):
+    X, W = _data(500, 4, s, seed=3)
+    ctx = _ctx(lib, X, 0, 1.0, 1.0, 1.0, prec)
     rows = torch.tensor([0, -1, 499, 500, 7], device="cuda")
     out = ctx.kernel_rows(rows, torch.from_numpy(W).cuda()).cpu().numpy()
     assert np.isnan(out[1]).all() and np.isnan(out[3]).all()
@@ -73,16 +84,28 @@ def test_kernel_rows_invalid_index_gives_nan_row(lib):
     _check_rows(out[[0, 2, 4]].astype(np.float64), X, np.array([0, 499, 7]), W, 0, 1.0, 1.0)
 
 
-def test_kernel_rows_regress_workload_full_size_sampled(lib):
+@pytest.mark.parametrize("prec", [0, 1])
+def test_kernel_rows_regress_workload_full_size_sampled(lib, prec):
     """n = 2^20, d = 11, Matern-3/2, b = 10^4 (the benchmark's launch); 48 rows checked."""
     P = synth.regress()
-    ctx = lib.Context(P.X, P.kernel, P.ell, P.sigma2, P.lam)
+    ctx = _ctx(lib, P.X, P.kernel, P.ell, P.sigma2, P.lam, prec)
     g = np.random.default_rng(11)
     rows = g.choice(P.X.shape[0], size=P.b, replace=False)
     W = g.standard_normal((P.X.shape[0], 1)).astype(np.float32)
     out = ctx.kernel_rows(torch.from_numpy(rows).cuda(), torch.from_numpy(W).cuda()).cpu().numpy()
     pick = g.choice(P.b, size=48, replace=False)
     _check_rows(out[pick].astype(np.float64), P.X, rows[pick], W, P.kernel, P.ell, P.sigma2)
+
+
+def test_kernel_rows_unaligned_rhs_view(lib):
+    """A contiguous W that starts 4 bytes past an allocation (no 16-byte alignment)."""
+    X, W = _data(900, 6, 1, seed=12)
+    ctx = lib.Context(X, 1, 1.2, 1.0, 1e-2)
+    buf = torch.zeros(901, device="cuda")
+    buf[1:] = torch.from_numpy(W[:, 0]).cuda()
+    rows = np.arange(0, 900, 3)
+    out = ctx.kernel_rows(torch.from_numpy(rows).cuda(), buf[1:]).cpu().numpy()
+    _check_rows(out.astype(np.float64), X, rows, W, 1, 1.2, 1.0)
 
 
 def test_sampler_matches_oracle_generator(lib):
@@ -94,11 +117,12 @@ def test_sampler_matches_oracle_generator(lib):
         np.testing.assert_allclose(v0.cpu().numpy(), OR.sample_v0(b, seed, t), rtol=2e-5, atol=2e-6)
 
 
+@pytest.mark.parametrize("prec,s", [(0, 2), (1, 1)])
 @pytest.mark.parametrize("kern", [0, 1, 2])
-def test_predict_matches_oracle(lib, kern):
-    X, W = _data(2500, 6, 2, seed=5)
+def test_predict_matches_oracle(lib, kern, prec, s):
+    X, W = _data(2500, 6, s, seed=5)
     Xt = np.random.default_rng(6).standard_normal((333, 6)).astype(np.float32)
-    ctx = lib.Context(X, kern, 1.1, 0.8, 1e-2)
+    ctx = _ctx(lib, X, kern, 1.1, 0.8, 1e-2, prec)
     out = ctx.predict(torch.from_numpy(Xt).cuda(), torch.from_numpy(W).cuda()).cpu().numpy()
     ref = gp.posterior_mean(Xt.astype(np.float64), X.astype(np.float64), W.astype(np.float64), kern, 1.1, 0.8)
     scale = gp.posterior_mean(Xt.astype(np.float64), X.astype(np.float64), np.abs(W.astype(np.float64)), kern, 1.1, 0.8)

@@ -50,11 +50,11 @@ def _check_trace(tr, rec, tol, rho=True, tol_eta=None):
         np.testing.assert_allclose(tr[:, 1], [x["rho"] for x in rec], rtol=tol)
 
 
-def _scheduled_case(lib, P, T, b, r, precond="nystrom", literal=False, s=None, seed=21):
+def _scheduled_case(lib, P, T, b, r, precond="nystrom", literal=False, s=None, seed=21, prec=None):
     n = P.X.shape[0]
     Y = P.Y if s is None else P.Y[:, :s]
     B, Om, v0 = synth.injected_schedule(n, b, r, T, seed=seed)
-    ctx = lib.Context(P.X, P.kernel, P.ell, P.sigma2, P.lam)
+    ctx = lib.Context(P.X, P.kernel, P.ell, P.sigma2, P.lam, precision=prec)
     opts = lib.default_opts(n, b=b, r=r, precond=1 if precond == "identity" else 0, literal=int(literal))
     W, tr, st = ctx.solve_scheduled(torch.from_numpy(np.ascontiguousarray(Y)).cuda(), torch.from_numpy(B).cuda(),
                                     torch.from_numpy(Om).cuda(), torch.from_numpy(v0).cuda(), opts=opts)
@@ -65,19 +65,21 @@ def _scheduled_case(lib, P, T, b, r, precond="nystrom", literal=False, s=None, s
     return W.cpu().numpy(), tr.cpu().numpy(), Wref, rec
 
 
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("T", [1, 2, 6])
-def test_scheduled_iterations_match_oracle_small(lib, T):
+def test_scheduled_iterations_match_oracle_small(lib, T, prec):
     P = synth.small()
-    W, tr, Wref, rec = _scheduled_case(lib, P, T, b=200, r=32)
+    W, tr, Wref, rec = _scheduled_case(lib, P, T, b=200, r=32, prec=prec)
     _check_trace(tr, rec, 1e-4)
     assert _rel(W, Wref) < 1e-4
 
 
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("kern", [1, 2])
-def test_scheduled_matern_regress_shape(lib, kern):
+def test_scheduled_matern_regress_shape(lib, kern, prec):
     P = synth.regress(n=6000, b=600)
     P["kernel"] = kern
-    W, tr, Wref, rec = _scheduled_case(lib, P, 4, b=600, r=64)
+    W, tr, Wref, rec = _scheduled_case(lib, P, 4, b=600, r=64, prec=prec)
     tol, tol_eta = _tol(rec, 600, P.sigma2), _tol_eta(rec, 600, P.sigma2)
     _check_trace(tr, rec, tol, tol_eta=tol_eta)
     assert _rel(W, Wref) < tol_eta
@@ -108,12 +110,13 @@ def test_scheduled_edge_shapes(lib, n, b, r, d):
     assert _rel(W, Wref) < tol_eta
 
 
-def test_small_workload_300_iterations_posterior_mean(lib):
+@pytest.mark.parametrize("prec", [0, 1])
+def test_small_workload_300_iterations_posterior_mean(lib, prec):
     """n=2000, d=8, RBF, b=200, r=32, 300 iterations, device-drawn randomness: the GPU
     trajectory against the oracle driven by the same counter-based generator."""
     P = synth.small()
     n = P.X.shape[0]
-    ctx = lib.Context(P.X, P.kernel, P.ell, P.sigma2, P.lam)
+    ctx = lib.Context(P.X, P.kernel, P.ell, P.sigma2, P.lam, precision=prec)
     opts = lib.default_opts(n, b=P.b, r=P.r, max_iters=P.iters, seed=0, check_every=0)
     W, st, status = ctx.solve(torch.from_numpy(P.Y).cuda(), opts=opts)
     W = W.cpu().numpy()
