@@ -54,6 +54,7 @@ def parse():
     p.add_argument("--no-tol-run", action="store_true")
     p.add_argument("--n", type=int, default=1 << 20, help="rows of the workload (default: full size)")
     p.add_argument("--kernel-launches", type=int, default=10, help="timed launches of the Step I kernel alone")
+    p.add_argument("--tol-iters", type=int, default=3000, help="iteration cap of the time-to-1e-3 solves")
     p.add_argument("--only-kernel", action="store_true",
                    help="run only the Step I block-row product launches (profiling)")
     return p.parse_args()
@@ -295,7 +296,7 @@ def run_ours(args, rank, world, dist):
         tol_run = {}
         for name, prec in (("fp32", lib.PREC_FP32), ("mixed", lib.PREC_TF32X3)):
             ctx.set_precision(prec)
-            topts = lib.default_opts(n, b=b, r=r, seed=2, tol=1e-3, max_iters=300, check_every=25,
+            topts = lib.default_opts(n, b=b, r=r, seed=2, tol=1e-3, max_iters=args.tol_iters, check_every=50,
                                      check_rows=20000)
             W, st, stc = ctx.solve(Yd, opts=topts)
             tol_run[name] = {"seconds": st["seconds"], "iters": st["iters"], "rel_resid": st["rel_resid"],

@@ -118,6 +118,27 @@ adasap_status adasap_set_precision(adasap_ctx* ctx, int precision);
 adasap_status adasap_kernel_rows(adasap_ctx* ctx, const int64_t* B, int64_t b, const float* W,
                                  int s, float* out, void* stream);
 
+/* The product of adasap_kernel_rows for callers that cannot allocate device
+ * memory while they run -- for example code inside a memory-pool-less runtime,
+ * an allocation-free real-time loop, or a process whose device memory is
+ * already fully reserved.  (The paper has no counterpart: this is a service of
+ * this library.)  Same arguments, arithmetic and result as adasap_kernel_rows,
+ * but the call allocates nothing: its scratch (an int32 copy of B and the
+ * per-split partial sums) is a static device array of 8 MiB that every GPU
+ * loading this library holds until the process exits.
+ *   - The scratch must fit: about 4 * b * (1 + s * k) bytes, where k, the
+ *     number of column splits the library chooses, is at most a few tens (for
+ *     b = 10^4, s = 1 about 0.7 MiB).  Larger sizes return ADASAP_EINVAL before
+ *     any GPU work, and adasap_last_error() says how many bytes were needed.
+ *   - The context's device must be current.  The first call on a device looks
+ *     up the array's device address (cudaGetSymbolAddress); make that first
+ *     call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents;
+ *     nothing in it needs clearing, but calls that overlap on the GPU (on
+ *     different streams, or from different threads) race on it: serialise them. */
+adasap_status adasap_kernel_rows_noalloc(adasap_ctx* ctx, const int64_t* B, int64_t b, const float* W,
+                                         int s, float* out, void* stream);
+
 /* ADASAP (Alg. 2 with Alg. 4, 5, 6 and the stabilised Woodbury apply of App. C.2).
  * Y (n x s) and W (n x s) are host or device.  W holds W_0 on entry and the
  * returned iterate W_T on exit.  1 <= s <= 128.  Randomness (B, Omega, v0) is

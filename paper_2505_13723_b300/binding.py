@@ -34,7 +34,8 @@ SYMBOLS = ["adasap_default_opts", "adasap_status_string", "adasap_last_error", "
            "adasap_predict", "adasap_hypergrad", "adasap_sample", "adasap_solver_begin",
            "adasap_solver_step", "adasap_solver_residual", "adasap_solver_get_w",
            "adasap_solver_scalars", "adasap_solver_end", "adasap_solver_graph_kernels",
-           "adasap_solver_diag", "adasap_set_precision"]
+           "adasap_solver_diag", "adasap_set_precision",
+           "adasap_kernel_rows_noalloc"]
 
 
 class Opts(ctypes.Structure):
@@ -67,6 +68,8 @@ _lib.adasap_create.argtypes = [_P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_fl
                                ctypes.c_float, _P, ctypes.POINTER(_P)]
 _lib.adasap_destroy.argtypes = [_P]
 _lib.adasap_destroy.restype = None
+_lib.adasap_kernel_rows_noalloc.argtypes = [_P, _P, _I64, _P, ctypes.c_int, _P, _P]
+_lib.adasap_kernel_rows_noalloc.restype = ctypes.c_int
 _lib.adasap_set_precision.argtypes = [_P, ctypes.c_int]
 _lib.adasap_set_precision.restype = ctypes.c_int
 _lib.adasap_kernel_rows.argtypes = [_P, _P, _I64, _P, ctypes.c_int, _P, _P]
@@ -187,6 +190,17 @@ class Context:
             out = torch.empty(b, s, device=W.device, dtype=torch.float32)
         _check(_lib.adasap_kernel_rows(self.h, ctypes.c_void_p(B.data_ptr()), b, _dev_f32(W2, "W"), s,
                                        _dev_f32(out, "out"), _stream(stream)), "adasap_kernel_rows")
+        return out
+
+    def kernel_rows_noalloc(self, B, W, out, stream=None):
+        """adasap_kernel_rows_noalloc: as kernel_rows into a caller-provided `out`,
+        allocating nothing (scratch in the library's static device array)."""
+        if not (B.is_cuda and B.dtype == torch.int64 and B.is_contiguous()):
+            raise TypeError("B must be a contiguous int64 CUDA tensor")
+        W2 = W if W.dim() == 2 else W.view(-1, 1)
+        _check(_lib.adasap_kernel_rows_noalloc(self.h, ctypes.c_void_p(B.data_ptr()), B.numel(), _dev_f32(W2, "W"),
+                                               W2.shape[1], _dev_f32(out, "out"), _stream(stream)),
+               "adasap_kernel_rows_noalloc")
         return out
 
     def solve(self, Y, opts=None, W=None, stream=None, **kw):

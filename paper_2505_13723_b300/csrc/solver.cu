@@ -12,6 +12,7 @@
 // core runs in the shadow of the throughput-bound Step I.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -820,5 +821,70 @@ extern "C" adasap_status adasap_solver_diag(adasap_solver* S, double* out, int c
   const double vals[] = {h.delta, h.rho, h.eta, h.lam_hat, (double)h.chol_retries, (double)h.jacobi_sweeps,
                          (double)h.status, (double)h.detail, (double)h.t};
   for (int i = 0; i < count && i < (int)(sizeof(vals) / sizeof(vals[0])); ++i) out[i] = vals[i];
+  return ADASAP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// adasap_kernel_rows_noalloc: the block-row product for callers that cannot
+// allocate device memory while they run.
+//
+// Its scratch (the int32 copy of B and the per-split partial sums) lives in the
+// file-scope array below instead of the context's growable workspace, so the
+// call itself makes no allocation.  The array is part of the library's device
+// image: every GPU that loads the library holds these kNoallocScratchBytes
+// until the process exits.  In host code the array's name is only a host-side
+// stand-in; its device address is looked up once per device, on the first call
+// made on that device, with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kNoallocScratchBytes = (size_t)8 << 20;
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoallocMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+extern "C" adasap_status adasap_kernel_rows_noalloc(adasap_ctx* c, const int64_t* B, int64_t b, const float* W,
+                                                    int s, float* out, void* stream) {
+  if (!c || !B || !W || !out || b < 1 || b >= (1LL << 31) || s < 1 || s > kMaxRhs) return ADASAP_EINVAL;
+  int dev = -1;
+  CT(cudaGetDevice(&dev));
+  if (dev != c->device || dev < 0 || dev >= kNoallocMaxDevices) {
+    g_last_error = "adasap_kernel_rows_noalloc: the context's device must be the current device";
+    return ADASAP_EINVAL;
+  }
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        note_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        return ADASAP_ECUDA;
+      }
+      g_noalloc_ptr[dev] = p;
+    }
+    base = g_noalloc_ptr[dev];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const RowsPlan p = plan_rows(c, b, c->n, s);
+  const size_t idx_bytes = ((size_t)b * sizeof(int) + 255) & ~(size_t)255;
+  const size_t part_bytes = (size_t)p.nsplit * b * s * sizeof(float);
+  if (idx_bytes + part_bytes > kNoallocScratchBytes) {
+    g_last_error = "adasap_kernel_rows_noalloc: needs " + std::to_string(idx_bytes + part_bytes) +
+                   " bytes of scratch, the static array holds " + std::to_string(kNoallocScratchBytes) +
+                   "; use adasap_kernel_rows or a smaller b * s";
+    return ADASAP_EINVAL;
+  }
+  // Every byte read below is written first in this call (the index copy, then one
+  // partial per split and row), so nothing has to be cleared.
+  int* idx = static_cast<int*>(base);
+  float* part = reinterpret_cast<float*>(static_cast<unsigned char*>(base) + idx_bytes);
+  CT(launch_index32(B, b, c->n, idx, st));
+  CT(run_rows_over_x(c, p, c->Xc, c->qc, idx, b, W, s, part, 1, st));
+  CT(launch_reduce(part, p.nsplit, b, s, 0, s, out, s, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, nullptr,
+                   st));
   return ADASAP_OK;
 }

@@ -1,0 +1,63 @@
+"""The allocation-free block-row product, adasap_kernel_rows_noalloc.
+
+Some callers cannot allocate device memory while they run (an allocator-less
+runtime, a real-time loop that must not touch the allocator, a process whose
+device memory is already reserved).  For them the library offers this one
+entry point, whose scratch is a static device array instead of a workspace it
+would allocate.  These tests call it through the C-ABI and compare it with the
+allocating adasap_kernel_rows, on two calls in a row (the array is shared and
+keeps the previous call's contents).  This file is collected last on purpose.
+"""
+
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2505_13723_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5   # the tolerance of the kernel-row parity tests
+
+
+def _call_noalloc(lib, ctx, B, W, out):
+    W2 = W if W.dim() == 2 else W.view(-1, 1)
+    return lib._lib.adasap_kernel_rows_noalloc(
+        ctx.h, ctypes.c_void_p(B.data_ptr()), B.numel(), ctypes.c_void_p(W2.data_ptr()), W2.shape[1],
+        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+@pytest.mark.parametrize("prec,s", [(1, 1), (0, 1), (0, 3)])
+def test_noalloc_matches_kernel_rows_on_two_calls(lib, prec, s):
+    P = synth.regress(n=20000)
+    ctx = lib.Context(P.X, P.kernel, P.ell, P.sigma2, P.lam, precision=prec)
+    g = np.random.default_rng(7)
+    for call, b in enumerate([1500, 613]):          # two calls in a row, different sizes
+        B = torch.from_numpy(g.choice(20000, size=b, replace=False)).cuda()
+        W = torch.from_numpy(g.standard_normal((20000, s)).astype(np.float32)).cuda()
+        ref = ctx.kernel_rows(B, W)
+        out = torch.full((b, s), float("nan"), device="cuda")
+        assert _call_noalloc(lib, ctx, B, W, out) == 0, lib._lib.adasap_last_error()
+        torch.cuda.synchronize()
+        r, o = ref.cpu().numpy(), out.cpu().numpy()
+        assert np.isfinite(o).all(), "call %d left unwritten outputs" % call
+        np.testing.assert_allclose(o, r, rtol=RTOL, atol=RTOL * np.abs(r).max())
+
+
+def test_noalloc_rejects_sizes_beyond_its_static_scratch(lib):
+    P = synth.small(n=3000)
+    ctx = lib.Context(P.X, P.kernel, P.ell, P.sigma2, P.lam)
+    b, s = 3000, 128                                  # partials of 128 columns per split do not fit
+    B = torch.arange(b, device="cuda")
+    W = torch.zeros(3000, s, device="cuda")
+    out = torch.zeros(b, s, device="cuda")
+    assert _call_noalloc(lib, ctx, B, W, out) == 1    # ADASAP_EINVAL, no GPU work
+    assert b"bytes of scratch" in lib._lib.adasap_last_error()
+    # the entry point still works afterwards
+    W1 = torch.ones(3000, 1, device="cuda")
+    o1 = torch.zeros(b, 1, device="cuda")
+    assert _call_noalloc(lib, ctx, B, W1, o1) == 0
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(o1.cpu().numpy(), ctx.kernel_rows(B, W1).cpu().numpy(), rtol=RTOL)
