@@ -12,10 +12,14 @@
 // matrix B^T B = C^{-T} (Y_nu^T Y_nu) C^{-1}: its eigenvectors are B's right
 // singular vectors V and its eigenvalues Sigma^2, and U = Y_nu (C^{-1} V Sigma^{-1}).
 // Y_nu^T Y_nu comes from the Gram of [Omega | M Omega] without forming Y_nu.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <type_traits>
 
 #include "internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace adasap {
 
@@ -28,7 +32,8 @@ namespace adasap {
 // an FP32 product error of eps * |a| |b| is below the data's own rounding.
 // Only upper 64 x 64 tiles are computed; the reduce mirrors them.
 // ---------------------------------------------------------------------------
-int gram_chunks_for(int64_t b) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, (b + 255) / 256)); }
+// chunks of at least 32 rows, enough CTAs (chunks x upper tiles) for ~4 per SM at c = 2r <= 256
+int gram_chunks_for(int64_t b) { return (int)std::max<int64_t>(1, std::min<int64_t>(240, (b + 31) / 32)); }
 
 __device__ __forceinline__ float cat_get(const float* A1, int64_t ld1, int c1, const float* A2, int64_t ld2,
                                          int c2, int64_t row, int col) {
@@ -129,21 +134,27 @@ cudaError_t launch_gram(const float* A1, int64_t ld1, int c1, const float* A2, i
 // with leading dimension ld (r + 1 keeps column reads conflict free).
 // Returns false, uniformly over the block, if a pivot is not positive.
 // ---------------------------------------------------------------------------
-__device__ bool chol_lower_smem(double* A, int r, int ld, int* flag) {
+template <typename T>
+__device__ bool chol_lower_smem(T* A, int r, int ld, int* flag) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ T s_rdk;
   for (int k = 0; k < r; ++k) {
     if (threadIdx.x == 0) {
-      const double d = A[k * ld + k];
-      *flag = (d > 0.0 && isfinite(d)) ? 0 : 1;
-      if (!*flag) A[k * ld + k] = sqrt(d);
+      const T d = A[k * ld + k];
+      *flag = (d > T(0) && isfinite(d)) ? 0 : 1;
+      if (!*flag) {
+        const T sd = sqrt(d);
+        A[k * ld + k] = sd;
+        s_rdk = T(1) / sd;
+      }
     }
     __syncthreads();
     if (*flag) return false;
-    const double dk = A[k * ld + k];
-    for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) A[i * ld + k] /= dk;
+    const T rdk = s_rdk;
+    for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) A[i * ld + k] *= rdk;
     __syncthreads();
     for (int i = k + 1 + warp; i < r; i += nw) {
-      const double lik = A[i * ld + k];
+      const T lik = A[i * ld + k];
       for (int j = k + 1 + lane; j <= i; j += 32) A[i * ld + j] -= lik * A[j * ld + k];
     }
     __syncthreads();
@@ -202,25 +213,26 @@ __global__ void __launch_bounds__(512) k_nys_chol(const double* __restrict__ G, 
 // where R' = trans ? R^T : R.  L and the reciprocals of its diagonal are
 // staged in shared memory; one warp per right-hand side column.
 constexpr int kTrsmWarps = 4;
+template <typename T>
 __global__ void __launch_bounds__(32 * kTrsmWarps) k_trsm(const double* __restrict__ L, int r,
                                                           const double* __restrict__ R, int trans, int upper,
                                                           double* __restrict__ X) {
-  extern __shared__ double shd[];
+  extern __shared__ double shd_trsm[];
   const int ld = r + 1;
-  double* sL = shd;                       // r x (r + 1)
-  double* rinv = shd + r * ld;            // r
-  double* xs = rinv + r;                  // kTrsmWarps x r
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) sL[(e / r) * ld + e % r] = L[e];
+  T* sL = reinterpret_cast<T*>(shd_trsm);  // r x (r + 1)
+  T* rinv = sL + r * ld;                  // r
+  T* xs = rinv + r;                       // kTrsmWarps x r
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) sL[(e / r) * ld + e % r] = (T)L[e];
   __syncthreads();
-  for (int i = threadIdx.x; i < r; i += blockDim.x) rinv[i] = 1.0 / sL[i * ld + i];
+  for (int i = threadIdx.x; i < r; i += blockDim.x) rinv[i] = T(1) / sL[i * ld + i];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = blockIdx.x * kTrsmWarps + warp;
   if (col >= r) return;
-  double* x = xs + warp * r;
+  T* x = xs + warp * r;
   for (int step = 0; step < r; ++step) {
     const int i = upper ? r - 1 - step : step;
-    double part = 0.0;
+    T part = T(0);
     if (!upper) {
       for (int k = lane; k < i; k += 32) part += sL[i * ld + k] * x[k];
     } else {
@@ -228,17 +240,18 @@ __global__ void __launch_bounds__(32 * kTrsmWarps) k_trsm(const double* __restri
     }
     part = warp_sum(part);
     if (lane == 0) {
-      const double rhs = trans ? R[(int64_t)col * r + i] : R[(int64_t)i * r + col];
+      const T rhs = (T)(trans ? R[(int64_t)col * r + i] : R[(int64_t)i * r + col]);
       x[i] = (rhs - part) * rinv[i];
     }
     __syncwarp();
   }
-  for (int i = lane; i < r; i += 32) X[(int64_t)i * r + col] = x[i];
+  for (int i = lane; i < r; i += 32) X[(int64_t)i * r + col] = (double)x[i];
 }
 
+template <typename T = double>
 static cudaError_t trsm(const double* L, int r, const double* R, int trans, int upper, double* X, cudaStream_t st) {
-  const size_t smem = ((size_t)r * (r + 1) + r + (size_t)kTrsmWarps * r) * sizeof(double);
-  k_trsm<<<(r + kTrsmWarps - 1) / kTrsmWarps, 32 * kTrsmWarps, smem, st>>>(L, r, R, trans, upper, X);
+  const size_t smem = ((size_t)r * (r + 1) + r + (size_t)kTrsmWarps * r) * sizeof(T);
+  k_trsm<T><<<(r + kTrsmWarps - 1) / kTrsmWarps, 32 * kTrsmWarps, smem, st>>>(L, r, R, trans, upper, X);
   return cudaGetLastError();
 }
 
@@ -248,10 +261,12 @@ static cudaError_t trsm(const double* L, int r, const double* R, int trans, int 
 // eigenvectors (the eigenvalues are refined in FP64 by k_rayleigh).
 // Parallel round-robin ordering: in each of the r2 - 1 rounds of a sweep the
 // r2/2 disjoint pairs are rotated concurrently, one warp per pair, so a round
-// needs one barrier.  W and V are stored column-major in shared memory.  A
-// pair is skipped when |w_p . w_q| <= 1e-6 |w_p| |w_q| or when it is below what
-// the columns' absolute FP32 noise can produce; sweeps stop when one rotates
-// nothing (at most kJacobiSweeps; Jacobi converges quadratically).
+// needs one barrier.  W and V are column-major in shared memory; the squared
+// column norms are carried along (updated exactly for each rotation and
+// recomputed every sweep), so a pair needs one dot product.  A pair is skipped
+// when |w_p . w_q| <= 1e-6 |w_p| |w_q| or when it is below what the columns'
+// absolute FP32 noise can produce; sweeps stop when one rotates nothing (at
+// most kJacobiSweeps; Jacobi converges quadratically).
 constexpr int kJacobiSweeps = 12;
 __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ A, int r, float* __restrict__ Vout,
                                                  DevScalars* sc) {
@@ -259,8 +274,8 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ A, i
   const int r2 = r + (r & 1);
   float* w = shf;               // r2 columns x r2 rows (column-major)
   float* v = shf + r2 * r2;
+  __shared__ float nrm[kMaxRank];
   __shared__ float mxs[32];
-  __shared__ int nrot;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double mx = 0.0;
   for (int i = threadIdx.x; i < r; i += blockDim.x) mx = fmax(mx, fabs(A[(int64_t)i * r + i]));
@@ -276,65 +291,96 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ A, i
     v[e] = (row == col) ? 1.0f : 0.0f;
   }
   __syncthreads();
-  // largest column norm^2 (scaled) for the absolute floor
-  float cmax = 0.f;
-  for (int col = warp; col < r; col += nw) {
-    float t = 0.f;
-    for (int k = lane; k < r2; k += 32) t = fmaf(w[col * r2 + k], w[col * r2 + k], t);
-    t = warp_sum(t);
-    cmax = fmaxf(cmax, t);
-  }
-  if (lane == 0) mxs[warp] = cmax;
-  __syncthreads();
-  float nmax = 0.f;
-  for (int k = 0; k < nw; ++k) nmax = fmaxf(nmax, mxs[k]);
-  // absolute FP32 noise carried by every column after rotations against the
-  // largest one: a dot product below noise * (|w_p| + |w_q|) cannot be reduced
-  const float noise = 4.0f * 1.1920929e-7f * sqrtf(nmax);
   const int half = r2 / 2;
+  float noise = 0.f;
   int sweep = 0;
   for (; sweep < kJacobiSweeps; ++sweep) {
-    if (threadIdx.x == 0) nrot = 0;
+    // exact squared column norms at the start of every sweep
+    for (int col = warp; col < r2; col += nw) {
+      float t = 0.f;
+      for (int k = lane; k < r2; k += 32) t = fmaf(w[col * r2 + k], w[col * r2 + k], t);
+      t = warp_sum(t);
+      if (lane == 0) nrm[col] = t;
+    }
     __syncthreads();
+    if (sweep == 0) {
+      float nmax = 0.f;
+      for (int k = 0; k < r2; ++k) nmax = fmaxf(nmax, nrm[k]);
+      // absolute FP32 noise carried by every column after rotations against the largest
+      noise = 4.0f * 1.1920929e-7f * sqrtf(nmax);
+    }
+    int rotated = 0;
     for (int round = 0; round < r2 - 1; ++round) {
-      for (int m = warp; m < half; m += nw) {
-        int p, q;
+      // a warp owns pairs m = warp and m = warp + nw (r2 <= 128, nw = 32): both are
+      // processed together so their latency chains overlap
+      int pp[2], qq[2];
+      bool act[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int m = warp + h * nw;
+        act[h] = m < half;
+        int p = 0, q = 0;
         if (m == 0) { p = round; q = r2 - 1; }
-        else { p = (round + m) % (r2 - 1); q = (round - m + r2 - 1) % (r2 - 1); }
-        float* wp = w + p * r2;
-        float* wq = w + q * r2;
-        float al = 0.f, be = 0.f, ga = 0.f;
-        for (int k = lane; k < r2; k += 32) {
-          const float a = wp[k], b = wq[k];
-          al = fmaf(a, a, al);
-          be = fmaf(b, b, be);
-          ga = fmaf(a, b, ga);
+        else {
+          p = round + m;
+          if (p >= r2 - 1) p -= r2 - 1;
+          q = round - m;
+          if (q < 0) q += r2 - 1;
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (fabsf(ga) > 1e-6f * sqrtf(al * be) && fabsf(ga) > noise * (sqrtf(al) + sqrtf(be))) {
-          const float zeta = (be - al) / (2.0f * ga);
-          const float t = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
-          const float c = rsqrtf(1.0f + t * t);
-          const float s = c * t;
+        pp[h] = p < q ? p : q;
+        qq[h] = p < q ? q : p;
+      }
+      float ga[2] = {0.f, 0.f};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!act[h]) continue;
+        const float* wp = w + pp[h] * r2;
+        const float* wq = w + qq[h] * r2;
+        for (int k = lane; k < r2; k += 32) ga[h] = fmaf(wp[k], wq[k], ga[h]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ga[0] += __shfl_xor_sync(0xffffffffu, ga[0], o);
+        ga[1] += __shfl_xor_sync(0xffffffffu, ga[1], o);
+      }
+      int mine = 0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!act[h]) continue;
+        const int p = pp[h], q = qq[h];
+        const float al = nrm[p], be = nrm[q], g = ga[h];
+        const float ab = al * be;
+        const float sab = ab * rsqrtf(fmaxf(ab, 1e-37f));
+        const float sa = al * rsqrtf(fmaxf(al, 1e-37f)), sb = be * rsqrtf(fmaxf(be, 1e-37f));
+        if (fabsf(g) > 1e-6f * sab && fabsf(g) > noise * (sa + sb)) {
+          const float zeta = __fdividef(be - al, 2.0f * g);
+          const float z2 = fmaf(zeta, zeta, 1.0f);
+          const float t = copysignf(1.0f, zeta) * __fdividef(1.0f, fabsf(zeta) + z2 * rsqrtf(z2));
+          const float c = rsqrtf(fmaf(t, t, 1.0f));
+          const float sn = c * t;
+          float* wp = w + p * r2;
+          float* wq = w + q * r2;
           float* vp = v + p * r2;
           float* vq = v + q * r2;
           for (int k = lane; k < r2; k += 32) {
-            const float a = wp[k], b = wq[k];
-            wp[k] = c * a - s * b;
-            wq[k] = s * a + c * b;
+            const float a = wp[k], bq = wq[k];
+            wp[k] = c * a - sn * bq;
+            wq[k] = sn * a + c * bq;
             const float x = vp[k], y = vq[k];
-            vp[k] = c * x - s * y;
-            vq[k] = s * x + c * y;
+            vp[k] = c * x - sn * y;
+            vq[k] = sn * x + c * y;
           }
-          if (lane == 0) atomicAdd(&nrot, 1);
+          if (lane == 0) {
+            // norms after a rotation that zeroes the pair's inner product
+            nrm[p] = c * c * al - 2.0f * c * sn * g + sn * sn * be;
+            nrm[q] = sn * sn * al + 2.0f * c * sn * g + c * c * be;
+          }
+          mine = 1;
         }
       }
-      __syncthreads();
+      rotated |= __syncthreads_or(mine);
     }
-    if (nrot == 0) break;
-    __syncthreads();
+    if (!rotated) break;
   }
   if (threadIdx.x == 0) sc->jacobi_sweeps = sweep;
   // Vout row-major: Vout[k * r + i] = component k of eigenvector i
@@ -467,19 +513,21 @@ static cudaError_t make_u(const float* A1, const float* A2, int64_t b, int r, co
 
 // FP64 Cholesky of an r x r SPD matrix into a lower factor (identity and a
 // status on failure), one CTA.
+template <typename T>
 __global__ void __launch_bounds__(512) k_chol_plain(const double* __restrict__ G, int r, double* __restrict__ L,
                                                     DevScalars* sc, int detail) {
-  extern __shared__ double sh[];
+  extern __shared__ double shd_chol[];
+  T* sh = reinterpret_cast<T*>(shd_chol);
   __shared__ int flag;
   const int ld = r + 1;
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) sh[(e / r) * ld + e % r] = G[e];
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) sh[(e / r) * ld + e % r] = (T)G[e];
   __syncthreads();
-  const bool ok = chol_lower_smem(sh, r, ld, &flag);
+  const bool ok = chol_lower_smem<T>(sh, r, ld, &flag);
   __syncthreads();
   if (!ok && threadIdx.x == 0) set_status(sc, ADASAP_ENUMERIC, detail);
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
-    L[e] = ok ? ((j <= i) ? sh[i * ld + j] : 0.0) : (i == j ? 1.0 : 0.0);
+    L[e] = ok ? ((j <= i) ? (double)sh[i * ld + j] : 0.0) : (i == j ? 1.0 : 0.0);
   }
 }
 
@@ -491,11 +539,21 @@ cudaError_t launch_orthonormalize(CoreBufs& cb, float* Om, float* tmp, DevScalar
   for (int pass = 0; pass < 2; ++pass) {
     const float* src = pass == 0 ? Om : tmp;
     float* dst = pass == 0 ? tmp : Om;
-    // pass 1 exact (a near-square Omega has cond^2 beyond FP32); pass 2 sees cond ~ 1
-    if ((e = launch_gram(src, r, r, nullptr, 0, 0, cb.b, cb.gram_part, cb.gram_chunks, cb.X1, pass == 0, st)))
-      return e;
-    k_chol_plain<<<1, 512, (size_t)r * (r + 1) * sizeof(double), st>>>(cb.X1, r, cb.Lc, sc, 6);
-    if ((e = trsm(cb.Lc, r, cb.Ident, 0, 0, cb.A, st))) return e;      // A = L^{-1}
+    // pass 1 exact when Omega is near square (cond(Omega)^2 can exceed FP32's reach);
+    // for b >= 4r a Gaussian Omega has cond ~ (1 + sqrt(r/b)) / (1 - sqrt(r/b)) <= 3.
+    // Pass 2 sees cond ~ 1.
+    // For b >= 4r the factorisations need only FP32 arithmetic (the target is FP32
+    // orthogonality and cond(Omega) <= 3), which avoids B300's slow FP64 latency chains.
+    const bool exact = pass == 0 && cb.b < 4 * (int64_t)r;
+    const bool wide64 = cb.b < 4 * (int64_t)r;
+    if ((e = launch_gram(src, r, r, nullptr, 0, 0, cb.b, cb.gram_part, cb.gram_chunks, cb.X1, exact, st))) return e;
+    if (wide64) {
+      k_chol_plain<double><<<1, 512, (size_t)r * (r + 1) * sizeof(double), st>>>(cb.X1, r, cb.Lc, sc, 6);
+      if ((e = trsm<double>(cb.Lc, r, cb.Ident, 0, 0, cb.A, st))) return e;      // A = L^{-1}
+    } else {
+      k_chol_plain<float><<<1, 512, (size_t)r * (r + 1) * sizeof(double), st>>>(cb.X1, r, cb.Lc, sc, 6);
+      if ((e = trsm<float>(cb.Lc, r, cb.Ident, 0, 0, cb.A, st))) return e;
+    }
     if ((e = make_u(src, nullptr, cb.b, r, cb.A, 1, sc, dst, st))) return e;
   }
   return cudaGetLastError();
@@ -546,12 +604,21 @@ __global__ void __launch_bounds__(512) k_wchol(const double* __restrict__ UtU, i
   }
 }
 
+// Per-iteration constants of the inverse square root (eq. inv_sqrt_nys_woodbury):
+// cis_k = (S_k + rho)^{-1/2} - rho^{-1/2}.
+__global__ void k_invsqrt_coef(const double* __restrict__ S, int r, const DevScalars* sc, double* __restrict__ cis) {
+  const double rho = sc->rho;
+  const double irs = 1.0 / sqrt(rho);
+  for (int k = threadIdx.x; k < r; k += blockDim.x) cis[k] = 1.0 / sqrt(S[k] + rho) - irs;
+}
+
 cudaError_t launch_woodbury_factor(CoreBufs& cb, double lam, DevScalars* sc, cudaStream_t st) {
   (void)lam;
   const int r = cb.r;
   cudaError_t e;
   if ((e = launch_gram(cb.U, r, r, nullptr, 0, 0, cb.b, cb.gram_part, cb.gram_chunks, cb.X1, false, st))) return e;
   k_wchol<<<1, 512, (size_t)r * (r + 1) * sizeof(double), st>>>(cb.X1, r, cb.S, cb.keep, sc, cb.Lw);
+  k_invsqrt_coef<<<1, 128, 0, st>>>(cb.S, r, sc, cb.cis);
   return cudaGetLastError();
 }
 
@@ -765,10 +832,11 @@ cudaError_t launch_woodbury_apply(CoreBufs& cb, int mode, const float* v, int s,
 
 // eta = 1 / lambda_hat, lambda_hat = (1/||v_{N-1}||) * sum(w_N . v_{N-1}) (Alg. 5,
 // Rayleigh-quotient reading).  A failed factorisation (status != 0) gives eta = 0.
-__global__ void k_set_eta(const double* __restrict__ dot_part, const double* __restrict__ alpha, DevScalars* sc) {
+__global__ void k_set_eta(const double* __restrict__ dot_part, int nparts, const double* __restrict__ alpha,
+                          DevScalars* sc) {
   __shared__ double red[33];
   double t = 0.0;
-  for (int i = threadIdx.x; i < kReduceBlocks; i += blockDim.x) t += dot_part[i];
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) t += dot_part[i];
   t = block_sum(t, red);
   if (threadIdx.x == 0) {
     const double lam_hat = alpha[1] * t;
@@ -781,8 +849,8 @@ __global__ void k_set_eta(const double* __restrict__ dot_part, const double* __r
 }
 
 cudaError_t launch_set_eta(CoreBufs& cb, DevScalars* sc, int identity, cudaStream_t st) {
-  (void)identity;
-  k_set_eta<<<1, 256, 0, st>>>(cb.dot_part, cb.alpha, sc);
+  // the identity path leaves per-block partials; the cluster apply leaves one sum
+  k_set_eta<<<1, 256, 0, st>>>(cb.dot_part, identity ? kReduceBlocks : 1, cb.alpha, sc);
   return cudaGetLastError();
 }
 
@@ -868,14 +936,180 @@ cudaError_t launch_tick(DevScalars* sc, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// One single-RHS Woodbury apply (App. C.2) in one launch of an 8-CTA cluster:
+//   mode kInvSqrtNormalised:  out = (P + rho I)^{-1/2} (v / ||v||)
+//   mode kInvSqrt:            out = (P + rho I)^{-1/2} v
+//   mode kInv:                out = (P + rho I)^{-1} v  (Cholesky-stabilised form)
+// Phase 1: each CTA reduces U^T v and ||v||^2 over its rows (a warp takes
+// eight rows at a time, lanes split k; FP32 per warp, FP64 across warps); the
+// partials meet through distributed shared memory; every CTA forms the
+// coefficients; phase 3 writes its rows of out = alpha v + U coef (one thread
+// per row) and, optionally, partial sums of out . dotv that CTA 0 collects
+// into *dot_out.
+// ---------------------------------------------------------------------------
+constexpr int kWbCluster = 8, kWbThreads = 256, kWbWarps = kWbThreads / 32, kWbRows = 8;
+
+struct WbArgs {
+  const float* U;
+  int64_t b;
+  int r;
+  const float* v;
+  int mode;
+  const double* keep;
+  const double* Lw;
+  const double* cis;
+  const DevScalars* sc;
+  float* out;
+  const float* dotv;
+  double* alpha;    // [0] alpha used, [1] 1/||v|| in normalised mode
+  double* dot_out;  // sum(out . dotv) when dotv != NULL
+};
+
+__global__ void __cluster_dims__(kWbCluster, 1, 1) __launch_bounds__(kWbThreads) k_wb_cluster(WbArgs a) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  __shared__ double part[kMaxRank + 2];        // this CTA's U^T v, ||v||^2, out . dotv
+  __shared__ double q[kMaxRank + 1];
+  __shared__ float coef[kMaxRank];
+  __shared__ float wtmp[kWbWarps][kMaxRank];
+  __shared__ double red[33];
+  __shared__ double s_alpha;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = a.r;
+  constexpr int KJ = kMaxRank / 32;
+  const int64_t per = (a.b + kWbCluster - 1) / kWbCluster;
+  const int64_t r0 = (int64_t)rank * per, r1 = min(a.b, r0 + per);
+  // ---- phase 1
+  float acc[KJ];
+#pragma unroll
+  for (int j = 0; j < KJ; ++j) acc[j] = 0.0f;
+  double vsq = 0.0;
+  for (int64_t i0 = r0 + (int64_t)warp * kWbRows; i0 < r1; i0 += (int64_t)kWbWarps * kWbRows) {
+    float vi[kWbRows], u[kWbRows][KJ];
+#pragma unroll
+    for (int t = 0; t < kWbRows; ++t) {
+      const int64_t i = i0 + t;
+      const bool ok = i < r1;
+      vi[t] = ok ? a.v[i] : 0.0f;
+#pragma unroll
+      for (int j = 0; j < KJ; ++j) {
+        const int k = lane + 32 * j;
+        u[t][j] = (ok && k < r) ? a.U[i * r + k] : 0.0f;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kWbRows; ++t) {
+#pragma unroll
+      for (int j = 0; j < KJ; ++j) acc[j] = fmaf(u[t][j], vi[t], acc[j]);
+      if (lane == 0) vsq += (double)vi[t] * (double)vi[t];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < KJ; ++j) {
+    const int k = lane + 32 * j;
+    if (k < r) wtmp[warp][k] = acc[j];
+  }
+  const double vsq_t = block_sum(vsq, red);   // contains __syncthreads
+  for (int k = threadIdx.x; k < r; k += kWbThreads) {
+    double t = 0.0;
+    for (int w = 0; w < kWbWarps; ++w) t += (double)wtmp[w][k];
+    part[k] = t;
+  }
+  if (threadIdx.x == 0) part[r] = vsq_t;
+  cl.sync();
+  // ---- phase 2: gather partials from every CTA of the cluster
+  for (int k = threadIdx.x; k <= r; k += kWbThreads) {
+    double t = 0.0;
+#pragma unroll
+    for (int c = 0; c < kWbCluster; ++c) t += cl.map_shared_rank(part, c)[k];
+    q[k] = t;
+  }
+  __syncthreads();
+  const double rho = a.sc->rho;
+  if (a.mode == kInv) {
+    // y = Lw^{-T} Lw^{-1} (keep . q) by warp 0, lanes splitting the dot products
+    if (warp == 0) {
+      for (int i = 0; i < r; ++i) {
+        double pt = 0.0;
+        for (int k = lane; k < i; k += 32) pt += a.Lw[i * r + k] * q[k];
+        pt = warp_sum(pt);
+        if (lane == 0) q[i] = (a.keep[i] * q[i] - pt) / a.Lw[i * r + i];
+        __syncwarp();
+      }
+      for (int i = r - 1; i >= 0; --i) {
+        double pt = 0.0;
+        for (int k = i + 1 + lane; k < r; k += 32) pt += a.Lw[k * r + i] * q[k];
+        pt = warp_sum(pt);
+        if (lane == 0) q[i] = (q[i] - pt) / a.Lw[i * r + i];
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < r; k += kWbThreads) coef[k] = (float)(-a.keep[k] * q[k] / rho);
+    if (threadIdx.x == 0) s_alpha = 1.0 / rho;
+  } else {
+    const double scale = (a.mode == kInvSqrtNormalised) ? (q[r] > 0.0 ? 1.0 / sqrt(q[r]) : 0.0) : 1.0;
+    for (int k = threadIdx.x; k < r; k += kWbThreads) coef[k] = (float)(scale * q[k] * a.cis[k]);
+    if (threadIdx.x == 0) {
+      s_alpha = scale / sqrt(rho);
+      if (rank == 0) {
+        a.alpha[0] = s_alpha;
+        if (a.mode == kInvSqrtNormalised) a.alpha[1] = scale;
+      }
+    }
+  }
+  __syncthreads();
+  const float al = (float)s_alpha;
+  // ---- phase 3: out rows, one thread per row (independent loads)
+  double dt = 0.0;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += kWbThreads) {
+    const float* ui = a.U + i * r;
+    float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f, t3 = 0.0f;
+    int k = 0;
+    for (; k + 4 <= r; k += 4) {
+      t0 = fmaf(ui[k], coef[k], t0);
+      t1 = fmaf(ui[k + 1], coef[k + 1], t1);
+      t2 = fmaf(ui[k + 2], coef[k + 2], t2);
+      t3 = fmaf(ui[k + 3], coef[k + 3], t3);
+    }
+    for (; k < r; ++k) t0 = fmaf(ui[k], coef[k], t0);
+    const float o = fmaf(al, a.v[i], (t0 + t1) + (t2 + t3));
+    a.out[i] = o;
+    if (a.dotv) dt += (double)o * (double)a.dotv[i];
+  }
+  if (a.dotv) {
+    const double dtt = block_sum(dt, red);
+    if (threadIdx.x == 0) part[kMaxRank + 1] = dtt;
+  }
+  cl.sync();
+  if (a.dotv && rank == 0 && threadIdx.x == 0) {
+    double t = 0.0;
+    for (int c = 0; c < kWbCluster; ++c) t += cl.map_shared_rank(part, c)[kMaxRank + 1];
+    *a.dot_out = t;
+  }
+  cl.sync();  // no CTA leaves while rank 0 may still read its shared memory
+}
+
+cudaError_t launch_wb_cluster(CoreBufs& cb, int mode, const float* v, float* out, const float* dotv, DevScalars* sc,
+                              cudaStream_t st) {
+  WbArgs a;
+  a.U = cb.U; a.b = cb.b; a.r = cb.r; a.v = v; a.mode = mode; a.keep = cb.keep; a.Lw = cb.Lw; a.cis = cb.cis;
+  a.sc = sc; a.out = out; a.dotv = dotv; a.alpha = cb.alpha; a.dot_out = cb.dot_part;
+  k_wb_cluster<<<kWbCluster, kWbThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t core_init() {
   const int big = 200 * 1024;
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_nys_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_make_u, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-  if ((e = cudaFuncSetAttribute(k_chol_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-  if ((e = cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_chol_plain<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_chol_plain<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_wchol, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_wcoef, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_wapply, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;

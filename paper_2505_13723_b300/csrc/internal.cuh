@@ -113,6 +113,7 @@ struct CoreBufs {
   double* dot_part;   // [kReduceBlocks]
   double* alpha;      // scalar apply coefficient
   double* Ident;      // r x r identity
+  double* cis;        // r  (S_k + rho)^{-1/2} - rho^{-1/2}
 };
 int gram_chunks_for(int64_t b);
 int utv_chunks_for(int64_t b);
@@ -129,6 +130,10 @@ cudaError_t launch_woodbury_apply(CoreBufs& cb, int mode, const float* v, int s,
                                   bool want_sq, bool want_dot, const float* dotv, DevScalars* sc,
                                   cudaStream_t st);
 cudaError_t launch_set_eta(CoreBufs& cb, DevScalars* sc, int identity, cudaStream_t st);
+// One single-RHS Woodbury apply in one 8-CTA cluster launch.  With dotv,
+// writes sum(out . dotv) to cb.dot_part[0].
+cudaError_t launch_wb_cluster(CoreBufs& cb, int mode, const float* v, float* out, const float* dotv, DevScalars* sc,
+                              cudaStream_t st);
 cudaError_t launch_nesterov(float* W, float* V, float* Z, int64_t count, float beta, float alpha,
                             int literal, cudaStream_t st);
 cudaError_t launch_scatter(float* W, float* V, float* Z, const int* B, int64_t b, int s,

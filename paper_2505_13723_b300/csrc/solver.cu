@@ -483,6 +483,7 @@ adasap_status alloc_solver(adasap_solver* S) {
   cb.dot_part = ar.get<double>(kReduceBlocks);
   cb.alpha = ar.get<double>(2);
   cb.Ident = ar.get<double>((size_t)rr * rr);
+  cb.cis = ar.get<double>(rr);
   return ar.err == cudaSuccess ? ADASAP_OK : ADASAP_ENOMEM;
 }
 
@@ -529,22 +530,34 @@ cudaError_t capture_iteration(adasap_solver* S, const int64_t* Bs, const float* 
   }
   // v0 copy and ||v0||^2 partials
   if (S->tc_pw) K(launch_build_tc(c->Xc, c->qc, S->B32, b, c->d, c->dp, S->XBhi, S->XBlo, s1));
-  K(launch_reduce(S->v0, 1, b, 1, 0, 1, S->vA, 1, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, cb.sq_part, s1));
-  float* vcur = S->vA;
-  float* vnext = S->vB;
+  // Alg. 5: v <- (P + rho I)^{-1/2} H (P + rho I)^{-1/2} v / ||v||, N times
+  const float* vcur = S->v0;
+  float* vbuf[2] = {S->vA, S->vB};
   for (int i = 0; i < S->o.power_iters; ++i) {
     const bool last = i == S->o.power_iters - 1;
-    K(launch_woodbury_apply(cb, kInvSqrtNormalised, vcur, 1, S->a, false, false, nullptr, c->sc, s1));
+    float* vnext = vbuf[i & 1];
+    if (!S->identity) K(launch_wb_cluster(cb, kInvSqrtNormalised, vcur, S->a, nullptr, c->sc, s1));
+    else {
+      K(launch_reduce(vcur, 1, b, 1, 0, 1, S->h, 1, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, cb.sq_part,
+                      s1));
+      K(launch_woodbury_apply(cb, kInvSqrtNormalised, S->h, 1, S->a, false, false, nullptr, c->sc, s1));
+    }
     kb.w = S->a; kb.ldw = 1;
     if (S->tc_pw)
       K(launch_rows_tc(c->kern, c->d, S->XB, S->qB, nullptr, b, c->dp, S->XBhi, S->XBlo, b, 1, S->a, 1, S->part2,
                        S->ns_pw, c->sigma2, c->err_dev, s1));
     else
       K(launch_rows(c->kern, c->dp, kb, 1, S->ns_pw, false, s1));
-    K(launch_reduce(S->part2, S->ns_pw, b, 1, 0, 1, S->h, 1, (float)lam, S->a, nullptr, 1, 0.f, nullptr, nullptr, 0,
-                    nullptr, s1));
-    K(launch_woodbury_apply(cb, kInvSqrt, S->h, 1, vnext, true, last, last ? vcur : nullptr, c->sc, s1));
-    std::swap(vcur, vnext);
+    if (!S->identity) {
+      K(launch_reduce(S->part2, S->ns_pw, b, 1, 0, 1, S->h, 1, (float)lam, S->a, nullptr, 1, 0.f, nullptr, nullptr,
+                      0, nullptr, s1));
+      K(launch_wb_cluster(cb, kInvSqrt, S->h, vnext, last ? vcur : nullptr, c->sc, s1));
+    } else {
+      K(launch_reduce(S->part2, S->ns_pw, b, 1, 0, 1, S->h, 1, (float)lam, S->a, nullptr, 1, 0.f, nullptr, nullptr,
+                      0, nullptr, s1));
+      K(launch_woodbury_apply(cb, kInvSqrt, S->h, 1, vnext, true, last, last ? vcur : nullptr, c->sc, s1));
+    }
+    vcur = vnext;
   }
   K(launch_set_eta(cb, c->sc, S->identity, s1));
   K(cudaEventRecord(c->ev_join, s1));
@@ -555,7 +568,10 @@ cudaError_t capture_iteration(adasap_solver* S, const int64_t* Bs, const float* 
                   s0));
   K(cudaStreamWaitEvent(s0, c->ev_join, 0));
   // Step IV: direction and NesterovAcc
-  K(launch_woodbury_apply(cb, kInv, S->R, s, S->D, false, false, nullptr, c->sc, s0));
+  if (!S->identity && s == 1)
+    K(launch_wb_cluster(cb, kInv, S->R, S->D, nullptr, c->sc, s0));
+  else
+    K(launch_woodbury_apply(cb, kInv, S->R, s, S->D, false, false, nullptr, c->sc, s0));
   K(launch_nesterov(S->W, S->V, S->Z, n * (int64_t)s, (float)S->beta, (float)S->alpha, S->literal, s0));
   K(launch_scatter(S->W, S->V, S->Z, S->B32, b, s, S->D, (float)S->gamma, (float)S->alpha, S->literal, c->sc, s0));
   if (trace) K(launch_trace(c->sc, trace, s0));
