@@ -31,6 +31,14 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
   return *reinterpret_cast<float2*>(&rd);
 }
 
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
+  unsigned long long ra = *reinterpret_cast<unsigned long long*>(&a);
+  unsigned long long rb = *reinterpret_cast<unsigned long long*>(&b);
+  unsigned long long rd;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+  return *reinterpret_cast<float2*>(&rd);
+}
+
 // ---- kernel epilogues --------------------------------------------------------
 // Columns and rows are stored pre-scaled: x' = kappa (x - mean) / ell with
 //   RBF  kappa^2 = log2(e)/2   -> u = kappa^2 r~^2,  k = sigma2 * 2^(-u)

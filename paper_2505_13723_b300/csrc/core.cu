@@ -44,7 +44,7 @@ __device__ __forceinline__ float cat_get(const float* A1, int64_t ld1, int c1, c
 
 // 64 x 64 output tiles, 256 threads x (4 x 4) outputs, 16-row slices.
 // EXACT: products and sums in FP64 (exact products of FP32 entries);
-// otherwise FP32 products summed in FP32 over a 16-row slice, then in FP64.
+// otherwise FP32 products summed in FP32 over 64 rows, then in FP64.
 template <bool EXACT>
 __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1, int64_t ld1, int c1,
                                                    const float* __restrict__ A2, int64_t ld2, int c2,
@@ -64,6 +64,12 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1,
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+  T f[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) f[u][v] = (T)0;
+  int slices = 0;
   for (int64_t s0 = r0; s0 < r1; s0 += KR) {
     __syncthreads();
     for (int e = tid; e < KR * TS; e += 256) {
@@ -74,11 +80,6 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1,
       sb[rr][cc] = ok ? (T)cat_get(A1, ld1, c1, A2, ld2, c2, row, tj * TS + cc) : (T)0;
     }
     __syncthreads();
-    T f[4][4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) f[u][v] = (T)0;
 #pragma unroll 4
     for (int rr = 0; rr < KR; ++rr) {
       T a[4], bb[4];
@@ -92,10 +93,19 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1,
 #pragma unroll
         for (int v = 0; v < 4; ++v) f[u][v] = fma(a[u], bb[v], f[u][v]);
     }
+    // FP64 accumulation every kSpan slices (exact products: every slice); FP64
+    // additions are expensive on this GPU, FP32 sums over 64 rows are not
+    constexpr int kSpan = EXACT ? 1 : 4;
+    if (++slices == kSpan || s0 + KR >= r1) {
+      slices = 0;
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) acc[u][v] += (double)f[u][v];
+        for (int v = 0; v < 4; ++v) {
+          acc[u][v] += (double)f[u][v];
+          f[u][v] = (T)0;
+        }
+    }
   }
 #pragma unroll
   for (int u = 0; u < 4; ++u)
@@ -107,12 +117,21 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1,
 }
 
 __global__ void k_gram_reduce(const double* __restrict__ part, int chunks, int c, double* __restrict__ G) {
+  const int64_t cc = (int64_t)c * c;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < c * c; e += gridDim.x * blockDim.x) {
     int i = e / c, j = e % c;
     if ((i >> 6) > (j >> 6)) { const int t = i; i = j; j = t; }
-    double acc = 0.0;
-    for (int ch = 0; ch < chunks; ++ch) acc += part[((int64_t)ch * c + i) * c + j];
-    G[e] = acc;
+    const int64_t o = (int64_t)i * c + j;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int ch = 0;
+    for (; ch + 4 <= chunks; ch += 4) {
+      a0 += part[ch * cc + o];
+      a1 += part[(ch + 1) * cc + o];
+      a2 += part[(ch + 2) * cc + o];
+      a3 += part[(ch + 3) * cc + o];
+    }
+    for (; ch < chunks; ++ch) a0 += part[ch * cc + o];
+    G[e] = (a0 + a1) + (a2 + a3);
   }
 }
 
@@ -120,6 +139,9 @@ cudaError_t launch_gram(const float* A1, int64_t ld1, int c1, const float* A2, i
                         int64_t m, double* part, int chunks, double* G, bool exact, cudaStream_t st) {
   const int c = c1 + c2;
   const int nt = (c + 63) / 64;
+  // about two resident CTAs per SM over the upper tiles; fewer partials to reduce
+  const int active = nt * (nt + 1) / 2;
+  chunks = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)chunks, (int64_t)(296 / active), (m + 31) / 32}));
   const int64_t chunk_rows = (m + chunks - 1) / chunks;
   if (exact)
     k_gram_part<true><<<dim3(chunks, nt, nt), 256, 0, st>>>(A1, ld1, c1, A2, ld2, c2, m, chunk_rows, part);
@@ -130,35 +152,35 @@ cudaError_t launch_gram(const float* A1, int64_t ld1, int c1, const float* A2, i
 }
 
 // ---------------------------------------------------------------------------
-// One-CTA FP64 Cholesky (lower, in place) of an r x r matrix in shared memory
-// with leading dimension ld (r + 1 keeps column reads conflict free).
-// Returns false, uniformly over the block, if a pivot is not positive.
+// One-CTA Cholesky (lower, in place) of an r x r matrix in shared memory with
+// leading dimension ld (r + 1 keeps column reads conflict free).  Right-looking
+// with deferred scaling, so a column costs one barrier: step k subtracts
+// A[i][k] A[j][k] / d_k from the trailing entries (d_k the pivot, column k
+// still unscaled), and the factor L[i][k] = A[i][k] / sqrt(d_k) is formed
+// once at the end.  Returns false, uniformly over the block, if a pivot is
+// not positive.  `piv` is caller shared scratch of r entries.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ bool chol_lower_smem(T* A, int r, int ld, int* flag) {
+__device__ bool chol_lower_smem(T* A, int r, int ld, T* piv) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __shared__ T s_rdk;
   for (int k = 0; k < r; ++k) {
-    if (threadIdx.x == 0) {
-      const T d = A[k * ld + k];
-      *flag = (d > T(0) && isfinite(d)) ? 0 : 1;
-      if (!*flag) {
-        const T sd = sqrt(d);
-        A[k * ld + k] = sd;
-        s_rdk = T(1) / sd;
-      }
-    }
     __syncthreads();
-    if (*flag) return false;
-    const T rdk = s_rdk;
-    for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) A[i * ld + k] *= rdk;
-    __syncthreads();
+    const T d = A[k * ld + k];
+    if (!(d > T(0) && isfinite(d))) return false;
+    const T rd = T(1) / d;
     for (int i = k + 1 + warp; i < r; i += nw) {
-      const T lik = A[i * ld + k];
-      for (int j = k + 1 + lane; j <= i; j += 32) A[i * ld + j] -= lik * A[j * ld + k];
+      const T aik = A[i * ld + k] * rd;
+      for (int j = k + 1 + lane; j <= i; j += 32) A[i * ld + j] -= aik * A[j * ld + k];
     }
-    __syncthreads();
   }
+  __syncthreads();
+  for (int k = threadIdx.x; k < r; k += blockDim.x) piv[k] = T(1) / sqrt(A[k * ld + k]);
+  __syncthreads();
+  for (int i = warp; i < r; i += nw)
+    for (int j = lane; j < i; j += 32) A[i * ld + j] *= piv[j];
+  __syncthreads();
+  for (int k = threadIdx.x; k < r; k += blockDim.x) A[k * ld + k] = T(1) / piv[k];
+  __syncthreads();
   return true;
 }
 
@@ -170,7 +192,7 @@ __global__ void __launch_bounds__(512) k_nys_chol(const double* __restrict__ G, 
                                                   DevScalars* sc) {
   extern __shared__ double sh[];
   __shared__ double red[33];
-  __shared__ int flag;
+  __shared__ double piv[kMaxRank];
   const int ld = r + 1, c = 2 * r;
   double tr = 0.0;
   for (int i = threadIdx.x; i < r; i += blockDim.x) tr += G[(int64_t)i * c + r + i];
@@ -185,7 +207,7 @@ __global__ void __launch_bounds__(512) k_nys_chol(const double* __restrict__ G, 
       sh[i * ld + j] = oty + delta * G[(int64_t)i * c + j];
     }
     __syncthreads();
-    ok = chol_lower_smem(sh, r, ld, &flag);
+    ok = chol_lower_smem<double>(sh, r, ld, piv);
     __syncthreads();
     if (ok) break;
     delta *= 10.0;
@@ -223,26 +245,30 @@ __global__ void __launch_bounds__(32 * kTrsmWarps) k_trsm(const double* __restri
   T* rinv = sL + r * ld;                  // r
   T* xs = rinv + r;                       // kTrsmWarps x r
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) sL[(e / r) * ld + e % r] = (T)L[e];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = blockIdx.x * kTrsmWarps + warp;
+  T* x = xs + warp * r;
+  // the right-hand side column is staged first, so the solve loop touches shared memory only
+  if (col < r)
+    for (int i = lane; i < r; i += 32) x[i] = (T)(trans ? R[(int64_t)col * r + i] : R[(int64_t)i * r + col]);
   __syncthreads();
   for (int i = threadIdx.x; i < r; i += blockDim.x) rinv[i] = T(1) / sL[i * ld + i];
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int col = blockIdx.x * kTrsmWarps + warp;
   if (col >= r) return;
-  T* x = xs + warp * r;
   for (int step = 0; step < r; ++step) {
     const int i = upper ? r - 1 - step : step;
     T part = T(0);
-    if (!upper) {
-      for (int k = lane; k < i; k += 32) part += sL[i * ld + k] * x[k];
-    } else {
-      for (int k = i + 1 + lane; k < r; k += 32) part += sL[k * ld + i] * x[k];
+#pragma unroll
+    for (int j = 0; j < kMaxRank / 32; ++j) {
+      const int k = lane + 32 * j;
+      if (!upper) {
+        if (k < i) part += sL[i * ld + k] * x[k];
+      } else {
+        if (k > i && k < r) part += sL[k * ld + i] * x[k];
+      }
     }
     part = warp_sum(part);
-    if (lane == 0) {
-      const T rhs = (T)(trans ? R[(int64_t)col * r + i] : R[(int64_t)i * r + col]);
-      x[i] = (rhs - part) * rinv[i];
-    }
+    if (lane == 0) x[i] = (x[i] - part) * rinv[i];
     __syncwarp();
   }
   for (int i = lane; i < r; i += 32) X[(int64_t)i * r + col] = (double)x[i];
@@ -260,125 +286,169 @@ static cudaError_t trsm(const double* L, int r, const double* R, int trans, int 
 // columns are orthogonal; then A V = W and, A being PSD, V holds A's
 // eigenvectors (the eigenvalues are refined in FP64 by k_rayleigh).
 // Parallel round-robin ordering: in each of the r2 - 1 rounds of a sweep the
-// r2/2 disjoint pairs are rotated concurrently, one warp per pair, so a round
-// needs one barrier.  W and V are column-major in shared memory; the squared
-// column norms are carried along (updated exactly for each rotation and
+// r2/2 disjoint pairs are rotated concurrently, one half-warp per pair, so a
+// round needs one barrier.  W and V are column-major in shared memory; the
+// squared column norms are carried along (updated exactly for each rotation and
 // recomputed every sweep), so a pair needs one dot product.  A pair is skipped
 // when |w_p . w_q| <= 1e-6 |w_p| |w_q| or when it is below what the columns'
 // absolute FP32 noise can produce; sweeps stop when one rotates nothing (at
 // most kJacobiSweeps; Jacobi converges quadratically).
+// The rounds are bound by instruction issue on the one SM, so a pair is
+// handled by 16 lanes with eight rows each (float4 slots l and l + 16 of the
+// column, so that a half-warp touches one contiguous 256-byte span; packed
+// f32x2 arithmetic), the two pairs of a warp share every shuffle, and one lane
+// per pair computes the rotation.
 constexpr int kJacobiSweeps = 12;
+static_assert(kMaxRank == 128, "Jacobi column slices assume 16 lanes x 8 rows");
+
+__device__ __forceinline__ float2 f2lo(float4 x) { return make_float2(x.x, x.y); }
+__device__ __forceinline__ float2 f2hi(float4 x) { return make_float2(x.z, x.w); }
+__device__ __forceinline__ float4 f4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+// (c a - s b, s a + c b) on four rows
+__device__ __forceinline__ void rotate4(float4& a, float4& b, float2 c2, float2 s2, float2 ns2) {
+  const float2 alo = f2lo(a), ahi = f2hi(a), blo = f2lo(b), bhi = f2hi(b);
+  a = f4(ffma2(c2, alo, fmul2(ns2, blo)), ffma2(c2, ahi, fmul2(ns2, bhi)));
+  b = f4(ffma2(s2, alo, fmul2(c2, blo)), ffma2(s2, ahi, fmul2(c2, bhi)));
+}
+
 __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ A, int r, float* __restrict__ Vout,
                                                  DevScalars* sc) {
-  extern __shared__ float shf[];
+  extern __shared__ float4 shj[];
   const int r2 = r + (r & 1);
-  float* w = shf;               // r2 columns x r2 rows (column-major)
-  float* v = shf + r2 * r2;
+  const int cs = (r2 + 3) / 4;   // float4 per column (<= 32)
+  const int ld = 4 * cs;         // floats per column
+  float4* w = shj;               // r2 columns x cs float4
+  float4* v = shj + r2 * cs;
   __shared__ float nrm[kMaxRank];
   __shared__ float mxs[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int hl = lane & 15, hsel = lane >> 4;
+  const unsigned full = 0xffffffffu;
+  const int s0 = hl, s1 = hl + 16;  // this lane's two float4 slots of a column
+  const bool has0 = s0 < cs, has1 = s1 < cs;
   double mx = 0.0;
   for (int i = threadIdx.x; i < r; i += blockDim.x) mx = fmax(mx, fabs(A[(int64_t)i * r + i]));
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(full, mx, o));
   if (lane == 0) mxs[warp] = (float)mx;
   __syncthreads();
   float amax = 0.f;
   for (int k = 0; k < nw; ++k) amax = fmaxf(amax, mxs[k]);
   const double scale = amax > 0.f ? 1.0 / (double)amax : 1.0;
-  for (int e = threadIdx.x; e < r2 * r2; e += blockDim.x) {
-    const int col = e / r2, row = e % r2;
-    w[e] = (row < r && col < r) ? (float)(A[(int64_t)row * r + col] * scale) : 0.0f;
-    v[e] = (row == col) ? 1.0f : 0.0f;
+  float* wf = reinterpret_cast<float*>(w);
+  float* vf = reinterpret_cast<float*>(v);
+  for (int e = threadIdx.x; e < r2 * ld; e += blockDim.x) {
+    const int col = e / ld, row = e % ld;
+    wf[e] = (row < r && col < r) ? (float)(A[(int64_t)row * r + col] * scale) : 0.0f;
+    vf[e] = (row == col) ? 1.0f : 0.0f;
   }
   __syncthreads();
   const int half = r2 / 2;
-  float noise = 0.f;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float noise2 = 0.f;
   int sweep = 0;
   for (; sweep < kJacobiSweeps; ++sweep) {
-    // exact squared column norms at the start of every sweep
-    for (int col = warp; col < r2; col += nw) {
-      float t = 0.f;
-      for (int k = lane; k < r2; k += 32) t = fmaf(w[col * r2 + k], w[col * r2 + k], t);
-      t = warp_sum(t);
-      if (lane == 0) nrm[col] = t;
+    // exact squared column norms at the start of every sweep, one half-warp per column
+    for (int c0 = 2 * warp; c0 < r2; c0 += 2 * nw) {  // warp-uniform trip count (shuffles below)
+      const int col = c0 + hsel;
+      const bool ok = col < r2;
+      const float4 x0 = (ok && has0) ? w[col * cs + s0] : z4;
+      const float4 x1 = (ok && has1) ? w[col * cs + s1] : z4;
+      float t = fmaf(x0.x, x0.x, fmaf(x0.y, x0.y, fmaf(x0.z, x0.z, x0.w * x0.w)));
+      t = fmaf(x1.x, x1.x, fmaf(x1.y, x1.y, fmaf(x1.z, x1.z, fmaf(x1.w, x1.w, t))));
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) t += __shfl_xor_sync(full, t, o);
+      if (ok && hl == 0) nrm[col] = t;
     }
     __syncthreads();
     if (sweep == 0) {
       float nmax = 0.f;
       for (int k = 0; k < r2; ++k) nmax = fmaxf(nmax, nrm[k]);
       // absolute FP32 noise carried by every column after rotations against the largest
-      noise = 4.0f * 1.1920929e-7f * sqrtf(nmax);
+      const float noise = 4.0f * 1.1920929e-7f * sqrtf(nmax);
+      noise2 = noise * noise;
     }
     int rotated = 0;
     for (int round = 0; round < r2 - 1; ++round) {
-      // a warp owns pairs m = warp and m = warp + nw (r2 <= 128, nw = 32): both are
-      // processed together so their latency chains overlap
-      int pp[2], qq[2];
-      bool act[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int m = warp + h * nw;
-        act[h] = m < half;
-        int p = 0, q = 0;
-        if (m == 0) { p = round; q = r2 - 1; }
-        else {
-          p = round + m;
-          if (p >= r2 - 1) p -= r2 - 1;
-          q = round - m;
-          if (q < 0) q += r2 - 1;
+      const int m = 2 * warp + hsel;  // this half-warp's pair
+      const bool act = m < half;
+      int p = 0, q = 0;
+      if (m == 0) {
+        p = round;
+        q = r2 - 1;
+      } else {
+        p = round + m;
+        if (p >= r2 - 1) p -= r2 - 1;
+        q = round - m;
+        if (q < 0) q += r2 - 1;
+      }
+      if (p > q) {
+        const int t = p;
+        p = q;
+        q = t;
+      }
+      float4 a0 = z4, a1 = z4, b0 = z4, b1 = z4;
+      if (act) {
+        if (has0) {
+          a0 = w[p * cs + s0];
+          b0 = w[q * cs + s0];
         }
-        pp[h] = p < q ? p : q;
-        qq[h] = p < q ? q : p;
+        if (has1) {
+          a1 = w[p * cs + s1];
+          b1 = w[q * cs + s1];
+        }
       }
-      float ga[2] = {0.f, 0.f};
+      float2 g2 = fmul2(f2lo(a0), f2lo(b0));
+      g2 = ffma2(f2hi(a0), f2hi(b0), g2);
+      g2 = ffma2(f2lo(a1), f2lo(b1), g2);
+      g2 = ffma2(f2hi(a1), f2hi(b1), g2);
+      float g = g2.x + g2.y;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (!act[h]) continue;
-        const float* wp = w + pp[h] * r2;
-        const float* wq = w + qq[h] * r2;
-        for (int k = lane; k < r2; k += 32) ga[h] = fmaf(wp[k], wq[k], ga[h]);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        ga[0] += __shfl_xor_sync(0xffffffffu, ga[0], o);
-        ga[1] += __shfl_xor_sync(0xffffffffu, ga[1], o);
-      }
-      int mine = 0;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (!act[h]) continue;
-        const int p = pp[h], q = qq[h];
-        const float al = nrm[p], be = nrm[q], g = ga[h];
-        const float ab = al * be;
-        const float sab = ab * rsqrtf(fmaxf(ab, 1e-37f));
-        const float sa = al * rsqrtf(fmaxf(al, 1e-37f)), sb = be * rsqrtf(fmaxf(be, 1e-37f));
-        if (fabsf(g) > 1e-6f * sab && fabsf(g) > noise * (sa + sb)) {
+      for (int o = 8; o > 0; o >>= 1) g += __shfl_xor_sync(full, g, o);
+      // rotation parameters on the half-warp's first lane
+      float cr = 1.0f, sr = 0.0f;
+      int rot = 0;
+      if (hl == 0 && act) {
+        const float al = nrm[p], be = nrm[q];
+        const float gg = g * g;
+        // |g| > 1e-6 |w_p| |w_q|  and  |g| > noise sqrt(|w_p|^2 + |w_q|^2)
+        if (gg > 1e-12f * al * be && gg > noise2 * (al + be)) {
           const float zeta = __fdividef(be - al, 2.0f * g);
           const float z2 = fmaf(zeta, zeta, 1.0f);
           const float t = copysignf(1.0f, zeta) * __fdividef(1.0f, fabsf(zeta) + z2 * rsqrtf(z2));
-          const float c = rsqrtf(fmaf(t, t, 1.0f));
-          const float sn = c * t;
-          float* wp = w + p * r2;
-          float* wq = w + q * r2;
-          float* vp = v + p * r2;
-          float* vq = v + q * r2;
-          for (int k = lane; k < r2; k += 32) {
-            const float a = wp[k], bq = wq[k];
-            wp[k] = c * a - sn * bq;
-            wq[k] = sn * a + c * bq;
-            const float x = vp[k], y = vq[k];
-            vp[k] = c * x - sn * y;
-            vq[k] = sn * x + c * y;
-          }
-          if (lane == 0) {
-            // norms after a rotation that zeroes the pair's inner product
-            nrm[p] = c * c * al - 2.0f * c * sn * g + sn * sn * be;
-            nrm[q] = sn * sn * al + 2.0f * c * sn * g + c * c * be;
-          }
-          mine = 1;
+          cr = rsqrtf(fmaf(t, t, 1.0f));
+          sr = cr * t;
+          rot = 1;
+          // norms after a rotation that zeroes the pair's inner product
+          nrm[p] = cr * cr * al - 2.0f * cr * sr * g + sr * sr * be;
+          nrm[q] = sr * sr * al + 2.0f * cr * sr * g + cr * cr * be;
         }
       }
-      rotated |= __syncthreads_or(mine);
+      const int src = lane & 16;
+      const float c = __shfl_sync(full, cr, src);
+      const float sn = __shfl_sync(full, sr, src);
+      const int doit = __shfl_sync(full, rot, src);
+      if (doit) {
+        const float2 c2 = make_float2(c, c), s2 = make_float2(sn, sn), ns2 = make_float2(-sn, -sn);
+        if (has0) {
+          rotate4(a0, b0, c2, s2, ns2);
+          w[p * cs + s0] = a0;
+          w[q * cs + s0] = b0;
+          float4 x = v[p * cs + s0], y = v[q * cs + s0];
+          rotate4(x, y, c2, s2, ns2);
+          v[p * cs + s0] = x;
+          v[q * cs + s0] = y;
+        }
+        if (has1) {
+          rotate4(a1, b1, c2, s2, ns2);
+          w[p * cs + s1] = a1;
+          w[q * cs + s1] = b1;
+          float4 x = v[p * cs + s1], y = v[q * cs + s1];
+          rotate4(x, y, c2, s2, ns2);
+          v[p * cs + s1] = x;
+          v[q * cs + s1] = y;
+        }
+      }
+      rotated |= __syncthreads_or(doit);
     }
     if (!rotated) break;
   }
@@ -386,7 +456,7 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ A, i
   // Vout row-major: Vout[k * r + i] = component k of eigenvector i
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int k = e / r, i = e % r;
-    Vout[e] = v[i * r2 + k];
+    Vout[e] = vf[i * ld + k];
   }
 }
 
@@ -461,7 +531,7 @@ __global__ void __launch_bounds__(256) k_make_u(const float* __restrict__ A1, co
   extern __shared__ float shm[];
   float* sT = shm;                  // r x r
   float* sY = shm + r * r;          // 32 x r
-  const double delta = A2 ? sc->delta : 0.0;
+  const float fdelta = A2 ? (float)sc->delta : 0.0f;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x)
     sT[e] = (float)(transT ? T[(e % r) * r + e / r] : T[e]);
   const int64_t row0 = (int64_t)blockIdx.x * 32;
@@ -469,7 +539,7 @@ __global__ void __launch_bounds__(256) k_make_u(const float* __restrict__ A1, co
     const int rr = e / r, k = e % r;
     const int64_t row = row0 + rr;
     float v = 0.0f;
-    if (row < b) v = A2 ? (float)((double)A1[row * r + k] + delta * (double)A2[row * r + k]) : A1[row * r + k];
+    if (row < b) v = A2 ? fmaf(fdelta, A2[row * r + k], A1[row * r + k]) : A1[row * r + k];
     sY[e] = v;
   }
   __syncthreads();
@@ -518,11 +588,11 @@ __global__ void __launch_bounds__(512) k_chol_plain(const double* __restrict__ G
                                                     DevScalars* sc, int detail) {
   extern __shared__ double shd_chol[];
   T* sh = reinterpret_cast<T*>(shd_chol);
-  __shared__ int flag;
+  __shared__ T piv[kMaxRank];
   const int ld = r + 1;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) sh[(e / r) * ld + e % r] = (T)G[e];
   __syncthreads();
-  const bool ok = chol_lower_smem<T>(sh, r, ld, &flag);
+  const bool ok = chol_lower_smem<T>(sh, r, ld, piv);
   __syncthreads();
   if (!ok && threadIdx.x == 0) set_status(sc, ADASAP_ENUMERIC, detail);
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
@@ -559,20 +629,26 @@ cudaError_t launch_orthonormalize(CoreBufs& cb, float* Om, float* tmp, DevScalar
   return cudaGetLastError();
 }
 
-cudaError_t launch_nystrom_core(CoreBufs& cb, double eps, double lam, DevScalars* sc, const float* Om,
-                                const float* Ysk, cudaStream_t st) {
+cudaError_t launch_nystrom_grams(CoreBufs& cb, const float* Om, const float* Ysk, cudaStream_t st) {
   const int r = cb.r;
   cudaError_t e;
   // Gram of [Omega | M Omega] -> (Omega^T Omega, Omega^T Y, Y^T Y)
   if ((e = launch_gram(Om, r, r, Ysk, r, r, cb.b, cb.gram_part, cb.gram_chunks, cb.G, false, st))) return e;
-  if ((e = launch_gram(Ysk, r, r, nullptr, 0, 0, cb.b, cb.gram_part, cb.gram_chunks, cb.Gyy, true, st))) return e;
+  return launch_gram(Ysk, r, r, nullptr, 0, 0, cb.b, cb.gram_part, cb.gram_chunks, cb.Gyy, true, st);
+}
+
+cudaError_t launch_nystrom_core(CoreBufs& cb, double eps, double lam, DevScalars* sc, const float* Om,
+                                const float* Ysk, cudaStream_t st) {
+  const int r = cb.r;
+  cudaError_t e;
   const size_t sm_chol = (size_t)r * (r + 1) * sizeof(double);
   k_nys_chol<<<1, 512, sm_chol, st>>>(cb.G, cb.Gyy, r, eps, cb.Lc, cb.Gnu, sc);
   // A = L^{-1} Gnu L^{-T}  (= C^{-T} Y_nu^T Y_nu C^{-1} = B^T B)
   if ((e = trsm(cb.Lc, r, cb.Gnu, 0, 0, cb.X1, st))) return e;
   if ((e = trsm(cb.Lc, r, cb.X1, 1, 0, cb.A, st))) return e;
   const int r2 = r + (r & 1);
-  k_jacobi<<<1, 1024, (size_t)2 * r2 * r2 * sizeof(float), st>>>(cb.A, r, cb.V32, sc);
+  k_jacobi<<<1, 32 * ((r2 / 2 + 1) / 2), (size_t)2 * r2 * (4 * ((r2 + 3) / 4)) * sizeof(float), st>>>(
+      cb.A, r, cb.V32, sc);
   k_rayleigh<<<r, 128, 0, st>>>(cb.A, cb.V32, r, cb.lam);
   k_nys_finalize<<<1, 256, 0, st>>>(cb.lam, cb.V32, r, lam, sc, cb.S, cb.keep, cb.X1);
   // T = L^{-T} T'
@@ -580,27 +656,90 @@ cudaError_t launch_nystrom_core(CoreBufs& cb, double eps, double lam, DevScalars
   return make_u(Ysk, Om, cb.b, r, cb.T, 0, sc, cb.U, st);
 }
 
-// L_w L_w^T = rho S^{-1} + U^T U on the kept eigenpairs (App. C.2, stabilised form)
-__global__ void __launch_bounds__(512) k_wchol(const double* __restrict__ UtU, int r, const double* __restrict__ S,
-                                               const double* __restrict__ keep, DevScalars* sc,
-                                               double* __restrict__ Lw) {
-  extern __shared__ double sh[];
-  __shared__ int flag;
-  const int ld = r + 1;
+// M = (rho S^{-1} + U^T U)^{-1} on the kept eigenpairs (App. C.2, stabilised
+// form; a dropped pair keeps a unit diagonal and zero coupling).  With U close
+// to orthonormal the matrix is D + E with D = diag(1 + rho / S_k) in [1, inf)
+// and E small, i.e. well conditioned after diagonal scaling, so the inverse is
+// taken in FP32 by Gauss-Jordan elimination without pivoting (its pivots are
+// those of the Cholesky factorisation; a non-positive one is reported).  The
+// elimination ping-pongs between two copies, one barrier per column.
+constexpr int kWfThreads = 512;
+__device__ __forceinline__ void set4(float4& x, int c, float v) {
+  if (c == 0) x.x = v;
+  else if (c == 1) x.y = v;
+  else if (c == 2) x.z = v;
+  else x.w = v;
+}
+__global__ void __launch_bounds__(kWfThreads) k_wfactor(const double* __restrict__ UtU, int r,
+                                                        const double* __restrict__ S, const double* __restrict__ keep,
+                                                        DevScalars* sc, float* __restrict__ Minv,
+                                                        float* __restrict__ Gu) {
+  extern __shared__ float4 shw4[];
+  const int nb = (r + 3) / 4;    // float4 per row
+  const int ld = 4 * nb;         // rows padded with zeros to a multiple of 4
+  float4* bufs[2] = {shw4, shw4 + r * nb};
   const double rho = sc->rho;
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-    const int i = e / r, j = e % r;
-    double v = keep[i] * keep[j] * UtU[e];
-    if (i == j) v += keep[i] > 0.0 ? rho / S[i] : 1.0;
-    sh[i * ld + j] = v;
+  for (int e = threadIdx.x; e < r * ld; e += blockDim.x) {
+    const int i = e / ld, j = e % ld;
+    float val = 0.0f;
+    if (j < r) {
+      const double g = UtU[i * r + j];
+      Gu[i * r + j] = (float)g;
+      double v = keep[i] * keep[j] * g;
+      if (i == j) v += keep[i] > 0.0 ? rho / S[i] : 1.0;
+      val = (float)v;
+    }
+    reinterpret_cast<float*>(bufs[0])[e] = val;
+  }
+  // this thread's (row, float4 column block) items, fixed over the elimination
+  constexpr int kItems = kMaxRank * (kMaxRank / 4) / kWfThreads;
+  int it_i[kItems], it_j[kItems];
+#pragma unroll
+  for (int m = 0; m < kItems; ++m) {
+    const int e = threadIdx.x + m * kWfThreads;
+    it_i[m] = e < r * nb ? e / nb : -1;
+    it_j[m] = e < r * nb ? e % nb : 0;
+  }
+  bool ok = true;
+  int cur = 0;
+  for (int k = 0; k < r; ++k) {
+    __syncthreads();
+    const float4* A4 = bufs[cur];
+    float4* B4 = bufs[cur ^ 1];
+    const float* Af = reinterpret_cast<const float*>(A4);
+    const float pv = Af[k * ld + k];
+    if (!(pv > 0.0f && isfinite(pv))) {
+      ok = false;
+      break;
+    }
+    const float rp = 1.0f / pv;
+    const int kb = k >> 2, kc = k & 3;
+#pragma unroll
+    for (int m = 0; m < kItems; ++m) {
+      const int i = it_i[m], jb = it_j[m];
+      if (i < 0) continue;
+      const float4 akj = A4[k * nb + jb];
+      float4 o;
+      if (i == k) {
+        o = make_float4(akj.x * rp, akj.y * rp, akj.z * rp, akj.w * rp);
+        if (jb == kb) set4(o, kc, rp);
+      } else {
+        const float fi = Af[i * ld + k] * rp;
+        const float4 aij = A4[i * nb + jb];
+        o = make_float4(fmaf(-fi, akj.x, aij.x), fmaf(-fi, akj.y, aij.y), fmaf(-fi, akj.z, aij.z),
+                        fmaf(-fi, akj.w, aij.w));
+        if (jb == kb) set4(o, kc, -fi);
+      }
+      B4[i * nb + jb] = o;
+    }
+    cur ^= 1;
   }
   __syncthreads();
-  const bool ok = chol_lower_smem(sh, r, ld, &flag);
-  __syncthreads();
   if (!ok && threadIdx.x == 0) set_status(sc, ADASAP_ENUMERIC, 3);
+  const float* Mf = reinterpret_cast<const float*>(bufs[cur]);
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
-    Lw[e] = ok ? ((j <= i) ? sh[i * ld + j] : 0.0) : (i == j ? 1.0 : 0.0);
+    Minv[e] = ok ? Mf[i * ld + j] : (i == j ? 1.0f : 0.0f);
   }
 }
 
@@ -617,7 +756,8 @@ cudaError_t launch_woodbury_factor(CoreBufs& cb, double lam, DevScalars* sc, cud
   const int r = cb.r;
   cudaError_t e;
   if ((e = launch_gram(cb.U, r, r, nullptr, 0, 0, cb.b, cb.gram_part, cb.gram_chunks, cb.X1, false, st))) return e;
-  k_wchol<<<1, 512, (size_t)r * (r + 1) * sizeof(double), st>>>(cb.X1, r, cb.S, cb.keep, sc, cb.Lw);
+  k_wfactor<<<1, kWfThreads, (size_t)2 * r * (4 * ((r + 3) / 4)) * sizeof(float), st>>>(cb.X1, r, cb.S, cb.keep,
+                                                                                        sc, cb.Minv, cb.Gu);
   k_invsqrt_coef<<<1, 128, 0, st>>>(cb.S, r, sc, cb.cis);
   return cudaGetLastError();
 }
@@ -675,7 +815,7 @@ __global__ void __launch_bounds__(256) k_utv(const float* __restrict__ U, int64_
 // alpha[1] = 1/||v|| of the input (normalised mode).
 __global__ void __launch_bounds__(256) k_wcoef(int mode, const double* __restrict__ part, int chunks, int r, int s,
                                                const double* __restrict__ S, const double* __restrict__ keep,
-                                               const double* __restrict__ Lw, const double* __restrict__ sq_part,
+                                               const float* __restrict__ Minv, const double* __restrict__ sq_part,
                                                DevScalars* sc, float* __restrict__ coef, double* __restrict__ alpha) {
   extern __shared__ double q[];  // r x s
   __shared__ double red[33];
@@ -695,26 +835,13 @@ __global__ void __launch_bounds__(256) k_wcoef(int mode, const double* __restric
   }
   __syncthreads();
   if (mode == kInv) {
-    // y = L^{-T} L^{-1} (keep . q): one warp per column, lanes split each dot product
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int c = warp; c < s; c += nw) {
-      for (int i = 0; i < r; ++i) {
-        double part = 0.0;
-        for (int k = lane; k < i; k += 32) part += Lw[i * r + k] * q[k * s + c];
-        part = warp_sum(part);
-        if (lane == 0) q[i * s + c] = (keep[i] * q[i * s + c] - part) / Lw[i * r + i];
-        __syncwarp();
-      }
-      for (int i = r - 1; i >= 0; --i) {
-        double part = 0.0;
-        for (int k = i + 1 + lane; k < r; k += 32) part += Lw[k * r + i] * q[k * s + c];
-        part = warp_sum(part);
-        if (lane == 0) q[i * s + c] = (q[i * s + c] - part) / Lw[i * r + i];
-        __syncwarp();
-      }
+    // coef = -keep . M (keep . q) / rho with M = (rho S^{-1} + U^T U)^{-1} (FP32: M is well conditioned)
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+      const int k = o / s, c = o % s;
+      float acc = 0.0f;
+      for (int j = 0; j < r; ++j) acc = fmaf(Minv[k * r + j], (float)(keep[j] * q[j * s + c]), acc);
+      coef[o] = (float)(-keep[k] * (double)acc / rho);
     }
-    __syncthreads();
-    for (int o = threadIdx.x; o < nout; o += blockDim.x) coef[o] = (float)(-keep[o / s] * q[o] / rho);
     if (threadIdx.x == 0) alpha[0] = 1.0 / rho;
   } else {
     const double irs = 1.0 / sqrt(rho);
@@ -823,8 +950,8 @@ cudaError_t launch_woodbury_apply(CoreBufs& cb, int mode, const float* v, int s,
   const int ogroups = (r * s + 256 * kUtvOut - 1) / (256 * kUtvOut);
   k_utv<<<dim3(cb.utv_chunks, ogroups), 256, (size_t)(32 * r + 32 * s) * sizeof(float), st>>>(cb.U, cb.b, r, v, s, s,
                                                                                                chunk_rows, cb.utv_part);
-  k_wcoef<<<1, 256, (size_t)r * s * sizeof(double), st>>>(mode, cb.utv_part, cb.utv_chunks, r, s, cb.S, cb.keep,
-                                                          cb.Lw, cb.sq_part, sc, cb.coef, cb.alpha);
+  k_wcoef<<<1, 256, (size_t)r * s * sizeof(double), st>>>(mode, cb.utv_part, cb.utv_chunks, r, s, cb.S,
+                                                              cb.keep, cb.Minv, cb.sq_part, sc, cb.coef, cb.alpha);
   k_wapply<<<kReduceBlocks, 256, (size_t)r * s * sizeof(float), st>>>(cb.U, cb.b, r, v, s, cb.coef, cb.alpha, out,
                                                                        sqp, dtp, dotv);
   return cudaGetLastError();
@@ -937,46 +1064,99 @@ cudaError_t launch_tick(DevScalars* sc, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// One single-RHS Woodbury apply (App. C.2) in one launch of an 8-CTA cluster:
-//   mode kInvSqrtNormalised:  out = (P + rho I)^{-1/2} (v / ||v||)
-//   mode kInvSqrt:            out = (P + rho I)^{-1/2} v
-//   mode kInv:                out = (P + rho I)^{-1} v  (Cholesky-stabilised form)
-// Phase 1: each CTA reduces U^T v and ||v||^2 over its rows (a warp takes
-// eight rows at a time, lanes split k; FP32 per warp, FP64 across warps); the
-// partials meet through distributed shared memory; every CTA forms the
-// coefficients; phase 3 writes its rows of out = alpha v + U coef (one thread
-// per row) and, optionally, partial sums of out . dotv that CTA 0 collects
-// into *dot_out.
+// Single-RHS Woodbury applies (App. C.2) and the randomized-powering steps of
+// Alg. 5, each in one launch of an 8-CTA cluster.  Every CTA owns a
+// contiguous slice of the b rows.
+//   phase 1  the CTA's rows of h (the input v, or h = sum_p part[p] + lambda a
+//            for a powering step), and partials of U^T h, ||h||^2 and a . h:
+//            a warp takes eight rows at a time, lanes split the r columns
+//   phase 2  the partials meet through distributed shared memory; every CTA
+//            forms the r coefficients of out = alpha h + U coef
+//   phase 3  the CTA's rows of out, eight rows per warp, the eight row sums
+//            reduced across the lanes with a transposing butterfly
+// Modes (see ApplyMode):
+//   kInvSqrtNormalised  out = P^{-1/2} v / ||v||
+//   kInv                out = P^{-1} v (stabilised form, through M)
+//   kInvUnit            out = P^{-1} h / sqrt(h^T P^{-1} h): with a_i =
+//                       P^{-1/2} v_i and v_i of unit norm, a_{i+1} = P^{-1/2}
+//                       v_{i+1} for v_{i+1} = P^{-1/2} H a_i / ||.|| (Alg. 5)
+//   kRayleighEta        lambda_hat = a . h = v^T P^{-1/2} H P^{-1/2} v, eta =
+//                       1 / lambda_hat (no output rows)
 // ---------------------------------------------------------------------------
-constexpr int kWbCluster = 8, kWbThreads = 256, kWbWarps = kWbThreads / 32, kWbRows = 8;
+constexpr int kWbCluster = 8, kWbThreads = 512, kWbWarps = kWbThreads / 32, kWbRows = 8;
 
 struct WbArgs {
   const float* U;
   int64_t b;
   int r;
-  const float* v;
   int mode;
+  const float* v;       // input rows (kInvSqrtNormalised, kInv)
+  const float* part;    // nsplit x b partial products (kInvUnit, kRayleighEta)
+  int nsplit;
+  const float* a;       // current powering iterate
+  float lam;
+  float* hbuf;          // b floats: h for phase 3 (kInvUnit)
   const double* keep;
-  const double* Lw;
+  const float* Minv;
+  const float* Gu;      // U^T U (FP32)
+  const double* S;
   const double* cis;
-  const DevScalars* sc;
+  DevScalars* sc;
   float* out;
-  const float* dotv;
-  double* alpha;    // [0] alpha used, [1] 1/||v|| in normalised mode
-  double* dot_out;  // sum(out . dotv) when dotv != NULL
 };
+
+// Sum over the 32 lanes of eight per-lane values x[0..7]; on return lane l
+// holds in x[0] the total of value l >> 2.
+__device__ __forceinline__ void transpose_sum8(float x[8], int lane) {
+  const unsigned full = 0xffffffffu;
+  {
+    const bool hi = lane & 16;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const float send = hi ? x[t] : x[t + 4];
+      const float keepv = hi ? x[t + 4] : x[t];
+      x[t] = keepv + __shfl_xor_sync(full, send, 16);
+    }
+  }
+  {
+    const bool hi = lane & 8;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const float send = hi ? x[t] : x[t + 2];
+      const float keepv = hi ? x[t + 2] : x[t];
+      x[t] = keepv + __shfl_xor_sync(full, send, 8);
+    }
+  }
+  {
+    const bool hi = lane & 4;
+    const float send = hi ? x[0] : x[1];
+    const float keepv = hi ? x[1] : x[0];
+    x[0] = keepv + __shfl_xor_sync(full, send, 4);
+  }
+  x[0] += __shfl_xor_sync(full, x[0], 2);
+  x[0] += __shfl_xor_sync(full, x[0], 1);
+}
+
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
 
 __global__ void __cluster_dims__(kWbCluster, 1, 1) __launch_bounds__(kWbThreads) k_wb_cluster(WbArgs a) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  __shared__ double part[kMaxRank + 2];        // this CTA's U^T v, ||v||^2, out . dotv
-  __shared__ double q[kMaxRank + 1];
+  __shared__ double part[kMaxRank + 2];        // this CTA's U^T h, ||h||^2, a . h
+  __shared__ double q[kMaxRank + 2];
   __shared__ float coef[kMaxRank];
   __shared__ float wtmp[kWbWarps][kMaxRank];
   __shared__ double red[33];
+  __shared__ double red2[33];
+  __shared__ double ys[kMaxRank];
+  __shared__ double zs[kMaxRank];
   __shared__ double s_alpha;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int r = a.r;
+  const int mode = a.mode;
+  const bool from_part = mode == kInvUnit || mode == kRayleighEta;
+  const bool need_u = mode != kRayleighEta;
   constexpr int KJ = kMaxRank / 32;
   const int64_t per = (a.b + kWbCluster - 1) / kWbCluster;
   const int64_t r0 = (int64_t)rank * per, r1 = min(a.b, r0 + per);
@@ -984,118 +1164,189 @@ __global__ void __cluster_dims__(kWbCluster, 1, 1) __launch_bounds__(kWbThreads)
   float acc[KJ];
 #pragma unroll
   for (int j = 0; j < KJ; ++j) acc[j] = 0.0f;
-  double vsq = 0.0;
+  // ||h||^2 and a . h: lane t < kWbRows sums row t of every group in FP32 (FP64
+  // arithmetic in this loop would cost far more than the loads on this GPU)
+  float hsq = 0.0f, ah = 0.0f;
   for (int64_t i0 = r0 + (int64_t)warp * kWbRows; i0 < r1; i0 += (int64_t)kWbWarps * kWbRows) {
-    float vi[kWbRows], u[kWbRows][KJ];
+    float hv[kWbRows];
+    if (from_part) {
+      float pv[kWbRows];
 #pragma unroll
-    for (int t = 0; t < kWbRows; ++t) {
-      const int64_t i = i0 + t;
-      const bool ok = i < r1;
-      vi[t] = ok ? a.v[i] : 0.0f;
+      for (int t = 0; t < kWbRows; ++t) pv[t] = 0.0f;
+      for (int p0 = 0; p0 < a.nsplit; p0 += 32) {
+        const int p = p0 + lane;
 #pragma unroll
-      for (int j = 0; j < KJ; ++j) {
-        const int k = lane + 32 * j;
-        u[t][j] = (ok && k < r) ? a.U[i * r + k] : 0.0f;
+        for (int t = 0; t < kWbRows; ++t) {
+          const int64_t i = i0 + t;
+          if (p < a.nsplit && i < r1) pv[t] += a.part[(int64_t)p * a.b + i];
+        }
+      }
+      transpose_sum8(pv, lane);
+#pragma unroll
+      for (int t = 0; t < kWbRows; ++t) {
+        const int64_t i = i0 + t;
+        const float ai = i < r1 ? a.a[i] : 0.0f;
+        hv[t] = i < r1 ? fmaf(a.lam, ai, __shfl_sync(0xffffffffu, pv[0], 4 * t)) : 0.0f;
+        if (lane == t) ah = fmaf(ai, hv[t], ah);
+      }
+      if (mode == kInvUnit && lane < kWbRows && i0 + lane < r1) {
+        float mine = hv[0];
+#pragma unroll
+        for (int t = 1; t < kWbRows; ++t) mine = (lane == t) ? hv[t] : mine;
+        a.hbuf[i0 + lane] = mine;
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < kWbRows; ++t) hv[t] = (i0 + t < r1) ? a.v[i0 + t] : 0.0f;
+    }
+    if (need_u) {
+      float u[kWbRows][KJ];
+#pragma unroll
+      for (int t = 0; t < kWbRows; ++t) {
+        const int64_t i = i0 + t;
+#pragma unroll
+        for (int j = 0; j < KJ; ++j) {
+          const int k = lane + 32 * j;
+          u[t][j] = (i < r1 && k < r) ? a.U[i * r + k] : 0.0f;
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < kWbRows; ++t) {
+#pragma unroll
+        for (int j = 0; j < KJ; ++j) acc[j] = fmaf(u[t][j], hv[t], acc[j]);
+        if (lane == t) hsq = fmaf(hv[t], hv[t], hsq);
       }
     }
+  }
+  if (need_u) {
 #pragma unroll
-    for (int t = 0; t < kWbRows; ++t) {
-#pragma unroll
-      for (int j = 0; j < KJ; ++j) acc[j] = fmaf(u[t][j], vi[t], acc[j]);
-      if (lane == 0) vsq += (double)vi[t] * (double)vi[t];
+    for (int j = 0; j < KJ; ++j) {
+      const int k = lane + 32 * j;
+      if (k < r) wtmp[warp][k] = acc[j];
     }
   }
-#pragma unroll
-  for (int j = 0; j < KJ; ++j) {
-    const int k = lane + 32 * j;
-    if (k < r) wtmp[warp][k] = acc[j];
+  const double hsq_t = block_sum((double)hsq, red);   // contains __syncthreads
+  const double ah_t = block_sum((double)ah, red2);
+  if (need_u) {
+    for (int k = threadIdx.x; k < r; k += kWbThreads) {
+      double t = 0.0;
+      for (int w = 0; w < kWbWarps; ++w) t += (double)wtmp[w][k];
+      part[k] = t;
+    }
   }
-  const double vsq_t = block_sum(vsq, red);   // contains __syncthreads
-  for (int k = threadIdx.x; k < r; k += kWbThreads) {
-    double t = 0.0;
-    for (int w = 0; w < kWbWarps; ++w) t += (double)wtmp[w][k];
-    part[k] = t;
+  if (threadIdx.x == 0) {
+    part[kMaxRank] = hsq_t;
+    part[kMaxRank + 1] = ah_t;
   }
-  if (threadIdx.x == 0) part[r] = vsq_t;
   cl.sync();
   // ---- phase 2: gather partials from every CTA of the cluster
-  for (int k = threadIdx.x; k <= r; k += kWbThreads) {
-    double t = 0.0;
+  for (int k = threadIdx.x; k < kMaxRank + 2; k += kWbThreads) {
+    if ((need_u && k < r) || k >= kMaxRank) {
+      double t = 0.0;
 #pragma unroll
-    for (int c = 0; c < kWbCluster; ++c) t += cl.map_shared_rank(part, c)[k];
-    q[k] = t;
+      for (int c = 0; c < kWbCluster; ++c) t += cl.map_shared_rank(part, c)[k];
+      q[k] = t;
+    }
   }
+  cluster_arrive();  // remote reads done; the matching wait precedes exit
   __syncthreads();
   const double rho = a.sc->rho;
-  if (a.mode == kInv) {
-    // y = Lw^{-T} Lw^{-1} (keep . q) by warp 0, lanes splitting the dot products
+  if (mode == kRayleighEta) {
+    if (rank == 0 && threadIdx.x == 0) {
+      DevScalars* sc = a.sc;
+      const double lam_hat = q[kMaxRank + 1];
+      sc->lam_hat = lam_hat;
+      double eta = (lam_hat > 0.0 && isfinite(lam_hat)) ? 1.0 / lam_hat : 0.0;
+      if (!(lam_hat > 0.0 && isfinite(lam_hat))) set_status(sc, ADASAP_ENUMERIC, 4);
+      if (sc->status != 0) eta = 0.0;
+      sc->eta = eta;
+    }
+    cluster_wait();
+    return;
+  }
+  if (mode == kInv) {
+    // coef = -keep . M (keep . q) / rho, one warp per row of M
+    for (int k = warp; k < r; k += kWbWarps) {
+      float t = 0.0f;
+      for (int j = lane; j < r; j += 32) t = fmaf(a.Minv[k * r + j], (float)(a.keep[j] * q[j]), t);
+      t = warp_sum(t);
+      if (lane == 0) coef[k] = (float)(-a.keep[k] * (double)t / rho);
+    }
+    if (threadIdx.x == 0) s_alpha = 1.0 / rho;
+  } else if (mode == kInvUnit) {
+    // The two inverse-square-root applies of Alg. 5 in closed form, exact for any U
+    // (P^{-1/2} = rho^{-1/2} I + U diag(cis) U^T, G = U^T U, t = U^T h, y = cis . t, z = G y):
+    //   w = P^{-1/2} h = rho^{-1/2} h + U y,  ||w||^2 = ||h||^2 / rho + 2 rho^{-1/2} t.y + y.z
+    //   P^{-1/2} w = rho^{-1} h + U (rho^{-1/2} y + cis . (rho^{-1/2} t + z))
+    const double irs = 1.0 / sqrt(rho);
+    for (int k = threadIdx.x; k < r; k += kWbThreads) ys[k] = a.cis[k] * q[k];
+    __syncthreads();
+    for (int k = warp; k < r; k += kWbWarps) {
+      float t = 0.0f;
+      for (int j = lane; j < r; j += 32) t = fmaf(a.Gu[k * r + j], (float)ys[j], t);
+      t = warp_sum(t);
+      if (lane == 0) zs[k] = (double)t;
+    }
+    __syncthreads();
     if (warp == 0) {
-      for (int i = 0; i < r; ++i) {
-        double pt = 0.0;
-        for (int k = lane; k < i; k += 32) pt += a.Lw[i * r + k] * q[k];
-        pt = warp_sum(pt);
-        if (lane == 0) q[i] = (a.keep[i] * q[i] - pt) / a.Lw[i * r + i];
-        __syncwarp();
-      }
-      for (int i = r - 1; i >= 0; --i) {
-        double pt = 0.0;
-        for (int k = i + 1 + lane; k < r; k += 32) pt += a.Lw[k * r + i] * q[k];
-        pt = warp_sum(pt);
-        if (lane == 0) q[i] = (q[i] - pt) / a.Lw[i * r + i];
-        __syncwarp();
+      double acc2 = 0.0;
+      for (int k = lane; k < r; k += 32) acc2 += 2.0 * irs * q[k] * ys[k] + ys[k] * zs[k];
+      acc2 = warp_sum(acc2);
+      if (lane == 0) {
+        const double w2 = q[kMaxRank] / rho + acc2;
+        red[32] = w2 > 0.0 ? 1.0 / sqrt(w2) : 0.0;
       }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < r; k += kWbThreads) coef[k] = (float)(-a.keep[k] * q[k] / rho);
-    if (threadIdx.x == 0) s_alpha = 1.0 / rho;
+    const double scale = red[32];
+    for (int k = threadIdx.x; k < r; k += kWbThreads)
+      coef[k] = (float)(scale * (irs * ys[k] + a.cis[k] * (irs * q[k] + zs[k])));
+    if (threadIdx.x == 0) s_alpha = scale / rho;
   } else {
-    const double scale = (a.mode == kInvSqrtNormalised) ? (q[r] > 0.0 ? 1.0 / sqrt(q[r]) : 0.0) : 1.0;
+    const double scale = q[kMaxRank] > 0.0 ? 1.0 / sqrt(q[kMaxRank]) : 0.0;
     for (int k = threadIdx.x; k < r; k += kWbThreads) coef[k] = (float)(scale * q[k] * a.cis[k]);
-    if (threadIdx.x == 0) {
-      s_alpha = scale / sqrt(rho);
-      if (rank == 0) {
-        a.alpha[0] = s_alpha;
-        if (a.mode == kInvSqrtNormalised) a.alpha[1] = scale;
-      }
-    }
+    if (threadIdx.x == 0) s_alpha = scale / sqrt(rho);
   }
   __syncthreads();
   const float al = (float)s_alpha;
-  // ---- phase 3: out rows, one thread per row (independent loads)
-  double dt = 0.0;
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += kWbThreads) {
-    const float* ui = a.U + i * r;
-    float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f, t3 = 0.0f;
-    int k = 0;
-    for (; k + 4 <= r; k += 4) {
-      t0 = fmaf(ui[k], coef[k], t0);
-      t1 = fmaf(ui[k + 1], coef[k + 1], t1);
-      t2 = fmaf(ui[k + 2], coef[k + 2], t2);
-      t3 = fmaf(ui[k + 3], coef[k + 3], t3);
+  float cf[KJ];
+#pragma unroll
+  for (int j = 0; j < KJ; ++j) cf[j] = (lane + 32 * j < r) ? coef[lane + 32 * j] : 0.0f;
+  const float* hsrc = from_part ? a.hbuf : a.v;
+  // ---- phase 3: out = alpha h + U coef over the CTA's rows (same row-to-warp map as phase 1)
+  for (int64_t i0 = r0 + (int64_t)warp * kWbRows; i0 < r1; i0 += (int64_t)kWbWarps * kWbRows) {
+    float x[kWbRows];
+#pragma unroll
+    for (int t = 0; t < kWbRows; ++t) {
+      const int64_t i = i0 + t;
+      float sacc = 0.0f;
+#pragma unroll
+      for (int j = 0; j < KJ; ++j) {
+        const int k = lane + 32 * j;
+        sacc = fmaf((i < r1 && k < r) ? a.U[i * r + k] : 0.0f, cf[j], sacc);
+      }
+      x[t] = sacc;
     }
-    for (; k < r; ++k) t0 = fmaf(ui[k], coef[k], t0);
-    const float o = fmaf(al, a.v[i], (t0 + t1) + (t2 + t3));
-    a.out[i] = o;
-    if (a.dotv) dt += (double)o * (double)a.dotv[i];
+    transpose_sum8(x, lane);
+    const int64_t i = i0 + (lane >> 2);
+    if ((lane & 3) == 0 && i < r1) a.out[i] = fmaf(al, hsrc[i], x[0]);
   }
-  if (a.dotv) {
-    const double dtt = block_sum(dt, red);
-    if (threadIdx.x == 0) part[kMaxRank + 1] = dtt;
-  }
-  cl.sync();
-  if (a.dotv && rank == 0 && threadIdx.x == 0) {
-    double t = 0.0;
-    for (int c = 0; c < kWbCluster; ++c) t += cl.map_shared_rank(part, c)[kMaxRank + 1];
-    *a.dot_out = t;
-  }
-  cl.sync();  // no CTA leaves while rank 0 may still read its shared memory
+  cluster_wait();
 }
 
-cudaError_t launch_wb_cluster(CoreBufs& cb, int mode, const float* v, float* out, const float* dotv, DevScalars* sc,
-                              cudaStream_t st) {
-  WbArgs a;
-  a.U = cb.U; a.b = cb.b; a.r = cb.r; a.v = v; a.mode = mode; a.keep = cb.keep; a.Lw = cb.Lw; a.cis = cb.cis;
-  a.sc = sc; a.out = out; a.dotv = dotv; a.alpha = cb.alpha; a.dot_out = cb.dot_part;
+cudaError_t launch_wb_cluster(CoreBufs& cb, int mode, const float* v, float* out, DevScalars* sc, cudaStream_t st) {
+  WbArgs a{};
+  a.U = cb.U; a.b = cb.b; a.r = cb.r; a.mode = mode; a.v = v; a.keep = cb.keep; a.Minv = cb.Minv; a.Gu = cb.Gu; a.S = cb.S;
+  a.cis = cb.cis; a.sc = sc; a.out = out;
+  k_wb_cluster<<<kWbCluster, kWbThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_power_step(CoreBufs& cb, int mode, const float* part, int nsplit, float lam, const float* acur,
+                              float* hbuf, float* anext, DevScalars* sc, cudaStream_t st) {
+  WbArgs a{};
+  a.U = cb.U; a.b = cb.b; a.r = cb.r; a.mode = mode; a.part = part; a.nsplit = nsplit; a.a = acur; a.lam = lam;
+  a.hbuf = hbuf; a.keep = cb.keep; a.Minv = cb.Minv; a.Gu = cb.Gu; a.S = cb.S; a.cis = cb.cis; a.sc = sc; a.out = anext;
   k_wb_cluster<<<kWbCluster, kWbThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
@@ -1110,7 +1361,7 @@ cudaError_t core_init() {
   if ((e = cudaFuncSetAttribute(k_chol_plain<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-  if ((e = cudaFuncSetAttribute(k_wchol, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_wfactor, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_wcoef, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_wapply, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   return cudaSuccess;

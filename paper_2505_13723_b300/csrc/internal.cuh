@@ -67,14 +67,18 @@ cudaError_t launch_index32(const int64_t* in, int64_t m, int64_t n, int* out, cu
 int tc_kp(int d);
 int64_t tc_npad(int64_t n);
 cudaError_t tc_init();
-int tc_nsplit(int64_t m, int64_t ncols);
+// Resident CTAs of the tensor-core kernel (one per SM) and its column split for
+// an m x ncols product spread over min(slots, max_ctas) persistent CTAs (0: all).
+int tc_slots();
+int tc_nsplit(int64_t m, int64_t ncols, int max_ctas = 0);
 // Split (hi, lo) column operands in the MMA layout for X' (or rows gidx of X').
 cudaError_t launch_build_tc(const float* X, const float* q, const int* gidx, int64_t n, int d, int dp, float* hi,
                             float* lo, cudaStream_t st);
 // part[p][i] = sigma2 * sum_{j in split p} k(x'_{row i}, x'_j) w[j] (s = 1).
 cudaError_t launch_rows_tc(int kern, int d, const float* xr, const float* qr, const int* ridx, int64_t m, int dp,
                            const float* bhi, const float* blo, int64_t ncols, int self_mode, const float* w,
-                           int64_t ldw, float* part, int nsplit, float sigma2, int* err, cudaStream_t st);
+                           int64_t ldw, float* part, int nsplit, float sigma2, int* err, cudaStream_t st,
+                           int max_ctas = 0);
 
 // ---- sampler (Philox4x32-10; definitions in sampler.cu) -------------------------
 cudaError_t launch_sample_block(uint64_t seed, const long long* t_dev, int64_t t_host, int64_t n,
@@ -104,7 +108,8 @@ struct CoreBufs {
   double* T;          // r x r  U = Y_nu T
   double* S;          // r      Nystrom eigenvalues (descending)
   double* keep;       // r      1 if S_i > 0 else 0
-  double* Lw;         // r x r  Cholesky of rho S^-1 + U^T U
+  float* Minv;        // r x r  (rho S^-1 + U^T U)^-1 on the kept pairs
+  float* Gu;          // r x r  U^T U
   float* U;           // b x r
   double* utv_part;   // [utv_chunks][r][s]
   int utv_chunks;
@@ -120,20 +125,27 @@ int utv_chunks_for(int64_t b);
 cudaError_t launch_gram(const float* A1, int64_t ld1, int c1, const float* A2, int64_t ld2, int c2,
                         int64_t m, double* part, int chunks, double* G, bool exact, cudaStream_t st);
 cudaError_t launch_orthonormalize(CoreBufs& cb, float* Om, float* tmp, DevScalars* sc, cudaStream_t st);
+// Gram matrices of the sketch (whole-GPU launches): G = [Omega | Y]^T [Omega | Y], Gyy = Y^T Y (exact products)
+cudaError_t launch_nystrom_grams(CoreBufs& cb, const float* Om, const float* Ysk, cudaStream_t st);
+// Alg. 4 from the Gram matrices on: Cholesky, eigenpairs, S, rho, U (mostly single-CTA launches)
 cudaError_t launch_nystrom_core(CoreBufs& cb, double eps, double lam, DevScalars* sc,
                                 const float* Om, const float* Ysk, cudaStream_t st);
 cudaError_t launch_woodbury_factor(CoreBufs& cb, double lam, DevScalars* sc, cudaStream_t st);
 // P^{-1/2}-type or P^{-1}-type apply of App. C.2 in three launches:
 //   utv: part = U^T v (per chunk); coef: small FP64 work; apply: out = alpha v + U coef.
-enum ApplyMode { kInvSqrt = 0, kInvSqrtNormalised = 1, kInv = 2 };
+// kInvUnit and kRayleighEta are the powering steps of Alg. 5 (cluster kernel only).
+enum ApplyMode { kInvSqrt = 0, kInvSqrtNormalised = 1, kInv = 2, kInvUnit = 3, kRayleighEta = 4 };
 cudaError_t launch_woodbury_apply(CoreBufs& cb, int mode, const float* v, int s, float* out,
                                   bool want_sq, bool want_dot, const float* dotv, DevScalars* sc,
                                   cudaStream_t st);
 cudaError_t launch_set_eta(CoreBufs& cb, DevScalars* sc, int identity, cudaStream_t st);
-// One single-RHS Woodbury apply in one 8-CTA cluster launch.  With dotv,
-// writes sum(out . dotv) to cb.dot_part[0].
-cudaError_t launch_wb_cluster(CoreBufs& cb, int mode, const float* v, float* out, const float* dotv, DevScalars* sc,
-                              cudaStream_t st);
+// One single-RHS Woodbury apply (kInvSqrtNormalised or kInv) in one 8-CTA cluster launch.
+cudaError_t launch_wb_cluster(CoreBufs& cb, int mode, const float* v, float* out, DevScalars* sc, cudaStream_t st);
+// One powering step of Alg. 5 on h = sum_p part[p] + lam * acur (nsplit x b partials):
+//   kInvUnit:     anext = P^{-1} h / sqrt(h^T P^{-1} h)  (h kept in hbuf)
+//   kRayleighEta: sc->lam_hat = acur . h, sc->eta = 1 / lam_hat
+cudaError_t launch_power_step(CoreBufs& cb, int mode, const float* part, int nsplit, float lam, const float* acur,
+                              float* hbuf, float* anext, DevScalars* sc, cudaStream_t st);
 cudaError_t launch_nesterov(float* W, float* V, float* Z, int64_t count, float beta, float alpha,
                             int literal, cudaStream_t st);
 cudaError_t launch_scatter(float* W, float* V, float* Z, const int* B, int64_t b, int s,

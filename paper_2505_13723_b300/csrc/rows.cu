@@ -413,7 +413,7 @@ __global__ void k_reduce(const float* __restrict__ part, int nsplit, int64_t m, 
     }
     const float v = (float)acc;
     out[i * ldo + c] = v;
-    sq += (double)v * (double)v;
+    if (blocksq) sq += (double)v * (double)v;
   }
   if (blocksq) {
     const double tot = block_sum(sq, red);

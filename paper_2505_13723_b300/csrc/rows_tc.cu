@@ -154,6 +154,7 @@ struct TcArgs {
   int wvec;          // w is 16-byte aligned with ldw == 1: float4 loads allowed
   float* part;       // nsplit x m
   int64_t cps;       // columns per split (multiple of 128)
+  int nsplit;
   float sigma2;
   int* err;          // set to 1 on a wait timeout
 };
@@ -178,12 +179,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(TcArgs a) {
   float* red = reinterpret_cast<float*>(tslot + 4);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t row0 = (int64_t)blockIdx.x * kTcM;
-  const int64_t c0 = (int64_t)blockIdx.y * a.cps;
-  const int64_t c1 = min(a.ncols, c0 + a.cps);
-  const int ntiles = c1 > c0 ? (int)((c1 - c0 + kTcN - 1) / kTcN) : 0;
+  const int64_t rtiles = (a.m + kTcM - 1) / kTcM;
+  const int64_t nitems = rtiles * a.nsplit;
 
-  // ---- set-up: barriers, row operands (hi/lo split), TMEM ------------------
+  // ---- set-up once per CTA: barriers, TMEM --------------------------------------
   if (tid == 0) {
     for (int i = 0; i < 2; ++i) {
       mbar_init(&full[i], 1);
@@ -195,34 +194,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(TcArgs a) {
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (tid < kTcM) {
-    const int64_t ri = row0 + tid;
-    float av[KP];
-#pragma unroll
-    for (int k = 0; k < KP; ++k) av[k] = 0.0f;
-    bool ok = ri < a.m;
-    int64_t src = ri;
-    if (ok && a.ridx) {
-      const int id = a.ridx[ri];
-      ok = id >= 0;
-      src = id;
-    }
-    if (ok) {
-      for (int k = 0; k < a.d; ++k) av[k] = -2.0f * a.xr[src * a.dp + k];
-      av[a.d] = a.qr[src];
-    } else {
-      av[a.d] = 1e20f;  // padded or invalid row: u is huge, the kernel value 0
-    }
-    av[a.d + 1] = 1.0f;
-#pragma unroll
-    for (int k = 0; k < KP; ++k) {
-      const float hi = tf32_round(av[k]);
-      const float lo = tf32_round(av[k] - hi);
-      sAhi[tc_off<KP>(tid, k)] = hi;
-      sAlo[tc_off<KP>(tid, k)] = lo;
-    }
-  }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(kTmemCols)
@@ -234,147 +205,199 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(TcArgs a) {
   tc_fence_after();
   const uint32_t tbase = *tslot;
 
-  if (warp == 0) {
-    // ---- producer --------------------------------------------------------------
-    if (lane == 0) {
-      int issued = 0;
-      for (int t = 0; t < ntiles; ++t) {
-        const int st = t & 1;
-        const uint32_t ph = (uint32_t)(t >> 1) & 1u;
-        if (!mbar_wait(&empty[st], ph ^ 1u, abort_flag)) {
-          *abort_flag = 1;
-          break;
-        }
-        mbar_arrive_expect_tx(&full[st], 2u * OPF * sizeof(float));
-        const int64_t off = (c0 + (int64_t)t * kTcN) * KP;
-        bulk_g2s(sB + (st * 2 + 0) * OPF, a.bhi + off, OPF * sizeof(float), &full[st]);
-        bulk_g2s(sB + (st * 2 + 1) * OPF, a.blo + off, OPF * sizeof(float), &full[st]);
-        issued = t + 1;
+  // Items (row tile, column split) are taken in grid-stride order with the row
+  // tile varying fastest, so the CTAs running at one time share column tiles in
+  // L2.  The pipeline phases run on across items (gt counts this CTA's tiles).
+  uint32_t gt = 0, ndrain = 0;
+  for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int64_t rtile = item % rtiles, split = item / rtiles;
+    const int64_t row0 = rtile * kTcM;
+    const int64_t c0 = split * a.cps;
+    const int64_t c1 = min(a.ncols, c0 + a.cps);
+    // after an abort the remaining items only write NaN partials (the flag is read
+    // after a block barrier, so every role agrees)
+    const int ntiles = (c1 > c0 && !*abort_flag) ? (int)((c1 - c0 + kTcN - 1) / kTcN) : 0;
+    // row operands (hi/lo split) of this item's row tile
+    if (tid < kTcM) {
+      const int64_t ri = row0 + tid;
+      float av[KP];
+#pragma unroll
+      for (int k = 0; k < KP; ++k) av[k] = 0.0f;
+      bool ok = ri < a.m;
+      int64_t src = ri;
+      if (ok && a.ridx) {
+        const int id = a.ridx[ri];
+        ok = id >= 0;
+        src = id;
       }
-      if (*abort_flag) {
-        // our copies still write shared memory: wait (bounded) for the last ones
-        for (int t = max(0, issued - 2); t < issued; ++t) {
-          const int st = t & 1;
-          const uint32_t ph = (uint32_t)(t >> 1) & 1u;
-          for (uint32_t it = 0; it < kWaitPolls && !mbar_try_wait(&full[st], ph); ++it) {
+      if (ok) {
+        for (int k = 0; k < a.d; ++k) av[k] = -2.0f * a.xr[src * a.dp + k];
+        av[a.d] = a.qr[src];
+      } else {
+        av[a.d] = 1e20f;  // padded or invalid row: u is huge, the kernel value 0
+      }
+      av[a.d + 1] = 1.0f;
+#pragma unroll
+      for (int k = 0; k < KP; ++k) {
+        const float hi = tf32_round(av[k]);
+        const float lo = tf32_round(av[k] - hi);
+        sAhi[tc_off<KP>(tid, k)] = hi;
+        sAlo[tc_off<KP>(tid, k)] = lo;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+
+    if (warp == 0) {
+      // ---- producer --------------------------------------------------------------
+      if (lane == 0) {
+        int issued = 0;
+        for (int t = 0; t < ntiles; ++t) {
+          const uint32_t g = gt + (uint32_t)t;
+          const int st = g & 1;
+          const uint32_t ph = (g >> 1) & 1u;
+          if (!mbar_wait(&empty[st], ph ^ 1u, abort_flag)) {
+            *abort_flag = 1;
+            break;
+          }
+          mbar_arrive_expect_tx(&full[st], 2u * OPF * sizeof(float));
+          const int64_t off = (c0 + (int64_t)t * kTcN) * KP;
+          bulk_g2s(sB + (st * 2 + 0) * OPF, a.bhi + off, OPF * sizeof(float), &full[st]);
+          bulk_g2s(sB + (st * 2 + 1) * OPF, a.blo + off, OPF * sizeof(float), &full[st]);
+          issued = t + 1;
+        }
+        if (*abort_flag) {
+          // our copies still write shared memory: wait (bounded) for the last ones
+          for (int t = max(0, issued - 2); t < issued; ++t) {
+            const uint32_t g = gt + (uint32_t)t;
+            const int st = g & 1;
+            const uint32_t ph = (g >> 1) & 1u;
+            for (uint32_t it = 0; it < kWaitPolls && !mbar_try_wait(&full[st], ph); ++it) {
+            }
           }
         }
       }
-    }
-  } else if (warp == 1) {
-    // ---- MMA issuer -------------------------------------------------------------
-    if (lane == 0) {
-      int issued = 0;
+    } else if (warp == 1) {
+      // ---- MMA issuer -------------------------------------------------------------
+      if (lane == 0) {
+        int issued = 0;
+        for (int t = 0; t < ntiles; ++t) {
+          const uint32_t g = gt + (uint32_t)t;
+          const int st = g & 1, buf = g & 1;
+          const uint32_t ph = (g >> 1) & 1u;
+          if (!mbar_wait(&full[st], ph, abort_flag) || !mbar_wait(&tempty[buf], ph ^ 1u, abort_flag)) {
+            *abort_flag = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t dt = tbase + (uint32_t)(buf * kTcN);
+          const uint32_t a_hi = smem_u32(sAhi), a_lo = smem_u32(sAlo);
+          const uint32_t b_hi = smem_u32(sB + (st * 2 + 0) * OPF), b_lo = smem_u32(sB + (st * 2 + 1) * OPF);
+          uint32_t acc = 0;
+#pragma unroll
+          for (int pass = 0; pass < 3; ++pass) {
+            const uint32_t A = pass == 2 ? a_lo : a_hi;
+            const uint32_t B = pass == 1 ? b_lo : b_hi;
+#pragma unroll
+            for (int ks = 0; ks < KP / 8; ++ks) {
+              tc_mma_tf32(dt, smem_desc(A + 256u * ks, 128u, 32u * KP), smem_desc(B + 256u * ks, 128u, 32u * KP),
+                          kIdescTf32, acc);
+              acc = 1;
+            }
+          }
+          tc_commit(&empty[st]);
+          tc_commit(&tfull[buf]);
+          issued = t + 1;
+        }
+        if (issued > 0) {
+          // all MMAs of this item complete before the row operands are rewritten
+          // (next item) or TMEM is released (end)
+          tc_commit(drain);
+          for (uint32_t it = 0; it < kWaitPolls && !mbar_try_wait(drain, ndrain & 1u); ++it) {
+          }
+          ++ndrain;
+        }
+      }
+    } else if (warp >= 4) {
+      // ---- epilogue ------------------------------------------------------------------
+      const int g = (warp - 4) >> 2, qd = warp & 3;
+      const int rl = qd * 32 + lane;
+      const int64_t ri = row0 + rl;
+      int64_t gi = -1;
+      bool bad = false;
+      if (ri < a.m) {
+        const int64_t src = a.ridx ? (int64_t)a.ridx[ri] : ri;
+        bad = src < 0;
+        if (a.self_mode) gi = src;
+      }
+      float acc = 0.0f, cmp = 0.0f;
       for (int t = 0; t < ntiles; ++t) {
-        const int st = t & 1, buf = t & 1;
-        const uint32_t ph = (uint32_t)(t >> 1) & 1u;
-        if (!mbar_wait(&full[st], ph, abort_flag) || !mbar_wait(&tempty[buf], ph ^ 1u, abort_flag)) {
+        const uint32_t gg = gt + (uint32_t)t;
+        const int buf = gg & 1;
+        const uint32_t ph = (gg >> 1) & 1u;
+        if (!mbar_wait(&tfull[buf], ph, abort_flag)) {
           *abort_flag = 1;
           break;
         }
         tc_fence_after();
-        const uint32_t dt = tbase + (uint32_t)(buf * kTcN);
-        const uint32_t a_hi = smem_u32(sAhi), a_lo = smem_u32(sAlo);
-        const uint32_t b_hi = smem_u32(sB + (st * 2 + 0) * OPF), b_lo = smem_u32(sB + (st * 2 + 1) * OPF);
-        uint32_t acc = 0;
+        uint32_t u0[32], u1[32];
+        const uint32_t taddr = tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)(buf * kTcN + g * 64);
+        TMEM_LD32(taddr, u0);
+        TMEM_LD32(taddr + 32u, u1);
+        TMEM_WAIT32(u0);
+        TMEM_WAIT32(u1);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
+        const int64_t jb = c0 + (int64_t)t * kTcN + g * 64;
+        float wv[64];
+        if (jb + 64 <= c1 && a.wvec) {
+          const float4* w4 = reinterpret_cast<const float4*>(a.w + jb);
 #pragma unroll
-        for (int pass = 0; pass < 3; ++pass) {
-          const uint32_t A = pass == 2 ? a_lo : a_hi;
-          const uint32_t B = pass == 1 ? b_lo : b_hi;
+          for (int i = 0; i < 16; ++i) {
+            const float4 x = __ldg(w4 + i);
+            wv[4 * i] = x.x; wv[4 * i + 1] = x.y; wv[4 * i + 2] = x.z; wv[4 * i + 3] = x.w;
+          }
+        } else {
 #pragma unroll
-          for (int ks = 0; ks < KP / 8; ++ks) {
-            tc_mma_tf32(dt, smem_desc(A + 256u * ks, 128u, 32u * KP), smem_desc(B + 256u * ks, 128u, 32u * KP),
-                        kIdescTf32, acc);
-            acc = 1;
+          for (int i = 0; i < 64; ++i) wv[i] = (jb + i < c1) ? __ldg(a.w + (jb + i) * a.ldw) : 0.0f;
+        }
+        const bool self_here = gi >= jb && gi < jb + 64;
+        float tacc = 0.0f;
+        if (__any_sync(0xffffffffu, self_here)) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const float ua = (jb + i == gi) ? 0.0f : fmaxf(__uint_as_float(u0[i]), 0.0f);
+            const float ub = (jb + 32 + i == gi) ? 0.0f : fmaxf(__uint_as_float(u1[i]), 0.0f);
+            tacc = fmaf(kval<KERN>(ua), wv[i], tacc);
+            tacc = fmaf(kval<KERN>(ub), wv[32 + i], tacc);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            tacc = fmaf(kval<KERN>(fmaxf(__uint_as_float(u0[i]), 0.0f)), wv[i], tacc);
+            tacc = fmaf(kval<KERN>(fmaxf(__uint_as_float(u1[i]), 0.0f)), wv[32 + i], tacc);
           }
         }
-        tc_commit(&empty[st]);
-        tc_commit(&tfull[buf]);
-        issued = t + 1;
+        const float y = tacc - cmp;
+        const float tt = acc + y;
+        cmp = (tt - acc) - y;
+        acc = tt;
       }
-      if (issued > 0) {
-        // all MMAs of this thread complete before TMEM is released
-        tc_commit(drain);
-        for (uint32_t it = 0; it < kWaitPolls && !mbar_try_wait(drain, 0); ++it) {
-        }
+      // combine the two warpgroups' column halves
+      if (g == 1) red[rl] = acc - cmp;
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      if (g == 0 && ri < a.m) {
+        const float tot = (acc - cmp) + red[rl];
+        a.part[split * a.m + ri] = (bad || *abort_flag) ? __int_as_float(0x7fc00000) : a.sigma2 * tot;
       }
     }
-  } else if (warp >= 4) {
-    // ---- epilogue ------------------------------------------------------------------
-    const int g = (warp - 4) >> 2, qd = warp & 3;
-    const int rl = qd * 32 + lane;
-    const int64_t ri = row0 + rl;
-    int64_t gi = -1;
-    bool bad = false;
-    if (ri < a.m) {
-      const int64_t src = a.ridx ? (int64_t)a.ridx[ri] : ri;
-      bad = src < 0;
-      if (a.self_mode) gi = src;
-    }
-    float acc = 0.0f, cmp = 0.0f;
-    for (int t = 0; t < ntiles; ++t) {
-      const int buf = t & 1;
-      const uint32_t ph = (uint32_t)(t >> 1) & 1u;
-      if (!mbar_wait(&tfull[buf], ph, abort_flag)) {
-        *abort_flag = 1;
-        break;
-      }
-      tc_fence_after();
-      uint32_t u0[32], u1[32];
-      const uint32_t taddr = tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)(buf * kTcN + g * 64);
-      TMEM_LD32(taddr, u0);
-      TMEM_LD32(taddr + 32u, u1);
-      TMEM_WAIT32(u0);
-      TMEM_WAIT32(u1);
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[buf]);
-      const int64_t jb = c0 + (int64_t)t * kTcN + g * 64;
-      float wv[64];
-      if (jb + 64 <= c1 && a.wvec) {
-        const float4* w4 = reinterpret_cast<const float4*>(a.w + jb);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const float4 x = __ldg(w4 + i);
-          wv[4 * i] = x.x; wv[4 * i + 1] = x.y; wv[4 * i + 2] = x.z; wv[4 * i + 3] = x.w;
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < 64; ++i) wv[i] = (jb + i < c1) ? __ldg(a.w + (jb + i) * a.ldw) : 0.0f;
-      }
-      const bool self_here = gi >= jb && gi < jb + 64;
-      float tacc = 0.0f;
-      if (__any_sync(0xffffffffu, self_here)) {
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const float ua = (jb + i == gi) ? 0.0f : fmaxf(__uint_as_float(u0[i]), 0.0f);
-          const float ub = (jb + 32 + i == gi) ? 0.0f : fmaxf(__uint_as_float(u1[i]), 0.0f);
-          tacc = fmaf(kval<KERN>(ua), wv[i], tacc);
-          tacc = fmaf(kval<KERN>(ub), wv[32 + i], tacc);
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          tacc = fmaf(kval<KERN>(fmaxf(__uint_as_float(u0[i]), 0.0f)), wv[i], tacc);
-          tacc = fmaf(kval<KERN>(fmaxf(__uint_as_float(u1[i]), 0.0f)), wv[32 + i], tacc);
-        }
-      }
-      const float y = tacc - cmp;
-      const float tt = acc + y;
-      cmp = (tt - acc) - y;
-      acc = tt;
-    }
-    // combine the two warpgroups' column halves
-    if (g == 1) red[rl] = acc - cmp;
-    asm volatile("bar.sync 1, 256;" ::: "memory");
-    if (g == 0 && ri < a.m) {
-      const float tot = (acc - cmp) + red[rl];
-      a.part[(int64_t)blockIdx.y * a.m + ri] =
-          (bad || *abort_flag) ? __int_as_float(0x7fc00000) : a.sigma2 * tot;
-    }
+    gt += (uint32_t)ntiles;
+    // item boundary: the row operands and both TMEM buffers are free again
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
   }
-  tc_fence_before();
-  __syncthreads();
   if (warp == 0 && lane == 0 && *abort_flag && a.err) atomicExch(a.err, 1);
   if (warp == 1) {
     tc_fence_after();
@@ -446,23 +469,27 @@ cudaError_t tc_init() {
   return cudaSuccess;
 }
 
-// Column splits: whole 128-column tiles, and a CTA count close to a whole
-// number of waves of the resident slots.
-int tc_nsplit(int64_t m, int64_t ncols) {
+// Column splits: whole 128-column tiles; items (row tile x split) are spread
+// over min(slots, max_ctas) persistent CTAs.
+int tc_slots() { return g_tc_slots > 0 ? g_tc_slots : 148; }
+
+int tc_nsplit(int64_t m, int64_t ncols, int max_ctas) {
   const int64_t rt = (m + kTcM - 1) / kTcM;
   const int64_t tiles = (ncols + kTcN - 1) / kTcN;
-  const int64_t slots = g_tc_slots > 0 ? g_tc_slots : 148;
+  const int64_t slots = (max_ctas > 0 && max_ctas < tc_slots()) ? max_ctas : tc_slots();
+  // An item costs its column tiles plus a start-up of about two tiles (row
+  // operands, pipeline fill and drain); minimise items per CTA x item cost.
+  constexpr double kStartupTiles = 2.0;
   int64_t best = 1;
-  double best_eff = -1.0;
+  double best_cost = 1e300;
   for (int64_t ns = 1; ns <= std::min<int64_t>(tiles, 4096); ++ns) {
     const int64_t tot = rt * ns;
     const int64_t waves = (tot + slots - 1) / slots;
     if (waves > 64) break;
-    // tiles per split is a ceiling, so the effective work per CTA is rounded up
     const int64_t tps = (tiles + ns - 1) / ns;
-    const double eff = (double)(rt * tiles) / (double)(waves * slots * tps);
-    if (eff > best_eff + 1e-9) {
-      best_eff = eff;
+    const double cost = (double)waves * ((double)tps + kStartupTiles);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
       best = ns;
     }
   }
@@ -470,15 +497,15 @@ int tc_nsplit(int64_t m, int64_t ncols) {
 }
 
 template <int KERN, int KP>
-static cudaError_t launch_tc_k(const TcArgs& a, int nsplit, cudaStream_t st) {
-  const dim3 grid((unsigned)((a.m + kTcM - 1) / kTcM), (unsigned)nsplit);
-  k_rows_tc<KERN, KP><<<grid, kTcThreads, std::max<size_t>(TcSmem<KP>::bytes, 80 * 1024), st>>>(a);
+static cudaError_t launch_tc_k(const TcArgs& a, int ctas, cudaStream_t st) {
+  k_rows_tc<KERN, KP><<<ctas, kTcThreads, std::max<size_t>(TcSmem<KP>::bytes, 80 * 1024), st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rows_tc(int kern, int d, const float* xr, const float* qr, const int* ridx, int64_t m, int dp,
                            const float* bhi, const float* blo, int64_t ncols, int self_mode, const float* w,
-                           int64_t ldw, float* part, int nsplit, float sigma2, int* err, cudaStream_t st) {
+                           int64_t ldw, float* part, int nsplit, float sigma2, int* err, cudaStream_t st,
+                           int max_ctas) {
   if (m <= 0 || ncols <= 0) return cudaSuccess;
   TcArgs a;
   a.xr = xr; a.qr = qr; a.ridx = ridx; a.m = m; a.dp = dp; a.d = d;
@@ -487,16 +514,20 @@ cudaError_t launch_rows_tc(int kern, int d, const float* xr, const float* qr, co
   a.wvec = (ldw == 1 && (reinterpret_cast<uintptr_t>(w) & 15u) == 0) ? 1 : 0;
   const int64_t tiles = (ncols + kTcN - 1) / kTcN;
   a.cps = (tiles + nsplit - 1) / nsplit * kTcN;
+  a.nsplit = nsplit;
+  const int64_t nitems = (m + kTcM - 1) / kTcM * (int64_t)nsplit;
+  const int slots = (max_ctas > 0 && max_ctas < tc_slots()) ? max_ctas : tc_slots();
+  const int ctas = (int)std::min<int64_t>(nitems, slots);
   const int kp = tc_kp(d);
   if (kp == 16) {
-    if (kern == 0) return launch_tc_k<0, 16>(a, nsplit, st);
-    if (kern == 1) return launch_tc_k<1, 16>(a, nsplit, st);
-    return launch_tc_k<2, 16>(a, nsplit, st);
+    if (kern == 0) return launch_tc_k<0, 16>(a, ctas, st);
+    if (kern == 1) return launch_tc_k<1, 16>(a, ctas, st);
+    return launch_tc_k<2, 16>(a, ctas, st);
   }
   if (kp == 32) {
-    if (kern == 0) return launch_tc_k<0, 32>(a, nsplit, st);
-    if (kern == 1) return launch_tc_k<1, 32>(a, nsplit, st);
-    return launch_tc_k<2, 32>(a, nsplit, st);
+    if (kern == 0) return launch_tc_k<0, 32>(a, ctas, st);
+    if (kern == 1) return launch_tc_k<1, 32>(a, ctas, st);
+    return launch_tc_k<2, 32>(a, ctas, st);
   }
   return cudaErrorInvalidValue;
 }

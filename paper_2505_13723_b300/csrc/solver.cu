@@ -2,14 +2,21 @@
 // the ADASAP iteration (Alg. 2) captured once as a CUDA graph and replayed,
 // the posterior mean, the hyperparameter adjoint and the device sampler.
 //
-// One iteration is a two-branch graph:
-//   sample B, Omega, v0 -> gather X_B
-//   branch 1 (high-priority stream): sketch K_BB Omega (Step II), Nystrom core
-//            (Alg. 4), Woodbury factor, randomized powering (Alg. 5) -> eta
-//   branch 2: block residual K_Bn Z + lambda Z_B - Y_B (Step I)
-//   join -> direction P^{-1} R (App. C.2) -> NesterovAcc (Alg. 6) -> t += 1
-// The branches are independent given B and Omega, so the latency-bound FP64
-// core runs in the shadow of the throughput-bound Step I.
+// One iteration is a graph with one two-branch section:
+//   sample B, Omega, v0 -> gather X_B -> thin QR of Omega -> sketch K_BB Omega
+//   (Step II) -> Gram matrices of the sketch                 (whole GPU)
+//   fork:  branch 1 (high-priority stream, kBranchSms SMs): the factorisations
+//            of Alg. 4 and the Woodbury factor
+//          branch 2 (persistent CTAs on the other SMs): block residual
+//            K_Bn Z + lambda Z_B - Y_B (Step I)
+//   join -> randomized powering (Alg. 5) -> eta -> direction P^{-1} R
+//           (App. C.2) -> NesterovAcc (Alg. 6) -> t += 1     (whole GPU)
+// The branches are independent given B and Omega, so the latency-bound
+// factorisations (mostly single-CTA launches) run beside the throughput-bound
+// Step I on SMs that Step I leaves free, instead of waiting for its CTAs to
+// retire.  The powering steps are short whole-GPU bursts (b x b products and
+// 8-CTA cluster applies) after the join.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -30,7 +37,12 @@ cudaError_t core_init();
 struct RowsPlan {
   bool tc;
   int nsplit;
+  int ctas;  // persistent CTAs of the tensor-core kernel (0: one per SM)
 };
+
+// SMs left to the factorisation branch while Step I runs (its launches are
+// mostly single-CTA; Step I's persistent CTAs occupy the other SMs throughout)
+constexpr int kBranchSms = 8;
 
 static thread_local std::string g_last_error;
 
@@ -284,10 +296,11 @@ adasap_status grow_ws(adasap_ctx* c, size_t bytes) {
   return ADASAP_OK;
 }
 
-RowsPlan plan_rows(const adasap_ctx* c, int64_t m, int64_t ncols, int s) {
+RowsPlan plan_rows(const adasap_ctx* c, int64_t m, int64_t ncols, int s, int reserve_sms = 0) {
   RowsPlan p;
   p.tc = c->prec == ADASAP_PREC_TF32X3 && c->kp > 0 && s == 1;
-  p.nsplit = p.tc ? tc_nsplit(m, ncols) : rows_nsplit(m, ncols, s, c->dp, false);
+  p.ctas = (p.tc && reserve_sms > 0) ? std::max(1, tc_slots() - reserve_sms) : 0;
+  p.nsplit = p.tc ? tc_nsplit(m, ncols, p.ctas) : rows_nsplit(m, ncols, s, c->dp, false);
   return p;
 }
 
@@ -296,7 +309,7 @@ cudaError_t run_rows_over_x(const adasap_ctx* c, const RowsPlan& p, const float*
                             int64_t m, const float* w, int s, float* part, int self_mode, cudaStream_t st) {
   if (p.tc)
     return launch_rows_tc(c->kern, c->d, xr, qr, ridx, m, c->dp, c->tc_hi, c->tc_lo, c->n, self_mode, w, s, part,
-                          p.nsplit, c->sigma2, c->err_dev, st);
+                          p.nsplit, c->sigma2, c->err_dev, st, p.ctas);
   return launch_rows(c->kern, c->dp, rows_over_x(c, xr, qr, ridx, m, w, s, part), s, p.nsplit, false, st);
 }
 
@@ -474,7 +487,8 @@ adasap_status alloc_solver(adasap_solver* S) {
   cb.T = ar.get<double>((size_t)rr * rr);
   cb.S = ar.get<double>(rr);
   cb.keep = ar.get<double>(rr);
-  cb.Lw = ar.get<double>((size_t)rr * rr);
+  cb.Minv = ar.get<float>((size_t)rr * rr);
+  cb.Gu = ar.get<float>((size_t)rr * rr);
   cb.U = ar.get<float>((size_t)b * rr);
   cb.utv_chunks = utv_chunks_for(b);
   cb.utv_part = ar.get<double>((size_t)cb.utv_chunks * rr * s);
@@ -512,64 +526,77 @@ cudaError_t capture_iteration(adasap_solver* S, const int64_t* Bs, const float* 
     K(launch_normals(S->o.seed, tdev, 0, b, 3, 1.0f, S->v0, s0));
   }
   K(launch_gather(c->Xc, c->qc, S->B32, b, c->dp, S->XB, S->qB, s0));
-  K(cudaEventRecord(c->ev_fork, s0));
-  K(cudaStreamWaitEvent(s1, c->ev_fork, 0));
-  // branch 1: Step II sketch, Step III Nystrom + preconditioner + stepsize
   RowsArgs kb;
   kb.xr = S->XB; kb.qr = S->qB; kb.ridx = nullptr; kb.m = b;
   kb.xc = S->XB; kb.qc = S->qB; kb.ncols = b;
   kb.part = S->part2; kb.cps = 0; kb.sigma2 = c->sigma2;
   if (!S->identity) {
-    K(launch_orthonormalize(cb, S->Om, S->Ysk, c->sc, s1));   // thin QR of Omega
+    // whole-GPU part of Steps II-III: thin QR of Omega, sketch K_BB Omega, its Gram matrices
+    K(launch_orthonormalize(cb, S->Om, S->Ysk, c->sc, s0));
     kb.w = S->Om; kb.ldw = r;
-    K(launch_rows(c->kern, c->dp, kb, r, S->ns_sk, false, s1));
+    K(launch_rows(c->kern, c->dp, kb, r, S->ns_sk, false, s0));
     K(launch_reduce(S->part2, S->ns_sk, b, r, 0, r, S->Ysk, r, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0,
-                    nullptr, s1));
+                    nullptr, s0));
+    K(launch_nystrom_grams(cb, S->Om, S->Ysk, s0));
+  }
+  K(cudaEventRecord(c->ev_fork, s0));
+  K(cudaStreamWaitEvent(s1, c->ev_fork, 0));
+  // branch 1: the factorisations of Alg. 4 and the Woodbury factor (App. C.2)
+  if (!S->identity) {
     K(launch_nystrom_core(cb, S->eps, lam, c->sc, S->Om, S->Ysk, s1));
     K(launch_woodbury_factor(cb, lam, c->sc, s1));
   }
-  // v0 copy and ||v0||^2 partials
   if (S->tc_pw) K(launch_build_tc(c->Xc, c->qc, S->B32, b, c->d, c->dp, S->XBhi, S->XBlo, s1));
-  // Alg. 5: v <- (P + rho I)^{-1/2} H (P + rho I)^{-1/2} v / ||v||, N times
-  const float* vcur = S->v0;
-  float* vbuf[2] = {S->vA, S->vB};
-  for (int i = 0; i < S->o.power_iters; ++i) {
-    const bool last = i == S->o.power_iters - 1;
-    float* vnext = vbuf[i & 1];
-    if (!S->identity) K(launch_wb_cluster(cb, kInvSqrtNormalised, vcur, S->a, nullptr, c->sc, s1));
-    else {
-      K(launch_reduce(vcur, 1, b, 1, 0, 1, S->h, 1, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, cb.sq_part,
-                      s1));
-      K(launch_woodbury_apply(cb, kInvSqrtNormalised, S->h, 1, S->a, false, false, nullptr, c->sc, s1));
-    }
-    kb.w = S->a; kb.ldw = 1;
-    if (S->tc_pw)
-      K(launch_rows_tc(c->kern, c->d, S->XB, S->qB, nullptr, b, c->dp, S->XBhi, S->XBlo, b, 1, S->a, 1, S->part2,
-                       S->ns_pw, c->sigma2, c->err_dev, s1));
-    else
-      K(launch_rows(c->kern, c->dp, kb, 1, S->ns_pw, false, s1));
-    if (!S->identity) {
-      K(launch_reduce(S->part2, S->ns_pw, b, 1, 0, 1, S->h, 1, (float)lam, S->a, nullptr, 1, 0.f, nullptr, nullptr,
-                      0, nullptr, s1));
-      K(launch_wb_cluster(cb, kInvSqrt, S->h, vnext, last ? vcur : nullptr, c->sc, s1));
-    } else {
-      K(launch_reduce(S->part2, S->ns_pw, b, 1, 0, 1, S->h, 1, (float)lam, S->a, nullptr, 1, 0.f, nullptr, nullptr,
-                      0, nullptr, s1));
-      K(launch_woodbury_apply(cb, kInvSqrt, S->h, 1, vnext, true, last, last ? vcur : nullptr, c->sc, s1));
-    }
-    vcur = vnext;
-  }
-  K(launch_set_eta(cb, c->sc, S->identity, s1));
   K(cudaEventRecord(c->ev_join, s1));
-  // branch 2: Step I block residual at the reading's point
+  // branch 2: Step I block residual at the reading's point, concurrent with branch 1
   float* P = S->literal ? S->W : S->Z;
   K(run_rows_over_x(c, S->plan1, c->Xc, c->qc, S->B32, b, P, s, S->part1, 1, s0));
   K(launch_reduce(S->part1, S->ns1, b, s, 0, s, S->R, s, (float)lam, P, S->B32, s, -1.f, S->Y, S->B32, s, nullptr,
                   s0));
   K(cudaStreamWaitEvent(s0, c->ev_join, 0));
+  // Alg. 5 after the join, on the whole GPU: v <- P^{-1/2} H P^{-1/2} v / ||v||, N times
+  kb.ldw = 1;
+  if (!S->identity) {
+    // carried as a_i = P^{-1/2} v_i: one cluster launch per H product
+    float* abuf[2] = {S->vA, S->vB};
+    K(launch_wb_cluster(cb, kInvSqrtNormalised, S->v0, abuf[0], c->sc, s0));
+    for (int i = 0; i < S->o.power_iters; ++i) {
+      const bool last = i == S->o.power_iters - 1;
+      float* acur = abuf[i & 1];
+      kb.w = acur;
+      if (S->tc_pw)
+        K(launch_rows_tc(c->kern, c->d, S->XB, S->qB, nullptr, b, c->dp, S->XBhi, S->XBlo, b, 1, acur, 1, S->part2,
+                         S->ns_pw, c->sigma2, c->err_dev, s0));
+      else
+        K(launch_rows(c->kern, c->dp, kb, 1, S->ns_pw, false, s0));
+      K(launch_power_step(cb, last ? kRayleighEta : kInvUnit, S->part2, S->ns_pw, (float)lam, acur, S->h,
+                          abuf[(i + 1) & 1], c->sc, s0));
+    }
+  } else {
+    const float* vcur = S->v0;
+    float* vbuf[2] = {S->vA, S->vB};
+    for (int i = 0; i < S->o.power_iters; ++i) {
+      const bool last = i == S->o.power_iters - 1;
+      float* vnext = vbuf[i & 1];
+      K(launch_reduce(vcur, 1, b, 1, 0, 1, S->h, 1, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, cb.sq_part,
+                      s0));
+      K(launch_woodbury_apply(cb, kInvSqrtNormalised, S->h, 1, S->a, false, false, nullptr, c->sc, s0));
+      kb.w = S->a;
+      if (S->tc_pw)
+        K(launch_rows_tc(c->kern, c->d, S->XB, S->qB, nullptr, b, c->dp, S->XBhi, S->XBlo, b, 1, S->a, 1, S->part2,
+                         S->ns_pw, c->sigma2, c->err_dev, s0));
+      else
+        K(launch_rows(c->kern, c->dp, kb, 1, S->ns_pw, false, s0));
+      K(launch_reduce(S->part2, S->ns_pw, b, 1, 0, 1, S->h, 1, (float)lam, S->a, nullptr, 1, 0.f, nullptr, nullptr,
+                      0, nullptr, s0));
+      K(launch_woodbury_apply(cb, kInvSqrt, S->h, 1, vnext, true, last, last ? vcur : nullptr, c->sc, s0));
+      vcur = vnext;
+    }
+    K(launch_set_eta(cb, c->sc, S->identity, s0));
+  }
   // Step IV: direction and NesterovAcc
   if (!S->identity && s == 1)
-    K(launch_wb_cluster(cb, kInv, S->R, S->D, nullptr, c->sc, s0));
+    K(launch_wb_cluster(cb, kInv, S->R, S->D, c->sc, s0));
   else
     K(launch_woodbury_apply(cb, kInv, S->R, s, S->D, false, false, nullptr, c->sc, s0));
   K(launch_nesterov(S->W, S->V, S->Z, n * (int64_t)s, (float)S->beta, (float)S->alpha, S->literal, s0));
@@ -611,7 +638,7 @@ adasap_status solver_begin(adasap_ctx* c, const float* Y, int s, const adasap_op
   S->eps = o->eps > 0 ? o->eps : std::ldexp(1.0, -23);
   S->literal = o->literal ? 1 : 0;
   S->mc = std::min<int64_t>(n, std::max<int64_t>(1, o->check_rows));
-  S->plan1 = plan_rows(c, b, n, s);
+  S->plan1 = plan_rows(c, b, n, s, kBranchSms);
   S->plan_c = plan_rows(c, S->mc, n, s);
   S->tc_pw = c->prec == ADASAP_PREC_TF32X3 && c->kp > 0;
   S->ns1 = S->plan1.nsplit;
