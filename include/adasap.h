@@ -176,9 +176,11 @@ adasap_status adasap_solver_residual(adasap_solver* sol, double* rel_resid, void
 adasap_status adasap_solver_get_w(adasap_solver* sol, float* W, void* stream);
 adasap_status adasap_solver_scalars(adasap_solver* sol, double* eta, double* rho, int* status, void* stream);
 void adasap_solver_end(adasap_solver* sol);
-/* Diagnostics of the last iteration (synchronises): out[0..8] = Delta, rho, eta,
+/* Diagnostics of the last iteration (synchronises): out[0..9] = Delta, rho, eta,
  * lambda_hat, Cholesky shift increases, Jacobi sweeps, status, status detail,
- * iteration counter; the first `count` are written. */
+ * iteration counter, and the code of the first bounded wait of a tensor-core
+ * kernel that timed out in this context (0: none; its outputs are then NaN);
+ * the first `count` are written. */
 adasap_status adasap_solver_diag(adasap_solver* sol, double* out, int count, void* stream);
 /* Number of kernel launches in one captured iteration (for launch accounting). */
 adasap_status adasap_solver_graph_kernels(adasap_solver* sol, int* count);

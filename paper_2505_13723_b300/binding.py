@@ -287,7 +287,7 @@ class Solver:
                                           _stream(stream)), "adasap_solver_scalars")
         return eta.value, rho.value, st.value
 
-    DIAG = ["delta", "rho", "eta", "lam_hat", "chol_retries", "jacobi_sweeps", "status", "detail", "t"]
+    DIAG = ["delta", "rho", "eta", "lam_hat", "chol_retries", "jacobi_sweeps", "status", "detail", "t", "tc_err"]
 
     def diag(self, stream=None):
         out = (ctypes.c_double * len(self.DIAG))()

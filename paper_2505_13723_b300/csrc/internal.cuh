@@ -80,6 +80,22 @@ cudaError_t launch_rows_tc(int kern, int d, const float* xr, const float* qr, co
                            int64_t ldw, float* part, int nsplit, float sigma2, int* err, cudaStream_t st,
                            int max_ctas = 0);
 
+// ---- multi-RHS tensor-core product (rows_tc_mrhs.cu) ------------------------------
+// Padded accumulator width for s right-hand sides, and the floats of one W
+// operand (hi or lo) for n rows.
+int tc_mrhs_sp(int s);
+int64_t tc_mrhs_wfloats(int64_t n, int s);
+cudaError_t tc_mrhs_init();
+int tc_mrhs_nsplit(int64_t m, int64_t ncols, int max_ctas = 0);
+// W (n x s, row stride ldw) -> chunked canonical B operands (hi; lo when passes == 3).
+cudaError_t launch_build_w_tc(const float* W, int64_t ldw, int64_t n, int s, int passes, float* whi, float* wlo,
+                              cudaStream_t st);
+// part[p][i][c] = sigma2 * sum_{j in split p} k(x'_{row i}, x'_j) W[j][c] on the tensor cores.
+cudaError_t launch_rows_tc_mrhs(int kern, int d, const float* xr, const float* qr, const int* ridx, int64_t m, int dp,
+                                const float* bhi, const float* blo, int64_t ncols, int self_mode, const float* whi,
+                                const float* wlo, int s, int passes, float* part, int nsplit, float sigma2, int* err,
+                                cudaStream_t st, int max_ctas = 0);
+
 // ---- sampler (Philox4x32-10; definitions in sampler.cu) -------------------------
 cudaError_t launch_sample_block(uint64_t seed, const long long* t_dev, int64_t t_host, int64_t n,
                                 int64_t b, int stream_tag, int* B32, int64_t* B64, cudaStream_t st);

@@ -26,111 +26,9 @@
 // NaN partials.
 #include <algorithm>
 
-#include "internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace adasap {
-
-constexpr int kTcM = 128, kTcN = 128, kTcThreads = 384;
-constexpr uint32_t kTmemCols = 256;
-constexpr uint32_t kWaitPolls = 1u << 20;  // a legitimate wait is one pipeline stage
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred P;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
-      "selp.b32 %0, 1, 0, P;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait on an mbarrier phase; false on timeout or when another role aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  for (uint32_t it = 0; it < kWaitPolls; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 255u && *abort_flag) return false;
-  }
-  return false;
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
-                   smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tc_mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                            uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-// Shared-memory matrix descriptor: start address, leading (K) byte offset,
-// stride (8-row group) byte offset, descriptor version 1, no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
-         (1ull << 46);
-}
-// Instruction descriptor: D = F32, A = B = TF32, both K-major, N = 128, M = 128.
-constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
-                                ((uint32_t)(kTcM >> 4) << 24);
-
-#define TMEM_LD32(taddr, r)                                                                                        \
-  asm volatile(                                                                                                    \
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18," \
-      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                                               \
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),          \
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),    \
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),  \
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])   \
-      : "r"(taddr))
-
-// tcgen05.wait::ld with the loaded registers as operands, so that no use of
-// them can be scheduled before the wait.
-#define TMEM_WAIT32(r)                                                                                             \
-  asm volatile("tcgen05.wait::ld.sync.aligned;"                                                                    \
-               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),  \
-                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),          \
-                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),        \
-                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),        \
-                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])                                                             \
-               :                                                                                                   \
-               : "memory")
-
-__device__ __forceinline__ float tf32_round(float x) {
-  uint32_t y;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
-  return __uint_as_float(y);
-}
-
-// float offset of element (row, k) in the no-swizzle K-major layout
-template <int KP>
-__host__ __device__ __forceinline__ int64_t tc_off(int64_t row, int k) {
-  return (row >> 3) * (8 * KP) + (k >> 2) * 32 + (row & 7) * 4 + (k & 3);
-}
 
 template <int KP>
 struct TcSmem {
@@ -258,6 +156,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(TcArgs a) {
           const uint32_t ph = (g >> 1) & 1u;
           if (!mbar_wait(&empty[st], ph ^ 1u, abort_flag)) {
             *abort_flag = 1;
+            tc_note_timeout(a.err, 1);
             break;
           }
           mbar_arrive_expect_tx(&full[st], 2u * OPF * sizeof(float));
@@ -272,8 +171,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(TcArgs a) {
             const uint32_t g = gt + (uint32_t)t;
             const int st = g & 1;
             const uint32_t ph = (g >> 1) & 1u;
-            for (uint32_t it = 0; it < kWaitPolls && !mbar_try_wait(&full[st], ph); ++it) {
-            }
+            mbar_wait(&full[st], ph, nullptr);
           }
         }
       }
@@ -287,6 +185,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(TcArgs a) {
           const uint32_t ph = (g >> 1) & 1u;
           if (!mbar_wait(&full[st], ph, abort_flag) || !mbar_wait(&tempty[buf], ph ^ 1u, abort_flag)) {
             *abort_flag = 1;
+            tc_note_timeout(a.err, 2);
             break;
           }
           tc_fence_after();
@@ -313,8 +212,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(TcArgs a) {
           // all MMAs of this item complete before the row operands are rewritten
           // (next item) or TMEM is released (end)
           tc_commit(drain);
-          for (uint32_t it = 0; it < kWaitPolls && !mbar_try_wait(drain, ndrain & 1u); ++it) {
-          }
+          mbar_wait(drain, ndrain & 1u, nullptr);
           ++ndrain;
         }
       }
@@ -337,6 +235,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(TcArgs a) {
         const uint32_t ph = (gg >> 1) & 1u;
         if (!mbar_wait(&tfull[buf], ph, abort_flag)) {
           *abort_flag = 1;
+          tc_note_timeout(a.err, 3);
           break;
         }
         tc_fence_after();
@@ -398,7 +297,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(TcArgs a) {
     __syncthreads();
     tc_fence_after();
   }
-  if (warp == 0 && lane == 0 && *abort_flag && a.err) atomicExch(a.err, 1);
+  if (warp == 0 && lane == 0 && *abort_flag) tc_note_timeout(a.err, 9);
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols) : "memory");

@@ -1,0 +1,529 @@
+// Multi-right-hand-side block-row product on the 5th-generation tensor cores:
+//   part[p][i][c] = sigma2 * sum_{j in split p} k(x'_{row i}, x'_j) W[j][c],   c < s, 2 <= s <= 128
+// (Alg. 2 Step I with s columns, the Step II sketch K_BB Omega with s = r, the
+// posterior mean of s samples).  Both contractions run on the tensor cores:
+//   1. squared distances of a 128 x 128 tile by the TF32-split MMAs of
+//      rows_tc.cu (a_i = [-2 x'_i, q_i, 1], b_j = [x'_j, 1, q_j]) into TMEM;
+//   2. the epilogue warps turn them into kernel values, split those into TF32
+//      hi/lo and store them as 32-column chunks in shared memory (the A operand
+//      of a second MMA, no-swizzle K-major layout);
+//   3. each chunk is multiplied by the matching 32-row chunk of W (the B
+//      operand, prebuilt hi/lo in the same layout by k_build_w_tc) into a
+//      128 x s_pad FP32 accumulator in TMEM:
+//        passes = 3: K_hi W_hi + K_hi W_lo + K_lo W_hi   (FP32-level accuracy)
+//        passes = 1: K_hi W_hi                           (TF32 inputs)
+// The accumulator spans one column split (at most kMrhsMaxCols columns, so that
+// the FP32 accumulation stays far below the product's tolerance); the splits
+// are summed in FP64 by k_reduce.
+//
+// CTA = 128 rows, 384 threads, one CTA per SM, persistent over (row tile,
+// split) items like rows_tc.cu:
+//   warp 0       producer: bulk copies of the column operand tiles (2-stage
+//                ring) and of the W chunks (2-slot ring), in the order the MMAs
+//                consume them
+//   warp 1       TMEM owner and MMA issuer: distance MMAs one tile ahead of
+//                the contraction MMAs of the previous tile
+//   warps 4..11  epilogue: warpgroup g forms chunks 2g, 2g + 1 of every tile in
+//                its own chunk slot (one producer per slot, so that a parity wait
+//                can never alias a phase two uses back), then reads its half of
+//                the accumulator
+// TMEM: columns [0, 256) two distance buffers, [256, 256 + s_pad) the
+// accumulator (512 allocated).  Every wait is bounded; on a timeout the CTA
+// raises the error flag, drains its copies and MMAs, frees TMEM and writes NaN.
+#include <algorithm>
+
+#include "tc_ptx.cuh"
+
+namespace adasap {
+
+namespace {
+
+constexpr int kCh = 32;                     // columns per contraction chunk
+constexpr int kChPerTile = kTcN / kCh;      // 4
+constexpr int kKSlots = 2, kWSlots = 2;     // K chunk slots (one per warpgroup), W chunk ring
+// The MMAs take a tile's chunks in the order j = 0..3 -> chunk column 2 (j & 1) + (j >> 1):
+// warpgroup 0's first, warpgroup 1's first, warpgroup 0's second, warpgroup 1's second.
+__host__ __device__ constexpr int chunk_col(int j) { return 2 * (j & 1) + (j >> 1); }
+constexpr uint32_t kMrhsTmemCols = 512;
+constexpr uint32_t kAccCol = 256;           // first accumulator column
+constexpr int64_t kMrhsMaxCols = 16384;     // columns accumulated in TMEM per item
+
+struct MrhsArgs {
+  const float* xr;
+  const float* qr;
+  const int* ridx;
+  int64_t m;
+  int dp, d;
+  const float* bhi;    // column distance operands (npad rows, canonical layout)
+  const float* blo;
+  int64_t ncols;
+  int self_mode;
+  const float* whi;    // W chunks: [npad / 32][s_pad x 32] canonical, hi and lo
+  const float* wlo;
+  int s, sp;           // right-hand sides and the padded accumulator width (multiple of 16)
+  int passes;          // 3 (split) or 1
+  float* part;         // nsplit x m x s
+  int64_t cps;         // columns per split (multiple of 128)
+  int nsplit;
+  float sigma2;
+  int* err;
+};
+
+// Shared-memory plan (bytes from a 128-byte aligned base)
+struct MrhsSmem {
+  size_t a, x, k, w, bars, total;
+  __host__ __device__ MrhsSmem(int kp, int sp) {
+    const size_t opf = (size_t)kTcM * kp * sizeof(float);
+    a = 0;                                                      // row operands hi, lo
+    x = a + 2 * opf;                                            // [2 stages][hi, lo] column tiles
+    k = x + 4 * opf;                                            // [kKSlots][hi, lo] 128 x 32 chunks
+    w = k + (size_t)kKSlots * 2 * kTcM * kCh * sizeof(float);   // [kWSlots][hi, lo] sp x 32 chunks
+    bars = w + (size_t)kWSlots * 2 * sp * kCh * sizeof(float);
+    total = bars + 32 * sizeof(uint64_t) + 64 + 128;
+  }
+};
+
+template <int KERN, int KP>
+__global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc_mrhs(MrhsArgs a) {
+  constexpr int OPF = kTcM * KP;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* base = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+  const MrhsSmem L(KP, a.sp);
+  float* sAhi = reinterpret_cast<float*>(base + L.a);
+  float* sAlo = sAhi + OPF;
+  float* sX = reinterpret_cast<float*>(base + L.x);   // [st][hi, lo][OPF]
+  float* sK = reinterpret_cast<float*>(base + L.k);   // [slot][hi, lo][128 * 32]
+  float* sW = reinterpret_cast<float*>(base + L.w);   // [slot][hi, lo][sp * 32]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bars);
+  uint64_t* full = bars;         // [2] column tiles landed
+  uint64_t* empty = bars + 2;    // [2] column tile stage free
+  uint64_t* tfull = bars + 4;    // [2] distance buffer ready
+  uint64_t* tempty = bars + 6;   // [2] distance buffer read (8 epilogue warps)
+  uint64_t* kfull = bars + 8;    // [2] K chunk written (4 warps of one warpgroup)
+  uint64_t* kempty = bars + 10;  // [2] K chunk consumed
+  uint64_t* wfull = bars + 12;   // [2] W chunk landed
+  uint64_t* wempty = bars + 14;  // [2] W chunk consumed
+  uint64_t* ofull = bars + 16;   // accumulator of the item complete
+  uint64_t* drain = bars + 17;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 18);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int sp = a.sp;
+  const int64_t rtiles = (a.m + kTcM - 1) / kTcM;
+  const int64_t nitems = rtiles * a.nsplit;
+  const uint32_t wbytes = (uint32_t)(sp * kCh * sizeof(float));
+
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 8);
+      mbar_init(&kfull[i], 4);
+      mbar_init(&kempty[i], 1);
+      mbar_init(&wfull[i], 1);
+      mbar_init(&wempty[i], 1);
+    }
+    mbar_init(ofull, 1);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(kMrhsTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+
+  uint32_t gt = 0, nof = 0, ndrain = 0;
+  for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int64_t rtile = item % rtiles, split = item / rtiles;
+    const int64_t row0 = rtile * kTcM;
+    const int64_t c0 = split * a.cps;
+    const int64_t c1 = min(a.ncols, c0 + a.cps);
+    const int ntiles = (c1 > c0 && !*abort_flag) ? (int)((c1 - c0 + kTcN - 1) / kTcN) : 0;
+    if (tid < kTcM) {
+      const int64_t ri = row0 + tid;
+      float av[KP];
+#pragma unroll
+      for (int k = 0; k < KP; ++k) av[k] = 0.0f;
+      bool ok = ri < a.m;
+      int64_t src = ri;
+      if (ok && a.ridx) {
+        const int id = a.ridx[ri];
+        ok = id >= 0;
+        src = id;
+      }
+      if (ok) {
+        for (int k = 0; k < a.d; ++k) av[k] = -2.0f * a.xr[src * a.dp + k];
+        av[a.d] = a.qr[src];
+      } else {
+        av[a.d] = 1e20f;
+      }
+      av[a.d + 1] = 1.0f;
+#pragma unroll
+      for (int k = 0; k < KP; ++k) {
+        const float hi = tf32_round(av[k]);
+        sAhi[tc_off<KP>(tid, k)] = hi;
+        sAlo[tc_off<KP>(tid, k)] = tf32_round(av[k] - hi);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+
+    if (warp == 0) {
+      // ---- producer: X(0); then per tile t: X(t + 1), W(t, 0..3) -----------------
+      if (lane == 0) {
+        int xi = 0;         // column tiles issued
+        int64_t wi = 0;     // W chunks issued (item-local)
+        bool ok = true;
+        auto issue_x = [&](int t) -> bool {
+          const uint32_t g = gt + (uint32_t)t;
+          const int st = g & 1;
+          if (!mbar_wait(&empty[st], ((g >> 1) & 1u) ^ 1u, abort_flag)) {
+            tc_note_timeout(a.err, 11);
+            return false;
+          }
+          mbar_arrive_expect_tx(&full[st], 2u * OPF * sizeof(float));
+          const int64_t off = (c0 + (int64_t)t * kTcN) * KP;
+          bulk_g2s(sX + (st * 2 + 0) * OPF, a.bhi + off, OPF * sizeof(float), &full[st]);
+          bulk_g2s(sX + (st * 2 + 1) * OPF, a.blo + off, OPF * sizeof(float), &full[st]);
+          return true;
+        };
+        if (ntiles > 0) ok = issue_x(0), xi = ok ? 1 : 0;
+        for (int t = 0; ok && t < ntiles; ++t) {
+          if (t + 1 < ntiles) {
+            if (!(ok = issue_x(t + 1))) break;
+            xi = t + 2;
+          }
+          for (int j = 0; j < kChPerTile; ++j) {
+            const uint32_t q = (gt + (uint32_t)t) * kChPerTile + (uint32_t)j;  // consumption index
+            const int sl = q & 1;
+            if (!mbar_wait(&wempty[sl], ((q >> 1) & 1u) ^ 1u, abort_flag)) {
+              tc_note_timeout(a.err, 12);
+              ok = false;
+              break;
+            }
+            mbar_arrive_expect_tx(&wfull[sl], (a.passes == 3 ? 2u : 1u) * wbytes);
+            const int64_t chunk = (c0 + (int64_t)t * kTcN) / kCh + chunk_col(j);
+            bulk_g2s(sW + (sl * 2 + 0) * sp * kCh, a.whi + chunk * sp * kCh, wbytes, &wfull[sl]);
+            if (a.passes == 3) bulk_g2s(sW + (sl * 2 + 1) * sp * kCh, a.wlo + chunk * sp * kCh, wbytes, &wfull[sl]);
+            ++wi;
+          }
+        }
+        if (!ok) {
+          *abort_flag = 1;
+          // our copies still write shared memory: wait (bounded) for the last of each ring
+          for (int t = max(0, xi - 2); t < xi; ++t) {
+            const uint32_t g = gt + (uint32_t)t;
+            mbar_wait(&full[g & 1], (g >> 1) & 1u, nullptr);
+          }
+          for (int64_t k = (wi > 2 ? wi - 2 : 0); k < wi; ++k) {
+            const uint32_t q = gt * kChPerTile + (uint32_t)k;
+            mbar_wait(&wfull[q & 1], (q >> 1) & 1u, nullptr);
+          }
+        }
+      }
+    } else if (warp == 1) {
+      // ---- MMA issuer: dist(0); per tile t: dist(t + 1), contr(t, 0..3) -------------
+      if (lane == 0) {
+        bool ok = true, any = false;
+        uint32_t acc_flag = 0;
+        auto issue_dist = [&](int t) -> bool {
+          const uint32_t g = gt + (uint32_t)t;
+          const int st = g & 1, buf = g & 1;
+          const uint32_t ph = (g >> 1) & 1u;
+          if (!mbar_wait(&full[st], ph, abort_flag) || !mbar_wait(&tempty[buf], ph ^ 1u, abort_flag)) {
+            tc_note_timeout(a.err, 13);
+            return false;
+          }
+          tc_fence_after();
+          const uint32_t dt = tbase + (uint32_t)(buf * kTcN);
+          const uint32_t a_hi = smem_u32(sAhi), a_lo = smem_u32(sAlo);
+          const uint32_t b_hi = smem_u32(sX + (st * 2 + 0) * OPF), b_lo = smem_u32(sX + (st * 2 + 1) * OPF);
+          uint32_t acc = 0;
+#pragma unroll
+          for (int pass = 0; pass < 3; ++pass) {
+            const uint32_t A = pass == 2 ? a_lo : a_hi;
+            const uint32_t B = pass == 1 ? b_lo : b_hi;
+#pragma unroll
+            for (int ks = 0; ks < KP / 8; ++ks) {
+              tc_mma_tf32(dt, smem_desc(A + 256u * ks, 128u, 32u * KP), smem_desc(B + 256u * ks, 128u, 32u * KP),
+                          kIdescTf32, acc);
+              acc = 1;
+            }
+          }
+          tc_commit(&empty[st]);
+          tc_commit(&tfull[buf]);
+          any = true;
+          return true;
+        };
+        const uint32_t idesc = tc_idesc_tf32(sp);
+        const uint32_t dacc = tbase + kAccCol;
+        if (ntiles > 0) ok = issue_dist(0);
+        for (int t = 0; ok && t < ntiles; ++t) {
+          if (t + 1 < ntiles && !(ok = issue_dist(t + 1))) break;
+          for (int j = 0; j < kChPerTile; ++j) {
+            const uint32_t gg = gt + (uint32_t)t;
+            const uint32_t q = gg * kChPerTile + (uint32_t)j;   // W ring: consumption index
+            const int wsl = q & 1;
+            const int ksl = j & 1;                              // K slot = producing warpgroup
+            const uint32_t ku = 2u * gg + (uint32_t)(j >> 1);  // its use of that slot
+            if (!mbar_wait(&kfull[ksl], ku & 1u, abort_flag)) {
+              tc_note_timeout(a.err, 14);
+              ok = false;
+              break;
+            }
+            if (!mbar_wait(&wfull[wsl], (q >> 1) & 1u, abort_flag)) {
+              tc_note_timeout(a.err, 18);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t k_hi = smem_u32(sK + (ksl * 2 + 0) * kTcM * kCh);
+            const uint32_t k_lo = smem_u32(sK + (ksl * 2 + 1) * kTcM * kCh);
+            const uint32_t w_hi = smem_u32(sW + (wsl * 2 + 0) * sp * kCh);
+            const uint32_t w_lo = smem_u32(sW + (wsl * 2 + 1) * sp * kCh);
+            for (int pass = 0; pass < a.passes; ++pass) {
+              const uint32_t A = pass == 2 ? k_lo : k_hi;
+              const uint32_t B = pass == 1 ? w_lo : w_hi;
+#pragma unroll
+              for (int ks = 0; ks < kCh / 8; ++ks) {
+                tc_mma_tf32(dacc, smem_desc(A + 256u * ks, 128u, 32u * kCh), smem_desc(B + 256u * ks, 128u, 32u * kCh),
+                            idesc, acc_flag);
+                acc_flag = 1;
+              }
+            }
+            tc_commit(&kempty[ksl]);
+            tc_commit(&wempty[wsl]);
+          }
+          if (!ok) break;
+        }
+        if (!ok) *abort_flag = 1;
+        // the accumulator is complete once every MMA above has finished (items
+        // with tiles only: both roles count those in nof)
+        if (ntiles > 0) tc_commit(ofull);
+        if (any) {
+          tc_commit(drain);
+          mbar_wait(drain, ndrain & 1u, nullptr);
+          ++ndrain;
+        }
+      }
+    } else if (warp >= 4) {
+      // ---- epilogue ------------------------------------------------------------------
+      const int g = (warp - 4) >> 2, qd = warp & 3;
+      const int rl = qd * 32 + lane;
+      const int64_t ri = row0 + rl;
+      int64_t gi = -1;
+      bool bad = false;
+      if (ri < a.m) {
+        const int64_t src = a.ridx ? (int64_t)a.ridx[ri] : ri;
+        bad = src < 0;
+        if (a.self_mode) gi = src;
+      }
+      for (int t = 0; t < ntiles; ++t) {
+        const uint32_t gg = gt + (uint32_t)t;
+        const int buf = gg & 1;
+        if (!mbar_wait(&tfull[buf], (gg >> 1) & 1u, abort_flag)) {
+          *abort_flag = 1;
+          tc_note_timeout(a.err, 15);
+          break;
+        }
+        tc_fence_after();
+        uint32_t u0[32], u1[32];
+        const uint32_t taddr = tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)(buf * kTcN + g * 64);
+        TMEM_LD32(taddr, u0);
+        TMEM_LD32(taddr + 32u, u1);
+        TMEM_WAIT32(u0);
+        TMEM_WAIT32(u1);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
+        bool stop = false;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = 2 * g + h;
+          const int sl = g;                                   // this warpgroup's own slot
+          const uint32_t ku = 2u * gg + (uint32_t)h;          // its use of the slot
+          if (!mbar_wait(&kempty[sl], (ku & 1u) ^ 1u, abort_flag)) {
+            tc_note_timeout(a.err, 16);
+            stop = true;
+            break;
+          }
+          const int64_t jb = c0 + (int64_t)t * kTcN + c * kCh;
+          float* khi = sK + (sl * 2 + 0) * kTcM * kCh;
+          float* klo = sK + (sl * 2 + 1) * kTcM * kCh;
+          const uint32_t* u = h ? u1 : u0;
+#pragma unroll
+          for (int k4 = 0; k4 < kCh / 4; ++k4) {
+            float kv[4], hv[4], lv[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int k = 4 * k4 + e;
+              const float uu = (jb + k == gi) ? 0.0f : fmaxf(__uint_as_float(u[k]), 0.0f);
+              kv[e] = kval<KERN>(uu);
+              hv[e] = tf32_round(kv[e]);
+              lv[e] = tf32_round(kv[e] - hv[e]);
+            }
+            const int off = (rl >> 3) * (8 * kCh) + k4 * 32 + (rl & 7) * 4;
+            *reinterpret_cast<float4*>(khi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+            if (a.passes == 3) *reinterpret_cast<float4*>(klo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&kfull[sl]);
+        }
+        if (stop) {
+          *abort_flag = 1;
+          break;
+        }
+      }
+      // ---- the item's accumulator: warpgroup g reads 16-column groups g, g + 2, ...
+      const bool have = ntiles == 0 || mbar_wait(ofull, nof & 1u, abort_flag);
+      if (!have) tc_note_timeout(a.err, 17);
+      tc_fence_after();
+      const bool nan_out = bad || !have || *abort_flag;
+      for (int cg16 = g; cg16 < sp / 16; cg16 += 2) {
+        uint32_t v[16];
+        if (ntiles > 0) {
+          TMEM_LD16(tbase + ((uint32_t)(qd * 32) << 16) + kAccCol + (uint32_t)(cg16 * 16), v);
+          TMEM_WAIT16(v);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) v[e] = 0u;  // an empty split contributes zero
+        }
+        if (ri < a.m) {
+          float* dst = a.part + (split * a.m + ri) * a.s;
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int c = cg16 * 16 + e;
+            if (c < a.s) dst[c] = nan_out ? __int_as_float(0x7fc00000) : a.sigma2 * __uint_as_float(v[e]);
+          }
+        }
+      }
+      tc_fence_before();
+    }
+    gt += (uint32_t)ntiles;
+    nof += ntiles > 0 ? 1u : 0u;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+  if (warp == 0 && lane == 0 && *abort_flag) tc_note_timeout(a.err, 19);
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kMrhsTmemCols)
+                 : "memory");
+  }
+}
+
+// W operand chunks: chunk q holds rows j in [32 q, 32 q + 32) of W as the
+// sp x 32 K-major B operand (element (c, j - 32 q) at tc_off<32>), hi and lo.
+__global__ void k_build_w_tc(const float* __restrict__ W, int64_t ldw, int64_t n, int s, int sp, int64_t npad,
+                             int passes, float* __restrict__ whi, float* __restrict__ wlo) {
+  const int64_t total = npad * sp;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / sp;
+    const int c = (int)(e - j * sp);
+    const float v = (j < n && c < s) ? W[j * ldw + c] : 0.0f;
+    const float h = tf32_round(v);
+    const int64_t off = (j / kCh) * (int64_t)sp * kCh + tc_off<kCh>(c, (int)(j % kCh));
+    whi[off] = h;
+    if (passes == 3) wlo[off] = tf32_round(v - h);
+  }
+}
+
+template <int KERN, int KP>
+cudaError_t mrhs_setup(int sp_max) {
+  const MrhsSmem L(KP, sp_max);
+  return cudaFuncSetAttribute(k_rows_tc_mrhs<KERN, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+}
+
+}  // namespace
+
+int tc_mrhs_sp(int s) { return (s + 15) / 16 * 16; }
+
+int64_t tc_mrhs_wfloats(int64_t n, int s) { return tc_npad(n) * tc_mrhs_sp(s); }
+
+cudaError_t tc_mrhs_init() {
+  cudaError_t e;
+  if ((e = mrhs_setup<0, 16>(kMaxRhs)) || (e = mrhs_setup<1, 16>(kMaxRhs)) || (e = mrhs_setup<2, 16>(kMaxRhs)) ||
+      (e = mrhs_setup<0, 32>(kMaxRhs)) || (e = mrhs_setup<1, 32>(kMaxRhs)) || (e = mrhs_setup<2, 32>(kMaxRhs)))
+    return e;
+  return cudaSuccess;
+}
+
+int tc_mrhs_nsplit(int64_t m, int64_t ncols, int max_ctas) {
+  // as tc_nsplit, with at most kMrhsMaxCols columns accumulated per item
+  const int64_t rt = (m + kTcM - 1) / kTcM;
+  const int64_t tiles = (ncols + kTcN - 1) / kTcN;
+  const int64_t slots = (max_ctas > 0 && max_ctas < tc_slots()) ? max_ctas : tc_slots();
+  const int64_t min_ns = (tiles + kMrhsMaxCols / kTcN - 1) / (kMrhsMaxCols / kTcN);
+  constexpr double kStartupTiles = 2.0;
+  int64_t best = std::max<int64_t>(1, min_ns);
+  double best_cost = 1e300;
+  for (int64_t ns = std::max<int64_t>(1, min_ns); ns <= std::min<int64_t>(tiles, 4096); ++ns) {
+    const int64_t tot = rt * ns;
+    const int64_t waves = (tot + slots - 1) / slots;
+    if (waves > 64 && ns > min_ns) break;
+    const int64_t tps = (tiles + ns - 1) / ns;
+    const double cost = (double)waves * ((double)tps + kStartupTiles);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = ns;
+    }
+  }
+  return (int)best;
+}
+
+cudaError_t launch_build_w_tc(const float* W, int64_t ldw, int64_t n, int s, int passes, float* whi, float* wlo,
+                              cudaStream_t st) {
+  const int sp = tc_mrhs_sp(s);
+  const int64_t npad = tc_npad(n);
+  const int blocks = (int)std::min<int64_t>((npad * sp + 255) / 256, 148 * 16);
+  k_build_w_tc<<<blocks, 256, 0, st>>>(W, ldw, n, s, sp, npad, passes, whi, wlo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rows_tc_mrhs(int kern, int d, const float* xr, const float* qr, const int* ridx, int64_t m, int dp,
+                                const float* bhi, const float* blo, int64_t ncols, int self_mode, const float* whi,
+                                const float* wlo, int s, int passes, float* part, int nsplit, float sigma2, int* err,
+                                cudaStream_t st, int max_ctas) {
+  if (m <= 0 || ncols <= 0) return cudaSuccess;
+  if (s < 1 || s > kMaxRhs || (passes != 1 && passes != 3)) return cudaErrorInvalidValue;
+  MrhsArgs a;
+  a.xr = xr; a.qr = qr; a.ridx = ridx; a.m = m; a.dp = dp; a.d = d;
+  a.bhi = bhi; a.blo = blo; a.ncols = ncols; a.self_mode = self_mode;
+  a.whi = whi; a.wlo = wlo; a.s = s; a.sp = tc_mrhs_sp(s); a.passes = passes;
+  a.part = part; a.sigma2 = sigma2; a.err = err;
+  const int64_t tiles = (ncols + kTcN - 1) / kTcN;
+  a.cps = (tiles + nsplit - 1) / nsplit * kTcN;
+  a.nsplit = nsplit;
+  const int64_t nitems = (m + kTcM - 1) / kTcM * (int64_t)nsplit;
+  const int slots = (max_ctas > 0 && max_ctas < tc_slots()) ? max_ctas : tc_slots();
+  const int ctas = (int)std::min<int64_t>(nitems, slots);
+  const int kp = tc_kp(d);
+  const size_t smem = MrhsSmem(kp, a.sp).total;
+#define ADASAP_MRHS(KE, KPV) k_rows_tc_mrhs<KE, KPV><<<ctas, kTcThreads, smem, st>>>(a)
+  if (kp == 16) {
+    if (kern == 0) ADASAP_MRHS(0, 16);
+    else if (kern == 1) ADASAP_MRHS(1, 16);
+    else ADASAP_MRHS(2, 16);
+  } else if (kp == 32) {
+    if (kern == 0) ADASAP_MRHS(0, 32);
+    else if (kern == 1) ADASAP_MRHS(1, 32);
+    else ADASAP_MRHS(2, 32);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+#undef ADASAP_MRHS
+  return cudaGetLastError();
+}
+
+}  // namespace adasap

@@ -35,9 +35,11 @@ cudaError_t core_init();
 // A product y = K(rows, X') w dispatched to the tensor-core kernel (s = 1,
 // split precision) or to the FP32 SIMT kernels.
 struct RowsPlan {
-  bool tc;
+  bool tc;     // tensor-core kernel: rows_tc.cu (s == 1) or rows_tc_mrhs.cu (s >= 2)
+  bool mrhs;
   int nsplit;
-  int ctas;  // persistent CTAs of the tensor-core kernel (0: one per SM)
+  int ctas;    // persistent CTAs of the tensor-core kernel (0: one per SM)
+  int64_t wop_floats;  // W operand scratch (hi + lo) of the multi-RHS kernel
 };
 
 // SMs left to the factorisation branch while Step I runs (its launches are
@@ -176,6 +178,7 @@ adasap_status adasap_create(const float* X, int64_t n, int d, int kernel, float 
   if (cudaGetDevice(&c->device) != cudaSuccess) return fail(ADASAP_ECUDA);
   if (core_init() != cudaSuccess) { note_error(cudaGetLastError(), "core_init"); return fail(ADASAP_ECUDA); }
   if (tc_init() != cudaSuccess) { note_error(cudaGetLastError(), "tc_init"); return fail(ADASAP_ECUDA); }
+  if (tc_mrhs_init() != cudaSuccess) { note_error(cudaGetLastError(), "tc_mrhs_init"); return fail(ADASAP_ECUDA); }
   c->n = n;
   c->d = d;
   c->dp = padded_dim(d);
@@ -298,15 +301,29 @@ adasap_status grow_ws(adasap_ctx* c, size_t bytes) {
 
 RowsPlan plan_rows(const adasap_ctx* c, int64_t m, int64_t ncols, int s, int reserve_sms = 0) {
   RowsPlan p;
-  p.tc = c->prec == ADASAP_PREC_TF32X3 && c->kp > 0 && s == 1;
+  p.tc = c->prec == ADASAP_PREC_TF32X3 && c->kp > 0;
+  p.mrhs = p.tc && s > 1;
   p.ctas = (p.tc && reserve_sms > 0) ? std::max(1, tc_slots() - reserve_sms) : 0;
-  p.nsplit = p.tc ? tc_nsplit(m, ncols, p.ctas) : rows_nsplit(m, ncols, s, c->dp, false);
+  p.nsplit = !p.tc ? rows_nsplit(m, ncols, s, c->dp, false)
+                   : (p.mrhs ? tc_mrhs_nsplit(m, ncols, p.ctas) : tc_nsplit(m, ncols, p.ctas));
+  p.wop_floats = p.mrhs ? 2 * tc_mrhs_wfloats(ncols, s) : 0;
   return p;
 }
 
 // y-partials of K(rows, X') W over all n columns of the context
+// (wop: p.wop_floats of scratch for the multi-RHS kernel's W operand; w has row stride s)
 cudaError_t run_rows_over_x(const adasap_ctx* c, const RowsPlan& p, const float* xr, const float* qr, const int* ridx,
-                            int64_t m, const float* w, int s, float* part, int self_mode, cudaStream_t st) {
+                            int64_t m, const float* w, int s, float* part, int self_mode, cudaStream_t st,
+                            float* wop = nullptr) {
+  if (p.mrhs) {
+    if (!wop) return cudaErrorInvalidValue;
+    float* whi = wop;
+    float* wlo = wop + p.wop_floats / 2;
+    cudaError_t e = launch_build_w_tc(w, s, c->n, s, 3, whi, wlo, st);
+    if (e != cudaSuccess) return e;
+    return launch_rows_tc_mrhs(c->kern, c->d, xr, qr, ridx, m, c->dp, c->tc_hi, c->tc_lo, c->n, self_mode, whi, wlo,
+                               s, 3, part, p.nsplit, c->sigma2, c->err_dev, st, p.ctas);
+  }
   if (p.tc)
     return launch_rows_tc(c->kern, c->d, xr, qr, ridx, m, c->dp, c->tc_hi, c->tc_lo, c->n, self_mode, w, s, part,
                           p.nsplit, c->sigma2, c->err_dev, st, p.ctas);
@@ -328,13 +345,15 @@ extern "C" adasap_status adasap_kernel_rows(adasap_ctx* c, const int64_t* B, int
   cudaStream_t st = (cudaStream_t)stream;
   const RowsPlan p = plan_rows(c, b, c->n, s);
   const size_t idx_bytes = ((size_t)b * sizeof(int) + 255) & ~(size_t)255;
-  const size_t part_bytes = (size_t)p.nsplit * b * s * sizeof(float);
-  const adasap_status g = grow_ws(c, idx_bytes + part_bytes);
+  const size_t part_bytes = ((size_t)p.nsplit * b * s * sizeof(float) + 255) & ~(size_t)255;
+  const size_t wop_bytes = (size_t)p.wop_floats * sizeof(float);
+  const adasap_status g = grow_ws(c, idx_bytes + part_bytes + wop_bytes);
   if (g != ADASAP_OK) return g;
   int* idx = (int*)c->ws;
   float* part = (float*)((char*)c->ws + idx_bytes);
+  float* wop = p.mrhs ? (float*)((char*)c->ws + idx_bytes + part_bytes) : nullptr;
   CT(launch_index32(B, b, c->n, idx, st));
-  CT(run_rows_over_x(c, p, c->Xc, c->qc, idx, b, W, s, part, 1, st));
+  CT(run_rows_over_x(c, p, c->Xc, c->qc, idx, b, W, s, part, 1, st, wop));
   CT(launch_reduce(part, p.nsplit, b, s, 0, s, out, s, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, nullptr,
                    st));
   return ADASAP_OK;
@@ -349,9 +368,10 @@ extern "C" adasap_status adasap_predict(adasap_ctx* c, const float* Xtest, int64
   float* xt = ar.get<float>((size_t)m * c->dp);
   float* qt = ar.get<float>((size_t)m);
   float* part = ar.get<float>((size_t)p.nsplit * m * s);
+  float* wop = p.mrhs ? ar.get<float>((size_t)p.wop_floats) : nullptr;
   if (ar.err != cudaSuccess) return ADASAP_ENOMEM;
   CT(launch_transform(Xtest, m, c->d, c->dp, c->mean_dev, c->kappa / (double)c->ell, xt, qt, st));
-  CT(run_rows_over_x(c, p, xt, qt, nullptr, m, W, s, part, 0, st));
+  CT(run_rows_over_x(c, p, xt, qt, nullptr, m, W, s, part, 0, st, wop));
   CT(launch_reduce(part, p.nsplit, m, s, 0, s, out, s, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, nullptr,
                    st));
   CT(cudaStreamSynchronize(st));  // the arena frees its buffers on return
@@ -414,6 +434,9 @@ struct adasap_solver {
   int ns1 = 1, ns_sk = 1, ns_pw = 1, ns_c = 1;
   RowsPlan plan1{}, plan_c{};
   bool tc_pw = false;              // K_BB v products on the tensor cores
+  bool sk_tc = false;              // sketch K_BB Omega on the tensor cores (multi-RHS kernel)
+  float* wop1 = nullptr;           // W operand scratch of Step I / the residual check (multi-RHS)
+  float* wsk = nullptr;            // Omega operand of the sketch (hi + lo)
   float *XBhi = nullptr, *XBlo = nullptr;
   double beta = 0, gamma = 0, alpha = 0, eps = 0;
   int literal = 0;
@@ -461,6 +484,9 @@ adasap_status alloc_solver(adasap_solver* S) {
     S->XBlo = ar.get<float>((size_t)tc_npad(b) * c->kp);
   }
   S->part2 = ar.get<float>(std::max((size_t)S->ns_sk * b * rr, (size_t)S->ns_pw * b));
+  const int64_t wop = std::max(S->plan1.wop_floats, S->plan_c.wop_floats);
+  if (wop > 0) S->wop1 = ar.get<float>((size_t)wop);
+  if (S->sk_tc) S->wsk = ar.get<float>((size_t)2 * tc_mrhs_wfloats(b, r));
   S->Ysk = ar.get<float>((size_t)b * rr);
   S->a = ar.get<float>(b);
   S->h = ar.get<float>(b);
@@ -533,8 +559,16 @@ cudaError_t capture_iteration(adasap_solver* S, const int64_t* Bs, const float* 
   if (!S->identity) {
     // whole-GPU part of Steps II-III: thin QR of Omega, sketch K_BB Omega, its Gram matrices
     K(launch_orthonormalize(cb, S->Om, S->Ysk, c->sc, s0));
-    kb.w = S->Om; kb.ldw = r;
-    K(launch_rows(c->kern, c->dp, kb, r, S->ns_sk, false, s0));
+    if (S->sk_tc) {
+      K(launch_build_tc(c->Xc, c->qc, S->B32, b, c->d, c->dp, S->XBhi, S->XBlo, s0));
+      const int64_t wf = tc_mrhs_wfloats(b, r);
+      K(launch_build_w_tc(S->Om, r, b, r, 3, S->wsk, S->wsk + wf, s0));
+      K(launch_rows_tc_mrhs(c->kern, c->d, S->XB, S->qB, nullptr, b, c->dp, S->XBhi, S->XBlo, b, 1, S->wsk,
+                            S->wsk + wf, r, 3, S->part2, S->ns_sk, c->sigma2, c->err_dev, s0));
+    } else {
+      kb.w = S->Om; kb.ldw = r;
+      K(launch_rows(c->kern, c->dp, kb, r, S->ns_sk, false, s0));
+    }
     K(launch_reduce(S->part2, S->ns_sk, b, r, 0, r, S->Ysk, r, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0,
                     nullptr, s0));
     K(launch_nystrom_grams(cb, S->Om, S->Ysk, s0));
@@ -546,11 +580,11 @@ cudaError_t capture_iteration(adasap_solver* S, const int64_t* Bs, const float* 
     K(launch_nystrom_core(cb, S->eps, lam, c->sc, S->Om, S->Ysk, s1));
     K(launch_woodbury_factor(cb, lam, c->sc, s1));
   }
-  if (S->tc_pw) K(launch_build_tc(c->Xc, c->qc, S->B32, b, c->d, c->dp, S->XBhi, S->XBlo, s1));
+  if (S->tc_pw && !S->sk_tc) K(launch_build_tc(c->Xc, c->qc, S->B32, b, c->d, c->dp, S->XBhi, S->XBlo, s1));
   K(cudaEventRecord(c->ev_join, s1));
   // branch 2: Step I block residual at the reading's point, concurrent with branch 1
   float* P = S->literal ? S->W : S->Z;
-  K(run_rows_over_x(c, S->plan1, c->Xc, c->qc, S->B32, b, P, s, S->part1, 1, s0));
+  K(run_rows_over_x(c, S->plan1, c->Xc, c->qc, S->B32, b, P, s, S->part1, 1, s0, S->wop1));
   K(launch_reduce(S->part1, S->ns1, b, s, 0, s, S->R, s, (float)lam, P, S->B32, s, -1.f, S->Y, S->B32, s, nullptr,
                   s0));
   K(cudaStreamWaitEvent(s0, c->ev_join, 0));
@@ -642,7 +676,8 @@ adasap_status solver_begin(adasap_ctx* c, const float* Y, int s, const adasap_op
   S->plan_c = plan_rows(c, S->mc, n, s);
   S->tc_pw = c->prec == ADASAP_PREC_TF32X3 && c->kp > 0;
   S->ns1 = S->plan1.nsplit;
-  S->ns_sk = identity ? 1 : rows_nsplit(b, b, r, c->dp, false);
+  S->sk_tc = S->tc_pw && !identity && r >= 2;
+  S->ns_sk = identity ? 1 : (S->sk_tc ? tc_mrhs_nsplit(b, b) : rows_nsplit(b, b, r, c->dp, false));
   S->ns_pw = S->tc_pw ? tc_nsplit(b, b) : rows_nsplit(b, b, 1, c->dp, false);
   S->ns_c = S->plan_c.nsplit;
   adasap_status st = alloc_solver(S);
@@ -691,7 +726,7 @@ adasap_status solver_residual(adasap_solver* S, double* rel, cudaStream_t us) {
     CT(launch_sample_block(S->o.seed, nullptr, S->iters, c->n, mc, 4, S->Cidx, nullptr, c->s0));
     cidx = S->Cidx;
   }
-  CT(run_rows_over_x(c, S->plan_c, c->Xc, c->qc, cidx, mc, S->W, s, S->cpart, 1, c->s0));
+  CT(run_rows_over_x(c, S->plan_c, c->Xc, c->qc, cidx, mc, S->W, s, S->cpart, 1, c->s0, S->wop1));
   CT(launch_reduce(S->cpart, S->ns_c, mc, s, 0, s, S->Rc, s, c->lambda, S->W, cidx, s, -1.f, S->Y, cidx, s, S->sqb,
                    c->s0));
   CT(launch_sum_blocks(S->sqb, kReduceBlocks, &c->sc->resid_sq, c->s0));
@@ -859,10 +894,12 @@ extern "C" adasap_status adasap_solver_diag(adasap_solver* S, double* out, int c
   CT(cudaEventRecord(c->ev_in, (cudaStream_t)stream));
   CT(cudaStreamWaitEvent(c->s0, c->ev_in, 0));
   CT(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->s0));
+  int tc_err = 0;
+  CT(cudaMemcpyAsync(&tc_err, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, c->s0));
   CT(cudaStreamSynchronize(c->s0));
   const DevScalars& h = *c->sc_host;
   const double vals[] = {h.delta, h.rho, h.eta, h.lam_hat, (double)h.chol_retries, (double)h.jacobi_sweeps,
-                         (double)h.status, (double)h.detail, (double)h.t};
+                         (double)h.status, (double)h.detail, (double)h.t, (double)tc_err};
   for (int i = 0; i < count && i < (int)(sizeof(vals) / sizeof(vals[0])); ++i) out[i] = vals[i];
   return ADASAP_OK;
 }
@@ -912,7 +949,13 @@ extern "C" adasap_status adasap_kernel_rows_noalloc(adasap_ctx* c, const int64_t
     base = g_noalloc_ptr[dev];
   }
   cudaStream_t st = (cudaStream_t)stream;
-  const RowsPlan p = plan_rows(c, b, c->n, s);
+  RowsPlan p = plan_rows(c, b, c->n, s);
+  if (p.mrhs) {  // the multi-RHS kernel needs W-operand scratch: keep the CUDA-core kernel here
+    p.tc = p.mrhs = false;
+    p.ctas = 0;
+    p.wop_floats = 0;
+    p.nsplit = rows_nsplit(b, c->n, s, c->dp, false);
+  }
   const size_t idx_bytes = ((size_t)b * sizeof(int) + 255) & ~(size_t)255;
   const size_t part_bytes = (size_t)p.nsplit * b * s * sizeof(float);
   if (idx_bytes + part_bytes > kNoallocScratchBytes) {

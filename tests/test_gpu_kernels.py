@@ -31,7 +31,7 @@ def _check_rows(got, X, rows, W, kern, ell, s2, rtol=RTOL_ROWS):
     ref = OK.kernel_apply(Xd[rows], Xd, W.astype(np.float64), kern, ell, s2)
     scale = OK.kernel_apply(Xd[rows], Xd, np.abs(W.astype(np.float64)), kern, ell, s2)
     err = np.abs(got - ref)
-    bad = err > rtol * scale + 1e-30
+    bad = ~(err <= rtol * scale + 1e-30)     # NaN outputs fail too
     assert not bad.any(), "max err/scale %.3e" % (err / np.maximum(scale, 1e-300)).max()
 
 
@@ -73,7 +73,35 @@ def test_kernel_rows_edge_sizes(lib, s, prec):
     _check_rows(out.astype(np.float64), X, rows, W, 2, 1.5, 0.7)
 
 
-@pytest.mark.parametrize("prec,s", [(0, 2), (1, 1)])
+@pytest.mark.parametrize("s,kern,d", [(2, 0, 3), (128, 1, 16), (33, 2, 9), (100, 1, 11)])
+def test_multi_rhs_tensor_core_product_spans_splits(lib, s, kern, d):
+    """s >= 2 on the tensor cores (kernel tile x W contraction in TMEM): more columns
+    than one accumulator span (several column splits), a ragged last tile, s up to 128."""
+    n, b = 40077, 300
+    X, W = _data(n, d, s, seed=s + kern)
+    ell = 0.8 * np.sqrt(d)
+    ctx = _ctx(lib, X, kern, ell, 0.9, 1e-2, lib.PREC_TF32X3)
+    rows = np.random.default_rng(s).choice(n, size=b, replace=False)
+    out = ctx.kernel_rows(torch.from_numpy(rows).cuda(), torch.from_numpy(W).cuda()).cpu().numpy()
+    _check_rows(out.astype(np.float64), X, rows, W, kern, ell, 0.9)
+
+
+@pytest.mark.parametrize("kern", [0, 1])
+def test_multi_rhs_tensor_core_product_many_items_per_cta(lib, kern):
+    """All 10,000 rows against 10,000 columns with s = 100 (the sketch K_BB Omega of
+    the 1M-point workload): more (row tile, split) items than CTAs, so every CTA
+    carries its pipeline phases across items; sampled rows against the oracle."""
+    n, d, s = 10000, 11, 100
+    X, W = _data(n, d, s, seed=7, dist="uniform")
+    ctx = _ctx(lib, X, kern, 0.3, 1.0, 1e-3, lib.PREC_TF32X3)
+    rows = np.arange(n)
+    out = ctx.kernel_rows(torch.from_numpy(rows).cuda(), torch.from_numpy(W).cuda()).cpu().numpy()
+    pick = np.random.default_rng(kern).choice(n, size=200, replace=False)
+    pick = np.concatenate([pick, [0, 127, 128, n - 1]])
+    _check_rows(out[pick].astype(np.float64), X, pick, W, kern, 0.3, 1.0)
+
+
+@pytest.mark.parametrize("prec,s", [(0, 2), (1, 1), (1, 2)])
 def test_kernel_rows_invalid_index_gives_nan_row(lib, prec, s):
     X, W = _data(500, 4, s, seed=3)
     ctx = _ctx(lib, X, 0, 1.0, 1.0, 1.0, prec)
