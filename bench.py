@@ -40,8 +40,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ADASAP s to rel-resid 1e-3 (mixed vs FP32); kernel-row Gentries/s, % roofline"
 UNIT = "Gentries/s"
-MUFU_PER_CLK_SM = 16
-SMS = 148
+
+
+# DRAM bytes per kernel entry of k_rows_tc (Step I shape, s = 1), from an ncu
+# capture of the current kernel (profiles/k_rows_tc_step1_regress.md)
+TC_DRAM_BYTES_PER_ENTRY = (36.985088e6 + 5.12e3) / (10000 * 262144)
 
 
 def parse():
@@ -54,7 +57,7 @@ def parse():
     p.add_argument("--no-tol-run", action="store_true")
     p.add_argument("--n", type=int, default=1 << 20, help="rows of the workload (default: full size)")
     p.add_argument("--kernel-launches", type=int, default=10, help="timed launches of the Step I kernel alone")
-    p.add_argument("--tol-iters", type=int, default=3000, help="iteration cap of the time-to-1e-3 solves")
+    p.add_argument("--tol-iters", type=int, default=6000, help="iteration cap of the time-to-1e-3 solves")
     p.add_argument("--only-kernel", action="store_true",
                    help="run only the Step I block-row product launches (profiling)")
     return p.parse_args()
@@ -68,10 +71,6 @@ def workload(n):
 def entries_per_step(P, power_iters=10):
     n, b = P.X.shape[0], P.b
     return b * n + b * b + power_iters * b * b
-
-
-def mufu_per_entry(kernel):
-    return 1 if kernel == 0 else 2
 
 
 def peaks():
@@ -194,7 +193,8 @@ def config_dict(P):
 
 # ----------------------------------------------------------------------------- GPU arm
 def run_kernel_only(args):
-    """Only the fused block-row product with the benchmark's launch shape (for ncu)."""
+    """Only the fused block-row products with the benchmark's launch shapes (for ncu):
+    Step I (b x n entries, s = 1), then the sketch (b x b entries, r right-hand sides)."""
     import torch
 
     from paper_2505_13723_b300 import binding as lib
@@ -206,9 +206,17 @@ def run_kernel_only(args):
     Wv = torch.from_numpy(g.standard_normal((n, 1)).astype(np.float32)).cuda()
     for _ in range(args.kernel_launches):
         ctx.kernel_rows(B, Wv)
+    # the sketch shape K(X_B, X_B) Omega (b x b entries, r = 100 right-hand sides)
+    cb = lib.Context(torch.from_numpy(np.ascontiguousarray(P.X[B.cpu().numpy()])).cuda(), P.kernel, P.ell,
+                     P.sigma2, P.lam)
+    Om = torch.from_numpy((g.standard_normal((b, P.r)) / np.sqrt(b)).astype(np.float32)).cuda()
+    rows = torch.arange(b, device="cuda")
+    for _ in range(args.kernel_launches):
+        cb.kernel_rows(rows, Om)
     torch.cuda.synchronize()
+    cb.close()
     ctx.close()
-    print(json.dumps({"only_kernel": True, "n": n, "b": b, "launches": args.kernel_launches}))
+    print(json.dumps({"only_kernel": True, "n": n, "b": b, "r": P.r, "launches": args.kernel_launches}))
 
 
 def run_ours(args, rank, world, dist):
@@ -287,8 +295,15 @@ def run_ours(args, rank, world, dist):
     k_ms, kclk = time_kernel(default_prec)
     k_rate = b * n / (k_ms * 1e-3)
     pk, pk_src = peaks()
-    mhz = float(pk.get("sm_max_mhz", 2032.0))
-    peak_entries = SMS * MUFU_PER_CLK_SM * mhz * 1e6 / mufu_per_entry(P.kernel)
+    # roofline of the block-row product: the special-function pipe, at the issue
+    # rates measured on this GPU (ex2, rsqrt per SM per cycle) and the SM clock
+    # sampled while the kernel ran
+    pipes = lib.measure_pipes()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    ksum = kclk.summary()
+    mhz = float(ksum.get("sm_mhz") or pk.get("sm_max_mhz", 2032.0))
+    clk_per_entry = 1.0 / pipes["ex2"] + (1.0 / pipes["rsqrt"] if P.kernel != 0 else 0.0)
+    peak_entries = sms * mhz * 1e6 / clk_per_entry
 
     # ---- time to relative residual 1e-3 (FP32), bounded
     tol_run = None
@@ -340,15 +355,23 @@ def run_ours(args, rank, world, dist):
             "dtype": "tf32x3+f32" if default_prec == lib.PREC_TF32X3 else "f32", "data": "synthetic",
             "config": config_dict(P),
             "roofline": {"bound": "alu", "achieved": k_rate / 1e9, "peak": peak_entries / 1e9,
-                         "unit": "Gentries/s", "frac": k_rate / peak_entries, "traffic": None,
+                         "unit": "Gentries/s", "frac": k_rate / peak_entries,
+                         "traffic": (TC_DRAM_BYTES_PER_ENTRY * b * n if default_prec == lib.PREC_TF32X3 else None),
+                         "traffic_basis": ("dram__bytes_read.sum + dram__bytes_write.sum of one k_rows_tc launch "
+                                           "at 10,000 x 262,144 entries (profiles/k_rows_tc_step1_regress.md), "
+                                           "scaled by the entries of this launch"),
                          "kernel": ("k_rows_tc (tcgen05 TF32x3 distances)" if default_prec == lib.PREC_TF32X3
                                     else "k_rows_narrow (FP32)")
                                    + " Step I block-row product, b=%d rows x n=%d" % (b, n),
                          "ms_per_launch": k_ms,
                          "fp32_cuda_core_kernel": {"ms_per_launch": fp32_ms,
                                                    "achieved": b * n / (fp32_ms * 1e-3) / 1e9},
-                         "peak_basis": "MUFU: %d/clk/SM x %d SMs x %.0f MHz / %d MUFU per entry (sm_max_mhz %s)"
-                                       % (MUFU_PER_CLK_SM, SMS, mhz, mufu_per_entry(P.kernel), pk_src)},
+                         "peak_basis": ("special-function pipe, measured on this GPU by adasap_measure_pipes: "
+                                        "ex2 %.1f and rsqrt %.1f per SM per clock; %s per entry; %d SMs x %.0f MHz "
+                                        "(median SM clock sampled during the kernel)"
+                                        % (pipes["ex2"], pipes["rsqrt"],
+                                           "1 ex2" if P.kernel == 0 else "1 ex2 + 1 rsqrt", sms, mhz)),
+                         "pipes_measured": pipes},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": kernels_per_iter * args.steps,
             "clocks": clk.summary(), "kernel_clocks": kclk.summary(),
             "time_to_tol": tol_run,

@@ -139,6 +139,13 @@ adasap_status adasap_kernel_rows(adasap_ctx* ctx, const int64_t* B, int64_t b, c
 adasap_status adasap_kernel_rows_noalloc(adasap_ctx* ctx, const int64_t* B, int64_t b, const float* W,
                                          int s, float* out, void* stream);
 
+/* Measurement support (the paper has no counterpart): the issue throughput of
+ * the pipes that bound the block-row product on the current device, measured
+ * by long independent dependency chains on every SM.  out[0] = ex2.approx,
+ * out[1] = rsqrt.approx, out[2] = FP32 FMA, each in operations per SM per
+ * clock cycle; the first `count` (<= 3) are written.  Synchronises `stream`. */
+adasap_status adasap_measure_pipes(double* out, int count, void* stream);
+
 /* ADASAP (Alg. 2 with Alg. 4, 5, 6 and the stabilised Woodbury apply of App. C.2).
  * Y (n x s) and W (n x s) are host or device.  W holds W_0 on entry and the
  * returned iterate W_T on exit.  1 <= s <= 128.  Randomness (B, Omega, v0) is

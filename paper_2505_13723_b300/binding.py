@@ -35,7 +35,7 @@ SYMBOLS = ["adasap_default_opts", "adasap_status_string", "adasap_last_error", "
            "adasap_solver_step", "adasap_solver_residual", "adasap_solver_get_w",
            "adasap_solver_scalars", "adasap_solver_end", "adasap_solver_graph_kernels",
            "adasap_solver_diag", "adasap_set_precision",
-           "adasap_kernel_rows_noalloc"]
+           "adasap_kernel_rows_noalloc", "adasap_measure_pipes"]
 
 
 class Opts(ctypes.Structure):
@@ -309,6 +309,13 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def measure_pipes(stream=None):
+    """adasap_measure_pipes: measured ex2, rsqrt and FP32-FMA issue rates (per SM per cycle)."""
+    out = (ctypes.c_double * 3)()
+    _check(_lib.adasap_measure_pipes(out, 3, _stream(stream)), "adasap_measure_pipes")
+    return {"ex2": out[0], "rsqrt": out[1], "ffma": out[2]}
 
 
 def sample(seed, t, n, b, r, stream=None):

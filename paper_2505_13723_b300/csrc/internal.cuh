@@ -96,6 +96,9 @@ cudaError_t launch_rows_tc_mrhs(int kern, int d, const float* xr, const float* q
                                 const float* wlo, int s, int passes, float* part, int nsplit, float sigma2, int* err,
                                 cudaStream_t st, int max_ctas = 0);
 
+// ---- pipe throughput probe (probe.cu): ex2, rsqrt, FFMA per SM per cycle -------------
+cudaError_t measure_pipes(double* out3, cudaStream_t st);
+
 // ---- sampler (Philox4x32-10; definitions in sampler.cu) -------------------------
 cudaError_t launch_sample_block(uint64_t seed, const long long* t_dev, int64_t t_host, int64_t n,
                                 int64_t b, int stream_tag, int* B32, int64_t* B64, cudaStream_t st);

@@ -1,0 +1,92 @@
+// Measured throughput of the arithmetic pipes that bound the block-row product
+// (special-function unit for ex2 / rsqrt, FP32 FMA), for the roofline the
+// benchmark reports.  Each thread runs kProbeChains independent dependency
+// chains so that latency is hidden and only issue throughput counts; the SM
+// clock over the run is taken from clock64 against the global timer.
+#include "internal.cuh"
+
+namespace adasap {
+namespace {
+
+constexpr int kProbeChains = 8;
+constexpr int kProbeThreads = 256;
+constexpr int kProbeBlocksPerSm = 4;
+
+template <int OP>
+__global__ void __launch_bounds__(kProbeThreads) k_pipe_probe(int iters, float* sink, long long* clk) {
+  float x[kProbeChains];
+#pragma unroll
+  for (int i = 0; i < kProbeChains; ++i) x[i] = 0.25f + 0.01f * i + 1e-6f * threadIdx.x;
+  long long c0 = 0, t0 = 0;
+  if (threadIdx.x == 0) {
+    c0 = clock64();
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  }
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < kProbeChains; ++i) {
+      if (OP == 0) x[i] = ex2_approx(-x[i]);            // stays in [0.5, 1]
+      else if (OP == 1) x[i] = rsqrt_approx(x[i]);      // alternates a, a^-1/2: stays finite
+      else x[i] = fmaf(x[i], 0.999f, 1e-4f);
+    }
+  }
+  float acc = 0.0f;
+#pragma unroll
+  for (int i = 0; i < kProbeChains; ++i) acc += x[i];
+  if (acc == 12345.0f) *sink = acc;  // keeps the chains live
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    long long t1;
+    const long long c1 = clock64();
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+    clk[0] = c1 - c0;
+    clk[1] = t1 - t0;
+  }
+}
+
+}  // namespace
+
+cudaError_t measure_pipes(double* out3, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
+  float* sink = nullptr;
+  long long* clk = nullptr;
+  if ((e = cudaMalloc(&sink, sizeof(float)))) return e;
+  if ((e = cudaMalloc(&clk, 2 * sizeof(long long)))) {
+    cudaFree(sink);
+    return e;
+  }
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  const int blocks = sms * kProbeBlocksPerSm;
+  const int iters = 2048;
+  for (int op = 0; op < 3 && e == cudaSuccess; ++op) {
+    auto launch = [&]() {
+      if (op == 0) k_pipe_probe<0><<<blocks, kProbeThreads, 0, st>>>(iters, sink, clk);
+      else if (op == 1) k_pipe_probe<1><<<blocks, kProbeThreads, 0, st>>>(iters, sink, clk);
+      else k_pipe_probe<2><<<blocks, kProbeThreads, 0, st>>>(iters, sink, clk);
+    };
+    launch();  // warm-up
+    cudaEventRecord(a, st);
+    launch();
+    cudaEventRecord(b, st);
+    long long h[2] = {0, 0};
+    if ((e = cudaMemcpyAsync(h, clk, sizeof(h), cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaStreamSynchronize(st)) || (e = cudaGetLastError()))
+      break;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, a, b);
+    const double ghz = h[1] > 0 ? (double)h[0] / (double)h[1] : 0.0;   // cycles per ns of block 0
+    const double ops = (double)blocks * kProbeThreads * kProbeChains * (double)iters;
+    // operations per SM per cycle, over the whole launch at the measured clock
+    out3[op] = (ms > 0.0f && ghz > 0.0) ? ops / ((double)sms * (double)ms * 1e6 * ghz) : 0.0;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(sink);
+  cudaFree(clk);
+  return e;
+}
+
+}  // namespace adasap

@@ -239,6 +239,9 @@ __global__ void __launch_bounds__(kThreads) k_rows_wide(RowsArgs a, int s) {
         make_float4(-2.f * v.x, -2.f * v.y, -2.f * v.z, -2.f * v.w);
   }
 
+  // the row set-up above is read by other threads below even when this split
+  // has no columns (the tile loop, and its barriers, then run zero times)
+  __syncthreads();
   float acc[RW][CW];
 #pragma unroll
   for (int i = 0; i < RW; ++i)

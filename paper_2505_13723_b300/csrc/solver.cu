@@ -409,6 +409,14 @@ extern "C" adasap_status adasap_hypergrad(adasap_ctx* c, const float* W, const f
   return ADASAP_OK;
 }
 
+extern "C" adasap_status adasap_measure_pipes(double* out, int count, void* stream) {
+  if (!out || count < 1) return ADASAP_EINVAL;
+  double v[3] = {0.0, 0.0, 0.0};
+  CT(measure_pipes(v, (cudaStream_t)stream));
+  for (int i = 0; i < count && i < 3; ++i) out[i] = v[i];
+  return ADASAP_OK;
+}
+
 extern "C" adasap_status adasap_sample(uint64_t seed, int64_t t, int64_t n, int64_t b, int r, int64_t* B,
                                        float* Omega, float* v0, void* stream) {
   if (n < 1 || n >= (1LL << 31) || b < 1 || b > n || r < 0 || t < 0 || t >= (1LL << 32)) return ADASAP_EINVAL;

@@ -86,6 +86,19 @@ def test_multi_rhs_tensor_core_product_spans_splits(lib, s, kern, d):
     _check_rows(out.astype(np.float64), X, rows, W, kern, ell, 0.9)
 
 
+@pytest.mark.parametrize("s", [5, 17])
+def test_fp32_wide_product_with_empty_column_splits(lib, s):
+    """n = 40,077 columns over the CUDA-core split count leaves the last splits without
+    columns; their partial sums must still be written (as zeros)."""
+    n, b = 40077, 300
+    X, W = _data(n, 11, s, seed=11 + s, dist="uniform")
+    ctx = _ctx(lib, X, 0, 0.3, 1.0, 1e-3, lib.PREC_FP32)
+    rows = np.arange(b)
+    for _ in range(2):
+        out = ctx.kernel_rows(torch.from_numpy(rows).cuda(), torch.from_numpy(W).cuda()).cpu().numpy()
+        _check_rows(out.astype(np.float64), X, rows, W, 0, 0.3, 1.0)
+
+
 @pytest.mark.parametrize("kern", [0, 1])
 def test_multi_rhs_tensor_core_product_many_items_per_cta(lib, kern):
     """All 10,000 rows against 10,000 columns with s = 100 (the sketch K_BB Omega of
