@@ -30,11 +30,19 @@
 
 namespace adasap {
 
+// Epilogue: 16 warps, warp w covering TMEM lane quadrant w % 4 and the 32-column
+// group (w - 4) / 4 of every 128-column tile.
+constexpr int kTcEpiWarps = 16;
+constexpr int kTcThreadsV2 = 32 * (4 + kTcEpiWarps);   // producer, MMA, 2 idle, epilogue
+constexpr int kTcWArrays = 3;                          // w, w / log2e, w / (3 log2e^2)
+
 template <int KP>
 struct TcSmem {
   static constexpr int OPF = kTcM * KP;  // floats per 128-row operand tile
   static constexpr size_t ops_bytes = (size_t)6 * OPF * sizeof(float);
-  static constexpr size_t bytes = ops_bytes + 16 * sizeof(uint64_t) + 16 + 128 * sizeof(float) + 16 + 1024;
+  static constexpr size_t w_bytes = (size_t)2 * kTcWArrays * kTcN * sizeof(float);   // [buf][array][128]
+  static constexpr size_t red_bytes = (size_t)4 * kTcM * sizeof(float);               // column-group partials
+  static constexpr size_t bytes = ops_bytes + w_bytes + red_bytes + 32 * sizeof(uint64_t) + 64 + 1024;
 };
 
 struct TcArgs {
@@ -49,7 +57,6 @@ struct TcArgs {
   int self_mode;     // 1: column j is the same point as the row's source index
   const float* w;
   int64_t ldw;
-  int wvec;          // w is 16-byte aligned with ldw == 1: float4 loads allowed
   float* part;       // nsplit x m
   int64_t cps;       // columns per split (multiple of 128)
   int nsplit;
@@ -57,8 +64,23 @@ struct TcArgs {
   int* err;          // set to 1 on a wait timeout
 };
 
+// Per-entry epilogue on the scaled distance v = log2(e)^2 u (M32, M52) or u (RBF),
+// accumulating k(u) w / sigma2 into acc; wl = w / log2(e), w3 = w / (3 log2(e)^2):
+//   RBF  k = 2^-u
+//   M32  k = (1 + a) e^-a   = 2^-a' (1 + a' / log2 e),              a' = sqrt(v)
+//   M52  k = (1 + a + a^2/3) e^-a = 2^-a' (1 + a'/log2 e + a'^2 / (3 log2^2 e))
+template <int KERN>
+__device__ __forceinline__ float tc_term(float v, float w, float wl, float w3, float acc) {
+  if (KERN == ADASAP_RBF) return fmaf(ex2_approx(-fmaxf(v, 0.0f)), w, acc);
+  const float vc = fmaxf(v, 1e-30f);
+  const float ap = vc * rsqrt_approx(vc);
+  const float e = ex2_approx(-ap);
+  if (KERN == ADASAP_MATERN32) return fmaf(e, fmaf(ap, wl, w), acc);
+  return fmaf(e, fmaf(ap, fmaf(ap, w3, wl), w), acc);
+}
+
 template <int KERN, int KP>
-__global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(TcArgs a) {
+__global__ void __launch_bounds__(kTcThreadsV2, 1) k_rows_tc(TcArgs a) {
   using L = TcSmem<KP>;
   constexpr int OPF = L::OPF;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -66,19 +88,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(TcArgs a) {
   float* sAhi = reinterpret_cast<float*>(base);
   float* sAlo = sAhi + OPF;
   float* sB = sAlo + OPF;  // [stage][hi, lo][OPF]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + L::ops_bytes);
-  uint64_t* full = bars;        // [2]
-  uint64_t* empty = bars + 2;   // [2]
-  uint64_t* tfull = bars + 4;   // [2]
-  uint64_t* tempty = bars + 6;  // [2]
-  uint64_t* drain = bars + 8;
+  float* sw = reinterpret_cast<float*>(base + L::ops_bytes);                 // [buf][array][128]
+  float* red = reinterpret_cast<float*>(base + L::ops_bytes + L::w_bytes);   // [group][128]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + L::ops_bytes + L::w_bytes + L::red_bytes);
+  uint64_t* full = bars;        // [2] column tiles landed (copies)
+  uint64_t* empty = bars + 2;   // [2] column tile stage consumed by the MMAs
+  uint64_t* tfull = bars + 4;   // [2] distance buffer ready
+  uint64_t* tempty = bars + 6;  // [2] distance buffer and w stage done (16 epilogue warps)
+  uint64_t* wfull = bars + 8;   // [2] w stage written
+  uint64_t* drain = bars + 10;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 16);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
-  float* red = reinterpret_cast<float*>(tslot + 4);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t rtiles = (a.m + kTcM - 1) / kTcM;
   const int64_t nitems = rtiles * a.nsplit;
+  // the row operand carries log2(e)^2 for the Matern kernels (see tc_term)
+  const float rscale = (KERN == ADASAP_RBF) ? 1.0f : kLog2e * kLog2e;
 
   // ---- set-up once per CTA: barriers, TMEM --------------------------------------
   if (tid == 0) {
@@ -86,7 +112,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(TcArgs a) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
       mbar_init(&tfull[i], 1);
-      mbar_init(&tempty[i], 8);
+      mbar_init(&tempty[i], kTcEpiWarps);
+      mbar_init(&wfull[i], 1);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -129,12 +156,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(TcArgs a) {
         src = id;
       }
       if (ok) {
-        for (int k = 0; k < a.d; ++k) av[k] = -2.0f * a.xr[src * a.dp + k];
-        av[a.d] = a.qr[src];
+        for (int k = 0; k < a.d; ++k) av[k] = -2.0f * rscale * a.xr[src * a.dp + k];
+        av[a.d] = rscale * a.qr[src];
+        av[a.d + 1] = rscale;
       } else {
         av[a.d] = 1e20f;  // padded or invalid row: u is huge, the kernel value 0
+        av[a.d + 1] = 1.0f;
       }
-      av[a.d + 1] = 1.0f;
 #pragma unroll
       for (int k = 0; k < KP; ++k) {
         const float hi = tf32_round(av[k]);
@@ -147,32 +175,51 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(TcArgs a) {
     __syncthreads();
 
     if (warp == 0) {
-      // ---- producer --------------------------------------------------------------
-      if (lane == 0) {
-        int issued = 0;
-        for (int t = 0; t < ntiles; ++t) {
-          const uint32_t g = gt + (uint32_t)t;
-          const int st = g & 1;
-          const uint32_t ph = (g >> 1) & 1u;
-          if (!mbar_wait(&empty[st], ph ^ 1u, abort_flag)) {
+      // ---- producer: column tiles by bulk copy (lane 0), w by the whole warp -------
+      int issued = 0;
+      for (int t = 0; t < ntiles; ++t) {
+        const uint32_t g = gt + (uint32_t)t;
+        const int st = g & 1;
+        const uint32_t ph = (g >> 1) & 1u;
+        int ok = 1;
+        if (lane == 0) {
+          // the stage's operands (MMAs of tile g - 2) and its w (epilogue of tile g - 2)
+          ok = mbar_wait(&empty[st], ph ^ 1u, abort_flag) && mbar_wait(&tempty[st], ph ^ 1u, abort_flag);
+          if (ok) {
+            mbar_arrive_expect_tx(&full[st], 2u * OPF * sizeof(float));
+            const int64_t off = (c0 + (int64_t)t * kTcN) * KP;
+            bulk_g2s(sB + (st * 2 + 0) * OPF, a.bhi + off, OPF * sizeof(float), &full[st]);
+            bulk_g2s(sB + (st * 2 + 1) * OPF, a.blo + off, OPF * sizeof(float), &full[st]);
+          } else {
             *abort_flag = 1;
             tc_note_timeout(a.err, 1);
-            break;
           }
-          mbar_arrive_expect_tx(&full[st], 2u * OPF * sizeof(float));
-          const int64_t off = (c0 + (int64_t)t * kTcN) * KP;
-          bulk_g2s(sB + (st * 2 + 0) * OPF, a.bhi + off, OPF * sizeof(float), &full[st]);
-          bulk_g2s(sB + (st * 2 + 1) * OPF, a.blo + off, OPF * sizeof(float), &full[st]);
-          issued = t + 1;
         }
-        if (*abort_flag) {
-          // our copies still write shared memory: wait (bounded) for the last ones
-          for (int t = max(0, issued - 2); t < issued; ++t) {
-            const uint32_t g = gt + (uint32_t)t;
-            const int st = g & 1;
-            const uint32_t ph = (g >> 1) & 1u;
-            mbar_wait(&full[st], ph, nullptr);
-          }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        issued = t + 1;
+        // w of the tile's 128 columns, zero past the split
+        float* wst = sw + st * kTcWArrays * kTcN;
+        const int64_t jb = c0 + (int64_t)t * kTcN + 4 * lane;
+        float wv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) wv[e] = (jb + e < c1) ? __ldg(a.w + (jb + e) * a.ldw) : 0.0f;
+        *reinterpret_cast<float4*>(wst + 4 * lane) = make_float4(wv[0], wv[1], wv[2], wv[3]);
+        if (KERN != ADASAP_RBF) {
+          const float il = 1.0f / kLog2e, i3 = 1.0f / (3.0f * kLog2e * kLog2e);
+          *reinterpret_cast<float4*>(wst + kTcN + 4 * lane) =
+              make_float4(wv[0] * il, wv[1] * il, wv[2] * il, wv[3] * il);
+          *reinterpret_cast<float4*>(wst + 2 * kTcN + 4 * lane) =
+              make_float4(wv[0] * i3, wv[1] * i3, wv[2] * i3, wv[3] * i3);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&wfull[st]);
+      }
+      if (lane == 0 && *abort_flag) {
+        // our copies still write shared memory: wait (bounded) for the last ones
+        for (int t = max(0, issued - 2); t < issued; ++t) {
+          const uint32_t g = gt + (uint32_t)t;
+          mbar_wait(&full[g & 1], (g >> 1) & 1u, nullptr);
         }
       }
     } else if (warp == 1) {
@@ -217,8 +264,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(TcArgs a) {
         }
       }
     } else if (warp >= 4) {
-      // ---- epilogue ------------------------------------------------------------------
-      const int g = (warp - 4) >> 2, qd = warp & 3;
+      // ---- epilogue: 32 rows (TMEM quadrant) x 32 columns (group) per warp ---------
+      const int qd = warp & 3, cg = (warp - 4) >> 2;
       const int rl = qd * 32 + lane;
       const int64_t ri = row0 + rl;
       int64_t gi = -1;
@@ -233,66 +280,57 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(TcArgs a) {
         const uint32_t gg = gt + (uint32_t)t;
         const int buf = gg & 1;
         const uint32_t ph = (gg >> 1) & 1u;
-        if (!mbar_wait(&tfull[buf], ph, abort_flag)) {
+        if (!mbar_wait(&tfull[buf], ph, abort_flag) || !mbar_wait(&wfull[buf], ph, abort_flag)) {
           *abort_flag = 1;
           tc_note_timeout(a.err, 3);
           break;
         }
         tc_fence_after();
-        uint32_t u0[32], u1[32];
-        const uint32_t taddr = tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)(buf * kTcN + g * 64);
-        TMEM_LD32(taddr, u0);
-        TMEM_LD32(taddr + 32u, u1);
-        TMEM_WAIT32(u0);
-        TMEM_WAIT32(u1);
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty[buf]);
-        const int64_t jb = c0 + (int64_t)t * kTcN + g * 64;
-        float wv[64];
-        if (jb + 64 <= c1 && a.wvec) {
-          const float4* w4 = reinterpret_cast<const float4*>(a.w + jb);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const float4 x = __ldg(w4 + i);
-            wv[4 * i] = x.x; wv[4 * i + 1] = x.y; wv[4 * i + 2] = x.z; wv[4 * i + 3] = x.w;
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < 64; ++i) wv[i] = (jb + i < c1) ? __ldg(a.w + (jb + i) * a.ldw) : 0.0f;
-        }
-        const bool self_here = gi >= jb && gi < jb + 64;
+        uint32_t u[32];
+        TMEM_LD32(tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)(buf * kTcN + cg * 32), u);
+        TMEM_WAIT32(u);
+        const float* wst = sw + buf * kTcWArrays * kTcN + cg * 32;
+        const int64_t jb = c0 + (int64_t)t * kTcN + cg * 32;
+        const bool self_here = gi >= jb && gi < jb + 32;
         float tacc = 0.0f;
         if (__any_sync(0xffffffffu, self_here)) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
-            const float ua = (jb + i == gi) ? 0.0f : fmaxf(__uint_as_float(u0[i]), 0.0f);
-            const float ub = (jb + 32 + i == gi) ? 0.0f : fmaxf(__uint_as_float(u1[i]), 0.0f);
-            tacc = fmaf(kval<KERN>(ua), wv[i], tacc);
-            tacc = fmaf(kval<KERN>(ub), wv[32 + i], tacc);
+            const float v = (jb + i == gi) ? 0.0f : __uint_as_float(u[i]);
+            tacc = tc_term<KERN>(v, wst[i], wst[kTcN + i], wst[2 * kTcN + i], tacc);
           }
         } else {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            tacc = fmaf(kval<KERN>(fmaxf(__uint_as_float(u0[i]), 0.0f)), wv[i], tacc);
-            tacc = fmaf(kval<KERN>(fmaxf(__uint_as_float(u1[i]), 0.0f)), wv[32 + i], tacc);
+          for (int i4 = 0; i4 < 8; ++i4) {
+            const float4 w4 = *reinterpret_cast<const float4*>(wst + 4 * i4);
+            float4 l4 = w4, t4 = w4;
+            if (KERN != ADASAP_RBF) l4 = *reinterpret_cast<const float4*>(wst + kTcN + 4 * i4);
+            if (KERN == ADASAP_MATERN52) t4 = *reinterpret_cast<const float4*>(wst + 2 * kTcN + 4 * i4);
+            tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 0]), w4.x, l4.x, t4.x, tacc);
+            tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 1]), w4.y, l4.y, t4.y, tacc);
+            tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 2]), w4.z, l4.z, t4.z, tacc);
+            tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 3]), w4.w, l4.w, t4.w, tacc);
           }
         }
+        // the distance buffer and the w stage of this tile are free again
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
         const float y = tacc - cmp;
         const float tt = acc + y;
         cmp = (tt - acc) - y;
         acc = tt;
       }
-      // combine the two warpgroups' column halves
-      if (g == 1) red[rl] = acc - cmp;
-      asm volatile("bar.sync 1, 256;" ::: "memory");
-      if (g == 0 && ri < a.m) {
-        const float tot = (acc - cmp) + red[rl];
+      // combine the four column groups' partial sums of each row
+      red[cg * kTcM + rl] = acc - cmp;
+      asm volatile("bar.sync 1, %0;" ::"r"(32 * kTcEpiWarps) : "memory");
+      if (cg == 0 && ri < a.m) {
+        const float tot = (red[rl] + red[kTcM + rl]) + (red[2 * kTcM + rl] + red[3 * kTcM + rl]);
         a.part[split * a.m + ri] = (bad || *abort_flag) ? __int_as_float(0x7fc00000) : a.sigma2 * tot;
       }
     }
     gt += (uint32_t)ntiles;
-    // item boundary: the row operands and both TMEM buffers are free again
+    // item boundary: the row operands, both TMEM buffers and red[] are free again
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -360,7 +398,7 @@ cudaError_t tc_init() {
       (e = tc_setup<1, 32>()) || (e = tc_setup<2, 32>()))
     return e;
   int per_sm = 0, dev = 0, sms = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_tc<1, 16>, kTcThreads,
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_tc<1, 16>, kTcThreadsV2,
                                                          std::max<size_t>(TcSmem<16>::bytes, 80 * 1024))))
     return e;
   if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
@@ -397,7 +435,7 @@ int tc_nsplit(int64_t m, int64_t ncols, int max_ctas) {
 
 template <int KERN, int KP>
 static cudaError_t launch_tc_k(const TcArgs& a, int ctas, cudaStream_t st) {
-  k_rows_tc<KERN, KP><<<ctas, kTcThreads, std::max<size_t>(TcSmem<KP>::bytes, 80 * 1024), st>>>(a);
+  k_rows_tc<KERN, KP><<<ctas, kTcThreadsV2, std::max<size_t>(TcSmem<KP>::bytes, 80 * 1024), st>>>(a);
   return cudaGetLastError();
 }
 
@@ -410,7 +448,6 @@ cudaError_t launch_rows_tc(int kern, int d, const float* xr, const float* qr, co
   a.xr = xr; a.qr = qr; a.ridx = ridx; a.m = m; a.dp = dp; a.d = d;
   a.bhi = bhi; a.blo = blo; a.ncols = ncols; a.self_mode = self_mode;
   a.w = w; a.ldw = ldw; a.part = part; a.sigma2 = sigma2; a.err = err;
-  a.wvec = (ldw == 1 && (reinterpret_cast<uintptr_t>(w) & 15u) == 0) ? 1 : 0;
   const int64_t tiles = (ncols + kTcN - 1) / kTcN;
   a.cps = (tiles + nsplit - 1) / nsplit * kTcN;
   a.nsplit = nsplit;
