@@ -36,10 +36,12 @@ constexpr int kTcEpiWarps = 16;
 constexpr int kTcThreadsV2 = 32 * (4 + kTcEpiWarps);   // producer, MMA, 2 idle, epilogue
 constexpr int kTcWArrays = 3;                          // w, w / log2e, w / (3 log2e^2)
 
+constexpr int kTcStages = 4;                           // column-operand ring depth
+
 template <int KP>
 struct TcSmem {
   static constexpr int OPF = kTcM * KP;  // floats per 128-row operand tile
-  static constexpr size_t ops_bytes = (size_t)6 * OPF * sizeof(float);
+  static constexpr size_t ops_bytes = (size_t)(2 + 2 * kTcStages) * OPF * sizeof(float);
   static constexpr size_t w_bytes = (size_t)2 * kTcWArrays * kTcN * sizeof(float);   // [buf][array][128]
   static constexpr size_t red_bytes = (size_t)4 * kTcM * sizeof(float);               // column-group partials
   static constexpr size_t bytes = ops_bytes + w_bytes + red_bytes + 32 * sizeof(uint64_t) + 64 + 1024;
@@ -91,12 +93,12 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1) k_rows_tc(TcArgs a) {
   float* sw = reinterpret_cast<float*>(base + L::ops_bytes);                 // [buf][array][128]
   float* red = reinterpret_cast<float*>(base + L::ops_bytes + L::w_bytes);   // [group][128]
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + L::ops_bytes + L::w_bytes + L::red_bytes);
-  uint64_t* full = bars;        // [2] column tiles landed (copies)
-  uint64_t* empty = bars + 2;   // [2] column tile stage consumed by the MMAs
-  uint64_t* tfull = bars + 4;   // [2] distance buffer ready
-  uint64_t* tempty = bars + 6;  // [2] distance buffer and w stage done (16 epilogue warps)
-  uint64_t* wfull = bars + 8;   // [2] w stage written
-  uint64_t* drain = bars + 10;
+  uint64_t* full = bars;                     // [kTcStages] column tiles landed (copies)
+  uint64_t* empty = bars + kTcStages;        // [kTcStages] column tile stage consumed by the MMAs
+  uint64_t* tfull = bars + 2 * kTcStages;    // [2] distance buffer ready
+  uint64_t* tempty = tfull + 2;              // [2] distance buffer and w stage done (16 epilogue warps)
+  uint64_t* wfull = tfull + 4;               // [2] w stage written
+  uint64_t* drain = tfull + 6;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 16);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
@@ -108,9 +110,11 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1) k_rows_tc(TcArgs a) {
 
   // ---- set-up once per CTA: barriers, TMEM --------------------------------------
   if (tid == 0) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kTcStages; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
       mbar_init(&tfull[i], 1);
       mbar_init(&tempty[i], kTcEpiWarps);
       mbar_init(&wfull[i], 1);
@@ -175,31 +179,37 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1) k_rows_tc(TcArgs a) {
     __syncthreads();
 
     if (warp == 0) {
-      // ---- producer: column tiles by bulk copy (lane 0), w by the whole warp -------
-      int issued = 0;
-      for (int t = 0; t < ntiles; ++t) {
-        const uint32_t g = gt + (uint32_t)t;
-        const int st = g & 1;
-        const uint32_t ph = (g >> 1) & 1u;
-        int ok = 1;
+      // ---- producer: column tiles by bulk copy (lane 0) up to kTcStages tiles ahead
+      // of the MMAs; w of each tile by the whole warp once the epilogue is done with
+      // the w stage (two tiles back) -------------------------------------------------
+      int xi = 0;  // column tiles issued
+      bool ok = true;
+      for (int t = 0; ok && t < ntiles; ++t) {
         if (lane == 0) {
-          // the stage's operands (MMAs of tile g - 2) and its w (epilogue of tile g - 2)
-          ok = mbar_wait(&empty[st], ph ^ 1u, abort_flag) && mbar_wait(&tempty[st], ph ^ 1u, abort_flag);
-          if (ok) {
+          for (; xi < ntiles && xi < t + kTcStages; ++xi) {
+            const uint32_t gx = gt + (uint32_t)xi;
+            const int st = gx % kTcStages;
+            if (!mbar_wait(&empty[st], ((gx / kTcStages) & 1u) ^ 1u, abort_flag)) {
+              ok = false;
+              break;
+            }
             mbar_arrive_expect_tx(&full[st], 2u * OPF * sizeof(float));
-            const int64_t off = (c0 + (int64_t)t * kTcN) * KP;
+            const int64_t off = (c0 + (int64_t)xi * kTcN) * KP;
             bulk_g2s(sB + (st * 2 + 0) * OPF, a.bhi + off, OPF * sizeof(float), &full[st]);
             bulk_g2s(sB + (st * 2 + 1) * OPF, a.blo + off, OPF * sizeof(float), &full[st]);
-          } else {
+          }
+          const uint32_t g = gt + (uint32_t)t;
+          if (ok) ok = mbar_wait(&tempty[g & 1], ((g >> 1) & 1u) ^ 1u, abort_flag);
+          if (!ok) {
             *abort_flag = 1;
             tc_note_timeout(a.err, 1);
           }
         }
-        ok = __shfl_sync(0xffffffffu, ok, 0);
+        ok = __shfl_sync(0xffffffffu, (int)ok, 0) != 0;
         if (!ok) break;
-        issued = t + 1;
         // w of the tile's 128 columns, zero past the split
-        float* wst = sw + st * kTcWArrays * kTcN;
+        const uint32_t g = gt + (uint32_t)t;
+        float* wst = sw + (g & 1) * kTcWArrays * kTcN;
         const int64_t jb = c0 + (int64_t)t * kTcN + 4 * lane;
         float wv[4];
 #pragma unroll
@@ -213,13 +223,13 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1) k_rows_tc(TcArgs a) {
               make_float4(wv[0] * i3, wv[1] * i3, wv[2] * i3, wv[3] * i3);
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&wfull[st]);
+        if (lane == 0) mbar_arrive(&wfull[g & 1]);
       }
       if (lane == 0 && *abort_flag) {
         // our copies still write shared memory: wait (bounded) for the last ones
-        for (int t = max(0, issued - 2); t < issued; ++t) {
-          const uint32_t g = gt + (uint32_t)t;
-          mbar_wait(&full[g & 1], (g >> 1) & 1u, nullptr);
+        for (int x = max(0, xi - kTcStages); x < xi; ++x) {
+          const uint32_t gx = gt + (uint32_t)x;
+          mbar_wait(&full[gx % kTcStages], (gx / kTcStages) & 1u, nullptr);
         }
       }
     } else if (warp == 1) {
@@ -228,9 +238,9 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1) k_rows_tc(TcArgs a) {
         int issued = 0;
         for (int t = 0; t < ntiles; ++t) {
           const uint32_t g = gt + (uint32_t)t;
-          const int st = g & 1, buf = g & 1;
-          const uint32_t ph = (g >> 1) & 1u;
-          if (!mbar_wait(&full[st], ph, abort_flag) || !mbar_wait(&tempty[buf], ph ^ 1u, abort_flag)) {
+          const int st = g % kTcStages, buf = g & 1;
+          if (!mbar_wait(&full[st], (g / kTcStages) & 1u, abort_flag) ||
+              !mbar_wait(&tempty[buf], ((g >> 1) & 1u) ^ 1u, abort_flag)) {
             *abort_flag = 1;
             tc_note_timeout(a.err, 2);
             break;
