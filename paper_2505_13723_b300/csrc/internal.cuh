@@ -102,8 +102,12 @@ cudaError_t measure_pipes(double* out3, cudaStream_t st);
 // ---- sampler (Philox4x32-10; definitions in sampler.cu) -------------------------
 cudaError_t launch_sample_block(uint64_t seed, const long long* t_dev, int64_t t_host, int64_t n,
                                 int64_t b, int stream_tag, int* B32, int64_t* B64, cudaStream_t st);
+// Iteration counter of the draw: (*t_dev if t_dev else 0) + t_host.
 cudaError_t launch_normals(uint64_t seed, const long long* t_dev, int64_t t_host, int64_t count,
                            int stream_tag, float scale, float* out, cudaStream_t st);
+// Omega of schedule iteration *t_dev + offset (skipped when that is >= T).
+cudaError_t launch_copy_omega(const float* Om_s, const long long* t_dev, int offset, int64_t T, int64_t b, int r,
+                              float* Om, cudaStream_t st);
 // Copy iteration t (read from t_dev) of a schedule into the working buffers.
 cudaError_t launch_copy_schedule(const int64_t* Bs, const float* Om_s, const float* v0s,
                                  const long long* t_dev, int64_t n, int64_t b, int r, int* B32,

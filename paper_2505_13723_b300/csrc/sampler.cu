@@ -86,7 +86,8 @@ cudaError_t launch_sample_block(uint64_t seed, const long long* t_dev, int64_t t
 
 __global__ void k_normals(uint64_t seed, const long long* __restrict__ t_dev, int64_t t_host, int64_t count, int tag,
                           float scale, float* __restrict__ out) {
-  const uint32_t t = (uint32_t)(t_dev ? *t_dev : t_host);
+  // iteration counter: the device counter (when given) plus the host offset
+  const uint32_t t = (uint32_t)((t_dev ? *t_dev : 0) + t_host);
   const uint2 key = seed_key(seed);
   const int64_t nblk = (count + 3) / 4;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nblk; j += (int64_t)gridDim.x * blockDim.x) {
@@ -111,6 +112,25 @@ cudaError_t launch_normals(uint64_t seed, const long long* t_dev, int64_t t_host
   if (count <= 0) return cudaSuccess;
   const int blocks = (int)std::min<int64_t>(((count + 3) / 4 + 255) / 256, 148 * 8);
   k_normals<<<blocks, 256, 0, st>>>(seed, t_dev, t_host, count, stream_tag, scale, out);
+  return cudaGetLastError();
+}
+
+// Omega of iteration t + offset of a caller-supplied schedule (nothing when
+// t + offset >= T, past the schedule's last iteration).
+__global__ void k_copy_omega(const float* __restrict__ Om_s, const long long* __restrict__ t_dev, int offset,
+                             int64_t T, int64_t total, float* __restrict__ Om) {
+  const long long t = *t_dev + offset;
+  if (t >= T) return;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    Om[e] = Om_s[t * total + e];
+}
+
+cudaError_t launch_copy_omega(const float* Om_s, const long long* t_dev, int offset, int64_t T, int64_t b, int r,
+                              float* Om, cudaStream_t st) {
+  const int64_t total = b * (int64_t)r;
+  if (total <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 8);
+  k_copy_omega<<<blocks, 256, 0, st>>>(Om_s, t_dev, offset, T, total, Om);
   return cudaGetLastError();
 }
 

@@ -44,7 +44,7 @@ struct RowsPlan {
 
 // SMs left to the factorisation branch while Step I runs (its launches are
 // mostly single-CTA; Step I's persistent CTAs occupy the other SMs throughout)
-constexpr int kBranchSms = 8;
+constexpr int kBranchSms = 4;
 
 static thread_local std::string g_last_error;
 
@@ -453,6 +453,9 @@ struct adasap_solver {
   float *Y = nullptr, *W = nullptr, *V = nullptr, *Z = nullptr;
   int* B32 = nullptr;
   float *Om = nullptr, *v0 = nullptr, *XB = nullptr, *qB = nullptr, *R = nullptr, *D = nullptr;
+  float* OmN = nullptr;   // Omega of the next iteration, orthonormalised one iteration ahead
+  int64_t T_sched = 0;    // iterations of a caller-supplied schedule
+  const float* Oms_sched = nullptr;
   float *part1 = nullptr, *part2 = nullptr, *Ysk = nullptr, *a = nullptr, *h = nullptr, *vA = nullptr, *vB = nullptr;
   int* Cidx = nullptr;
   float *Rc = nullptr, *cpart = nullptr;
@@ -481,6 +484,7 @@ adasap_status alloc_solver(adasap_solver* S) {
   S->Z = ar.get<float>(ns_);
   S->B32 = ar.get<int>(b);
   S->Om = ar.get<float>((size_t)b * rr);
+  S->OmN = ar.get<float>((size_t)b * rr);
   S->v0 = ar.get<float>(b);
   S->XB = ar.get<float>((size_t)b * c->dp);
   S->qB = ar.get<float>(b);
@@ -535,6 +539,20 @@ adasap_status alloc_solver(adasap_solver* S) {
   return ar.err == cudaSuccess ? ADASAP_OK : ADASAP_ENOMEM;
 }
 
+// Draw Omega of iteration t + offset (t = the device counter) into OmN and
+// orthonormalise it (Alg. 2 Step II with reading R2: thin QR).
+cudaError_t next_omega(adasap_solver* S, int offset, cudaStream_t st) {
+  adasap_ctx* c = S->c;
+  const int64_t b = S->b;
+  const int r = S->r;
+  const long long* tdev = &c->sc->t;
+  cudaError_t e;
+  if (S->sched) e = launch_copy_omega(S->Oms_sched, tdev, offset, S->T_sched, b, r, S->OmN, st);
+  else e = launch_normals(S->o.seed, tdev, offset, b * (int64_t)r, 2, (float)(1.0 / std::sqrt((double)b)), S->OmN, st);
+  if (e != cudaSuccess) return e;
+  return launch_orthonormalize(S->cb, S->OmN, S->Ysk, c->sc, st);
+}
+
 // Record one ADASAP iteration on s0 (forking to s1) into S->graph.
 cudaError_t capture_iteration(adasap_solver* S, const int64_t* Bs, const float* Oms, const float* v0s, double* trace) {
   adasap_ctx* c = S->c;
@@ -551,22 +569,21 @@ cudaError_t capture_iteration(adasap_solver* S, const int64_t* Bs, const float* 
   };
   const long long* tdev = &c->sc->t;
   // sample B, Omega, v0 (Alg. 2; Alg. 5)
+  // (Omega_t was drawn and orthonormalised one iteration ahead, into OmN)
   if (S->sched) {
-    K(launch_copy_schedule(Bs, Oms, v0s, tdev, n, b, r, S->B32, S->Om, S->v0, c->sc, s0));
+    K(launch_copy_schedule(Bs, nullptr, v0s, tdev, n, b, r, S->B32, S->Om, S->v0, c->sc, s0));
   } else {
     K(launch_sample_block(S->o.seed, tdev, 0, n, b, 1, S->B32, nullptr, s0));
-    if (!S->identity)
-      K(launch_normals(S->o.seed, tdev, 0, b * (int64_t)r, 2, (float)(1.0 / std::sqrt((double)b)), S->Om, s0));
     K(launch_normals(S->o.seed, tdev, 0, b, 3, 1.0f, S->v0, s0));
   }
+  if (!S->identity) K(cudaMemcpyAsync(S->Om, S->OmN, (size_t)b * r * sizeof(float), cudaMemcpyDeviceToDevice, s0));
   K(launch_gather(c->Xc, c->qc, S->B32, b, c->dp, S->XB, S->qB, s0));
   RowsArgs kb;
   kb.xr = S->XB; kb.qr = S->qB; kb.ridx = nullptr; kb.m = b;
   kb.xc = S->XB; kb.qc = S->qB; kb.ncols = b;
   kb.part = S->part2; kb.cps = 0; kb.sigma2 = c->sigma2;
   if (!S->identity) {
-    // whole-GPU part of Steps II-III: thin QR of Omega, sketch K_BB Omega, its Gram matrices
-    K(launch_orthonormalize(cb, S->Om, S->Ysk, c->sc, s0));
+    // whole-GPU part of Steps II-III: sketch K_BB Omega and its Gram matrices
     if (S->sk_tc) {
       K(launch_build_tc(c->Xc, c->qc, S->B32, b, c->d, c->dp, S->XBhi, S->XBlo, s0));
       const int64_t wf = tc_mrhs_wfloats(b, r);
@@ -587,6 +604,9 @@ cudaError_t capture_iteration(adasap_solver* S, const int64_t* Bs, const float* 
   if (!S->identity) {
     K(launch_nystrom_core(cb, S->eps, lam, c->sc, S->Om, S->Ysk, s1));
     K(launch_woodbury_factor(cb, lam, c->sc, s1));
+    // Omega of iteration t + 1 and its thin QR, off the critical path (the sketch
+    // buffer serves as scratch: the Nystrom core is done with it)
+    K(next_omega(S, 1, s1));
   }
   if (S->tc_pw && !S->sk_tc) K(launch_build_tc(c->Xc, c->qc, S->B32, b, c->d, c->dp, S->XBhi, S->XBlo, s1));
   K(cudaEventRecord(c->ev_join, s1));
@@ -653,7 +673,7 @@ cudaError_t capture_iteration(adasap_solver* S, const int64_t* Bs, const float* 
 
 adasap_status solver_begin(adasap_ctx* c, const float* Y, int s, const adasap_opts* o, const int64_t* Bs,
                            const float* Oms, const float* v0s, const float* W0, double* trace, cudaStream_t us,
-                           adasap_solver** out) {
+                           adasap_solver** out, int64_t T_sched = 0) {
   if (!c || !Y || !o || !out || s < 1 || s > kMaxRhs) return ADASAP_EINVAL;
   *out = nullptr;
   const int64_t n = c->n, b = o->b;
@@ -668,6 +688,8 @@ adasap_status solver_begin(adasap_ctx* c, const float* Y, int s, const adasap_op
   S->s = s;
   S->o = *o;
   S->sched = Bs != nullptr;
+  S->T_sched = T_sched;
+  S->Oms_sched = Oms;
   S->identity = identity;
   S->r = r;
   S->b = b;
@@ -719,6 +741,10 @@ adasap_status solver_begin(adasap_ctx* c, const float* Y, int s, const adasap_op
   if ((e = cudaMemcpyAsync(S->Z, S->W, bytes, cudaMemcpyDeviceToDevice, c->s0))) return fail(e, "Z0");
   if ((e = cudaStreamSynchronize(c->s0))) return fail(e, "sync");
   if ((e = capture_iteration(S, Bs, Oms, v0s, trace))) return fail(e, "graph capture");
+  // Omega of the first iteration (each iteration then prepares the next one's)
+  if (!S->identity && !(S->sched && S->T_sched == 0) &&
+      ((e = next_omega(S, 0, c->s0)) || (e = cudaStreamSynchronize(c->s0))))
+    return fail(e, "first Omega");
   *out = S;
   return ADASAP_OK;
 }
@@ -870,7 +896,8 @@ extern "C" adasap_status adasap_solve_scheduled(adasap_ctx* c, const float* Y, i
   if (!B_sched || !W || !o || T < 0) return ADASAP_EINVAL;
   try {
     adasap_solver* S = nullptr;
-    adasap_status st = solver_begin(c, Y, s, o, B_sched, Omega_sched, v0_sched, W, trace, (cudaStream_t)stream, &S);
+    adasap_status st =
+        solver_begin(c, Y, s, o, B_sched, Omega_sched, v0_sched, W, trace, (cudaStream_t)stream, &S, T);
     if (st != ADASAP_OK) return st;
     st = solve_loop(S, W, stats, T, (cudaStream_t)stream);
     delete S;
