@@ -32,7 +32,7 @@ namespace adasap {
 // an FP32 product error of eps * |a| |b| is below the data's own rounding.
 // Only upper 64 x 64 tiles are computed; the reduce mirrors them.
 // ---------------------------------------------------------------------------
-// chunks of at least 32 rows, enough CTAs (chunks x upper tiles) for ~4 per SM at c = 2r <= 256
+// chunks of at least 32 rows (the launch caps them at about two CTAs per SM over the upper tiles)
 int gram_chunks_for(int64_t b) { return (int)std::max<int64_t>(1, std::min<int64_t>(240, (b + 31) / 32)); }
 
 __device__ __forceinline__ float cat_get(const float* A1, int64_t ld1, int c1, const float* A2, int64_t ld2,
@@ -42,68 +42,95 @@ __device__ __forceinline__ float cat_get(const float* A1, int64_t ld1, int c1, c
   return 0.0f;
 }
 
-// 64 x 64 output tiles, 256 threads x (4 x 4) outputs, 16-row slices.
-// EXACT: products and sums in FP64 (exact products of FP32 entries);
-// otherwise FP32 products summed in FP32 over 64 rows, then in FP64.
+// 64 x 64 output tiles, 256 threads x (4 x 4) outputs; rows are staged 32 at a
+// time in shared memory, the next slice prefetched into registers while the
+// current one is used.
+//   EXACT: every product is split exactly into p + e (p = fl(a b), e = fma(a, b, -p),
+//          an error-free transformation) and p is summed in double-float (Knuth's
+//          TwoSum), e in FP32: the chunk sum carries a relative error of about
+//          rows x 2^-48 of sum |a b| -- FP64-like, at FP32-pipe throughput (FP64
+//          arithmetic runs at a small fraction of it on this GPU)
+//   else:  FP32 products summed in FP32, flushed to FP64 every 64 rows.
 template <bool EXACT>
 __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1, int64_t ld1, int c1,
                                                    const float* __restrict__ A2, int64_t ld2, int c2,
                                                    int64_t m, int64_t chunk_rows, double* __restrict__ part) {
-  constexpr int TS = 64, KR = 16;
-  using T = typename std::conditional<EXACT, double, float>::type;
+  constexpr int TS = 64, KR = 32, PER = KR * TS / 256;  // floats per thread per matrix and slice
   const int ti = blockIdx.y, tj = blockIdx.z;
   if (ti > tj) return;
   const int c = c1 + c2;
-  __shared__ T sa[KR][TS + 1];
-  __shared__ T sb[KR][TS + 1];
+  __shared__ float sa[KR][TS + 1];
+  __shared__ float sb[KR][TS + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int64_t r0 = (int64_t)blockIdx.x * chunk_rows;
   const int64_t r1 = min(m, r0 + chunk_rows);
+  float hi[4][4], lo[4][4];
   double acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
-  T f[4][4];
+    for (int v = 0; v < 4; ++v) {
+      hi[u][v] = 0.0f;
+      lo[u][v] = 0.0f;
+      acc[u][v] = 0.0;
+    }
+  float pa[PER], pb[PER];
+  auto fetch = [&](int64_t s0) {
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) f[u][v] = (T)0;
-  int slices = 0;
-  for (int64_t s0 = r0; s0 < r1; s0 += KR) {
-    __syncthreads();
-    for (int e = tid; e < KR * TS; e += 256) {
+    for (int k = 0; k < PER; ++k) {
+      const int e = tid + 256 * k;
       const int rr = e / TS, cc = e % TS;
       const int64_t row = s0 + rr;
       const bool ok = row < r1;
-      sa[rr][cc] = ok ? (T)cat_get(A1, ld1, c1, A2, ld2, c2, row, ti * TS + cc) : (T)0;
-      sb[rr][cc] = ok ? (T)cat_get(A1, ld1, c1, A2, ld2, c2, row, tj * TS + cc) : (T)0;
+      pa[k] = ok ? cat_get(A1, ld1, c1, A2, ld2, c2, row, ti * TS + cc) : 0.0f;
+      pb[k] = ok ? cat_get(A1, ld1, c1, A2, ld2, c2, row, tj * TS + cc) : 0.0f;
+    }
+  };
+  if (r0 < r1) fetch(r0);
+  int slices = 0;
+  for (int64_t s0 = r0; s0 < r1; s0 += KR) {
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int e = tid + 256 * k;
+      sa[e / TS][e % TS] = pa[k];
+      sb[e / TS][e % TS] = pb[k];
     }
     __syncthreads();
+    if (s0 + KR < r1) fetch(s0 + KR);  // in flight during the products below
 #pragma unroll 4
     for (int rr = 0; rr < KR; ++rr) {
-      T a[4], bb[4];
+      float av[4], bv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        a[u] = sa[rr][ty + 16 * u];
-        bb[u] = sb[rr][tx + 16 * u];
+        av[u] = sa[rr][ty + 16 * u];
+        bv[u] = sb[rr][tx + 16 * u];
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) f[u][v] = fma(a[u], bb[v], f[u][v]);
+        for (int v = 0; v < 4; ++v) {
+          if (EXACT) {
+            const float p = av[u] * bv[v];
+            const float e = fmaf(av[u], bv[v], -p);
+            const float sum = hi[u][v] + p;
+            const float z = sum - hi[u][v];
+            const float err = (hi[u][v] - (sum - z)) + (p - z);
+            hi[u][v] = sum;
+            lo[u][v] += err + e;
+          } else {
+            hi[u][v] = fmaf(av[u], bv[v], hi[u][v]);
+          }
+        }
     }
-    // FP64 accumulation every kSpan slices (exact products: every slice); FP64
-    // additions are expensive on this GPU, FP32 sums over 64 rows are not
-    constexpr int kSpan = EXACT ? 1 : 4;
-    if (++slices == kSpan || s0 + KR >= r1) {
+    if (!EXACT && ++slices == 2) {
       slices = 0;
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          acc[u][v] += (double)f[u][v];
-          f[u][v] = (T)0;
+          acc[u][v] += (double)hi[u][v];
+          hi[u][v] = 0.0f;
         }
     }
   }
@@ -112,7 +139,8 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1,
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const int i = ti * TS + ty + 16 * u, j = tj * TS + tx + 16 * v;
-      if (i < c && j < c) part[((int64_t)blockIdx.x * c + i) * c + j] = acc[u][v];
+      const double tot = acc[u][v] + (double)hi[u][v] + (double)lo[u][v];
+      if (i < c && j < c) part[((int64_t)blockIdx.x * c + i) * c + j] = tot;
     }
 }
 
