@@ -12,14 +12,12 @@
 // matrix B^T B = C^{-T} (Y_nu^T Y_nu) C^{-1}: its eigenvectors are B's right
 // singular vectors V and its eigenvalues Sigma^2, and U = Y_nu (C^{-1} V Sigma^{-1}).
 // Y_nu^T Y_nu comes from the Gram of [Omega | M Omega] without forming Y_nu.
-#include <cooperative_groups.h>
 
 #include <algorithm>
 #include <type_traits>
 
 #include "internal.cuh"
 
-namespace cg = cooperative_groups;
 
 namespace adasap {
 
@@ -1004,7 +1002,7 @@ __global__ void k_set_eta(const double* __restrict__ dot_part, int nparts, const
 }
 
 cudaError_t launch_set_eta(CoreBufs& cb, DevScalars* sc, int identity, cudaStream_t st) {
-  // the identity path leaves per-block partials; the cluster apply leaves one sum
+  // (identity preconditioner only: per-block partials of the k_iapply dot product)
   k_set_eta<<<1, 256, 0, st>>>(cb.dot_part, identity ? kReduceBlocks : 1, cb.alpha, sc);
   return cudaGetLastError();
 }
@@ -1093,25 +1091,26 @@ cudaError_t launch_tick(DevScalars* sc, cudaStream_t st) {
 
 // ---------------------------------------------------------------------------
 // Single-RHS Woodbury applies (App. C.2) and the randomized-powering steps of
-// Alg. 5, each in one launch of an 8-CTA cluster.  Every CTA owns a
-// contiguous slice of the b rows.
-//   phase 1  the CTA's rows of h (the input v, or h = sum_p part[p] + lambda a
-//            for a powering step), and partials of U^T h, ||h||^2 and a . h:
-//            a warp takes eight rows at a time, lanes split the r columns
-//   phase 2  the partials meet through distributed shared memory; every CTA
-//            forms the r coefficients of out = alpha h + U coef
-//   phase 3  the CTA's rows of out, eight rows per warp, the eight row sums
-//            reduced across the lanes with a transposing butterfly
+// Alg. 5 as two whole-GPU launches over contiguous row chunks (one chunk per
+// block):
+//   A  the chunk's rows of h (the input v, or h = sum_p part[p] + lambda a for a
+//      powering step), and its partials of U^T h, ||h||^2 and a . h: a warp
+//      takes eight rows at a time, lanes split the r columns
+//   B  every block sums the partials of all chunks in a fixed order (so the
+//      result does not depend on scheduling), forms the r coefficients of
+//      out = alpha h + U coef, and writes its chunk's rows, eight rows per warp
+//      with the row sums reduced across lanes by a transposing butterfly
 // Modes (see ApplyMode):
 //   kInvSqrtNormalised  out = P^{-1/2} v / ||v||
 //   kInv                out = P^{-1} v (stabilised form, through M)
-//   kInvUnit            out = P^{-1} h / sqrt(h^T P^{-1} h): with a_i =
+//   kInvUnit            out = P^{-1/2} P^{-1/2} h / ||P^{-1/2} h||: with a_i =
 //                       P^{-1/2} v_i and v_i of unit norm, a_{i+1} = P^{-1/2}
 //                       v_{i+1} for v_{i+1} = P^{-1/2} H a_i / ||.|| (Alg. 5)
 //   kRayleighEta        lambda_hat = a . h = v^T P^{-1/2} H P^{-1/2} v, eta =
 //                       1 / lambda_hat (no output rows)
 // ---------------------------------------------------------------------------
-constexpr int kWbCluster = 8, kWbThreads = 512, kWbWarps = kWbThreads / 32, kWbRows = 8;
+constexpr int kWbThreads = 256, kWbWarps = kWbThreads / 32, kWbRows = 8;
+constexpr int kWbSlots = kMaxRank + 2;     // per-chunk partials: U^T h, ||h||^2, a . h
 
 struct WbArgs {
   const float* U;
@@ -1123,7 +1122,7 @@ struct WbArgs {
   int nsplit;
   const float* a;       // current powering iterate
   float lam;
-  float* hbuf;          // b floats: h for phase 3 (kInvUnit)
+  float* hbuf;          // b floats: h of the powering step, for launch B
   const double* keep;
   const float* Minv;
   const float* Gu;      // U^T U (FP32)
@@ -1131,6 +1130,11 @@ struct WbArgs {
   const double* cis;
   DevScalars* sc;
   float* out;
+  double* wpart;        // nchunk x kWbSlots partials
+  float* wcoef;         // coef[0..r) and alpha at [kMaxRank] (written by the last block of launch A)
+  unsigned int* count;  // blocks of launch A done (reset by its last block)
+  int nchunk;
+  int64_t per;          // rows per chunk
 };
 
 // Sum over the 32 lanes of eight per-lane values x[0..7]; on return lane l
@@ -1165,35 +1169,114 @@ __device__ __forceinline__ void transpose_sum8(float x[8], int lane) {
   x[0] += __shfl_xor_sync(full, x[0], 1);
 }
 
-__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
-__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
+// y[k] = sum_j M[k][j] x[j] (M r x r row-major FP32 in global memory, x in shared
+// memory) by one block: warps take four rows at a time, lanes split j, so a
+// warp has 16 independent loads in flight.
+__device__ void block_matvec(const float* __restrict__ M, const float* x, int r, double* y) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k0 = 4 * warp; k0 < r; k0 += 4 * kWbWarps) {
+    float t[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int jj = 0; jj < kMaxRank / 32; ++jj) {
+      const int j = lane + 32 * jj;
+      if (j < r) {
+        const float xj = x[j];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (k0 + u < r) t[u] = fmaf(M[(k0 + u) * r + j], xj, t[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float v = warp_sum(t[u]);
+      if (lane == 0 && k0 + u < r) y[k0 + u] = (double)v;
+    }
+  }
+}
 
-__global__ void __cluster_dims__(kWbCluster, 1, 1) __launch_bounds__(kWbThreads) k_wb_cluster(WbArgs a) {
-  cg::cluster_group cl = cg::this_cluster();
-  const int rank = (int)cl.block_rank();
-  __shared__ double part[kMaxRank + 2];        // this CTA's U^T h, ||h||^2, a . h
-  __shared__ double q[kMaxRank + 2];
-  __shared__ float coef[kMaxRank];
+// Coefficients of out = alpha h + U coef from the totals q (U^T h, ||h||^2,
+// a . h), by one block: written to a.wcoef[0..r) and a.wcoef[kMaxRank] = alpha.
+__device__ void wb_coefficients(const WbArgs& a, const double* q, double* ys, double* zs, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = a.r;
+  const int mode = a.mode;
+  const double rho = a.sc->rho;
+  float* coef = a.wcoef;
+  if (mode == kRayleighEta) {
+    if (threadIdx.x == 0) {
+      // lambda_hat = a . h -> eta (Alg. 5)
+      DevScalars* sc = a.sc;
+      const double lam_hat = q[kMaxRank + 1];
+      sc->lam_hat = lam_hat;
+      double eta = (lam_hat > 0.0 && isfinite(lam_hat)) ? 1.0 / lam_hat : 0.0;
+      if (!(lam_hat > 0.0 && isfinite(lam_hat))) set_status(sc, ADASAP_ENUMERIC, 4);
+      if (sc->status != 0) eta = 0.0;
+      sc->eta = eta;
+    }
+    return;
+  }
+  __shared__ float xs[kMaxRank];
+  if (mode == kInv) {
+    // coef = -keep . M (keep . q) / rho
+    for (int k = threadIdx.x; k < r; k += kWbThreads) xs[k] = (float)(a.keep[k] * q[k]);
+    __syncthreads();
+    block_matvec(a.Minv, xs, r, zs);
+    __syncthreads();
+    for (int k = threadIdx.x; k < r; k += kWbThreads) coef[k] = (float)(-a.keep[k] * zs[k] / rho);
+    if (threadIdx.x == 0) coef[kMaxRank] = (float)(1.0 / rho);
+  } else if (mode == kInvUnit) {
+    // The two inverse-square-root applies of Alg. 5 in closed form, exact for any U
+    // (P^{-1/2} = rho^{-1/2} I + U diag(cis) U^T, G = U^T U, t = U^T h, y = cis . t, z = G y):
+    //   w = P^{-1/2} h = rho^{-1/2} h + U y,  ||w||^2 = ||h||^2 / rho + 2 rho^{-1/2} t.y + y.z
+    //   P^{-1/2} w = rho^{-1} h + U (rho^{-1/2} y + cis . (rho^{-1/2} t + z))
+    const double irs = 1.0 / sqrt(rho);
+    for (int k = threadIdx.x; k < r; k += kWbThreads) {
+      ys[k] = a.cis[k] * q[k];
+      xs[k] = (float)ys[k];
+    }
+    __syncthreads();
+    block_matvec(a.Gu, xs, r, zs);
+    __syncthreads();
+    if (warp == 0) {
+      double acc2 = 0.0;
+      for (int k = lane; k < r; k += 32) acc2 += 2.0 * irs * q[k] * ys[k] + ys[k] * zs[k];
+      acc2 = warp_sum(acc2);
+      if (lane == 0) {
+        const double w2 = q[kMaxRank] / rho + acc2;
+        red[32] = w2 > 0.0 ? 1.0 / sqrt(w2) : 0.0;
+      }
+    }
+    __syncthreads();
+    const double scale = red[32];
+    for (int k = threadIdx.x; k < r; k += kWbThreads)
+      coef[k] = (float)(scale * (irs * ys[k] + a.cis[k] * (irs * q[k] + zs[k])));
+    if (threadIdx.x == 0) coef[kMaxRank] = (float)(scale / rho);
+  } else {
+    const double scale = q[kMaxRank] > 0.0 ? 1.0 / sqrt(q[kMaxRank]) : 0.0;
+    for (int k = threadIdx.x; k < r; k += kWbThreads) coef[k] = (float)(scale * q[k] * a.cis[k]);
+    if (threadIdx.x == 0) coef[kMaxRank] = (float)(scale / sqrt(rho));
+  }
+}
+
+__global__ void __launch_bounds__(kWbThreads) k_wb_partials(WbArgs a) {
   __shared__ float wtmp[kWbWarps][kMaxRank];
   __shared__ double red[33];
   __shared__ double red2[33];
+  __shared__ double q[kWbSlots];
   __shared__ double ys[kMaxRank];
   __shared__ double zs[kMaxRank];
-  __shared__ double s_alpha;
+  __shared__ int s_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int r = a.r;
   const int mode = a.mode;
   const bool from_part = mode == kInvUnit || mode == kRayleighEta;
   const bool need_u = mode != kRayleighEta;
   constexpr int KJ = kMaxRank / 32;
-  const int64_t per = (a.b + kWbCluster - 1) / kWbCluster;
-  const int64_t r0 = (int64_t)rank * per, r1 = min(a.b, r0 + per);
-  // ---- phase 1
+  const int64_t r0 = (int64_t)blockIdx.x * a.per, r1 = min(a.b, r0 + a.per);
   float acc[KJ];
 #pragma unroll
   for (int j = 0; j < KJ; ++j) acc[j] = 0.0f;
-  // ||h||^2 and a . h: lane t < kWbRows sums row t of every group in FP32 (FP64
-  // arithmetic in this loop would cost far more than the loads on this GPU)
+  // ||h||^2 and a . h: lane t < kWbRows sums row t of every group in FP32
   float hsq = 0.0f, ah = 0.0f;
   for (int64_t i0 = r0 + (int64_t)warp * kWbRows; i0 < r1; i0 += (int64_t)kWbWarps * kWbRows) {
     float hv[kWbRows];
@@ -1255,93 +1338,76 @@ __global__ void __cluster_dims__(kWbCluster, 1, 1) __launch_bounds__(kWbThreads)
   }
   const double hsq_t = block_sum((double)hsq, red);   // contains __syncthreads
   const double ah_t = block_sum((double)ah, red2);
+  double* dst = a.wpart + (int64_t)blockIdx.x * kWbSlots;
   if (need_u) {
     for (int k = threadIdx.x; k < r; k += kWbThreads) {
       double t = 0.0;
       for (int w = 0; w < kWbWarps; ++w) t += (double)wtmp[w][k];
-      part[k] = t;
+      dst[k] = t;
     }
   }
   if (threadIdx.x == 0) {
-    part[kMaxRank] = hsq_t;
-    part[kMaxRank + 1] = ah_t;
+    dst[kMaxRank] = hsq_t;
+    dst[kMaxRank + 1] = ah_t;
   }
-  cl.sync();
-  // ---- phase 2: gather partials from every CTA of the cluster
-  for (int k = threadIdx.x; k < kMaxRank + 2; k += kWbThreads) {
-    if ((need_u && k < r) || k >= kMaxRank) {
-      double t = 0.0;
-#pragma unroll
-      for (int c = 0; c < kWbCluster; ++c) t += cl.map_shared_rank(part, c)[k];
-      q[k] = t;
-    }
-  }
-  cluster_arrive();  // remote reads done; the matching wait precedes exit
+  // The last block to finish sums the partials of all chunks in chunk order (a
+  // fixed lane split and shuffle tree: the totals do not depend on which block is
+  // last) and forms the coefficients.  No block waits for another.
+  __threadfence();
   __syncthreads();
-  const double rho = a.sc->rho;
-  if (mode == kRayleighEta) {
-    if (rank == 0 && threadIdx.x == 0) {
-      DevScalars* sc = a.sc;
-      const double lam_hat = q[kMaxRank + 1];
-      sc->lam_hat = lam_hat;
-      double eta = (lam_hat > 0.0 && isfinite(lam_hat)) ? 1.0 / lam_hat : 0.0;
-      if (!(lam_hat > 0.0 && isfinite(lam_hat))) set_status(sc, ADASAP_ENUMERIC, 4);
-      if (sc->status != 0) eta = 0.0;
-      sc->eta = eta;
-    }
-    cluster_wait();
-    return;
-  }
-  if (mode == kInv) {
-    // coef = -keep . M (keep . q) / rho, one warp per row of M
-    for (int k = warp; k < r; k += kWbWarps) {
-      float t = 0.0f;
-      for (int j = lane; j < r; j += 32) t = fmaf(a.Minv[k * r + j], (float)(a.keep[j] * q[j]), t);
-      t = warp_sum(t);
-      if (lane == 0) coef[k] = (float)(-a.keep[k] * (double)t / rho);
-    }
-    if (threadIdx.x == 0) s_alpha = 1.0 / rho;
-  } else if (mode == kInvUnit) {
-    // The two inverse-square-root applies of Alg. 5 in closed form, exact for any U
-    // (P^{-1/2} = rho^{-1/2} I + U diag(cis) U^T, G = U^T U, t = U^T h, y = cis . t, z = G y):
-    //   w = P^{-1/2} h = rho^{-1/2} h + U y,  ||w||^2 = ||h||^2 / rho + 2 rho^{-1/2} t.y + y.z
-    //   P^{-1/2} w = rho^{-1} h + U (rho^{-1/2} y + cis . (rho^{-1/2} t + z))
-    const double irs = 1.0 / sqrt(rho);
-    for (int k = threadIdx.x; k < r; k += kWbThreads) ys[k] = a.cis[k] * q[k];
-    __syncthreads();
-    for (int k = warp; k < r; k += kWbWarps) {
-      float t = 0.0f;
-      for (int j = lane; j < r; j += 32) t = fmaf(a.Gu[k * r + j], (float)ys[j], t);
-      t = warp_sum(t);
-      if (lane == 0) zs[k] = (double)t;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      double acc2 = 0.0;
-      for (int k = lane; k < r; k += 32) acc2 += 2.0 * irs * q[k] * ys[k] + ys[k] * zs[k];
-      acc2 = warp_sum(acc2);
-      if (lane == 0) {
-        const double w2 = q[kMaxRank] / rho + acc2;
-        red[32] = w2 > 0.0 ? 1.0 / sqrt(w2) : 0.0;
+  if (threadIdx.x == 0) s_last = atomicAdd(a.count, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  {
+    // warp w sums chunks w, w + 8, ... (four in flight); lane j slots j, j + 32, ...
+    // (coalesced); the eight warp sums are then added in warp order
+    constexpr int KS = (kWbSlots + 31) / 32;
+    double t[KS];
+#pragma unroll
+    for (int m = 0; m < KS; ++m) t[m] = 0.0;
+    for (int c0 = warp; c0 < a.nchunk; c0 += 4 * kWbWarps) {
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        const int c = c0 + cc * kWbWarps;
+        if (c < a.nchunk) {
+#pragma unroll
+          for (int m = 0; m < KS; ++m) {
+            const int k = lane + 32 * m;
+            if (k < kWbSlots) t[m] += __ldcg(a.wpart + (int64_t)c * kWbSlots + k);
+          }
+        }
       }
     }
+    __shared__ double wsum[kWbWarps][kWbSlots];
+#pragma unroll
+    for (int m = 0; m < KS; ++m) {
+      const int k = lane + 32 * m;
+      if (k < kWbSlots) wsum[warp][k] = t[m];
+    }
     __syncthreads();
-    const double scale = red[32];
-    for (int k = threadIdx.x; k < r; k += kWbThreads)
-      coef[k] = (float)(scale * (irs * ys[k] + a.cis[k] * (irs * q[k] + zs[k])));
-    if (threadIdx.x == 0) s_alpha = scale / rho;
-  } else {
-    const double scale = q[kMaxRank] > 0.0 ? 1.0 / sqrt(q[kMaxRank]) : 0.0;
-    for (int k = threadIdx.x; k < r; k += kWbThreads) coef[k] = (float)(scale * q[k] * a.cis[k]);
-    if (threadIdx.x == 0) s_alpha = scale / sqrt(rho);
+    for (int k = threadIdx.x; k < kWbSlots; k += kWbThreads) {
+      double v = 0.0;
+#pragma unroll
+      for (int w = 0; w < kWbWarps; ++w) v += wsum[w][k];
+      q[k] = v;
+    }
   }
+  if (threadIdx.x == 0) *a.count = 0u;
   __syncthreads();
-  const float al = (float)s_alpha;
+  wb_coefficients(a, q, ys, zs, red);
+}
+
+__global__ void __launch_bounds__(kWbThreads) k_wb_apply(WbArgs a) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = a.r;
+  constexpr int KJ = kMaxRank / 32;
+  const float al = a.wcoef[kMaxRank];
   float cf[KJ];
 #pragma unroll
-  for (int j = 0; j < KJ; ++j) cf[j] = (lane + 32 * j < r) ? coef[lane + 32 * j] : 0.0f;
-  const float* hsrc = from_part ? a.hbuf : a.v;
-  // ---- phase 3: out = alpha h + U coef over the CTA's rows (same row-to-warp map as phase 1)
+  for (int j = 0; j < KJ; ++j) cf[j] = (lane + 32 * j < r) ? a.wcoef[lane + 32 * j] : 0.0f;
+  const float* hsrc = a.mode == kInvUnit ? a.hbuf : a.v;
+  const int64_t r0 = (int64_t)blockIdx.x * a.per, r1 = min(a.b, r0 + a.per);
   for (int64_t i0 = r0 + (int64_t)warp * kWbRows; i0 < r1; i0 += (int64_t)kWbWarps * kWbRows) {
     float x[kWbRows];
 #pragma unroll
@@ -1359,24 +1425,34 @@ __global__ void __cluster_dims__(kWbCluster, 1, 1) __launch_bounds__(kWbThreads)
     const int64_t i = i0 + (lane >> 2);
     if ((lane & 3) == 0 && i < r1) a.out[i] = fmaf(al, hsrc[i], x[0]);
   }
-  cluster_wait();
 }
 
-cudaError_t launch_wb_cluster(CoreBufs& cb, int mode, const float* v, float* out, DevScalars* sc, cudaStream_t st) {
-  WbArgs a{};
-  a.U = cb.U; a.b = cb.b; a.r = cb.r; a.mode = mode; a.v = v; a.keep = cb.keep; a.Minv = cb.Minv; a.Gu = cb.Gu; a.S = cb.S;
-  a.cis = cb.cis; a.sc = sc; a.out = out;
-  k_wb_cluster<<<kWbCluster, kWbThreads, 0, st>>>(a);
+static cudaError_t launch_wb(WbArgs& a, CoreBufs& cb, cudaStream_t st) {
+  a.U = cb.U; a.b = cb.b; a.r = cb.r; a.keep = cb.keep; a.Minv = cb.Minv; a.Gu = cb.Gu; a.S = cb.S; a.cis = cb.cis;
+  a.wpart = cb.wb_part;
+  a.wcoef = cb.wb_coef;
+  a.count = cb.wb_count;
+  a.nchunk = wb_chunks_for(cb.b);
+  a.per = (cb.b + a.nchunk - 1) / a.nchunk;
+  k_wb_partials<<<a.nchunk, kWbThreads, 0, st>>>(a);
+  if (a.mode != kRayleighEta) k_wb_apply<<<a.nchunk, kWbThreads, 0, st>>>(a);
   return cudaGetLastError();
+}
+
+// enough chunks for the whole GPU, few enough that the last block's sum is short
+int wb_chunks_for(int64_t b) { return (int)std::max<int64_t>(1, std::min<int64_t>(148, (b + 31) / 32)); }
+
+cudaError_t launch_wb_single(CoreBufs& cb, int mode, const float* v, float* out, DevScalars* sc, cudaStream_t st) {
+  WbArgs a{};
+  a.mode = mode; a.v = v; a.sc = sc; a.out = out;
+  return launch_wb(a, cb, st);
 }
 
 cudaError_t launch_power_step(CoreBufs& cb, int mode, const float* part, int nsplit, float lam, const float* acur,
                               float* hbuf, float* anext, DevScalars* sc, cudaStream_t st) {
   WbArgs a{};
-  a.U = cb.U; a.b = cb.b; a.r = cb.r; a.mode = mode; a.part = part; a.nsplit = nsplit; a.a = acur; a.lam = lam;
-  a.hbuf = hbuf; a.keep = cb.keep; a.Minv = cb.Minv; a.Gu = cb.Gu; a.S = cb.S; a.cis = cb.cis; a.sc = sc; a.out = anext;
-  k_wb_cluster<<<kWbCluster, kWbThreads, 0, st>>>(a);
-  return cudaGetLastError();
+  a.mode = mode; a.part = part; a.nsplit = nsplit; a.a = acur; a.lam = lam; a.hbuf = hbuf; a.sc = sc; a.out = anext;
+  return launch_wb(a, cb, st);
 }
 
 cudaError_t core_init() {

@@ -142,7 +142,11 @@ struct CoreBufs {
   double* alpha;      // scalar apply coefficient
   double* Ident;      // r x r identity
   double* cis;        // r  (S_k + rho)^{-1/2} - rho^{-1/2}
+  double* wb_part;    // [wb_chunks_for(b)][kMaxRank + 2] partials of the single-RHS applies
+  float* wb_coef;     // [kMaxRank + 1] apply coefficients and alpha
+  unsigned int* wb_count;  // finished-block counter (zero between launches)
 };
+int wb_chunks_for(int64_t b);
 int gram_chunks_for(int64_t b);
 int utv_chunks_for(int64_t b);
 cudaError_t launch_gram(const float* A1, int64_t ld1, int c1, const float* A2, int64_t ld2, int c2,
@@ -156,14 +160,14 @@ cudaError_t launch_nystrom_core(CoreBufs& cb, double eps, double lam, DevScalars
 cudaError_t launch_woodbury_factor(CoreBufs& cb, double lam, DevScalars* sc, cudaStream_t st);
 // P^{-1/2}-type or P^{-1}-type apply of App. C.2 in three launches:
 //   utv: part = U^T v (per chunk); coef: small FP64 work; apply: out = alpha v + U coef.
-// kInvUnit and kRayleighEta are the powering steps of Alg. 5 (cluster kernel only).
+// kInvUnit and kRayleighEta are the powering steps of Alg. 5 (single-RHS applies only).
 enum ApplyMode { kInvSqrt = 0, kInvSqrtNormalised = 1, kInv = 2, kInvUnit = 3, kRayleighEta = 4 };
 cudaError_t launch_woodbury_apply(CoreBufs& cb, int mode, const float* v, int s, float* out,
                                   bool want_sq, bool want_dot, const float* dotv, DevScalars* sc,
                                   cudaStream_t st);
 cudaError_t launch_set_eta(CoreBufs& cb, DevScalars* sc, int identity, cudaStream_t st);
-// One single-RHS Woodbury apply (kInvSqrtNormalised or kInv) in one 8-CTA cluster launch.
-cudaError_t launch_wb_cluster(CoreBufs& cb, int mode, const float* v, float* out, DevScalars* sc, cudaStream_t st);
+// One single-RHS Woodbury apply (kInvSqrtNormalised or kInv): two whole-GPU launches.
+cudaError_t launch_wb_single(CoreBufs& cb, int mode, const float* v, float* out, DevScalars* sc, cudaStream_t st);
 // One powering step of Alg. 5 on h = sum_p part[p] + lam * acur (nsplit x b partials):
 //   kInvUnit:     anext = P^{-1} h / sqrt(h^T P^{-1} h)  (h kept in hbuf)
 //   kRayleighEta: sc->lam_hat = acur . h, sc->eta = 1 / lam_hat

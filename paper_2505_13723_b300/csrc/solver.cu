@@ -15,7 +15,7 @@
 // factorisations (mostly single-CTA launches) run beside the throughput-bound
 // Step I on SMs that Step I leaves free, instead of waiting for its CTAs to
 // retire.  The powering steps are short whole-GPU bursts (b x b products and
-// 8-CTA cluster applies) after the join.
+// two-launch Woodbury applies) after the join.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -536,6 +536,10 @@ adasap_status alloc_solver(adasap_solver* S) {
   cb.alpha = ar.get<double>(2);
   cb.Ident = ar.get<double>((size_t)rr * rr);
   cb.cis = ar.get<double>(rr);
+  cb.wb_part = ar.get<double>((size_t)wb_chunks_for(b) * (kMaxRank + 2));
+  cb.wb_coef = ar.get<float>(kMaxRank + 1);
+  cb.wb_count = ar.get<unsigned int>(1);
+  if (cb.wb_count && cudaMemset(cb.wb_count, 0, sizeof(unsigned int)) != cudaSuccess) return ADASAP_ECUDA;
   return ar.err == cudaSuccess ? ADASAP_OK : ADASAP_ENOMEM;
 }
 
@@ -619,9 +623,9 @@ cudaError_t capture_iteration(adasap_solver* S, const int64_t* Bs, const float* 
   // Alg. 5 after the join, on the whole GPU: v <- P^{-1/2} H P^{-1/2} v / ||v||, N times
   kb.ldw = 1;
   if (!S->identity) {
-    // carried as a_i = P^{-1/2} v_i: one cluster launch per H product
+    // carried as a_i = P^{-1/2} v_i: one apply (two launches) per H product
     float* abuf[2] = {S->vA, S->vB};
-    K(launch_wb_cluster(cb, kInvSqrtNormalised, S->v0, abuf[0], c->sc, s0));
+    K(launch_wb_single(cb, kInvSqrtNormalised, S->v0, abuf[0], c->sc, s0));
     for (int i = 0; i < S->o.power_iters; ++i) {
       const bool last = i == S->o.power_iters - 1;
       float* acur = abuf[i & 1];
@@ -658,7 +662,7 @@ cudaError_t capture_iteration(adasap_solver* S, const int64_t* Bs, const float* 
   }
   // Step IV: direction and NesterovAcc
   if (!S->identity && s == 1)
-    K(launch_wb_cluster(cb, kInv, S->R, S->D, c->sc, s0));
+    K(launch_wb_single(cb, kInv, S->R, S->D, c->sc, s0));
   else
     K(launch_woodbury_apply(cb, kInv, S->R, s, S->D, false, false, nullptr, c->sc, s0));
   K(launch_nesterov(S->W, S->V, S->Z, n * (int64_t)s, (float)S->beta, (float)S->alpha, S->literal, s0));
