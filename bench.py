@@ -44,7 +44,7 @@ UNIT = "Gentries/s"
 
 # DRAM bytes per kernel entry of k_rows_tc (Step I shape, s = 1), from an ncu
 # capture of the current kernel (profiles/k_rows_tc_step1_regress.md)
-TC_DRAM_BYTES_PER_ENTRY = (36.961792e6 + 6.656e3) / (10000 * 262144)
+TC_DRAM_BYTES_PER_ENTRY = (36.93696e6 + 6.4e3) / (10000 * 262144)
 
 
 def parse():
@@ -191,6 +191,21 @@ def config_dict(P):
             "parallelism": "replicas"}
 
 
+def whole_job(t_local, units_local, dist, device):
+    """(max over ranks of the timed seconds, sum over ranks of the units processed).
+
+    Every rank is an independent replica (weak scaling), so the whole-job rate is
+    the units all ranks processed over the slowest rank's time."""
+    if dist is None:
+        return t_local, units_local
+    import torch
+    t = torch.tensor([t_local], device=device, dtype=torch.float64)
+    u = torch.tensor([units_local], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_kernel_only(args):
     """Only the fused block-row products with the benchmark's launch shapes (for ncu):
@@ -261,13 +276,9 @@ def run_ours(args, rank, world, dist):
     eta, rho, status = sol.scalars()
     diag = sol.diag()
     sol.close()
-    t_max = t_local
-    if dist is not None:
-        tt = torch.tensor([t_local], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
     ent = entries_per_step(P)
-    value = ent * args.steps * world / t_max / 1e9
+    t_max, units = whole_job(t_local, float(ent * args.steps), dist, dev)
+    value = units / t_max / 1e9
 
     # ---- the dominant kernel alone: Step I block-row product, same launch shape
     g = np.random.default_rng(5)
