@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-tol-run", action="store_true")
+    p.add_argument("--no-multi-rhs", action="store_true", help="skip the many-right-hand-sides comparison")
     p.add_argument("--n", type=int, default=1 << 20, help="rows of the workload (default: full size)")
     p.add_argument("--kernel-launches", type=int, default=10, help="timed launches of the Step I kernel alone")
     p.add_argument("--tol-iters", type=int, default=6000, help="iteration cap of the time-to-1e-3 solves")
@@ -329,6 +330,38 @@ def run_ours(args, rank, world, dist):
                              "reached": bool(st["rel_resid"] <= 1e-3), "resid_rows_sampled": 20000}
         ctx.set_precision(default_prec)
 
+    # ---- many right-hand sides: the multirhs workload (n = 2^18, s = 64), device time per
+    # iteration of the batched tensor-core solve of all 64 columns against the plain FP32
+    # single-RHS solve of one column (the batched form replaces 64 such solves)
+    multi = None
+    if rank == 0 and not args.no_multi_rhs:
+        from paper_2505_13723_b300 import synth
+        Q = synth.multirhs()
+        cq = lib.Context(torch.from_numpy(Q.X).to(dev), Q.kernel, Q.ell, Q.sigma2, Q.lam)
+        Yq = torch.from_numpy(Q.Y).to(dev)
+
+        def per_iter(prec, Yc, iters=40):
+            cq.set_precision(prec)
+            so = lib.Solver(cq, Yc, opts=lib.default_opts(Q.X.shape[0], b=Q.b, r=Q.r, seed=3, check_every=0,
+                                                          max_iters=iters + 3))
+            so.step(3)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            so.step(iters)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            so.close()
+            return e0.elapsed_time(e1) / iters
+
+        mixed_batched = per_iter(lib.PREC_TF32X3, Yq)
+        fp32_single = per_iter(lib.PREC_FP32, Yq[:, :1].contiguous())
+        cq.close()
+        multi = {"workload": "multirhs: n=262144, d=16, X~N(0,I), RBF ell=2, lambda=1e-2, b=4096, r=64, s=64",
+                 "ms_per_iteration_mixed_batched_s64": mixed_batched,
+                 "ms_per_iteration_fp32_single_rhs": fp32_single,
+                 "speedup_vs_64_fp32_single_rhs_solves": 64.0 * fp32_single / mixed_batched}
+
     # ---- end to end through the C-ABI with host buffers
     e2e = None
     if rank == 0:
@@ -386,6 +419,7 @@ def run_ours(args, rank, world, dist):
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": kernels_per_iter * args.steps,
             "clocks": clk.summary(), "kernel_clocks": kclk.summary(),
             "time_to_tol": tol_run,
+            "multi_rhs": multi,
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
             "solver_state": {"rel_resid_after": rel, "eta": eta, "rho": rho, "status": status,
                              "jacobi_sweeps": diag["jacobi_sweeps"], "chol_retries": diag["chol_retries"],

@@ -185,3 +185,27 @@ def test_invalid_schedule_index_is_reported_not_faulted(lib):
         ctx.solve_scheduled(torch.from_numpy(P.Y).cuda(), torch.from_numpy(B).cuda(), torch.from_numpy(Om).cuda(),
                             torch.from_numpy(v0).cuda(), opts=opts)
     assert ei.value.status == 1
+
+
+def test_taxi_scale_block_rows_and_iterations(lib):
+    """The largest workload, n = 2^25 (X 1.2 GB), d = 9, RBF, b = 10^5, r = 100: the
+    block-row product on sampled rows against the oracle, then two solver iterations
+    that finish with status 0 (the kernel is never materialised)."""
+    from oracle import kernels as OK
+    P = synth.taxi()
+    n = P.X.shape[0]
+    ctx = lib.Context(torch.from_numpy(P.X).cuda(), P.kernel, P.ell, P.sigma2, P.lam)
+    w = torch.from_numpy(P.Y).cuda()
+    rows = np.random.default_rng(0).choice(n, size=16, replace=False)
+    y = ctx.kernel_rows(torch.from_numpy(rows).cuda(), w).cpu().numpy().astype(np.float64)
+    Xd, Yd = P.X.astype(np.float64), P.Y.astype(np.float64)
+    ref = OK.kernel_apply(Xd[rows], Xd, Yd, P.kernel, P.ell, P.sigma2)
+    scale = OK.kernel_apply(Xd[rows], Xd, np.abs(Yd), P.kernel, P.ell, P.sigma2)
+    assert np.all(np.abs(y - ref) <= 1e-5 * scale)
+    opts = lib.default_opts(n, b=P.b, r=P.r, seed=5, check_every=0, max_iters=2)
+    sol = lib.Solver(ctx, w, opts=opts)
+    sol.step(2)
+    d = sol.diag()
+    assert d["status"] == 0 and d["tc_err"] == 0 and d["t"] == 2 and d["eta"] > 0
+    assert 0.0 < sol.residual() < 1.0
+    sol.close()
