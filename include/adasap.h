@@ -81,6 +81,9 @@ typedef struct {
   int check_every;     /* evaluate the residual every this many iterations (0: only at the end). */
   int64_t check_rows;  /* residual on all rows if n <= check_rows, else on this many sampled rows. */
   double eps;          /* eps of Alg. 4's shift Delta = eps * Tr(Omega^T M Omega); 0 => 2^-23. */
+  int tail_average;    /* 1: return the tail average (Alg. 1 / 2) mean(W_j, j = ceil(T/2) .. T) of
+                          T = max_iters iterations; the run then has exactly T iterations (no
+                          tolerance stop, residual taken at the end on the average).  Default 0. */
 } adasap_opts;
 
 typedef struct {
@@ -196,6 +199,13 @@ adasap_status adasap_solver_graph_kernels(adasap_solver* sol, int* count);
  *   out (m x s) = K(Xtest, X) W,  Xtest (m x d) device, W (n x s) device. */
 adasap_status adasap_predict(adasap_ctx* ctx, const float* Xtest, int64_t m, const float* W, int s,
                              float* out, void* stream);
+
+/* Exact relative residual of any W on all n rows (the convergence measure; its
+ * Step I-style products over row chunks of 65,536):
+ *   *rel = ||(K + lambda I) W - Y||_F / ||Y||_F,  Y and W (n x s) host or device.
+ * Synchronises `stream`. */
+adasap_status adasap_residual(adasap_ctx* ctx, const float* Y, const float* W, int s, double* rel,
+                              void* stream);
 
 /* Kernel adjoint for hyperparameter fitting (App. D.1):
  *   d_ell    = sum_c G[:,c]^T (dK/dell)    W[:,c]

@@ -35,7 +35,7 @@ SYMBOLS = ["adasap_default_opts", "adasap_status_string", "adasap_last_error", "
            "adasap_solver_step", "adasap_solver_residual", "adasap_solver_get_w",
            "adasap_solver_scalars", "adasap_solver_end", "adasap_solver_graph_kernels",
            "adasap_solver_diag", "adasap_set_precision",
-           "adasap_kernel_rows_noalloc", "adasap_measure_pipes"]
+           "adasap_kernel_rows_noalloc", "adasap_measure_pipes", "adasap_residual"]
 
 
 class Opts(ctypes.Structure):
@@ -43,7 +43,7 @@ class Opts(ctypes.Structure):
                 ("tol", ctypes.c_double), ("power_iters", ctypes.c_int), ("mu", ctypes.c_double),
                 ("nu", ctypes.c_double), ("precond", ctypes.c_int), ("literal", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("check_every", ctypes.c_int),
-                ("check_rows", ctypes.c_int64), ("eps", ctypes.c_double)]
+                ("check_rows", ctypes.c_int64), ("eps", ctypes.c_double), ("tail_average", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -236,6 +236,17 @@ class Context:
             _stream(stream))
         _check(status, "adasap_solve_scheduled (stage %d)" % st.status_detail)
         return W, tr, st.as_dict()
+
+    def residual(self, Y, W, stream=None):
+        """adasap_residual: ||(K + lambda I) W - Y||_F / ||Y||_F on all rows."""
+        Y2 = Y.reshape(Y.shape[0], -1) if Y.ndim == 1 else Y
+        W2 = W.reshape(W.shape[0], -1) if W.ndim == 1 else W
+        if tuple(Y2.shape) != tuple(W2.shape) or Y2.shape[0] != self.n:
+            raise ValueError("Y and W must both be (n, s) with n = %d" % self.n)
+        rel = ctypes.c_double()
+        _check(_lib.adasap_residual(self.h, _ptr_any(Y2, "Y"), _ptr_any(W2, "W"), Y2.shape[1], ctypes.byref(rel),
+                                    _stream(stream)), "adasap_residual")
+        return rel.value
 
     def predict(self, Xtest, W, stream=None):
         W2 = W if W.dim() == 2 else W.view(-1, 1)

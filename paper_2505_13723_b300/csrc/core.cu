@@ -1028,6 +1028,27 @@ __global__ void k_nesterov(float* __restrict__ W, float* __restrict__ V, float* 
   }
 }
 
+// Tail averaging (Alg. 1 / 2): Wbar += W after each averaged iteration; at the
+// end W = Wbar / count.
+__global__ void k_tail_add(const float* __restrict__ W, float* __restrict__ Wbar, int64_t count) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+    Wbar[e] += W[e];
+}
+__global__ void k_tail_finish(const float* __restrict__ Wbar, float* __restrict__ W, int64_t count, float inv) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+    W[e] = Wbar[e] * inv;
+}
+cudaError_t launch_tail_add(const float* W, float* Wbar, int64_t count, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((count + 255) / 256, 148 * 8);
+  k_tail_add<<<blocks, 256, 0, st>>>(W, Wbar, count);
+  return cudaGetLastError();
+}
+cudaError_t launch_tail_finish(const float* Wbar, float* W, int64_t count, float inv, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((count + 255) / 256, 148 * 8);
+  k_tail_finish<<<blocks, 256, 0, st>>>(Wbar, W, count, inv);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_nesterov(float* W, float* V, float* Z, int64_t count, float beta, float alpha, int literal,
                             cudaStream_t st) {
   const int blocks = (int)std::min<int64_t>((count + 255) / 256, 148 * 16);
@@ -1060,16 +1081,21 @@ cudaError_t launch_scatter(float* W, float* V, float* Z, const int* B, int64_t b
   return cudaGetLastError();
 }
 
-__global__ void k_sum_blocks(const double* __restrict__ parts, int count, double* dst) {
+__global__ void k_sum_blocks(const double* __restrict__ parts, int count, double* dst, int add) {
   __shared__ double red[33];
   double t = 0.0;
   for (int i = threadIdx.x; i < count; i += blockDim.x) t += parts[i];
   t = block_sum(t, red);
-  if (threadIdx.x == 0) *dst = t;
+  if (threadIdx.x == 0) *dst = add ? *dst + t : t;
 }
 
 cudaError_t launch_sum_blocks(const double* parts, int count, double* dst, cudaStream_t st) {
-  k_sum_blocks<<<1, 256, 0, st>>>(parts, count, dst);
+  k_sum_blocks<<<1, 256, 0, st>>>(parts, count, dst, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_blocks_add(const double* parts, int count, double* dst, cudaStream_t st) {
+  k_sum_blocks<<<1, 256, 0, st>>>(parts, count, dst, 1);
   return cudaGetLastError();
 }
 

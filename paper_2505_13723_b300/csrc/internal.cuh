@@ -59,6 +59,8 @@ cudaError_t launch_colsum(const float* X, int64_t n, int d, double* partials, cu
 // x' = kappa (x - mean) / ell, padded to dp; q = ||x'||^2 (FP64 then rounded).
 cudaError_t launch_transform(const float* X, int64_t n, int d, int dp, const double* mean_dev,
                              double scale, float* out, float* q, cudaStream_t st);
+// out[i] = start + i (int32 row indices of a contiguous row range)
+cudaError_t launch_iota32(int* out, int64_t start, int64_t m, cudaStream_t st);
 // int64 indices -> int32, entries outside [0, n) become -1.
 cudaError_t launch_index32(const int64_t* in, int64_t m, int64_t n, int* out, cudaStream_t st);
 
@@ -178,7 +180,10 @@ cudaError_t launch_nesterov(float* W, float* V, float* Z, int64_t count, float b
 cudaError_t launch_scatter(float* W, float* V, float* Z, const int* B, int64_t b, int s,
                            const float* D, float gamma, float alpha, int literal, DevScalars* sc,
                            cudaStream_t st);
+cudaError_t launch_tail_add(const float* W, float* Wbar, int64_t count, cudaStream_t st);
+cudaError_t launch_tail_finish(const float* Wbar, float* W, int64_t count, float inv, cudaStream_t st);
 cudaError_t launch_sum_blocks(const double* parts, int count, double* dst, cudaStream_t st);
+cudaError_t launch_sum_blocks_add(const double* parts, int count, double* dst, cudaStream_t st);   // *dst += sum
 cudaError_t launch_trace(DevScalars* sc, double* trace, cudaStream_t st);
 cudaError_t launch_tick(DevScalars* sc, cudaStream_t st);
 cudaError_t launch_scale_copy(const float* src, float* dst, int64_t count, cudaStream_t st);

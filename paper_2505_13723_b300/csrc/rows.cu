@@ -434,6 +434,18 @@ cudaError_t launch_reduce(const float* part, int nsplit, int64_t m, int na, int 
   return cudaGetLastError();
 }
 
+__global__ void k_iota32(int* __restrict__ out, int64_t start, int64_t m) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (int)(start + i);
+}
+
+cudaError_t launch_iota32(int* out, int64_t start, int64_t m, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((m + 255) / 256, 148 * 8);
+  k_iota32<<<blocks, 256, 0, st>>>(out, start, m);
+  return cudaGetLastError();
+}
+
 __global__ void k_gather(const float* __restrict__ X, const float* __restrict__ q,
                          const int* __restrict__ idx, int64_t m, int dp4, float* __restrict__ out,
                          float* __restrict__ qout) {

@@ -144,6 +144,7 @@ void adasap_default_opts(adasap_opts* o, int64_t n) {
   o->check_every = 10;
   o->check_rows = 65536;
   o->eps = 0.0;
+  o->tail_average = 0;
 }
 
 const char* adasap_status_string(adasap_status s) {
@@ -378,6 +379,52 @@ extern "C" adasap_status adasap_predict(adasap_ctx* c, const float* Xtest, int64
   return ADASAP_OK;
 }
 
+extern "C" adasap_status adasap_residual(adasap_ctx* c, const float* Y, const float* W, int s, double* rel,
+                                         void* stream) {
+  if (!c || !Y || !W || !rel || s < 1 || s > kMaxRhs) return ADASAP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = c->n;
+  const int64_t mb = std::min<int64_t>(n, (int64_t)1 << 16);  // rows per chunk
+  const RowsPlan p = plan_rows(c, mb, n, s);
+  Arena ar;
+  const size_t ns_ = (size_t)n * s;
+  const float* Yd = Y;
+  const float* Wd = W;
+  float* ycopy = nullptr;
+  float* wcopy = nullptr;
+  if (!is_device_ptr(Y)) Yd = ycopy = ar.get<float>(ns_);
+  if (!is_device_ptr(W)) Wd = wcopy = ar.get<float>(ns_);
+  int* idx = ar.get<int>((size_t)mb);
+  float* part = ar.get<float>((size_t)p.nsplit * mb * s);
+  float* res = ar.get<float>((size_t)mb * s);
+  float* wop = p.mrhs ? ar.get<float>((size_t)p.wop_floats) : nullptr;
+  double* sq = ar.get<double>(kReduceBlocks);
+  double* acc = ar.get<double>(2);
+  if (ar.err != cudaSuccess) return ADASAP_ENOMEM;
+  if (ycopy) CT(cudaMemcpyAsync(ycopy, Y, ns_ * sizeof(float), cudaMemcpyHostToDevice, st));
+  if (wcopy) CT(cudaMemcpyAsync(wcopy, W, ns_ * sizeof(float), cudaMemcpyHostToDevice, st));
+  // ||Y||^2 (the reduce writes a copy of Y into a scratch it does not need: chunk by chunk)
+  CT(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
+  for (int64_t i0 = 0; i0 < n; i0 += mb) {
+    const int64_t m = std::min(mb, n - i0);
+    CT(launch_reduce(Yd + i0 * s, 1, m, s, 0, s, res, s, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, sq, st));
+    CT(launch_sum_blocks_add(sq, kReduceBlocks, acc + 1, st));
+  }
+  // ||(K + lambda I) W - Y||^2 over row chunks, each a batched block-row product
+  for (int64_t i0 = 0; i0 < n; i0 += mb) {
+    const int64_t m = std::min(mb, n - i0);
+    CT(launch_iota32(idx, i0, m, st));
+    CT(run_rows_over_x(c, p, c->Xc, c->qc, idx, m, Wd, s, part, 1, st, wop));
+    CT(launch_reduce(part, p.nsplit, m, s, 0, s, res, s, c->lambda, Wd, idx, s, -1.f, Yd, idx, s, sq, st));
+    CT(launch_sum_blocks_add(sq, kReduceBlocks, acc, st));
+  }
+  double h[2];
+  CT(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CT(cudaStreamSynchronize(st));
+  *rel = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : NAN;
+  return ADASAP_OK;
+}
+
 extern "C" adasap_status adasap_hypergrad(adasap_ctx* c, const float* W, const float* G, int s, double* d_ell,
                                           double* d_sigma2, void* stream) {
   if (!c || !W || !G || !d_ell || !d_sigma2 || s < 1 || s > kMaxRhs) return ADASAP_EINVAL;
@@ -454,6 +501,7 @@ struct adasap_solver {
   int* B32 = nullptr;
   float *Om = nullptr, *v0 = nullptr, *XB = nullptr, *qB = nullptr, *R = nullptr, *D = nullptr;
   float* OmN = nullptr;   // Omega of the next iteration, orthonormalised one iteration ahead
+  float* Wbar = nullptr;  // running sum of the tail iterates (opts.tail_average)
   int64_t T_sched = 0;    // iterations of a caller-supplied schedule
   const float* Oms_sched = nullptr;
   float *part1 = nullptr, *part2 = nullptr, *Ysk = nullptr, *a = nullptr, *h = nullptr, *vA = nullptr, *vB = nullptr;
@@ -485,6 +533,7 @@ adasap_status alloc_solver(adasap_solver* S) {
   S->B32 = ar.get<int>(b);
   S->Om = ar.get<float>((size_t)b * rr);
   S->OmN = ar.get<float>((size_t)b * rr);
+  if (S->o.tail_average) S->Wbar = ar.get<float>(ns_);
   S->v0 = ar.get<float>(b);
   S->XB = ar.get<float>((size_t)b * c->dp);
   S->qB = ar.get<float>(b);
@@ -831,8 +880,23 @@ adasap_status solve_loop(adasap_solver* S, float* W, adasap_stats* stats, int T_
   double rel = NAN;
   bool converged = false, checked_last = false;
   int it = 0;
+  const size_t wbytes = (size_t)c->n * S->s * sizeof(float);
+  const int64_t wcount = c->n * (int64_t)S->s;
   CT(cudaEventRecord(c->ev_t0, c->s0));
-  while (it < T_run) {
+  if (o.tail_average) {
+    // Alg. 1 / 2 tail averaging over exactly T_run iterations: mean(W_j, j = ceil(T/2) .. T)
+    const int j0 = (T_run + 1) / 2;
+    if (j0 == 0) CT(cudaMemcpyAsync(S->Wbar, S->W, wbytes, cudaMemcpyDeviceToDevice, c->s0));
+    else CT(cudaMemsetAsync(S->Wbar, 0, wbytes, c->s0));
+    for (it = 1; it <= T_run; ++it) {
+      CT(cudaGraphLaunch(S->exec, c->s0));
+      if (it >= j0) CT(launch_tail_add(S->W, S->Wbar, wcount, c->s0));
+    }
+    it = T_run;
+    S->iters = it;
+    CT(launch_tail_finish(S->Wbar, S->W, wcount, 1.0f / (float)(T_run - j0 + 1), c->s0));
+  }
+  while (!o.tail_average && it < T_run) {
     int k = T_run - it;
     if (!S->sched && o.check_every > 0) k = std::min(k, o.check_every - (it % o.check_every));
     for (int i = 0; i < k; ++i) CT(cudaGraphLaunch(S->exec, c->s0));
@@ -853,12 +917,12 @@ adasap_status solve_loop(adasap_solver* S, float* W, adasap_stats* stats, int T_
   CT(cudaStreamSynchronize(c->s0));
   float ms = 0.f;
   CT(cudaEventElapsedTime(&ms, c->ev_t0, c->ev_t1));
-  if (st == ADASAP_OK && !checked_last && !S->sched) {
+  if (st == ADASAP_OK && !checked_last && !S->sched) {  // (with tail averaging: on the average)
     st = solver_residual(S, &rel, c->s0);
     if (st == ADASAP_OK && o.tol > 0 && rel <= o.tol) converged = true;
   }
   CT(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->s0));
-  CT(cudaMemcpyAsync(W, S->W, (size_t)c->n * S->s * sizeof(float), cudaMemcpyDefault, c->s0));
+  CT(cudaMemcpyAsync(W, S->W, wbytes, cudaMemcpyDefault, c->s0));
   CT(cudaStreamSynchronize(c->s0));
   if (st == ADASAP_OK && c->sc_host->status != 0) st = (adasap_status)c->sc_host->status;
   if (stats) {
@@ -870,7 +934,7 @@ adasap_status solve_loop(adasap_solver* S, float* W, adasap_stats* stats, int T_
     stats->last_rho = c->sc_host->rho;
     stats->status_detail = c->sc_host->detail;
   }
-  if (st == ADASAP_OK && !S->sched && o.tol > 0 && !converged) st = ADASAP_ENOTCONVERGED;
+  if (st == ADASAP_OK && !S->sched && !o.tail_average && o.tol > 0 && !converged) st = ADASAP_ENOTCONVERGED;
   CT(cudaEventRecord(c->ev_out, c->s0));
   CT(cudaStreamWaitEvent(us, c->ev_out, 0));
   return st;

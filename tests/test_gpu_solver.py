@@ -22,6 +22,7 @@ import torch
 
 from oracle import adasap as OA
 from oracle import gp
+from oracle import kernels as OK
 from oracle import rng as OR
 from paper_2505_13723_b300 import synth
 
@@ -72,6 +73,21 @@ def test_scheduled_iterations_match_oracle_small(lib, T, prec):
     W, tr, Wref, rec = _scheduled_case(lib, P, T, b=200, r=32, prec=prec)
     _check_trace(tr, rec, 1e-4)
     assert _rel(W, Wref) < 1e-4
+
+
+@pytest.mark.parametrize("T", [1, 6, 7])
+def test_scheduled_tail_average_matches_oracle(lib, T):
+    """opts.tail_average: mean(W_j, j = ceil(T/2) .. T) (Alg. 1 / 2) against the oracle's."""
+    P = synth.small()
+    n = P.X.shape[0]
+    B, Om, v0 = synth.injected_schedule(n, 200, 32, T, seed=31)
+    ctx = lib.Context(P.X, P.kernel, P.ell, P.sigma2, P.lam)
+    opts = lib.default_opts(n, b=200, r=32, tail_average=1)
+    W, tr, st = ctx.solve_scheduled(torch.from_numpy(P.Y).cuda(), torch.from_numpy(B).cuda(),
+                                    torch.from_numpy(Om).cuda(), torch.from_numpy(v0).cuda(), opts=opts)
+    Wref = OA.adasap(P.X.astype(np.float64), P.Y.astype(np.float64), P.kernel, P.ell, P.sigma2, P.lam, 200, 32, T,
+                     synth.schedule_fn(B, Om, v0), tail_average=True)
+    assert _rel(W.cpu().numpy(), Wref) < 1e-4
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -209,3 +225,37 @@ def test_taxi_scale_block_rows_and_iterations(lib):
     assert d["status"] == 0 and d["tc_err"] == 0 and d["t"] == 2 and d["eta"] > 0
     assert 0.0 < sol.residual() < 1.0
     sol.close()
+
+
+@pytest.mark.parametrize("kern,s,host", [(0, 1, False), (1, 3, True), (2, 1, True)])
+def test_exact_residual_matches_oracle(lib, kern, s, host):
+    """adasap_residual: ||(K + lambda I) W - Y|| / ||Y|| on all rows (the measure of Sec. 5)."""
+    P = synth.small(n=2000)
+    rng = np.random.default_rng(kern + 10 * s)
+    Y = rng.standard_normal((2000, s)).astype(np.float32)
+    W = rng.standard_normal((2000, s)).astype(np.float32)
+    ctx = lib.Context(P.X, kern, P.ell, P.sigma2, P.lam)
+    args = (Y, W) if host else (torch.from_numpy(Y).cuda(), torch.from_numpy(W).cuda())
+    rel = ctx.residual(*args)
+    ref = gp.rel_residual(P.X.astype(np.float64), W, Y, kern, P.ell, P.sigma2, P.lam)
+    assert abs(rel - ref) <= 1e-5 * ref
+    assert ctx.residual(Y, np.zeros_like(W)) == pytest.approx(1.0, rel=1e-12)
+
+
+def test_exact_residual_spans_row_chunks(lib):
+    """n = 70,000 rows (two chunks of the batched launch, the second ragged) with
+    W non-zero on 64 rows, so that the oracle's K(X, X) W = K(X, X_nz) W_nz is
+    exact and cheap."""
+    n, d = 70000, 4
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    Y = rng.standard_normal((n, 1)).astype(np.float32)
+    nz = np.sort(rng.choice(n, 64, replace=False))
+    W = np.zeros((n, 1), np.float32)
+    W[nz] = 10 * rng.standard_normal((64, 1))
+    ctx = lib.Context(X, 0, 1.0, 1.0, 1e-2)
+    rel = ctx.residual(torch.from_numpy(Y).cuda(), torch.from_numpy(W).cuda())
+    Xd = X.astype(np.float64)
+    R = OK.kernel_apply(Xd, Xd[nz], W[nz].astype(np.float64), 0, 1.0, 1.0) + 1e-2 * W - Y
+    ref = float(np.linalg.norm(R) / np.linalg.norm(Y.astype(np.float64)))
+    assert abs(rel - ref) <= 1e-5 * ref
