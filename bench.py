@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-tol-run", action="store_true")
     p.add_argument("--no-multi-rhs", action="store_true", help="skip the many-right-hand-sides comparison")
+    p.add_argument("--no-batched", action="store_true", help="skip the uneven batch of independent systems")
+    p.add_argument("--batched-iters", type=int, default=40, help="iterations of the batched-systems timing")
     p.add_argument("--n", type=int, default=1 << 20, help="rows of the workload (default: full size)")
     p.add_argument("--kernel-launches", type=int, default=10, help="timed launches of the Step I kernel alone")
     p.add_argument("--tol-iters", type=int, default=6000, help="iteration cap of the time-to-1e-3 solves")
@@ -362,6 +364,39 @@ def run_ours(args, rank, world, dist):
                  "ms_per_iteration_fp32_single_rhs": fp32_single,
                  "speedup_vs_64_fp32_single_rhs_solves": 64.0 * fp32_single / mixed_batched}
 
+    # ---- the uneven batch: 48 independent Matern-5/2 systems (n log-uniform in [4096, 65536],
+    # b = n/50, r = 50) iterated together by adasap_solve_batched, against the same systems
+    # solved one after another (device time per iteration of all 48)
+    batched = None
+    if rank == 0 and not args.no_batched:
+        from paper_2505_13723_b300 import synth
+        systems = synth.bo_systems()
+        ctxs = [lib.Context(torch.from_numpy(Q.X).to(dev), Q.kernel, Q.ell, Q.sigma2, Q.lam) for Q in systems]
+        Ys = [torch.from_numpy(Q.Y).to(dev) for Q in systems]
+        it_b = args.batched_iters
+        bopts = [lib.default_opts(Q.X.shape[0], b=Q.b, r=Q.r, seed=40 + k, check_every=0, max_iters=it_b)
+                 for k, Q in enumerate(systems)]
+        _, bst, bstatus = lib.solve_batched(ctxs, Ys, opts=bopts)
+        t_batch = max(x["seconds"] for x in bst) / it_b
+        it_s = max(3, it_b // 4)
+        t_seq = 0.0
+        for k, (Q, cq, Yq) in enumerate(zip(systems, ctxs, Ys)):
+            _, sst, _ = cq.solve(Yq, opts=lib.default_opts(Q.X.shape[0], b=Q.b, r=Q.r, seed=40 + k,
+                                                            check_every=0, max_iters=it_s))
+            t_seq += sst["seconds"] / it_s
+        for cq in ctxs:
+            cq.close()
+        ent_b = sum(Q.b * Q.X.shape[0] + 11 * Q.b * Q.b for Q in systems)
+        batched = {"workload": "bo: 48 systems, n log-uniform in [4096, 65536] (sum %d), d in {4, 8, 12}, "
+                               "X~U[-1,1]^d, Matern-5/2 ell~U[0.2,1], lambda=1e-3, b=n/50, r=50"
+                               % sum(Q.X.shape[0] for Q in systems),
+                   "ms_per_iteration_batched": 1e3 * t_batch,
+                   "ms_per_iteration_one_after_another": 1e3 * t_seq,
+                   "speedup": t_seq / t_batch,
+                   "gentries_per_s_batched": ent_b / t_batch / 1e9,
+                   "entries_per_iteration": ent_b, "status": bstatus,
+                   "iterations_timed": {"batched": it_b, "one_after_another": it_s}}
+
     # ---- end to end through the C-ABI with host buffers
     e2e = None
     if rank == 0:
@@ -420,6 +455,7 @@ def run_ours(args, rank, world, dist):
             "clocks": clk.summary(), "kernel_clocks": kclk.summary(),
             "time_to_tol": tol_run,
             "multi_rhs": multi,
+            "batched_systems": batched,
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
             "solver_state": {"rel_resid_after": rel, "eta": eta, "rho": rho, "status": status,
                              "jacobi_sweeps": diag["jacobi_sweeps"], "chol_retries": diag["chol_retries"],

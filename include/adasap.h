@@ -62,7 +62,8 @@ typedef enum { ADASAP_RBF = 0, ADASAP_MATERN32 = 1, ADASAP_MATERN52 = 2 } adasap
  *   ADASAP_PREC_FP32    FP32 CUDA-core distances and epilogue
  *   ADASAP_PREC_TF32X3  distances on the tensor cores (tcgen05, TF32 hi/lo split
  *                       with three products; FP32 epilogue); needs d <= 30.
- * Products with more than one right-hand side use the FP32 CUDA-core kernels. */
+ * With ADASAP_PREC_TF32X3, products with more than one right-hand side use the
+ * multi-RHS tensor-core kernel (W split into TF32 hi/lo as well). */
 typedef enum { ADASAP_PREC_FP32 = 0, ADASAP_PREC_TF32X3 = 1 } adasap_precision;
 
 /* Options of adasap_solve.  adasap_default_opts fills the paper's defaults. */
@@ -164,6 +165,25 @@ adasap_status adasap_solve_scheduled(adasap_ctx* ctx, const float* Y, int s,
                                      const adasap_opts* opts, const int64_t* B_sched,
                                      const float* Omega_sched, const float* v0_sched, int T,
                                      float* W, double* trace, adasap_stats* stats, void* stream);
+
+/* Many independent systems of uneven size solved together (for example the
+ * GP models of a Bayesian-optimisation campaign, Sec. 5.3).  System i is
+ * ctxs[i] with Y[i] and W[i] (n_i x s, host or device; W[i] holds W_0 on entry
+ * and the returned iterate on exit) and its own options opts[i] (Alg. 2 as in
+ * adasap_solve; tail_average must be 0).  One CUDA graph holds one iteration of
+ * every system still running, each system on its context's streams; the Step I
+ * products and the K_BB a products of Alg. 5 of all systems that use the
+ * single-right-hand-side tensor-core kernel (s = 1, ADASAP_PREC_TF32X3, Nystrom
+ * preconditioner) run as one grouped persistent launch per kernel kind, with a
+ * column split chosen before the first iteration by timing candidates.  A
+ * system leaves the batch (and the graph is re-captured without it) when a
+ * residual check meets opts[i].tol or after opts[i].max_iters iterations.
+ * stats (nsys entries, may be NULL) as in adasap_solve, with seconds = device
+ * time from the start of the batch until the system left it.  The contexts
+ * must be distinct.  Returns the first error of any system, else
+ * ADASAP_ENOTCONVERGED if a system with tol > 0 missed it, else ADASAP_OK. */
+adasap_status adasap_solve_batched(int nsys, adasap_ctx* const* ctxs, const float* const* Y, int s,
+                                   const adasap_opts* opts, float* const* W, adasap_stats* stats, void* stream);
 
 /* Incremental form of adasap_solve (same arithmetic), for callers that step
  * the solver themselves or time it.  One active solver per context: the

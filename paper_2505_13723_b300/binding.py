@@ -35,7 +35,8 @@ SYMBOLS = ["adasap_default_opts", "adasap_status_string", "adasap_last_error", "
            "adasap_solver_step", "adasap_solver_residual", "adasap_solver_get_w",
            "adasap_solver_scalars", "adasap_solver_end", "adasap_solver_graph_kernels",
            "adasap_solver_diag", "adasap_set_precision",
-           "adasap_kernel_rows_noalloc", "adasap_measure_pipes", "adasap_residual"]
+           "adasap_kernel_rows_noalloc", "adasap_measure_pipes", "adasap_residual",
+           "adasap_solve_batched"]
 
 
 class Opts(ctypes.Structure):
@@ -90,6 +91,11 @@ _lib.adasap_solver_graph_kernels.argtypes = [_P, ctypes.POINTER(ctypes.c_int)]
 _lib.adasap_solver_graph_kernels.restype = ctypes.c_int
 _lib.adasap_solver_diag.argtypes = [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int, _P]
 _lib.adasap_solver_diag.restype = ctypes.c_int
+_lib.adasap_residual.argtypes = [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]
+_lib.adasap_residual.restype = ctypes.c_int
+_lib.adasap_solve_batched.argtypes = [ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int,
+                                      ctypes.POINTER(Opts), ctypes.POINTER(_P), ctypes.POINTER(Stats), _P]
+_lib.adasap_solve_batched.restype = ctypes.c_int
 _lib.adasap_solver_end.argtypes = [_P]
 _lib.adasap_solver_end.restype = None
 for _f in ["adasap_solver_begin", "adasap_solver_step", "adasap_solver_residual", "adasap_solver_get_w",
@@ -320,6 +326,33 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def solve_batched(contexts, Ys, opts=None, Ws=None, stream=None):
+    """adasap_solve_batched over independent systems (contexts[i], Ys[i]); Ys / Ws host or
+    device (n_i x s).  opts: list of Opts (default: default_opts(n_i)).  Returns
+    (Ws, list of stats dicts, status)."""
+    k = len(contexts)
+    if len(Ys) != k or k == 0:
+        raise ValueError("one Y per context")
+    Y2 = [Y.reshape(Y.shape[0], -1) if Y.ndim == 1 else Y for Y in Ys]
+    s = Y2[0].shape[1]
+    for ctx, Y in zip(contexts, Y2):
+        if Y.shape[0] != ctx.n or Y.shape[1] != s:
+            raise ValueError("Y_i must be (n_i, s) with one s for all systems")
+    if opts is None:
+        opts = [default_opts(ctx.n) for ctx in contexts]
+    if Ws is None:
+        Ws = [torch.zeros(ctx.n, s, device="cuda", dtype=torch.float32) if isinstance(Y, torch.Tensor)
+              else np.zeros((ctx.n, s), dtype=np.float32) for ctx, Y in zip(contexts, Y2)]
+    ctx_arr = (ctypes.c_void_p * k)(*[ctx.h.value for ctx in contexts])
+    y_arr = (ctypes.c_void_p * k)(*[_ptr_any(Y, "Y").value for Y in Y2])
+    w_arr = (ctypes.c_void_p * k)(*[_ptr_any(W, "W").value for W in Ws])
+    o_arr = (Opts * k)(*opts)
+    st_arr = (Stats * k)()
+    status = _lib.adasap_solve_batched(k, ctx_arr, y_arr, s, o_arr, w_arr, st_arr, _stream(stream))
+    _check(status, "adasap_solve_batched", allow=(7,))
+    return Ws, [st.as_dict() for st in st_arr], status
 
 
 def measure_pipes(stream=None):

@@ -65,6 +65,34 @@ cudaError_t launch_iota32(int* out, int64_t start, int64_t m, cudaStream_t st);
 cudaError_t launch_index32(const int64_t* in, int64_t m, int64_t n, int* out, cudaStream_t st);
 
 // ---- tensor-core block-row product (rows_tc.cu) ------------------------------------
+// One block-row product on the tensor cores (rows_tc.cu): rows (x', q) with an
+// optional row index, the column operands in the split canonical layout, w.
+struct TcArgs {
+  const float* xr;   // rows, x' form (m rows of stride dp), or gathered block
+  const float* qr;
+  const int* ridx;   // row -> source row (NULL: identity); < 0 marks an invalid row
+  int64_t m;
+  int dp, d;
+  const float* bhi;  // columns: split operands in the canonical layout (npad rows)
+  const float* blo;
+  int64_t ncols;
+  int self_mode;     // 1: column j is the same point as the row's source index
+  const float* w;
+  int64_t ldw;
+  float* part;       // nsplit x m
+  int64_t cps;       // columns per split (multiple of 128)
+  int nsplit;
+  float sigma2;
+  int* err;          // set to 1 on a wait timeout
+};
+TcArgs make_tc_args(int d, const float* xr, const float* qr, const int* ridx, int64_t m, int dp, const float* bhi,
+                    const float* blo, int64_t ncols, int self_mode, const float* w, int64_t ldw, float* part,
+                    int nsplit, float sigma2, int* err);
+int64_t tc_items(const TcArgs& a);   // (row tile, split) items of one product
+// Several independent products (grp[g], device) in one persistent launch of at
+// most `ctas` CTAs; gstart (device, ngrp + 1) is the prefix sum of tc_items.
+cudaError_t launch_rows_tc_grouped(int kern, int kp, const TcArgs* grp, const int64_t* gstart, int ngrp,
+                                   int64_t nitems, int* err, int ctas, cudaStream_t st);
 // K of the augmented MMA operands (16 or 32; 0 if d + 2 > 32) and padded row count.
 int tc_kp(int d);
 int64_t tc_npad(int64_t n);

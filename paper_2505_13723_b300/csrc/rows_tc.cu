@@ -8,22 +8,26 @@
 // MMAs, hi.hi + hi.lo + lo.hi (the dropped lo.lo term is 2^-22 relative); a
 // row paired with its own column (the diagonal of K_BB / K_Bn) gets u = 0.
 //
-// CTA = 128 rows x a column range, 384 threads:
+// CTA = 128 rows x a column range, 640 threads, persistent over (row tile,
+// column split) items:
 //   warp 0       producer: bulk copies (cp.async.bulk, the TMA engine) of
-//                128-column operand tiles into a 2-stage shared-memory ring
+//                128-column operand tiles into a 4-stage shared-memory ring,
+//                and the w values of each tile into a 2-stage w buffer
 //   warp 1       owns the TMEM allocation (2 x 128 FP32 accumulator columns)
 //                and issues the MMAs from one thread (tcgen05.mma kind::tf32,
 //                M = 128, N = 128, K = 8 per instruction)
-//   warps 4..11  epilogue: two warpgroups, each tcgen05.ld-ing 64 columns of
-//                its 128 TMEM lanes (one row per thread), applying the RBF /
-//                Matern epilogue and contracting with w in registers
+//   warps 4..19  epilogue: warp w tcgen05.ld-s 32 rows (TMEM lane quadrant
+//                w % 4) x 32 columns of the tile, applies the RBF / Matern
+//                epilogue and contracts with w in registers
 // Operands live in shared memory in the no-swizzle K-major canonical layout:
 // 8-row core groups of 16-byte K chunks (LBO = 128 B between K chunks,
 // SBO = 32 * KP B between 8-row groups).  The column operands are prebuilt in
 // that layout in global memory (padded to a multiple of 128 rows), so a tile
 // is one contiguous copy.  Every mbarrier wait is bounded: on timeout the CTA
 // raises an error flag, drains its own copies and MMAs, frees TMEM and writes
-// NaN partials.
+// NaN partials.  The grouped form takes the items of several independent
+// products (for example the block-row products of many GP systems) in one
+// launch.
 #include <algorithm>
 
 #include "tc_ptx.cuh"
@@ -47,25 +51,6 @@ struct TcSmem {
   static constexpr size_t bytes = ops_bytes + w_bytes + red_bytes + 32 * sizeof(uint64_t) + 64 + 1024;
 };
 
-struct TcArgs {
-  const float* xr;   // rows, x' form (m rows of stride dp), or gathered block
-  const float* qr;
-  const int* ridx;   // row -> source row (NULL: identity); < 0 marks an invalid row
-  int64_t m;
-  int dp, d;
-  const float* bhi;  // columns: split operands in the canonical layout (npad rows)
-  const float* blo;
-  int64_t ncols;
-  int self_mode;     // 1: column j is the same point as the row's source index
-  const float* w;
-  int64_t ldw;
-  float* part;       // nsplit x m
-  int64_t cps;       // columns per split (multiple of 128)
-  int nsplit;
-  float sigma2;
-  int* err;          // set to 1 on a wait timeout
-};
-
 // Per-entry epilogue on the scaled distance v = log2(e)^2 u (M32, M52) or u (RBF),
 // accumulating k(u) w / sigma2 into acc; wl = w / log2(e), w3 = w / (3 log2(e)^2):
 //   RBF  k = 2^-u
@@ -81,8 +66,11 @@ __device__ __forceinline__ float tc_term(float v, float w, float wl, float w3, f
   return fmaf(e, fmaf(ap, fmaf(ap, w3, wl), w), acc);
 }
 
-template <int KERN, int KP>
-__global__ void __launch_bounds__(kTcThreadsV2, 1) k_rows_tc(TcArgs a) {
+// GROUPED: the items of several independent products (one TcArgs each; item
+// ranges gstart[g] .. gstart[g + 1]) in one persistent launch.
+template <int KERN, int KP, bool GROUPED>
+__global__ void __launch_bounds__(kTcThreadsV2, 1)
+    k_rows_tc(TcArgs a0, const TcArgs* __restrict__ grp, const int64_t* __restrict__ gstart, int ngrp) {
   using L = TcSmem<KP>;
   constexpr int OPF = L::OPF;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -103,8 +91,7 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1) k_rows_tc(TcArgs a) {
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t rtiles = (a.m + kTcM - 1) / kTcM;
-  const int64_t nitems = rtiles * a.nsplit;
+  const int64_t nitems = GROUPED ? gstart[ngrp] : (a0.m + kTcM - 1) / kTcM * a0.nsplit;
   // the row operand carries log2(e)^2 for the Matern kernels (see tc_term)
   const float rscale = (KERN == ADASAP_RBF) ? 1.0f : kLog2e * kLog2e;
 
@@ -139,7 +126,19 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1) k_rows_tc(TcArgs a) {
   // L2.  The pipeline phases run on across items (gt counts this CTA's tiles).
   uint32_t gt = 0, ndrain = 0;
   for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
-    const int64_t rtile = item % rtiles, split = item / rtiles;
+    int sys = 0;
+    if (GROUPED) {  // the product this item belongs to: last g with gstart[g] <= item
+      int hi = ngrp - 1;
+      while (sys < hi) {
+        const int mid = (sys + hi + 1) >> 1;
+        if (gstart[mid] <= item) sys = mid;
+        else hi = mid - 1;
+      }
+    }
+    const TcArgs& a = GROUPED ? grp[sys] : a0;
+    const int64_t li = GROUPED ? item - gstart[sys] : item;
+    const int64_t rtiles = (a.m + kTcM - 1) / kTcM;
+    const int64_t rtile = li % rtiles, split = li / rtiles;
     const int64_t row0 = rtile * kTcM;
     const int64_t c0 = split * a.cps;
     const int64_t c1 = min(a.ncols, c0 + a.cps);
@@ -345,7 +344,7 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1) k_rows_tc(TcArgs a) {
     __syncthreads();
     tc_fence_after();
   }
-  if (warp == 0 && lane == 0 && *abort_flag) tc_note_timeout(a.err, 9);
+  if (warp == 0 && lane == 0 && *abort_flag) tc_note_timeout(a0.err, 9);
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols) : "memory");
@@ -398,8 +397,10 @@ static int g_tc_slots = 0;  // resident CTAs of k_rows_tc per SM x SMs
 
 template <int KERN, int KP>
 static cudaError_t tc_setup() {
-  return cudaFuncSetAttribute(k_rows_tc<KERN, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)std::max<size_t>(TcSmem<KP>::bytes, 80 * 1024));
+  const int bytes = (int)std::max<size_t>(TcSmem<KP>::bytes, 80 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_rows_tc<KERN, KP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_rows_tc<KERN, KP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 cudaError_t tc_init() {
@@ -408,7 +409,7 @@ cudaError_t tc_init() {
       (e = tc_setup<1, 32>()) || (e = tc_setup<2, 32>()))
     return e;
   int per_sm = 0, dev = 0, sms = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_tc<1, 16>, kTcThreadsV2,
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_tc<1, 16, false>, kTcThreadsV2,
                                                          std::max<size_t>(TcSmem<16>::bytes, 80 * 1024))))
     return e;
   if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
@@ -443,17 +444,33 @@ int tc_nsplit(int64_t m, int64_t ncols, int max_ctas) {
   return (int)best;
 }
 
-template <int KERN, int KP>
-static cudaError_t launch_tc_k(const TcArgs& a, int ctas, cudaStream_t st) {
-  k_rows_tc<KERN, KP><<<ctas, kTcThreadsV2, std::max<size_t>(TcSmem<KP>::bytes, 80 * 1024), st>>>(a);
+template <int KERN, int KP, bool G>
+static cudaError_t launch_tc_k(const TcArgs& a, const TcArgs* grp, const int64_t* gstart, int ngrp, int ctas,
+                               cudaStream_t st) {
+  k_rows_tc<KERN, KP, G><<<ctas, kTcThreadsV2, std::max<size_t>(TcSmem<KP>::bytes, 80 * 1024), st>>>(a, grp, gstart,
+                                                                                                     ngrp);
   return cudaGetLastError();
 }
 
-cudaError_t launch_rows_tc(int kern, int d, const float* xr, const float* qr, const int* ridx, int64_t m, int dp,
-                           const float* bhi, const float* blo, int64_t ncols, int self_mode, const float* w,
-                           int64_t ldw, float* part, int nsplit, float sigma2, int* err, cudaStream_t st,
-                           int max_ctas) {
-  if (m <= 0 || ncols <= 0) return cudaSuccess;
+template <bool G>
+static cudaError_t launch_tc_any(int kern, int kp, const TcArgs& a, const TcArgs* grp, const int64_t* gstart,
+                                 int ngrp, int ctas, cudaStream_t st) {
+  if (kp == 16) {
+    if (kern == 0) return launch_tc_k<0, 16, G>(a, grp, gstart, ngrp, ctas, st);
+    if (kern == 1) return launch_tc_k<1, 16, G>(a, grp, gstart, ngrp, ctas, st);
+    return launch_tc_k<2, 16, G>(a, grp, gstart, ngrp, ctas, st);
+  }
+  if (kp == 32) {
+    if (kern == 0) return launch_tc_k<0, 32, G>(a, grp, gstart, ngrp, ctas, st);
+    if (kern == 1) return launch_tc_k<1, 32, G>(a, grp, gstart, ngrp, ctas, st);
+    return launch_tc_k<2, 32, G>(a, grp, gstart, ngrp, ctas, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+TcArgs make_tc_args(int d, const float* xr, const float* qr, const int* ridx, int64_t m, int dp, const float* bhi,
+                    const float* blo, int64_t ncols, int self_mode, const float* w, int64_t ldw, float* part,
+                    int nsplit, float sigma2, int* err) {
   TcArgs a;
   a.xr = xr; a.qr = qr; a.ridx = ridx; a.m = m; a.dp = dp; a.d = d;
   a.bhi = bhi; a.blo = blo; a.ncols = ncols; a.self_mode = self_mode;
@@ -461,21 +478,28 @@ cudaError_t launch_rows_tc(int kern, int d, const float* xr, const float* qr, co
   const int64_t tiles = (ncols + kTcN - 1) / kTcN;
   a.cps = (tiles + nsplit - 1) / nsplit * kTcN;
   a.nsplit = nsplit;
-  const int64_t nitems = (m + kTcM - 1) / kTcM * (int64_t)nsplit;
+  return a;
+}
+
+int64_t tc_items(const TcArgs& a) { return (a.m + kTcM - 1) / kTcM * (int64_t)a.nsplit; }
+
+cudaError_t launch_rows_tc(int kern, int d, const float* xr, const float* qr, const int* ridx, int64_t m, int dp,
+                           const float* bhi, const float* blo, int64_t ncols, int self_mode, const float* w,
+                           int64_t ldw, float* part, int nsplit, float sigma2, int* err, cudaStream_t st,
+                           int max_ctas) {
+  if (m <= 0 || ncols <= 0) return cudaSuccess;
+  const TcArgs a = make_tc_args(d, xr, qr, ridx, m, dp, bhi, blo, ncols, self_mode, w, ldw, part, nsplit, sigma2, err);
   const int slots = (max_ctas > 0 && max_ctas < tc_slots()) ? max_ctas : tc_slots();
-  const int ctas = (int)std::min<int64_t>(nitems, slots);
-  const int kp = tc_kp(d);
-  if (kp == 16) {
-    if (kern == 0) return launch_tc_k<0, 16>(a, ctas, st);
-    if (kern == 1) return launch_tc_k<1, 16>(a, ctas, st);
-    return launch_tc_k<2, 16>(a, ctas, st);
-  }
-  if (kp == 32) {
-    if (kern == 0) return launch_tc_k<0, 32>(a, ctas, st);
-    if (kern == 1) return launch_tc_k<1, 32>(a, ctas, st);
-    return launch_tc_k<2, 32>(a, ctas, st);
-  }
-  return cudaErrorInvalidValue;
+  const int ctas = (int)std::min<int64_t>(tc_items(a), slots);
+  return launch_tc_any<false>(kern, tc_kp(d), a, nullptr, nullptr, 0, ctas, st);
+}
+
+cudaError_t launch_rows_tc_grouped(int kern, int kp, const TcArgs* grp, const int64_t* gstart, int ngrp,
+                                   int64_t nitems, int* err, int ctas, cudaStream_t st) {
+  if (ngrp < 1 || nitems <= 0) return cudaSuccess;
+  TcArgs a0 = {};
+  a0.err = err;
+  return launch_tc_any<true>(kern, kp, a0, grp, gstart, ngrp, (int)std::min<int64_t>(nitems, ctas), st);
 }
 
 }  // namespace adasap

@@ -592,6 +592,16 @@ adasap_status alloc_solver(adasap_solver* S) {
   return ar.err == cudaSuccess ? ADASAP_OK : ADASAP_ENOMEM;
 }
 
+// K_BB-shaped product operands: rows and columns both the gathered block
+RowsArgs block_args(adasap_solver* S) {
+  RowsArgs kb;
+  kb.xr = S->XB; kb.qr = S->qB; kb.ridx = nullptr; kb.m = S->b;
+  kb.xc = S->XB; kb.qc = S->qB; kb.ncols = S->b;
+  kb.part = S->part2; kb.cps = 0; kb.sigma2 = S->c->sigma2;
+  kb.w = nullptr; kb.ldw = 1;
+  return kb;
+}
+
 // Draw Omega of iteration t + offset (t = the device counter) into OmN and
 // orthonormalise it (Alg. 2 Step II with reading R2: thin QR).
 cudaError_t next_omega(adasap_solver* S, int offset, cudaStream_t st) {
@@ -606,127 +616,195 @@ cudaError_t next_omega(adasap_solver* S, int offset, cudaStream_t st) {
   return launch_orthonormalize(S->cb, S->OmN, S->Ysk, c->sc, st);
 }
 
-// Record one ADASAP iteration on s0 (forking to s1) into S->graph.
-cudaError_t capture_iteration(adasap_solver* S, const int64_t* Bs, const float* Oms, const float* v0s, double* trace) {
+// ---- one iteration, recorded in phases ---------------------------------------
+// The phases end where a batch of independent systems meets for a grouped
+// launch: before Step I and before each K_BB a product of Alg. 5.  Each phase
+// records on the system's own streams (s0, forking to s1 and joining back).
+#define KR(x)                              \
+  do {                                     \
+    const cudaError_t e_ = (x);            \
+    if (e_ != cudaSuccess) return e_;      \
+  } while (0)
+
+// sample, gather, sketch and Gram matrices; fork the factorisation branch to s1
+cudaError_t rec_head(adasap_solver* S, const int64_t* Bs, const float* v0s) {
   adasap_ctx* c = S->c;
   cudaStream_t s0 = c->s0, s1 = c->s1;
   const int64_t n = c->n, b = S->b;
-  const int s = S->s, r = S->r;
-  const double lam = c->lambda;
+  const int r = S->r;
   CoreBufs& cb = S->cb;
-  cudaError_t e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) return e;
-  cudaError_t ce = cudaSuccess;
-  auto K = [&](cudaError_t x) {
-    if (ce == cudaSuccess && x != cudaSuccess) ce = x;
-  };
   const long long* tdev = &c->sc->t;
   // sample B, Omega, v0 (Alg. 2; Alg. 5)
   // (Omega_t was drawn and orthonormalised one iteration ahead, into OmN)
   if (S->sched) {
-    K(launch_copy_schedule(Bs, nullptr, v0s, tdev, n, b, r, S->B32, S->Om, S->v0, c->sc, s0));
+    KR(launch_copy_schedule(Bs, nullptr, v0s, tdev, n, b, r, S->B32, S->Om, S->v0, c->sc, s0));
   } else {
-    K(launch_sample_block(S->o.seed, tdev, 0, n, b, 1, S->B32, nullptr, s0));
-    K(launch_normals(S->o.seed, tdev, 0, b, 3, 1.0f, S->v0, s0));
+    KR(launch_sample_block(S->o.seed, tdev, 0, n, b, 1, S->B32, nullptr, s0));
+    KR(launch_normals(S->o.seed, tdev, 0, b, 3, 1.0f, S->v0, s0));
   }
-  if (!S->identity) K(cudaMemcpyAsync(S->Om, S->OmN, (size_t)b * r * sizeof(float), cudaMemcpyDeviceToDevice, s0));
-  K(launch_gather(c->Xc, c->qc, S->B32, b, c->dp, S->XB, S->qB, s0));
-  RowsArgs kb;
-  kb.xr = S->XB; kb.qr = S->qB; kb.ridx = nullptr; kb.m = b;
-  kb.xc = S->XB; kb.qc = S->qB; kb.ncols = b;
-  kb.part = S->part2; kb.cps = 0; kb.sigma2 = c->sigma2;
+  if (!S->identity) KR(cudaMemcpyAsync(S->Om, S->OmN, (size_t)b * r * sizeof(float), cudaMemcpyDeviceToDevice, s0));
+  KR(launch_gather(c->Xc, c->qc, S->B32, b, c->dp, S->XB, S->qB, s0));
   if (!S->identity) {
     // whole-GPU part of Steps II-III: sketch K_BB Omega and its Gram matrices
     if (S->sk_tc) {
-      K(launch_build_tc(c->Xc, c->qc, S->B32, b, c->d, c->dp, S->XBhi, S->XBlo, s0));
+      KR(launch_build_tc(c->Xc, c->qc, S->B32, b, c->d, c->dp, S->XBhi, S->XBlo, s0));
       const int64_t wf = tc_mrhs_wfloats(b, r);
-      K(launch_build_w_tc(S->Om, r, b, r, 3, S->wsk, S->wsk + wf, s0));
-      K(launch_rows_tc_mrhs(c->kern, c->d, S->XB, S->qB, nullptr, b, c->dp, S->XBhi, S->XBlo, b, 1, S->wsk,
-                            S->wsk + wf, r, 3, S->part2, S->ns_sk, c->sigma2, c->err_dev, s0));
+      KR(launch_build_w_tc(S->Om, r, b, r, 3, S->wsk, S->wsk + wf, s0));
+      KR(launch_rows_tc_mrhs(c->kern, c->d, S->XB, S->qB, nullptr, b, c->dp, S->XBhi, S->XBlo, b, 1, S->wsk,
+                             S->wsk + wf, r, 3, S->part2, S->ns_sk, c->sigma2, c->err_dev, s0));
     } else {
-      kb.w = S->Om; kb.ldw = r;
-      K(launch_rows(c->kern, c->dp, kb, r, S->ns_sk, false, s0));
+      RowsArgs kb = block_args(S);
+      kb.w = S->Om;
+      kb.ldw = r;
+      KR(launch_rows(c->kern, c->dp, kb, r, S->ns_sk, false, s0));
     }
-    K(launch_reduce(S->part2, S->ns_sk, b, r, 0, r, S->Ysk, r, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0,
-                    nullptr, s0));
-    K(launch_nystrom_grams(cb, S->Om, S->Ysk, s0));
+    KR(launch_reduce(S->part2, S->ns_sk, b, r, 0, r, S->Ysk, r, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0,
+                     nullptr, s0));
+    KR(launch_nystrom_grams(cb, S->Om, S->Ysk, s0));
   }
-  K(cudaEventRecord(c->ev_fork, s0));
-  K(cudaStreamWaitEvent(s1, c->ev_fork, 0));
+  KR(cudaEventRecord(c->ev_fork, s0));
+  KR(cudaStreamWaitEvent(s1, c->ev_fork, 0));
   // branch 1: the factorisations of Alg. 4 and the Woodbury factor (App. C.2)
   if (!S->identity) {
-    K(launch_nystrom_core(cb, S->eps, lam, c->sc, S->Om, S->Ysk, s1));
-    K(launch_woodbury_factor(cb, lam, c->sc, s1));
+    KR(launch_nystrom_core(cb, S->eps, c->lambda, c->sc, S->Om, S->Ysk, s1));
+    KR(launch_woodbury_factor(cb, c->lambda, c->sc, s1));
     // Omega of iteration t + 1 and its thin QR, off the critical path (the sketch
     // buffer serves as scratch: the Nystrom core is done with it)
-    K(next_omega(S, 1, s1));
+    KR(next_omega(S, 1, s1));
   }
-  if (S->tc_pw && !S->sk_tc) K(launch_build_tc(c->Xc, c->qc, S->B32, b, c->d, c->dp, S->XBhi, S->XBlo, s1));
-  K(cudaEventRecord(c->ev_join, s1));
-  // branch 2: Step I block residual at the reading's point, concurrent with branch 1
-  float* P = S->literal ? S->W : S->Z;
-  K(run_rows_over_x(c, S->plan1, c->Xc, c->qc, S->B32, b, P, s, S->part1, 1, s0, S->wop1));
-  K(launch_reduce(S->part1, S->ns1, b, s, 0, s, S->R, s, (float)lam, P, S->B32, s, -1.f, S->Y, S->B32, s, nullptr,
-                  s0));
-  K(cudaStreamWaitEvent(s0, c->ev_join, 0));
-  // Alg. 5 after the join, on the whole GPU: v <- P^{-1/2} H P^{-1/2} v / ||v||, N times
+  if (S->tc_pw && !S->sk_tc) KR(launch_build_tc(c->Xc, c->qc, S->B32, b, c->d, c->dp, S->XBhi, S->XBlo, s1));
+  KR(cudaEventRecord(c->ev_join, s1));
+  return cudaSuccess;
+}
+
+// the point at which Step I takes the residual (reading R1)
+float* step1_point(adasap_solver* S) { return S->literal ? S->W : S->Z; }
+
+// branch 2: the Step I block product, concurrent with branch 1
+cudaError_t rec_step1(adasap_solver* S) {
+  adasap_ctx* c = S->c;
+  return run_rows_over_x(c, S->plan1, c->Xc, c->qc, S->B32, S->b, step1_point(S), S->s, S->part1, 1, c->s0,
+                         S->wop1);
+}
+
+// block residual R = K_Bn P + lambda P_B - Y_B from the Step I partials; join branch 1
+cudaError_t rec_step1_finish(adasap_solver* S) {
+  adasap_ctx* c = S->c;
+  const int s = S->s;
+  float* P = step1_point(S);
+  KR(launch_reduce(S->part1, S->ns1, S->b, s, 0, s, S->R, s, (float)c->lambda, P, S->B32, s, -1.f, S->Y, S->B32, s,
+                   nullptr, c->s0));
+  return cudaStreamWaitEvent(c->s0, c->ev_join, 0);
+}
+
+// Alg. 5 with the Nystrom preconditioner, carried as a_i = P^{-1/2} v_i: one
+// apply (two launches) per H product
+float* power_buf(adasap_solver* S, int i) { return (i & 1) ? S->vB : S->vA; }
+
+cudaError_t rec_power_init(adasap_solver* S) {
+  return launch_wb_single(S->cb, kInvSqrtNormalised, S->v0, power_buf(S, 0), S->c->sc, S->c->s0);
+}
+
+cudaError_t rec_power_rows(adasap_solver* S, int i) {
+  adasap_ctx* c = S->c;
+  float* acur = power_buf(S, i);
+  if (S->tc_pw)
+    return launch_rows_tc(c->kern, c->d, S->XB, S->qB, nullptr, S->b, c->dp, S->XBhi, S->XBlo, S->b, 1, acur, 1,
+                          S->part2, S->ns_pw, c->sigma2, c->err_dev, c->s0);
+  RowsArgs kb = block_args(S);
+  kb.w = acur;
   kb.ldw = 1;
-  if (!S->identity) {
-    // carried as a_i = P^{-1/2} v_i: one apply (two launches) per H product
-    float* abuf[2] = {S->vA, S->vB};
-    K(launch_wb_single(cb, kInvSqrtNormalised, S->v0, abuf[0], c->sc, s0));
-    for (int i = 0; i < S->o.power_iters; ++i) {
-      const bool last = i == S->o.power_iters - 1;
-      float* acur = abuf[i & 1];
-      kb.w = acur;
-      if (S->tc_pw)
-        K(launch_rows_tc(c->kern, c->d, S->XB, S->qB, nullptr, b, c->dp, S->XBhi, S->XBlo, b, 1, acur, 1, S->part2,
-                         S->ns_pw, c->sigma2, c->err_dev, s0));
-      else
-        K(launch_rows(c->kern, c->dp, kb, 1, S->ns_pw, false, s0));
-      K(launch_power_step(cb, last ? kRayleighEta : kInvUnit, S->part2, S->ns_pw, (float)lam, acur, S->h,
-                          abuf[(i + 1) & 1], c->sc, s0));
-    }
-  } else {
-    const float* vcur = S->v0;
-    float* vbuf[2] = {S->vA, S->vB};
-    for (int i = 0; i < S->o.power_iters; ++i) {
-      const bool last = i == S->o.power_iters - 1;
-      float* vnext = vbuf[i & 1];
-      K(launch_reduce(vcur, 1, b, 1, 0, 1, S->h, 1, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, cb.sq_part,
-                      s0));
-      K(launch_woodbury_apply(cb, kInvSqrtNormalised, S->h, 1, S->a, false, false, nullptr, c->sc, s0));
-      kb.w = S->a;
-      if (S->tc_pw)
-        K(launch_rows_tc(c->kern, c->d, S->XB, S->qB, nullptr, b, c->dp, S->XBhi, S->XBlo, b, 1, S->a, 1, S->part2,
-                         S->ns_pw, c->sigma2, c->err_dev, s0));
-      else
-        K(launch_rows(c->kern, c->dp, kb, 1, S->ns_pw, false, s0));
-      K(launch_reduce(S->part2, S->ns_pw, b, 1, 0, 1, S->h, 1, (float)lam, S->a, nullptr, 1, 0.f, nullptr, nullptr,
-                      0, nullptr, s0));
-      K(launch_woodbury_apply(cb, kInvSqrt, S->h, 1, vnext, true, last, last ? vcur : nullptr, c->sc, s0));
-      vcur = vnext;
-    }
-    K(launch_set_eta(cb, c->sc, S->identity, s0));
+  return launch_rows(c->kern, c->dp, kb, 1, S->ns_pw, false, c->s0);
+}
+
+cudaError_t rec_power_apply(adasap_solver* S, int i) {
+  adasap_ctx* c = S->c;
+  const bool last = i == S->o.power_iters - 1;
+  return launch_power_step(S->cb, last ? kRayleighEta : kInvUnit, S->part2, S->ns_pw, (float)c->lambda,
+                           power_buf(S, i), S->h, power_buf(S, i + 1), c->sc, c->s0);
+}
+
+// Alg. 5 with the identity preconditioner (ADASAP-I)
+cudaError_t rec_power_identity(adasap_solver* S) {
+  adasap_ctx* c = S->c;
+  cudaStream_t s0 = c->s0;
+  const int64_t b = S->b;
+  CoreBufs& cb = S->cb;
+  const float* vcur = S->v0;
+  float* vbuf[2] = {S->vA, S->vB};
+  RowsArgs kb = block_args(S);
+  kb.ldw = 1;
+  for (int i = 0; i < S->o.power_iters; ++i) {
+    const bool last = i == S->o.power_iters - 1;
+    float* vnext = vbuf[i & 1];
+    KR(launch_reduce(vcur, 1, b, 1, 0, 1, S->h, 1, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, cb.sq_part,
+                     s0));
+    KR(launch_woodbury_apply(cb, kInvSqrtNormalised, S->h, 1, S->a, false, false, nullptr, c->sc, s0));
+    kb.w = S->a;
+    if (S->tc_pw)
+      KR(launch_rows_tc(c->kern, c->d, S->XB, S->qB, nullptr, b, c->dp, S->XBhi, S->XBlo, b, 1, S->a, 1, S->part2,
+                        S->ns_pw, c->sigma2, c->err_dev, s0));
+    else
+      KR(launch_rows(c->kern, c->dp, kb, 1, S->ns_pw, false, s0));
+    KR(launch_reduce(S->part2, S->ns_pw, b, 1, 0, 1, S->h, 1, (float)c->lambda, S->a, nullptr, 1, 0.f, nullptr,
+                     nullptr, 0, nullptr, s0));
+    KR(launch_woodbury_apply(cb, kInvSqrt, S->h, 1, vnext, true, last, last ? vcur : nullptr, c->sc, s0));
+    vcur = vnext;
   }
-  // Step IV: direction and NesterovAcc
+  return launch_set_eta(cb, c->sc, S->identity, s0);
+}
+
+// Step IV: direction and NesterovAcc; t += 1
+cudaError_t rec_tail(adasap_solver* S, double* trace) {
+  adasap_ctx* c = S->c;
+  cudaStream_t s0 = c->s0;
+  const int s = S->s;
   if (!S->identity && s == 1)
-    K(launch_wb_single(cb, kInv, S->R, S->D, c->sc, s0));
+    KR(launch_wb_single(S->cb, kInv, S->R, S->D, c->sc, s0));
   else
-    K(launch_woodbury_apply(cb, kInv, S->R, s, S->D, false, false, nullptr, c->sc, s0));
-  K(launch_nesterov(S->W, S->V, S->Z, n * (int64_t)s, (float)S->beta, (float)S->alpha, S->literal, s0));
-  K(launch_scatter(S->W, S->V, S->Z, S->B32, b, s, S->D, (float)S->gamma, (float)S->alpha, S->literal, c->sc, s0));
-  if (trace) K(launch_trace(c->sc, trace, s0));
-  K(launch_tick(c->sc, s0));
+    KR(launch_woodbury_apply(S->cb, kInv, S->R, s, S->D, false, false, nullptr, c->sc, s0));
+  KR(launch_nesterov(S->W, S->V, S->Z, c->n * (int64_t)s, (float)S->beta, (float)S->alpha, S->literal, s0));
+  KR(launch_scatter(S->W, S->V, S->Z, S->B32, S->b, s, S->D, (float)S->gamma, (float)S->alpha, S->literal, c->sc,
+                    s0));
+  if (trace) KR(launch_trace(c->sc, trace, s0));
+  return launch_tick(c->sc, s0);
+}
+
+// the whole iteration of one system
+cudaError_t rec_iteration(adasap_solver* S, const int64_t* Bs, const float* v0s, double* trace) {
+  KR(rec_head(S, Bs, v0s));
+  KR(rec_step1(S));
+  KR(rec_step1_finish(S));
+  // Alg. 5 after the join, on the whole GPU: v <- P^{-1/2} H P^{-1/2} v / ||v||, N times
+  if (S->identity) {
+    KR(rec_power_identity(S));
+  } else {
+    KR(rec_power_init(S));
+    for (int i = 0; i < S->o.power_iters; ++i) {
+      KR(rec_power_rows(S, i));
+      KR(rec_power_apply(S, i));
+    }
+  }
+  return rec_tail(S, trace);
+}
+
+// Record one ADASAP iteration on s0 (forking to s1) into S->graph.
+cudaError_t capture_iteration(adasap_solver* S, const int64_t* Bs, const float* v0s, double* trace) {
+  cudaStream_t s0 = S->c->s0;
+  cudaError_t e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  const cudaError_t ce = rec_iteration(S, Bs, v0s, trace);
   e = cudaStreamEndCapture(s0, &S->graph);
   if (ce != cudaSuccess) return ce;
   if (e != cudaSuccess) return e;
   return cudaGraphInstantiateWithFlags(&S->exec, S->graph, cudaGraphInstantiateFlagUseNodePriority);
 }
 
-adasap_status solver_begin(adasap_ctx* c, const float* Y, int s, const adasap_opts* o, const int64_t* Bs,
-                           const float* Oms, const float* v0s, const float* W0, double* trace, cudaStream_t us,
-                           adasap_solver** out, int64_t T_sched = 0) {
+// Allocate the solver state, copy Y and W0, and draw the first Omega; the
+// iteration graph is captured by the caller (one system, or a batch).
+adasap_status solver_prepare(adasap_ctx* c, const float* Y, int s, const adasap_opts* o, const int64_t* Bs,
+                             const float* Oms, const float* v0s, const float* W0, cudaStream_t us,
+                             adasap_solver** out, int64_t T_sched, int reserve_sms) {
   if (!c || !Y || !o || !out || s < 1 || s > kMaxRhs) return ADASAP_EINVAL;
   *out = nullptr;
   const int64_t n = c->n, b = o->b;
@@ -755,7 +833,7 @@ adasap_status solver_begin(adasap_ctx* c, const float* Y, int s, const adasap_op
   S->eps = o->eps > 0 ? o->eps : std::ldexp(1.0, -23);
   S->literal = o->literal ? 1 : 0;
   S->mc = std::min<int64_t>(n, std::max<int64_t>(1, o->check_rows));
-  S->plan1 = plan_rows(c, b, n, s, kBranchSms);
+  S->plan1 = plan_rows(c, b, n, s, reserve_sms);
   S->plan_c = plan_rows(c, S->mc, n, s);
   S->tc_pw = c->prec == ADASAP_PREC_TF32X3 && c->kp > 0;
   S->ns1 = S->plan1.nsplit;
@@ -792,13 +870,25 @@ adasap_status solver_begin(adasap_ctx* c, const float* Y, int s, const adasap_op
   if ((e = launch_sum_blocks(S->sqb, kReduceBlocks, &c->sc->ysq, c->s0))) return fail(e, "ysq");
   if ((e = cudaMemcpyAsync(S->V, S->W, bytes, cudaMemcpyDeviceToDevice, c->s0))) return fail(e, "V0");
   if ((e = cudaMemcpyAsync(S->Z, S->W, bytes, cudaMemcpyDeviceToDevice, c->s0))) return fail(e, "Z0");
-  if ((e = cudaStreamSynchronize(c->s0))) return fail(e, "sync");
-  if ((e = capture_iteration(S, Bs, Oms, v0s, trace))) return fail(e, "graph capture");
   // Omega of the first iteration (each iteration then prepares the next one's)
-  if (!S->identity && !(S->sched && S->T_sched == 0) &&
-      ((e = next_omega(S, 0, c->s0)) || (e = cudaStreamSynchronize(c->s0))))
-    return fail(e, "first Omega");
+  if (!S->identity && !(S->sched && S->T_sched == 0) && (e = next_omega(S, 0, c->s0))) return fail(e, "first Omega");
+  if ((e = cudaStreamSynchronize(c->s0))) return fail(e, "sync");
   *out = S;
+  return ADASAP_OK;
+}
+
+adasap_status solver_begin(adasap_ctx* c, const float* Y, int s, const adasap_opts* o, const int64_t* Bs,
+                           const float* Oms, const float* v0s, const float* W0, double* trace, cudaStream_t us,
+                           adasap_solver** out, int64_t T_sched = 0) {
+  adasap_status st = solver_prepare(c, Y, s, o, Bs, Oms, v0s, W0, us, out, T_sched, kBranchSms);
+  if (st != ADASAP_OK) return st;
+  const cudaError_t e = capture_iteration(*out, Bs, v0s, trace);
+  if (e != cudaSuccess) {
+    note_error(e, "graph capture");
+    delete *out;
+    *out = nullptr;
+    return ADASAP_ECUDA;
+  }
   return ADASAP_OK;
 }
 
@@ -970,6 +1060,384 @@ extern "C" adasap_status adasap_solve_scheduled(adasap_ctx* c, const float* Y, i
     st = solve_loop(S, W, stats, T, (cudaStream_t)stream);
     delete S;
     return st;
+  } catch (...) {
+    return ADASAP_ENOMEM;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Many independent systems (uneven n) iterated together: adasap_solve_batched.
+// One graph holds one iteration of every active system, each on its own
+// streams; the Step I products and the K_BB a products of Alg. 5 of all
+// systems that share a kernel and operand width run as one grouped persistent
+// tensor-core launch each, whose column split the batch autotunes.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct GroupedProduct {
+  int kern = 0, kp = 0;
+  std::vector<int> members;      // indices into Batch::S
+  TcArgs* grp = nullptr;         // device, one per member
+  int64_t* gstart = nullptr;     // device, prefix sums of the members' items
+  int64_t nitems = 0;
+};
+
+struct Batch {
+  std::vector<adasap_solver*> S;
+  std::vector<char> active, grouped;
+  std::vector<int> ns1_max, nspw_max;   // split capacity of each system's partial buffers
+  cudaStream_t ms = nullptr;
+  cudaEvent_t ev = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+  int tpi1 = 32, tpipw = 4;             // column tiles per item of the grouped launches
+  int ctas = 0;
+  std::vector<GroupedProduct> step1, pw[2];
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  void free_groups() {
+    for (auto* v : {&step1, &pw[0], &pw[1]}) {
+      for (GroupedProduct& g : *v) {
+        cudaFree(g.grp);
+        cudaFree(g.gstart);
+      }
+      v->clear();
+    }
+  }
+  void free_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+  }
+  ~Batch() {
+    if (ms) cudaStreamSynchronize(ms);
+    free_graph();
+    free_groups();
+    for (adasap_solver* x : S) delete x;
+    if (ev) cudaEventDestroy(ev);
+    if (ev_t0) cudaEventDestroy(ev_t0);
+    if (ev_t1) cudaEventDestroy(ev_t1);
+    if (ms) cudaStreamDestroy(ms);
+  }
+};
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// A system joins the grouped launches when both of its products run on the
+// single-RHS tensor-core kernel.
+bool groupable(const adasap_solver* S) {
+  return !S->identity && !S->sched && S->s == 1 && S->plan1.tc && !S->plan1.mrhs && S->tc_pw;
+}
+
+// column tiles of the tensor-core kernel are 128 wide
+int step1_splits(const adasap_solver* S, int tpi) { return (int)ceil_div(tc_npad(S->c->n) / 128, tpi); }
+int power_splits(const adasap_solver* S, int tpi) { return (int)ceil_div(tc_npad(S->b) / 128, tpi); }
+
+// Grouped launch descriptions for the active groupable systems; which = 0 Step I,
+// 1 / 2 the K_BB a product on power buffer 0 / 1.
+cudaError_t build_groups(Batch& bt, int which, int tpi, std::vector<GroupedProduct>& out) {
+  std::vector<GroupedProduct> cls;
+  std::vector<std::vector<TcArgs>> args;
+  for (size_t i = 0; i < bt.S.size(); ++i) {
+    if (!bt.active[i] || !bt.grouped[i]) continue;
+    adasap_solver* S = bt.S[i];
+    adasap_ctx* c = S->c;
+    size_t k = 0;
+    while (k < cls.size() && !(cls[k].kern == c->kern && cls[k].kp == c->kp)) ++k;
+    if (k == cls.size()) {
+      cls.emplace_back();
+      cls.back().kern = c->kern;
+      cls.back().kp = c->kp;
+      args.emplace_back();
+    }
+    TcArgs a;
+    if (which == 0)
+      a = make_tc_args(c->d, c->Xc, c->qc, S->B32, S->b, c->dp, c->tc_hi, c->tc_lo, c->n, 1, step1_point(S), S->s,
+                       S->part1, step1_splits(S, tpi), c->sigma2, c->err_dev);
+    else
+      a = make_tc_args(c->d, S->XB, S->qB, nullptr, S->b, c->dp, S->XBhi, S->XBlo, S->b, 1, power_buf(S, which - 1),
+                       1, S->part2, power_splits(S, tpi), c->sigma2, c->err_dev);
+    cls[k].members.push_back((int)i);
+    args[k].push_back(a);
+  }
+  for (size_t k = 0; k < cls.size(); ++k) {
+    std::vector<int64_t> start(1, 0);
+    for (const TcArgs& a : args[k]) start.push_back(start.back() + tc_items(a));
+    GroupedProduct& g = cls[k];
+    g.nitems = start.back();
+    cudaError_t e;
+    if ((e = cudaMalloc(&g.grp, args[k].size() * sizeof(TcArgs))) ||
+        (e = cudaMalloc(&g.gstart, start.size() * sizeof(int64_t))) ||
+        (e = cudaMemcpy(g.grp, args[k].data(), args[k].size() * sizeof(TcArgs), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(g.gstart, start.data(), start.size() * sizeof(int64_t), cudaMemcpyHostToDevice))) {
+      out.insert(out.end(), cls.begin(), cls.begin() + k + 1);
+      return e;
+    }
+  }
+  out.insert(out.end(), cls.begin(), cls.end());
+  return cudaSuccess;
+}
+
+cudaError_t launch_groups(const Batch& bt, const std::vector<GroupedProduct>& gs, cudaStream_t st) {
+  for (const GroupedProduct& g : gs)
+    KR(launch_rows_tc_grouped(g.kern, g.kp, g.grp, g.gstart, (int)g.members.size(), g.nitems,
+                              bt.S[g.members[0]]->c->err_dev, bt.ctas, st));
+  return cudaSuccess;
+}
+
+// Splits of the grouped launches and the partial buffers sized for them.
+void set_splits(Batch& bt) {
+  for (size_t i = 0; i < bt.S.size(); ++i) {
+    if (!bt.grouped[i]) continue;
+    bt.S[i]->ns1 = step1_splits(bt.S[i], bt.tpi1);
+    bt.S[i]->ns_pw = power_splits(bt.S[i], bt.tpipw);
+  }
+}
+
+// Column tiles per item of each grouped product, by timing each candidate
+// launch alone on the stream (the partial buffers are scratch until the first
+// iteration writes them; B holds row 0 until the first sample).
+adasap_status autotune(Batch& bt) {
+  const int c1[] = {8, 16, 32, 64};
+  const int cpw[] = {1, 2, 4, 8};
+  for (int which = 0; which < 2; ++which) {
+    float best = 1e30f;
+    for (int tpi : (which == 0 ? c1 : cpw)) {
+      std::vector<GroupedProduct> gs;
+      cudaError_t e = build_groups(bt, which == 0 ? 0 : 1, tpi, gs);
+      float ms = 0.f;
+      if (e == cudaSuccess) {
+        for (int rep = 0; rep < 5 && e == cudaSuccess; ++rep) {
+          if (rep == 2) e = cudaEventRecord(bt.ev_t0, bt.ms);
+          if (e == cudaSuccess) e = launch_groups(bt, gs, bt.ms);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(bt.ev_t1, bt.ms);
+        if (e == cudaSuccess) e = cudaEventSynchronize(bt.ev_t1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, bt.ev_t0, bt.ev_t1);
+      }
+      for (GroupedProduct& g : gs) {
+        cudaFree(g.grp);
+        cudaFree(g.gstart);
+      }
+      if (e != cudaSuccess) {
+        note_error(e, "autotune");
+        return ADASAP_ECUDA;
+      }
+      if (ms < best) {
+        best = ms;
+        (which == 0 ? bt.tpi1 : bt.tpipw) = tpi;
+      }
+    }
+  }
+  return ADASAP_OK;
+}
+
+// One iteration of every active system.
+cudaError_t rec_batch(Batch& bt) {
+  cudaStream_t ms = bt.ms;
+  std::vector<adasap_solver*> act, grp;
+  for (size_t i = 0; i < bt.S.size(); ++i)
+    if (bt.active[i]) {
+      act.push_back(bt.S[i]);
+      if (bt.grouped[i]) grp.push_back(bt.S[i]);
+    }
+  auto fork = [&](const std::vector<adasap_solver*>& v) -> cudaError_t {
+    KR(cudaEventRecord(bt.ev, ms));
+    for (adasap_solver* S : v) KR(cudaStreamWaitEvent(S->c->s0, bt.ev, 0));
+    return cudaSuccess;
+  };
+  auto join = [&](const std::vector<adasap_solver*>& v) -> cudaError_t {
+    for (adasap_solver* S : v) {
+      KR(cudaEventRecord(S->c->ev_out, S->c->s0));
+      KR(cudaStreamWaitEvent(ms, S->c->ev_out, 0));
+    }
+    return cudaSuccess;
+  };
+  KR(fork(act));
+  for (adasap_solver* S : act) KR(rec_head(S, nullptr, nullptr));
+  for (adasap_solver* S : act)
+    if (!groupable(S)) KR(rec_step1(S));
+  if (!grp.empty()) {
+    KR(join(grp));
+    KR(launch_groups(bt, bt.step1, ms));
+    KR(fork(grp));
+  }
+  for (adasap_solver* S : act) {
+    KR(rec_step1_finish(S));
+    KR(S->identity ? rec_power_identity(S) : rec_power_init(S));
+  }
+  const int np = act.empty() ? 0 : act[0]->o.power_iters;
+  for (int i = 0; i < np; ++i) {
+    for (adasap_solver* S : act)
+      if (!S->identity && !groupable(S)) KR(rec_power_rows(S, i));
+    if (!grp.empty()) {
+      KR(join(grp));
+      KR(launch_groups(bt, bt.pw[i & 1], ms));
+      KR(fork(grp));
+    }
+    for (adasap_solver* S : act)
+      if (!S->identity) KR(rec_power_apply(S, i));
+  }
+  for (adasap_solver* S : act) KR(rec_tail(S, nullptr));
+  return join(act);
+}
+
+adasap_status rebuild(Batch& bt) {
+  bt.free_graph();
+  bt.free_groups();
+  cudaError_t e;
+  if ((e = build_groups(bt, 0, bt.tpi1, bt.step1)) || (e = build_groups(bt, 1, bt.tpipw, bt.pw[0])) ||
+      (e = build_groups(bt, 2, bt.tpipw, bt.pw[1]))) {
+    note_error(e, "grouped launch tables");
+    return ADASAP_ECUDA;
+  }
+  if ((e = cudaStreamBeginCapture(bt.ms, cudaStreamCaptureModeThreadLocal))) {
+    note_error(e, "batch capture");
+    return ADASAP_ECUDA;
+  }
+  const cudaError_t ce = rec_batch(bt);
+  e = cudaStreamEndCapture(bt.ms, &bt.graph);
+  if (ce != cudaSuccess || e != cudaSuccess) {
+    note_error(ce != cudaSuccess ? ce : e, "batch capture");
+    return ADASAP_ECUDA;
+  }
+  if ((e = cudaGraphInstantiateWithFlags(&bt.exec, bt.graph, cudaGraphInstantiateFlagUseNodePriority))) {
+    note_error(e, "batch instantiate");
+    return ADASAP_ECUDA;
+  }
+  return ADASAP_OK;
+}
+
+adasap_status solve_batched(int nsys, adasap_ctx* const* ctxs, const float* const* Y, int s,
+                            const adasap_opts* opts, float* const* W, adasap_stats* stats, cudaStream_t us) {
+  for (int i = 0; i < nsys; ++i) {
+    if (!ctxs[i] || !Y[i] || !W[i] || opts[i].tail_average || opts[i].max_iters < 0) return ADASAP_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return ADASAP_EINVAL;  // one active solver per context
+  }
+  Batch bt;
+  CT(cudaStreamCreateWithFlags(&bt.ms, cudaStreamNonBlocking));
+  CT(cudaEventCreateWithFlags(&bt.ev, cudaEventDisableTiming));
+  CT(cudaEventCreate(&bt.ev_t0));
+  CT(cudaEventCreate(&bt.ev_t1));
+  // persistent CTAs of the grouped launches: the rest of the GPU runs the
+  // systems' factorisation branches (mostly single-CTA launches)
+  const int reserve = std::min(32, std::max(kBranchSms, nsys / 4));
+  bt.ctas = std::max(1, tc_slots() - reserve);
+  bt.S.assign(nsys, nullptr);
+  bt.active.assign(nsys, 1);
+  bt.grouped.assign(nsys, 0);
+  for (int i = 0; i < nsys; ++i) {
+    const adasap_status st =
+        solver_prepare(ctxs[i], Y[i], s, &opts[i], nullptr, nullptr, nullptr, W[i], us, &bt.S[i], 0, reserve);
+    if (st != ADASAP_OK) return st;
+    adasap_solver* S = bt.S[i];
+    bt.grouped[i] = groupable(S);
+    if (!bt.grouped[i]) continue;
+    // partial buffers for the smallest split candidates; B = row 0 until the first sample
+    const int64_t b = S->b;
+    S->part1 = S->ar.get<float>((size_t)step1_splits(S, 8) * b);
+    const size_t pw = std::max((size_t)power_splits(S, 1) * b, (size_t)S->ns_sk * b * S->r);
+    S->part2 = S->ar.get<float>(pw);
+    if (S->ar.err != cudaSuccess) return ADASAP_ENOMEM;
+    CT(cudaMemset(S->B32, 0, (size_t)b * sizeof(int)));
+  }
+  CT(cudaDeviceSynchronize());
+  int ngrouped = 0;
+  for (int i = 0; i < nsys; ++i) ngrouped += bt.grouped[i];
+  if (ngrouped > 0) {
+    const adasap_status st = autotune(bt);
+    if (st != ADASAP_OK) return st;
+  }
+  set_splits(bt);
+  // iterate: every system leaves the batch at its own tolerance or max_iters
+  std::vector<double> rel(nsys, NAN), secs(nsys, 0.0);
+  std::vector<adasap_status> res(nsys, ADASAP_OK);
+  std::vector<char> checked(nsys, 0), conv(nsys, 0);
+  CT(cudaEventRecord(bt.ev_t0, bt.ms));
+  int nactive = nsys;
+  adasap_status st = ADASAP_OK;
+  auto leave = [&](int i) -> adasap_status {
+    CT(cudaEventRecord(bt.ev_t1, bt.ms));
+    CT(cudaEventSynchronize(bt.ev_t1));
+    float ms = 0.f;
+    CT(cudaEventElapsedTime(&ms, bt.ev_t0, bt.ev_t1));
+    secs[i] = ms * 1e-3;
+    bt.active[i] = 0;
+    --nactive;
+    return ADASAP_OK;
+  };
+  for (int i = 0; i < nsys; ++i)
+    if (opts[i].max_iters == 0 && (st = leave(i)) != ADASAP_OK) return st;
+  if (nactive > 0 && (st = rebuild(bt)) != ADASAP_OK) return st;
+  while (nactive > 0) {
+    int64_t k = INT64_MAX;
+    for (int i = 0; i < nsys; ++i) {
+      if (!bt.active[i]) continue;
+      const adasap_opts& o = bt.S[i]->o;
+      int64_t ki = o.max_iters - bt.S[i]->iters;
+      if (o.check_every > 0) ki = std::min<int64_t>(ki, o.check_every - bt.S[i]->iters % o.check_every);
+      k = std::min(k, ki);
+    }
+    for (int64_t j = 0; j < k; ++j) CT(cudaGraphLaunch(bt.exec, bt.ms));
+    bool changed = false;
+    for (int i = 0; i < nsys; ++i) {
+      if (!bt.active[i]) continue;
+      adasap_solver* S = bt.S[i];
+      S->iters += k;
+      checked[i] = 0;
+      const bool at_max = S->iters >= S->o.max_iters;
+      const bool due = S->o.check_every > 0 && S->iters % S->o.check_every == 0;
+      if (!due && !at_max) continue;
+      if (due) {
+        res[i] = solver_residual(S, &rel[i], bt.ms);
+        checked[i] = 1;
+        conv[i] = res[i] == ADASAP_OK && S->o.tol > 0 && rel[i] <= S->o.tol;
+      }
+      if (res[i] != ADASAP_OK || conv[i] || at_max) {
+        if ((st = leave(i)) != ADASAP_OK) return st;
+        changed = true;
+      }
+    }
+    if (changed && nactive > 0 && (st = rebuild(bt)) != ADASAP_OK) return st;
+  }
+  CT(cudaStreamSynchronize(bt.ms));
+  adasap_status worst = ADASAP_OK;
+  for (int i = 0; i < nsys; ++i) {
+    adasap_solver* S = bt.S[i];
+    adasap_ctx* c = S->c;
+    if (res[i] == ADASAP_OK && !checked[i]) {
+      res[i] = solver_residual(S, &rel[i], bt.ms);
+      conv[i] = res[i] == ADASAP_OK && S->o.tol > 0 && rel[i] <= S->o.tol;
+    }
+    CT(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->s0));
+    CT(cudaMemcpyAsync(W[i], S->W, (size_t)c->n * s * sizeof(float), cudaMemcpyDefault, c->s0));
+    CT(cudaStreamSynchronize(c->s0));
+    if (res[i] == ADASAP_OK && c->sc_host->status != 0) res[i] = (adasap_status)c->sc_host->status;
+    if (res[i] == ADASAP_OK && S->o.tol > 0 && !conv[i]) res[i] = ADASAP_ENOTCONVERGED;
+    if (stats) {
+      stats[i].iters = (int)S->iters;
+      stats[i].rel_resid = rel[i];
+      stats[i].resid_exact = S->mc == c->n ? 1 : 0;
+      stats[i].seconds = secs[i];
+      stats[i].last_eta = c->sc_host->eta;
+      stats[i].last_rho = c->sc_host->rho;
+      stats[i].status_detail = c->sc_host->detail;
+    }
+    if (worst == ADASAP_OK || (worst == ADASAP_ENOTCONVERGED && res[i] != ADASAP_OK)) worst = res[i];
+  }
+  CT(cudaEventRecord(bt.ev, bt.ms));
+  CT(cudaStreamWaitEvent(us, bt.ev, 0));
+  return worst;
+}
+
+}  // namespace
+
+extern "C" adasap_status adasap_solve_batched(int nsys, adasap_ctx* const* ctxs, const float* const* Y, int s,
+                                              const adasap_opts* opts, float* const* W, adasap_stats* stats,
+                                              void* stream) {
+  if (nsys < 1 || !ctxs || !Y || !opts || !W || s < 1 || s > kMaxRhs) return ADASAP_EINVAL;
+  try {
+    return solve_batched(nsys, ctxs, Y, s, opts, W, stats, (cudaStream_t)stream);
   } catch (...) {
     return ADASAP_ENOMEM;
   }
