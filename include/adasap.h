@@ -170,7 +170,7 @@ adasap_status adasap_solve_scheduled(adasap_ctx* ctx, const float* Y, int s,
  * GP models of a Bayesian-optimisation campaign, Sec. 5.3).  System i is
  * ctxs[i] with Y[i] and W[i] (n_i x s, host or device; W[i] holds W_0 on entry
  * and the returned iterate on exit) and its own options opts[i] (Alg. 2 as in
- * adasap_solve; tail_average must be 0).  One CUDA graph holds one iteration of
+ * adasap_solve; tail_average must be 0, power_iters the same for all).  One CUDA graph holds one iteration of
  * every system still running, each system on its context's streams; the Step I
  * products and the K_BB a products of Alg. 5 of all systems that use the
  * single-right-hand-side tensor-core kernel (s = 1, ADASAP_PREC_TF32X3, Nystrom

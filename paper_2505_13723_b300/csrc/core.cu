@@ -1138,31 +1138,6 @@ cudaError_t launch_tick(DevScalars* sc, cudaStream_t st) {
 constexpr int kWbThreads = 256, kWbWarps = kWbThreads / 32, kWbRows = 8;
 constexpr int kWbSlots = kMaxRank + 2;     // per-chunk partials: U^T h, ||h||^2, a . h
 
-struct WbArgs {
-  const float* U;
-  int64_t b;
-  int r;
-  int mode;
-  const float* v;       // input rows (kInvSqrtNormalised, kInv)
-  const float* part;    // nsplit x b partial products (kInvUnit, kRayleighEta)
-  int nsplit;
-  const float* a;       // current powering iterate
-  float lam;
-  float* hbuf;          // b floats: h of the powering step, for launch B
-  const double* keep;
-  const float* Minv;
-  const float* Gu;      // U^T U (FP32)
-  const double* S;
-  const double* cis;
-  DevScalars* sc;
-  float* out;
-  double* wpart;        // nchunk x kWbSlots partials
-  float* wcoef;         // coef[0..r) and alpha at [kMaxRank] (written by the last block of launch A)
-  unsigned int* count;  // blocks of launch A done (reset by its last block)
-  int nchunk;
-  int64_t per;          // rows per chunk
-};
-
 // Sum over the 32 lanes of eight per-lane values x[0..7]; on return lane l
 // holds in x[0] the total of value l >> 2.
 __device__ __forceinline__ void transpose_sum8(float x[8], int lane) {
@@ -1284,7 +1259,8 @@ __device__ void wb_coefficients(const WbArgs& a, const double* q, double* ys, do
   }
 }
 
-__global__ void __launch_bounds__(kWbThreads) k_wb_partials(WbArgs a) {
+// Chunk `chunk` of launch A (partials; the last chunk to finish reduces them).
+__device__ __forceinline__ void wb_partials_body(const WbArgs& a, int chunk) {
   __shared__ float wtmp[kWbWarps][kMaxRank];
   __shared__ double red[33];
   __shared__ double red2[33];
@@ -1298,7 +1274,7 @@ __global__ void __launch_bounds__(kWbThreads) k_wb_partials(WbArgs a) {
   const bool from_part = mode == kInvUnit || mode == kRayleighEta;
   const bool need_u = mode != kRayleighEta;
   constexpr int KJ = kMaxRank / 32;
-  const int64_t r0 = (int64_t)blockIdx.x * a.per, r1 = min(a.b, r0 + a.per);
+  const int64_t r0 = (int64_t)chunk * a.per, r1 = min(a.b, r0 + a.per);
   float acc[KJ];
 #pragma unroll
   for (int j = 0; j < KJ; ++j) acc[j] = 0.0f;
@@ -1364,7 +1340,7 @@ __global__ void __launch_bounds__(kWbThreads) k_wb_partials(WbArgs a) {
   }
   const double hsq_t = block_sum((double)hsq, red);   // contains __syncthreads
   const double ah_t = block_sum((double)ah, red2);
-  double* dst = a.wpart + (int64_t)blockIdx.x * kWbSlots;
+  double* dst = a.wpart + (int64_t)chunk * kWbSlots;
   if (need_u) {
     for (int k = threadIdx.x; k < r; k += kWbThreads) {
       double t = 0.0;
@@ -1381,7 +1357,7 @@ __global__ void __launch_bounds__(kWbThreads) k_wb_partials(WbArgs a) {
   // last) and forms the coefficients.  No block waits for another.
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(a.count, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) s_last = atomicAdd(a.count, 1u) == (unsigned)a.nchunk - 1u;
   __syncthreads();
   if (!s_last) return;
   __threadfence();
@@ -1424,7 +1400,10 @@ __global__ void __launch_bounds__(kWbThreads) k_wb_partials(WbArgs a) {
   wb_coefficients(a, q, ys, zs, red);
 }
 
-__global__ void __launch_bounds__(kWbThreads) k_wb_apply(WbArgs a) {
+__global__ void __launch_bounds__(kWbThreads) k_wb_partials(WbArgs a) { wb_partials_body(a, blockIdx.x); }
+
+// Launch B: out = U coef + alpha h, chunk `chunk` of the rows.
+__device__ __forceinline__ void wb_apply_body(const WbArgs& a, int chunk) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int r = a.r;
   constexpr int KJ = kMaxRank / 32;
@@ -1433,7 +1412,7 @@ __global__ void __launch_bounds__(kWbThreads) k_wb_apply(WbArgs a) {
 #pragma unroll
   for (int j = 0; j < KJ; ++j) cf[j] = (lane + 32 * j < r) ? a.wcoef[lane + 32 * j] : 0.0f;
   const float* hsrc = a.mode == kInvUnit ? a.hbuf : a.v;
-  const int64_t r0 = (int64_t)blockIdx.x * a.per, r1 = min(a.b, r0 + a.per);
+  const int64_t r0 = (int64_t)chunk * a.per, r1 = min(a.b, r0 + a.per);
   for (int64_t i0 = r0 + (int64_t)warp * kWbRows; i0 < r1; i0 += (int64_t)kWbWarps * kWbRows) {
     float x[kWbRows];
 #pragma unroll
@@ -1453,15 +1432,55 @@ __global__ void __launch_bounds__(kWbThreads) k_wb_apply(WbArgs a) {
   }
 }
 
-static cudaError_t launch_wb(WbArgs& a, CoreBufs& cb, cudaStream_t st) {
+__global__ void __launch_bounds__(kWbThreads) k_wb_apply(WbArgs a) { wb_apply_body(a, blockIdx.x); }
+
+// Grouped forms: system blockIdx.y of g, its chunks blockIdx.x < g[y].nchunk.
+__global__ void __launch_bounds__(kWbThreads) k_wb_partials_g(const WbArgs* __restrict__ g) {
+  const WbArgs& a = g[blockIdx.y];
+  if ((int)blockIdx.x < a.nchunk) wb_partials_body(a, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kWbThreads) k_wb_apply_g(const WbArgs* __restrict__ g) {
+  const WbArgs& a = g[blockIdx.y];
+  if ((int)blockIdx.x < a.nchunk) wb_apply_body(a, blockIdx.x);
+}
+
+static void fill_wb(WbArgs& a, CoreBufs& cb) {
   a.U = cb.U; a.b = cb.b; a.r = cb.r; a.keep = cb.keep; a.Minv = cb.Minv; a.Gu = cb.Gu; a.S = cb.S; a.cis = cb.cis;
   a.wpart = cb.wb_part;
   a.wcoef = cb.wb_coef;
   a.count = cb.wb_count;
   a.nchunk = wb_chunks_for(cb.b);
   a.per = (cb.b + a.nchunk - 1) / a.nchunk;
+}
+
+static cudaError_t launch_wb(WbArgs& a, CoreBufs& cb, cudaStream_t st) {
+  fill_wb(a, cb);
   k_wb_partials<<<a.nchunk, kWbThreads, 0, st>>>(a);
   if (a.mode != kRayleighEta) k_wb_apply<<<a.nchunk, kWbThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+WbArgs wb_args_single(CoreBufs& cb, int mode, const float* v, float* out, DevScalars* sc) {
+  WbArgs a{};
+  a.mode = mode; a.v = v; a.sc = sc; a.out = out;
+  fill_wb(a, cb);
+  return a;
+}
+
+WbArgs wb_args_power(CoreBufs& cb, int mode, const float* part, int nsplit, float lam, const float* acur,
+                     float* hbuf, float* anext, DevScalars* sc) {
+  WbArgs a{};
+  a.mode = mode; a.part = part; a.nsplit = nsplit; a.a = acur; a.lam = lam; a.hbuf = hbuf; a.sc = sc; a.out = anext;
+  fill_wb(a, cb);
+  return a;
+}
+
+cudaError_t launch_wb_grouped(const WbArgs* g, int ngrp, int max_chunks, int mode, cudaStream_t st) {
+  if (ngrp < 1) return cudaSuccess;
+  const dim3 grid(max_chunks, ngrp);
+  k_wb_partials_g<<<grid, kWbThreads, 0, st>>>(g);
+  if (mode != kRayleighEta) k_wb_apply_g<<<grid, kWbThreads, 0, st>>>(g);
   return cudaGetLastError();
 }
 

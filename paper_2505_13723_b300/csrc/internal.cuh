@@ -198,6 +198,37 @@ cudaError_t launch_woodbury_apply(CoreBufs& cb, int mode, const float* v, int s,
 cudaError_t launch_set_eta(CoreBufs& cb, DevScalars* sc, int identity, cudaStream_t st);
 // One single-RHS Woodbury apply (kInvSqrtNormalised or kInv): two whole-GPU launches.
 cudaError_t launch_wb_single(CoreBufs& cb, int mode, const float* v, float* out, DevScalars* sc, cudaStream_t st);
+// Arguments of one two-launch Woodbury apply (core.cu), and the grouped form:
+// the applies of several systems (g: device array) in one pair of launches of
+// max_chunks x ngrp blocks (max_chunks >= every g[i].nchunk); all share `mode`.
+struct WbArgs {
+  const float* U;
+  int64_t b;
+  int r;
+  int mode;
+  const float* v;       // input rows (kInvSqrtNormalised, kInv)
+  const float* part;    // nsplit x b partial products (kInvUnit, kRayleighEta)
+  int nsplit;
+  const float* a;       // current powering iterate
+  float lam;
+  float* hbuf;          // b floats: h of the powering step, for launch B
+  const double* keep;
+  const float* Minv;
+  const float* Gu;      // U^T U (FP32)
+  const double* S;
+  const double* cis;
+  DevScalars* sc;
+  float* out;
+  double* wpart;        // nchunk x kWbSlots partials
+  float* wcoef;         // coef[0..r) and alpha at [kMaxRank] (written by the last block of launch A)
+  unsigned int* count;  // blocks of launch A done (reset by its last block)
+  int nchunk;
+  int64_t per;          // rows per chunk
+};
+WbArgs wb_args_single(CoreBufs& cb, int mode, const float* v, float* out, DevScalars* sc);
+WbArgs wb_args_power(CoreBufs& cb, int mode, const float* part, int nsplit, float lam, const float* acur,
+                     float* hbuf, float* anext, DevScalars* sc);
+cudaError_t launch_wb_grouped(const WbArgs* g, int ngrp, int max_chunks, int mode, cudaStream_t st);
 // One powering step of Alg. 5 on h = sum_p part[p] + lam * acur (nsplit x b partials):
 //   kInvUnit:     anext = P^{-1} h / sqrt(h^T P^{-1} h)  (h kept in hbuf)
 //   kRayleighEta: sc->lam_hat = acur . h, sc->eta = 1 / lam_hat

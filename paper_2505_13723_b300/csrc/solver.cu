@@ -754,15 +754,18 @@ cudaError_t rec_power_identity(adasap_solver* S) {
   return launch_set_eta(cb, c->sc, S->identity, s0);
 }
 
-// Step IV: direction and NesterovAcc; t += 1
-cudaError_t rec_tail(adasap_solver* S, double* trace) {
+// Step IV-a: direction D = P^{-1} R
+cudaError_t rec_direction(adasap_solver* S) {
+  adasap_ctx* c = S->c;
+  if (!S->identity && S->s == 1) return launch_wb_single(S->cb, kInv, S->R, S->D, c->sc, c->s0);
+  return launch_woodbury_apply(S->cb, kInv, S->R, S->s, S->D, false, false, nullptr, c->sc, c->s0);
+}
+
+// Step IV-b: NesterovAcc; t += 1
+cudaError_t rec_update(adasap_solver* S, double* trace) {
   adasap_ctx* c = S->c;
   cudaStream_t s0 = c->s0;
   const int s = S->s;
-  if (!S->identity && s == 1)
-    KR(launch_wb_single(S->cb, kInv, S->R, S->D, c->sc, s0));
-  else
-    KR(launch_woodbury_apply(S->cb, kInv, S->R, s, S->D, false, false, nullptr, c->sc, s0));
   KR(launch_nesterov(S->W, S->V, S->Z, c->n * (int64_t)s, (float)S->beta, (float)S->alpha, S->literal, s0));
   KR(launch_scatter(S->W, S->V, S->Z, S->B32, S->b, s, S->D, (float)S->gamma, (float)S->alpha, S->literal, c->sc,
                     s0));
@@ -785,7 +788,8 @@ cudaError_t rec_iteration(adasap_solver* S, const int64_t* Bs, const float* v0s,
       KR(rec_power_apply(S, i));
     }
   }
-  return rec_tail(S, trace);
+  KR(rec_direction(S));
+  return rec_update(S, trace);
 }
 
 // Record one ADASAP iteration on s0 (forking to s1) into S->graph.
@@ -1091,6 +1095,10 @@ struct Batch {
   int tpi1 = 32, tpipw = 4;             // column tiles per item of the grouped launches
   int ctas = 0;
   std::vector<GroupedProduct> step1, pw[2];
+  // grouped Woodbury applies of the grouped systems: powering start, powering
+  // steps on buffer 0 / 1, the last (Rayleigh) step, the direction
+  WbArgs* wb[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int nwb = 0, wb_chunks = 1;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   void free_groups() {
@@ -1101,6 +1109,11 @@ struct Batch {
       }
       v->clear();
     }
+    for (WbArgs*& w : wb) {
+      cudaFree(w);
+      w = nullptr;
+    }
+    nwb = 0;
   }
   void free_graph() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -1174,6 +1187,33 @@ cudaError_t build_groups(Batch& bt, int which, int tpi, std::vector<GroupedProdu
     }
   }
   out.insert(out.end(), cls.begin(), cls.end());
+  return cudaSuccess;
+}
+
+cudaError_t build_wb(Batch& bt) {
+  std::vector<WbArgs> h[5];
+  bt.wb_chunks = 1;
+  for (size_t i = 0; i < bt.S.size(); ++i) {
+    if (!bt.active[i] || !bt.grouped[i]) continue;
+    adasap_solver* S = bt.S[i];
+    adasap_ctx* c = S->c;
+    const int np = S->o.power_iters;
+    const float lam = (float)c->lambda;
+    h[0].push_back(wb_args_single(S->cb, kInvSqrtNormalised, S->v0, power_buf(S, 0), c->sc));
+    for (int par = 0; par < 2; ++par)
+      h[1 + par].push_back(wb_args_power(S->cb, kInvUnit, S->part2, S->ns_pw, lam, power_buf(S, par), S->h,
+                                         power_buf(S, par + 1), c->sc));
+    h[3].push_back(wb_args_power(S->cb, kRayleighEta, S->part2, S->ns_pw, lam, power_buf(S, np - 1), S->h,
+                                 power_buf(S, np), c->sc));
+    h[4].push_back(wb_args_single(S->cb, kInv, S->R, S->D, c->sc));
+    bt.wb_chunks = std::max(bt.wb_chunks, h[0].back().nchunk);
+  }
+  bt.nwb = (int)h[0].size();
+  if (bt.nwb == 0) return cudaSuccess;
+  for (int k = 0; k < 5; ++k) {
+    KR(cudaMalloc(&bt.wb[k], h[k].size() * sizeof(WbArgs)));
+    KR(cudaMemcpy(bt.wb[k], h[k].data(), h[k].size() * sizeof(WbArgs), cudaMemcpyHostToDevice));
+  }
   return cudaSuccess;
 }
 
@@ -1261,23 +1301,37 @@ cudaError_t rec_batch(Batch& bt) {
     KR(launch_groups(bt, bt.step1, ms));
     KR(fork(grp));
   }
+  // the grouped systems' powering and direction run on the batch stream: one
+  // grouped product and one grouped apply per powering step
   for (adasap_solver* S : act) {
     KR(rec_step1_finish(S));
-    KR(S->identity ? rec_power_identity(S) : rec_power_init(S));
+    if (S->identity) KR(rec_power_identity(S));
+    else if (!groupable(S)) KR(rec_power_init(S));
+  }
+  if (!grp.empty()) {
+    KR(join(grp));
+    KR(launch_wb_grouped(bt.wb[0], bt.nwb, bt.wb_chunks, kInvSqrtNormalised, ms));
   }
   const int np = act.empty() ? 0 : act[0]->o.power_iters;
   for (int i = 0; i < np; ++i) {
     for (adasap_solver* S : act)
       if (!S->identity && !groupable(S)) KR(rec_power_rows(S, i));
     if (!grp.empty()) {
-      KR(join(grp));
       KR(launch_groups(bt, bt.pw[i & 1], ms));
-      KR(fork(grp));
+      const bool last = i == np - 1;
+      KR(launch_wb_grouped(bt.wb[last ? 3 : 1 + (i & 1)], bt.nwb, bt.wb_chunks, last ? kRayleighEta : kInvUnit, ms));
     }
     for (adasap_solver* S : act)
-      if (!S->identity) KR(rec_power_apply(S, i));
+      if (!S->identity && !groupable(S)) KR(rec_power_apply(S, i));
   }
-  for (adasap_solver* S : act) KR(rec_tail(S, nullptr));
+  if (!grp.empty()) {
+    KR(launch_wb_grouped(bt.wb[4], bt.nwb, bt.wb_chunks, kInv, ms));
+    KR(fork(grp));
+  }
+  for (adasap_solver* S : act) {
+    if (!groupable(S)) KR(rec_direction(S));
+    KR(rec_update(S, nullptr));
+  }
   return join(act);
 }
 
@@ -1286,7 +1340,7 @@ adasap_status rebuild(Batch& bt) {
   bt.free_groups();
   cudaError_t e;
   if ((e = build_groups(bt, 0, bt.tpi1, bt.step1)) || (e = build_groups(bt, 1, bt.tpipw, bt.pw[0])) ||
-      (e = build_groups(bt, 2, bt.tpipw, bt.pw[1]))) {
+      (e = build_groups(bt, 2, bt.tpipw, bt.pw[1])) || (e = build_wb(bt))) {
     note_error(e, "grouped launch tables");
     return ADASAP_ECUDA;
   }
@@ -1310,7 +1364,9 @@ adasap_status rebuild(Batch& bt) {
 adasap_status solve_batched(int nsys, adasap_ctx* const* ctxs, const float* const* Y, int s,
                             const adasap_opts* opts, float* const* W, adasap_stats* stats, cudaStream_t us) {
   for (int i = 0; i < nsys; ++i) {
-    if (!ctxs[i] || !Y[i] || !W[i] || opts[i].tail_average || opts[i].max_iters < 0) return ADASAP_EINVAL;
+    if (!ctxs[i] || !Y[i] || !W[i] || opts[i].tail_average || opts[i].max_iters < 0 ||
+        opts[i].power_iters != opts[0].power_iters)
+      return ADASAP_EINVAL;
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == ctxs[i]) return ADASAP_EINVAL;  // one active solver per context
   }

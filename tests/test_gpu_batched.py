@@ -119,3 +119,11 @@ def test_batched_invalid_arguments(lib):
     o2 = lib.default_opts(Ps[0].X.shape[0], b=Ps[0].b, r=Ps[0].r, max_iters=2, tail_average=1)
     with pytest.raises(lib.AdasapError):
         lib.solve_batched([ctx], [Ps[0].Y], opts=[o2])
+
+
+def test_batched_requires_one_powering_length(lib):
+    Ps = _systems(2, 300, 400, seed=15)
+    ctxs = [lib.Context(P.X, P.kernel, P.ell, P.sigma2, P.lam) for P in Ps]
+    opts = [lib.default_opts(P.X.shape[0], b=P.b, r=P.r, max_iters=2, power_iters=10 + k) for k, P in enumerate(Ps)]
+    with pytest.raises(lib.AdasapError):
+        lib.solve_batched(ctxs, [P.Y for P in Ps], opts=opts)
