@@ -21,6 +21,9 @@ adasap   -- Alg. 1 (SAP), Alg. 2 (ADASAP), Alg. 4 (Nystrom), the Woodbury
             applies of App. C.2, Alg. 5 (GetStepsize), Alg. 6 (NesterovAcc).
 gp       -- dense Cholesky reference solve, posterior mean, residuals,
             hyperparameter adjoint.
+pathwise -- random-feature prior draws, pathwise-conditioned posterior
+            samples (Sec. 2.1), the textbook posterior covariance, test RMSE
+            and NLL.
 
 Parity status: every public function is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` against something other than itself (a library
