@@ -227,6 +227,40 @@ adasap_status adasap_predict(adasap_ctx* ctx, const float* Xtest, int64_t m, con
 adasap_status adasap_residual(adasap_ctx* ctx, const float* Y, const float* W, int s, double* rel,
                               void* stream);
 
+/* Random-feature prior draws for pathwise conditioning (Sec. 2.1; Rahimi & Recht
+ * features, q = 2048 in the paper's runs, App. D.3):
+ *   F[i][j] = sqrt(2 sigma2 / q) * sum_l theta[l][j] cos(omega_l . x_i + phase_l),
+ *   omega_l = z_l / ell (RBF) or z_l * sqrt(2 nu / u_l) / ell (Matern-nu, nu = 3/2, 5/2),
+ * so that E[F[i][j] F[i'][j]] = k(x_i, x_i').  The caller draws the randomness:
+ * z (q x d) ~ N(0, 1), u (q) ~ chi^2(2 nu) (ignored for RBF, may be NULL then),
+ * phase (q) ~ U[0, 2 pi), theta (q x s) ~ N(0, 1).  Xq (m x d) raw points;
+ * F (m x s).  All device.  Synchronises `stream`. */
+adasap_status adasap_rf_prior(adasap_ctx* ctx, const float* Xq, int64_t m, const float* z, const float* u,
+                              const float* phase, const float* theta, int q, int s, float* F, void* stream);
+
+/* Posterior samples by pathwise conditioning (Sec. 2.1, eq. pathwise_conditoning,
+ * with the prior cross-covariance k(X*, X) in front of the solve):
+ *   f_n(X*)_j = f_j(X*) + k(X*, X) W_j,  W_j = (K + lambda I)^{-1} (y - f_j(X) - zeta_j),
+ * for ns samples j, f_j the random-feature draws of adasap_rf_prior (z, u, phase,
+ * theta (q x ns)) and zeta (n x ns) ~ N(0, lambda I) drawn by the caller.  All
+ * ns (+ 1) systems are one ADASAP solve with opts (adasap_solve).  With
+ * with_mean = 1 column 0 of W and out is the posterior mean (right-hand side y,
+ * no prior draw) and the samples are columns 1..ns.  y (n), Xtest (m x d), out
+ * (m x (ns + with_mean)), W (n x (ns + with_mean), W_0 on entry) all device.
+ * Returns the solve's status (ADASAP_ENOTCONVERGED keeps W and out valid). */
+adasap_status adasap_pathwise(adasap_ctx* ctx, const float* y, const float* Xtest, int64_t m, const float* z,
+                              const float* u, const float* phase, const float* theta, int q, const float* zeta,
+                              int ns, int with_mean, const adasap_opts* opts, float* out, float* W,
+                              adasap_stats* stats, void* stream);
+
+/* Test metrics of Sec. 5.1 (the paper reports them without formulas): RMSE of
+ * the posterior mean, and the mean NLL of ytest under N(mean_i, var_i + noise)
+ * with var_i the sample variance (divisor s - 1) of the s samples at point i.
+ * mean (row stride ld_mean), samples (m x s, row stride ld_samples), ytest (m)
+ * device; FP64 sums.  s >= 2.  Synchronises `stream`. */
+adasap_status adasap_rmse_nll(const float* mean, int64_t ld_mean, const float* samples, int64_t ld_samples, int s,
+                              const float* ytest, int64_t m, double noise, double* rmse, double* nll, void* stream);
+
 /* Kernel adjoint for hyperparameter fitting (App. D.1):
  *   d_ell    = sum_c G[:,c]^T (dK/dell)    W[:,c]
  *   d_sigma2 = sum_c G[:,c]^T (dK/dsigma2) W[:,c]

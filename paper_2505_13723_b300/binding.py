@@ -36,7 +36,7 @@ SYMBOLS = ["adasap_default_opts", "adasap_status_string", "adasap_last_error", "
            "adasap_solver_scalars", "adasap_solver_end", "adasap_solver_graph_kernels",
            "adasap_solver_diag", "adasap_set_precision",
            "adasap_kernel_rows_noalloc", "adasap_measure_pipes", "adasap_residual",
-           "adasap_solve_batched"]
+           "adasap_solve_batched", "adasap_rf_prior", "adasap_pathwise", "adasap_rmse_nll"]
 
 
 class Opts(ctypes.Structure):
@@ -96,6 +96,14 @@ _lib.adasap_residual.restype = ctypes.c_int
 _lib.adasap_solve_batched.argtypes = [ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int,
                                       ctypes.POINTER(Opts), ctypes.POINTER(_P), ctypes.POINTER(Stats), _P]
 _lib.adasap_solve_batched.restype = ctypes.c_int
+_lib.adasap_rf_prior.argtypes = [_P, _P, _I64, _P, _P, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P]
+_lib.adasap_rf_prior.restype = ctypes.c_int
+_lib.adasap_pathwise.argtypes = [_P, _P, _P, _I64, _P, _P, _P, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(Opts), _P, _P, ctypes.POINTER(Stats), _P]
+_lib.adasap_pathwise.restype = ctypes.c_int
+_lib.adasap_rmse_nll.argtypes = [_P, _I64, _P, _I64, ctypes.c_int, _P, _I64, ctypes.c_double,
+                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _P]
+_lib.adasap_rmse_nll.restype = ctypes.c_int
 _lib.adasap_solver_end.argtypes = [_P]
 _lib.adasap_solver_end.restype = None
 for _f in ["adasap_solver_begin", "adasap_solver_step", "adasap_solver_residual", "adasap_solver_get_w",
@@ -254,6 +262,34 @@ class Context:
                                     _stream(stream)), "adasap_residual")
         return rel.value
 
+    def rf_prior(self, Xq, z, u, phase, theta, stream=None):
+        """adasap_rf_prior: random-feature prior draws f(Xq) (m x s); all device tensors."""
+        m, q, s = Xq.shape[0], z.shape[0], theta.shape[1]
+        F = torch.empty(m, s, device=Xq.device, dtype=torch.float32)
+        _check(_lib.adasap_rf_prior(self.h, _dev_f32(Xq, "Xq"), m, _dev_f32(z, "z"),
+                                    _dev_f32(u, "u") if u is not None else None, _dev_f32(phase, "phase"),
+                                    _dev_f32(theta, "theta"), q, s, _dev_f32(F, "F"), _stream(stream)),
+               "adasap_rf_prior")
+        return F
+
+    def pathwise(self, y, Xtest, z, u, phase, theta, zeta, with_mean=True, opts=None, W=None, stream=None, **kw):
+        """adasap_pathwise: (out (m x (ns + with_mean)), W, stats, status); column 0 = posterior
+        mean when with_mean.  All device tensors."""
+        m, q, ns = Xtest.shape[0], z.shape[0], theta.shape[1]
+        sc = ns + (1 if with_mean else 0)
+        o = opts if opts is not None else default_opts(self.n, **kw)
+        if W is None:
+            W = torch.zeros(self.n, sc, device=y.device, dtype=torch.float32)
+        out = torch.empty(m, sc, device=y.device, dtype=torch.float32)
+        st = Stats()
+        status = _lib.adasap_pathwise(self.h, _dev_f32(y, "y"), _dev_f32(Xtest, "Xtest"), m, _dev_f32(z, "z"),
+                                      _dev_f32(u, "u") if u is not None else None, _dev_f32(phase, "phase"),
+                                      _dev_f32(theta, "theta"), q, _dev_f32(zeta, "zeta"), ns, int(bool(with_mean)),
+                                      ctypes.byref(o), _dev_f32(out, "out"), _dev_f32(W, "W"), ctypes.byref(st),
+                                      _stream(stream))
+        _check(status, "adasap_pathwise", allow=(7,))
+        return out, W, st.as_dict(), status
+
     def predict(self, Xtest, W, stream=None):
         W2 = W if W.dim() == 2 else W.view(-1, 1)
         m, s = Xtest.shape[0], W2.shape[1]
@@ -353,6 +389,23 @@ def solve_batched(contexts, Ys, opts=None, Ws=None, stream=None):
     status = _lib.adasap_solve_batched(k, ctx_arr, y_arr, s, o_arr, w_arr, st_arr, _stream(stream))
     _check(status, "adasap_solve_batched", allow=(7,))
     return Ws, [st.as_dict() for st in st_arr], status
+
+
+def rmse_nll(mean, samples, ytest, noise, stream=None):
+    """adasap_rmse_nll on device tensors: mean (m,) or a column view, samples (m, s) (row stride
+    may exceed s), ytest (m,).  Returns (rmse, nll)."""
+    m, s = samples.shape
+    for t, name in ((mean, "mean"), (samples, "samples"), (ytest, "ytest")):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32):
+            raise TypeError("%s must be a float32 CUDA tensor" % name)
+    if samples.stride(1) != 1 or ytest.stride(0) != 1:
+        raise TypeError("samples rows and ytest must be contiguous")
+    ldm = mean.stride(0)
+    rm, nl = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.adasap_rmse_nll(ctypes.c_void_p(mean.data_ptr()), ldm, ctypes.c_void_p(samples.data_ptr()),
+                                samples.stride(0), s, ctypes.c_void_p(ytest.data_ptr()), m, float(noise),
+                                ctypes.byref(rm), ctypes.byref(nl), _stream(stream)), "adasap_rmse_nll")
+    return rm.value, nl.value
 
 
 def measure_pipes(stream=None):

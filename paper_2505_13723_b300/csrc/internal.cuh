@@ -64,6 +64,21 @@ cudaError_t launch_iota32(int* out, int64_t start, int64_t m, cudaStream_t st);
 // int64 indices -> int32, entries outside [0, n) become -1.
 cudaError_t launch_index32(const int64_t* in, int64_t m, int64_t n, int* out, cudaStream_t st);
 
+// ---- random-feature prior and pathwise conditioning (pathwise.cu) -------------------
+cudaError_t rf_init();
+// omega (q x dp) and phase constants for points in the context's x' form.
+cudaError_t launch_rf_prep(const float* z, const float* u, const float* phase, int q, int d, int dp, int kern,
+                           const double* mean, double ell, double kappa, float* omega, float* cphase,
+                           cudaStream_t st);
+// out[i][coff + j] = scale * sum_l theta[l][j] cos(omega_l . x_i + c_l) + (y ? y[i] : 0)
+//                    + gz * zin[i][zoff + j]   (zin may alias out)
+cudaError_t launch_rf_apply(const float* x, int64_t m, int dp, const float* omega, const float* cphase,
+                            const float* theta, int q, int s, float scale, const float* y, const float* zin,
+                            int64_t ldz, int zoff, float gz, float* out, int64_t ldo, int coff, cudaStream_t st);
+// per-block [sum err^2, sum nll] of the test metrics (blocks x 2 doubles)
+cudaError_t launch_rmse_nll(const float* mean, int64_t ldm, const float* smp, int64_t lds, int s, const float* yt,
+                            int64_t m, double noise, double* parts, int blocks, cudaStream_t st);
+
 // ---- tensor-core block-row product (rows_tc.cu) ------------------------------------
 // One block-row product on the tensor cores (rows_tc.cu): rows (x', q) with an
 // optional row index, the column operands in the split canonical layout, w.

@@ -180,6 +180,7 @@ adasap_status adasap_create(const float* X, int64_t n, int d, int kernel, float 
   if (core_init() != cudaSuccess) { note_error(cudaGetLastError(), "core_init"); return fail(ADASAP_ECUDA); }
   if (tc_init() != cudaSuccess) { note_error(cudaGetLastError(), "tc_init"); return fail(ADASAP_ECUDA); }
   if (tc_mrhs_init() != cudaSuccess) { note_error(cudaGetLastError(), "tc_mrhs_init"); return fail(ADASAP_ECUDA); }
+  if (rf_init() != cudaSuccess) { note_error(cudaGetLastError(), "rf_init"); return fail(ADASAP_ECUDA); }
   c->n = n;
   c->d = d;
   c->dp = padded_dim(d);
@@ -1497,6 +1498,92 @@ extern "C" adasap_status adasap_solve_batched(int nsys, adasap_ctx* const* ctxs,
   } catch (...) {
     return ADASAP_ENOMEM;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Pathwise conditioning (Sec. 2.1): random-feature prior draws, the s-column
+// solve, the samples at test points, and their test metrics.
+// ---------------------------------------------------------------------------
+extern "C" adasap_status adasap_rf_prior(adasap_ctx* c, const float* Xq, int64_t m, const float* z, const float* u,
+                                         const float* phase, const float* theta, int q, int s, float* F,
+                                         void* stream) {
+  if (!c || !Xq || !z || !phase || !theta || !F || m < 1 || m >= (1LL << 31) || q < 1 || s < 1 || s > kMaxRhs ||
+      (c->kern != ADASAP_RBF && !u))
+    return ADASAP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Arena ar;
+  float* xt = ar.get<float>((size_t)m * c->dp);
+  float* qt = ar.get<float>((size_t)m);
+  float* om = ar.get<float>((size_t)q * c->dp);
+  float* cph = ar.get<float>((size_t)q);
+  if (ar.err != cudaSuccess) return ADASAP_ENOMEM;
+  CT(launch_transform(Xq, m, c->d, c->dp, c->mean_dev, c->kappa / (double)c->ell, xt, qt, st));
+  CT(launch_rf_prep(z, u, phase, q, c->d, c->dp, c->kern, c->mean_dev, c->ell, c->kappa, om, cph, st));
+  CT(launch_rf_apply(xt, m, c->dp, om, cph, theta, q, s, (float)std::sqrt(2.0 * c->sigma2 / q), nullptr, nullptr, 0,
+                     0, 0.f, F, s, 0, st));
+  CT(cudaStreamSynchronize(st));  // the arena frees its buffers on return
+  return ADASAP_OK;
+}
+
+extern "C" adasap_status adasap_pathwise(adasap_ctx* c, const float* y, const float* Xtest, int64_t m,
+                                         const float* z, const float* u, const float* phase, const float* theta,
+                                         int q, const float* zeta, int ns, int with_mean, const adasap_opts* o,
+                                         float* out, float* W, adasap_stats* stats, void* stream) {
+  const int sc = ns + (with_mean ? 1 : 0);
+  if (!c || !y || !Xtest || !z || !phase || !theta || !zeta || !o || !out || !W || m < 1 || m >= (1LL << 31) ||
+      q < 1 || ns < 1 || sc > kMaxRhs || (c->kern != ADASAP_RBF && !u))
+    return ADASAP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = c->n;
+  const int off = with_mean ? 1 : 0;
+  const float scale = (float)std::sqrt(2.0 * c->sigma2 / q);
+  Arena ar;
+  float* R = ar.get<float>((size_t)n * sc);
+  float* om = ar.get<float>((size_t)q * c->dp);
+  float* cph = ar.get<float>((size_t)q);
+  float* xt = ar.get<float>((size_t)m * c->dp);
+  float* qt = ar.get<float>((size_t)m);
+  if (ar.err != cudaSuccess) return ADASAP_ENOMEM;
+  CT(launch_rf_prep(z, u, phase, q, c->d, c->dp, c->kern, c->mean_dev, c->ell, c->kappa, om, cph, st));
+  // right-hand sides: [y,] y - f_j(X) - zeta_j
+  if (with_mean)
+    CT(launch_reduce(y, 1, n, 1, 0, 1, R, sc, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, nullptr, st));
+  CT(launch_rf_apply(c->Xc, n, c->dp, om, cph, theta, q, ns, -scale, y, zeta, ns, 0, -1.f, R, sc, off, st));
+  // W = (K + lambda I)^{-1} R by ADASAP (one solve for all columns)
+  const adasap_status s1 = adasap_solve(c, R, sc, o, W, stats, stream);
+  if (s1 != ADASAP_OK && s1 != ADASAP_ENOTCONVERGED) return s1;
+  // samples: k(X*, X) W [+ f(X*) on the sample columns]
+  const adasap_status s2 = adasap_predict(c, Xtest, m, W, sc, out, stream);
+  if (s2 != ADASAP_OK) return s2;
+  CT(launch_transform(Xtest, m, c->d, c->dp, c->mean_dev, c->kappa / (double)c->ell, xt, qt, st));
+  CT(launch_rf_apply(xt, m, c->dp, om, cph, theta, q, ns, scale, nullptr, out, sc, off, 1.f, out, sc, off, st));
+  CT(cudaStreamSynchronize(st));
+  return s1;
+}
+
+extern "C" adasap_status adasap_rmse_nll(const float* mean, int64_t ld_mean, const float* samples,
+                                         int64_t ld_samples, int s, const float* ytest, int64_t m, double noise,
+                                         double* rmse, double* nll, void* stream) {
+  if (!mean || !samples || !ytest || !rmse || !nll || m < 1 || s < 2 || ld_mean < 1 || ld_samples < s ||
+      !(noise >= 0.0))
+    return ADASAP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int blocks = (int)std::min<int64_t>((m + 255) / 256, 296);
+  Arena ar;
+  double* parts = ar.get<double>((size_t)2 * blocks);
+  if (ar.err != cudaSuccess) return ADASAP_ENOMEM;
+  CT(launch_rmse_nll(mean, ld_mean, samples, ld_samples, s, ytest, m, noise, parts, blocks, st));
+  std::vector<double> h((size_t)2 * blocks);
+  CT(cudaMemcpyAsync(h.data(), parts, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CT(cudaStreamSynchronize(st));
+  double se = 0.0, nl = 0.0;
+  for (int b = 0; b < blocks; ++b) {
+    se += h[2 * b];
+    nl += h[2 * b + 1];
+  }
+  *rmse = std::sqrt(se / (double)m);
+  *nll = nl / (double)m;
+  return ADASAP_OK;
 }
 
 extern "C" adasap_status adasap_solver_graph_kernels(adasap_solver* S, int* count) {

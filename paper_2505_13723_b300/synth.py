@@ -127,3 +127,16 @@ def schedule_fn(B, Om, v0):
     def sched(t):
         return B[t], Om[t].astype(np.float64), v0[t].astype(np.float64)
     return sched
+
+
+def rf_draws(q, d, dof, ns, n, noise, seed=7):
+    """Randomness of the random-feature prior and of pathwise conditioning:
+    z (q, d) ~ N(0, 1), u (q,) ~ chi^2(dof) (None when dof is None), phase (q,) ~ U[0, 2 pi),
+    theta (q, ns) ~ N(0, 1), zeta (n, ns) ~ N(0, noise).  All float32."""
+    rng = np.random.default_rng(seed)
+    z = rng.standard_normal((q, d)).astype(np.float32)
+    u = rng.chisquare(dof, q).astype(np.float32) if dof is not None else None
+    phase = rng.uniform(0.0, 2.0 * np.pi, q).astype(np.float32)
+    theta = rng.standard_normal((q, ns)).astype(np.float32)
+    zeta = (np.sqrt(noise) * rng.standard_normal((n, ns))).astype(np.float32)
+    return z, u, phase, theta, zeta
