@@ -357,10 +357,12 @@ def run_ours(args, rank, world, dist):
             return e0.elapsed_time(e1) / iters
 
         mixed_batched = per_iter(lib.PREC_TF32X3, Yq)
+        tf32_batched = per_iter(lib.PREC_TF32, Yq)
         fp32_single = per_iter(lib.PREC_FP32, Yq[:, :1].contiguous())
         cq.close()
         multi = {"workload": "multirhs: n=262144, d=16, X~N(0,I), RBF ell=2, lambda=1e-2, b=4096, r=64, s=64",
                  "ms_per_iteration_mixed_batched_s64": mixed_batched,
+                 "ms_per_iteration_tf32_single_pass_contraction_s64": tf32_batched,
                  "ms_per_iteration_fp32_single_rhs": fp32_single,
                  "speedup_vs_64_fp32_single_rhs_solves": 64.0 * fp32_single / mixed_batched}
 

@@ -63,8 +63,14 @@ typedef enum { ADASAP_RBF = 0, ADASAP_MATERN32 = 1, ADASAP_MATERN52 = 2 } adasap
  *   ADASAP_PREC_TF32X3  distances on the tensor cores (tcgen05, TF32 hi/lo split
  *                       with three products; FP32 epilogue); needs d <= 30.
  * With ADASAP_PREC_TF32X3, products with more than one right-hand side use the
- * multi-RHS tensor-core kernel (W split into TF32 hi/lo as well). */
-typedef enum { ADASAP_PREC_FP32 = 0, ADASAP_PREC_TF32X3 = 1 } adasap_precision;
+ * multi-RHS tensor-core kernel (W split into TF32 hi/lo as well).
+ *   ADASAP_PREC_TF32    as ADASAP_PREC_TF32X3, but the multi-RHS contraction
+ *                       K(X_B, X) W takes one MMA on TF32-rounded kernel values
+ *                       and W (relative rounding 2^-11 per product: error below
+ *                       1e-3 of sum_j |k_ij||w_j|); the low-precision mode of the
+ *                       contraction.  Single-RHS products and the sketch keep
+ *                       the split arithmetic. */
+typedef enum { ADASAP_PREC_FP32 = 0, ADASAP_PREC_TF32X3 = 1, ADASAP_PREC_TF32 = 2 } adasap_precision;
 
 /* Options of adasap_solve.  adasap_default_opts fills the paper's defaults. */
 typedef struct {

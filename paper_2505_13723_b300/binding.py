@@ -21,7 +21,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 RBF, MATERN32, MATERN52 = 0, 1, 2
-PREC_FP32, PREC_TF32X3 = 0, 1
+PREC_FP32, PREC_TF32X3, PREC_TF32 = 0, 1, 2
 KERNELS = {"rbf": RBF, "matern32": MATERN32, "matern52": MATERN52}
 
 STATUS = {0: "ADASAP_OK", 1: "ADASAP_EINVAL", 2: "ADASAP_ENOMEM", 3: "ADASAP_ECUDA",

@@ -37,6 +37,7 @@ cudaError_t core_init();
 struct RowsPlan {
   bool tc;     // tensor-core kernel: rows_tc.cu (s == 1) or rows_tc_mrhs.cu (s >= 2)
   bool mrhs;
+  int passes;  // contraction MMAs of the multi-RHS kernel: 3 (split W and K) or 1 (TF32)
   int nsplit;
   int ctas;    // persistent CTAs of the tensor-core kernel (0: one per SM)
   int64_t wop_floats;  // W operand scratch (hi + lo) of the multi-RHS kernel
@@ -77,7 +78,7 @@ struct adasap_ctx {
   DevScalars* sc_host = nullptr;  // pinned
   void* ws = nullptr;             // kernel_rows workspace
   size_t ws_bytes = 0;
-  int prec = 0;                   // ADASAP_PREC_FP32 or ADASAP_PREC_TF32X3
+  int prec = 0;                   // ADASAP_PREC_FP32, ADASAP_PREC_TF32X3 or ADASAP_PREC_TF32
   int kp = 0;                     // K of the tensor-core operands (0: unavailable)
   int64_t npad = 0;
   float* tc_hi = nullptr;         // split column operands of X' (npad x kp, MMA layout)
@@ -303,7 +304,8 @@ adasap_status grow_ws(adasap_ctx* c, size_t bytes) {
 
 RowsPlan plan_rows(const adasap_ctx* c, int64_t m, int64_t ncols, int s, int reserve_sms = 0) {
   RowsPlan p;
-  p.tc = c->prec == ADASAP_PREC_TF32X3 && c->kp > 0;
+  p.tc = c->prec != ADASAP_PREC_FP32 && c->kp > 0;
+  p.passes = c->prec == ADASAP_PREC_TF32 ? 1 : 3;
   p.mrhs = p.tc && s > 1;
   p.ctas = (p.tc && reserve_sms > 0) ? std::max(1, tc_slots() - reserve_sms) : 0;
   p.nsplit = !p.tc ? rows_nsplit(m, ncols, s, c->dp, false)
@@ -321,10 +323,10 @@ cudaError_t run_rows_over_x(const adasap_ctx* c, const RowsPlan& p, const float*
     if (!wop) return cudaErrorInvalidValue;
     float* whi = wop;
     float* wlo = wop + p.wop_floats / 2;
-    cudaError_t e = launch_build_w_tc(w, s, c->n, s, 3, whi, wlo, st);
+    cudaError_t e = launch_build_w_tc(w, s, c->n, s, p.passes, whi, wlo, st);
     if (e != cudaSuccess) return e;
     return launch_rows_tc_mrhs(c->kern, c->d, xr, qr, ridx, m, c->dp, c->tc_hi, c->tc_lo, c->n, self_mode, whi, wlo,
-                               s, 3, part, p.nsplit, c->sigma2, c->err_dev, st, p.ctas);
+                               s, p.passes, part, p.nsplit, c->sigma2, c->err_dev, st, p.ctas);
   }
   if (p.tc)
     return launch_rows_tc(c->kern, c->d, xr, qr, ridx, m, c->dp, c->tc_hi, c->tc_lo, c->n, self_mode, w, s, part,
@@ -335,8 +337,8 @@ cudaError_t run_rows_over_x(const adasap_ctx* c, const RowsPlan& p, const float*
 }  // namespace
 
 extern "C" adasap_status adasap_set_precision(adasap_ctx* c, int prec) {
-  if (!c || (prec != ADASAP_PREC_FP32 && prec != ADASAP_PREC_TF32X3)) return ADASAP_EINVAL;
-  if (prec == ADASAP_PREC_TF32X3 && c->kp == 0) return ADASAP_EINVAL;
+  if (!c || (prec != ADASAP_PREC_FP32 && prec != ADASAP_PREC_TF32X3 && prec != ADASAP_PREC_TF32)) return ADASAP_EINVAL;
+  if (prec != ADASAP_PREC_FP32 && c->kp == 0) return ADASAP_EINVAL;
   c->prec = prec;
   return ADASAP_OK;
 }
@@ -840,7 +842,7 @@ adasap_status solver_prepare(adasap_ctx* c, const float* Y, int s, const adasap_
   S->mc = std::min<int64_t>(n, std::max<int64_t>(1, o->check_rows));
   S->plan1 = plan_rows(c, b, n, s, reserve_sms);
   S->plan_c = plan_rows(c, S->mc, n, s);
-  S->tc_pw = c->prec == ADASAP_PREC_TF32X3 && c->kp > 0;
+  S->tc_pw = c->prec != ADASAP_PREC_FP32 && c->kp > 0;
   S->ns1 = S->plan1.nsplit;
   S->sk_tc = S->tc_pw && !identity && r >= 2;
   S->ns_sk = identity ? 1 : (S->sk_tc ? tc_mrhs_nsplit(b, b) : rows_nsplit(b, b, r, c->dp, false));

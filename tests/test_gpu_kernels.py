@@ -86,6 +86,25 @@ def test_multi_rhs_tensor_core_product_spans_splits(lib, s, kern, d):
     _check_rows(out.astype(np.float64), X, rows, W, kern, ell, 0.9)
 
 
+@pytest.mark.parametrize("kern,d,s", [(0, 16, 64), (1, 11, 2), (2, 8, 100)])
+def test_multi_rhs_single_pass_tf32_contraction(lib, kern, d, s):
+    """ADASAP_PREC_TF32: one MMA on TF32-rounded kernel values and W (2^-11 relative
+    rounding each, so a product is off by at most ~2^-10 relative, plus the FP32
+    accumulation): held to 3e-3 of sum_j |k_ij||w_j|, the low-precision bound; the
+    typical error is far inside it and still far above the split form's."""
+    n, b = 20011, 257
+    X, W = _data(n, d, s, seed=3 * s + kern)
+    ell = 0.8 * np.sqrt(d)
+    ctx = _ctx(lib, X, kern, ell, 1.1, 1e-2, lib.PREC_TF32)
+    rows = np.random.default_rng(s).choice(n, size=b, replace=False)
+    out = ctx.kernel_rows(torch.from_numpy(rows).cuda(), torch.from_numpy(W).cuda()).cpu().numpy()
+    _check_rows(out.astype(np.float64), X, rows, W, kern, ell, 1.1, rtol=3e-3)
+    Xd = X.astype(np.float64)
+    ref = OK.kernel_apply(Xd[rows], Xd, W.astype(np.float64), kern, ell, 1.1)
+    scale = OK.kernel_apply(Xd[rows], Xd, np.abs(W.astype(np.float64)), kern, ell, 1.1)
+    assert np.median(np.abs(out - ref) / scale) < 3e-4
+
+
 @pytest.mark.parametrize("s", [5, 17])
 def test_fp32_wide_product_with_empty_column_splits(lib, s):
     """n = 40,077 columns over the CUDA-core split count leaves the last splits without
