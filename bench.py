@@ -58,11 +58,14 @@ def parse():
     p.add_argument("--no-multi-rhs", action="store_true", help="skip the many-right-hand-sides comparison")
     p.add_argument("--no-batched", action="store_true", help="skip the uneven batch of independent systems")
     p.add_argument("--batched-iters", type=int, default=40, help="iterations of the batched-systems timing")
+    p.add_argument("--no-pathwise", action="store_true", help="skip the pathwise posterior-sampling timing")
     p.add_argument("--n", type=int, default=1 << 20, help="rows of the workload (default: full size)")
     p.add_argument("--kernel-launches", type=int, default=10, help="timed launches of the Step I kernel alone")
     p.add_argument("--tol-iters", type=int, default=6000, help="iteration cap of the time-to-1e-3 solves")
     p.add_argument("--only-kernel", action="store_true",
                    help="run only the Step I block-row product launches (profiling)")
+    p.add_argument("--only-workload", choices=["multirhs", "bo"],
+                   help="run only --warmup + --steps iterations of that workload's solver (profiling)")
     return p.parse_args()
 
 
@@ -210,6 +213,37 @@ def whole_job(t_local, units_local, dist, device):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def run_workload_only(args):
+    """Iterations of one secondary workload alone (for launch lists under ncu): the multirhs
+    solve (s = 64, split precision) or the bo batch (48 systems in one graph)."""
+    import torch
+
+    from paper_2505_13723_b300 import binding as lib
+    from paper_2505_13723_b300 import synth
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    if args.only_workload == "multirhs":
+        Q = synth.multirhs()
+        cq = lib.Context(torch.from_numpy(Q.X).to(dev), Q.kernel, Q.ell, Q.sigma2, Q.lam)
+        so = lib.Solver(cq, torch.from_numpy(Q.Y).to(dev),
+                        opts=lib.default_opts(Q.X.shape[0], b=Q.b, r=Q.r, seed=3, check_every=0,
+                                              max_iters=args.warmup + args.steps))
+        so.step(args.warmup + args.steps)
+        torch.cuda.synchronize()
+        kernels = so.graph_kernels()
+        so.close()
+    else:
+        systems = synth.bo_systems()
+        ctxs = [lib.Context(torch.from_numpy(Q.X).to(dev), Q.kernel, Q.ell, Q.sigma2, Q.lam) for Q in systems]
+        opts = [lib.default_opts(Q.X.shape[0], b=Q.b, r=Q.r, seed=40 + k, check_every=0,
+                                 max_iters=args.warmup + args.steps) for k, Q in enumerate(systems)]
+        lib.solve_batched(ctxs, [torch.from_numpy(Q.Y).to(dev) for Q in systems], opts=opts)
+        torch.cuda.synchronize()
+        kernels = None
+    print(json.dumps({"workload": args.only_workload, "iterations": args.warmup + args.steps,
+                      "kernels_per_iteration": kernels, "wall_s": time.perf_counter() - t0}), flush=True)
+
+
 def run_kernel_only(args):
     """Only the fused block-row products with the benchmark's launch shapes (for ncu):
     Step I (b x n entries, s = 1), then the sketch (b x b entries, r right-hand sides)."""
@@ -399,6 +433,45 @@ def run_ours(args, rank, world, dist):
                    "entries_per_iteration": ent_b, "status": bstatus,
                    "iterations_timed": {"batched": it_b, "one_after_another": it_s}}
 
+    # ---- pathwise conditioning (Sec. 2.1) on the multirhs workload: 2048 random features,
+    # 63 samples plus the posterior mean in one 64-column solve
+    pathwise = None
+    if rank == 0 and not args.no_pathwise:
+        from paper_2505_13723_b300 import synth
+        Q = synth.multirhs()
+        nq, dq = Q.X.shape
+        ns, q = 63, 2048
+        z, u, phase, theta, zeta = synth.rf_draws(q, dq, None, ns, nq, Q.lam, seed=1)
+        cq = lib.Context(torch.from_numpy(Q.X).to(dev), Q.kernel, Q.ell, Q.sigma2, Q.lam)
+        Xq = torch.from_numpy(Q.X).to(dev)
+        zt, pt, tt, zet = [torch.from_numpy(a).to(dev) for a in (z, phase, theta, zeta)]
+        for _ in range(2):
+            cq.rf_prior(Xq, zt, None, pt, tt)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(5):
+            cq.rf_prior(Xq, zt, None, pt, tt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rf_ms = e0.elapsed_time(e1) / 5
+        it_p = 40
+        yq = torch.from_numpy(Q.Y[:, 0].copy()).to(dev)
+        Xt = torch.from_numpy(Q.Xtest).to(dev)
+        t0 = time.perf_counter()
+        out, _, pst, pstatus = cq.pathwise(yq, Xt, zt, None, pt, tt, zet,
+                                           opts=lib.default_opts(nq, b=Q.b, r=Q.r, seed=2, check_every=0,
+                                                                 max_iters=it_p))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        cq.close()
+        pathwise = {"workload": "multirhs: n=262144, d=16, RBF ell=2, lambda=1e-2; q=2048 random features, "
+                                "63 samples + posterior mean (s=64), 10000 test points, b=4096, r=64",
+                    "rf_prior_ms_n262144_q2048_s63": rf_ms,
+                    "rf_prior_gflops": 2.0 * nq * q * ns / (rf_ms * 1e-3) / 1e9,
+                    "solve_ms_per_iteration": 1e3 * pst["seconds"] / it_p,
+                    "seconds_total_%d_iterations" % it_p: wall, "status": pstatus}
+
     # ---- end to end through the C-ABI with host buffers
     e2e = None
     if rank == 0:
@@ -458,6 +531,7 @@ def run_ours(args, rank, world, dist):
             "time_to_tol": tol_run,
             "multi_rhs": multi,
             "batched_systems": batched,
+            "pathwise_sampling": pathwise,
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
             "solver_state": {"rel_resid_after": rel, "eta": eta, "rho": rho, "status": status,
                              "jacobi_sweeps": diag["jacobi_sweeps"], "chol_retries": diag["chol_retries"],
@@ -479,7 +553,9 @@ def main():
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
             tdist.init_process_group("nccl")
         dist = tdist
-    if args.only_kernel:
+    if args.only_workload:
+        run_workload_only(args)
+    elif args.only_kernel:
         run_kernel_only(args)
     elif args.impl == "reference":
         run_reference(args, rank, world)
