@@ -80,7 +80,9 @@ typedef struct {
   double tol;          /* stop when the relative residual estimate <= tol (0: never). */
   int power_iters;     /* randomized-powering iterations N of Alg. 5.  Default 10 (App. C.3). */
   double mu, nu;       /* acceleration parameters (Alg. 2); 0 => mu = lambda, nu = n/b (Sec. 4.2). */
-  int precond;         /* 0 = Nystrom (ADASAP), 1 = identity (ADASAP-I, Sec. 5). */
+  int precond;         /* 0 = Nystrom (ADASAP), 1 = identity (ADASAP-I, Sec. 5), 2 = SAP with the
+                          exact block solve (Alg. 1: W_B -= (K_BB + lambda I)^{-1} R_B, no stepsize,
+                          no acceleration; b <= 8192; r, mu, nu, power_iters unused). */
   int literal;         /* 0: residual at Z_t and Z_{t+1} from V_{t+1} (standard accelerated
                           sketch-and-project); 1: residual at W_t and Z_{t+1} from V_t, as
                           Alg. 2 / Alg. 6 print. */
@@ -103,7 +105,8 @@ typedef struct {
   int status_detail;   /* stage of a device-side failure: 1 Nystrom core Cholesky (after 3
                           shift increases), 2 non-finite eigenvalue, 3 Woodbury Cholesky,
                           4 non-positive stepsize estimate, 5 schedule row out of range,
-                          6 Cholesky of the test matrix's Gram (thin QR of Omega) */
+                          6 Cholesky of the test matrix's Gram (thin QR of Omega),
+                          7 non-positive pivot of the exact block solve (precond 2) */
 } adasap_stats;
 
 void adasap_default_opts(adasap_opts* opts, int64_t n);
@@ -176,7 +179,8 @@ adasap_status adasap_solve_scheduled(adasap_ctx* ctx, const float* Y, int s,
  * GP models of a Bayesian-optimisation campaign, Sec. 5.3).  System i is
  * ctxs[i] with Y[i] and W[i] (n_i x s, host or device; W[i] holds W_0 on entry
  * and the returned iterate on exit) and its own options opts[i] (Alg. 2 as in
- * adasap_solve; tail_average must be 0, power_iters the same for all).  One CUDA graph holds one iteration of
+ * adasap_solve; tail_average must be 0, precond 0 or 1, power_iters the same
+ * for all).  One CUDA graph holds one iteration of
  * every system still running, each system on its context's streams; the Step I
  * products and the K_BB a products of Alg. 5 of all systems that use the
  * single-right-hand-side tensor-core kernel (s = 1, ADASAP_PREC_TF32X3, Nystrom

@@ -117,7 +117,8 @@ struct DevScalars {
   int status;        // first error (adasap_status), 0 if none
   int detail;        // stage of the first error: 1 Nystrom core Cholesky, 2 non-finite
                      // eigenvalue, 3 Woodbury Cholesky, 4 non-positive stepsize estimate,
-                     // 5 schedule row out of range, 6 test-matrix QR Cholesky
+                     // 5 schedule row out of range, 6 test-matrix QR Cholesky,
+                     // 7 exact block Cholesky (SAP)
   int chol_retries;  // number of Delta increases in the last iteration
   int jacobi_sweeps; // sweeps of the last eigen-solve
   long long t;       // iteration counter

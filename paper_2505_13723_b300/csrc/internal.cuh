@@ -64,6 +64,23 @@ cudaError_t launch_iota32(int* out, int64_t start, int64_t m, cudaStream_t st);
 // int64 indices -> int32, entries outside [0, n) become -1.
 cudaError_t launch_index32(const int64_t* in, int64_t m, int64_t n, int* out, cudaStream_t st);
 
+// ---- exact block solve of Alg. 1 (blockchol.cu) ------------------------------------
+constexpr int64_t kMaxExactBlock = 8192;   // b of the exact solve (two bp x bp FP32 matrices)
+int64_t chol_pad(int64_t b);               // b rounded up to the 32-row tile
+// H = sigma2 k(X_B, X_B) + lambda I (bp x bp, identity padding) from the gathered block
+cudaError_t launch_form_h(int kern, const float* xb, int64_t b, int dp, float sigma2, float lam, float* H,
+                          cudaStream_t st);
+// blocked Cholesky in place (lower triangle of A), inverted diagonal tiles in Linv (bp x 32)
+cudaError_t launch_block_chol(float* A, int64_t b, float* Linv, DevScalars* sc, cudaStream_t st);
+// D = (L L^T)^{-1} R (add = 0) or D += (L L^T)^{-1} R (add = 1); R, D, Y: bp x s
+cudaError_t launch_chol_solve(const float* L, int64_t b, const float* Linv, const float* R, int s, float* Y,
+                              float* D, int add, cudaStream_t st);
+// E = R - H D, FP64 sums
+cudaError_t launch_h_residual(const float* H, int64_t b, const float* D, const float* R, int s, float* E,
+                              cudaStream_t st);
+// W[B[i]] -= D[i]
+cudaError_t launch_block_sub(float* W, const int* B, int64_t b, int s, const float* D, cudaStream_t st);
+
 // ---- random-feature prior and pathwise conditioning (pathwise.cu) -------------------
 cudaError_t rf_init();
 // omega (q x dp) and phase constants for points in the context's x' form.

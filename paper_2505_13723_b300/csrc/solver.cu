@@ -486,7 +486,10 @@ struct adasap_solver {
   int s = 1;
   adasap_opts o{};
   bool sched = false;
-  bool identity = false;
+  bool identity = false;           // no Nystrom sketch (ADASAP-I, or the exact solve)
+  bool exact = false;              // Alg. 1 with the exact block solve (Cholesky of K_BB + lambda I)
+  float *Hf = nullptr, *Hc = nullptr, *Linv = nullptr;   // factor, copy of H, inverted diagonal tiles
+  float *Rp = nullptr, *Dp = nullptr, *Yp = nullptr, *Ep = nullptr;  // padded b x s blocks
   int r = 0;
   int64_t b = 0, mc = 0;
   int ns1 = 1, ns_sk = 1, ns_pw = 1, ns_c = 1;
@@ -551,6 +554,19 @@ adasap_status alloc_solver(adasap_solver* S) {
   const int64_t wop = std::max(S->plan1.wop_floats, S->plan_c.wop_floats);
   if (wop > 0) S->wop1 = ar.get<float>((size_t)wop);
   if (S->sk_tc) S->wsk = ar.get<float>((size_t)2 * tc_mrhs_wfloats(b, r));
+  if (S->exact) {
+    const size_t bp = (size_t)chol_pad(b);
+    S->Hf = ar.get<float>(bp * bp);
+    S->Hc = ar.get<float>(bp * bp);
+    S->Linv = ar.get<float>(bp * 32);
+    S->Rp = ar.get<float>(bp * s);
+    S->Dp = ar.get<float>(bp * s);
+    S->Yp = ar.get<float>(bp * s);
+    S->Ep = ar.get<float>(bp * s);
+    if (ar.err != cudaSuccess) return ADASAP_ENOMEM;
+    for (float* z : {S->Rp, S->Dp, S->Yp, S->Ep})
+      if (cudaMemset(z, 0, bp * s * sizeof(float)) != cudaSuccess) return ADASAP_ECUDA;
+  }
   S->Ysk = ar.get<float>((size_t)b * rr);
   S->a = ar.get<float>(b);
   S->h = ar.get<float>(b);
@@ -776,8 +792,42 @@ cudaError_t rec_update(adasap_solver* S, double* trace) {
   return launch_tick(c->sc, s0);
 }
 
+// One iteration of Alg. 1 (SAP) with the exact block solve: the factorisation of
+// K_BB + lambda I (branch s1) beside the Step I product at W_t (s0), then the
+// refined substitution and W_B -= D.
+cudaError_t rec_iteration_exact(adasap_solver* S, const int64_t* Bs, const float* v0s, double* trace) {
+  adasap_ctx* c = S->c;
+  cudaStream_t s0 = c->s0, s1 = c->s1;
+  const int64_t n = c->n, b = S->b;
+  const int s = S->s;
+  const long long* tdev = &c->sc->t;
+  if (S->sched) KR(launch_copy_schedule(Bs, nullptr, v0s, tdev, n, b, 0, S->B32, nullptr, S->v0, c->sc, s0));
+  else KR(launch_sample_block(S->o.seed, tdev, 0, n, b, 1, S->B32, nullptr, s0));
+  KR(launch_gather(c->Xc, c->qc, S->B32, b, c->dp, S->XB, S->qB, s0));
+  KR(cudaEventRecord(c->ev_fork, s0));
+  KR(cudaStreamWaitEvent(s1, c->ev_fork, 0));
+  const size_t bp = (size_t)chol_pad(b);
+  KR(launch_form_h(c->kern, S->XB, b, c->dp, c->sigma2, c->lambda, S->Hf, s1));
+  KR(cudaMemcpyAsync(S->Hc, S->Hf, bp * bp * sizeof(float), cudaMemcpyDeviceToDevice, s1));
+  KR(launch_block_chol(S->Hf, b, S->Linv, c->sc, s1));
+  KR(cudaEventRecord(c->ev_join, s1));
+  KR(run_rows_over_x(c, S->plan1, c->Xc, c->qc, S->B32, b, S->W, s, S->part1, 1, s0, S->wop1));
+  KR(launch_reduce(S->part1, S->ns1, b, s, 0, s, S->Rp, s, (float)c->lambda, S->W, S->B32, s, -1.f, S->Y, S->B32, s,
+                   nullptr, s0));
+  KR(cudaStreamWaitEvent(s0, c->ev_join, 0));
+  KR(launch_chol_solve(S->Hf, b, S->Linv, S->Rp, s, S->Yp, S->Dp, 0, s0));
+  for (int k = 0; k < 2; ++k) {
+    KR(launch_h_residual(S->Hc, b, S->Dp, S->Rp, s, S->Ep, s0));
+    KR(launch_chol_solve(S->Hf, b, S->Linv, S->Ep, s, S->Yp, S->Dp, 1, s0));
+  }
+  KR(launch_block_sub(S->W, S->B32, b, s, S->Dp, s0));
+  if (trace) KR(launch_trace(c->sc, trace, s0));
+  return launch_tick(c->sc, s0);
+}
+
 // the whole iteration of one system
 cudaError_t rec_iteration(adasap_solver* S, const int64_t* Bs, const float* v0s, double* trace) {
+  if (S->exact) return rec_iteration_exact(S, Bs, v0s, trace);
   KR(rec_head(S, Bs, v0s));
   KR(rec_step1(S));
   KR(rec_step1_finish(S));
@@ -815,9 +865,11 @@ adasap_status solver_prepare(adasap_ctx* c, const float* Y, int s, const adasap_
   if (!c || !Y || !o || !out || s < 1 || s > kMaxRhs) return ADASAP_EINVAL;
   *out = nullptr;
   const int64_t n = c->n, b = o->b;
-  const bool identity = o->precond == 1;
+  const bool exact = o->precond == 2;            // Alg. 1 (SAP): exact block solve
+  const bool identity = o->precond == 1 || exact;  // no Nystrom sketch
   const int r = identity ? 0 : o->r;
-  if (b < 1 || b > n || o->power_iters < 1 || (o->precond != 0 && o->precond != 1)) return ADASAP_EINVAL;
+  if (b < 1 || b > n || o->power_iters < 1 || o->precond < 0 || o->precond > 2) return ADASAP_EINVAL;
+  if (exact && b > kMaxExactBlock) return ADASAP_EINVAL;
   if (!identity && (r < 1 || r > kMaxRank || r > b)) return ADASAP_EINVAL;
   if (Bs && (!v0s || (!identity && !Oms))) return ADASAP_EINVAL;
   adasap_solver* S = new (std::nothrow) adasap_solver();
@@ -829,6 +881,7 @@ adasap_status solver_prepare(adasap_ctx* c, const float* Y, int s, const adasap_
   S->T_sched = T_sched;
   S->Oms_sched = Oms;
   S->identity = identity;
+  S->exact = exact;
   S->r = r;
   S->b = b;
   const double lam = c->lambda;
@@ -1367,7 +1420,7 @@ adasap_status rebuild(Batch& bt) {
 adasap_status solve_batched(int nsys, adasap_ctx* const* ctxs, const float* const* Y, int s,
                             const adasap_opts* opts, float* const* W, adasap_stats* stats, cudaStream_t us) {
   for (int i = 0; i < nsys; ++i) {
-    if (!ctxs[i] || !Y[i] || !W[i] || opts[i].tail_average || opts[i].max_iters < 0 ||
+    if (!ctxs[i] || !Y[i] || !W[i] || opts[i].tail_average || opts[i].max_iters < 0 || opts[i].precond == 2 ||
         opts[i].power_iters != opts[0].power_iters)
       return ADASAP_EINVAL;
     for (int j = 0; j < i; ++j)
