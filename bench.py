@@ -59,6 +59,7 @@ def parse():
     p.add_argument("--no-batched", action="store_true", help="skip the uneven batch of independent systems")
     p.add_argument("--batched-iters", type=int, default=40, help="iterations of the batched-systems timing")
     p.add_argument("--no-pathwise", action="store_true", help="skip the pathwise posterior-sampling timing")
+    p.add_argument("--no-sap", action="store_true", help="skip the exact-block-solve SAP timing")
     p.add_argument("--n", type=int, default=1 << 20, help="rows of the workload (default: full size)")
     p.add_argument("--kernel-launches", type=int, default=10, help="timed launches of the Step I kernel alone")
     p.add_argument("--tol-iters", type=int, default=6000, help="iteration cap of the time-to-1e-3 solves")
@@ -472,6 +473,25 @@ def run_ours(args, rank, world, dist):
                     "solve_ms_per_iteration": 1e3 * pst["seconds"] / it_p,
                     "seconds_total_%d_iterations" % it_p: wall, "status": pstatus}
 
+    # ---- Alg. 1 (SAP) with the exact block solve at b = 4096 on the benchmark workload, against
+    # ADASAP (Nystrom, r = 100) at the same block size: device time per iteration
+    sap = None
+    if rank == 0 and not args.no_sap:
+        sap = {"workload": "regress (n=%d) with b=4096" % n}
+        for name, extra in (("sap_exact", dict(precond=2)), ("adasap_r100", dict(r=100))):
+            so = lib.Solver(ctx, Yd, opts=lib.default_opts(n, b=4096, seed=6, check_every=0, max_iters=20, **extra))
+            so.step(2)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            so.step(8)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sap[name + "_ms_per_iteration"] = e0.elapsed_time(e1) / 8
+            sap[name + "_rel_resid_after_10"] = so.residual()
+            so.close()
+        sap["cholesky_flops_per_iteration"] = 4096 ** 3 / 3
+
     # ---- end to end through the C-ABI with host buffers
     e2e = None
     if rank == 0:
@@ -532,6 +552,7 @@ def run_ours(args, rank, world, dist):
             "multi_rhs": multi,
             "batched_systems": batched,
             "pathwise_sampling": pathwise,
+            "sap_exact_block": sap,
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
             "solver_state": {"rel_resid_after": rel, "eta": eta, "rho": rho, "status": status,
                              "jacobi_sweeps": diag["jacobi_sweeps"], "chol_retries": diag["chol_retries"],
