@@ -40,13 +40,18 @@ constexpr int kTcEpiWarps = 16;
 constexpr int kTcThreadsV2 = 32 * (4 + kTcEpiWarps);   // producer, MMA, 2 idle, epilogue
 constexpr int kTcWArrays = 3;                          // w, w / log2e, w / (3 log2e^2)
 
-constexpr int kTcStages = 4;                           // column-operand ring depth
+constexpr int kTcBufs = 4;                             // TMEM distance buffers and w stages
+constexpr uint32_t kTcTmemCols = kTcBufs * kTcN;       // 512: the whole TMEM of the SM
 
 template <int KP>
 struct TcSmem {
   static constexpr int OPF = kTcM * KP;  // floats per 128-row operand tile
-  static constexpr size_t ops_bytes = (size_t)(2 + 2 * kTcStages) * OPF * sizeof(float);
-  static constexpr size_t w_bytes = (size_t)2 * kTcWArrays * kTcN * sizeof(float);   // [buf][array][128]
+  // column-operand ring depth: copies are issued this many tiles ahead of the MMAs,
+  // enough to cover the copy latency under load (shared memory: 8 x 16 KB at KP = 16,
+  // 5 x 32 KB at KP = 32)
+  static constexpr int kStages = KP == 16 ? 8 : 5;
+  static constexpr size_t ops_bytes = (size_t)(2 + 2 * kStages) * OPF * sizeof(float);
+  static constexpr size_t w_bytes = (size_t)kTcBufs * kTcWArrays * kTcN * sizeof(float);   // [buf][array][128]
   static constexpr size_t red_bytes = (size_t)4 * kTcM * sizeof(float);               // column-group partials
   static constexpr size_t bytes = ops_bytes + w_bytes + red_bytes + 32 * sizeof(uint64_t) + 64 + 1024;
 };
@@ -73,6 +78,7 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
     k_rows_tc(TcArgs a0, const TcArgs* __restrict__ grp, const int64_t* __restrict__ gstart, int ngrp) {
   using L = TcSmem<KP>;
   constexpr int OPF = L::OPF;
+  constexpr int kTcStages = L::kStages;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   float* sAhi = reinterpret_cast<float*>(base);
@@ -83,11 +89,11 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + L::ops_bytes + L::w_bytes + L::red_bytes);
   uint64_t* full = bars;                     // [kTcStages] column tiles landed (copies)
   uint64_t* empty = bars + kTcStages;        // [kTcStages] column tile stage consumed by the MMAs
-  uint64_t* tfull = bars + 2 * kTcStages;    // [2] distance buffer ready
-  uint64_t* tempty = tfull + 2;              // [2] distance buffer and w stage done (16 epilogue warps)
-  uint64_t* wfull = tfull + 4;               // [2] w stage written
-  uint64_t* drain = tfull + 6;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 16);
+  uint64_t* tfull = bars + 2 * kTcStages;    // [kTcBufs] distance buffer ready
+  uint64_t* tempty = tfull + kTcBufs;        // [kTcBufs] distance buffer and w stage done (4 epilogue warps)
+  uint64_t* wfull = tfull + 2 * kTcBufs;     // [kTcBufs] w stage written
+  uint64_t* drain = tfull + 3 * kTcBufs;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -101,9 +107,9 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kTcBufs; ++i) {
       mbar_init(&tfull[i], 1);
-      mbar_init(&tempty[i], kTcEpiWarps);
+      mbar_init(&tempty[i], kTcEpiWarps / kTcBufs);   // the four warps of group i
       mbar_init(&wfull[i], 1);
     }
     mbar_init(drain, 1);
@@ -112,7 +118,7 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"(kTmemCols)
+                 "r"(kTcTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -180,9 +186,19 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
     if (warp == 0) {
       // ---- producer: column tiles by bulk copy (lane 0) up to kTcStages tiles ahead
       // of the MMAs; w of each tile by the whole warp once the epilogue is done with
-      // the w stage (two tiles back) -------------------------------------------------
+      // the w stage (kTcBufs tiles back) ---------------------------------------------
       int xi = 0;  // column tiles issued
       bool ok = true;
+      // w of tile t (zero past the split), loaded two tiles ahead so that the global
+      // load latency overlaps the waits and stores of the tiles in between
+      auto load_w = [&](int t, float (&wv)[4]) {
+        const int64_t jb = c0 + (int64_t)t * kTcN + 4 * lane;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) wv[e] = (t < ntiles && jb + e < c1) ? __ldg(a.w + (jb + e) * a.ldw) : 0.0f;
+      };
+      float wa[4], wb[4];
+      load_w(0, wa);
+      load_w(1, wb);
       for (int t = 0; ok && t < ntiles; ++t) {
         if (lane == 0) {
           for (; xi < ntiles && xi < t + kTcStages; ++xi) {
@@ -198,7 +214,7 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
             bulk_g2s(sB + (st * 2 + 1) * OPF, a.blo + off, OPF * sizeof(float), &full[st]);
           }
           const uint32_t g = gt + (uint32_t)t;
-          if (ok) ok = mbar_wait(&tempty[g & 1], ((g >> 1) & 1u) ^ 1u, abort_flag);
+          if (ok) ok = mbar_wait(&tempty[g % kTcBufs], ((g / kTcBufs) & 1u) ^ 1u, abort_flag);
           if (!ok) {
             *abort_flag = 1;
             tc_note_timeout(a.err, 1);
@@ -206,13 +222,16 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
         }
         ok = __shfl_sync(0xffffffffu, (int)ok, 0) != 0;
         if (!ok) break;
-        // w of the tile's 128 columns, zero past the split
+        // w of the tile's 128 columns
         const uint32_t g = gt + (uint32_t)t;
-        float* wst = sw + (g & 1) * kTcWArrays * kTcN;
-        const int64_t jb = c0 + (int64_t)t * kTcN + 4 * lane;
+        float* wst = sw + (g % kTcBufs) * kTcWArrays * kTcN;
         float wv[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) wv[e] = (jb + e < c1) ? __ldg(a.w + (jb + e) * a.ldw) : 0.0f;
+        for (int e = 0; e < 4; ++e) {
+          wv[e] = wa[e];
+          wa[e] = wb[e];
+        }
+        load_w(t + 2, wb);
         *reinterpret_cast<float4*>(wst + 4 * lane) = make_float4(wv[0], wv[1], wv[2], wv[3]);
         if (KERN != ADASAP_RBF) {
           const float il = 1.0f / kLog2e, i3 = 1.0f / (3.0f * kLog2e * kLog2e);
@@ -222,7 +241,7 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
               make_float4(wv[0] * i3, wv[1] * i3, wv[2] * i3, wv[3] * i3);
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&wfull[g & 1]);
+        if (lane == 0) mbar_arrive(&wfull[g % kTcBufs]);
       }
       if (lane == 0 && *abort_flag) {
         // our copies still write shared memory: wait (bounded) for the last ones
@@ -237,9 +256,9 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
         int issued = 0;
         for (int t = 0; t < ntiles; ++t) {
           const uint32_t g = gt + (uint32_t)t;
-          const int st = g % kTcStages, buf = g & 1;
+          const int st = g % kTcStages, buf = g % kTcBufs;
           if (!mbar_wait(&full[st], (g / kTcStages) & 1u, abort_flag) ||
-              !mbar_wait(&tempty[buf], ((g >> 1) & 1u) ^ 1u, abort_flag)) {
+              !mbar_wait(&tempty[buf], ((g / kTcBufs) & 1u) ^ 1u, abort_flag)) {
             *abort_flag = 1;
             tc_note_timeout(a.err, 2);
             break;
@@ -285,52 +304,59 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
         if (a.self_mode) gi = src;
       }
       float acc = 0.0f, cmp = 0.0f;
-      for (int t = 0; t < ntiles; ++t) {
+      // group cg takes the tiles g = gt + t with g % kTcBufs == cg (TMEM buffer and w
+      // stage cg), all 128 columns of its quadrant's rows, so the four groups work
+      // on four consecutive tiles at once and one group's TMEM-load latency hides
+      // behind the others' arithmetic
+      const int t0 = (int)(((uint32_t)cg + kTcBufs - gt % kTcBufs) % kTcBufs);
+      for (int t = t0; t < ntiles; t += kTcBufs) {
         const uint32_t gg = gt + (uint32_t)t;
-        const int buf = gg & 1;
-        const uint32_t ph = (gg >> 1) & 1u;
-        if (!mbar_wait(&tfull[buf], ph, abort_flag) || !mbar_wait(&wfull[buf], ph, abort_flag)) {
+        const uint32_t ph = (gg / kTcBufs) & 1u;
+        if (!mbar_wait(&tfull[cg], ph, abort_flag) || !mbar_wait(&wfull[cg], ph, abort_flag)) {
           *abort_flag = 1;
           tc_note_timeout(a.err, 3);
           break;
         }
         tc_fence_after();
-        uint32_t u[32];
-        TMEM_LD32(tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)(buf * kTcN + cg * 32), u);
-        TMEM_WAIT32(u);
-        const float* wst = sw + buf * kTcWArrays * kTcN + cg * 32;
-        const int64_t jb = c0 + (int64_t)t * kTcN + cg * 32;
-        const bool self_here = gi >= jb && gi < jb + 32;
         float tacc = 0.0f;
-        if (__any_sync(0xffffffffu, self_here)) {
+#pragma unroll 1
+        for (int cc = 0; cc < kTcN / 32; ++cc) {
+          uint32_t u[32];
+          TMEM_LD32(tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)(cg * kTcN + cc * 32), u);
+          TMEM_WAIT32(u);
+          const float* wst = sw + cg * kTcWArrays * kTcN + cc * 32;
+          const int64_t jb = c0 + (int64_t)t * kTcN + cc * 32;
+          const bool self_here = gi >= jb && gi < jb + 32;
+          if (__any_sync(0xffffffffu, self_here)) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const float v = (jb + i == gi) ? 0.0f : __uint_as_float(u[i]);
-            tacc = tc_term<KERN>(v, wst[i], wst[kTcN + i], wst[2 * kTcN + i], tacc);
-          }
-        } else {
+            for (int i = 0; i < 32; ++i) {
+              const float v = (jb + i == gi) ? 0.0f : __uint_as_float(u[i]);
+              tacc = tc_term<KERN>(v, wst[i], wst[kTcN + i], wst[2 * kTcN + i], tacc);
+            }
+          } else {
 #pragma unroll
-          for (int i4 = 0; i4 < 8; ++i4) {
-            const float4 w4 = *reinterpret_cast<const float4*>(wst + 4 * i4);
-            float4 l4 = w4, t4 = w4;
-            if (KERN != ADASAP_RBF) l4 = *reinterpret_cast<const float4*>(wst + kTcN + 4 * i4);
-            if (KERN == ADASAP_MATERN52) t4 = *reinterpret_cast<const float4*>(wst + 2 * kTcN + 4 * i4);
-            tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 0]), w4.x, l4.x, t4.x, tacc);
-            tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 1]), w4.y, l4.y, t4.y, tacc);
-            tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 2]), w4.z, l4.z, t4.z, tacc);
-            tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 3]), w4.w, l4.w, t4.w, tacc);
+            for (int i4 = 0; i4 < 8; ++i4) {
+              const float4 w4 = *reinterpret_cast<const float4*>(wst + 4 * i4);
+              float4 l4 = w4, t4 = w4;
+              if (KERN != ADASAP_RBF) l4 = *reinterpret_cast<const float4*>(wst + kTcN + 4 * i4);
+              if (KERN == ADASAP_MATERN52) t4 = *reinterpret_cast<const float4*>(wst + 2 * kTcN + 4 * i4);
+              tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 0]), w4.x, l4.x, t4.x, tacc);
+              tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 1]), w4.y, l4.y, t4.y, tacc);
+              tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 2]), w4.z, l4.z, t4.z, tacc);
+              tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 3]), w4.w, l4.w, t4.w, tacc);
+            }
           }
         }
         // the distance buffer and the w stage of this tile are free again
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty[buf]);
+        if (lane == 0) mbar_arrive(&tempty[cg]);
         const float y = tacc - cmp;
         const float tt = acc + y;
         cmp = (tt - acc) - y;
         acc = tt;
       }
-      // combine the four column groups' partial sums of each row
+      // combine the four groups' partial sums of each row
       red[cg * kTcM + rl] = acc - cmp;
       asm volatile("bar.sync 1, %0;" ::"r"(32 * kTcEpiWarps) : "memory");
       if (cg == 0 && ri < a.m) {
@@ -347,7 +373,7 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
   if (warp == 0 && lane == 0 && *abort_flag) tc_note_timeout(a0.err, 9);
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTcTmemCols) : "memory");
   }
 }
 

@@ -7,7 +7,6 @@
 namespace adasap {
 
 constexpr int kTcM = 128, kTcN = 128, kTcThreads = 384;
-constexpr uint32_t kTmemCols = 256;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
