@@ -40,7 +40,10 @@ namespace {
 
 constexpr int kCh = 32;                     // columns per contraction chunk
 constexpr int kChPerTile = kTcN / kCh;      // 4
-constexpr int kKSlots = 2, kWSlots = 2;     // K chunk slots (one per warpgroup), W chunk ring
+constexpr int kWSlots = 2;                  // W chunk ring
+// K chunk slots: one or two per epilogue warpgroup (two where shared memory allows:
+// the warpgroup then writes its second chunk of a tile while the MMAs read the first)
+constexpr size_t kMrhsSmemMax = 232448;     // opt-in shared memory per CTA
 // The MMAs take a tile's chunks in the order j = 0..3 -> chunk column 2 (j & 1) + (j >> 1):
 // warpgroup 0's first, warpgroup 1's first, warpgroup 0's second, warpgroup 1's second.
 __host__ __device__ constexpr int chunk_col(int j) { return 2 * (j & 1) + (j >> 1); }
@@ -62,6 +65,7 @@ struct MrhsArgs {
   const float* wlo;
   int s, sp;           // right-hand sides and the padded accumulator width (multiple of 16)
   int passes;          // 3 (split) or 1
+  int nks;             // K chunk slots per epilogue warpgroup (1 or 2)
   float* part;         // nsplit x m x s
   int64_t cps;         // columns per split (multiple of 128)
   int nsplit;
@@ -71,13 +75,14 @@ struct MrhsArgs {
 
 // Shared-memory plan (bytes from a 128-byte aligned base)
 struct MrhsSmem {
-  size_t a, x, k, w, bars, total;
-  __host__ __device__ MrhsSmem(int kp, int sp) {
+  size_t a, x, k, kslot, w, bars, total;   // kslot: floats per K slot
+  __host__ __device__ MrhsSmem(int kp, int sp, int passes, int nks) {
     const size_t opf = (size_t)kTcM * kp * sizeof(float);
+    kslot = (size_t)(passes == 3 ? 2 : 1) * kTcM * kCh;
     a = 0;                                                      // row operands hi, lo
     x = a + 2 * opf;                                            // [2 stages][hi, lo] column tiles
-    k = x + 4 * opf;                                            // [kKSlots][hi, lo] 128 x 32 chunks
-    w = k + (size_t)kKSlots * 2 * kTcM * kCh * sizeof(float);   // [kWSlots][hi, lo] sp x 32 chunks
+    k = x + 4 * opf;                                            // [2 nks slots][hi(, lo)] 128 x 32 chunks
+    w = k + (size_t)2 * nks * kslot * sizeof(float);            // [kWSlots][hi, lo] sp x 32 chunks
     bars = w + (size_t)kWSlots * 2 * sp * kCh * sizeof(float);
     total = bars + 32 * sizeof(uint64_t) + 64 + 128;
   }
@@ -88,24 +93,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc_mrhs(MrhsArgs a) {
   constexpr int OPF = kTcM * KP;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
-  const MrhsSmem L(KP, a.sp);
+  const MrhsSmem L(KP, a.sp, a.passes, a.nks);
   float* sAhi = reinterpret_cast<float*>(base + L.a);
   float* sAlo = sAhi + OPF;
   float* sX = reinterpret_cast<float*>(base + L.x);   // [st][hi, lo][OPF]
-  float* sK = reinterpret_cast<float*>(base + L.k);   // [slot][hi, lo][128 * 32]
+  float* sK = reinterpret_cast<float*>(base + L.k);   // [slot][hi(, lo)][128 * 32]
   float* sW = reinterpret_cast<float*>(base + L.w);   // [slot][hi, lo][sp * 32]
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bars);
   uint64_t* full = bars;         // [2] column tiles landed
   uint64_t* empty = bars + 2;    // [2] column tile stage free
   uint64_t* tfull = bars + 4;    // [2] distance buffer ready
   uint64_t* tempty = bars + 6;   // [2] distance buffer read (8 epilogue warps)
-  uint64_t* kfull = bars + 8;    // [2] K chunk written (4 warps of one warpgroup)
-  uint64_t* kempty = bars + 10;  // [2] K chunk consumed
-  uint64_t* wfull = bars + 12;   // [2] W chunk landed
-  uint64_t* wempty = bars + 14;  // [2] W chunk consumed
-  uint64_t* ofull = bars + 16;   // accumulator of the item complete
-  uint64_t* drain = bars + 17;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 18);
+  uint64_t* kfull = bars + 8;    // [2 nks] K chunk written (4 warps of one warpgroup)
+  uint64_t* kempty = bars + 12;  // [2 nks] K chunk consumed
+  uint64_t* wfull = bars + 16;   // [2] W chunk landed
+  uint64_t* wempty = bars + 18;  // [2] W chunk consumed
+  uint64_t* ofull = bars + 20;   // accumulator of the item complete
+  uint64_t* drain = bars + 21;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 22);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -120,10 +125,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc_mrhs(MrhsArgs a) {
       mbar_init(&empty[i], 1);
       mbar_init(&tfull[i], 1);
       mbar_init(&tempty[i], 8);
-      mbar_init(&kfull[i], 4);
-      mbar_init(&kempty[i], 1);
       mbar_init(&wfull[i], 1);
       mbar_init(&wempty[i], 1);
+    }
+    for (int i = 0; i < 4; ++i) {
+      mbar_init(&kfull[i], 4);
+      mbar_init(&kempty[i], 1);
     }
     mbar_init(ofull, 1);
     mbar_init(drain, 1);
@@ -273,8 +280,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc_mrhs(MrhsArgs a) {
             const uint32_t gg = gt + (uint32_t)t;
             const uint32_t q = gg * kChPerTile + (uint32_t)j;   // W ring: consumption index
             const int wsl = q & 1;
-            const int ksl = j & 1;                              // K slot = producing warpgroup
-            const uint32_t ku = 2u * gg + (uint32_t)(j >> 1);  // its use of that slot
+            // chunk j comes from warpgroup j & 1 (its chunk j >> 1 of the tile)
+            const int ksl = a.nks == 2 ? 2 * (j & 1) + (j >> 1) : (j & 1);
+            const uint32_t ku = a.nks == 2 ? gg : 2u * gg + (uint32_t)(j >> 1);  // use of that slot
             if (!mbar_wait(&kfull[ksl], ku & 1u, abort_flag)) {
               tc_note_timeout(a.err, 14);
               ok = false;
@@ -286,8 +294,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc_mrhs(MrhsArgs a) {
               break;
             }
             tc_fence_after();
-            const uint32_t k_hi = smem_u32(sK + (ksl * 2 + 0) * kTcM * kCh);
-            const uint32_t k_lo = smem_u32(sK + (ksl * 2 + 1) * kTcM * kCh);
+            const uint32_t k_hi = smem_u32(sK + ksl * L.kslot);
+            const uint32_t k_lo = k_hi + (uint32_t)(kTcM * kCh * sizeof(float));
             const uint32_t w_hi = smem_u32(sW + (wsl * 2 + 0) * sp * kCh);
             const uint32_t w_lo = smem_u32(sW + (wsl * 2 + 1) * sp * kCh);
             for (int pass = 0; pass < a.passes; ++pass) {
@@ -349,16 +357,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc_mrhs(MrhsArgs a) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int c = 2 * g + h;
-          const int sl = g;                                   // this warpgroup's own slot
-          const uint32_t ku = 2u * gg + (uint32_t)h;          // its use of the slot
+          const int sl = a.nks == 2 ? 2 * g + h : g;                   // this warpgroup's slot
+          const uint32_t ku = a.nks == 2 ? gg : 2u * gg + (uint32_t)h;  // its use of the slot
           if (!mbar_wait(&kempty[sl], (ku & 1u) ^ 1u, abort_flag)) {
             tc_note_timeout(a.err, 16);
             stop = true;
             break;
           }
           const int64_t jb = c0 + (int64_t)t * kTcN + c * kCh;
-          float* khi = sK + (sl * 2 + 0) * kTcM * kCh;
-          float* klo = sK + (sl * 2 + 1) * kTcM * kCh;
+          float* khi = sK + sl * L.kslot;
+          float* klo = khi + kTcM * kCh;
           const uint32_t* u = h ? u1 : u0;
 #pragma unroll
           for (int k4 = 0; k4 < kCh / 4; ++k4) {
@@ -441,8 +449,9 @@ __global__ void k_build_w_tc(const float* __restrict__ W, int64_t ldw, int64_t n
 
 template <int KERN, int KP>
 cudaError_t mrhs_setup(int sp_max) {
-  const MrhsSmem L(KP, sp_max);
-  return cudaFuncSetAttribute(k_rows_tc_mrhs<KERN, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+  const size_t need = MrhsSmem(KP, sp_max, 3, 1).total;   // the largest plan launched
+  return cudaFuncSetAttribute(k_rows_tc_mrhs<KERN, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)std::max(need, kMrhsSmemMax));
 }
 
 }  // namespace
@@ -501,6 +510,8 @@ cudaError_t launch_rows_tc_mrhs(int kern, int d, const float* xr, const float* q
   a.xr = xr; a.qr = qr; a.ridx = ridx; a.m = m; a.dp = dp; a.d = d;
   a.bhi = bhi; a.blo = blo; a.ncols = ncols; a.self_mode = self_mode;
   a.whi = whi; a.wlo = wlo; a.s = s; a.sp = tc_mrhs_sp(s); a.passes = passes;
+  const int kp = tc_kp(d);
+  a.nks = MrhsSmem(kp, a.sp, passes, 2).total <= kMrhsSmemMax ? 2 : 1;
   a.part = part; a.sigma2 = sigma2; a.err = err;
   const int64_t tiles = (ncols + kTcN - 1) / kTcN;
   a.cps = (tiles + nsplit - 1) / nsplit * kTcN;
@@ -508,8 +519,7 @@ cudaError_t launch_rows_tc_mrhs(int kern, int d, const float* xr, const float* q
   const int64_t nitems = (m + kTcM - 1) / kTcM * (int64_t)nsplit;
   const int slots = (max_ctas > 0 && max_ctas < tc_slots()) ? max_ctas : tc_slots();
   const int ctas = (int)std::min<int64_t>(nitems, slots);
-  const int kp = tc_kp(d);
-  const size_t smem = MrhsSmem(kp, a.sp).total;
+  const size_t smem = MrhsSmem(kp, a.sp, passes, a.nks).total;
 #define ADASAP_MRHS(KE, KPV) k_rows_tc_mrhs<KE, KPV><<<ctas, kTcThreads, smem, st>>>(a)
   if (kp == 16) {
     if (kern == 0) ADASAP_MRHS(0, 16);
