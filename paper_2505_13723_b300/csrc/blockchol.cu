@@ -1,13 +1,13 @@
 // Exact block solve of Alg. 1 (SAP): D = (K_BB + lambda I)^{-1} R.
 //
 //   H = sigma2 k(X_B, X_B) + lambda I formed explicitly in FP32 (difference-form
-//       distances), padded to bp = 32 * ceil(b / 32) rows with the identity;
-//   H = L L^T by a right-looking blocked Cholesky over 32 x 32 tiles: per
+//       distances), padded to bp = 64 * ceil(b / 64) rows with the identity;
+//   H = L L^T by a right-looking blocked Cholesky over 64 x 64 tiles: per
 //       panel k, k_chol_diag factors the diagonal tile and inverts it,
 //       k_chol_panel forms L_ik = A_ik L_kk^{-T} for the tiles below, and
 //       k_chol_update applies A_IJ -= L_Ik L_Jk^T to the trailing tiles;
 //   D by blocked forward and backward substitution with the inverted
-//       diagonal tiles (one CTA: the substitution is a chain of b / 32 steps),
+//       diagonal tiles (one CTA: the substitution is a chain of b / 64 steps),
 //       then refined twice: D += (L L^T)^{-1} (R - H D), with R - H D
 //       accumulated in FP64 against a copy of H.
 // The refinement removes the factorisation's rounding (FP32, growing with b),
@@ -20,7 +20,7 @@
 
 namespace adasap {
 
-constexpr int kCb = 32;
+constexpr int kCb = 64;   // tile (and panel) width
 
 template <int KERN>
 __global__ void k_form_h(const float* __restrict__ xb, int64_t b, int64_t bp, int dp, float sigma2, float lam,
@@ -42,15 +42,18 @@ __global__ void k_form_h(const float* __restrict__ xb, int64_t b, int64_t bp, in
   }
 }
 
-// Diagonal tile k: Cholesky in shared memory, then the inverse of the factor.
-__global__ void __launch_bounds__(kCb* kCb) k_chol_diag(float* __restrict__ A, int64_t bp, int k,
-                                                        float* __restrict__ Linv, DevScalars* sc) {
+// Diagonal tile k (64 x 64, 1024 threads, 4 entries each): Cholesky in shared
+// memory, then the inverse of the factor (one thread per column).
+__global__ void __launch_bounds__(1024) k_chol_diag(float* __restrict__ A, int64_t bp, int k,
+                                                    float* __restrict__ Linv, DevScalars* sc) {
   __shared__ float T[kCb][kCb + 1];
   __shared__ float I[kCb][kCb + 1];
-  const int r = threadIdx.x / kCb, c = threadIdx.x % kCb;
   const int64_t o = (int64_t)k * kCb;
-  T[r][c] = A[(o + r) * bp + o + c];
-  I[r][c] = 0.0f;
+  for (int e = threadIdx.x; e < kCb * kCb; e += 1024) {
+    const int r = e / kCb, c = e % kCb;
+    T[r][c] = A[(o + r) * bp + o + c];
+    I[r][c] = 0.0f;
+  }
   __syncthreads();
   for (int j = 0; j < kCb; ++j) {
     if (threadIdx.x == 0) {
@@ -63,12 +66,14 @@ __global__ void __launch_bounds__(kCb* kCb) k_chol_diag(float* __restrict__ A, i
       }
     }
     __syncthreads();
-    if (c == j && r > j) T[r][j] /= T[j][j];
+    if ((int)threadIdx.x > j && (int)threadIdx.x < kCb) T[threadIdx.x][j] /= T[j][j];
     __syncthreads();
-    if (r > j && c > j && c <= r) T[r][c] = fmaf(-T[r][j], T[c][j], T[r][c]);
+    for (int e = threadIdx.x; e < kCb * kCb; e += 1024) {
+      const int r = e / kCb, c = e % kCb;
+      if (r > j && c > j && c <= r) T[r][c] = fmaf(-T[r][j], T[c][j], T[r][c]);
+    }
     __syncthreads();
   }
-  // column c of L^{-1} by forward substitution (one thread per column)
   if (threadIdx.x < kCb) {
     const int col = threadIdx.x;
     for (int i = col; i < kCb; ++i) {
@@ -78,27 +83,38 @@ __global__ void __launch_bounds__(kCb* kCb) k_chol_diag(float* __restrict__ A, i
     }
   }
   __syncthreads();
-  if (c <= r) A[(o + r) * bp + o + c] = T[r][c];
-  Linv[(int64_t)k * kCb * kCb + r * kCb + c] = I[r][c];
+  for (int e = threadIdx.x; e < kCb * kCb; e += 1024) {
+    const int r = e / kCb, c = e % kCb;
+    if (c <= r) A[(o + r) * bp + o + c] = T[r][c];
+    Linv[(int64_t)k * kCb * kCb + e] = I[r][c];
+  }
 }
 
-// Tiles (i, k) below the diagonal: L_ik = A_ik L_kk^{-T}.
-__global__ void __launch_bounds__(kCb* kCb) k_chol_panel(float* __restrict__ A, int64_t bp, int k,
-                                                         const float* __restrict__ Linv) {
+// Tiles (i, k) below the diagonal: L_ik = A_ik L_kk^{-T} (1024 threads, 4 outputs each).
+__global__ void __launch_bounds__(1024) k_chol_panel(float* __restrict__ A, int64_t bp, int k,
+                                                     const float* __restrict__ Linv) {
   __shared__ float T[kCb][kCb + 1];
   __shared__ float Li[kCb][kCb + 1];
-  const int r = threadIdx.x / kCb, c = threadIdx.x % kCb;
   const int64_t oi = (int64_t)(k + 1 + blockIdx.x) * kCb, ok = (int64_t)k * kCb;
-  T[r][c] = A[(oi + r) * bp + ok + c];
-  Li[r][c] = Linv[(int64_t)k * kCb * kCb + r * kCb + c];
+  for (int e = threadIdx.x; e < kCb * kCb; e += 1024) {
+    const int r = e / kCb, c = e % kCb;
+    T[r][c] = A[(oi + r) * bp + ok + c];
+    Li[r][c] = Linv[(int64_t)k * kCb * kCb + e];
+  }
   __syncthreads();
-  float acc = 0.0f;
+  const int c = threadIdx.x % kCb, r0 = threadIdx.x / kCb;   // rows r0 + 16 t
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll 8
-  for (int m = 0; m < kCb; ++m) acc = fmaf(T[r][m], Li[c][m], acc);
-  A[(oi + r) * bp + ok + c] = acc;
+  for (int m = 0; m < kCb; ++m) {
+    const float l = Li[c][m];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) acc[t] = fmaf(T[r0 + 16 * t][m], l, acc[t]);
+  }
+#pragma unroll
+  for (int t = 0; t < 4; ++t) A[(oi + r0 + 16 * t) * bp + ok + c] = acc[t];
 }
 
-// Trailing tiles I >= J > k: A_IJ -= L_Ik L_Jk^T (256 threads, 4 outputs each).
+// Trailing tiles I >= J > k: A_IJ -= L_Ik L_Jk^T (256 threads, a 4 x 4 register tile each).
 __global__ void __launch_bounds__(256) k_chol_update(float* __restrict__ A, int64_t bp, int k, int nt) {
   const int J = k + 1 + blockIdx.x, I = k + 1 + blockIdx.y;
   if (J > I) return;
@@ -111,43 +127,53 @@ __global__ void __launch_bounds__(256) k_chol_update(float* __restrict__ A, int6
     Q[r][c] = A[(oJ + r) * bp + ok + c];
   }
   __syncthreads();
-  const int c = threadIdx.x % kCb, r0 = threadIdx.x / kCb;   // rows r0, r0 + 8, r0 + 16, r0 + 24
-  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll 8
+  const int tc = threadIdx.x % 16, tr = threadIdx.x / 16;   // rows tr + 16 a, columns tc + 16 b
+  float acc[4][4] = {};
+#pragma unroll 4
   for (int m = 0; m < kCb; ++m) {
-    const float q = Q[c][m];
+    float pv[4], qv[4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) acc[t] = fmaf(P[r0 + 8 * t][m], q, acc[t]);
+    for (int t = 0; t < 4; ++t) {
+      pv[t] = P[tr + 16 * t][m];
+      qv[t] = Q[tc + 16 * t][m];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(pv[a], qv[b], acc[a][b]);
   }
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    const int64_t idx = (oI + r0 + 8 * t) * bp + oJ + c;
-    A[idx] -= acc[t];
-  }
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) A[(oI + tr + 16 * a) * bp + oJ + tc + 16 * b] -= acc[a][b];
 }
 
 // D (+)= (L L^T)^{-1} R by blocked substitution, one CTA of 1024 threads; R and
-// D are bp x s (row stride s), Y is bp x s scratch.  Forward: warp w sums row w
-// of the block over the lanes (coalesced along a row of L); backward: lane l
-// owns row l of the block and warp p one 32-wide slice of the rows below
-// (coalesced along a row of L, which is a column of L^T).
+// D are bp x s (row stride s), Y is bp x s scratch.  Forward: warp w sums rows w
+// and w + 32 of the block over the lanes (coalesced along a row of L); backward:
+// lane l owns rows l and l + 32 of the block and warp p one slice of the rows
+// below (coalesced along a row of L, which is a column of L^T).
 __global__ void __launch_bounds__(1024) k_chol_solve(const float* __restrict__ L, int64_t bp,
                                                      const float* __restrict__ Linv, const float* __restrict__ R,
                                                      int s, float* __restrict__ Y, float* __restrict__ D, int add) {
-  __shared__ float part[kCb][kCb + 1];
+  __shared__ float part[kCb][33];
   __shared__ float tmp[kCb];
-  const int rr = threadIdx.x % kCb, p = threadIdx.x / kCb;   // lane, warp
+  const int lane = threadIdx.x % 32, p = threadIdx.x / 32;
   const int nt = (int)(bp / kCb);
   for (int col = 0; col < s; ++col) {
     // forward: Y_K = Linv_K (R_K - sum_{J<K} L_KJ Y_J)
     for (int K = 0; K < nt; ++K) {
-      const int64_t wrow = (int64_t)K * kCb + p;
-      float acc = 0.0f;
-      for (int64_t m = rr; m < (int64_t)K * kCb; m += kCb) acc = fmaf(L[wrow * bp + m], Y[m * s + col], acc);
-      acc = warp_sum(acc);
-      if (rr == 0) tmp[p] = R[wrow * s + col] - acc;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t wrow = (int64_t)K * kCb + p + 32 * h;
+        float acc = 0.0f;
+        for (int64_t m = lane; m < (int64_t)K * kCb; m += 32) acc = fmaf(L[wrow * bp + m], Y[m * s + col], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) tmp[p + 32 * h] = R[wrow * s + col] - acc;
+      }
       __syncthreads();
-      if (p == 0) {
+      if (threadIdx.x < kCb) {
+        const int rr = threadIdx.x;
         float y = 0.0f;
         for (int m = 0; m < kCb; ++m) y = fmaf(Linv[(int64_t)K * kCb * kCb + rr * kCb + m], tmp[m], y);
         Y[((int64_t)K * kCb + rr) * s + col] = y;
@@ -156,18 +182,25 @@ __global__ void __launch_bounds__(1024) k_chol_solve(const float* __restrict__ L
     }
     // backward: X_K = Linv_K^T (Y_K - sum_{J>K} L_JK^T X_J), written into Y
     for (int K = nt - 1; K >= 0; --K) {
-      const int64_t row = (int64_t)K * kCb + rr;
-      float acc = 0.0f;
-      for (int64_t m = (int64_t)(K + 1) * kCb + p; m < bp; m += kCb) acc = fmaf(L[m * bp + row], Y[m * s + col], acc);
-      part[rr][p] = acc;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t row = (int64_t)K * kCb + lane + 32 * h;
+        float acc = 0.0f;
+        for (int64_t m = (int64_t)(K + 1) * kCb + p; m < bp; m += 32) acc = fmaf(L[m * bp + row], Y[m * s + col], acc);
+        part[lane + 32 * h][p] = acc;
+      }
       __syncthreads();
-      if (p == 0) {
+      if (threadIdx.x < kCb) {
+        const int rr = threadIdx.x;
+        const int64_t row = (int64_t)K * kCb + rr;
         float t = Y[row * s + col];
-        for (int q = 0; q < kCb; ++q) t -= part[rr][q];
+        for (int q = 0; q < 32; ++q) t -= part[rr][q];
         tmp[rr] = t;
       }
       __syncthreads();
-      if (p == 0) {
+      if (threadIdx.x < kCb) {
+        const int rr = threadIdx.x;
+        const int64_t row = (int64_t)K * kCb + rr;
         float x = 0.0f;
         for (int m = 0; m < kCb; ++m) x = fmaf(Linv[(int64_t)K * kCb * kCb + m * kCb + rr], tmp[m], x);
         Y[row * s + col] = x;
@@ -216,14 +249,16 @@ cudaError_t launch_form_h(int kern, const float* xb, int64_t b, int dp, float si
   return cudaGetLastError();
 }
 
+int64_t chol_linv_floats(int64_t b) { return chol_pad(b) * kCb; }
+
 cudaError_t launch_block_chol(float* A, int64_t b, float* Linv, DevScalars* sc, cudaStream_t st) {
   const int64_t bp = chol_pad(b);
   const int nt = (int)(bp / kCb);
   for (int k = 0; k < nt; ++k) {
-    k_chol_diag<<<1, kCb * kCb, 0, st>>>(A, bp, k, Linv, sc);
+    k_chol_diag<<<1, 1024, 0, st>>>(A, bp, k, Linv, sc);
     const int rest = nt - k - 1;
     if (rest > 0) {
-      k_chol_panel<<<rest, kCb * kCb, 0, st>>>(A, bp, k, Linv);
+      k_chol_panel<<<rest, 1024, 0, st>>>(A, bp, k, Linv);
       k_chol_update<<<dim3(rest, rest), 256, 0, st>>>(A, bp, k, nt);
     }
     const cudaError_t e = cudaGetLastError();

@@ -66,11 +66,12 @@ cudaError_t launch_index32(const int64_t* in, int64_t m, int64_t n, int* out, cu
 
 // ---- exact block solve of Alg. 1 (blockchol.cu) ------------------------------------
 constexpr int64_t kMaxExactBlock = 8192;   // b of the exact solve (two bp x bp FP32 matrices)
-int64_t chol_pad(int64_t b);               // b rounded up to the 32-row tile
+int64_t chol_pad(int64_t b);               // b rounded up to the 64-row tile
+int64_t chol_linv_floats(int64_t b);       // floats of the inverted diagonal tiles
 // H = sigma2 k(X_B, X_B) + lambda I (bp x bp, identity padding) from the gathered block
 cudaError_t launch_form_h(int kern, const float* xb, int64_t b, int dp, float sigma2, float lam, float* H,
                           cudaStream_t st);
-// blocked Cholesky in place (lower triangle of A), inverted diagonal tiles in Linv (bp x 32)
+// blocked Cholesky in place (lower triangle of A), inverted diagonal tiles in Linv
 cudaError_t launch_block_chol(float* A, int64_t b, float* Linv, DevScalars* sc, cudaStream_t st);
 // D = (L L^T)^{-1} R (add = 0) or D += (L L^T)^{-1} R (add = 1); R, D, Y: bp x s
 cudaError_t launch_chol_solve(const float* L, int64_t b, const float* Linv, const float* R, int s, float* Y,

@@ -558,7 +558,7 @@ adasap_status alloc_solver(adasap_solver* S) {
     const size_t bp = (size_t)chol_pad(b);
     S->Hf = ar.get<float>(bp * bp);
     S->Hc = ar.get<float>(bp * bp);
-    S->Linv = ar.get<float>(bp * 32);
+    S->Linv = ar.get<float>((size_t)chol_linv_floats(b));
     S->Rp = ar.get<float>(bp * s);
     S->Dp = ar.get<float>(bp * s);
     S->Yp = ar.get<float>(bp * s);

@@ -127,3 +127,23 @@ def test_batched_requires_one_powering_length(lib):
     opts = [lib.default_opts(P.X.shape[0], b=P.b, r=P.r, max_iters=2, power_iters=10 + k) for k, P in enumerate(Ps)]
     with pytest.raises(lib.AdasapError):
         lib.solve_batched(ctxs, [P.Y for P in Ps], opts=opts)
+
+
+def test_batched_multi_rhs_members(lib):
+    """s = 2: no member joins the grouped single-RHS launches; every system's own
+    multi-RHS path runs inside the batch graph."""
+    Ps = _systems(3, 400, 1500, seed=16)
+    T = 3
+    rng = np.random.default_rng(16)
+    Ys = [np.concatenate([P.Y, rng.standard_normal((P.X.shape[0], 1)).astype(np.float32)], axis=1) for P in Ps]
+    ctxs = [lib.Context(P.X, P.kernel, P.ell, P.sigma2, P.lam) for P in Ps]
+    opts = [lib.default_opts(P.X.shape[0], b=P.b, r=P.r, max_iters=T, check_every=0, seed=500 + k)
+            for k, P in enumerate(Ps)]
+    Ws, stats, status = lib.solve_batched(ctxs, [torch.from_numpy(Y).cuda() for Y in Ys], opts=opts)
+    assert status == 0
+    for k, (P, Y, W) in enumerate(zip(Ps, Ys, Ws)):
+        n = P.X.shape[0]
+        rec = []
+        Wref = OA.adasap(P.X.astype(np.float64), Y.astype(np.float64), P.kernel, P.ell, P.sigma2, P.lam, P.b, P.r,
+                         T, OR.philox_schedule(n, P.b, P.r, seed=500 + k), record=rec)
+        assert _rel(W.cpu().numpy(), Wref) < _tol_eta(rec, P.b, P.sigma2), k

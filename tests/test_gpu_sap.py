@@ -47,7 +47,7 @@ def test_sap_exact_matches_oracle(lib, kern, b, T, tail):
 
 
 def test_sap_exact_one_block_is_the_solution(lib):
-    """b = n (ragged against the 32-row tiles): one step from W_0 = 0 solves the system
+    """b = n (ragged against the 64-row tiles): one step from W_0 = 0 solves the system
     (the oracle's Cholesky solution, and the GPU's own exact residual)."""
     P = synth.small(n=700, d=5)
     n = P.X.shape[0]
@@ -63,7 +63,7 @@ def test_sap_exact_one_block_is_the_solution(lib):
 
 
 def test_sap_exact_multi_rhs_large_block(lib):
-    """b = 2048 (64 tiles, 64 panels of the blocked Cholesky), s = 3, two iterations."""
+    """b = 2048 (32 tiles, 32 panels of the blocked Cholesky), s = 3, two iterations."""
     P = synth.multirhs(n=4096, s=3, b=2048)
     n = P.X.shape[0]
     lam = 0.5
