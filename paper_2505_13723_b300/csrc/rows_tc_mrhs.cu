@@ -12,9 +12,10 @@
 //      128 x s_pad FP32 accumulator in TMEM:
 //        passes = 3: K_hi W_hi + K_hi W_lo + K_lo W_hi   (FP32-level accuracy)
 //        passes = 1: K_hi W_hi                           (TF32 inputs)
-// The accumulator spans one column split (at most kMrhsMaxCols columns, so that
-// the FP32 accumulation stays far below the product's tolerance); the splits
-// are summed in FP64 by k_reduce.
+// The accumulators span one column split (at most kMrhsMaxCols columns, the even
+// and odd tiles in two accumulators, so that the FP32 accumulation in the tensor
+// cores stays below the product's tolerance even for sums of one sign); the
+// splits are summed in FP64 by k_reduce.
 //
 // CTA = 128 rows, 384 threads, one CTA per SM, persistent over (row tile,
 // split) items like rows_tc.cu:
@@ -27,8 +28,8 @@
 //                its own chunk slot (one producer per slot, so that a parity wait
 //                can never alias a phase two uses back), then reads its half of
 //                the accumulator
-// TMEM: columns [0, 256) two distance buffers, [256, 256 + s_pad) the
-// accumulator (512 allocated).  Every wait is bounded; on a timeout the CTA
+// TMEM: columns [0, 256) two distance buffers, [256, 256 + s_pad) and
+// [384, 384 + s_pad) the accumulators of the even and odd tiles (512 allocated).  Every wait is bounded; on a timeout the CTA
 // raises the error flag, drains its copies and MMAs, frees TMEM and writes NaN.
 #include <algorithm>
 
@@ -48,8 +49,9 @@ constexpr size_t kMrhsSmemMax = 232448;     // opt-in shared memory per CTA
 // warpgroup 0's first, warpgroup 1's first, warpgroup 0's second, warpgroup 1's second.
 __host__ __device__ constexpr int chunk_col(int j) { return 2 * (j & 1) + (j >> 1); }
 constexpr uint32_t kMrhsTmemCols = 512;
-constexpr uint32_t kAccCol = 256;           // first accumulator column
-constexpr int64_t kMrhsMaxCols = 16384;     // columns accumulated in TMEM per item
+constexpr uint32_t kAccCol = 256;           // first accumulator column (even tiles)
+constexpr uint32_t kAccCol2 = 384;          // second accumulator (odd tiles): two sums of half the terms each
+constexpr int64_t kMrhsMaxCols = 4096;      // columns accumulated in TMEM per item (2048 per accumulator)
 
 struct MrhsArgs {
   const float* xr;
@@ -241,7 +243,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc_mrhs(MrhsArgs a) {
       // ---- MMA issuer: dist(0); per tile t: dist(t + 1), contr(t, 0..3) -------------
       if (lane == 0) {
         bool ok = true, any = false;
-        uint32_t acc_flag = 0;
+        uint32_t acc_flag[2] = {0u, 0u};
         auto issue_dist = [&](int t) -> bool {
           const uint32_t g = gt + (uint32_t)t;
           const int st = g & 1, buf = g & 1;
@@ -303,9 +305,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc_mrhs(MrhsArgs a) {
               const uint32_t B = pass == 1 ? w_lo : w_hi;
 #pragma unroll
               for (int ks = 0; ks < kCh / 8; ++ks) {
-                tc_mma_tf32(dacc, smem_desc(A + 256u * ks, 128u, 32u * kCh), smem_desc(B + 256u * ks, 128u, 32u * kCh),
-                            idesc, acc_flag);
-                acc_flag = 1;
+                tc_mma_tf32(dacc + (uint32_t)(t & 1) * (kAccCol2 - kAccCol), smem_desc(A + 256u * ks, 128u, 32u * kCh),
+                            smem_desc(B + 256u * ks, 128u, 32u * kCh), idesc, acc_flag[t & 1]);
+                acc_flag[t & 1] = 1;
               }
             }
             tc_commit(&kempty[ksl]);
@@ -402,6 +404,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc_mrhs(MrhsArgs a) {
         if (ntiles > 0) {
           TMEM_LD16(tbase + ((uint32_t)(qd * 32) << 16) + kAccCol + (uint32_t)(cg16 * 16), v);
           TMEM_WAIT16(v);
+          if (ntiles > 1) {   // the odd tiles' accumulator
+            uint32_t v2[16];
+            TMEM_LD16(tbase + ((uint32_t)(qd * 32) << 16) + kAccCol2 + (uint32_t)(cg16 * 16), v2);
+            TMEM_WAIT16(v2);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) v[e] = __float_as_uint(__uint_as_float(v[e]) + __uint_as_float(v2[e]));
+          }
         } else {
 #pragma unroll
           for (int e = 0; e < 16; ++e) v[e] = 0u;  // an empty split contributes zero

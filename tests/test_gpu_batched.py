@@ -147,3 +147,24 @@ def test_batched_multi_rhs_members(lib):
         Wref = OA.adasap(P.X.astype(np.float64), Y.astype(np.float64), P.kernel, P.ell, P.sigma2, P.lam, P.b, P.r,
                          T, OR.philox_schedule(n, P.b, P.r, seed=500 + k), record=rec)
         assert _rel(W.cpu().numpy(), Wref) < _tol_eta(rec, P.b, P.sigma2), k
+
+
+def test_batched_bo_workload_full_size(lib):
+    """The 48-system bo workload as benchmarked (n log-uniform in [4096, 65536], b = n/50,
+    r = 50), two iterations: every system finishes with status 0 and a finite residual, and
+    the two smallest systems match the oracle's replay of their device randomness."""
+    Ps = synth.bo_systems()
+    T = 2
+    ctxs = [lib.Context(torch.from_numpy(P.X).cuda(), P.kernel, P.ell, P.sigma2, P.lam) for P in Ps]
+    opts = [lib.default_opts(P.X.shape[0], b=P.b, r=P.r, max_iters=T, check_every=0, check_rows=4096,
+                             seed=40 + k) for k, P in enumerate(Ps)]
+    Ws, stats, status = lib.solve_batched(ctxs, [torch.from_numpy(P.Y).cuda() for P in Ps], opts=opts)
+    assert status == 0
+    assert all(st["iters"] == T and np.isfinite(st["rel_resid"]) for st in stats)
+    for k in np.argsort([P.X.shape[0] for P in Ps])[:2]:
+        P = Ps[k]
+        n = P.X.shape[0]
+        rec = []
+        Wref = OA.adasap(P.X.astype(np.float64), P.Y.astype(np.float64), P.kernel, P.ell, P.sigma2, P.lam, P.b,
+                         P.r, T, OR.philox_schedule(n, P.b, P.r, seed=40 + int(k)), record=rec)
+        assert _rel(Ws[k].cpu().numpy(), Wref) < _tol_eta(rec, P.b, P.sigma2), (k, n)

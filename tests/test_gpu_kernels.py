@@ -157,6 +157,20 @@ def test_kernel_rows_regress_workload_full_size_sampled(lib, prec):
     _check_rows(out[pick].astype(np.float64), P.X, rows[pick], W, P.kernel, P.ell, P.sigma2)
 
 
+@pytest.mark.parametrize("prec", [1, 2])
+def test_kernel_rows_multirhs_workload_full_size_sampled(lib, prec):
+    """n = 2^18, d = 16, RBF, b = 4096, s = 64 (the multi-RHS Step I launch the benchmark
+    times); 24 rows checked, at the split (1e-5) and single-pass TF32 (3e-3) bounds."""
+    P = synth.multirhs()
+    ctx = _ctx(lib, P.X, P.kernel, P.ell, P.sigma2, P.lam, prec)
+    g = np.random.default_rng(12)
+    rows = g.choice(P.X.shape[0], size=P.b, replace=False)
+    out = ctx.kernel_rows(torch.from_numpy(rows).cuda(), torch.from_numpy(P.Y).cuda()).cpu().numpy()
+    pick = g.choice(P.b, size=24, replace=False)
+    _check_rows(out[pick].astype(np.float64), P.X, rows[pick], P.Y, P.kernel, P.ell, P.sigma2,
+                rtol=RTOL_ROWS if prec == 1 else 3e-3)
+
+
 def test_kernel_rows_unaligned_rhs_view(lib):
     """A contiguous W that starts 4 bytes past an allocation (no 16-byte alignment)."""
     X, W = _data(900, 6, 1, seed=12)

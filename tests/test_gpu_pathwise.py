@@ -147,3 +147,20 @@ def test_rmse_nll_matches_oracle(lib):
     rm, nl = lib.rmse_nll(o[:, 0], o[:, 1:], torch.from_numpy(yt).cuda(), 0.01)
     rm_ref, nl_ref = PW.rmse_nll(out[:, 0], out[:, 1:], yt, 0.01)
     assert rm == pytest.approx(rm_ref, rel=1e-9) and nl == pytest.approx(nl_ref, rel=1e-9)
+
+
+def test_rf_prior_multirhs_workload_full_size_sampled(lib):
+    """The prior draw the pathwise benchmark times: n = 2^18 training points, q = 2048,
+    63 samples; 32 sampled points checked against the oracle."""
+    P = synth.multirhs()
+    n, d = P.X.shape
+    q, ns = 2048, 63
+    z, u, phase, theta, _ = synth.rf_draws(q, d, None, ns, 1, P.lam, seed=1)
+    ctx = lib.Context(P.X, P.kernel, P.ell, P.sigma2, P.lam)
+    F = ctx.rf_prior(*_cuda(P.X, z, u, phase, theta)).cpu().numpy()
+    pick = np.random.default_rng(3).choice(n, size=32, replace=False)
+    ref = PW.rf_prior(P.X[pick], z, u, phase, theta, P.kernel, P.ell, P.sigma2)
+    omega = PW.rf_frequencies(z, u, P.kernel, P.ell)
+    A = np.abs(P.X[pick].astype(np.float64) @ omega.T + phase.astype(np.float64)).max()
+    bound = (q * 2.0 ** -24 + 4e-7 * (1.0 + A)) * np.sqrt(2 * P.sigma2 / q) * np.abs(theta).astype(np.float64).sum(0)
+    assert (np.abs(F[pick] - ref) <= bound[None, :]).all()
