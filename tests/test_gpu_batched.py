@@ -77,9 +77,12 @@ def test_batched_uneven_systems_match_oracle(lib):
 
 def test_batched_mixed_members(lib):
     """Systems that cannot join the grouped launches (identity preconditioner, FP32
-    CUDA-core precision, an RBF kernel in a group of its own) iterate in the same graph."""
-    Ps = _systems(4, 500, 2000, seed=12)
+    CUDA-core precision) iterate in the same graph as grouped ones, and the grouped ones
+    form several classes (an RBF kernel; d = 20, whose operands are 32 wide)."""
+    Ps = _systems(5, 500, 2000, seed=12)
     Ps[2]["kernel"] = synth.RBF
+    rng = np.random.default_rng(12)
+    Ps[4]["X"] = rng.uniform(-1.0, 1.0, (Ps[4].X.shape[0], 20)).astype(np.float32)
     T = 4
     ctxs = [lib.Context(P.X, P.kernel, P.ell, P.sigma2, P.lam) for P in Ps]
     ctxs[1].set_precision(lib.PREC_FP32)
