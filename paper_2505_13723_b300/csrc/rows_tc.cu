@@ -63,7 +63,10 @@ struct TcSmem {
 //   M52  k = (1 + a + a^2/3) e^-a = 2^-a' (1 + a'/log2 e + a'^2 / (3 log2^2 e))
 template <int KERN>
 __device__ __forceinline__ float tc_term(float v, float w, float wl, float w3, float acc) {
-  if (KERN == ADASAP_RBF) return fmaf(ex2_approx(-fmaxf(v, 0.0f)), w, acc);
+  // RBF: for a near-duplicate pair u may come out below 0 by the rounding of q_i + q_j - 2 x_i.x_j
+  // (about 2^-22 (q_i + q_j)); 2^{-u} is then 1 + O(1e-6), inside the product's tolerance, so the
+  // RBF term needs no clamp
+  if (KERN == ADASAP_RBF) return fmaf(ex2_approx(-v), w, acc);
   const float vc = fmaxf(v, 1e-30f);
   const float ap = vc * rsqrt_approx(vc);
   const float e = ex2_approx(-ap);
