@@ -9,8 +9,9 @@ Matern-3/2, ell = 0.3, lambda = 1e-3, b = 10^4, r = 100, one right-hand side
 value: kernel entries k(x_i, x_j) evaluated per second over whole iterations
   (b n for Step I, b^2 for the sketch, N b^2 for the N powering products).
 roofline: the fused kernel-row product (Step I's kernel) timed alone with CUDA
-  events; its peak is the MUFU bound (16 MUFU results/clk/SM, 148 SMs, max SM
-  clock; Matern needs rsqrt + ex2 per entry, RBF ex2 only).
+  events; its peak is the special-function-pipe bound at the issue rates
+  measured on the GPU (adasap_measure_pipes), the SMs and the SM clock sampled
+  during the kernel (Matern needs sqrt + ex2 per entry, RBF ex2 only).
 e2e: the same entries through the C-ABI with host buffers (create + solve +
   copy-back inside the timed region).
 cpu_baseline / --impl reference: the FP64 oracle's block-row product on a
@@ -345,13 +346,13 @@ def run_ours(args, rank, world, dist):
     k_rate = b * n / (k_ms * 1e-3)
     pk, pk_src = peaks()
     # roofline of the block-row product: the special-function pipe, at the issue
-    # rates measured on this GPU (ex2, rsqrt per SM per cycle) and the SM clock
+    # rates measured on this GPU (ex2, sqrt per SM per cycle) and the SM clock
     # sampled while the kernel ran
     pipes = lib.measure_pipes()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     ksum = kclk.summary()
     mhz = float(ksum.get("sm_mhz") or pk.get("sm_max_mhz", 2032.0))
-    clk_per_entry = 1.0 / pipes["ex2"] + (1.0 / pipes["rsqrt"] if P.kernel != 0 else 0.0)
+    clk_per_entry = 1.0 / pipes["ex2"] + (1.0 / pipes["sqrt"] if P.kernel != 0 else 0.0)
     peak_entries = sms * mhz * 1e6 / clk_per_entry
 
     # ---- time to relative residual 1e-3 (FP32), bounded
@@ -541,10 +542,10 @@ def run_ours(args, rank, world, dist):
                          "fp32_cuda_core_kernel": {"ms_per_launch": fp32_ms,
                                                    "achieved": b * n / (fp32_ms * 1e-3) / 1e9},
                          "peak_basis": ("special-function pipe, measured on this GPU by adasap_measure_pipes: "
-                                        "ex2 %.1f and rsqrt %.1f per SM per clock; %s per entry; %d SMs x %.0f MHz "
+                                        "ex2 %.1f and sqrt %.1f per SM per clock; %s per entry; %d SMs x %.0f MHz "
                                         "(median SM clock sampled during the kernel)"
-                                        % (pipes["ex2"], pipes["rsqrt"],
-                                           "1 ex2" if P.kernel == 0 else "1 ex2 + 1 rsqrt", sms, mhz)),
+                                        % (pipes["ex2"], pipes["sqrt"],
+                                           "1 ex2" if P.kernel == 0 else "1 ex2 + 1 sqrt", sms, mhz)),
                          "pipes_measured": pipes},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": kernels_per_iter * args.steps,
             "clocks": clk.summary(), "kernel_clocks": kclk.summary(),

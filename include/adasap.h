@@ -155,8 +155,9 @@ adasap_status adasap_kernel_rows_noalloc(adasap_ctx* ctx, const int64_t* B, int6
 /* Measurement support (the paper has no counterpart): the issue throughput of
  * the pipes that bound the block-row product on the current device, measured
  * by long independent dependency chains on every SM.  out[0] = ex2.approx,
- * out[1] = rsqrt.approx, out[2] = FP32 FMA, each in operations per SM per
- * clock cycle; the first `count` (<= 3) are written.  Synchronises `stream`. */
+ * out[1] = rsqrt.approx, out[2] = FP32 FMA, out[3] = sqrt.approx, each in
+ * operations per SM per clock cycle; the first `count` (<= 4) are written.
+ * Synchronises `stream`. */
 adasap_status adasap_measure_pipes(double* out, int count, void* stream);
 
 /* ADASAP (Alg. 2 with Alg. 4, 5, 6 and the stabilised Woodbury apply of App. C.2).

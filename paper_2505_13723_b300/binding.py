@@ -409,10 +409,10 @@ def rmse_nll(mean, samples, ytest, noise, stream=None):
 
 
 def measure_pipes(stream=None):
-    """adasap_measure_pipes: measured ex2, rsqrt and FP32-FMA issue rates (per SM per cycle)."""
-    out = (ctypes.c_double * 3)()
-    _check(_lib.adasap_measure_pipes(out, 3, _stream(stream)), "adasap_measure_pipes")
-    return {"ex2": out[0], "rsqrt": out[1], "ffma": out[2]}
+    """adasap_measure_pipes: measured ex2, rsqrt, FP32-FMA and sqrt issue rates (per SM per cycle)."""
+    out = (ctypes.c_double * 4)()
+    _check(_lib.adasap_measure_pipes(out, 4, _stream(stream)), "adasap_measure_pipes")
+    return {"ex2": out[0], "rsqrt": out[1], "ffma": out[2], "sqrt": out[3]}
 
 
 def sample(seed, t, n, b, r, stream=None):

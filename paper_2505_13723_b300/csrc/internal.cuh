@@ -160,7 +160,7 @@ cudaError_t launch_rows_tc_mrhs(int kern, int d, const float* xr, const float* q
                                 cudaStream_t st, int max_ctas = 0);
 
 // ---- pipe throughput probe (probe.cu): ex2, rsqrt, FFMA per SM per cycle -------------
-cudaError_t measure_pipes(double* out3, cudaStream_t st);
+cudaError_t measure_pipes(double* out4, cudaStream_t st);   // ex2, rsqrt, FFMA, sqrt
 
 // ---- sampler (Philox4x32-10; definitions in sampler.cu) -------------------------
 cudaError_t launch_sample_block(uint64_t seed, const long long* t_dev, int64_t t_host, int64_t n,

@@ -1,5 +1,5 @@
 // Measured throughput of the arithmetic pipes that bound the block-row product
-// (special-function unit for ex2 / rsqrt, FP32 FMA), for the roofline the
+// (special-function unit for ex2 / rsqrt / sqrt, FP32 FMA), for the roofline the
 // benchmark reports.  Each thread runs kProbeChains independent dependency
 // chains so that latency is hidden and only issue throughput counts; the SM
 // clock over the run is taken from clock64 against the global timer.
@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(kProbeThreads) k_pipe_probe(int iters, float* 
     for (int i = 0; i < kProbeChains; ++i) {
       if (OP == 0) x[i] = ex2_approx(-x[i]);            // stays in [0.5, 1]
       else if (OP == 1) x[i] = rsqrt_approx(x[i]);      // alternates a, a^-1/2: stays finite
+      else if (OP == 3) x[i] = sqrt_approx(x[i]);       // tends to 1 from below: stays finite
       else x[i] = fmaf(x[i], 0.999f, 1e-4f);
     }
   }
@@ -45,7 +46,7 @@ __global__ void __launch_bounds__(kProbeThreads) k_pipe_probe(int iters, float* 
 
 }  // namespace
 
-cudaError_t measure_pipes(double* out3, cudaStream_t st) {
+cudaError_t measure_pipes(double* out4, cudaStream_t st) {
   int dev = 0, sms = 0;
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
@@ -61,11 +62,12 @@ cudaError_t measure_pipes(double* out3, cudaStream_t st) {
   cudaEventCreate(&b);
   const int blocks = sms * kProbeBlocksPerSm;
   const int iters = 2048;
-  for (int op = 0; op < 3 && e == cudaSuccess; ++op) {
+  for (int op = 0; op < 4 && e == cudaSuccess; ++op) {
     auto launch = [&]() {
       if (op == 0) k_pipe_probe<0><<<blocks, kProbeThreads, 0, st>>>(iters, sink, clk);
       else if (op == 1) k_pipe_probe<1><<<blocks, kProbeThreads, 0, st>>>(iters, sink, clk);
-      else k_pipe_probe<2><<<blocks, kProbeThreads, 0, st>>>(iters, sink, clk);
+      else if (op == 2) k_pipe_probe<2><<<blocks, kProbeThreads, 0, st>>>(iters, sink, clk);
+      else k_pipe_probe<3><<<blocks, kProbeThreads, 0, st>>>(iters, sink, clk);
     };
     launch();  // warm-up
     cudaEventRecord(a, st);
@@ -80,7 +82,7 @@ cudaError_t measure_pipes(double* out3, cudaStream_t st) {
     const double ghz = h[1] > 0 ? (double)h[0] / (double)h[1] : 0.0;   // cycles per ns of block 0
     const double ops = (double)blocks * kProbeThreads * kProbeChains * (double)iters;
     // operations per SM per cycle, over the whole launch at the measured clock
-    out3[op] = (ms > 0.0f && ghz > 0.0) ? ops / ((double)sms * (double)ms * 1e6 * ghz) : 0.0;
+    out4[op] = (ms > 0.0f && ghz > 0.0) ? ops / ((double)sms * (double)ms * 1e6 * ghz) : 0.0;
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);

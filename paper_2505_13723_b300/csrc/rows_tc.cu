@@ -67,8 +67,7 @@ __device__ __forceinline__ float tc_term(float v, float w, float wl, float w3, f
   // (about 2^-22 (q_i + q_j)); 2^{-u} is then 1 + O(1e-6), inside the product's tolerance, so the
   // RBF term needs no clamp
   if (KERN == ADASAP_RBF) return fmaf(ex2_approx(-v), w, acc);
-  const float vc = fmaxf(v, 1e-30f);
-  const float ap = vc * rsqrt_approx(vc);
+  const float ap = sqrt_approx(fmaxf(v, 0.0f));   // a' (one special-function op)
   const float e = ex2_approx(-ap);
   if (KERN == ADASAP_MATERN32) return fmaf(e, fmaf(ap, wl, w), acc);
   return fmaf(e, fmaf(ap, fmaf(ap, w3, wl), w), acc);

@@ -461,9 +461,9 @@ extern "C" adasap_status adasap_hypergrad(adasap_ctx* c, const float* W, const f
 
 extern "C" adasap_status adasap_measure_pipes(double* out, int count, void* stream) {
   if (!out || count < 1) return ADASAP_EINVAL;
-  double v[3] = {0.0, 0.0, 0.0};
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
   CT(measure_pipes(v, (cudaStream_t)stream));
-  for (int i = 0; i < count && i < 3; ++i) out[i] = v[i];
+  for (int i = 0; i < count && i < 4; ++i) out[i] = v[i];
   return ADASAP_OK;
 }
 
