@@ -53,7 +53,7 @@ __device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
 template <int KERN>
 __device__ __forceinline__ float kval(float u) {
   if (KERN == ADASAP_RBF) return ex2_approx(-u);
-  float a = u * rsqrt_approx(fmaxf(u, 1e-30f));
+  float a = sqrt_approx(fmaxf(u, 0.0f));
   float e = ex2_approx(-kLog2e * a);
   if (KERN == ADASAP_MATERN32) return fmaf(a, e, e);
   float p = fmaf(a, fmaf(a, 1.0f / 3.0f, 1.0f), 1.0f);
@@ -71,7 +71,7 @@ __device__ __forceinline__ void kval_grad(float u, float& kv, float& gv) {
     gv = (2.0f * kLn2) * u * e;
     return;
   }
-  float a = u * rsqrt_approx(fmaxf(u, 1e-30f));
+  float a = sqrt_approx(fmaxf(u, 0.0f));
   float e = ex2_approx(-kLog2e * a);
   if (KERN == ADASAP_MATERN32) {
     kv = fmaf(a, e, e);
