@@ -839,11 +839,18 @@ __global__ void __launch_bounds__(256) k_utv(const float* __restrict__ U, int64_
 
 // Small FP64 step between U^T v and the apply.  alpha[0] = coefficient of v,
 // alpha[1] = 1/||v|| of the input (normalised mode).
-__global__ void __launch_bounds__(256) k_wcoef(int mode, const double* __restrict__ part, int chunks, int r, int s,
-                                               const double* __restrict__ S, const double* __restrict__ keep,
-                                               const float* __restrict__ Minv, const double* __restrict__ sq_part,
-                                               DevScalars* sc, float* __restrict__ coef, double* __restrict__ alpha) {
-  extern __shared__ double q[];  // r x s
+// Coefficients of the multi-RHS applies from the k_utv partials, spread over many
+// blocks (the FP64 sums of the chunk partials were the bottleneck of a one-block
+// form on this GPU's FP64 pipe): thread o sums the chunks of output o = k*s + c.
+//   kInv:  qk[o] = keep_k q[o] (FP32), finished by k_wcoef_inv
+//   else:  coef[o] = scale q[o] ((S_k + rho)^{-1/2} - rho^{-1/2}), alpha = scale rho^{-1/2}
+constexpr int kWcoefThreads = 128;
+__global__ void __launch_bounds__(kWcoefThreads) k_wcoef(int mode, const double* __restrict__ part, int chunks, int r,
+                                                         int s, const double* __restrict__ S,
+                                                         const double* __restrict__ keep,
+                                                         const double* __restrict__ sq_part, DevScalars* sc,
+                                                         float* __restrict__ coef, float* __restrict__ qk,
+                                                         double* __restrict__ alpha) {
   __shared__ double red[33];
   const double rho = sc->rho;
   double scale = 1.0;
@@ -854,31 +861,34 @@ __global__ void __launch_bounds__(256) k_wcoef(int mode, const double* __restric
     scale = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
   }
   const int nout = r * s;
-  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-    double acc = 0.0;
-    for (int ch = 0; ch < chunks; ++ch) acc += part[(int64_t)ch * nout + o];
-    q[o] = acc;
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o < nout) {
+    double q = 0.0;
+    for (int ch = 0; ch < chunks; ++ch) q += part[(int64_t)ch * nout + o];
+    const int k = o / s;
+    if (mode == kInv) qk[o] = (float)(keep[k] * q);
+    else coef[o] = (float)(scale * q * (1.0 / sqrt(S[k] + rho) - 1.0 / sqrt(rho)));
   }
-  __syncthreads();
-  if (mode == kInv) {
-    // coef = -keep . M (keep . q) / rho with M = (rho S^{-1} + U^T U)^{-1} (FP32: M is well conditioned)
-    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-      const int k = o / s, c = o % s;
-      float acc = 0.0f;
-      for (int j = 0; j < r; ++j) acc = fmaf(Minv[k * r + j], (float)(keep[j] * q[j * s + c]), acc);
-      coef[o] = (float)(-keep[k] * (double)acc / rho);
-    }
-    if (threadIdx.x == 0) alpha[0] = 1.0 / rho;
-  } else {
-    const double irs = 1.0 / sqrt(rho);
-    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-      const int k = o / s;
-      coef[o] = (float)(scale * q[o] * (1.0 / sqrt(S[k] + rho) - irs));
-    }
-    if (threadIdx.x == 0) {
-      alpha[0] = scale * irs;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (mode == kInv) {
+      alpha[0] = 1.0 / rho;
+    } else {
+      alpha[0] = scale / sqrt(rho);
       if (mode == kInvSqrtNormalised) alpha[1] = scale;
     }
+  }
+}
+
+// kInv: coef = -keep . M qk / rho with M = (rho S^{-1} + U^T U)^{-1} (FP32: M is well
+// conditioned); block k, thread c.
+__global__ void k_wcoef_inv(int r, int s, const double* __restrict__ keep, const float* __restrict__ Minv,
+                            const float* __restrict__ qk, DevScalars* sc, float* __restrict__ coef) {
+  const int k = blockIdx.x;
+  const double rho = sc->rho;
+  for (int c = threadIdx.x; c < s; c += blockDim.x) {
+    float acc = 0.0f;
+    for (int j = 0; j < r; ++j) acc = fmaf(Minv[k * r + j], qk[j * s + c], acc);
+    coef[k * s + c] = (float)(-keep[k] * (double)acc / rho);
   }
 }
 
@@ -976,8 +986,9 @@ cudaError_t launch_woodbury_apply(CoreBufs& cb, int mode, const float* v, int s,
   const int ogroups = (r * s + 256 * kUtvOut - 1) / (256 * kUtvOut);
   k_utv<<<dim3(cb.utv_chunks, ogroups), 256, (size_t)(32 * r + 32 * s) * sizeof(float), st>>>(cb.U, cb.b, r, v, s, s,
                                                                                                chunk_rows, cb.utv_part);
-  k_wcoef<<<1, 256, (size_t)r * s * sizeof(double), st>>>(mode, cb.utv_part, cb.utv_chunks, r, s, cb.S,
-                                                              cb.keep, cb.Minv, cb.sq_part, sc, cb.coef, cb.alpha);
+  k_wcoef<<<(r * s + kWcoefThreads - 1) / kWcoefThreads, kWcoefThreads, 0, st>>>(
+      mode, cb.utv_part, cb.utv_chunks, r, s, cb.S, cb.keep, cb.sq_part, sc, cb.coef, cb.qk, cb.alpha);
+  if (mode == kInv) k_wcoef_inv<<<r, 64, 0, st>>>(r, s, cb.keep, cb.Minv, cb.qk, sc, cb.coef);
   k_wapply<<<kReduceBlocks, 256, (size_t)r * s * sizeof(float), st>>>(cb.U, cb.b, r, v, s, cb.coef, cb.alpha, out,
                                                                        sqp, dtp, dotv);
   return cudaGetLastError();
@@ -1511,7 +1522,6 @@ cudaError_t core_init() {
   if ((e = cudaFuncSetAttribute(k_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_wfactor, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-  if ((e = cudaFuncSetAttribute(k_wcoef, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_wapply, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   return cudaSuccess;
 }

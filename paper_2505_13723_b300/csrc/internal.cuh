@@ -200,6 +200,7 @@ struct CoreBufs {
   double* utv_part;   // [utv_chunks][r][s]
   int utv_chunks;
   float* coef;        // r x s
+  float* qk;          // r x s: keep . (U^T v) of the multi-RHS inverse apply
   double* sq_part;    // [kReduceBlocks] sums of squares / dots
   double* dot_part;   // [kReduceBlocks]
   double* alpha;      // scalar apply coefficient

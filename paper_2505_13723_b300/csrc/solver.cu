@@ -599,6 +599,7 @@ adasap_status alloc_solver(adasap_solver* S) {
   cb.utv_chunks = utv_chunks_for(b);
   cb.utv_part = ar.get<double>((size_t)cb.utv_chunks * rr * s);
   cb.coef = ar.get<float>((size_t)rr * s);
+  cb.qk = ar.get<float>((size_t)rr * s);
   cb.sq_part = ar.get<double>(kReduceBlocks);
   cb.dot_part = ar.get<double>(kReduceBlocks);
   cb.alpha = ar.get<double>(2);
