@@ -160,6 +160,19 @@ adasap_status adasap_kernel_rows_noalloc(adasap_ctx* ctx, const int64_t* B, int6
  * Synchronises `stream`. */
 adasap_status adasap_measure_pipes(double* out, int count, void* stream);
 
+/* Device-side failures (the paper has no counterpart).  Every wait inside the
+ * tensor-core kernels is bounded in time; a kernel whose wait runs out records a
+ * code in its context, writes NaN in place of the affected outputs and returns,
+ * leaving the context usable.  adasap_check_device synchronises `stream`,
+ * returns ADASAP_ETIMEOUT with *code (may be NULL) the first recorded code, or
+ * ADASAP_OK with *code = 0, and clears the record.  The solvers check it at each
+ * residual evaluation and return ADASAP_ETIMEOUT.
+ * adasap_wait_selftest enqueues, for tests of this path, a one-thread kernel whose
+ * bounded wait nothing completes: after limit_ns (<= 10^9) it records code 99 in
+ * the context and returns, so that adasap_check_device then reports it. */
+adasap_status adasap_check_device(adasap_ctx* ctx, int* code, void* stream);
+adasap_status adasap_wait_selftest(adasap_ctx* ctx, uint64_t limit_ns, void* stream);
+
 /* ADASAP (Alg. 2 with Alg. 4, 5, 6 and the stabilised Woodbury apply of App. C.2).
  * Y (n x s) and W (n x s) are host or device.  W holds W_0 on entry and the
  * returned iterate W_T on exit.  1 <= s <= 128.  Randomness (B, Omega, v0) is

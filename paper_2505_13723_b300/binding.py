@@ -36,7 +36,8 @@ SYMBOLS = ["adasap_default_opts", "adasap_status_string", "adasap_last_error", "
            "adasap_solver_scalars", "adasap_solver_end", "adasap_solver_graph_kernels",
            "adasap_solver_diag", "adasap_set_precision",
            "adasap_kernel_rows_noalloc", "adasap_measure_pipes", "adasap_residual",
-           "adasap_solve_batched", "adasap_rf_prior", "adasap_pathwise", "adasap_rmse_nll"]
+           "adasap_solve_batched", "adasap_rf_prior", "adasap_pathwise", "adasap_rmse_nll",
+           "adasap_check_device", "adasap_wait_selftest"]
 
 
 class Opts(ctypes.Structure):
@@ -104,6 +105,10 @@ _lib.adasap_pathwise.restype = ctypes.c_int
 _lib.adasap_rmse_nll.argtypes = [_P, _I64, _P, _I64, ctypes.c_int, _P, _I64, ctypes.c_double,
                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _P]
 _lib.adasap_rmse_nll.restype = ctypes.c_int
+_lib.adasap_check_device.argtypes = [_P, ctypes.POINTER(ctypes.c_int), _P]
+_lib.adasap_check_device.restype = ctypes.c_int
+_lib.adasap_wait_selftest.argtypes = [_P, ctypes.c_uint64, _P]
+_lib.adasap_wait_selftest.restype = ctypes.c_int
 _lib.adasap_solver_end.argtypes = [_P]
 _lib.adasap_solver_end.restype = None
 for _f in ["adasap_solver_begin", "adasap_solver_step", "adasap_solver_residual", "adasap_solver_get_w",
@@ -289,6 +294,18 @@ class Context:
                                       _stream(stream))
         _check(status, "adasap_pathwise", allow=(7,))
         return out, W, st.as_dict(), status
+
+    def check_device(self, stream=None):
+        """adasap_check_device: (status, code) of the bounded device waits since the last check
+        (status 6 = ETIMEOUT); clears the record."""
+        code = ctypes.c_int()
+        status = _lib.adasap_check_device(self.h, ctypes.byref(code), _stream(stream))
+        _check(status, "adasap_check_device", allow=(6,))
+        return status, code.value
+
+    def wait_selftest(self, limit_ns, stream=None):
+        """adasap_wait_selftest: enqueue a bounded wait that nothing completes (test of the failure path)."""
+        _check(_lib.adasap_wait_selftest(self.h, int(limit_ns), _stream(stream)), "adasap_wait_selftest")
 
     def predict(self, Xtest, W, stream=None):
         W2 = W if W.dim() == 2 else W.view(-1, 1)

@@ -161,6 +161,9 @@ cudaError_t launch_rows_tc_mrhs(int kern, int d, const float* xr, const float* q
 
 // ---- pipe throughput probe (probe.cu): ex2, rsqrt, FFMA per SM per cycle -------------
 cudaError_t measure_pipes(double* out4, cudaStream_t st);   // ex2, rsqrt, FFMA, sqrt
+// A bounded wait that no arrival completes: records kWaitSelfTestCode in err after limit_ns.
+constexpr int kWaitSelfTestCode = 99;
+cudaError_t launch_wait_selftest(uint64_t limit_ns, int* err, cudaStream_t st);
 
 // ---- sampler (Philox4x32-10; definitions in sampler.cu) -------------------------
 cudaError_t launch_sample_block(uint64_t seed, const long long* t_dev, int64_t t_host, int64_t n,

@@ -3,7 +3,7 @@
 // benchmark reports.  Each thread runs kProbeChains independent dependency
 // chains so that latency is hidden and only issue throughput counts; the SM
 // clock over the run is taken from clock64 against the global timer.
-#include "internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace adasap {
 namespace {
@@ -89,6 +89,25 @@ cudaError_t measure_pipes(double* out4, cudaStream_t st) {
   cudaFree(sink);
   cudaFree(clk);
   return e;
+}
+
+// The failure path of the bounded waits, exercised without a fault: one thread
+// waits on an mbarrier that nothing ever arrives on, with the same bounded wait
+// the tensor-core kernels use; when the limit runs out it records code kWaitSelfTestCode
+// in the context's error flag (as a timed-out tensor-core kernel does) and returns.
+__global__ void k_wait_selftest(uint64_t limit_ns, int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0u, nullptr, limit_ns)) tc_note_timeout(err, kWaitSelfTestCode);
+}
+
+cudaError_t launch_wait_selftest(uint64_t limit_ns, int* err, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(limit_ns, err);
+  return cudaGetLastError();
 }
 
 }  // namespace adasap

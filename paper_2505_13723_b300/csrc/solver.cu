@@ -969,10 +969,13 @@ adasap_status solver_residual(adasap_solver* S, double* rel, cudaStream_t us) {
                    c->s0));
   CT(launch_sum_blocks(S->sqb, kReduceBlocks, &c->sc->resid_sq, c->s0));
   CT(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->s0));
+  int tc_err = 0;
+  CT(cudaMemcpyAsync(&tc_err, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, c->s0));
   CT(cudaStreamSynchronize(c->s0));
   const DevScalars& hs = *c->sc_host;
   *rel = std::sqrt(hs.resid_sq * ((double)c->n / (double)mc) / hs.ysq);
   if (hs.status != 0) return (adasap_status)hs.status;
+  if (tc_err != 0) return ADASAP_ETIMEOUT;   // a tensor-core kernel gave up a wait (its outputs are NaN)
   if (!std::isfinite(*rel) || *rel > 1e8) return ADASAP_EDIVERGED;
   return ADASAP_OK;
 }
@@ -1639,6 +1642,28 @@ extern "C" adasap_status adasap_rmse_nll(const float* mean, int64_t ld_mean, con
   }
   *rmse = std::sqrt(se / (double)m);
   *nll = nl / (double)m;
+  return ADASAP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device-side failures of bounded waits (the paper has no counterpart).
+// ---------------------------------------------------------------------------
+extern "C" adasap_status adasap_check_device(adasap_ctx* c, int* code, void* stream) {
+  if (!c) return ADASAP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  CT(cudaEventRecord(c->ev_in, st));
+  CT(cudaStreamWaitEvent(c->s0, c->ev_in, 0));
+  int h = 0;
+  CT(cudaMemcpyAsync(&h, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, c->s0));
+  CT(cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->s0));
+  CT(cudaStreamSynchronize(c->s0));
+  if (code) *code = h;
+  return h != 0 ? ADASAP_ETIMEOUT : ADASAP_OK;
+}
+
+extern "C" adasap_status adasap_wait_selftest(adasap_ctx* c, uint64_t limit_ns, void* stream) {
+  if (!c || limit_ns > 1000000000ull) return ADASAP_EINVAL;
+  CT(launch_wait_selftest(limit_ns, c->err_dev, (cudaStream_t)stream));
   return ADASAP_OK;
 }
 
