@@ -53,12 +53,12 @@ def test_rf_prior_matches_oracle(lib, kern, d, m, q, s):
     assert (np.abs(F - ref) <= bound[None, :]).all(), np.abs(F - ref).max()
 
 
-def _pathwise_case(lib, P, ns, T, seed, kern=None):
+def _pathwise_case(lib, P, ns, T, seed, kern=None, prec=None):
     kern = P.kernel if kern is None else kern
     n, d = P.X.shape
     q = 512
     z, u, phase, theta, zeta = synth.rf_draws(q, d, DOF[kern], ns, n, P.lam, seed=seed)
-    ctx = lib.Context(P.X, kern, P.ell, P.sigma2, P.lam)
+    ctx = lib.Context(P.X, kern, P.ell, P.sigma2, P.lam, precision=prec)
     y = P.Y[:, 0].copy()
     opts = lib.default_opts(n, b=P.b, r=P.r, max_iters=T, check_every=0, seed=seed)
     out, W, st, status = ctx.pathwise(*_cuda(y, P.Xtest, z, u, phase, theta, zeta), opts=opts)
@@ -80,12 +80,13 @@ def _tol_eta(rec, b, sigma2, power_iters=10):
     return max(1e-4, (2 * power_iters + 1) * base)
 
 
-@pytest.mark.parametrize("kern", [0, 1])
-def test_pathwise_samples_match_oracle(lib, kern):
+@pytest.mark.parametrize("kern,prec", [(0, None), (1, None), (2, 0)])
+def test_pathwise_samples_match_oracle(lib, kern, prec):
     """Seven samples plus the mean through 6 ADASAP iterations (device randomness, replayed
-    by the oracle): W and the samples at 500 test points."""
+    by the oracle): W and the samples at 500 test points; the last case on the FP32
+    CUDA-core path."""
     P = synth.small(n=1500)
-    out, W, out_ref, Wref, rec, status = _pathwise_case(lib, P, ns=7, T=6, seed=17 + kern, kern=kern)
+    out, W, out_ref, Wref, rec, status = _pathwise_case(lib, P, ns=7, T=6, seed=17 + kern, kern=kern, prec=prec)
     assert status == 0
     tol = _tol_eta(rec, P.b, P.sigma2)
     assert _rel(W, Wref) < tol
