@@ -229,6 +229,16 @@ adasap_status adasap_solver_step(adasap_solver* sol, int iters, void* stream);
 adasap_status adasap_solver_residual(adasap_solver* sol, double* rel_resid, void* stream);
 adasap_status adasap_solver_get_w(adasap_solver* sol, float* W, void* stream);
 adasap_status adasap_solver_scalars(adasap_solver* sol, double* eta, double* rho, int* status, void* stream);
+/* Checkpoint and resume of a stepped solve (the paper has no counterpart).
+ * Between iterations the whole state of Alg. 2 is (W_t, V_t, Z_t) and t, since
+ * the draws B, Omega, v0 of iteration t depend only on opts->seed and t.
+ *   get_state: copy W, V, Z (n x s each, host or device) and t; synchronises.
+ *   set_state: load them into a solver begun on the same context with the same
+ *              Y and options (0 <= t < 2^32); steps then continue the same
+ *              trajectory.  Synchronises `stream`. */
+adasap_status adasap_solver_get_state(adasap_solver* sol, float* W, float* V, float* Z, int64_t* t, void* stream);
+adasap_status adasap_solver_set_state(adasap_solver* sol, const float* W, const float* V, const float* Z, int64_t t,
+                                      void* stream);
 void adasap_solver_end(adasap_solver* sol);
 /* Diagnostics of the last iteration (synchronises): out[0..9] = Delta, rho, eta,
  * lambda_hat, Cholesky shift increases, Jacobi sweeps, status, status detail,

@@ -37,7 +37,8 @@ SYMBOLS = ["adasap_default_opts", "adasap_status_string", "adasap_last_error", "
            "adasap_solver_diag", "adasap_set_precision",
            "adasap_kernel_rows_noalloc", "adasap_measure_pipes", "adasap_residual",
            "adasap_solve_batched", "adasap_rf_prior", "adasap_pathwise", "adasap_rmse_nll",
-           "adasap_check_device", "adasap_wait_selftest"]
+           "adasap_check_device", "adasap_wait_selftest", "adasap_solver_get_state",
+           "adasap_solver_set_state"]
 
 
 class Opts(ctypes.Structure):
@@ -109,6 +110,10 @@ _lib.adasap_check_device.argtypes = [_P, ctypes.POINTER(ctypes.c_int), _P]
 _lib.adasap_check_device.restype = ctypes.c_int
 _lib.adasap_wait_selftest.argtypes = [_P, ctypes.c_uint64, _P]
 _lib.adasap_wait_selftest.restype = ctypes.c_int
+_lib.adasap_solver_get_state.argtypes = [_P, _P, _P, _P, ctypes.POINTER(_I64), _P]
+_lib.adasap_solver_get_state.restype = ctypes.c_int
+_lib.adasap_solver_set_state.argtypes = [_P, _P, _P, _P, _I64, _P]
+_lib.adasap_solver_set_state.restype = ctypes.c_int
 _lib.adasap_solver_end.argtypes = [_P]
 _lib.adasap_solver_end.restype = None
 for _f in ["adasap_solver_begin", "adasap_solver_step", "adasap_solver_residual", "adasap_solver_get_w",
@@ -350,6 +355,20 @@ class Solver:
             out = torch.empty(self.context.n, self.s, device="cuda", dtype=torch.float32)
         _check(_lib.adasap_solver_get_w(self.h, _ptr_any(out, "W"), _stream(stream)), "adasap_solver_get_w")
         return out
+
+    def get_state(self, stream=None):
+        """adasap_solver_get_state: (W, V, Z, t) as device tensors and an int."""
+        mk = lambda: torch.empty(self.context.n, self.s, device="cuda", dtype=torch.float32)
+        W, V, Z = mk(), mk(), mk()
+        t = _I64()
+        _check(_lib.adasap_solver_get_state(self.h, _ptr_any(W, "W"), _ptr_any(V, "V"), _ptr_any(Z, "Z"),
+                                            ctypes.byref(t), _stream(stream)), "adasap_solver_get_state")
+        return W, V, Z, t.value
+
+    def set_state(self, W, V, Z, t, stream=None):
+        """adasap_solver_set_state: resume from (W, V, Z, t) (host or device arrays)."""
+        _check(_lib.adasap_solver_set_state(self.h, _ptr_any(W, "W"), _ptr_any(V, "V"), _ptr_any(Z, "Z"), int(t),
+                                            _stream(stream)), "adasap_solver_set_state")
 
     def scalars(self, stream=None):
         eta, rho, st = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()

@@ -1009,6 +1009,44 @@ extern "C" adasap_status adasap_solver_get_w(adasap_solver* S, float* W, void* s
   return ADASAP_OK;
 }
 
+// Checkpoint and resume: (W, V, Z) and the iteration counter t are the whole
+// state of Alg. 2 between iterations (the draws of iteration t depend only on the
+// seed and t).
+extern "C" adasap_status adasap_solver_get_state(adasap_solver* S, float* W, float* V, float* Z, int64_t* t,
+                                                 void* stream) {
+  if (!S || !W || !V || !Z || !t) return ADASAP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)S->c->n * S->s * sizeof(float);
+  long long tc = 0;
+  CT(cudaMemcpyAsync(W, S->W, bytes, cudaMemcpyDefault, st));
+  CT(cudaMemcpyAsync(V, S->V, bytes, cudaMemcpyDefault, st));
+  CT(cudaMemcpyAsync(Z, S->Z, bytes, cudaMemcpyDefault, st));
+  CT(cudaMemcpyAsync(&tc, &S->c->sc->t, sizeof(long long), cudaMemcpyDeviceToHost, st));
+  CT(cudaStreamSynchronize(st));
+  *t = (int64_t)tc;
+  return ADASAP_OK;
+}
+
+extern "C" adasap_status adasap_solver_set_state(adasap_solver* S, const float* W, const float* V, const float* Z,
+                                                 int64_t t, void* stream) {
+  if (!S || !W || !V || !Z || t < 0 || t >= (1LL << 32) || (S->sched && t > S->T_sched)) return ADASAP_EINVAL;
+  adasap_ctx* c = S->c;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)c->n * S->s * sizeof(float);
+  const long long tc = (long long)t;
+  CT(cudaEventRecord(c->ev_in, st));
+  CT(cudaStreamWaitEvent(c->s0, c->ev_in, 0));
+  CT(cudaMemcpyAsync(S->W, W, bytes, cudaMemcpyDefault, c->s0));
+  CT(cudaMemcpyAsync(S->V, V, bytes, cudaMemcpyDefault, c->s0));
+  CT(cudaMemcpyAsync(S->Z, Z, bytes, cudaMemcpyDefault, c->s0));
+  CT(cudaMemcpyAsync(&c->sc->t, &tc, sizeof(long long), cudaMemcpyHostToDevice, c->s0));
+  // Omega of iteration t (each iteration then prepares the next one's)
+  if (!S->identity && !(S->sched && t == S->T_sched)) CT(next_omega(S, 0, c->s0));
+  CT(cudaStreamSynchronize(c->s0));
+  S->iters = t;
+  return ADASAP_OK;
+}
+
 extern "C" adasap_status adasap_solver_scalars(adasap_solver* S, double* eta, double* rho, int* status,
                                                void* stream) {
   if (!S) return ADASAP_EINVAL;

@@ -259,3 +259,29 @@ def test_exact_residual_spans_row_chunks(lib):
     R = OK.kernel_apply(Xd, Xd[nz], W[nz].astype(np.float64), 0, 1.0, 1.0) + 1e-2 * W - Y
     ref = float(np.linalg.norm(R) / np.linalg.norm(Y.astype(np.float64)))
     assert abs(rel - ref) <= 1e-5 * ref
+
+
+@pytest.mark.parametrize("precond", [0, 1, 2])
+def test_checkpoint_resume_continues_the_trajectory(lib, precond):
+    """State after 5 iterations, saved and loaded into a fresh solver (host buffers),
+    then 5 more iterations: the same W_10 as 10 iterations without the interruption."""
+    P = synth.small(n=1200)
+    n = P.X.shape[0]
+    ctx = lib.Context(P.X, P.kernel, P.ell, P.sigma2, P.lam)
+    Y = torch.from_numpy(P.Y).cuda()
+    opts = lib.default_opts(n, b=120, r=24, max_iters=100, check_every=0, seed=12, precond=precond)
+    a = lib.Solver(ctx, Y, opts=opts)
+    a.step(5)
+    W5, V5, Z5, t5 = a.get_state()
+    a.step(5)
+    W10 = a.get_w().cpu().numpy()
+    a.close()
+    assert t5 == 5
+    b = lib.Solver(ctx, Y, opts=opts)
+    b.set_state(W5.cpu().numpy(), V5.cpu().numpy(), Z5.cpu().numpy(), t5)
+    b.step(5)
+    W10b = b.get_w().cpu().numpy()
+    _, _, _, t10 = b.get_state()
+    b.close()
+    assert t10 == 10
+    assert np.abs(W10b - W10).max() <= 1e-6 * np.abs(W10).max()
