@@ -72,7 +72,7 @@ struct adasap_ctx {
   float* qc = nullptr;      // n, ||x'||^2
   double* mean_dev = nullptr;
   cudaStream_t s0 = nullptr, s1 = nullptr;
-  cudaEvent_t ev_in = nullptr, ev_fork = nullptr, ev_join = nullptr, ev_out = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_fork = nullptr, ev_join = nullptr, ev_out = nullptr, ev_omega = nullptr;
   cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
   DevScalars* sc = nullptr;
   DevScalars* sc_host = nullptr;  // pinned
@@ -194,7 +194,7 @@ adasap_status adasap_create(const float* X, int64_t n, int d, int kernel, float 
   if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) return fail(ADASAP_ECUDA);
   if (cudaStreamCreateWithPriority(&c->s0, cudaStreamNonBlocking, lo) != cudaSuccess) return fail(ADASAP_ECUDA);
   if (cudaStreamCreateWithPriority(&c->s1, cudaStreamNonBlocking, hi) != cudaSuccess) return fail(ADASAP_ECUDA);
-  cudaEvent_t* evs[] = {&c->ev_in, &c->ev_fork, &c->ev_join, &c->ev_out};
+  cudaEvent_t* evs[] = {&c->ev_in, &c->ev_fork, &c->ev_join, &c->ev_out, &c->ev_omega};
   for (cudaEvent_t* e : evs)
     if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return fail(ADASAP_ECUDA);
   if (cudaEventCreate(&c->ev_t0) != cudaSuccess || cudaEventCreate(&c->ev_t1) != cudaSuccess)
@@ -262,7 +262,7 @@ void adasap_destroy(adasap_ctx* c) {
   cudaFree(c->tc_lo);
   cudaFree(c->err_dev);
   if (c->sc_host) cudaFreeHost(c->sc_host);
-  cudaEvent_t evs[] = {c->ev_in, c->ev_fork, c->ev_join, c->ev_out, c->ev_t0, c->ev_t1};
+  cudaEvent_t evs[] = {c->ev_in, c->ev_fork, c->ev_join, c->ev_out, c->ev_omega, c->ev_t0, c->ev_t1};
   for (cudaEvent_t e : evs)
     if (e) cudaEventDestroy(e);
   if (c->s0) cudaStreamDestroy(c->s0);
@@ -688,12 +688,16 @@ cudaError_t rec_head(adasap_solver* S, const int64_t* Bs, const float* v0s) {
   if (!S->identity) {
     KR(launch_nystrom_core(cb, S->eps, c->lambda, c->sc, S->Om, S->Ysk, s1));
     KR(launch_woodbury_factor(cb, c->lambda, c->sc, s1));
-    // Omega of iteration t + 1 and its thin QR, off the critical path (the sketch
-    // buffer serves as scratch: the Nystrom core is done with it)
-    KR(next_omega(S, 1, s1));
   }
   if (S->tc_pw && !S->sk_tc) KR(launch_build_tc(c->Xc, c->qc, S->B32, b, c->d, c->dp, S->XBhi, S->XBlo, s1));
   KR(cudaEventRecord(c->ev_join, s1));
+  if (!S->identity) {
+    // Omega of iteration t + 1 and its thin QR, beside the power loop and the
+    // direction (the sketch buffer serves as scratch: the Nystrom core is done
+    // with it); the update waits for it before the iteration counter moves
+    KR(next_omega(S, 1, s1));
+    KR(cudaEventRecord(c->ev_omega, s1));
+  }
   return cudaSuccess;
 }
 
@@ -790,6 +794,7 @@ cudaError_t rec_update(adasap_solver* S, double* trace) {
   KR(launch_scatter(S->W, S->V, S->Z, S->B32, S->b, s, S->D, (float)S->gamma, (float)S->alpha, S->literal, c->sc,
                     s0));
   if (trace) KR(launch_trace(c->sc, trace, s0));
+  if (!S->identity) KR(cudaStreamWaitEvent(s0, c->ev_omega, 0));
   return launch_tick(c->sc, s0);
 }
 
