@@ -23,12 +23,16 @@ namespace adasap {
 
 // ---------------------------------------------------------------------------
 // Gram matrix of the row-concatenation [A1 | A2] (m x (c1 + c2), c <= 256),
-// accumulated in FP64.  With `exact` the products of the FP32 entries are
-// formed in FP64 (exact: 24 + 24 bits).  Exactness matters for Y_nu^T Y_nu:
-// B^T B = C^{-T} (Y_nu^T Y_nu) C^{-1} multiplies its absolute error by cond(C)^2,
-// so FP32 products would swamp the small Nystrom eigenvalues; everywhere else
-// an FP32 product error of eps * |a| |b| is below the data's own rounding.
-// Only upper 64 x 64 tiles are computed; the reduce mirrors them.
+// accumulated in double-float on the FP32 pipes (FP64 arithmetic runs at a
+// small fraction of their rate on this GPU) and returned in FP64.  With
+// `exact` every product of two FP32 entries is also kept exactly (p + e).
+// Exactness matters for Y_nu^T Y_nu: B^T B = C^{-T} (Y_nu^T Y_nu) C^{-1}
+// multiplies its absolute error by cond(C)^2, so FP32 product errors would
+// swamp the small Nystrom eigenvalues; everywhere else an FP32 product error
+// of eps * |a| |b| is below the data's own rounding.  Only the upper 64 x 64
+// tiles whose first row is below `rows` are computed (callers read only the
+// entries with min(i, j) < rows; the tiles left out are returned as zero); the
+// reduce mirrors them.
 // ---------------------------------------------------------------------------
 // chunks of at least 32 rows (the launch caps them at about two CTAs per SM over the upper tiles)
 int gram_chunks_for(int64_t b) { return (int)std::max<int64_t>(1, std::min<int64_t>(240, (b + 31) / 32)); }
@@ -40,37 +44,67 @@ __device__ __forceinline__ float cat_get(const float* A1, int64_t ld1, int c1, c
   return 0.0f;
 }
 
-// 64 x 64 output tiles, 256 threads x (4 x 4) outputs; rows are staged 32 at a
-// time in shared memory, the next slice prefetched into registers while the
-// current one is used.
+// (H, L) += x in double-float (Knuth's TwoSum, the rounding error into L)
+__device__ __forceinline__ void gram_ff_add(float& H, float& L, float x) {
+  const float s = H + x;
+  const float z = s - H;
+  L += (H - (s - z)) + (x - z);
+  H = s;
+}
+
+// the p-th computed tile (ti <= tj, 64 ti < rows) of an nt x nt tiling
+__device__ __forceinline__ void gram_tile(int p, int nt, int rows, int& ti, int& tj) {
+  ti = 0;
+  tj = 0;
+  for (int i = 0; i < nt && 64 * i < rows; ++i) {
+    const int cnt = nt - i;
+    if (p < cnt) {
+      ti = i;
+      tj = i + p;
+      return;
+    }
+    p -= cnt;
+  }
+}
+
+__host__ __device__ inline int gram_active_tiles(int nt, int rows) {
+  int cnt = 0;
+  for (int i = 0; i < nt && 64 * i < rows; ++i) cnt += nt - i;
+  return cnt;
+}
+
+// 64 x 64 output tiles (blockIdx.y = computed tile, blockIdx.x = row chunk),
+// 256 threads x (4 x 4) outputs; rows are staged 32 at a time in shared memory,
+// the next slice prefetched into registers while the current one is used.
 //   EXACT: every product is split exactly into p + e (p = fl(a b), e = fma(a, b, -p),
-//          an error-free transformation) and p is summed in double-float (Knuth's
-//          TwoSum), e in FP32: the chunk sum carries a relative error of about
-//          rows x 2^-48 of sum |a b| -- FP64-like, at FP32-pipe throughput (FP64
-//          arithmetic runs at a small fraction of it on this GPU)
-//   else:  FP32 products summed in FP32, flushed to FP64 every 64 rows.
+//          an error-free transformation), p summed in double-float and e in FP32:
+//          the chunk sum carries a relative error of about rows x 2^-48 of sum |a b|
+//   else:  FP32 products summed in FP32 over 64 rows, those sums in double-float.
+// The chunk's partial of entry (i, j) is written as the pair (hi, lo).
 template <bool EXACT>
 __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1, int64_t ld1, int c1,
                                                    const float* __restrict__ A2, int64_t ld2, int c2,
-                                                   int64_t m, int64_t chunk_rows, double* __restrict__ part) {
+                                                   int64_t m, int64_t chunk_rows, int rows,
+                                                   float2* __restrict__ part) {
   constexpr int TS = 64, KR = 32, PER = KR * TS / 256;  // floats per thread per matrix and slice
-  const int ti = blockIdx.y, tj = blockIdx.z;
-  if (ti > tj) return;
   const int c = c1 + c2;
+  const int nt = (c + TS - 1) / TS;
+  int ti, tj;
+  gram_tile(blockIdx.y, nt, rows, ti, tj);
   __shared__ float sa[KR][TS + 1];
   __shared__ float sb[KR][TS + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int64_t r0 = (int64_t)blockIdx.x * chunk_rows;
   const int64_t r1 = min(m, r0 + chunk_rows);
-  float hi[4][4], lo[4][4];
-  double acc[4][4];
+  float hi[4][4], lo[4][4], H[4][4], L[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       hi[u][v] = 0.0f;
       lo[u][v] = 0.0f;
-      acc[u][v] = 0.0;
+      H[u][v] = 0.0f;
+      L[u][v] = 0.0f;
     }
   float pa[PER], pb[PER];
   auto fetch = [&](int64_t s0) {
@@ -127,7 +161,7 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1,
       for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          acc[u][v] += (double)hi[u][v];
+          gram_ff_add(H[u][v], L[u][v], hi[u][v]);
           hi[u][v] = 0.0f;
         }
     }
@@ -137,43 +171,72 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1,
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const int i = ti * TS + ty + 16 * u, j = tj * TS + tx + 16 * v;
-      const double tot = acc[u][v] + (double)hi[u][v] + (double)lo[u][v];
-      if (i < c && j < c) part[((int64_t)blockIdx.x * c + i) * c + j] = tot;
+      float th, tl;
+      if (EXACT) {
+        th = hi[u][v];
+        tl = lo[u][v];
+      } else {
+        th = H[u][v];
+        tl = L[u][v];
+        gram_ff_add(th, tl, hi[u][v]);
+      }
+      if (i < c && j < c) part[((int64_t)blockIdx.x * c + i) * c + j] = make_float2(th, tl);
     }
 }
 
-__global__ void k_gram_reduce(const double* __restrict__ part, int chunks, int c, double* __restrict__ G) {
+// G[i][j] = sum over chunks of the (hi, lo) partials, in chunk order within
+// each of 8 interleaved subsets and then in subset order (double-float);
+// block = 32 entries x 8 subsets.
+__global__ void __launch_bounds__(256) k_gram_reduce(const float2* __restrict__ part, int chunks, int c, int rows,
+                                                     double* __restrict__ G) {
+  __shared__ float2 sh[8][33];
+  const int x = threadIdx.x & 31, y = threadIdx.x >> 5;
   const int64_t cc = (int64_t)c * c;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < c * c; e += gridDim.x * blockDim.x) {
-    int i = e / c, j = e % c;
-    if ((i >> 6) > (j >> 6)) { const int t = i; i = j; j = t; }
+  const int e = blockIdx.x * 32 + x;
+  int i = e / c, j = e % c;
+  if ((i >> 6) > (j >> 6)) {
+    const int t = i;
+    i = j;
+    j = t;
+  }
+  const bool need = e < c * c && 64 * (i >> 6) < rows;
+  float H = 0.0f, L = 0.0f;
+  if (need) {
     const int64_t o = (int64_t)i * c + j;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int ch = 0;
-    for (; ch + 4 <= chunks; ch += 4) {
-      a0 += part[ch * cc + o];
-      a1 += part[(ch + 1) * cc + o];
-      a2 += part[(ch + 2) * cc + o];
-      a3 += part[(ch + 3) * cc + o];
+#pragma unroll 4
+    for (int ch = y; ch < chunks; ch += 8) {
+      const float2 v = part[ch * cc + o];
+      gram_ff_add(H, L, v.x);
+      L += v.y;
     }
-    for (; ch < chunks; ++ch) a0 += part[ch * cc + o];
-    G[e] = (a0 + a1) + (a2 + a3);
+  }
+  sh[y][x] = make_float2(H, L);
+  __syncthreads();
+  if (y == 0 && e < c * c) {
+    float h = 0.0f, l = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      gram_ff_add(h, l, sh[k][x].x);
+      l += sh[k][x].y;
+    }
+    G[e] = need ? (double)h + (double)l : 0.0;
   }
 }
 
 cudaError_t launch_gram(const float* A1, int64_t ld1, int c1, const float* A2, int64_t ld2, int c2,
-                        int64_t m, double* part, int chunks, double* G, bool exact, cudaStream_t st) {
+                        int64_t m, float2* part, int chunks, double* G, bool exact, cudaStream_t st, int rows) {
   const int c = c1 + c2;
   const int nt = (c + 63) / 64;
-  // about two resident CTAs per SM over the upper tiles; fewer partials to reduce
-  const int active = nt * (nt + 1) / 2;
+  if (rows <= 0 || rows > c) rows = c;
+  // about two resident CTAs per SM over the computed tiles; fewer partials to reduce
+  const int active = gram_active_tiles(nt, rows);
   chunks = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)chunks, (int64_t)(296 / active), (m + 31) / 32}));
   const int64_t chunk_rows = (m + chunks - 1) / chunks;
   if (exact)
-    k_gram_part<true><<<dim3(chunks, nt, nt), 256, 0, st>>>(A1, ld1, c1, A2, ld2, c2, m, chunk_rows, part);
+    k_gram_part<true><<<dim3(chunks, active), 256, 0, st>>>(A1, ld1, c1, A2, ld2, c2, m, chunk_rows, rows, part);
   else
-    k_gram_part<false><<<dim3(chunks, nt, nt), 256, 0, st>>>(A1, ld1, c1, A2, ld2, c2, m, chunk_rows, part);
-  k_gram_reduce<<<std::min(148, (c * c + 255) / 256), 256, 0, st>>>(part, chunks, c, G);
+    k_gram_part<false><<<dim3(chunks, active), 256, 0, st>>>(A1, ld1, c1, A2, ld2, c2, m, chunk_rows, rows, part);
+  k_gram_reduce<<<(c * c + 31) / 32, 256, 0, st>>>(part, chunks, c, rows, G);
   return cudaGetLastError();
 }
 
@@ -659,7 +722,8 @@ cudaError_t launch_nystrom_grams(CoreBufs& cb, const float* Om, const float* Ysk
   const int r = cb.r;
   cudaError_t e;
   // Gram of [Omega | M Omega] -> (Omega^T Omega, Omega^T Y, Y^T Y)
-  if ((e = launch_gram(Om, r, r, Ysk, r, r, cb.b, cb.gram_part, cb.gram_chunks, cb.G, false, st))) return e;
+  // (the Y^T Y block of this one is not used: the exact Gram below supplies it)
+  if ((e = launch_gram(Om, r, r, Ysk, r, r, cb.b, cb.gram_part, cb.gram_chunks, cb.G, false, st, r))) return e;
   return launch_gram(Ysk, r, r, nullptr, 0, 0, cb.b, cb.gram_part, cb.gram_chunks, cb.Gyy, true, st);
 }
 
@@ -1129,13 +1193,16 @@ cudaError_t launch_tick(DevScalars* sc, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // Single-RHS Woodbury applies (App. C.2) and the randomized-powering steps of
 // Alg. 5 as two whole-GPU launches over contiguous row chunks (one chunk per
-// block):
+// block, at most 64 rows, so that each warp takes one group of eight rows):
 //   A  the chunk's rows of h (the input v, or h = sum_p part[p] + lambda a for a
-//      powering step), and its partials of U^T h, ||h||^2 and a . h: a warp
-//      takes eight rows at a time, lanes split the r columns
-//   B  every block sums the partials of all chunks in a fixed order (so the
-//      result does not depend on scheduling), forms the r coefficients of
-//      out = alpha h + U coef, and writes its chunk's rows, eight rows per warp
+//      powering step), and its FP32 partials of U^T h, ||h||^2 and a . h: a warp
+//      takes eight rows at a time, lanes split the r columns.  The last block to
+//      finish sums the partials of all chunks in a fixed order (so the result does
+//      not depend on which block is last) in double-float, and forms the r
+//      coefficients of out = alpha h + U coef.  Its operands (the r x r matrix,
+//      cis or keep, rho) are fetched into registers together with the partials,
+//      so that the tail of the launch is one round trip to L2 and a few barriers.
+//   B  out = alpha h + U coef over the chunk's rows, eight rows per warp
 //      with the row sums reduced across lanes by a transposing butterfly
 // Modes (see ApplyMode):
 //   kInvSqrtNormalised  out = P^{-1/2} v / ||v||
@@ -1148,6 +1215,11 @@ cudaError_t launch_tick(DevScalars* sc, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 constexpr int kWbThreads = 256, kWbWarps = kWbThreads / 32, kWbRows = 8;
 constexpr int kWbSlots = kMaxRank + 2;     // per-chunk partials: U^T h, ||h||^2, a . h
+constexpr int kWbSlotsP = (kWbSlots + 3) & ~3;   // float4-aligned stride of one chunk's partials
+constexpr int kWbG4 = kWbSlotsP / 4;             // float4 groups of one chunk
+constexpr int kWbSub = kWbThreads / kWbG4;       // chunk subsets summed side by side by the last block
+constexpr int kWbMaxChunks = 296;
+static_assert(kWbThreads >= kMaxRank, "one thread per coefficient");
 
 // Sum over the 32 lanes of eight per-lane values x[0..7]; on return lane l
 // holds in x[0] the total of value l >> 2.
@@ -1181,41 +1253,69 @@ __device__ __forceinline__ void transpose_sum8(float x[8], int lane) {
   x[0] += __shfl_xor_sync(full, x[0], 1);
 }
 
-// y[k] = sum_j M[k][j] x[j] (M r x r row-major FP32 in global memory, x in shared
-// memory) by one block: warps take four rows at a time, lanes split j, so a
-// warp has 16 independent loads in flight.
-__device__ void block_matvec(const float* __restrict__ M, const float* x, int r, double* y) {
+// The r x r matrix of the coefficient step (U^T U or M), fetched into registers
+// by the last block before its partial sums arrive: warps take four rows at a
+// time (rows 4 w + 32 p + u), lanes split the columns.
+constexpr int kMvPass = kMaxRank / (4 * kWbWarps);
+struct MvRegs {
+  float m[kMvPass][4][kMaxRank / 32];
+};
+__device__ __forceinline__ void mv_fetch(const float* __restrict__ M, int r, MvRegs& R) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k0 = 4 * warp; k0 < r; k0 += 4 * kWbWarps) {
-    float t[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int jj = 0; jj < kMaxRank / 32; ++jj) {
-      const int j = lane + 32 * jj;
-      if (j < r) {
-        const float xj = x[j];
+  for (int p = 0; p < kMvPass; ++p)
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (k0 + u < r) t[u] = fmaf(M[(k0 + u) * r + j], xj, t[u]);
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int jj = 0; jj < kMaxRank / 32; ++jj) {
+        const int k = 4 * warp + 32 * p + u, j = lane + 32 * jj;
+        R.m[p][u][jj] = (k < r && j < r) ? __ldg(M + k * r + j) : 0.0f;
       }
-    }
+}
+
+// y[k] = sum_j M[k][j] x[j] from the fetched rows (x in shared memory)
+__device__ __forceinline__ void mv_apply(const MvRegs& R, const float* x, int r, double* y) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float xv[kMaxRank / 32];
+#pragma unroll
+  for (int jj = 0; jj < kMaxRank / 32; ++jj) xv[jj] = (lane + 32 * jj < r) ? x[lane + 32 * jj] : 0.0f;
+#pragma unroll
+  for (int p = 0; p < kMvPass; ++p)
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const float v = warp_sum(t[u]);
-      if (lane == 0 && k0 + u < r) y[k0 + u] = (double)v;
+      float t = 0.0f;
+#pragma unroll
+      for (int jj = 0; jj < kMaxRank / 32; ++jj) t = fmaf(R.m[p][u][jj], xv[jj], t);
+      t = warp_sum(t);
+      const int k = 4 * warp + 32 * p + u;
+      if (lane == 0 && k < r) y[k] = (double)t;
     }
-  }
 }
+
+// (H, L) += x in double-float (Knuth's TwoSum, then the error into L)
+__device__ __forceinline__ void ff_add(float& H, float& L, float x) {
+  const float s = H + x;
+  const float z = s - H;
+  L += (H - (s - z)) + (x - z);
+  H = s;
+}
+
+// Scalars of the coefficient step, formed once by thread 0 while the partials load.
+struct WbScalars {
+  double rho, irho, irs;
+};
 
 // Coefficients of out = alpha h + U coef from the totals q (U^T h, ||h||^2,
 // a . h), by one block: written to a.wcoef[0..r) and a.wcoef[kMaxRank] = alpha.
-__device__ void wb_coefficients(const WbArgs& a, const double* q, double* ys, double* zs, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Thread k < r holds cis_k (kInvUnit, kInvSqrtNormalised) or keep_k (kInv).
+__device__ void wb_coefficients(const WbArgs& a, const double* q, double* ys, double* zs, double* red,
+                                const MvRegs& R, const WbScalars& w, double cis_k, double keep_k) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
   const int r = a.r;
   const int mode = a.mode;
-  const double rho = a.sc->rho;
   float* coef = a.wcoef;
   if (mode == kRayleighEta) {
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       // lambda_hat = a . h -> eta (Alg. 5)
       DevScalars* sc = a.sc;
       const double lam_hat = q[kMaxRank + 1];
@@ -1230,56 +1330,57 @@ __device__ void wb_coefficients(const WbArgs& a, const double* q, double* ys, do
   __shared__ float xs[kMaxRank];
   if (mode == kInv) {
     // coef = -keep . M (keep . q) / rho
-    for (int k = threadIdx.x; k < r; k += kWbThreads) xs[k] = (float)(a.keep[k] * q[k]);
+    if (tid < r) xs[tid] = (float)(keep_k * q[tid]);
     __syncthreads();
-    block_matvec(a.Minv, xs, r, zs);
+    mv_apply(R, xs, r, zs);
     __syncthreads();
-    for (int k = threadIdx.x; k < r; k += kWbThreads) coef[k] = (float)(-a.keep[k] * zs[k] / rho);
-    if (threadIdx.x == 0) coef[kMaxRank] = (float)(1.0 / rho);
+    if (tid < r) coef[tid] = (float)(-keep_k * zs[tid] * w.irho);
+    if (tid == 0) coef[kMaxRank] = (float)w.irho;
   } else if (mode == kInvUnit) {
     // The two inverse-square-root applies of Alg. 5 in closed form, exact for any U
     // (P^{-1/2} = rho^{-1/2} I + U diag(cis) U^T, G = U^T U, t = U^T h, y = cis . t, z = G y):
     //   w = P^{-1/2} h = rho^{-1/2} h + U y,  ||w||^2 = ||h||^2 / rho + 2 rho^{-1/2} t.y + y.z
     //   P^{-1/2} w = rho^{-1} h + U (rho^{-1/2} y + cis . (rho^{-1/2} t + z))
-    const double irs = 1.0 / sqrt(rho);
-    for (int k = threadIdx.x; k < r; k += kWbThreads) {
-      ys[k] = a.cis[k] * q[k];
-      xs[k] = (float)ys[k];
+    if (tid < r) {
+      ys[tid] = cis_k * q[tid];
+      xs[tid] = (float)ys[tid];
     }
     __syncthreads();
-    block_matvec(a.Gu, xs, r, zs);
+    mv_apply(R, xs, r, zs);
     __syncthreads();
     if (warp == 0) {
       double acc2 = 0.0;
-      for (int k = lane; k < r; k += 32) acc2 += 2.0 * irs * q[k] * ys[k] + ys[k] * zs[k];
+      for (int k = lane; k < r; k += 32) acc2 += 2.0 * w.irs * q[k] * ys[k] + ys[k] * zs[k];
       acc2 = warp_sum(acc2);
       if (lane == 0) {
-        const double w2 = q[kMaxRank] / rho + acc2;
+        const double w2 = q[kMaxRank] * w.irho + acc2;
         red[32] = w2 > 0.0 ? 1.0 / sqrt(w2) : 0.0;
       }
     }
     __syncthreads();
     const double scale = red[32];
-    for (int k = threadIdx.x; k < r; k += kWbThreads)
-      coef[k] = (float)(scale * (irs * ys[k] + a.cis[k] * (irs * q[k] + zs[k])));
-    if (threadIdx.x == 0) coef[kMaxRank] = (float)(scale / rho);
+    if (tid < r) coef[tid] = (float)(scale * (w.irs * ys[tid] + cis_k * (w.irs * q[tid] + zs[tid])));
+    if (tid == 0) coef[kMaxRank] = (float)(scale * w.irho);
   } else {
     const double scale = q[kMaxRank] > 0.0 ? 1.0 / sqrt(q[kMaxRank]) : 0.0;
-    for (int k = threadIdx.x; k < r; k += kWbThreads) coef[k] = (float)(scale * q[k] * a.cis[k]);
-    if (threadIdx.x == 0) coef[kMaxRank] = (float)(scale / sqrt(rho));
+    if (tid < r) coef[tid] = (float)(scale * q[tid] * cis_k);
+    if (tid == 0) coef[kMaxRank] = (float)(scale * w.irs);
   }
 }
 
 // Chunk `chunk` of launch A (partials; the last chunk to finish reduces them).
 __device__ __forceinline__ void wb_partials_body(const WbArgs& a, int chunk) {
   __shared__ float wtmp[kWbWarps][kMaxRank];
+  __shared__ float wred[2][kWbWarps];
+  __shared__ float sh_hi[kWbSub][kWbSlotsP];
+  __shared__ float sh_lo[kWbSub][kWbSlotsP];
   __shared__ double red[33];
-  __shared__ double red2[33];
   __shared__ double q[kWbSlots];
   __shared__ double ys[kMaxRank];
   __shared__ double zs[kMaxRank];
+  __shared__ WbScalars wsc;
   __shared__ int s_last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
   const int r = a.r;
   const int mode = a.mode;
   const bool from_part = mode == kInvUnit || mode == kRayleighEta;
@@ -1342,73 +1443,86 @@ __device__ __forceinline__ void wb_partials_body(const WbArgs& a, int chunk) {
       }
     }
   }
-  if (need_u) {
+  // the chunk's partials in FP32, warps added in warp order
 #pragma unroll
-    for (int j = 0; j < KJ; ++j) {
-      const int k = lane + 32 * j;
-      if (k < r) wtmp[warp][k] = acc[j];
+  for (int j = 0; j < KJ; ++j) wtmp[warp][lane + 32 * j] = acc[j];
+  hsq = warp_sum(hsq);
+  ah = warp_sum(ah);
+  if (lane == 0) {
+    wred[0][warp] = hsq;
+    wred[1][warp] = ah;
+  }
+  __syncthreads();
+  float* dst = a.wpart + (int64_t)chunk * kWbSlotsP;
+  for (int k = tid; k < kWbSlotsP; k += kWbThreads) {
+    float t = 0.0f;
+    if (k < r && need_u) {
+#pragma unroll
+      for (int w = 0; w < kWbWarps; ++w) t += wtmp[w][k];
+    } else if (k == kMaxRank || k == kMaxRank + 1) {
+#pragma unroll
+      for (int w = 0; w < kWbWarps; ++w) t += wred[k - kMaxRank][w];
     }
+    dst[k] = t;
   }
-  const double hsq_t = block_sum((double)hsq, red);   // contains __syncthreads
-  const double ah_t = block_sum((double)ah, red2);
-  double* dst = a.wpart + (int64_t)chunk * kWbSlots;
-  if (need_u) {
-    for (int k = threadIdx.x; k < r; k += kWbThreads) {
-      double t = 0.0;
-      for (int w = 0; w < kWbWarps; ++w) t += (double)wtmp[w][k];
-      dst[k] = t;
-    }
-  }
-  if (threadIdx.x == 0) {
-    dst[kMaxRank] = hsq_t;
-    dst[kMaxRank + 1] = ah_t;
-  }
-  // The last block to finish sums the partials of all chunks in chunk order (a
-  // fixed lane split and shuffle tree: the totals do not depend on which block is
-  // last) and forms the coefficients.  No block waits for another.
+  // The last block to finish sums the partials of all chunks; no block waits
+  // for another.
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(a.count, 1u) == (unsigned)a.nchunk - 1u;
+  if (tid == 0) s_last = atomicAdd(a.count, 1u) == (unsigned)a.nchunk - 1u;
   __syncthreads();
   if (!s_last) return;
   __threadfence();
+  // operands of the coefficient step, in flight with the partials below
+  MvRegs R;
+  const float* M = mode == kInv ? a.Minv : (mode == kInvUnit ? a.Gu : nullptr);
+  if (M) mv_fetch(M, r, R);
+  double cis_k = 0.0, keep_k = 0.0;
+  if (tid < r) {
+    if (mode == kInv) keep_k = a.keep[tid];
+    else if (mode != kRayleighEta) cis_k = a.cis[tid];
+  }
+  if (tid == 0 && mode != kRayleighEta) {
+    const double rho = a.sc->rho;
+    wsc.rho = rho;
+    wsc.irho = 1.0 / rho;
+    wsc.irs = 1.0 / sqrt(rho);
+  }
+  // thread (g, j) adds float4 group g of chunks j, j + kWbSub, ... in double-float;
+  // the kWbSub subsets are then added in subset order
   {
-    // warp w sums chunks w, w + 8, ... (four in flight); lane j slots j, j + 32, ...
-    // (coalesced); the eight warp sums are then added in warp order
-    constexpr int KS = (kWbSlots + 31) / 32;
-    double t[KS];
+    const int g = tid % kWbG4, j = tid / kWbG4;
+    float H[4] = {0.0f, 0.0f, 0.0f, 0.0f}, L[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (j < kWbSub) {
+      const float4* src = reinterpret_cast<const float4*>(a.wpart) + g;
+#pragma unroll 8
+      for (int c = j; c < a.nchunk; c += kWbSub) {
+        const float4 v = __ldcg(src + (int64_t)c * kWbG4);
+        ff_add(H[0], L[0], v.x);
+        ff_add(H[1], L[1], v.y);
+        ff_add(H[2], L[2], v.z);
+        ff_add(H[3], L[3], v.w);
+      }
 #pragma unroll
-    for (int m = 0; m < KS; ++m) t[m] = 0.0;
-    for (int c0 = warp; c0 < a.nchunk; c0 += 4 * kWbWarps) {
-#pragma unroll
-      for (int cc = 0; cc < 4; ++cc) {
-        const int c = c0 + cc * kWbWarps;
-        if (c < a.nchunk) {
-#pragma unroll
-          for (int m = 0; m < KS; ++m) {
-            const int k = lane + 32 * m;
-            if (k < kWbSlots) t[m] += __ldcg(a.wpart + (int64_t)c * kWbSlots + k);
-          }
-        }
+      for (int e = 0; e < 4; ++e) {
+        sh_hi[j][4 * g + e] = H[e];
+        sh_lo[j][4 * g + e] = L[e];
       }
     }
-    __shared__ double wsum[kWbWarps][kWbSlots];
-#pragma unroll
-    for (int m = 0; m < KS; ++m) {
-      const int k = lane + 32 * m;
-      if (k < kWbSlots) wsum[warp][k] = t[m];
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < kWbSlots; k += kWbThreads) {
-      double v = 0.0;
-#pragma unroll
-      for (int w = 0; w < kWbWarps; ++w) v += wsum[w][k];
-      q[k] = v;
-    }
   }
-  if (threadIdx.x == 0) *a.count = 0u;
   __syncthreads();
-  wb_coefficients(a, q, ys, zs, red);
+  for (int k = tid; k < kWbSlots; k += kWbThreads) {
+    float H = 0.0f, L = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kWbSub; ++j) {
+      ff_add(H, L, sh_hi[j][k]);
+      L += sh_lo[j][k];
+    }
+    q[k] = (double)H + (double)L;
+  }
+  if (tid == 0) *a.count = 0u;
+  __syncthreads();
+  wb_coefficients(a, q, ys, zs, red, R, wsc, cis_k, keep_k);
 }
 
 __global__ void __launch_bounds__(kWbThreads) k_wb_partials(WbArgs a) { wb_partials_body(a, blockIdx.x); }
@@ -1495,8 +1609,10 @@ cudaError_t launch_wb_grouped(const WbArgs* g, int ngrp, int max_chunks, int mod
   return cudaGetLastError();
 }
 
-// enough chunks for the whole GPU, few enough that the last block's sum is short
-int wb_chunks_for(int64_t b) { return (int)std::max<int64_t>(1, std::min<int64_t>(148, (b + 31) / 32)); }
+// chunks of at most 64 rows (one group of eight rows per warp) while that keeps
+// the last block's sum short
+int wb_chunks_for(int64_t b) { return (int)std::max<int64_t>(1, std::min<int64_t>(kWbMaxChunks, (b + 63) / 64)); }
+size_t wb_part_floats(int64_t b) { return (size_t)wb_chunks_for(b) * kWbSlotsP; }
 
 cudaError_t launch_wb_single(CoreBufs& cb, int mode, const float* v, float* out, DevScalars* sc, cudaStream_t st) {
   WbArgs a{};

@@ -184,7 +184,7 @@ struct CoreBufs {
   int r, s;
   int64_t b;
   // Gram workspace
-  double* gram_part;  // [gram_chunks][2r][2r]
+  float2* gram_part;  // [gram_chunks][2r][2r] (hi, lo) partial pairs
   int gram_chunks;
   double* G;          // 2r x 2r
   double* Lc;         // r x r lower Cholesky of the Nystrom core
@@ -209,15 +209,17 @@ struct CoreBufs {
   double* alpha;      // scalar apply coefficient
   double* Ident;      // r x r identity
   double* cis;        // r  (S_k + rho)^{-1/2} - rho^{-1/2}
-  double* wb_part;    // [wb_chunks_for(b)][kMaxRank + 2] partials of the single-RHS applies
+  float* wb_part;     // wb_part_floats(b): per-chunk partials of the single-RHS applies
   float* wb_coef;     // [kMaxRank + 1] apply coefficients and alpha
   unsigned int* wb_count;  // finished-block counter (zero between launches)
 };
 int wb_chunks_for(int64_t b);
+size_t wb_part_floats(int64_t b);  // floats of CoreBufs::wb_part for block size b
 int gram_chunks_for(int64_t b);
 int utv_chunks_for(int64_t b);
 cudaError_t launch_gram(const float* A1, int64_t ld1, int c1, const float* A2, int64_t ld2, int c2,
-                        int64_t m, double* part, int chunks, double* G, bool exact, cudaStream_t st);
+                        int64_t m, float2* part, int chunks, double* G, bool exact, cudaStream_t st,
+                        int rows = 0 /* entries with min(i, j) >= rows are not needed (0: all) */);
 cudaError_t launch_orthonormalize(CoreBufs& cb, float* Om, float* tmp, DevScalars* sc, cudaStream_t st);
 // Gram matrices of the sketch (whole-GPU launches): G = [Omega | Y]^T [Omega | Y], Gyy = Y^T Y (exact products)
 cudaError_t launch_nystrom_grams(CoreBufs& cb, const float* Om, const float* Ysk, cudaStream_t st);
@@ -256,7 +258,7 @@ struct WbArgs {
   const double* cis;
   DevScalars* sc;
   float* out;
-  double* wpart;        // nchunk x kWbSlots partials
+  float* wpart;         // nchunk x kWbSlotsP partials (16-byte aligned)
   float* wcoef;         // coef[0..r) and alpha at [kMaxRank] (written by the last block of launch A)
   unsigned int* count;  // blocks of launch A done (reset by its last block)
   int nchunk;

@@ -581,7 +581,7 @@ adasap_status alloc_solver(adasap_solver* S) {
   cb.s = s;
   cb.b = b;
   cb.gram_chunks = gram_chunks_for(b);
-  cb.gram_part = ar.get<double>((size_t)cb.gram_chunks * 4 * rr * rr);
+  cb.gram_part = ar.get<float2>((size_t)cb.gram_chunks * 4 * rr * rr);
   cb.G = ar.get<double>((size_t)4 * rr * rr);
   cb.Lc = ar.get<double>((size_t)rr * rr);
   cb.Gnu = ar.get<double>((size_t)rr * rr);
@@ -605,7 +605,7 @@ adasap_status alloc_solver(adasap_solver* S) {
   cb.alpha = ar.get<double>(2);
   cb.Ident = ar.get<double>((size_t)rr * rr);
   cb.cis = ar.get<double>(rr);
-  cb.wb_part = ar.get<double>((size_t)wb_chunks_for(b) * (kMaxRank + 2));
+  cb.wb_part = ar.get<float>(wb_part_floats(b));
   cb.wb_coef = ar.get<float>(kMaxRank + 1);
   cb.wb_count = ar.get<unsigned int>(1);
   if (cb.wb_count && cudaMemset(cb.wb_count, 0, sizeof(unsigned int)) != cudaSuccess) return ADASAP_ECUDA;
