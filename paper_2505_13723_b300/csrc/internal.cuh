@@ -117,6 +117,7 @@ struct TcArgs {
   int nsplit;
   float sigma2;
   int* err;          // set to 1 on a wait timeout
+  int flat;          // 1: equal tile runs per CTA (one product only; nsplit = tc_flat_slots)
 };
 TcArgs make_tc_args(int d, const float* xr, const float* qr, const int* ridx, int64_t m, int dp, const float* bhi,
                     const float* blo, int64_t ncols, int self_mode, const float* w, int64_t ldw, float* part,
@@ -134,6 +135,11 @@ cudaError_t tc_init();
 // an m x ncols product spread over min(slots, max_ctas) persistent CTAs (0: all).
 int tc_slots();
 int tc_nsplit(int64_t m, int64_t ncols, int max_ctas = 0);
+// Partial slots of the flat schedule (equal tile runs per CTA) when it is the
+// cheaper one, else 0; launch_rows_tc takes that schedule when nsplit equals it.
+int tc_flat_slots(int64_t m, int64_t ncols, int max_ctas = 0);
+// tc_flat_slots if non-zero, else tc_nsplit: the split count for launch_rows_tc.
+int tc_plan_nsplit(int64_t m, int64_t ncols, int max_ctas = 0);
 // Split (hi, lo) column operands in the MMA layout for X' (or rows gidx of X').
 cudaError_t launch_build_tc(const float* X, const float* q, const int* gidx, int64_t n, int d, int dp, float* hi,
                             float* lo, cudaStream_t st);

@@ -133,7 +133,17 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
   // tile varying fastest, so the CTAs running at one time share column tiles in
   // L2.  The pipeline phases run on across items (gt counts this CTA's tiles).
   uint32_t gt = 0, ndrain = 0;
-  for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+  // Flat mode (one product): CTA x takes the tiles [x T / G, (x + 1) T / G) of the
+  // row-tile-major sequence of all T tiles (G CTAs, T >= G), as runs within one
+  // row tile each.  A run's partials go to slot x - (first CTA of its row tile);
+  // the CTA that ends a row tile zeroes the slots after its own, so every slot
+  // of every row is written.
+  const bool flat = !GROUPED && a0.flat;
+  const int64_t ctiles = (a0.ncols + kTcN - 1) / kTcN;
+  const int64_t ftotal = flat ? (a0.m + kTcM - 1) / kTcM * ctiles : 0;
+  int64_t fpos = flat ? (int64_t)blockIdx.x * ftotal / gridDim.x : 0;
+  const int64_t fend = flat ? ((int64_t)blockIdx.x + 1) * ftotal / gridDim.x : 0;
+  for (int64_t item = blockIdx.x; flat ? fpos < fend : item < nitems; item += gridDim.x) {
     int sys = 0;
     if (GROUPED) {  // the product this item belongs to: last g with gstart[g] <= item
       int hi = ngrp - 1;
@@ -146,10 +156,24 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
     const TcArgs& a = GROUPED ? grp[sys] : a0;
     const int64_t li = GROUPED ? item - gstart[sys] : item;
     const int64_t rtiles = (a.m + kTcM - 1) / kTcM;
-    const int64_t rtile = li % rtiles, split = li / rtiles;
+    int64_t rtile, split, c0, c1;
+    bool row_end = false;
+    if (flat) {
+      rtile = fpos / ctiles;
+      const int64_t tb = fpos % ctiles, te = min(ctiles, tb + (fend - fpos));
+      // first CTA of the row tile: the largest y with y T / G <= rtile * ctiles
+      split = (int64_t)blockIdx.x - ((rtile * ctiles + 1) * (int64_t)gridDim.x - 1) / ftotal;
+      c0 = tb * kTcN;
+      c1 = min(a.ncols, te * kTcN);
+      row_end = te == ctiles;
+      fpos += te - tb;
+    } else {
+      rtile = li % rtiles;
+      split = li / rtiles;
+      c0 = split * a.cps;
+      c1 = min(a.ncols, c0 + a.cps);
+    }
     const int64_t row0 = rtile * kTcM;
-    const int64_t c0 = split * a.cps;
-    const int64_t c1 = min(a.ncols, c0 + a.cps);
     // after an abort the remaining items only write NaN partials (the flag is read
     // after a block barrier, so every role agrees)
     const int ntiles = (c1 > c0 && !*abort_flag) ? (int)((c1 - c0 + kTcN - 1) / kTcN) : 0;
@@ -364,6 +388,8 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
       if (cg == 0 && ri < a.m) {
         const float tot = (red[rl] + red[kTcM + rl]) + (red[2 * kTcM + rl] + red[3 * kTcM + rl]);
         a.part[split * a.m + ri] = (bad || *abort_flag) ? __int_as_float(0x7fc00000) : a.sigma2 * tot;
+        if (row_end)
+          for (int64_t s2 = split + 1; s2 < a.nsplit; ++s2) a.part[s2 * a.m + ri] = 0.0f;
       }
     }
     gt += (uint32_t)ntiles;
@@ -472,6 +498,33 @@ int tc_nsplit(int64_t m, int64_t ncols, int max_ctas) {
   return (int)best;
 }
 
+// Flat mode (see the kernel): the partial slots a row needs when the T tiles of
+// the product are cut into G equal runs, or 0 when that is not cheaper than the
+// best (row tile x split) items (same cost model: a run costs its tiles plus a
+// start-up of two tiles; a CTA's share meets at most ceil((P - 1) / tiles) + 1
+// row tiles, and a row tile at most 1 + ceil((tiles - 1) / floor(T / G)) CTAs).
+// Only for products of at most 64 tiles per CTA: with more, the item order (row
+// tile fastest) lets the CTAs running at one time share column tiles in L2,
+// which equal runs give up, and the waves it rounds to cost little.
+int tc_flat_slots(int64_t m, int64_t ncols, int max_ctas) {
+  const int64_t rt = (m + kTcM - 1) / kTcM;
+  const int64_t tiles = (ncols + kTcN - 1) / kTcN;
+  const int64_t G = (max_ctas > 0 && max_ctas < tc_slots()) ? max_ctas : tc_slots();
+  const int64_t T = rt * tiles;
+  if (T < 2 * G || T > 64 * G) return 0;
+  const int64_t P = (T + G - 1) / G, pmin = T / G;
+  const double flat_cost = (double)P + 2.0 * (double)((P - 1 + tiles - 1) / tiles + 1);
+  const int64_t ns = tc_nsplit(m, ncols, max_ctas);
+  const double gs_cost = (double)((rt * ns + G - 1) / G) * ((double)((tiles + ns - 1) / ns) + 2.0);
+  if (!(flat_cost < gs_cost)) return 0;
+  return (int)std::min<int64_t>(G, 1 + (tiles - 1 + pmin - 1) / pmin);
+}
+
+int tc_plan_nsplit(int64_t m, int64_t ncols, int max_ctas) {
+  const int fs = tc_flat_slots(m, ncols, max_ctas);
+  return fs > 0 ? fs : tc_nsplit(m, ncols, max_ctas);
+}
+
 template <int KERN, int KP, bool G>
 static cudaError_t launch_tc_k(const TcArgs& a, const TcArgs* grp, const int64_t* gstart, int ngrp, int ctas,
                                cudaStream_t st) {
@@ -506,6 +559,7 @@ TcArgs make_tc_args(int d, const float* xr, const float* qr, const int* ridx, in
   const int64_t tiles = (ncols + kTcN - 1) / kTcN;
   a.cps = (tiles + nsplit - 1) / nsplit * kTcN;
   a.nsplit = nsplit;
+  a.flat = 0;
   return a;
 }
 
@@ -516,9 +570,16 @@ cudaError_t launch_rows_tc(int kern, int d, const float* xr, const float* qr, co
                            int64_t ldw, float* part, int nsplit, float sigma2, int* err, cudaStream_t st,
                            int max_ctas) {
   if (m <= 0 || ncols <= 0) return cudaSuccess;
-  const TcArgs a = make_tc_args(d, xr, qr, ridx, m, dp, bhi, blo, ncols, self_mode, w, ldw, part, nsplit, sigma2, err);
+  TcArgs a = make_tc_args(d, xr, qr, ridx, m, dp, bhi, blo, ncols, self_mode, w, ldw, part, nsplit, sigma2, err);
   const int slots = (max_ctas > 0 && max_ctas < tc_slots()) ? max_ctas : tc_slots();
-  const int ctas = (int)std::min<int64_t>(tc_items(a), slots);
+  int ctas = (int)std::min<int64_t>(tc_items(a), slots);
+  // the flat schedule when the caller's slot count is the one it needs (either
+  // schedule writes every slot of every row)
+  const int fs = tc_flat_slots(m, ncols, max_ctas);
+  if (fs > 0 && nsplit == fs) {
+    a.flat = 1;
+    ctas = slots;
+  }
   return launch_tc_any<false>(kern, tc_kp(d), a, nullptr, nullptr, 0, ctas, st);
 }
 

@@ -309,7 +309,7 @@ RowsPlan plan_rows(const adasap_ctx* c, int64_t m, int64_t ncols, int s, int res
   p.mrhs = p.tc && s > 1;
   p.ctas = (p.tc && reserve_sms > 0) ? std::max(1, tc_slots() - reserve_sms) : 0;
   p.nsplit = !p.tc ? rows_nsplit(m, ncols, s, c->dp, false)
-                   : (p.mrhs ? tc_mrhs_nsplit(m, ncols, p.ctas) : tc_nsplit(m, ncols, p.ctas));
+                   : (p.mrhs ? tc_mrhs_nsplit(m, ncols, p.ctas) : tc_plan_nsplit(m, ncols, p.ctas));
   p.wop_floats = p.mrhs ? 2 * tc_mrhs_wfloats(ncols, s) : 0;
   return p;
 }
@@ -905,7 +905,7 @@ adasap_status solver_prepare(adasap_ctx* c, const float* Y, int s, const adasap_
   S->ns1 = S->plan1.nsplit;
   S->sk_tc = S->tc_pw && !identity && r >= 2;
   S->ns_sk = identity ? 1 : (S->sk_tc ? tc_mrhs_nsplit(b, b) : rows_nsplit(b, b, r, c->dp, false));
-  S->ns_pw = S->tc_pw ? tc_nsplit(b, b) : rows_nsplit(b, b, 1, c->dp, false);
+  S->ns_pw = S->tc_pw ? tc_plan_nsplit(b, b) : rows_nsplit(b, b, 1, c->dp, false);
   S->ns_c = S->plan_c.nsplit;
   adasap_status st = alloc_solver(S);
   if (st != ADASAP_OK) { delete S; return st; }

@@ -133,6 +133,25 @@ def test_multi_rhs_tensor_core_product_many_items_per_cta(lib, kern):
     _check_rows(out[pick].astype(np.float64), X, pick, W, kern, 0.3, 1.0)
 
 
+@pytest.mark.parametrize("m,n,kern", [(4999, 20011, 1), (2500, 50001, 2), (9999, 10001, 0)])
+def test_tensor_core_flat_schedule_ragged(lib, m, n, kern):
+    """Single-RHS tensor-core products whose tiles are cut into equal runs per CTA
+    (the flat schedule: at these sizes a row tile meets up to 5, 9 and 3 CTAs, each
+    writing its own partial slot and the last one zeroing the rest), with the last
+    row tile and the last column tile ragged.  Rows sampled from every row tile,
+    plus the whole last one."""
+    d = 11
+    X, W = _data(n, d, 1, seed=m + kern)
+    ell = 0.8 * np.sqrt(d)
+    ctx = _ctx(lib, X, kern, ell, 0.7, 1e-3, lib.PREC_TF32X3)
+    g = np.random.default_rng(m)
+    rows = g.choice(n, size=m, replace=False)
+    out = ctx.kernel_rows(torch.from_numpy(rows).cuda(), torch.from_numpy(W).cuda()).cpu().numpy()
+    last = (m - 1) // 128 * 128
+    pick = np.unique(np.concatenate([g.choice(last, size=300, replace=False), np.arange(last, m)]))
+    _check_rows(out[pick].astype(np.float64), X, rows[pick], W, kern, ell, 0.7)
+
+
 @pytest.mark.parametrize("prec,s", [(0, 2), (1, 1), (1, 2)])
 def test_kernel_rows_invalid_index_gives_nan_row(lib, prec, s):
     X, W = _data(500, 4, s, seed=3)
