@@ -83,6 +83,17 @@ __device__ __forceinline__ void kval_grad(float u, float& kv, float& gv) {
 }
 
 // ---- reductions ------------------------------------------------------------
+// (H, L) += x in double-float arithmetic (Knuth's TwoSum: H + x is split exactly
+// into its rounded sum and rounding error, the error accumulated in L).  Sums of
+// FP32 terms carried this way keep about 48 bits on the FP32 pipes; FP64
+// arithmetic runs at a small fraction of their rate on this GPU.
+__device__ __forceinline__ void ff_add(float& H, float& L, float x) {
+  const float s = H + x;
+  const float z = s - H;
+  L += (H - (s - z)) + (x - z);
+  H = s;
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -44,14 +44,6 @@ __device__ __forceinline__ float cat_get(const float* A1, int64_t ld1, int c1, c
   return 0.0f;
 }
 
-// (H, L) += x in double-float (Knuth's TwoSum, the rounding error into L)
-__device__ __forceinline__ void gram_ff_add(float& H, float& L, float x) {
-  const float s = H + x;
-  const float z = s - H;
-  L += (H - (s - z)) + (x - z);
-  H = s;
-}
-
 // the p-th computed tile (ti <= tj, 64 ti < rows) of an nt x nt tiling
 __device__ __forceinline__ void gram_tile(int p, int nt, int rows, int& ti, int& tj) {
   ti = 0;
@@ -161,7 +153,7 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1,
       for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          gram_ff_add(H[u][v], L[u][v], hi[u][v]);
+          ff_add(H[u][v], L[u][v], hi[u][v]);
           hi[u][v] = 0.0f;
         }
     }
@@ -178,7 +170,7 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1,
       } else {
         th = H[u][v];
         tl = L[u][v];
-        gram_ff_add(th, tl, hi[u][v]);
+        ff_add(th, tl, hi[u][v]);
       }
       if (i < c && j < c) part[((int64_t)blockIdx.x * c + i) * c + j] = make_float2(th, tl);
     }
@@ -206,7 +198,7 @@ __global__ void __launch_bounds__(256) k_gram_reduce(const float2* __restrict__ 
 #pragma unroll 4
     for (int ch = y; ch < chunks; ch += 8) {
       const float2 v = part[ch * cc + o];
-      gram_ff_add(H, L, v.x);
+      ff_add(H, L, v.x);
       L += v.y;
     }
   }
@@ -216,7 +208,7 @@ __global__ void __launch_bounds__(256) k_gram_reduce(const float2* __restrict__ 
     float h = 0.0f, l = 0.0f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      gram_ff_add(h, l, sh[k][x].x);
+      ff_add(h, l, sh[k][x].x);
       l += sh[k][x].y;
     }
     G[e] = need ? (double)h + (double)l : 0.0;
@@ -1290,14 +1282,6 @@ __device__ __forceinline__ void mv_apply(const MvRegs& R, const float* x, int r,
       const int k = 4 * warp + 32 * p + u;
       if (lane == 0 && k < r) y[k] = (double)t;
     }
-}
-
-// (H, L) += x in double-float (Knuth's TwoSum, then the error into L)
-__device__ __forceinline__ void ff_add(float& H, float& L, float x) {
-  const float s = H + x;
-  const float z = s - H;
-  L += (H - (s - z)) + (x - z);
-  H = s;
 }
 
 // Scalars of the coefficient step, formed once by thread 0 while the partials load.

@@ -392,6 +392,9 @@ cudaError_t launch_rows(int kern, int dp, const RowsArgs& a, int s, int nsplit, 
 }
 
 // ---------------------------------------------------------------------------
+// out[i][c] = sum_p part[p][i][coff + c] + beta A[aidx i][c] + gamma B[bidx i][c],
+// summed in double-float (the products beta A, gamma B split exactly) and
+// rounded once to FP32; blocksq (optional) gets each block's sum of out^2.
 __global__ void k_reduce(const float* __restrict__ part, int nsplit, int64_t m, int na, int coff,
                          int s, float* __restrict__ out, int64_t ldo, float beta,
                          const float* __restrict__ A, const int* __restrict__ aidx, int64_t lda,
@@ -402,19 +405,28 @@ __global__ void k_reduce(const float* __restrict__ part, int nsplit, int64_t m, 
   double sq = 0.0;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / s;
+    const int64_t i = s == 1 ? e : e / s;
     const int c = (int)(e - i * s);
-    double acc = 0.0;
-    for (int p = 0; p < nsplit; ++p) acc += (double)part[((int64_t)p * m + i) * na + coff + c];
+    float H = 0.0f, L = 0.0f;
+    const float* src = part + i * na + coff + c;
+    const int64_t pstride = m * na;
+#pragma unroll 4
+    for (int p = 0; p < nsplit; ++p) ff_add(H, L, __ldg(src + p * pstride));
     if (beta != 0.0f) {
       const int64_t ai = aidx ? aidx[i] : i;
-      acc += (double)beta * (double)A[ai * lda + c];
+      const float av = A[ai * lda + c];
+      const float pr = beta * av;
+      ff_add(H, L, pr);
+      L += fmaf(beta, av, -pr);
     }
     if (gamma != 0.0f) {
       const int64_t bi = bidx ? bidx[i] : i;
-      acc += (double)gamma * (double)B[bi * ldb + c];
+      const float bv = B[bi * ldb + c];
+      const float pr = gamma * bv;
+      ff_add(H, L, pr);
+      L += fmaf(gamma, bv, -pr);
     }
-    const float v = (float)acc;
+    const float v = H + L;
     out[i * ldo + c] = v;
     if (blocksq) sq += (double)v * (double)v;
   }

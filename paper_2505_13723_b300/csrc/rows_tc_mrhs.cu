@@ -15,7 +15,7 @@
 // The accumulators span one column split (at most kMrhsMaxCols columns, the even
 // and odd tiles in two accumulators, so that the FP32 accumulation in the tensor
 // cores stays below the product's tolerance even for sums of one sign); the
-// splits are summed in FP64 by k_reduce.
+// splits are summed in double-float by k_reduce.
 //
 // CTA = 128 rows, 384 threads, one CTA per SM, persistent over (row tile,
 // split) items like rows_tc.cu:
