@@ -66,8 +66,11 @@ __host__ __device__ inline int gram_active_tiles(int nt, int rows) {
 }
 
 // 64 x 64 output tiles (blockIdx.y = computed tile, blockIdx.x = row chunk),
-// 256 threads x (4 x 4) outputs; rows are staged 32 at a time in shared memory,
-// the next slice prefetched into registers while the current one is used.
+// 256 threads x (4 x 4) outputs, thread (ty, tx) owning rows 4 ty .. 4 ty + 3 and
+// columns 4 tx .. 4 tx + 3 of the tile, so that its operands of one row are two
+// 16-byte shared-memory loads (three wavefronts per warp instead of eight); rows
+// are staged 32 at a time in shared memory, the next slice prefetched into
+// registers while the current one is used.
 //   EXACT: every product is split exactly into p + e (p = fl(a b), e = fma(a, b, -p),
 //          an error-free transformation), p summed in double-float and e in FP32:
 //          the chunk sum carries a relative error of about rows x 2^-48 of sum |a b|
@@ -83,8 +86,8 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1,
   const int nt = (c + TS - 1) / TS;
   int ti, tj;
   gram_tile(blockIdx.y, nt, rows, ti, tj);
-  __shared__ float sa[KR][TS + 1];
-  __shared__ float sb[KR][TS + 1];
+  __shared__ __align__(16) float sa[KR][TS + 4];
+  __shared__ __align__(16) float sb[KR][TS + 4];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int64_t r0 = (int64_t)blockIdx.x * chunk_rows;
   const int64_t r1 = min(m, r0 + chunk_rows);
@@ -124,12 +127,10 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1,
     if (s0 + KR < r1) fetch(s0 + KR);  // in flight during the products below
 #pragma unroll 4
     for (int rr = 0; rr < KR; ++rr) {
-      float av[4], bv[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        av[u] = sa[rr][ty + 16 * u];
-        bv[u] = sb[rr][tx + 16 * u];
-      }
+      const float4 a4 = *reinterpret_cast<const float4*>(&sa[rr][4 * ty]);
+      const float4 b4 = *reinterpret_cast<const float4*>(&sb[rr][4 * tx]);
+      const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+      const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1,
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      const int i = ti * TS + ty + 16 * u, j = tj * TS + tx + 16 * v;
+      const int i = ti * TS + 4 * ty + u, j = tj * TS + 4 * tx + v;
       float th, tl;
       if (EXACT) {
         th = hi[u][v];
@@ -314,7 +315,11 @@ __global__ void __launch_bounds__(512) k_nys_chol(const double* __restrict__ G, 
 // Column-wise triangular solves with the lower factor L (r x r, row-major):
 //   upper == 0:  L X = R'     upper == 1:  L^T X = R'
 // where R' = trans ? R^T : R.  L and the reciprocals of its diagonal are
-// staged in shared memory; one warp per right-hand side column.
+// staged in shared memory; one warp per right-hand side column solves in column
+// (axpy) form -- lane l holds rows l, l + 32, ...; at step i the owner of row i
+// finishes x_i, broadcasts it, and every lane subtracts L[k][i] x_i (lower) or
+// L[i][k] x_i (upper) from its rows still to come, so a step needs no
+// reduction (half the FP64 instructions of the dot-product form).
 constexpr int kTrsmWarps = 4;
 template <typename T>
 __global__ void __launch_bounds__(32 * kTrsmWarps) k_trsm(const double* __restrict__ L, int r,
@@ -324,40 +329,46 @@ __global__ void __launch_bounds__(32 * kTrsmWarps) k_trsm(const double* __restri
   const int ld = r + 1;
   T* sL = reinterpret_cast<T*>(shd_trsm);  // r x (r + 1)
   T* rinv = sL + r * ld;                  // r
-  T* xs = rinv + r;                       // kTrsmWarps x r
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) sL[(e / r) * ld + e % r] = (T)L[e];
+  const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = blockIdx.x * kTrsmWarps + warp;
-  T* x = xs + warp * r;
-  // the right-hand side column is staged first, so the solve loop touches shared memory only
-  if (col < r)
-    for (int i = lane; i < r; i += 32) x[i] = (T)(trans ? R[(int64_t)col * r + i] : R[(int64_t)i * r + col]);
+  constexpr int KJ = kMaxRank / 32;
+  T x[KJ];
+#pragma unroll
+  for (int j = 0; j < KJ; ++j) {
+    const int k = lane + 32 * j;
+    x[j] = (col < r && k < r) ? (T)(trans ? R[(int64_t)col * r + k] : R[(int64_t)k * r + col]) : T(0);
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < r; i += blockDim.x) rinv[i] = T(1) / sL[i * ld + i];
   __syncthreads();
   if (col >= r) return;
   for (int step = 0; step < r; ++step) {
     const int i = upper ? r - 1 - step : step;
-    T part = T(0);
+    const int jo = i >> 5, lo = i & 31;
+    T xi = x[0];
 #pragma unroll
-    for (int j = 0; j < kMaxRank / 32; ++j) {
+    for (int j = 1; j < KJ; ++j)
+      if (jo == j) xi = x[j];
+    xi = __shfl_sync(full, xi * rinv[i], lo);
+#pragma unroll
+    for (int j = 0; j < KJ; ++j) {
       const int k = lane + 32 * j;
-      if (!upper) {
-        if (k < i) part += sL[i * ld + k] * x[k];
-      } else {
-        if (k > i && k < r) part += sL[k * ld + i] * x[k];
-      }
+      if (k == i) x[j] = xi;
+      else if (!upper ? (k > i && k < r) : (k < i)) x[j] -= (upper ? sL[i * ld + k] : sL[k * ld + i]) * xi;
     }
-    part = warp_sum(part);
-    if (lane == 0) x[i] = (x[i] - part) * rinv[i];
-    __syncwarp();
   }
-  for (int i = lane; i < r; i += 32) X[(int64_t)i * r + col] = (double)x[i];
+#pragma unroll
+  for (int j = 0; j < KJ; ++j) {
+    const int k = lane + 32 * j;
+    if (k < r) X[(int64_t)k * r + col] = (double)x[j];
+  }
 }
 
 template <typename T = double>
 static cudaError_t trsm(const double* L, int r, const double* R, int trans, int upper, double* X, cudaStream_t st) {
-  const size_t smem = ((size_t)r * (r + 1) + r + (size_t)kTrsmWarps * r) * sizeof(T);
+  const size_t smem = ((size_t)r * (r + 1) + r) * sizeof(T);
   k_trsm<T><<<(r + kTrsmWarps - 1) / kTrsmWarps, 32 * kTrsmWarps, smem, st>>>(L, r, R, trans, upper, X);
   return cudaGetLastError();
 }

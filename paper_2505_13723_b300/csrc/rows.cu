@@ -441,8 +441,13 @@ cudaError_t launch_reduce(const float* part, int nsplit, int64_t m, int na, int 
                           int64_t lda, float gamma, const float* B, const int* bidx, int64_t ldb,
                           double* blocksq, cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
-  k_reduce<<<kReduceBlocks, 256, 0, st>>>(part, nsplit, m, na, coff, s, out, ldo, beta, A, aidx,
-                                          lda, gamma, B, bidx, ldb, blocksq);
+  // kReduceBlocks blocks when the per-block sums of squares are wanted (their
+  // count is fixed); otherwise about one element per thread, for more loads in
+  // flight
+  const int blocks = blocksq ? kReduceBlocks
+                             : (int)std::max<int64_t>(1, std::min<int64_t>((m * s + 255) / 256, 148 * 16));
+  k_reduce<<<blocks, 256, 0, st>>>(part, nsplit, m, na, coff, s, out, ldo, beta, A, aidx, lda, gamma, B, bidx,
+                                   ldb, blocksq);
   return cudaGetLastError();
 }
 
