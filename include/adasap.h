@@ -173,6 +173,18 @@ adasap_status adasap_measure_pipes(double* out, int count, void* stream);
 adasap_status adasap_check_device(adasap_ctx* ctx, int* code, void* stream);
 adasap_status adasap_wait_selftest(adasap_ctx* ctx, uint64_t limit_ns, void* stream);
 
+/* Work schedule of a single-RHS tensor-core block-row product (host only, no
+ * device needed; the paper has no counterpart: Step I of Alg. 2 and the K_BB a
+ * products of Alg. 5 are split over the CTAs of one GPU).  For an m x ncols
+ * product on min(resident CTAs, max_ctas) CTAs (max_ctas <= 0: all) it returns
+ * in *nsplit the partial slots per row and in *flat 1 when the launch takes
+ * equal tile runs per CTA (else (row tile x column split) items).  For the
+ * equal runs it walks every CTA's runs through the kernel's own decoding and
+ * returns ADASAP_ENUMERIC if a tile would not be covered exactly once or a
+ * (row, slot) not written exactly once; ADASAP_EINVAL for m, ncols < 1 or a
+ * NULL pointer. */
+adasap_status adasap_schedule_check(int64_t m, int64_t ncols, int max_ctas, int* nsplit, int* flat);
+
 /* ADASAP (Alg. 2 with Alg. 4, 5, 6 and the stabilised Woodbury apply of App. C.2).
  * Y (n x s) and W (n x s) are host or device.  W holds W_0 on entry and the
  * returned iterate W_T on exit.  1 <= s <= 128.  Randomness (B, Omega, v0) is

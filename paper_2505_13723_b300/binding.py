@@ -38,7 +38,7 @@ SYMBOLS = ["adasap_default_opts", "adasap_status_string", "adasap_last_error", "
            "adasap_kernel_rows_noalloc", "adasap_measure_pipes", "adasap_residual",
            "adasap_solve_batched", "adasap_rf_prior", "adasap_pathwise", "adasap_rmse_nll",
            "adasap_check_device", "adasap_wait_selftest", "adasap_solver_get_state",
-           "adasap_solver_set_state"]
+           "adasap_solver_set_state", "adasap_schedule_check"]
 
 
 class Opts(ctypes.Structure):
@@ -110,6 +110,9 @@ _lib.adasap_check_device.argtypes = [_P, ctypes.POINTER(ctypes.c_int), _P]
 _lib.adasap_check_device.restype = ctypes.c_int
 _lib.adasap_wait_selftest.argtypes = [_P, ctypes.c_uint64, _P]
 _lib.adasap_wait_selftest.restype = ctypes.c_int
+_lib.adasap_schedule_check.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int)]
+_lib.adasap_schedule_check.restype = ctypes.c_int
 _lib.adasap_solver_get_state.argtypes = [_P, _P, _P, _P, ctypes.POINTER(_I64), _P]
 _lib.adasap_solver_get_state.restype = ctypes.c_int
 _lib.adasap_solver_set_state.argtypes = [_P, _P, _P, _P, _I64, _P]
@@ -442,6 +445,14 @@ def rmse_nll(mean, samples, ytest, noise, stream=None):
                                 samples.stride(0), s, ctypes.c_void_p(ytest.data_ptr()), m, float(noise),
                                 ctypes.byref(rm), ctypes.byref(nl), _stream(stream)), "adasap_rmse_nll")
     return rm.value, nl.value
+
+
+def schedule_check(m, ncols, max_ctas=0):
+    """adasap_schedule_check (host only): (status, nsplit, flat) of the single-RHS tensor-core
+    product's work schedule; status is ADASAP_OK (0) when every tile and (row, slot) is covered once."""
+    ns, fl = ctypes.c_int(), ctypes.c_int()
+    st = _lib.adasap_schedule_check(int(m), int(ncols), int(max_ctas), ctypes.byref(ns), ctypes.byref(fl))
+    return st, ns.value, bool(fl.value)
 
 
 def measure_pipes(stream=None):

@@ -140,6 +140,8 @@ int tc_nsplit(int64_t m, int64_t ncols, int max_ctas = 0);
 int tc_flat_slots(int64_t m, int64_t ncols, int max_ctas = 0);
 // tc_flat_slots if non-zero, else tc_nsplit: the split count for launch_rows_tc.
 int tc_plan_nsplit(int64_t m, int64_t ncols, int max_ctas = 0);
+// Host walk of the flat schedule (0: consistent); see adasap_schedule_check.
+int tc_schedule_check(int64_t m, int64_t ncols, int max_ctas, int* nsplit, int* flat);
 // Split (hi, lo) column operands in the MMA layout for X' (or rows gidx of X').
 cudaError_t launch_build_tc(const float* X, const float* q, const int* gidx, int64_t n, int d, int dp, float* hi,
                             float* lo, cudaStream_t st);

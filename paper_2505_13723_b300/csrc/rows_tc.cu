@@ -9,16 +9,19 @@
 // row paired with its own column (the diagonal of K_BB / K_Bn) gets u = 0.
 //
 // CTA = 128 rows x a column range, 640 threads, persistent over (row tile,
-// column split) items:
+// column split) items, or over equal runs of tiles (the flat schedule, for
+// small products):
 //   warp 0       producer: bulk copies (cp.async.bulk, the TMA engine) of
-//                128-column operand tiles into a 4-stage shared-memory ring,
-//                and the w values of each tile into a 2-stage w buffer
-//   warp 1       owns the TMEM allocation (2 x 128 FP32 accumulator columns)
-//                and issues the MMAs from one thread (tcgen05.mma kind::tf32,
-//                M = 128, N = 128, K = 8 per instruction)
-//   warps 4..19  epilogue: warp w tcgen05.ld-s 32 rows (TMEM lane quadrant
-//                w % 4) x 32 columns of the tile, applies the RBF / Matern
-//                epilogue and contracts with w in registers
+//                128-column operand tiles into an 8-stage shared-memory ring
+//                (5 at KP = 32), and the w values of each tile, loaded two
+//                tiles ahead, into a 4-stage w buffer
+//   warp 1       owns the TMEM allocation (4 x 128 FP32 distance columns, the
+//                whole TMEM) and issues the MMAs from one thread
+//                (tcgen05.mma kind::tf32, M = 128, N = 128, K = 8 per instruction)
+//   warps 4..19  epilogue in four groups of four warps: group g takes every
+//                fourth tile (TMEM buffer g); warp w tcgen05.ld-s the 32 rows of
+//                TMEM lane quadrant w % 4, all 128 columns, applies the RBF /
+//                Matern epilogue and contracts with w in registers
 // Operands live in shared memory in the no-swizzle K-major canonical layout:
 // 8-row core groups of 16-byte K chunks (LBO = 128 B between K chunks,
 // SBO = 32 * KP B between 8-row groups).  The column operands are prebuilt in
@@ -29,6 +32,7 @@
 // products (for example the block-row products of many GP systems) in one
 // launch.
 #include <algorithm>
+#include <vector>
 
 #include "tc_ptx.cuh"
 
@@ -71,6 +75,27 @@ __device__ __forceinline__ float tc_term(float v, float w, float wl, float w3, f
   const float e = ex2_approx(-ap);
   if (KERN == ADASAP_MATERN32) return fmaf(e, fmaf(ap, wl, w), acc);
   return fmaf(e, fmaf(ap, fmaf(ap, w3, wl), w), acc);
+}
+
+// One run of the flat schedule: CTA x of G takes the flattened tiles
+// [x T / G, (x + 1) T / G) of the row-tile-major sequence of all T tiles
+// (ctiles per row tile); the run starting at fpos (< fend, the end of the
+// share) lies in row tile `rtile`, covers its column tiles [tb, te), writes
+// partial slot x - (first CTA of the row tile) -- the largest y with
+// y T / G <= rtile * ctiles -- and ends the row tile when te == ctiles.
+struct TcFlatRun {
+  int64_t rtile, tb, te, slot;
+  bool row_end;
+};
+__host__ __device__ __forceinline__ TcFlatRun tc_flat_run(int64_t x, int64_t G, int64_t T, int64_t ctiles,
+                                                          int64_t fpos, int64_t fend) {
+  TcFlatRun run;
+  run.rtile = fpos / ctiles;
+  run.tb = fpos % ctiles;
+  run.te = run.tb + (fend - fpos) < ctiles ? run.tb + (fend - fpos) : ctiles;
+  run.slot = x - ((run.rtile * ctiles + 1) * G - 1) / T;
+  run.row_end = run.te == ctiles;
+  return run;
 }
 
 // GROUPED: the items of several independent products (one TcArgs each; item
@@ -159,14 +184,13 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
     int64_t rtile, split, c0, c1;
     bool row_end = false;
     if (flat) {
-      rtile = fpos / ctiles;
-      const int64_t tb = fpos % ctiles, te = min(ctiles, tb + (fend - fpos));
-      // first CTA of the row tile: the largest y with y T / G <= rtile * ctiles
-      split = (int64_t)blockIdx.x - ((rtile * ctiles + 1) * (int64_t)gridDim.x - 1) / ftotal;
-      c0 = tb * kTcN;
-      c1 = min(a.ncols, te * kTcN);
-      row_end = te == ctiles;
-      fpos += te - tb;
+      const TcFlatRun run = tc_flat_run(blockIdx.x, gridDim.x, ftotal, ctiles, fpos, fend);
+      rtile = run.rtile;
+      split = run.slot;
+      c0 = run.tb * kTcN;
+      c1 = min(a.ncols, run.te * kTcN);
+      row_end = run.row_end;
+      fpos += run.te - run.tb;
     } else {
       rtile = li % rtiles;
       split = li / rtiles;
@@ -523,6 +547,40 @@ int tc_flat_slots(int64_t m, int64_t ncols, int max_ctas) {
 int tc_plan_nsplit(int64_t m, int64_t ncols, int max_ctas) {
   const int fs = tc_flat_slots(m, ncols, max_ctas);
   return fs > 0 ? fs : tc_nsplit(m, ncols, max_ctas);
+}
+
+// Host walk of the schedule launch_rows_tc takes for an m x ncols product on
+// min(slots, max_ctas) CTAs: with the flat schedule every tile must be covered
+// once and every (row tile, slot) written once, through the kernel's own run
+// decoding (tc_flat_run).
+int tc_schedule_check(int64_t m, int64_t ncols, int max_ctas, int* nsplit, int* flat) {
+  const int ns = tc_plan_nsplit(m, ncols, max_ctas);
+  const int fs = tc_flat_slots(m, ncols, max_ctas);
+  *nsplit = ns;
+  *flat = fs > 0 && ns == fs;
+  if (!*flat) return 0;  // items (row tile, split): item li writes slot li / rtiles of its rows
+  const int64_t rt = (m + kTcM - 1) / kTcM, ctiles = (ncols + kTcN - 1) / kTcN, T = rt * ctiles;
+  const int64_t G = (max_ctas > 0 && max_ctas < tc_slots()) ? max_ctas : tc_slots();
+  std::vector<int> tiles((size_t)T, 0), slots((size_t)(rt * ns), 0);
+  for (int64_t x = 0; x < G; ++x) {
+    int64_t fpos = x * T / G;
+    const int64_t fend = (x + 1) * T / G;
+    if (fend <= fpos) return 1;  // a CTA without tiles would leave its slot unwritten
+    while (fpos < fend) {
+      const TcFlatRun run = tc_flat_run(x, G, T, ctiles, fpos, fend);
+      if (run.slot < 0 || run.slot >= ns || run.te <= run.tb) return 2;
+      for (int64_t t = run.tb; t < run.te; ++t) ++tiles[(size_t)(run.rtile * ctiles + t)];
+      ++slots[(size_t)(run.rtile * ns + run.slot)];
+      if (run.row_end)
+        for (int64_t s2 = run.slot + 1; s2 < ns; ++s2) ++slots[(size_t)(run.rtile * ns + s2)];
+      fpos += run.te - run.tb;
+    }
+  }
+  for (int c : tiles)
+    if (c != 1) return 3;
+  for (int c : slots)
+    if (c != 1) return 4;
+  return 0;
 }
 
 template <int KERN, int KP, bool G>

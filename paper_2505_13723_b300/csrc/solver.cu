@@ -1710,6 +1710,11 @@ extern "C" adasap_status adasap_wait_selftest(adasap_ctx* c, uint64_t limit_ns, 
   return ADASAP_OK;
 }
 
+extern "C" adasap_status adasap_schedule_check(int64_t m, int64_t ncols, int max_ctas, int* nsplit, int* flat) {
+  if (m < 1 || ncols < 1 || !nsplit || !flat) return ADASAP_EINVAL;
+  return tc_schedule_check(m, ncols, max_ctas, nsplit, flat) == 0 ? ADASAP_OK : ADASAP_ENUMERIC;
+}
+
 extern "C" adasap_status adasap_solver_graph_kernels(adasap_solver* S, int* count) {
   if (!S || !count || !S->graph) return ADASAP_EINVAL;
   size_t nn = 0;
