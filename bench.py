@@ -45,7 +45,7 @@ UNIT = "Gentries/s"
 
 # DRAM bytes per kernel entry of k_rows_tc (Step I shape, s = 1), from an ncu
 # capture of the current kernel (profiles/k_rows_tc_step1_regress.md)
-TC_DRAM_BYTES_PER_ENTRY = (36.944896e6 + 7.936e3) / (10000 * 262144)
+TC_DRAM_BYTES_PER_ENTRY = (36.943872e6 + 13.312e3) / (10000 * 262144)
 
 
 def parse():
