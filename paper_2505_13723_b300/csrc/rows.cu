@@ -3,7 +3,7 @@
 //
 // This is Step I of Alg. 2 (K_Bn W, which App. C.1's ColDistMatMat splits by
 // columns over GPUs -- here the column split is over CTAs of one GPU with a
-// deterministic FP64 second-stage reduce) and Step II (the Nystrom sketch
+// deterministic double-float second-stage reduce) and Step II (the Nystrom sketch
 // K_BB Omega, App. C.1 RowDistMatMat), plus the K_BB v products of Alg. 5,
 // the posterior mean (Sec. 2) and the hyperparameter adjoint (App. D.1).
 //
