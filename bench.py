@@ -30,11 +30,7 @@ import subprocess
 import sys
 import time
 
-# the CPU oracle legs run on one host thread (BLAS included); set before numpy loads
-for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-    os.environ.setdefault(_v, "1")
-
-import numpy as np  # noqa: E402
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -43,8 +39,8 @@ METRIC = "ADASAP s to rel-resid 1e-3 (mixed vs FP32); kernel-row Gentries/s, % r
 UNIT = "Gentries/s"
 
 
-# DRAM bytes per kernel entry of k_rows_tc (Step I shape, s = 1), from an ncu
-# capture of the current kernel (profiles/k_rows_tc_step1_regress.md)
+# DRAM bytes per kernel entry of k_rows_tc (Step I shape, s = 1): dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu-captured launch at 10,000 x 262,144 entries, Matern-3/2
 TC_DRAM_BYTES_PER_ENTRY = (36.943872e6 + 13.312e3) / (10000 * 262144)
 
 
@@ -143,24 +139,46 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_rows_rate(P, target_s=10.0, max_rows=None):
-    """Entries/s of the oracle's block-row product (FP64 NumPy, one thread) on sampled rows."""
+def host_cores():
+    """Host cores this process may run on (its CPU affinity set)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_rows_rate(P, target_s=10.0, max_rows=None, threads=None):
+    """Entries/s of the oracle's block-row product (FP64 NumPy) on sampled rows.
+
+    The sampled rows are cut into one group per thread and each thread runs the
+    oracle's kernel_rows on its group (NumPy releases the interpreter lock in the
+    elementwise work, so the threads run on separate cores); BLAS is held to one
+    thread inside each so that the host cores are not oversubscribed.
+    Returns (entries/s, rows, seconds, threads)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from threadpoolctl import threadpool_limits
+
     from oracle import kernels as OK
     X = P.X.astype(np.float64)
     W = P.Y.astype(np.float64)
+    n = X.shape[0]
+    threads = max(1, min(threads or host_cores(), 64))
     g = np.random.default_rng(0)
-    rows = g.choice(X.shape[0], size=2, replace=False)
-    t0 = time.perf_counter()
-    OK.kernel_rows(X, rows, W, P.kernel, P.ell, P.sigma2)
-    per_row = (time.perf_counter() - t0) / 2
-    k = max(1, int(target_s / max(per_row, 1e-6)))
-    if max_rows:
-        k = min(k, max_rows)
-    rows = g.choice(X.shape[0], size=k, replace=False)
-    t0 = time.perf_counter()
-    OK.kernel_rows(X, rows, W, P.kernel, P.ell, P.sigma2)
-    dt = time.perf_counter() - t0
-    return k * X.shape[0] / dt, k, dt
+    with threadpool_limits(1), ThreadPoolExecutor(threads) as pool:
+        probe = g.choice(n, size=threads, replace=False)
+        t0 = time.perf_counter()
+        list(pool.map(lambda r: OK.kernel_rows(X, [r], W, P.kernel, P.ell, P.sigma2), probe))
+        per_row = (time.perf_counter() - t0) / threads     # wall time per row with all threads busy
+        k = max(threads, int(target_s / max(per_row, 1e-6)))
+        if max_rows:
+            k = max(1, min(k, max_rows))
+        rows = g.choice(n, size=k, replace=False)
+        groups = [grp for grp in np.array_split(rows, min(threads, k)) if len(grp)]
+        t0 = time.perf_counter()
+        list(pool.map(lambda grp: OK.kernel_rows(X, grp, W, P.kernel, P.ell, P.sigma2), groups))
+        dt = time.perf_counter() - t0
+    return k * n / dt, k, dt, len(groups)
 
 
 def run_reference(args, rank, world):
@@ -170,10 +188,10 @@ def run_reference(args, rank, world):
     n = P.X.shape[0]
     for _ in range(args.warmup):
         oracle_rows_rate(P, target_s=0.5, max_rows=2)
-    rates, tot_rows, tot_t = [], 0, 0.0
+    rates, tot_rows, tot_t, used = [], 0, 0.0, 1
     t_all = time.perf_counter()
     for _ in range(args.steps):
-        rate, k, dt = oracle_rows_rate(P, target_s=5.0)
+        rate, k, dt, used = oracle_rows_rate(P, target_s=5.0)
         rates.append(rate)
         tot_rows += k
         tot_t += dt
@@ -182,13 +200,57 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(P),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
                              "sample": "FP64 NumPy block-row product K(X_B, X) w on %d sampled rows x n=%d per "
-                                       "step (%.1f s of host work per step)" % (tot_rows // args.steps, n,
-                                                                                 tot_t / args.steps)},
+                                       "step (%.1f s per step), rows split over %d threads (host affinity set: "
+                                       "%d cores)" % (tot_rows // args.steps, n, tot_t / args.steps, used,
+                                                      host_cores())},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t_all}
     print(json.dumps(line), flush=True)
+
+
+# TF32 dense tensor rate relative to BF16 (nominal dense figures of this GPU: 1.1 and 2.25 PFLOP/s)
+TF32_PER_BF16 = 1.1 / 2.25
+
+
+def mrhs_roofline(entries, d, s, ms, pk, pk_src, pipes, sms, mhz):
+    """Roofline of the multi-RHS block-row product (k_rows_tc_mrhs, RBF) at s right-hand sides.
+
+    Algorithmic work per kernel entry: 2 d flops of distance and 2 s flops of contraction,
+    both on the tensor pipe, plus one ex2 on the special-function pipe.  The tensor peak is
+    TF32: the measured BF16 dense rate times the nominal TF32 / BF16 ratio.  The kernel
+    executes more than the algorithmic flops: three TF32 passes (hi/lo split, FP32
+    accuracy) of 2 (KP + s_pad) flops per entry with KP = 16 or 32 and s_pad = s rounded
+    up to 16, or one pass in the single-pass TF32 mode; both are reported."""
+    kp = 16 if d + 2 <= 16 else 32
+    s_pad = (s + 15) // 16 * 16
+    alg = 2.0 * d + 2.0 * s
+    tf32_peak = pk["bf16_tflops"] * TF32_PER_BF16 * 1e12
+    sfu_peak = sms * mhz * 1e6 * pipes["ex2"]
+    t = ms["tf32x3"] * 1e-3
+    out = {"bound": "tensor", "unit": "TFLOP/s",
+           "achieved": alg * entries / t / 1e12, "peak": tf32_peak / 1e12,
+           "frac": alg * entries / t / tf32_peak, "traffic": None,
+           "kernel": "k_rows_tc_mrhs (tcgen05 TF32x3 distances and contraction), b x n = %d entries, s = %d"
+                     % (entries, s),
+           "ms_per_launch": ms["tf32x3"],
+           "flops_per_entry_algorithmic": alg,
+           "peak_basis": "TF32 dense = %s BF16 burst %.1f TFLOP/s x %.3f (nominal TF32 / BF16)"
+                         % (pk_src, pk["bf16_tflops"], TF32_PER_BF16),
+           "executed_tf32x3": {"flops_per_entry": 3 * 2.0 * (kp + s_pad),
+                               "tflops": 3 * 2.0 * (kp + s_pad) * entries / t / 1e12,
+                               "frac_of_tf32_peak": 3 * 2.0 * (kp + s_pad) * entries / t / tf32_peak},
+           "special_function_pipe": {"entries_per_s": entries / t, "peak_entries_per_s": sfu_peak,
+                                     "frac": entries / t / sfu_peak,
+                                     "basis": "1 ex2 per entry at %.1f per SM per clock (adasap_measure_pipes)"
+                                              % pipes["ex2"]}}
+    if "tf32" in ms:
+        t1 = ms["tf32"] * 1e-3
+        out["single_pass_tf32"] = {"ms_per_launch": ms["tf32"],
+                                   "flops_per_entry_executed": 2.0 * (3 * kp + s_pad),
+                                   "frac_of_tf32_peak_executed": 2.0 * (3 * kp + s_pad) * entries / t1 / tf32_peak}
+    return out
 
 
 def config_dict(P):
@@ -364,8 +426,11 @@ def run_ours(args, rank, world, dist):
             topts = lib.default_opts(n, b=b, r=r, seed=2, tol=1e-3, max_iters=args.tol_iters, check_every=50,
                                      check_rows=20000)
             W, st, stc = ctx.solve(Yd, opts=topts)
-            tol_run[name] = {"seconds": st["seconds"], "iters": st["iters"], "rel_resid": st["rel_resid"],
-                             "reached": bool(st["rel_resid"] <= 1e-3), "resid_rows_sampled": 20000}
+            # the stop was taken on 20,000 sampled rows; confirm on all n rows (adasap_residual)
+            exact = ctx.residual(Yd, W)
+            tol_run[name] = {"seconds": st["seconds"], "iters": st["iters"],
+                             "rel_resid_sampled": st["rel_resid"], "resid_rows_sampled": 20000,
+                             "rel_resid_exact": exact, "reached": bool(exact <= 1e-3)}
         ctx.set_precision(default_prec)
 
     # ---- many right-hand sides: the multirhs workload (n = 2^18, s = 64), device time per
@@ -395,12 +460,33 @@ def run_ours(args, rank, world, dist):
         mixed_batched = per_iter(lib.PREC_TF32X3, Yq)
         tf32_batched = per_iter(lib.PREC_TF32, Yq)
         fp32_single = per_iter(lib.PREC_FP32, Yq[:, :1].contiguous())
+        # the s = 64 Step I launch alone (b x n entries against 64 right-hand sides)
+        nq, dq = Q.X.shape
+        gq = np.random.default_rng(6)
+        Bq = torch.from_numpy(gq.choice(nq, size=Q.b, replace=False)).to(dev)
+        m_ms = {}
+        for name, prec in (("tf32x3", lib.PREC_TF32X3), ("tf32", lib.PREC_TF32)):
+            cq.set_precision(prec)
+            for _ in range(3):
+                cq.kernel_rows(Bq, Yq)
+            es = [torch.cuda.Event(enable_timing=True) for _ in range(args.kernel_launches)]
+            ee = [torch.cuda.Event(enable_timing=True) for _ in range(args.kernel_launches)]
+            torch.cuda.synchronize()
+            for i in range(args.kernel_launches):
+                flush.zero_()
+                es[i].record(stream)
+                cq.kernel_rows(Bq, Yq)
+                ee[i].record(stream)
+            torch.cuda.synchronize()
+            m_ms[name] = statistics.mean(a.elapsed_time(e) for a, e in zip(es, ee))
+        cq.set_precision(lib.PREC_TF32X3)
         cq.close()
         multi = {"workload": "multirhs: n=262144, d=16, X~N(0,I), RBF ell=2, lambda=1e-2, b=4096, r=64, s=64",
                  "ms_per_iteration_mixed_batched_s64": mixed_batched,
                  "ms_per_iteration_tf32_single_pass_contraction_s64": tf32_batched,
                  "ms_per_iteration_fp32_single_rhs": fp32_single,
-                 "speedup_vs_64_fp32_single_rhs_solves": 64.0 * fp32_single / mixed_batched}
+                 "speedup_vs_64_fp32_single_rhs_solves": 64.0 * fp32_single / mixed_batched,
+                 "roofline": mrhs_roofline(Q.b * nq, dq, Q.Y.shape[1], m_ms, pk, pk_src, pipes, sms, mhz)}
 
     # ---- the uneven batch: 48 independent Matern-5/2 systems (n log-uniform in [4096, 65536],
     # b = n/50, r = 50) iterated together by adasap_solve_batched, against the same systems
@@ -518,12 +604,13 @@ def run_ours(args, rank, world, dist):
     cpu = None
     if not args.no_cpu_baseline:
         try:
-            rate, k, dt = oracle_rows_rate(P, target_s=12.0)
-            cpu = {"value": rate / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": "FP64 NumPy block-row product K(X_B, X) w, %d sampled rows x n=%d (%.1f s), one "
-                             "thread" % (k, n, dt)}
+            rate, k, dt, used = oracle_rows_rate(P, target_s=12.0)
+            cpu = {"value": rate / 1e9, "unit": UNIT, "cores": used, "kind": "oracle",
+                   "sample": "FP64 NumPy block-row product K(X_B, X) w, %d sampled rows x n=%d (%.1f s), rows "
+                             "split over %d threads (host affinity set: %d cores)" % (k, n, dt, used,
+                                                                                       host_cores())}
         except Exception as ex:  # report, do not lose the GPU line
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": repr(ex)}
+            cpu = {"value": None, "unit": UNIT, "cores": host_cores(), "kind": "oracle", "error": repr(ex)}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -532,9 +619,9 @@ def run_ours(args, rank, world, dist):
             "roofline": {"bound": "alu", "achieved": k_rate / 1e9, "peak": peak_entries / 1e9,
                          "unit": "Gentries/s", "frac": k_rate / peak_entries,
                          "traffic": (TC_DRAM_BYTES_PER_ENTRY * b * n if default_prec == lib.PREC_TF32X3 else None),
-                         "traffic_basis": ("dram__bytes_read.sum + dram__bytes_write.sum of one k_rows_tc launch "
-                                           "at 10,000 x 262,144 entries (profiles/k_rows_tc_step1_regress.md), "
-                                           "scaled by the entries of this launch"),
+                         "traffic_basis": ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu-captured "
+                                           "k_rows_tc launch at 10,000 x 262,144 entries, scaled by the entries "
+                                           "of this launch"),
                          "kernel": ("k_rows_tc (tcgen05 TF32x3 distances)" if default_prec == lib.PREC_TF32X3
                                     else "k_rows_narrow (FP32)")
                                    + " Step I block-row product, b=%d rows x n=%d" % (b, n),

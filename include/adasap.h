@@ -135,17 +135,28 @@ adasap_status adasap_kernel_rows(adasap_ctx* ctx, const int64_t* B, int64_t b, c
  * memory while they run -- for example code inside a memory-pool-less runtime,
  * an allocation-free real-time loop, or a process whose device memory is
  * already fully reserved.  (The paper has no counterpart: this is a service of
- * this library.)  Same arguments, arithmetic and result as adasap_kernel_rows,
- * but the call allocates nothing: its scratch (an int32 copy of B and the
- * per-split partial sums) is a static device array of 8 MiB that every GPU
- * loading this library holds until the process exits.
- *   - The scratch must fit: about 4 * b * (1 + s * k) bytes, where k, the
- *     number of column splits the library chooses, is at most a few tens (for
- *     b = 10^4, s = 1 about 0.7 MiB).  Larger sizes return ADASAP_EINVAL before
- *     any GPU work, and adasap_last_error() says how many bytes were needed.
- *   - The context's device must be current.  The first call on a device looks
- *     up the array's device address (cudaGetSymbolAddress); make that first
- *     call before any stream capture.
+ * this library.)  Same arguments and product as adasap_kernel_rows, but the
+ * call allocates nothing: its scratch (an int32 copy of B and the per-split
+ * partial sums) is a static device array of 8 MiB that every GPU loading this
+ * library holds until the process exits.
+ *   - Arithmetic: for s = 1, and for any s in ADASAP_PREC_FP32, the same kernel
+ *     and result as adasap_kernel_rows.  For s >= 2 in a tensor-core precision
+ *     (ADASAP_PREC_TF32X3, ADASAP_PREC_TF32) the product runs in plain FP32 on
+ *     the CUDA cores (the multi-RHS tensor-core kernel needs an operand copy of
+ *     W that the array does not hold), so the result agrees with
+ *     adasap_kernel_rows within that precision's tolerance, not bit for bit.
+ *   - The scratch must fit: 4 * b bytes for the index copy plus 4 * b * s * k
+ *     for the partials, where k, the number of column splits the library
+ *     chooses, GROWS as b shrinks (it aims at a fixed number of work items, so
+ *     b * k stays roughly constant): b * k is at most about 1.2e6 on the
+ *     tensor-core path (s = 1) and about 2368 * 64 on the CUDA-core path, so
+ *     the partials take at most about 4.9 MB for s = 1 and about 0.61 MB per
+ *     right-hand side otherwise.  Sizes that do not fit return ADASAP_EINVAL
+ *     before any GPU work, and adasap_last_error() gives the bytes needed.
+ *   - The context's device must be current, and its index below 64 (the
+ *     per-device address table).  The first call on a device looks up the
+ *     array's device address (cudaGetSymbolAddress); make that first call
+ *     before any stream capture.
  *   - All calls share the one array and it keeps the last call's contents;
  *     nothing in it needs clearing, but calls that overlap on the GPU (on
  *     different streams, or from different threads) race on it: serialise them. */

@@ -1,5 +1,7 @@
 // Step III and IV of Alg. 2 on the GPU:
-//   - Gram matrices of b x r panels (FP32 products, FP64 accumulation)
+//   - Gram matrices of b x r panels (FP32 products, or error-free split
+//     products for the Gram of M Omega, accumulated in double-float on the
+//     FP32 pipes)
 //   - the randomized Nystrom factorisation of Alg. 4 on its r x r core
 //     (FP64 Cholesky and triangular solves; eigenvectors by FP32 cyclic
 //     Jacobi with FP64 Rayleigh-quotient eigenvalues)

@@ -1773,7 +1773,13 @@ extern "C" adasap_status adasap_kernel_rows_noalloc(adasap_ctx* c, const int64_t
   if (!c || !B || !W || !out || b < 1 || b >= (1LL << 31) || s < 1 || s > kMaxRhs) return ADASAP_EINVAL;
   int dev = -1;
   CT(cudaGetDevice(&dev));
-  if (dev != c->device || dev < 0 || dev >= kNoallocMaxDevices) {
+  if (dev < 0 || dev >= kNoallocMaxDevices) {
+    g_last_error = "adasap_kernel_rows_noalloc: device index " + std::to_string(dev) +
+                   " is beyond the per-device address table (devices 0.." + std::to_string(kNoallocMaxDevices - 1) +
+                   ")";
+    return ADASAP_EINVAL;
+  }
+  if (dev != c->device) {
     g_last_error = "adasap_kernel_rows_noalloc: the context's device must be the current device";
     return ADASAP_EINVAL;
   }

@@ -4,8 +4,9 @@ one graph, grouped tensor-core launches) against the FP64 oracle.
 Each system runs Alg. 2 with its own device randomness (Philox keyed by its
 seed); the oracle replays the same counter-based draws.  The grouped launch
 changes only the column split of the Step I and K_BB a sums (rounding order),
-so the per-system tolerance is the one of the single-system parity tests:
-tol = max(1e-4, (2N + 1) * 4 * 2^-23 * b * sigma2 / min_t rho_t).
+so the per-system tolerance is the one of the single-system parity tests
+(tests/_parity.py): 10x the oracle's own sensitivity to FP32-level rounding of
+X and Omega, capped by max(1e-4, (2N + 1) * 4 * 2^-23 * b * sigma2 / min_t rho_t).
 """
 
 import numpy as np
@@ -17,6 +18,8 @@ from oracle import gp
 from oracle import rng as OR
 from paper_2505_13723_b300 import synth
 
+import _parity as PT
+
 pytestmark = pytest.mark.gpu
 
 
@@ -24,12 +27,6 @@ def _rel(a, b):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-
-
-def _tol_eta(rec, b, sigma2, power_iters=10):
-    rhos = [x["rho"] for x in rec if x["rho"] is not None]
-    base = 1e-4 if not rhos else max(1e-4, 4 * 2.0 ** -23 * b * sigma2 / min(rhos))
-    return max(1e-4, (2 * power_iters + 1) * base)
 
 
 def _systems(count, nmin, nmax, seed, lam=1e-2):
@@ -43,13 +40,21 @@ def _systems(count, nmin, nmax, seed, lam=1e-2):
     return out
 
 
-def _oracle(P, T, seed, precond="nystrom"):
+def _oracle(P, T, seed, precond="nystrom", Y=None):
+    """The oracle's W_T and its sensitivity (tests/_parity.py) for one system."""
     n = P.X.shape[0]
-    rec = []
-    W = OA.adasap(P.X.astype(np.float64), P.Y.astype(np.float64), P.kernel, P.ell, P.sigma2, P.lam, P.b,
-                  P.r, T, OR.philox_schedule(n, P.b, P.r, seed=seed),
-                  precond=precond, record=rec)
-    return W, rec
+    Yd = (P.Y if Y is None else Y).astype(np.float64)
+
+    def run(Xp, sched):
+        rec = []
+        W = OA.adasap(Xp, Yd, P.kernel, P.ell, P.sigma2, P.lam, P.b, P.r, T, sched, precond=precond, record=rec)
+        return W, rec
+
+    return PT.sensitivity(run, P.X, OR.philox_schedule(n, P.b, P.r, seed=seed), seed=seed)
+
+
+def _check_w(name, W, Wref, rec, sens, P):
+    PT.check(name, [("W", _rel(W, Wref), sens["W"], PT.a_priori_cap(rec, P.b, P.sigma2))])
 
 
 def test_batched_uneven_systems_match_oracle(lib):
@@ -64,12 +69,12 @@ def test_batched_uneven_systems_match_oracle(lib):
     assert status == 0
     for k, (P, ctx, W, st) in enumerate(zip(Ps, ctxs, Ws, stats)):
         assert st["iters"] == T and st["resid_exact"] == 1
-        Wref, rec = _oracle(P, T, 100 + k)
-        tol = _tol_eta(rec, P.b, P.sigma2)
-        assert _rel(W.cpu().numpy(), Wref) < tol, (k, P.X.shape)
+        Wref, rec, sens = _oracle(P, T, 100 + k)
+        _check_w("batched uneven k=%d" % k, W.cpu().numpy(), Wref, rec, sens, P)
         # same system alone (same seed): equal up to the rounding order of the split sums
         Wone, _, _ = ctx.solve(torch.from_numpy(P.Y).cuda(), opts=opts[k])
-        assert _rel(W.cpu().numpy(), Wone.cpu().numpy()) < tol
+        PT.check("batched vs alone k=%d" % k, [("W", _rel(W.cpu().numpy(), Wone.cpu().numpy()), sens["W"],
+                                                PT.a_priori_cap(rec, P.b, P.sigma2))])
         # the reported residual is the exact one of the returned W
         ref = gp.rel_residual(P.X.astype(np.float64), W.cpu().numpy(), P.Y, P.kernel, P.ell, P.sigma2, P.lam)
         assert abs(st["rel_resid"] - ref) <= 1e-3 * ref
@@ -92,8 +97,8 @@ def test_batched_mixed_members(lib):
     Ws, stats, status = lib.solve_batched(ctxs, [P.Y for P in Ps], opts=opts)
     assert status == 0 and all(isinstance(W, np.ndarray) for W in Ws)
     for k, (P, W) in enumerate(zip(Ps, Ws)):
-        Wref, rec = _oracle(P, T, 200 + k, precond="identity" if k == 3 else "nystrom")
-        assert _rel(W, Wref) < _tol_eta(rec, P.b, P.sigma2), k
+        Wref, rec, sens = _oracle(P, T, 200 + k, precond="identity" if k == 3 else "nystrom")
+        _check_w("batched mixed k=%d" % k, W, Wref, rec, sens, P)
 
 
 def test_batched_systems_leave_at_their_tolerance(lib):
@@ -145,11 +150,8 @@ def test_batched_multi_rhs_members(lib):
     Ws, stats, status = lib.solve_batched(ctxs, [torch.from_numpy(Y).cuda() for Y in Ys], opts=opts)
     assert status == 0
     for k, (P, Y, W) in enumerate(zip(Ps, Ys, Ws)):
-        n = P.X.shape[0]
-        rec = []
-        Wref = OA.adasap(P.X.astype(np.float64), Y.astype(np.float64), P.kernel, P.ell, P.sigma2, P.lam, P.b, P.r,
-                         T, OR.philox_schedule(n, P.b, P.r, seed=500 + k), record=rec)
-        assert _rel(W.cpu().numpy(), Wref) < _tol_eta(rec, P.b, P.sigma2), k
+        Wref, rec, sens = _oracle(P, T, 500 + k, Y=Y)
+        _check_w("batched s=2 k=%d" % k, W.cpu().numpy(), Wref, rec, sens, P)
 
 
 def test_batched_bo_workload_full_size(lib):
@@ -166,8 +168,5 @@ def test_batched_bo_workload_full_size(lib):
     assert all(st["iters"] == T and np.isfinite(st["rel_resid"]) for st in stats)
     for k in np.argsort([P.X.shape[0] for P in Ps])[:2]:
         P = Ps[k]
-        n = P.X.shape[0]
-        rec = []
-        Wref = OA.adasap(P.X.astype(np.float64), P.Y.astype(np.float64), P.kernel, P.ell, P.sigma2, P.lam, P.b,
-                         P.r, T, OR.philox_schedule(n, P.b, P.r, seed=40 + int(k)), record=rec)
-        assert _rel(Ws[k].cpu().numpy(), Wref) < _tol_eta(rec, P.b, P.sigma2), (k, n)
+        Wref, rec, sens = _oracle(P, T, 40 + int(k))
+        _check_w("bo full-size k=%d n=%d" % (k, P.X.shape[0]), Ws[k].cpu().numpy(), Wref, rec, sens, P)

@@ -264,6 +264,32 @@ def test_hypergrad_at_16384_against_finite_differences(lib):
     assert abs(d_s2 - fd_s2) <= 1e-4 * abs(fd_s2)
 
 
+def test_hypergrad_at_16384_against_oracle_on_sampled_rows(lib):
+    """The adjoint at n = 16,384 (BO-shaped data, Matern-5/2, s = 2) against the oracle's
+    hypergradient: G is non-zero on 300 sampled rows only, so the oracle's sums
+    sum_i G_i (dK/dell W)_i and sum_i G_i (K W)_i / sigma2 need those 300 kernel rows,
+    while the GPU's adjoint still runs over all n x n entries (the zero rows add
+    nothing).  Held to 1e-5 of the same sums with absolute values."""
+    g = np.random.default_rng(19)
+    n, d, s = 16384, 8, 2
+    X = g.uniform(-1, 1, (n, d)).astype(np.float32)
+    W = g.standard_normal((n, s)).astype(np.float32)
+    G = np.zeros((n, s), np.float32)
+    rows = np.sort(g.choice(n, size=300, replace=False))
+    G[rows] = g.standard_normal((300, s))
+    ell, s2, kern = 0.6, 1.3, 2
+    ctx = lib.Context(X, kern, ell, s2, 1e-3)
+    d_ell, d_s2 = ctx.hypergrad(torch.from_numpy(W).cuda(), torch.from_numpy(G).cuda())
+    Xd, Wd, Gd = X.astype(np.float64), W.astype(np.float64), G[rows].astype(np.float64)
+    dKW = OK.kernel_apply(Xd[rows], Xd, Wd, kern, ell, s2, deriv=True)
+    KW = OK.kernel_apply(Xd[rows], Xd, Wd, kern, ell, s2)
+    r_ell, r_s2 = float(np.sum(Gd * dKW)), float(np.sum(Gd * KW) / s2)
+    a_ell = float(np.sum(np.abs(Gd) * OK.kernel_apply(Xd[rows], Xd, np.abs(Wd), kern, ell, s2, deriv=True)))
+    a_s2 = float(np.sum(np.abs(Gd) * OK.kernel_apply(Xd[rows], Xd, np.abs(Wd), kern, ell, s2)) / s2)
+    assert abs(d_ell - r_ell) <= 1e-5 * a_ell, (d_ell, r_ell, a_ell)
+    assert abs(d_s2 - r_s2) <= 1e-5 * a_s2, (d_s2, r_s2, a_s2)
+
+
 def test_autograd_function_gradients(lib):
     X, W = _data(800, 4, 2, seed=10)
     ctx = lib.Context(X, 1, 0.7, 1.2, 1e-2)

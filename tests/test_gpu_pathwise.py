@@ -6,6 +6,10 @@ Tolerance of the prior draws.  Each feature term is theta * cos(arg) with
 cosine one ulp, and the q-term FP32 sum a relative error of at most about
 q * 2^-24 of the sum of absolute terms (recursive summation).  So each entry is
 held to  (q * 2^-24 + 4e-7 * (1 + A)) * sqrt(2 sigma2 / q) * sum_l |theta_l|.
+
+The posterior samples after a few ADASAP iterations are held to 10x the
+oracle's own sensitivity to FP32-level rounding of X and Omega
+(tests/_parity.py), capped by the solver tests' a-priori bound.
 """
 
 import numpy as np
@@ -18,6 +22,8 @@ from oracle import kernels as OK
 from oracle import pathwise as PW
 from oracle import rng as OR
 from paper_2505_13723_b300 import synth
+
+import _parity as PT
 
 pytestmark = pytest.mark.gpu
 
@@ -62,22 +68,30 @@ def _pathwise_case(lib, P, ns, T, seed, kern=None, prec=None):
     y = P.Y[:, 0].copy()
     opts = lib.default_opts(n, b=P.b, r=P.r, max_iters=T, check_every=0, seed=seed)
     out, W, st, status = ctx.pathwise(*_cuda(y, P.Xtest, z, u, phase, theta, zeta), opts=opts)
-    Xd, Xt = P.X.astype(np.float64), P.Xtest.astype(np.float64)
-    FX = PW.rf_prior(Xd, z, u, phase, theta, kern, P.ell, P.sigma2)
-    Fs = PW.rf_prior(Xt, z, u, phase, theta, kern, P.ell, P.sigma2)
-    R = np.concatenate([y.astype(np.float64)[:, None], PW.pathwise_rhs(y, FX, zeta)], axis=1)
-    rec = []
-    Wref = OA.adasap(Xd, R, kern, P.ell, P.sigma2, P.lam, P.b, P.r, T, OR.philox_schedule(n, P.b, P.r, seed=seed),
-                     record=rec)
-    out_ref = np.concatenate([gp.posterior_mean(Xt, Xd, Wref[:, :1], kern, P.ell, P.sigma2),
-                              PW.pathwise_samples(Xt, Xd, Wref[:, 1:], Fs, kern, P.ell, P.sigma2)], axis=1)
-    return out.cpu().numpy(), W.cpu().numpy(), out_ref, Wref, rec, status
+    Xt = P.Xtest.astype(np.float64)
 
+    def run(Xd, sched):
+        FX = PW.rf_prior(Xd, z, u, phase, theta, kern, P.ell, P.sigma2)
+        Fs = PW.rf_prior(Xt, z, u, phase, theta, kern, P.ell, P.sigma2)
+        R = np.concatenate([y.astype(np.float64)[:, None], PW.pathwise_rhs(y, FX, zeta)], axis=1)
+        rec = []
+        Wref = OA.adasap(Xd, R, kern, P.ell, P.sigma2, P.lam, P.b, P.r, T, sched, record=rec)
+        out_ref = np.concatenate([gp.posterior_mean(Xt, Xd, Wref[:, :1], kern, P.ell, P.sigma2),
+                                  PW.pathwise_samples(Xt, Xd, Wref[:, 1:], Fs, kern, P.ell, P.sigma2)], axis=1)
+        # W and the samples together, so that the sensitivity covers both
+        return (Wref, out_ref), rec
 
-def _tol_eta(rec, b, sigma2, power_iters=10):
-    rhos = [x["rho"] for x in rec if x["rho"] is not None]
-    base = max(1e-4, 4 * 2.0 ** -23 * b * sigma2 / min(rhos))
-    return max(1e-4, (2 * power_iters + 1) * base)
+    sens_all = {}
+
+    def run_flat(Xd, sched):
+        (Wr, outr), rec = run(Xd, sched)
+        sens_all.setdefault("runs", []).append((Wr, outr))
+        return np.concatenate([Wr.ravel(), outr.ravel()]), rec
+
+    _, rec, _ = PT.sensitivity(run_flat, P.X, OR.philox_schedule(n, P.b, P.r, seed=seed), seed=seed)
+    (Wref, out_ref), pert = sens_all["runs"][0], sens_all["runs"][1:]
+    sens = {"W": max(PT.rel(a, Wref) for a, _ in pert), "out": max(PT.rel(b, out_ref) for _, b in pert)}
+    return out.cpu().numpy(), W.cpu().numpy(), out_ref, Wref, rec, sens, status
 
 
 @pytest.mark.parametrize("kern,prec", [(0, None), (1, None), (2, 0)])
@@ -86,11 +100,12 @@ def test_pathwise_samples_match_oracle(lib, kern, prec):
     by the oracle): W and the samples at 500 test points; the last case on the FP32
     CUDA-core path."""
     P = synth.small(n=1500)
-    out, W, out_ref, Wref, rec, status = _pathwise_case(lib, P, ns=7, T=6, seed=17 + kern, kern=kern, prec=prec)
+    out, W, out_ref, Wref, rec, sens, status = _pathwise_case(lib, P, ns=7, T=6, seed=17 + kern, kern=kern,
+                                                              prec=prec)
     assert status == 0
-    tol = _tol_eta(rec, P.b, P.sigma2)
-    assert _rel(W, Wref) < tol
-    assert _rel(out, out_ref) < tol
+    cap = PT.a_priori_cap(rec, P.b, P.sigma2)
+    PT.check("pathwise kern=%d prec=%s" % (kern, prec), [("W", _rel(W, Wref), sens["W"], cap),
+                                                         ("samples", _rel(out, out_ref), sens["out"], cap)])
 
 
 def test_pathwise_converged_matches_cholesky(lib):
@@ -128,12 +143,17 @@ def test_pathwise_single_sample_without_mean(lib):
     Xd, Xt = P.X.astype(np.float64), P.Xtest.astype(np.float64)
     FX = PW.rf_prior(Xd, z, u, phase, theta, 2, P.ell, P.sigma2)
     Fs = PW.rf_prior(Xt, z, u, phase, theta, 2, P.ell, P.sigma2)
-    rec = []
-    Wref = OA.adasap(Xd, PW.pathwise_rhs(y, FX, zeta), 2, P.ell, P.sigma2, P.lam, 70, 20, 3,
-                     OR.philox_schedule(n, 70, 20, seed=9), record=rec)
-    ref = PW.pathwise_samples(Xt, Xd, Wref, Fs, 2, P.ell, P.sigma2)
+    rhs = PW.pathwise_rhs(y, FX, zeta)
+
+    def run(Xp, sched):
+        rec = []
+        Wr = OA.adasap(Xp, rhs, 2, P.ell, P.sigma2, P.lam, 70, 20, 3, sched, record=rec)
+        return PW.pathwise_samples(Xt, Xp, Wr, Fs, 2, P.ell, P.sigma2), rec
+
+    ref, rec, sens = PT.sensitivity(run, Xd, OR.philox_schedule(n, 70, 20, seed=9), seed=9)
     assert out.shape == (P.Xtest.shape[0], 1)
-    assert _rel(out.cpu().numpy(), ref) < _tol_eta(rec, 70, P.sigma2)
+    PT.check("pathwise one sample", [("samples", _rel(out.cpu().numpy(), ref), sens["W"],
+                                      PT.a_priori_cap(rec, 70, P.sigma2))])
     # a Matern context without its chi-square draws is refused
     with pytest.raises(lib.AdasapError):
         ctx.rf_prior(*_cuda(P.Xtest, z, None, phase, theta))

@@ -4,9 +4,12 @@ the FP64 oracle.
 The GPU forms H = K_BB + lambda I from the FP32 centred, scaled points, so its
 entries differ from the oracle's by ~2^-23 relative; the direction H^{-1} R then
 moves by up to cond(H) times that.  cond(H) <= (b sigma2 + lambda) / lambda, so the
-tolerance is  tol = max(1e-4, 10 * 2^-23 * (b sigma2 + lambda) / lambda).  The
+a-priori bound is  max(1e-4, 10 * 2^-23 * (b sigma2 + lambda) / lambda).  The
 blocked FP32 Cholesky's own rounding is removed by two refinement steps (residual
 R - H D in FP64), which the one-block test checks against the GPU's own residual.
+The W_T checks against the oracle's Alg. 1 use 10x the oracle's own sensitivity
+to FP32-level rounding of the points X (tests/_parity.py), with that bound as the
+cap.
 """
 
 import numpy as np
@@ -17,6 +20,8 @@ from oracle import adasap as OA
 from oracle import gp
 from oracle import rng as OR
 from paper_2505_13723_b300 import synth
+
+import _parity as PT
 
 pytestmark = pytest.mark.gpu
 
@@ -41,9 +46,15 @@ def test_sap_exact_matches_oracle(lib, kern, b, T, tail):
     opts = lib.default_opts(n, b=b, precond=2, max_iters=T, check_every=0, seed=5 + b, tail_average=int(tail))
     W, st, status = ctx.solve(torch.from_numpy(P.Y).cuda(), opts=opts)
     assert status == 0 and st["iters"] == T
-    Wref = OA.sap(P.X.astype(np.float64), P.Y.astype(np.float64), kern, P.ell, P.sigma2, lam, b, T,
-                  lambda t: OR.sample_block(n, b, 5 + b, t), tail_average=tail)
-    assert _rel(W.cpu().numpy(), Wref) < _tol(b, P.sigma2, lam)
+    Yd = P.Y.astype(np.float64)
+
+    def run(Xp, _):
+        return OA.sap(Xp, Yd, kern, P.ell, P.sigma2, lam, b, T, lambda t: OR.sample_block(n, b, 5 + b, t),
+                      tail_average=tail), []
+
+    Wref, _, sens = PT.sensitivity(run, P.X, None, seed=b)
+    PT.check("sap kern=%d b=%d T=%d" % (kern, b, T), [("W", _rel(W.cpu().numpy(), Wref), sens["W"],
+                                                        _tol(b, P.sigma2, lam))])
 
 
 def test_sap_exact_one_block_is_the_solution(lib):
@@ -71,9 +82,13 @@ def test_sap_exact_multi_rhs_large_block(lib):
     opts = lib.default_opts(n, b=2048, precond=2, max_iters=2, check_every=0, seed=8)
     W, st, status = ctx.solve(torch.from_numpy(P.Y).cuda(), opts=opts)
     assert status == 0
-    Wref = OA.sap(P.X.astype(np.float64), P.Y.astype(np.float64), P.kernel, P.ell, P.sigma2, lam, 2048, 2,
-                  lambda t: OR.sample_block(n, 2048, 8, t))
-    assert _rel(W.cpu().numpy(), Wref) < _tol(2048, P.sigma2, lam)
+    Yd = P.Y.astype(np.float64)
+
+    def run(Xp, _):
+        return OA.sap(Xp, Yd, P.kernel, P.ell, P.sigma2, lam, 2048, 2, lambda t: OR.sample_block(n, 2048, 8, t)), []
+
+    Wref, _, sens = PT.sensitivity(run, P.X, None, seed=8)
+    PT.check("sap b=2048 s=3", [("W", _rel(W.cpu().numpy(), Wref), sens["W"], _tol(2048, P.sigma2, lam))])
 
 
 def test_sap_exact_converges_and_batch_refuses_it(lib):

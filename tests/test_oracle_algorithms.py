@@ -130,6 +130,29 @@ def _small_problem(n=240, d=3, seed=7, lam=0.1, kernel=K.RBF, ell=1.0):
     return X, y[:, None], kernel, ell, 1.0, lam
 
 
+def test_accel_params_hand_values_where_each_root_and_nu_matter():
+    """Alg. 2's initialisation: beta = 1 - sqrt(mu/nu), gamma = 1/sqrt(mu nu),
+    alpha = 1/(1 + gamma nu), against values worked out by hand.
+
+    At (mu, nu) = (1/4, 16): mu/nu = 1/64 and mu nu = 4, so beta = 7/8,
+    gamma = 1/2 and alpha = 1/9.  A dropped root gives beta = 63/64 or
+    gamma = 1/4; a dropped nu in alpha gives 2/3; mu and nu swapped give
+    beta = -7.  At (1/100, 4): beta = 1 - 1/20, gamma = 5, alpha = 1/21
+    (gamma > 1 here, so gamma and 1/gamma are told apart as well)."""
+    for (mu, nu), want in (((0.25, 16.0), (7 / 8, 1 / 2, 1 / 9)),
+                           ((0.01, 4.0), (19 / 20, 5.0, 1 / 21))):
+        got = A.accel_params(mu, nu)
+        np.testing.assert_allclose(got, want, rtol=1e-15, atol=0)
+    # the plausible slips all land elsewhere at the first point
+    beta, gamma, alpha = A.accel_params(0.25, 16.0)
+    for wrong in (1 - 0.25 / 16, 1 - np.sqrt(16 / 0.25)):
+        assert abs(beta - wrong) > 0.1
+    for wrong in (1 / (0.25 * 16), np.sqrt(0.25 * 16)):
+        assert abs(gamma - wrong) > 0.2
+    for wrong in (1 / (1 + gamma), 1 / (1 + 1 / (0.25 * 16) * 16), gamma * 16 / (1 + gamma * 16)):
+        assert abs(alpha - wrong) > 0.05
+
+
 def test_accel_params_special_case_mu_equals_nu_is_plain_sap():
     X, Y, kern, ell, s2, lam = _small_problem()
     beta, gamma, alpha = A.accel_params(1.0, 1.0)

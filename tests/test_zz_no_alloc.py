@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import kernels as OK
 from paper_2505_13723_b300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -44,6 +45,29 @@ def test_noalloc_matches_kernel_rows_on_two_calls(lib, prec, s):
         r, o = ref.cpu().numpy(), out.cpu().numpy()
         assert np.isfinite(o).all(), "call %d left unwritten outputs" % call
         np.testing.assert_allclose(o, r, rtol=RTOL, atol=RTOL * np.abs(r).max())
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_noalloc_multi_rhs_on_a_tensor_core_precision_runs_fp32(lib, prec):
+    """s = 3 in a tensor-core precision: the allocation-free call takes the plain FP32
+    CUDA-core kernel, so it is held to the FP32 parity bound against the oracle
+    (|out - ref| <= 1e-5 * sum_j |k_ij| |w_j|), on two calls in a row."""
+    P = synth.regress(n=20000)
+    ctx = lib.Context(P.X, P.kernel, P.ell, P.sigma2, P.lam, precision=prec)
+    Xd = P.X.astype(np.float64)
+    g = np.random.default_rng(9 + prec)
+    for call, b in enumerate([700, 257]):
+        rows = g.choice(20000, size=b, replace=False)
+        W = g.standard_normal((20000, 3)).astype(np.float32)
+        out = torch.full((b, 3), float("nan"), device="cuda")
+        assert _call_noalloc(lib, ctx, torch.from_numpy(rows).cuda(), torch.from_numpy(W).cuda(), out) == 0, \
+            lib._lib.adasap_last_error()
+        torch.cuda.synchronize()
+        o = out.cpu().numpy().astype(np.float64)
+        ref = OK.kernel_rows(Xd, rows, W.astype(np.float64), P.kernel, P.ell, P.sigma2)
+        scale = OK.kernel_rows(Xd, rows, np.abs(W.astype(np.float64)), P.kernel, P.ell, P.sigma2)
+        assert np.isfinite(o).all(), "call %d left unwritten outputs" % call
+        assert (np.abs(o - ref) <= RTOL * scale).all(), (call, np.max(np.abs(o - ref) / scale))
 
 
 def test_noalloc_rejects_sizes_beyond_its_static_scratch(lib):
