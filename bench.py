@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--tol-iters", type=int, default=6000, help="iteration cap of the time-to-1e-3 solves")
     p.add_argument("--only-kernel", action="store_true",
                    help="run only the Step I block-row product launches (profiling)")
+    p.add_argument("--kern", choices=["rbf", "matern32", "matern52"], default="matern32",
+                   help="covariance kernel of the --only-kernel launches (the workload's own: matern32)")
     p.add_argument("--only-workload", choices=["multirhs", "bo"],
                    help="run only --warmup + --steps iterations of that workload's solver (profiling)")
     return p.parse_args()
@@ -315,6 +317,7 @@ def run_kernel_only(args):
 
     from paper_2505_13723_b300 import binding as lib
     P = workload(args.n)
+    P["kernel"] = {"rbf": 0, "matern32": 1, "matern52": 2}[args.kern]
     n, b = P.X.shape[0], P.b
     ctx = lib.Context(torch.from_numpy(P.X).cuda(), P.kernel, P.ell, P.sigma2, P.lam)
     g = np.random.default_rng(5)
@@ -332,7 +335,8 @@ def run_kernel_only(args):
     torch.cuda.synchronize()
     cb.close()
     ctx.close()
-    print(json.dumps({"only_kernel": True, "n": n, "b": b, "r": P.r, "launches": args.kernel_launches}))
+    print(json.dumps({"only_kernel": True, "kernel": args.kern, "n": n, "b": b, "r": P.r,
+                      "launches": args.kernel_launches}))
 
 
 def run_ours(args, rank, world, dist):
