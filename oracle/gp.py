@@ -11,6 +11,13 @@
                   With W = (K + lambda I)^{-1} y and G = W this is the building
                   block of d(y^T W)/dtheta = -W^T (dK/dtheta) W used when the
                   kernel hyperparameters are fitted (App. D.1).
+  subspace_rel_error  ||proj_l(m_hat) - proj_l(m_n)||_H^2 / ||proj_l(m_n)||_H^2, the
+                  error of a posterior-mean estimate m_hat = k(., X) w along the top-l
+                  spectral basis functions (Sec. 3, Thm. main; the tail-averaging
+                  experiment of the appendix), via the identity
+                  ||proj_l(m') - proj_l(m_n)||_H^2 = ||Q_l (w - w*)||_K^2 with Q_l the
+                  projector onto the top-l eigenvectors of K (App. proof of the
+                  main theorem).
 """
 
 import numpy as np
@@ -49,3 +56,15 @@ def hypergrad(X, W, G, kernel, ell, sigma2):
     dKW = K.kernel_apply(X, X, W, kernel, ell, sigma2, deriv=True)
     KW = K.kernel_apply(X, X, W, kernel, ell, sigma2)
     return float(np.sum(G * dKW)), float(np.sum(G * KW) / sigma2)
+
+
+def subspace_rel_error(evals, evecs, w, wstar, top):
+    """||Q_l (w - w*)||_K^2 / ||Q_l w*||_K^2 for l = top.
+
+    evals, evecs: the eigenpairs of K in descending order (evecs[:, i] the i-th);
+    ||Q_l z||_K^2 = sum_{i <= l} lambda_i (v_i^T z)^2 because Q_l and K commute."""
+    V = np.asarray(evecs, dtype=np.float64)[:, :top]
+    lam = np.asarray(evals, dtype=np.float64)[:top]
+    num = np.sum(lam * (V.T @ (np.asarray(w, np.float64) - np.asarray(wstar, np.float64))) ** 2)
+    den = np.sum(lam * (V.T @ np.asarray(wstar, np.float64)) ** 2)
+    return float(num / den)
