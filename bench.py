@@ -157,9 +157,14 @@ def oracle_rows_rate(P, target_s=10.0, max_rows=None, threads=None):
     elementwise work, so the threads run on separate cores); BLAS is held to one
     thread inside each so that the host cores are not oversubscribed.
     Returns (entries/s, rows, seconds, threads)."""
+    import contextlib
     from concurrent.futures import ThreadPoolExecutor
 
-    from threadpoolctl import threadpool_limits
+    try:
+        from threadpoolctl import threadpool_limits
+    except ImportError:   # not on every host: the oracle's one BLAS call is a small matrix-vector product
+        def threadpool_limits(_):
+            return contextlib.nullcontext()
 
     from oracle import kernels as OK
     X = P.X.astype(np.float64)

@@ -38,6 +38,14 @@ a keyword argument here so that tests can discriminate between them):
   Stabilised Woodbury with S_i = 0   eigenpairs with S_i = 0 are dropped (the
       limit rho / S_i -> infinity).
   Tail average         W_bar_T = mean(W_j, j = ceil(T/2) .. T).
+
+perturb (tests only; default None, which leaves the arithmetic above exactly as
+written): a callback perturb(tag, array) -> array applied to the kernel block
+K_BB where a single-precision implementation forms it more than once -- once
+for the sketch K_BB Omega (tag "K_BB sketch") and once in the products of the
+power iteration (tag "K_BB powering"; for SAP "K_BB solve") -- so that a test
+can measure how far rounding of those copies at the FP32 level (Sec. 5 runs in
+single precision) moves eta, rho and W.
 """
 
 import numpy as np
@@ -167,7 +175,7 @@ def block_residual(X, Y, P, rows, kernel, ell, sigma2, lam):
 
 def adasap(X, Y, kernel, ell, sigma2, lam, b, r, T, schedule, W0=None,
            mu=None, nu=None, precond="nystrom", point="z", nesterov="standard",
-           eps=EPS_FP32, power_iters=10, tail_average=False, record=None):
+           eps=EPS_FP32, power_iters=10, tail_average=False, record=None, perturb=None):
     """Alg. 2 (ADASAP) for (K + lambda I) W = Y.
 
     schedule(t) -> (B_t, Omega_t, v0_t) supplies the iteration's randomness.
@@ -196,11 +204,12 @@ def adasap(X, Y, kernel, ell, sigma2, lam, b, r, T, schedule, W0=None,
         R = block_residual(X, Y2, Pt, Bt, kernel, ell, sigma2, lam)
         XB = X[Bt]
         KBB = K.kernel_matrix(XB, XB, kernel, ell, sigma2)
-        H_mv = lambda v: KBB @ v + lam * v
+        KBB_pow = KBB if perturb is None else perturb("K_BB powering", KBB)
+        H_mv = lambda v: KBB_pow @ v + lam * v
         if precond == "nystrom":
             # Step II: Nystrom sketch K_BB Omega (Omega orthonormalised)
             Omega = orthonormalize(Omega)
-            MOmega = KBB @ Omega
+            MOmega = (KBB if perturb is None else perturb("K_BB sketch", KBB)) @ Omega
             # Step III: Nystrom approximation, preconditioner, stepsize
             U, S, Delta = nystrom(MOmega, Omega, eps=eps)
             rho = damping(S, lam)
@@ -230,7 +239,7 @@ def adasap(X, Y, kernel, ell, sigma2, lam, b, r, T, schedule, W0=None,
     return out[:, 0] if vec else out
 
 
-def sap(X, Y, kernel, ell, sigma2, lam, b, T, blocks, W0=None, tail_average=False):
+def sap(X, Y, kernel, ell, sigma2, lam, b, T, blocks, W0=None, tail_average=False, perturb=None):
     """Alg. 1 (SAP) with the exact block solve (K_BB + lambda I)^{-1}.
 
     blocks(t) -> B_t.  Returns W_T (or the tail average).
@@ -245,7 +254,8 @@ def sap(X, Y, kernel, ell, sigma2, lam, b, T, blocks, W0=None, tail_average=Fals
         Bt = np.asarray(blocks(t))
         R = block_residual(X, Y2, W, Bt, kernel, ell, sigma2, lam)
         XB = X[Bt]
-        Hb = K.kernel_matrix(XB, XB, kernel, ell, sigma2) + lam * np.eye(len(Bt))
+        KBB = K.kernel_matrix(XB, XB, kernel, ell, sigma2)
+        Hb = (KBB if perturb is None else perturb("K_BB solve", KBB)) + lam * np.eye(len(Bt))
         DB = sla.cho_solve(sla.cho_factor(Hb), R)
         W = W.copy()
         W[Bt] -= DB

@@ -45,9 +45,10 @@ def _oracle(P, T, seed, precond="nystrom", Y=None):
     n = P.X.shape[0]
     Yd = (P.Y if Y is None else Y).astype(np.float64)
 
-    def run(Xp, sched):
+    def run(Xp, sched, hook):
         rec = []
-        W = OA.adasap(Xp, Yd, P.kernel, P.ell, P.sigma2, P.lam, P.b, P.r, T, sched, precond=precond, record=rec)
+        W = OA.adasap(Xp, Yd, P.kernel, P.ell, P.sigma2, P.lam, P.b, P.r, T, sched, precond=precond, record=rec,
+                      perturb=hook)
         return W, rec
 
     return PT.sensitivity(run, P.X, OR.philox_schedule(n, P.b, P.r, seed=seed), seed=seed)

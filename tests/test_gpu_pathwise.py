@@ -70,12 +70,12 @@ def _pathwise_case(lib, P, ns, T, seed, kern=None, prec=None):
     out, W, st, status = ctx.pathwise(*_cuda(y, P.Xtest, z, u, phase, theta, zeta), opts=opts)
     Xt = P.Xtest.astype(np.float64)
 
-    def run(Xd, sched):
+    def run(Xd, sched, hook):
         FX = PW.rf_prior(Xd, z, u, phase, theta, kern, P.ell, P.sigma2)
         Fs = PW.rf_prior(Xt, z, u, phase, theta, kern, P.ell, P.sigma2)
         R = np.concatenate([y.astype(np.float64)[:, None], PW.pathwise_rhs(y, FX, zeta)], axis=1)
         rec = []
-        Wref = OA.adasap(Xd, R, kern, P.ell, P.sigma2, P.lam, P.b, P.r, T, sched, record=rec)
+        Wref = OA.adasap(Xd, R, kern, P.ell, P.sigma2, P.lam, P.b, P.r, T, sched, record=rec, perturb=hook)
         out_ref = np.concatenate([gp.posterior_mean(Xt, Xd, Wref[:, :1], kern, P.ell, P.sigma2),
                                   PW.pathwise_samples(Xt, Xd, Wref[:, 1:], Fs, kern, P.ell, P.sigma2)], axis=1)
         # W and the samples together, so that the sensitivity covers both
@@ -83,8 +83,8 @@ def _pathwise_case(lib, P, ns, T, seed, kern=None, prec=None):
 
     sens_all = {}
 
-    def run_flat(Xd, sched):
-        (Wr, outr), rec = run(Xd, sched)
+    def run_flat(Xd, sched, hook):
+        (Wr, outr), rec = run(Xd, sched, hook)
         sens_all.setdefault("runs", []).append((Wr, outr))
         return np.concatenate([Wr.ravel(), outr.ravel()]), rec
 
@@ -145,9 +145,9 @@ def test_pathwise_single_sample_without_mean(lib):
     Fs = PW.rf_prior(Xt, z, u, phase, theta, 2, P.ell, P.sigma2)
     rhs = PW.pathwise_rhs(y, FX, zeta)
 
-    def run(Xp, sched):
+    def run(Xp, sched, hook):
         rec = []
-        Wr = OA.adasap(Xp, rhs, 2, P.ell, P.sigma2, P.lam, 70, 20, 3, sched, record=rec)
+        Wr = OA.adasap(Xp, rhs, 2, P.ell, P.sigma2, P.lam, 70, 20, 3, sched, record=rec, perturb=hook)
         return PW.pathwise_samples(Xt, Xp, Wr, Fs, 2, P.ell, P.sigma2), rec
 
     ref, rec, sens = PT.sensitivity(run, Xd, OR.philox_schedule(n, 70, 20, seed=9), seed=9)

@@ -48,9 +48,9 @@ def test_sap_exact_matches_oracle(lib, kern, b, T, tail):
     assert status == 0 and st["iters"] == T
     Yd = P.Y.astype(np.float64)
 
-    def run(Xp, _):
+    def run(Xp, _, hook):
         return OA.sap(Xp, Yd, kern, P.ell, P.sigma2, lam, b, T, lambda t: OR.sample_block(n, b, 5 + b, t),
-                      tail_average=tail), []
+                      tail_average=tail, perturb=hook), []
 
     Wref, _, sens = PT.sensitivity(run, P.X, None, seed=b)
     PT.check("sap kern=%d b=%d T=%d" % (kern, b, T), [("W", _rel(W.cpu().numpy(), Wref), sens["W"],
@@ -84,8 +84,9 @@ def test_sap_exact_multi_rhs_large_block(lib):
     assert status == 0
     Yd = P.Y.astype(np.float64)
 
-    def run(Xp, _):
-        return OA.sap(Xp, Yd, P.kernel, P.ell, P.sigma2, lam, 2048, 2, lambda t: OR.sample_block(n, 2048, 8, t)), []
+    def run(Xp, _, hook):
+        return OA.sap(Xp, Yd, P.kernel, P.ell, P.sigma2, lam, 2048, 2, lambda t: OR.sample_block(n, 2048, 8, t),
+                      perturb=hook), []
 
     Wref, _, sens = PT.sensitivity(run, P.X, None, seed=8)
     PT.check("sap b=2048 s=3", [("W", _rel(W.cpu().numpy(), Wref), sens["W"], _tol(2048, P.sigma2, lam))])
