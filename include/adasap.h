@@ -171,6 +171,17 @@ adasap_status adasap_kernel_rows_noalloc(adasap_ctx* ctx, const int64_t* B, int6
  * Synchronises `stream`. */
 adasap_status adasap_measure_pipes(double* out, int count, void* stream);
 
+/* Self-test support (the paper has no counterpart): evaluates, element by
+ * element, a device function of the block-row epilogues, so that tests can hold
+ * it to its error bound on a dense grid.  fn = 0: the square root computed on the
+ * FMA pipe that the Matern epilogues use for a share of their entries (Newton
+ * steps from a bit-pattern seed; inputs below 1e-30 are taken as 1e-30, and on
+ * [1e-30, 1e21] the result is the correctly rounded square root to within half an
+ * ulp); fn = 1: sqrt.approx of the special-function unit.  x and out are device
+ * arrays of n floats (they may alias); the call is asynchronous on `stream`.
+ * ADASAP_EINVAL for another fn, n < 0, or a NULL array with n > 0. */
+adasap_status adasap_eval_math(int fn, const float* x, int64_t n, float* out, void* stream);
+
 /* Device-side failures (the paper has no counterpart).  Every wait inside the
  * tensor-core kernels is bounded in time; a kernel whose wait runs out records a
  * code in its context, writes NaN in place of the affected outputs and returns,

@@ -38,7 +38,7 @@ SYMBOLS = ["adasap_default_opts", "adasap_status_string", "adasap_last_error", "
            "adasap_kernel_rows_noalloc", "adasap_measure_pipes", "adasap_residual",
            "adasap_solve_batched", "adasap_rf_prior", "adasap_pathwise", "adasap_rmse_nll",
            "adasap_check_device", "adasap_wait_selftest", "adasap_solver_get_state",
-           "adasap_solver_set_state", "adasap_schedule_check"]
+           "adasap_solver_set_state", "adasap_schedule_check", "adasap_eval_math"]
 
 
 class Opts(ctypes.Structure):
@@ -113,6 +113,8 @@ _lib.adasap_wait_selftest.restype = ctypes.c_int
 _lib.adasap_schedule_check.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int)]
 _lib.adasap_schedule_check.restype = ctypes.c_int
+_lib.adasap_eval_math.argtypes = [ctypes.c_int, _P, _I64, _P, _P]
+_lib.adasap_eval_math.restype = ctypes.c_int
 _lib.adasap_solver_get_state.argtypes = [_P, _P, _P, _P, ctypes.POINTER(_I64), _P]
 _lib.adasap_solver_get_state.restype = ctypes.c_int
 _lib.adasap_solver_set_state.argtypes = [_P, _P, _P, _P, _I64, _P]
@@ -453,6 +455,16 @@ def schedule_check(m, ncols, max_ctas=0):
     ns, fl = ctypes.c_int(), ctypes.c_int()
     st = _lib.adasap_schedule_check(int(m), int(ncols), int(max_ctas), ctypes.byref(ns), ctypes.byref(fl))
     return st, ns.value, bool(fl.value)
+
+
+def eval_math(fn, x, stream=None):
+    """adasap_eval_math: f(x) element by element on the device (fn 0: the FMA-pipe square
+    root of the Matern epilogues, 1: sqrt.approx)."""
+    xt = x.contiguous()
+    out = torch.empty_like(xt)
+    _check(_lib.adasap_eval_math(int(fn), _dev_f32(xt, "x"), xt.numel(), ctypes.c_void_p(out.data_ptr()),
+                                 _stream(stream)), "adasap_eval_math")
+    return out
 
 
 def measure_pipes(stream=None):

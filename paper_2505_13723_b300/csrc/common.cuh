@@ -26,6 +26,28 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+// sqrt(v) for finite v >= 0 on the FMA pipe (no special-function unit): a seed for
+// 1/sqrt(v) from the IEEE bit pattern (the exponent halved and negated by one
+// integer subtraction: the magic-constant method, analysed by C. Lomont, "Fast
+// inverse square root", 2003), two Newton steps r <- r (3/2 - v r^2 / 2) (relative
+// error 3.4e-2 -> 1.7e-3 -> 4.6e-6), then one coupled correction of s = v r,
+// s <- s + (r / 2)(v - s^2), which squares the error again.  v is first clamped to
+// at least 1e-30 (at v = 0 the seed's square would overflow; sqrt(1e-30) = 1e-15
+// is zero for every kernel epilogue here), and over [1e-30, 1e21] the result is
+// within 0.5 ulp of the correctly rounded square root.  Eleven FMA-pipe
+// operations, two integer ones and the clamp, used for a share of the entries of
+// the Matern epilogues, whose sqrt.approx would otherwise take half of the
+// special-function unit's time.
+__device__ __forceinline__ float sqrt_fma(float v) {
+  v = fmaxf(v, 1e-30f);
+  float r = __int_as_float(0x5f3759df - (__float_as_int(v) >> 1));
+  const float h = 0.5f * v;
+  r = r * fmaf(-h, r * r, 1.5f);
+  r = r * fmaf(-h, r * r, 1.5f);
+  const float s = v * r;
+  return fmaf(0.5f * r, fmaf(-s, s, v), s);
+}
+
 // d = a * b + c on two lanes at once (sm_100+ packed FP32 FMA)
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
   unsigned long long ra = *reinterpret_cast<unsigned long long*>(&a);

@@ -118,6 +118,7 @@ struct TcArgs {
   float sigma2;
   int* err;          // set to 1 on a wait timeout
   int flat;          // 1: equal tile runs per CTA (one product only; nsplit = tc_flat_slots)
+  const float* wp;   // w prepared per 128-column tile by launch_prep_w (NULL: the kernel stages w itself)
 };
 TcArgs make_tc_args(int d, const float* xr, const float* qr, const int* ridx, int64_t m, int dp, const float* bhi,
                     const float* blo, int64_t ncols, int self_mode, const float* w, int64_t ldw, float* part,
@@ -149,7 +150,12 @@ cudaError_t launch_build_tc(const float* X, const float* q, const int* gidx, int
 cudaError_t launch_rows_tc(int kern, int d, const float* xr, const float* qr, const int* ridx, int64_t m, int dp,
                            const float* bhi, const float* blo, int64_t ncols, int self_mode, const float* w,
                            int64_t ldw, float* part, int nsplit, float sigma2, int* err, cudaStream_t st,
-                           int max_ctas = 0);
+                           int max_ctas = 0, const float* wp = nullptr);
+// w (ncols entries, stride ldw) laid out for the tensor-core kernel's bulk copies: per
+// 128-column tile t, wp[t][0][:] = w, and for the Matern kernels wp[t][1][:] = w / log2(e),
+// wp[t][2][:] = w / (3 log2(e)^2); zero past ncols.  tc_wprep_floats: floats of wp.
+int64_t tc_wprep_floats(int64_t ncols, int kern);
+cudaError_t launch_prep_w(int kern, const float* w, int64_t ldw, int64_t ncols, float* wp, cudaStream_t st);
 
 // ---- multi-RHS tensor-core product (rows_tc_mrhs.cu) ------------------------------
 // Padded accumulator width for s right-hand sides, and the floats of one W
@@ -169,6 +175,8 @@ cudaError_t launch_rows_tc_mrhs(int kern, int d, const float* xr, const float* q
 
 // ---- pipe throughput probe (probe.cu): ex2, rsqrt, FFMA per SM per cycle -------------
 cudaError_t measure_pipes(double* out4, cudaStream_t st);   // ex2, rsqrt, FFMA, sqrt
+// out[i] = f(x[i]): fn 0 the FMA-pipe square root (sqrt_fma), 1 sqrt.approx
+cudaError_t launch_eval_math(int fn, const float* x, int64_t n, float* out, cudaStream_t st);
 // A bounded wait that no arrival completes: records kWaitSelfTestCode in err after limit_ns.
 constexpr int kWaitSelfTestCode = 99;
 cudaError_t launch_wait_selftest(uint64_t limit_ns, int* err, cudaStream_t st);

@@ -3,6 +3,8 @@
 // benchmark reports.  Each thread runs kProbeChains independent dependency
 // chains so that latency is hidden and only issue throughput counts; the SM
 // clock over the run is taken from clock64 against the global timer.
+#include <algorithm>
+
 #include "tc_ptx.cuh"
 
 namespace adasap {
@@ -89,6 +91,19 @@ cudaError_t measure_pipes(double* out4, cudaStream_t st) {
   cudaFree(sink);
   cudaFree(clk);
   return e;
+}
+
+// Element-by-element evaluation of the epilogues' device functions (self-test support).
+__global__ void k_eval_math(int fn, const float* __restrict__ x, int64_t n, float* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = fn == 0 ? sqrt_fma(x[i]) : sqrt_approx(x[i]);
+}
+
+cudaError_t launch_eval_math(int fn, const float* x, int64_t n, float* out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 16);
+  k_eval_math<<<blocks, 256, 0, st>>>(fn, x, n, out);
+  return cudaGetLastError();
 }
 
 // The failure path of the bounded waits, exercised without a fault: one thread

@@ -11,17 +11,26 @@
 // CTA = 128 rows x a column range, 640 threads, persistent over (row tile,
 // column split) items, or over equal runs of tiles (the flat schedule, for
 // small products):
-//   warp 0       producer: bulk copies (cp.async.bulk, the TMA engine) of
+//   warp 0       copy producer: bulk copies (cp.async.bulk, the TMA engine) of
 //                128-column operand tiles into an 8-stage shared-memory ring
-//                (5 at KP = 32), and the w values of each tile, loaded two
-//                tiles ahead, into a 4-stage w buffer
-//   warp 1       owns the TMEM allocation (4 x 128 FP32 distance columns, the
-//                whole TMEM) and issues the MMAs from one thread
-//                (tcgen05.mma kind::tf32, M = 128, N = 128, K = 8 per instruction)
+//                (5 at KP = 32), as fast as the MMAs free the stages
+//   warps 1, 3   MMA issuers, one thread each: warp 1 the even tiles, warp 3 the
+//                odd ones (tcgen05.mma kind::tf32, M = 128, N = 128, K = 8 per
+//                instruction); warp 1 owns the TMEM allocation (4 x 128 FP32
+//                distance columns, the whole TMEM).  One issuer spent about as long
+//                in its two barrier waits per tile as in issuing the tile's six
+//                MMAs, so the tensor pipe idled half the time.
+//   warp 2       w producer: the w values of each tile (loaded two tiles ahead)
+//                into an 8-stage w ring, twice as deep as the TMEM ring, so that
+//                the w of a tile is in place before its TMEM buffer is
 //   warps 4..19  epilogue in four groups of four warps: group g takes every
 //                fourth tile (TMEM buffer g); warp w tcgen05.ld-s the 32 rows of
-//                TMEM lane quadrant w % 4, all 128 columns, applies the RBF /
-//                Matern epilogue and contracts with w in registers
+//                TMEM lane quadrant w % 4, all 128 columns, releases the buffer
+//                once its last load has landed, applies the RBF / Matern
+//                epilogue and contracts with w in registers
+// (One warp staging both the copies and w gated every tile on that warp's
+// serial chain of barrier waits, copy issues and w stores: about 1,500 clocks
+// per tile, three times the special-function pipe's time for an RBF tile.)
 // Operands live in shared memory in the no-swizzle K-major canonical layout:
 // 8-row core groups of 16-byte K chunks (LBO = 128 B between K chunks,
 // SBO = 32 * KP B between 8-row groups).  The column operands are prebuilt in
@@ -44,7 +53,9 @@ constexpr int kTcEpiWarps = 16;
 constexpr int kTcThreadsV2 = 32 * (4 + kTcEpiWarps);   // producer, MMA, 2 idle, epilogue
 constexpr int kTcWArrays = 3;                          // w, w / log2e, w / (3 log2e^2)
 
-constexpr int kTcBufs = 4;                             // TMEM distance buffers and w stages
+constexpr int kTcBufs = 4;                             // TMEM distance buffers
+constexpr int kTcWStages = 2 * kTcBufs;                // w ring
+constexpr int kTcWPre = 4;                             // tiles of w held in registers ahead of the ring
 constexpr uint32_t kTcTmemCols = kTcBufs * kTcN;       // 512: the whole TMEM of the SM
 
 template <int KP>
@@ -55,23 +66,36 @@ struct TcSmem {
   // 5 x 32 KB at KP = 32)
   static constexpr int kStages = KP == 16 ? 8 : 5;
   static constexpr size_t ops_bytes = (size_t)(2 + 2 * kStages) * OPF * sizeof(float);
-  static constexpr size_t w_bytes = (size_t)kTcBufs * kTcWArrays * kTcN * sizeof(float);   // [buf][array][128]
-  static constexpr size_t red_bytes = (size_t)4 * kTcM * sizeof(float);               // column-group partials
-  static constexpr size_t bytes = ops_bytes + w_bytes + red_bytes + 32 * sizeof(uint64_t) + 64 + 1024;
+  static constexpr size_t w_bytes = (size_t)kTcWStages * kTcWArrays * kTcN * sizeof(float);   // [stage][array][128]
+  static constexpr size_t red_bytes = (size_t)4 * kTcM * sizeof(float);                   // column-group partials
+  static constexpr size_t bytes = ops_bytes + w_bytes + red_bytes + 64 * sizeof(uint64_t) + 64 + 1024;
 };
+
+// Matern epilogues: of every 8 consecutive entries of a chunk, this many take
+// their square root on the FMA pipe (sqrt_fma) instead of the special-function
+// unit, whose sqrt issues at half its ex2 rate on this GPU (15.8 against 31.5 per
+// SM per clock): per entry that unit then needs (1 - k/8)/15.8 + 1/31.5 clocks
+// instead of 1/15.8 + 1/31.5, for about fourteen more issued instructions per
+// moved sqrt.  Measured on the Step I launch (10^4 x 2^20 entries): Matern-3/2
+// 4.02 ms at k = 0, 3.85 at k = 1, 4.03 at k = 2; Matern-5/2, whose epilogue
+// issues more instructions per entry, 4.14 at k = 0 and 1 and slower above.
+template <int KERN>
+__host__ __device__ constexpr int sqrt_fma_per8() { return KERN == ADASAP_MATERN32 ? 1 : 0; }
 
 // Per-entry epilogue on the scaled distance v = log2(e)^2 u (M32, M52) or u (RBF),
 // accumulating k(u) w / sigma2 into acc; wl = w / log2(e), w3 = w / (3 log2(e)^2):
 //   RBF  k = 2^-u
 //   M32  k = (1 + a) e^-a   = 2^-a' (1 + a' / log2 e),              a' = sqrt(v)
 //   M52  k = (1 + a + a^2/3) e^-a = 2^-a' (1 + a'/log2 e + a'^2 / (3 log2^2 e))
+// sw: a' from sqrt_fma (FMA pipe) instead of sqrt.approx (special-function unit);
+// a compile-time constant at every call (unrolled loops).
 template <int KERN>
-__device__ __forceinline__ float tc_term(float v, float w, float wl, float w3, float acc) {
+__device__ __forceinline__ float tc_term(float v, float w, float wl, float w3, float acc, bool sw = false) {
   // RBF: for a near-duplicate pair u may come out below 0 by the rounding of q_i + q_j - 2 x_i.x_j
   // (about 2^-22 (q_i + q_j)); 2^{-u} is then 1 + O(1e-6), inside the product's tolerance, so the
   // RBF term needs no clamp
   if (KERN == ADASAP_RBF) return fmaf(ex2_approx(-v), w, acc);
-  const float ap = sqrt_approx(fmaxf(v, 0.0f));   // a' (one special-function op)
+  const float ap = sw ? sqrt_fma(v) : sqrt_approx(fmaxf(v, 0.0f));   // a' (clamped at 0 or 1e-30)
   const float e = ex2_approx(-ap);
   if (KERN == ADASAP_MATERN32) return fmaf(e, fmaf(ap, wl, w), acc);
   return fmaf(e, fmaf(ap, fmaf(ap, w3, wl), w), acc);
@@ -111,16 +135,17 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
   float* sAhi = reinterpret_cast<float*>(base);
   float* sAlo = sAhi + OPF;
   float* sB = sAlo + OPF;  // [stage][hi, lo][OPF]
-  float* sw = reinterpret_cast<float*>(base + L::ops_bytes);                 // [buf][array][128]
+  float* sw = reinterpret_cast<float*>(base + L::ops_bytes);                 // [stage][array][128]
   float* red = reinterpret_cast<float*>(base + L::ops_bytes + L::w_bytes);   // [group][128]
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + L::ops_bytes + L::w_bytes + L::red_bytes);
   uint64_t* full = bars;                     // [kTcStages] column tiles landed (copies)
   uint64_t* empty = bars + kTcStages;        // [kTcStages] column tile stage consumed by the MMAs
   uint64_t* tfull = bars + 2 * kTcStages;    // [kTcBufs] distance buffer ready
-  uint64_t* tempty = tfull + kTcBufs;        // [kTcBufs] distance buffer and w stage done (4 epilogue warps)
-  uint64_t* wfull = tfull + 2 * kTcBufs;     // [kTcBufs] w stage written
-  uint64_t* drain = tfull + 3 * kTcBufs;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* tempty = tfull + kTcBufs;        // [kTcBufs] distance buffer read (4 epilogue warps)
+  uint64_t* wfull = tfull + 2 * kTcBufs;     // [kTcWStages] w stage written
+  uint64_t* wempty = wfull + kTcWStages;     // [kTcWStages] w stage read (4 epilogue warps)
+  uint64_t* drain = wempty + kTcWStages;     // [2] one per MMA issuer
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -137,9 +162,13 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
     for (int i = 0; i < kTcBufs; ++i) {
       mbar_init(&tfull[i], 1);
       mbar_init(&tempty[i], kTcEpiWarps / kTcBufs);   // the four warps of group i
-      mbar_init(&wfull[i], 1);
     }
-    mbar_init(drain, 1);
+    for (int i = 0; i < kTcWStages; ++i) {
+      mbar_init(&wfull[i], 1);
+      mbar_init(&wempty[i], kTcEpiWarps / kTcBufs);   // the four warps of the group taking that tile
+    }
+    mbar_init(&drain[0], 1);
+    mbar_init(&drain[1], 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -234,54 +263,100 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
     __syncthreads();
 
     if (warp == 0) {
-      // ---- producer: column tiles by bulk copy (lane 0) up to kTcStages tiles ahead
-      // of the MMAs; w of each tile by the whole warp once the epilogue is done with
-      // the w stage (kTcBufs tiles back) ---------------------------------------------
-      int xi = 0;  // column tiles issued
+      // ---- copy producer: column tiles by bulk copy (lane 0), each as soon as the
+      // MMAs have freed its stage ------------------------------------------------------
+      if (lane == 0) {
+        int xi = 0;  // column tiles issued
+        for (; xi < ntiles; ++xi) {
+          const uint32_t gx = gt + (uint32_t)xi;
+          const int st = gx % kTcStages;
+          if (!mbar_wait(&empty[st], ((gx / kTcStages) & 1u) ^ 1u, abort_flag)) {
+            *abort_flag = 1;
+            tc_note_timeout(a.err, 1);
+            break;
+          }
+          mbar_arrive_expect_tx(&full[st], 2u * OPF * sizeof(float));
+          const int64_t off = (c0 + (int64_t)xi * kTcN) * KP;
+          bulk_g2s(sB + (st * 2 + 0) * OPF, a.bhi + off, OPF * sizeof(float), &full[st]);
+          bulk_g2s(sB + (st * 2 + 1) * OPF, a.blo + off, OPF * sizeof(float), &full[st]);
+        }
+        if (*abort_flag) {
+          // our copies still write shared memory: wait (bounded) for the last ones
+          for (int x = max(0, xi - kTcStages); x < xi; ++x) {
+            const uint32_t gx = gt + (uint32_t)x;
+            mbar_wait(&full[gx % kTcStages], (gx / kTcStages) & 1u, nullptr);
+          }
+        }
+      }
+    } else if (warp == 2 && a.wp) {
+      // ---- w producer, prepared w: one bulk copy of each tile's w arrays (lane 0)
+      // into the w ring, once the epilogue is done with the stage's previous tile -------
+      if (lane == 0) {
+        constexpr uint32_t wbytes = (KERN == ADASAP_RBF ? 1u : (uint32_t)kTcWArrays) * kTcN * sizeof(float);
+        const float* wsrc = a.wp + (c0 / kTcN) * (wbytes / sizeof(float));
+        int wi = 0;  // tiles issued
+        for (; wi < ntiles; ++wi) {
+          const uint32_t g = gt + (uint32_t)wi;
+          const int ws = g % kTcWStages;
+          if (!mbar_wait(&wempty[ws], ((g / kTcWStages) & 1u) ^ 1u, abort_flag)) {
+            *abort_flag = 1;
+            tc_note_timeout(a.err, 4);
+            break;
+          }
+          mbar_arrive_expect_tx(&wfull[ws], wbytes);
+          bulk_g2s(sw + ws * kTcWArrays * kTcN, wsrc + (int64_t)wi * (wbytes / sizeof(float)), wbytes, &wfull[ws]);
+        }
+        if (*abort_flag) {
+          // our copies still write shared memory: wait (bounded) for the last ones
+          for (int x = max(0, wi - kTcWStages); x < wi; ++x) {
+            const uint32_t gx = gt + (uint32_t)x;
+            mbar_wait(&wfull[gx % kTcWStages], (gx / kTcWStages) & 1u, nullptr);
+          }
+        }
+      }
+    } else if (warp == 2) {
+      // ---- w producer, w as given (any stride or alignment): w of every tile into
+      // the w ring (whole warp), once the epilogue is done with the stage's previous
+      // tile (kTcWStages tiles back) -------------------------------------------------
       bool ok = true;
-      // w of tile t (zero past the split), loaded two tiles ahead so that the global
-      // load latency overlaps the waits and stores of the tiles in between
+      // w of tile t (zero past the split), loaded kTcWPre tiles ahead so that the
+      // global load latency overlaps the waits and stores of the tiles in between
+      // (one 16-byte load per lane where w is contiguous and 16-byte aligned)
+      const bool vec = a.ldw == 1 && ((reinterpret_cast<uintptr_t>(a.w) & 15u) == 0);
       auto load_w = [&](int t, float (&wv)[4]) {
         const int64_t jb = c0 + (int64_t)t * kTcN + 4 * lane;
+        if (vec && t < ntiles && jb + 3 < c1) {
+          const float4 q = __ldg(reinterpret_cast<const float4*>(a.w + jb));
+          wv[0] = q.x, wv[1] = q.y, wv[2] = q.z, wv[3] = q.w;
+          return;
+        }
 #pragma unroll
         for (int e = 0; e < 4; ++e) wv[e] = (t < ntiles && jb + e < c1) ? __ldg(a.w + (jb + e) * a.ldw) : 0.0f;
       };
-      float wa[4], wb[4];
-      load_w(0, wa);
-      load_w(1, wb);
+      float wq[kTcWPre][4];
+#pragma unroll
+      for (int k = 0; k < kTcWPre; ++k) load_w(k, wq[k]);
       for (int t = 0; ok && t < ntiles; ++t) {
+        const uint32_t g = gt + (uint32_t)t;
+        const int ws = g % kTcWStages;
         if (lane == 0) {
-          for (; xi < ntiles && xi < t + kTcStages; ++xi) {
-            const uint32_t gx = gt + (uint32_t)xi;
-            const int st = gx % kTcStages;
-            if (!mbar_wait(&empty[st], ((gx / kTcStages) & 1u) ^ 1u, abort_flag)) {
-              ok = false;
-              break;
-            }
-            mbar_arrive_expect_tx(&full[st], 2u * OPF * sizeof(float));
-            const int64_t off = (c0 + (int64_t)xi * kTcN) * KP;
-            bulk_g2s(sB + (st * 2 + 0) * OPF, a.bhi + off, OPF * sizeof(float), &full[st]);
-            bulk_g2s(sB + (st * 2 + 1) * OPF, a.blo + off, OPF * sizeof(float), &full[st]);
-          }
-          const uint32_t g = gt + (uint32_t)t;
-          if (ok) ok = mbar_wait(&tempty[g % kTcBufs], ((g / kTcBufs) & 1u) ^ 1u, abort_flag);
+          ok = mbar_wait(&wempty[ws], ((g / kTcWStages) & 1u) ^ 1u, abort_flag);
           if (!ok) {
             *abort_flag = 1;
-            tc_note_timeout(a.err, 1);
+            tc_note_timeout(a.err, 4);
           }
         }
         ok = __shfl_sync(0xffffffffu, (int)ok, 0) != 0;
         if (!ok) break;
-        // w of the tile's 128 columns
-        const uint32_t g = gt + (uint32_t)t;
-        float* wst = sw + (g % kTcBufs) * kTcWArrays * kTcN;
         float wv[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          wv[e] = wa[e];
-          wa[e] = wb[e];
+          wv[e] = wq[0][e];
+#pragma unroll
+          for (int k = 0; k + 1 < kTcWPre; ++k) wq[k][e] = wq[k + 1][e];
         }
-        load_w(t + 2, wb);
+        load_w(t + kTcWPre, wq[kTcWPre - 1]);
+        float* wst = sw + ws * kTcWArrays * kTcN;
         *reinterpret_cast<float4*>(wst + 4 * lane) = make_float4(wv[0], wv[1], wv[2], wv[3]);
         if (KERN != ADASAP_RBF) {
           const float il = 1.0f / kLog2e, i3 = 1.0f / (3.0f * kLog2e * kLog2e);
@@ -291,20 +366,14 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
               make_float4(wv[0] * i3, wv[1] * i3, wv[2] * i3, wv[3] * i3);
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&wfull[g % kTcBufs]);
+        if (lane == 0) mbar_arrive(&wfull[ws]);
       }
-      if (lane == 0 && *abort_flag) {
-        // our copies still write shared memory: wait (bounded) for the last ones
-        for (int x = max(0, xi - kTcStages); x < xi; ++x) {
-          const uint32_t gx = gt + (uint32_t)x;
-          mbar_wait(&full[gx % kTcStages], (gx / kTcStages) & 1u, nullptr);
-        }
-      }
-    } else if (warp == 1) {
-      // ---- MMA issuer -------------------------------------------------------------
+    } else if (warp == 1 || warp == 3) {
+      // ---- MMA issuers: tiles g = gt + t with g % 2 == iss ----------------------------
+      const int iss = warp == 1 ? 0 : 1;
       if (lane == 0) {
         int issued = 0;
-        for (int t = 0; t < ntiles; ++t) {
+        for (int t = (int)(((uint32_t)iss + 2u - gt % 2u) % 2u); t < ntiles; t += 2) {
           const uint32_t g = gt + (uint32_t)t;
           const int st = g % kTcStages, buf = g % kTcBufs;
           if (!mbar_wait(&full[st], (g / kTcStages) & 1u, abort_flag) ||
@@ -334,10 +403,10 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
           issued = t + 1;
         }
         if (issued > 0) {
-          // all MMAs of this item complete before the row operands are rewritten
-          // (next item) or TMEM is released (end)
-          tc_commit(drain);
-          mbar_wait(drain, ndrain & 1u, nullptr);
+          // all MMAs of this issuer in this item complete before the row operands are
+          // rewritten (next item) or TMEM is released (end)
+          tc_commit(&drain[iss]);
+          mbar_wait(&drain[iss], ndrain & 1u, nullptr);
           ++ndrain;
         }
       }
@@ -362,7 +431,8 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
       for (int t = t0; t < ntiles; t += kTcBufs) {
         const uint32_t gg = gt + (uint32_t)t;
         const uint32_t ph = (gg / kTcBufs) & 1u;
-        if (!mbar_wait(&tfull[cg], ph, abort_flag) || !mbar_wait(&wfull[cg], ph, abort_flag)) {
+        const int ws = gg % kTcWStages;
+        if (!mbar_wait(&tfull[cg], ph, abort_flag) || !mbar_wait(&wfull[ws], (gg / kTcWStages) & 1u, abort_flag)) {
           *abort_flag = 1;
           tc_note_timeout(a.err, 3);
           break;
@@ -374,7 +444,13 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
           uint32_t u[32];
           TMEM_LD32(tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)(cg * kTcN + cc * 32), u);
           TMEM_WAIT32(u);
-          const float* wst = sw + cg * kTcWArrays * kTcN + cc * 32;
+          if (cc == kTcN / 32 - 1) {
+            // the last load of the tile has landed: the distance buffer is free for the next MMA
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[cg]);
+          }
+          const float* wst = sw + ws * kTcWArrays * kTcN + cc * 32;
           const int64_t jb = c0 + (int64_t)t * kTcN + cc * 32;
           const bool self_here = gi >= jb && gi < jb + 32;
           if (__any_sync(0xffffffffu, self_here)) {
@@ -390,17 +466,18 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
               float4 l4 = w4, t4 = w4;
               if (KERN != ADASAP_RBF) l4 = *reinterpret_cast<const float4*>(wst + kTcN + 4 * i4);
               if (KERN == ADASAP_MATERN52) t4 = *reinterpret_cast<const float4*>(wst + 2 * kTcN + 4 * i4);
-              tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 0]), w4.x, l4.x, t4.x, tacc);
-              tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 1]), w4.y, l4.y, t4.y, tacc);
-              tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 2]), w4.z, l4.z, t4.z, tacc);
-              tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 3]), w4.w, l4.w, t4.w, tacc);
+              // entry 4 i4 + e of the chunk; (4 i4 + e) % 8 < sqrt_fma_per8 takes the FMA-pipe sqrt
+              const int h = 4 * (i4 & 1);
+              tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 0]), w4.x, l4.x, t4.x, tacc, h + 0 < sqrt_fma_per8<KERN>());
+              tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 1]), w4.y, l4.y, t4.y, tacc, h + 1 < sqrt_fma_per8<KERN>());
+              tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 2]), w4.z, l4.z, t4.z, tacc, h + 2 < sqrt_fma_per8<KERN>());
+              tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 3]), w4.w, l4.w, t4.w, tacc, h + 3 < sqrt_fma_per8<KERN>());
             }
           }
         }
-        // the distance buffer and the w stage of this tile are free again
-        tc_fence_before();
+        // the w stage of this tile is free again
         __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty[cg]);
+        if (lane == 0) mbar_arrive(&wempty[ws]);
         const float y = tacc - cmp;
         const float tt = acc + y;
         cmp = (tt - acc) - y;
@@ -457,8 +534,36 @@ __global__ void k_build_tc(const float* __restrict__ X, const float* __restrict_
   }
 }
 
+// w per 128-column tile (see launch_prep_w): A arrays of 128 floats per tile
+template <int A>
+__global__ void k_prep_w(const float* __restrict__ w, int64_t ldw, int64_t ncols, int64_t npad,
+                         float* __restrict__ wp) {
+  const float il = 1.0f / kLog2e, i3 = 1.0f / (3.0f * kLog2e * kLog2e);
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < npad; j += (int64_t)gridDim.x * blockDim.x) {
+    const float v = j < ncols ? w[j * ldw] : 0.0f;
+    float* o = wp + (j / kTcN) * (A * kTcN) + (j % kTcN);
+    o[0] = v;
+    if (A == 3) {
+      o[kTcN] = v * il;
+      o[2 * kTcN] = v * i3;
+    }
+  }
+}
+
 int tc_kp(int d) { return d + 2 <= 16 ? 16 : (d + 2 <= 32 ? 32 : 0); }
 int64_t tc_npad(int64_t n) { return (n + kTcN - 1) / kTcN * kTcN; }
+
+int64_t tc_wprep_floats(int64_t ncols, int kern) {
+  return tc_npad(ncols) * (kern == ADASAP_RBF ? 1 : kTcWArrays);
+}
+
+cudaError_t launch_prep_w(int kern, const float* w, int64_t ldw, int64_t ncols, float* wp, cudaStream_t st) {
+  const int64_t npad = tc_npad(ncols);
+  const int blocks = (int)std::min<int64_t>((npad + 255) / 256, 148 * 8);
+  if (kern == ADASAP_RBF) k_prep_w<1><<<blocks, 256, 0, st>>>(w, ldw, ncols, npad, wp);
+  else k_prep_w<kTcWArrays><<<blocks, 256, 0, st>>>(w, ldw, ncols, npad, wp);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_build_tc(const float* X, const float* q, const int* gidx, int64_t n, int d, int dp, float* hi,
                             float* lo, cudaStream_t st) {
@@ -618,6 +723,7 @@ TcArgs make_tc_args(int d, const float* xr, const float* qr, const int* ridx, in
   a.cps = (tiles + nsplit - 1) / nsplit * kTcN;
   a.nsplit = nsplit;
   a.flat = 0;
+  a.wp = nullptr;
   return a;
 }
 
@@ -626,9 +732,10 @@ int64_t tc_items(const TcArgs& a) { return (a.m + kTcM - 1) / kTcM * (int64_t)a.
 cudaError_t launch_rows_tc(int kern, int d, const float* xr, const float* qr, const int* ridx, int64_t m, int dp,
                            const float* bhi, const float* blo, int64_t ncols, int self_mode, const float* w,
                            int64_t ldw, float* part, int nsplit, float sigma2, int* err, cudaStream_t st,
-                           int max_ctas) {
+                           int max_ctas, const float* wp) {
   if (m <= 0 || ncols <= 0) return cudaSuccess;
   TcArgs a = make_tc_args(d, xr, qr, ridx, m, dp, bhi, blo, ncols, self_mode, w, ldw, part, nsplit, sigma2, err);
+  a.wp = wp;
   const int slots = (max_ctas > 0 && max_ctas < tc_slots()) ? max_ctas : tc_slots();
   int ctas = (int)std::min<int64_t>(tc_items(a), slots);
   // the flat schedule when the caller's slot count is the one it needs (either

@@ -40,7 +40,7 @@ struct RowsPlan {
   int passes;  // contraction MMAs of the multi-RHS kernel: 3 (split W and K) or 1 (TF32)
   int nsplit;
   int ctas;    // persistent CTAs of the tensor-core kernel (0: one per SM)
-  int64_t wop_floats;  // W operand scratch (hi + lo) of the multi-RHS kernel
+  int64_t wop_floats;  // W operand scratch: hi + lo of the multi-RHS kernel, or the tile-prepared w
 };
 
 // SMs left to the factorisation branch while Step I runs (its launches are
@@ -310,12 +310,13 @@ RowsPlan plan_rows(const adasap_ctx* c, int64_t m, int64_t ncols, int s, int res
   p.ctas = (p.tc && reserve_sms > 0) ? std::max(1, tc_slots() - reserve_sms) : 0;
   p.nsplit = !p.tc ? rows_nsplit(m, ncols, s, c->dp, false)
                    : (p.mrhs ? tc_mrhs_nsplit(m, ncols, p.ctas) : tc_plan_nsplit(m, ncols, p.ctas));
-  p.wop_floats = p.mrhs ? 2 * tc_mrhs_wfloats(ncols, s) : 0;
+  p.wop_floats = p.mrhs ? 2 * tc_mrhs_wfloats(ncols, s) : (p.tc ? tc_wprep_floats(ncols, c->kern) : 0);
   return p;
 }
 
 // y-partials of K(rows, X') W over all n columns of the context
-// (wop: p.wop_floats of scratch for the multi-RHS kernel's W operand; w has row stride s)
+// (wop: p.wop_floats of scratch for the multi-RHS kernel's W operand, required there; for the
+// single-RHS tensor-core kernel the tile-prepared w, optional; w has row stride s)
 cudaError_t run_rows_over_x(const adasap_ctx* c, const RowsPlan& p, const float* xr, const float* qr, const int* ridx,
                             int64_t m, const float* w, int s, float* part, int self_mode, cudaStream_t st,
                             float* wop = nullptr) {
@@ -328,9 +329,14 @@ cudaError_t run_rows_over_x(const adasap_ctx* c, const RowsPlan& p, const float*
     return launch_rows_tc_mrhs(c->kern, c->d, xr, qr, ridx, m, c->dp, c->tc_hi, c->tc_lo, c->n, self_mode, whi, wlo,
                                s, p.passes, part, p.nsplit, c->sigma2, c->err_dev, st, p.ctas);
   }
-  if (p.tc)
+  if (p.tc) {
+    if (wop) {
+      cudaError_t e = launch_prep_w(c->kern, w, s, c->n, wop, st);
+      if (e != cudaSuccess) return e;
+    }
     return launch_rows_tc(c->kern, c->d, xr, qr, ridx, m, c->dp, c->tc_hi, c->tc_lo, c->n, self_mode, w, s, part,
-                          p.nsplit, c->sigma2, c->err_dev, st, p.ctas);
+                          p.nsplit, c->sigma2, c->err_dev, st, p.ctas, wop);
+  }
   return launch_rows(c->kern, c->dp, rows_over_x(c, xr, qr, ridx, m, w, s, part), s, p.nsplit, false, st);
 }
 
@@ -355,7 +361,7 @@ extern "C" adasap_status adasap_kernel_rows(adasap_ctx* c, const int64_t* B, int
   if (g != ADASAP_OK) return g;
   int* idx = (int*)c->ws;
   float* part = (float*)((char*)c->ws + idx_bytes);
-  float* wop = p.mrhs ? (float*)((char*)c->ws + idx_bytes + part_bytes) : nullptr;
+  float* wop = p.wop_floats > 0 ? (float*)((char*)c->ws + idx_bytes + part_bytes) : nullptr;
   CT(launch_index32(B, b, c->n, idx, st));
   CT(run_rows_over_x(c, p, c->Xc, c->qc, idx, b, W, s, part, 1, st, wop));
   CT(launch_reduce(part, p.nsplit, b, s, 0, s, out, s, 0.f, nullptr, nullptr, 0, 0.f, nullptr, nullptr, 0, nullptr,
@@ -372,7 +378,7 @@ extern "C" adasap_status adasap_predict(adasap_ctx* c, const float* Xtest, int64
   float* xt = ar.get<float>((size_t)m * c->dp);
   float* qt = ar.get<float>((size_t)m);
   float* part = ar.get<float>((size_t)p.nsplit * m * s);
-  float* wop = p.mrhs ? ar.get<float>((size_t)p.wop_floats) : nullptr;
+  float* wop = p.wop_floats > 0 ? ar.get<float>((size_t)p.wop_floats) : nullptr;
   if (ar.err != cudaSuccess) return ADASAP_ENOMEM;
   CT(launch_transform(Xtest, m, c->d, c->dp, c->mean_dev, c->kappa / (double)c->ell, xt, qt, st));
   CT(run_rows_over_x(c, p, xt, qt, nullptr, m, W, s, part, 0, st, wop));
@@ -400,7 +406,7 @@ extern "C" adasap_status adasap_residual(adasap_ctx* c, const float* Y, const fl
   int* idx = ar.get<int>((size_t)mb);
   float* part = ar.get<float>((size_t)p.nsplit * mb * s);
   float* res = ar.get<float>((size_t)mb * s);
-  float* wop = p.mrhs ? ar.get<float>((size_t)p.wop_floats) : nullptr;
+  float* wop = p.wop_floats > 0 ? ar.get<float>((size_t)p.wop_floats) : nullptr;
   double* sq = ar.get<double>(kReduceBlocks);
   double* acc = ar.get<double>(2);
   if (ar.err != cudaSuccess) return ADASAP_ENOMEM;
@@ -464,6 +470,12 @@ extern "C" adasap_status adasap_measure_pipes(double* out, int count, void* stre
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   CT(measure_pipes(v, (cudaStream_t)stream));
   for (int i = 0; i < count && i < 4; ++i) out[i] = v[i];
+  return ADASAP_OK;
+}
+
+extern "C" adasap_status adasap_eval_math(int fn, const float* x, int64_t n, float* out, void* stream) {
+  if ((fn != 0 && fn != 1) || n < 0 || (n > 0 && (!x || !out))) return ADASAP_EINVAL;
+  CT(launch_eval_math(fn, x, n, out, (cudaStream_t)stream));
   return ADASAP_OK;
 }
 

@@ -308,3 +308,26 @@ def test_autograd_function_gradients(lib):
     r_ell, r_s2 = gp.hypergrad(Xd, W.astype(np.float64), Gn, 1, 0.7, 1.2)
     assert abs(ell.grad.item() - r_ell) <= 1e-4 * abs(r_ell) + 1e-3
     assert abs(s2.grad.item() - r_s2) <= 1e-4 * abs(r_s2) + 1e-3
+
+
+def test_fma_pipe_sqrt_is_correctly_rounded_on_a_dense_grid(lib):
+    """The square root the Matern epilogues take on the FMA pipe (Newton steps from a
+    bit-pattern seed): within half an ulp of the correctly rounded square root on
+    2^22 points spread log-uniformly over [1e-30, 1e21] plus every float in [1, 4)
+    spaced 64 ulps apart, exactly 0 -> 1e-15 (the documented clamp), and no worse
+    than the special-function unit's sqrt.approx on the same points."""
+    g = np.random.default_rng(21)
+    x = np.exp(g.uniform(np.log(1e-30), np.log(1e21), 1 << 22)).astype(np.float32)
+    dense = np.arange(np.float32(1.0).view(np.int32), np.float32(4.0).view(np.int32), 64,
+                      dtype=np.int32).view(np.float32)
+    x = np.concatenate([x, dense])
+    xt = torch.from_numpy(x).cuda()
+    got = lib.eval_math(0, xt).cpu().numpy().astype(np.float64)
+    mufu = lib.eval_math(1, xt).cpu().numpy().astype(np.float64)
+    exact = np.sqrt(x.astype(np.float64))
+    ulp = np.spacing(exact.astype(np.float32)).astype(np.float64)
+    err = np.abs(got - exact) / ulp
+    assert err.max() <= 0.5 + 1e-3, err.max()
+    assert err.max() <= (np.abs(mufu - exact) / ulp).max() + 1e-3
+    z = lib.eval_math(0, torch.zeros(4, device="cuda")).cpu().numpy()
+    np.testing.assert_allclose(z, 1e-15, rtol=1e-6)
