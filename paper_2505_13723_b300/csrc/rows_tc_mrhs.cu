@@ -12,6 +12,13 @@
 //      128 x s_pad FP32 accumulator in TMEM:
 //        passes = 3: K_hi W_hi + K_hi W_lo + K_lo W_hi   (FP32-level accuracy)
 //        passes = 1: K_hi W_hi                           (TF32 inputs)
+// Kernel values are split into TF32 hi/lo by integer operations (tf32_split) rather
+// than cvt.rna.tf32.f32: same rounding, and measured faster (RBF, 4,096 x 262,144
+// entries, s = 64: 1.87 -> 1.63 ms with the RBF-only fast path below).  Variants
+// that kept the kernel-value chunks in TMEM as the A operand (tcgen05.st, then
+// tcgen05.mma with A in tensor memory), or split the epilogue into four warpgroups,
+// measured no faster: a TF32 MMA of M = 128, K = 8 takes about 90 clocks here, so
+// the 48 contraction MMAs of a tile set its time.
 // The accumulators span one column split (at most kMrhsMaxCols columns, the even
 // and odd tiles in two accumulators, so that the FP32 accumulation in the tensor
 // cores stays below the product's tolerance even for sums of one sign); the
@@ -19,9 +26,9 @@
 //
 // CTA = 128 rows, 384 threads, one CTA per SM, persistent over (row tile,
 // split) items like rows_tc.cu:
-//   warp 0       producer: bulk copies of the column operand tiles (2-stage
-//                ring) and of the W chunks (2-slot ring), in the order the MMAs
-//                consume them
+//   warp 0       producer: bulk copies of the column operand tiles (1- or
+//                2-stage ring) and of the W chunks (2-slot ring), in the order the
+//                MMAs consume them
 //   warp 1       TMEM owner and MMA issuer: distance MMAs one tile ahead of
 //                the contraction MMAs of the previous tile
 //   warps 4..11  epilogue: warpgroup g forms chunks 2g, 2g + 1 of every tile in
@@ -68,6 +75,7 @@ struct MrhsArgs {
   int s, sp;           // right-hand sides and the padded accumulator width (multiple of 16)
   int passes;          // 3 (split) or 1
   int nks;             // K chunk slots per epilogue warpgroup (1 or 2)
+  int nx;              // column operand stages (1 or 2)
   float* part;         // nsplit x m x s
   int64_t cps;         // columns per split (multiple of 128)
   int nsplit;
@@ -78,12 +86,12 @@ struct MrhsArgs {
 // Shared-memory plan (bytes from a 128-byte aligned base)
 struct MrhsSmem {
   size_t a, x, k, kslot, w, bars, total;   // kslot: floats per K slot
-  __host__ __device__ MrhsSmem(int kp, int sp, int passes, int nks) {
+  __host__ __device__ MrhsSmem(int kp, int sp, int passes, int nks, int nx = 2) {
     const size_t opf = (size_t)kTcM * kp * sizeof(float);
     kslot = (size_t)(passes == 3 ? 2 : 1) * kTcM * kCh;
     a = 0;                                                      // row operands hi, lo
     x = a + 2 * opf;                                            // [2 stages][hi, lo] column tiles
-    k = x + 4 * opf;                                            // [2 nks slots][hi(, lo)] 128 x 32 chunks
+    k = x + (size_t)2 * nx * opf;                               // [2 nks slots][hi(, lo)] 128 x 32 chunks
     w = k + (size_t)2 * nks * kslot * sizeof(float);            // [kWSlots][hi, lo] sp x 32 chunks
     bars = w + (size_t)kWSlots * 2 * sp * kCh * sizeof(float);
     total = bars + 32 * sizeof(uint64_t) + 64 + 128;
@@ -95,7 +103,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc_mrhs(MrhsArgs a) {
   constexpr int OPF = kTcM * KP;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
-  const MrhsSmem L(KP, a.sp, a.passes, a.nks);
+  const MrhsSmem L(KP, a.sp, a.passes, a.nks, a.nx);
   float* sAhi = reinterpret_cast<float*>(base + L.a);
   float* sAlo = sAhi + OPF;
   float* sX = reinterpret_cast<float*>(base + L.x);   // [st][hi, lo][OPF]
@@ -194,8 +202,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc_mrhs(MrhsArgs a) {
         bool ok = true;
         auto issue_x = [&](int t) -> bool {
           const uint32_t g = gt + (uint32_t)t;
-          const int st = g & 1;
-          if (!mbar_wait(&empty[st], ((g >> 1) & 1u) ^ 1u, abort_flag)) {
+          const int st = (int)(g % (uint32_t)a.nx);
+          if (!mbar_wait(&empty[st], ((g / (uint32_t)a.nx) & 1u) ^ 1u, abort_flag)) {
             tc_note_timeout(a.err, 11);
             return false;
           }
@@ -229,9 +237,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc_mrhs(MrhsArgs a) {
         if (!ok) {
           *abort_flag = 1;
           // our copies still write shared memory: wait (bounded) for the last of each ring
-          for (int t = max(0, xi - 2); t < xi; ++t) {
+          for (int t = max(0, xi - a.nx); t < xi; ++t) {
             const uint32_t g = gt + (uint32_t)t;
-            mbar_wait(&full[g & 1], (g >> 1) & 1u, nullptr);
+            mbar_wait(&full[g % (uint32_t)a.nx], (g / (uint32_t)a.nx) & 1u, nullptr);
           }
           for (int64_t k = (wi > 2 ? wi - 2 : 0); k < wi; ++k) {
             const uint32_t q = gt * kChPerTile + (uint32_t)k;
@@ -246,9 +254,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc_mrhs(MrhsArgs a) {
         uint32_t acc_flag[2] = {0u, 0u};
         auto issue_dist = [&](int t) -> bool {
           const uint32_t g = gt + (uint32_t)t;
-          const int st = g & 1, buf = g & 1;
+          const int st = (int)(g % (uint32_t)a.nx), buf = g & 1;
           const uint32_t ph = (g >> 1) & 1u;
-          if (!mbar_wait(&full[st], ph, abort_flag) || !mbar_wait(&tempty[buf], ph ^ 1u, abort_flag)) {
+          if (!mbar_wait(&full[st], (g / (uint32_t)a.nx) & 1u, abort_flag) ||
+              !mbar_wait(&tempty[buf], ph ^ 1u, abort_flag)) {
             tc_note_timeout(a.err, 13);
             return false;
           }
@@ -370,20 +379,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc_mrhs(MrhsArgs a) {
           float* khi = sK + sl * L.kslot;
           float* klo = khi + kTcM * kCh;
           const uint32_t* u = h ? u1 : u0;
+          // RBF chunks without the row's own column skip the per-entry test and clamp (the
+          // RBF term needs no clamp); the Matern chunks keep them (measured faster there)
+          const bool fast = KERN == ADASAP_RBF && !__any_sync(0xffffffffu, gi >= jb && gi < jb + kCh);
+          if (fast) {
 #pragma unroll
-          for (int k4 = 0; k4 < kCh / 4; ++k4) {
-            float kv[4], hv[4], lv[4];
+            for (int k4 = 0; k4 < kCh / 4; ++k4) {
+              float hv[4], lv[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int k = 4 * k4 + e;
-              const float uu = (jb + k == gi) ? 0.0f : fmaxf(__uint_as_float(u[k]), 0.0f);
-              kv[e] = kval<KERN>(uu);
-              hv[e] = tf32_round(kv[e]);
-              lv[e] = tf32_round(kv[e] - hv[e]);
+              for (int e = 0; e < 4; ++e) tf32_split(kval<KERN>(__uint_as_float(u[4 * k4 + e])), hv[e], lv[e]);
+              const int off = (rl >> 3) * (8 * kCh) + k4 * 32 + (rl & 7) * 4;
+              *reinterpret_cast<float4*>(khi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+              if (a.passes == 3) *reinterpret_cast<float4*>(klo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
             }
-            const int off = (rl >> 3) * (8 * kCh) + k4 * 32 + (rl & 7) * 4;
-            *reinterpret_cast<float4*>(khi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-            if (a.passes == 3) *reinterpret_cast<float4*>(klo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+          } else {
+#pragma unroll
+            for (int k4 = 0; k4 < kCh / 4; ++k4) {
+              float hv[4], lv[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const int k = 4 * k4 + e;
+                const float uu = (jb + k == gi) ? 0.0f : fmaxf(__uint_as_float(u[k]), 0.0f);
+                tf32_split(kval<KERN>(uu), hv[e], lv[e]);
+              }
+              const int off = (rl >> 3) * (8 * kCh) + k4 * 32 + (rl & 7) * 4;
+              *reinterpret_cast<float4*>(khi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+              if (a.passes == 3) *reinterpret_cast<float4*>(klo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+            }
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           __syncwarp();
@@ -520,7 +542,13 @@ cudaError_t launch_rows_tc_mrhs(int kern, int d, const float* xr, const float* q
   a.bhi = bhi; a.blo = blo; a.ncols = ncols; a.self_mode = self_mode;
   a.whi = whi; a.wlo = wlo; a.s = s; a.sp = tc_mrhs_sp(s); a.passes = passes;
   const int kp = tc_kp(d);
-  a.nks = MrhsSmem(kp, a.sp, passes, 2).total <= kMrhsSmemMax ? 2 : 1;
+  // two K slots per warpgroup (the epilogue writes a tile's second chunk while the
+  // MMAs read the first) before a second column-operand stage (a contraction tile is
+  // long enough to reload the one stage behind the distance MMA)
+  a.nks = 2;
+  a.nx = 2;
+  if (MrhsSmem(kp, a.sp, passes, 2, 2).total > kMrhsSmemMax) a.nx = 1;
+  if (MrhsSmem(kp, a.sp, passes, 2, 1).total > kMrhsSmemMax) a.nks = 1, a.nx = 2;
   a.part = part; a.sigma2 = sigma2; a.err = err;
   const int64_t tiles = (ncols + kTcN - 1) / kTcN;
   a.cps = (tiles + nsplit - 1) / nsplit * kTcN;
@@ -528,7 +556,7 @@ cudaError_t launch_rows_tc_mrhs(int kern, int d, const float* xr, const float* q
   const int64_t nitems = (m + kTcM - 1) / kTcM * (int64_t)nsplit;
   const int slots = (max_ctas > 0 && max_ctas < tc_slots()) ? max_ctas : tc_slots();
   const int ctas = (int)std::min<int64_t>(nitems, slots);
-  const size_t smem = MrhsSmem(kp, a.sp, passes, a.nks).total;
+  const size_t smem = MrhsSmem(kp, a.sp, passes, a.nks, a.nx).total;
 #define ADASAP_MRHS(KE, KPV) k_rows_tc_mrhs<KE, KPV><<<ctas, kTcThreads, smem, st>>>(a)
   if (kp == 16) {
     if (kern == 0) ADASAP_MRHS(0, 16);

@@ -115,6 +115,16 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(y);
 }
 
+// x = hi + lo with hi and lo TF32 values, each rounded to nearest (ties away from
+// zero, as cvt.rna.tf32.f32) by integer operations on the bit pattern: adding half
+// of the 13 dropped bits' unit to the magnitude and clearing them rounds it (a
+// carry into the exponent is the correct rounding); lo = x - hi is exact and is
+// rounded the same way.  For finite x.
+__device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
+  hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
+  lo = __uint_as_float((__float_as_uint(x - hi) + 0x1000u) & 0xffffe000u);
+}
+
 // float offset of element (row, k) in the no-swizzle K-major layout
 template <int KP>
 __host__ __device__ __forceinline__ int64_t tc_off(int64_t row, int k) {

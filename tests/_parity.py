@@ -145,4 +145,4 @@ def check(test, items, recorded=None):
         rows.append((quantity, observed, sens, tol, cap))
     bad = [r for r in rows if not (r[1] < r[3])]   # NaN fails
     assert not bad, "; ".join("%s %s: observed %.3g >= tol %.3g (oracle sensitivity %.3g, cap %.3g)"
-                              % ((test,) + r) for r in bad)
+                              % (test, q, obs, tol, sens, cap) for q, obs, sens, tol, cap in bad)
