@@ -79,6 +79,10 @@ struct TcSmem {
 // moved sqrt.  Measured on the Step I launch (10^4 x 2^20 entries): Matern-3/2
 // 4.02 ms at k = 0, 3.85 at k = 1, 4.03 at k = 2; Matern-5/2, whose epilogue
 // issues more instructions per entry, 4.14 at k = 0 and 1 and slower above.
+// With the Newton steps of two entries packed into f32x2 instructions (half the
+// issue cost per moved sqrt) k = 2 measured 3.84 against 3.86 ms and k = 3, 4
+// slower: past one in eight the kernel is not bound by one pipe but by how well
+// its 4 epilogue warps per scheduler hide the special-function latency.
 template <int KERN>
 __host__ __device__ constexpr int sqrt_fma_per8() { return KERN == ADASAP_MATERN32 ? 1 : 0; }
 
@@ -99,6 +103,132 @@ __device__ __forceinline__ float tc_term(float v, float w, float wl, float w3, f
   const float e = ex2_approx(-ap);
   if (KERN == ADASAP_MATERN32) return fmaf(e, fmaf(ap, wl, w), acc);
   return fmaf(e, fmaf(ap, fmaf(ap, w3, wl), w), acc);
+}
+
+// Epilogue of one 128 x 128 distance tile for one warp: its 32 rows (one TMEM lane
+// quadrant, tq) against the tile's 128 columns, as four 32-column TMEM loads; the
+// tile's w arrays start at wt.  After the last load has landed the distance
+// buffer is released to the MMA issuers (tempty).  Returns this thread's sum of
+// k(u) w / sigma2 over the tile.
+//
+// RBF takes one of two forms per tile, chosen by one vote of the warp:
+// Fast form: no column of the tile is a row's own point, so every entry goes
+// through tc_term unchanged, summed into four independent chains (with one
+// special-function op and one FMA per entry, a single chain leaves the FMA
+// latency exposed), two loads' worth of code unrolled.  Against a test of
+// every 32-column chunk this cut the instructions per entry from 4.25 to 3.6
+// and the Step I launch (10^4 x 2^20 entries) from 2.05 to 1.72 ms.
+template <int KERN>
+__host__ __device__ constexpr int tc_fast_chains() { return KERN == ADASAP_RBF ? 4 : 1; }
+
+template <int KERN>
+__device__ __forceinline__ float tc_tile_fast(uint32_t tq, const float* __restrict__ wt, uint64_t* tempty_bar,
+                                              int lane) {
+  constexpr int NC = tc_fast_chains<KERN>();
+  float ta[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll(KERN == ADASAP_RBF ? 2 : 1)
+  for (int cc = 0; cc < kTcN / 32; ++cc) {
+    uint32_t u[32];
+    TMEM_LD32(tq + (uint32_t)(cc * 32), u);
+    TMEM_WAIT32(u);
+    if (cc == kTcN / 32 - 1) {
+      // the last load of the tile has landed: the distance buffer is free for the next MMA
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty_bar);
+    }
+    const float* wst = wt + cc * 32;
+#pragma unroll
+    for (int i4 = 0; i4 < 8; ++i4) {
+      const float4 w4 = *reinterpret_cast<const float4*>(wst + 4 * i4);
+      float4 l4 = w4, t4 = w4;
+      if (KERN != ADASAP_RBF) l4 = *reinterpret_cast<const float4*>(wst + kTcN + 4 * i4);
+      if (KERN == ADASAP_MATERN52) t4 = *reinterpret_cast<const float4*>(wst + 2 * kTcN + 4 * i4);
+      // entry 4 i4 + e of the chunk; (4 i4 + e) % 8 < sqrt_fma_per8 takes the FMA-pipe sqrt
+      const int h = 4 * (i4 & 1);
+      ta[0 % NC] = tc_term<KERN>(__uint_as_float(u[4 * i4 + 0]), w4.x, l4.x, t4.x, ta[0 % NC], h + 0 < sqrt_fma_per8<KERN>());
+      ta[1 % NC] = tc_term<KERN>(__uint_as_float(u[4 * i4 + 1]), w4.y, l4.y, t4.y, ta[1 % NC], h + 1 < sqrt_fma_per8<KERN>());
+      ta[2 % NC] = tc_term<KERN>(__uint_as_float(u[4 * i4 + 2]), w4.z, l4.z, t4.z, ta[2 % NC], h + 2 < sqrt_fma_per8<KERN>());
+      ta[3 % NC] = tc_term<KERN>(__uint_as_float(u[4 * i4 + 3]), w4.w, l4.w, t4.w, ta[3 % NC], h + 3 < sqrt_fma_per8<KERN>());
+    }
+  }
+  return NC == 1 ? ta[0] : (ta[0] + ta[1]) + (ta[2] + ta[3]);
+}
+
+// Self form: the tile holds the own point gi (a global column index, -1 for none)
+// of at least one of the warp's rows; that entry is taken at u = 0 exactly (the
+// split distance leaves a rounding residue of about 2^-22 (q_i + q_j) there).
+// Such tiles are rare: one row tile in ctiles for a product of a point set with
+// itself, about 32 * 128 / n of the tiles for gathered rows against all n points.
+template <int KERN>
+__device__ __forceinline__ float tc_tile_self(uint32_t tq, const float* __restrict__ wt, uint64_t* tempty_bar,
+                                           int lane, int64_t jt, int64_t gi) {
+  float ta = 0.0f;
+#pragma unroll 1
+  for (int cc = 0; cc < kTcN / 32; ++cc) {
+    uint32_t u[32];
+    TMEM_LD32(tq + (uint32_t)(cc * 32), u);
+    TMEM_WAIT32(u);
+    if (cc == kTcN / 32 - 1) {
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty_bar);
+    }
+    const float* wst = wt + cc * 32;
+    const int64_t jb = jt + cc * 32;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const float v = (jb + i == gi) ? 0.0f : __uint_as_float(u[i]);
+      ta = tc_term<KERN>(v, wst[i], wst[kTcN + i], wst[2 * kTcN + i], ta);
+    }
+  }
+  return ta;
+}
+
+// Matern epilogues: one chain and a test of every 32-column chunk for the rows'
+// own points (same u = 0 rule).  Their two special-function ops per entry hide
+// the chain's latency, and this form measured faster for them than the
+// per-tile choice above (Matern-3/2 Step I, 10^4 x 2^20 entries: 3.87 against
+// 4.07 ms).
+template <int KERN>
+__device__ __forceinline__ float tc_tile_chunked(uint32_t tq, const float* __restrict__ wt, uint64_t* tempty_bar,
+                                                 int lane, int64_t jt, int64_t gi) {
+  float ta = 0.0f;
+#pragma unroll 1
+  for (int cc = 0; cc < kTcN / 32; ++cc) {
+    uint32_t u[32];
+    TMEM_LD32(tq + (uint32_t)(cc * 32), u);
+    TMEM_WAIT32(u);
+    if (cc == kTcN / 32 - 1) {
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty_bar);
+    }
+    const float* wst = wt + cc * 32;
+    const int64_t jb = jt + cc * 32;
+    if (__any_sync(0xffffffffu, gi >= jb && gi < jb + 32)) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const float v = (jb + i == gi) ? 0.0f : __uint_as_float(u[i]);
+        ta = tc_term<KERN>(v, wst[i], wst[kTcN + i], wst[2 * kTcN + i], ta);
+      }
+    } else {
+#pragma unroll
+      for (int i4 = 0; i4 < 8; ++i4) {
+        const float4 w4 = *reinterpret_cast<const float4*>(wst + 4 * i4);
+        const float4 l4 = *reinterpret_cast<const float4*>(wst + kTcN + 4 * i4);
+        float4 t4 = w4;
+        if (KERN == ADASAP_MATERN52) t4 = *reinterpret_cast<const float4*>(wst + 2 * kTcN + 4 * i4);
+        // entry 4 i4 + e of the chunk; (4 i4 + e) % 8 < sqrt_fma_per8 takes the FMA-pipe sqrt
+        const int h = 4 * (i4 & 1);
+        ta = tc_term<KERN>(__uint_as_float(u[4 * i4 + 0]), w4.x, l4.x, t4.x, ta, h + 0 < sqrt_fma_per8<KERN>());
+        ta = tc_term<KERN>(__uint_as_float(u[4 * i4 + 1]), w4.y, l4.y, t4.y, ta, h + 1 < sqrt_fma_per8<KERN>());
+        ta = tc_term<KERN>(__uint_as_float(u[4 * i4 + 2]), w4.z, l4.z, t4.z, ta, h + 2 < sqrt_fma_per8<KERN>());
+        ta = tc_term<KERN>(__uint_as_float(u[4 * i4 + 3]), w4.w, l4.w, t4.w, ta, h + 3 < sqrt_fma_per8<KERN>());
+      }
+    }
+  }
+  return ta;
 }
 
 // One run of the flat schedule: CTA x of G takes the flattened tiles
@@ -438,42 +568,16 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
           break;
         }
         tc_fence_after();
-        float tacc = 0.0f;
-#pragma unroll 1
-        for (int cc = 0; cc < kTcN / 32; ++cc) {
-          uint32_t u[32];
-          TMEM_LD32(tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)(cg * kTcN + cc * 32), u);
-          TMEM_WAIT32(u);
-          if (cc == kTcN / 32 - 1) {
-            // the last load of the tile has landed: the distance buffer is free for the next MMA
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[cg]);
-          }
-          const float* wst = sw + ws * kTcWArrays * kTcN + cc * 32;
-          const int64_t jb = c0 + (int64_t)t * kTcN + cc * 32;
-          const bool self_here = gi >= jb && gi < jb + 32;
-          if (__any_sync(0xffffffffu, self_here)) {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const float v = (jb + i == gi) ? 0.0f : __uint_as_float(u[i]);
-              tacc = tc_term<KERN>(v, wst[i], wst[kTcN + i], wst[2 * kTcN + i], tacc);
-            }
-          } else {
-#pragma unroll
-            for (int i4 = 0; i4 < 8; ++i4) {
-              const float4 w4 = *reinterpret_cast<const float4*>(wst + 4 * i4);
-              float4 l4 = w4, t4 = w4;
-              if (KERN != ADASAP_RBF) l4 = *reinterpret_cast<const float4*>(wst + kTcN + 4 * i4);
-              if (KERN == ADASAP_MATERN52) t4 = *reinterpret_cast<const float4*>(wst + 2 * kTcN + 4 * i4);
-              // entry 4 i4 + e of the chunk; (4 i4 + e) % 8 < sqrt_fma_per8 takes the FMA-pipe sqrt
-              const int h = 4 * (i4 & 1);
-              tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 0]), w4.x, l4.x, t4.x, tacc, h + 0 < sqrt_fma_per8<KERN>());
-              tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 1]), w4.y, l4.y, t4.y, tacc, h + 1 < sqrt_fma_per8<KERN>());
-              tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 2]), w4.z, l4.z, t4.z, tacc, h + 2 < sqrt_fma_per8<KERN>());
-              tacc = tc_term<KERN>(__uint_as_float(u[4 * i4 + 3]), w4.w, l4.w, t4.w, tacc, h + 3 < sqrt_fma_per8<KERN>());
-            }
-          }
+        const uint32_t tq = tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)(cg * kTcN);
+        const float* wt = sw + ws * kTcWArrays * kTcN;
+        const int64_t jt = c0 + (int64_t)t * kTcN;
+        float tacc;
+        if (KERN == ADASAP_RBF) {
+          // one vote per tile decides whether any of the warp's rows meets its own point here
+          tacc = __any_sync(0xffffffffu, gi >= jt && gi < jt + kTcN) ? tc_tile_self<KERN>(tq, wt, &tempty[cg], lane, jt, gi)
+                                                                     : tc_tile_fast<KERN>(tq, wt, &tempty[cg], lane);
+        } else {
+          tacc = tc_tile_chunked<KERN>(tq, wt, &tempty[cg], lane, jt, gi);
         }
         // the w stage of this tile is free again
         __syncwarp();
