@@ -182,6 +182,37 @@ constexpr int kWaitSelfTestCode = 99;
 cudaError_t launch_wait_selftest(uint64_t limit_ns, int* err, cudaStream_t st);
 
 // ---- sampler (Philox4x32-10; definitions in sampler.cu) -------------------------
+// Inputs of one iteration of one system, in one launch (k_head_prep): the
+// block B (Feistel sample), its gathered rows and tensor-core operands, the
+// start vector v0, Omega_t (copied from the buffer it was prepared in one
+// iteration ahead) and the sketch's split B operand from Omega_t.  Each part
+// has the same arithmetic as its own kernel (launch_sample_block, tag 1;
+// launch_normals, tag 3; launch_gather; launch_build_tc; launch_build_w_tc,
+// three passes).  A table of these, one per system, is launched at once with
+// blockIdx.y selecting the system.
+struct HeadPrepArgs {
+  uint64_t seed;
+  const long long* t_dev;   // iteration counter
+  int64_t n, b, npad;       // points, block size, tc_npad(b)
+  int h;                    // Feistel half width for n
+  int d, dp, r, sp;         // sp = tc_mrhs_sp(r)
+  const float* Xc;
+  const float* qc;
+  int* B32;
+  float* XB;
+  float* qB;
+  float* XBhi;
+  float* XBlo;
+  float* v0;
+  const float* OmN;
+  float* Om;
+  float* whi;
+  float* wlo;
+};
+int64_t head_prep_work(const HeadPrepArgs& a);   // work items of one system
+// tab: device array of nsys entries, all with tc_kp(d) == kp
+cudaError_t launch_head_prep(const HeadPrepArgs* tab, int nsys, int kp, int64_t max_work, cudaStream_t st);
+int feistel_half_width(int64_t n);
 cudaError_t launch_sample_block(uint64_t seed, const long long* t_dev, int64_t t_host, int64_t n,
                                 int64_t b, int stream_tag, int* B32, int64_t* B64, cudaStream_t st);
 // Iteration counter of the draw: (*t_dev if t_dev else 0) + t_host.

@@ -43,6 +43,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "prep.cuh"
 #include "tc_ptx.cuh"
 
 namespace adasap {
@@ -618,23 +619,8 @@ template <int KP>
 __global__ void k_build_tc(const float* __restrict__ X, const float* __restrict__ q, const int* __restrict__ gidx,
                            int64_t n, int64_t npad, int d, int dp, float* __restrict__ hi, float* __restrict__ lo) {
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < npad; j += (int64_t)gridDim.x * blockDim.x) {
-    float bv[KP];
-#pragma unroll
-    for (int k = 0; k < KP; ++k) bv[k] = 0.0f;
-    if (j < n) {
-      const int64_t src = gidx ? (int64_t)max(gidx[j], 0) : j;
-      for (int k = 0; k < d; ++k) bv[k] = X[src * dp + k];
-      bv[d + 1] = q[src];
-    } else {
-      bv[d + 1] = 1e20f;
-    }
-    bv[d] = 1.0f;
-#pragma unroll
-    for (int k = 0; k < KP; ++k) {
-      const float h = tf32_round(bv[k]);
-      hi[tc_off<KP>(j, k)] = h;
-      lo[tc_off<KP>(j, k)] = tf32_round(bv[k] - h);
-    }
+    const int64_t src = j < n ? (gidx ? (int64_t)max(gidx[j], 0) : j) : -1;
+    build_tc_row<KP>(X, q, src, d, dp, j, hi, lo);
   }
 }
 

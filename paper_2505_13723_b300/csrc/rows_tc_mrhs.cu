@@ -40,6 +40,7 @@
 // raises the error flag, drains its copies and MMAs, frees TMEM and writes NaN.
 #include <algorithm>
 
+#include "prep.cuh"
 #include "tc_ptx.cuh"
 
 namespace adasap {
@@ -47,6 +48,7 @@ namespace adasap {
 namespace {
 
 constexpr int kCh = 32;                     // columns per contraction chunk
+static_assert(kCh == 32, "build_w_elem lays out chunks of 32 rows");
 constexpr int kChPerTile = kTcN / kCh;      // 4
 constexpr int kWSlots = 2;                  // W chunk ring
 // K chunk slots: one or two per epilogue warpgroup (two where shared memory allows:
@@ -470,11 +472,7 @@ __global__ void k_build_w_tc(const float* __restrict__ W, int64_t ldw, int64_t n
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = e / sp;
     const int c = (int)(e - j * sp);
-    const float v = (j < n && c < s) ? W[j * ldw + c] : 0.0f;
-    const float h = tf32_round(v);
-    const int64_t off = (j / kCh) * (int64_t)sp * kCh + tc_off<kCh>(c, (int)(j % kCh));
-    whi[off] = h;
-    if (passes == 3) wlo[off] = tf32_round(v - h);
+    build_w_elem((j < n && c < s) ? W[j * ldw + c] : 0.0f, j, c, sp, passes, whi, wlo);
   }
 }
 

@@ -21,57 +21,18 @@
 #include <algorithm>
 
 #include "internal.cuh"
+#include "prep.cuh"
 
 namespace adasap {
-
-__host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
-  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
-#pragma unroll
-  for (int rnd = 0; rnd < 10; ++rnd) {
-    if (rnd > 0) {
-      k.x += 0x9E3779B9u;
-      k.y += 0xBB67AE85u;
-    }
-    const uint64_t p0 = (uint64_t)M0 * c.x;
-    const uint64_t p1 = (uint64_t)M1 * c.z;
-    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
-    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
-    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-  }
-  return c;
-}
-
-__device__ __forceinline__ uint2 seed_key(uint64_t seed) {
-  return make_uint2((uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32));
-}
-
-static int feistel_half_bits(int64_t n) {
-  int k = 2;
-  while (k < 62 && (1LL << k) < n) ++k;
-  return (k + 1) / 2;
-}
 
 __global__ void k_sample_block(uint64_t seed, const long long* __restrict__ t_dev, int64_t t_host, int64_t n,
                                int64_t b, int h, int tag, int* __restrict__ B32, int64_t* __restrict__ B64) {
   const uint32_t t = (uint32_t)(t_dev ? *t_dev : t_host);
   const uint2 key = seed_key(seed);
-  const uint32_t mask = (h >= 32) ? 0xFFFFFFFFu : ((1u << h) - 1u);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b; i += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t x = (uint64_t)i;
-    // every step applies the bijection of [0, 2^(2h)); the walk returns below n
-    // within the cycle of i, so it terminates
-    do {
-      uint32_t L = (uint32_t)(x >> h) & mask, R = (uint32_t)x & mask;
-      for (uint32_t j = 0; j < 4; ++j) {
-        const uint32_t F = philox4x32_10(make_uint4(R, t, j, (uint32_t)tag), key).x & mask;
-        const uint32_t nl = R;
-        R = L ^ F;
-        L = nl;
-      }
-      x = ((uint64_t)L << h) | R;
-    } while (x >= (uint64_t)n);
+    const int64_t x = feistel_index(i, n, h, t, tag, key);
     if (B32) B32[i] = (int)x;
-    if (B64) B64[i] = (int64_t)x;
+    if (B64) B64[i] = x;
   }
 }
 
@@ -90,21 +51,8 @@ __global__ void k_normals(uint64_t seed, const long long* __restrict__ t_dev, in
   const uint32_t t = (uint32_t)((t_dev ? *t_dev : 0) + t_host);
   const uint2 key = seed_key(seed);
   const int64_t nblk = (count + 3) / 4;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nblk; j += (int64_t)gridDim.x * blockDim.x) {
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)j, t, 0u, (uint32_t)tag), key);
-    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {
-      const float u0 = fmaf((float)ws[2 * p], 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-      const float u1 = fmaf((float)ws[2 * p + 1], 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-      const float rad = sqrtf(-2.0f * logf(u0));
-      float sn, cs;
-      sincospif(2.0f * u1, &sn, &cs);
-      const int64_t e0 = 4 * j + 2 * p;
-      if (e0 < count) out[e0] = scale * rad * cs;
-      if (e0 + 1 < count) out[e0 + 1] = scale * rad * sn;
-    }
-  }
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nblk; j += (int64_t)gridDim.x * blockDim.x)
+    normals4(j, t, tag, key, scale, count, out);
 }
 
 cudaError_t launch_normals(uint64_t seed, const long long* t_dev, int64_t t_host, int64_t count, int stream_tag,
@@ -161,6 +109,60 @@ cudaError_t launch_copy_schedule(const int64_t* Bs, const float* Om_s, const flo
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 8);
   k_copy_schedule<<<blocks, 256, 0, st>>>(Bs, r > 0 ? Om_s : nullptr, v0s, t_dev, n, b, std::max(r, 1), B32, Om, v0,
                                           sc);
+  return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------
+// k_head_prep: one launch for the inputs of an iteration (see HeadPrepArgs).
+// Work items of system y: rows j < npad (sample, gather and split operand of
+// row j; padding rows past b), then the (b + 3) / 4 normal quadruples of v0,
+// then the npad x sp elements of Omega_t's operand (and its copy).  The row
+// items read nothing another item writes, so no item waits for another.
+// ---------------------------------------------------------------------------
+int64_t head_prep_work(const HeadPrepArgs& a) { return a.npad + (a.b + 3) / 4 + a.npad * a.sp; }
+
+int feistel_half_width(int64_t n) { return feistel_half_bits(n); }
+
+template <int KP>
+__global__ void k_head_prep(const HeadPrepArgs* __restrict__ tab) {
+  const HeadPrepArgs a = tab[blockIdx.y];
+  const uint32_t t = (uint32_t)*a.t_dev;
+  const uint2 key = seed_key(a.seed);
+  const int64_t nrow = a.npad, nnorm = (a.b + 3) / 4;
+  const int64_t total = nrow + nnorm + a.npad * a.sp;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < nrow) {
+      int64_t src = -1;
+      if (e < a.b) {
+        src = feistel_index(e, a.n, a.h, t, 1, key);
+        a.B32[e] = (int)src;
+        const float4* xs = reinterpret_cast<const float4*>(a.Xc + src * a.dp);
+        float4* xd = reinterpret_cast<float4*>(a.XB + e * a.dp);
+        for (int k4 = 0; k4 < a.dp / 4; ++k4) xd[k4] = xs[k4];
+        a.qB[e] = a.qc[src];
+      }
+      build_tc_row<KP>(a.Xc, a.qc, src, a.d, a.dp, e, a.XBhi, a.XBlo);
+    } else if (e < nrow + nnorm) {
+      normals4(e - nrow, t, 3, key, 1.0f, a.b, a.v0);
+    } else {
+      const int64_t f = e - nrow - nnorm;
+      const int64_t j = f / a.sp;
+      const int c = (int)(f - j * a.sp);
+      const bool in = j < a.b && c < a.r;
+      const float v = in ? a.OmN[j * a.r + c] : 0.0f;
+      if (in) a.Om[j * a.r + c] = v;
+      build_w_elem(v, j, c, a.sp, 3, a.whi, a.wlo);
+    }
+  }
+}
+
+cudaError_t launch_head_prep(const HeadPrepArgs* tab, int nsys, int kp, int64_t max_work, cudaStream_t st) {
+  if (nsys <= 0 || max_work <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)std::min<int64_t>((max_work + 255) / 256, nsys > 1 ? 64 : 148 * 8), (unsigned)nsys);
+  if (kp == 16) k_head_prep<16><<<grid, 256, 0, st>>>(tab);
+  else if (kp == 32) k_head_prep<32><<<grid, 256, 0, st>>>(tab);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

@@ -510,6 +510,9 @@ struct adasap_solver {
   bool sk_tc = false;              // sketch K_BB Omega on the tensor cores (multi-RHS kernel)
   float* wop1 = nullptr;           // W operand scratch of Step I / the residual check (multi-RHS)
   float* wsk = nullptr;            // Omega operand of the sketch (hi + lo)
+  bool use_prep = false;           // the inputs of an iteration come from k_head_prep (one launch)
+  HeadPrepArgs prep{};
+  HeadPrepArgs* prep_dev = nullptr;
   float *XBhi = nullptr, *XBlo = nullptr;
   double beta = 0, gamma = 0, alpha = 0, eps = 0;
   int literal = 0;
@@ -621,6 +624,36 @@ adasap_status alloc_solver(adasap_solver* S) {
   cb.wb_coef = ar.get<float>(kMaxRank + 1);
   cb.wb_count = ar.get<unsigned int>(1);
   if (cb.wb_count && cudaMemset(cb.wb_count, 0, sizeof(unsigned int)) != cudaSuccess) return ADASAP_ECUDA;
+  // sampled block, Nystrom sketch on the tensor cores: the inputs of an iteration in one launch
+  if (!S->sched && !S->identity && S->sk_tc && S->XBhi && ar.err == cudaSuccess) {
+    HeadPrepArgs& p = S->prep;
+    p.seed = S->o.seed;
+    p.t_dev = &c->sc->t;
+    p.n = n;
+    p.b = b;
+    p.npad = tc_npad(b);
+    p.h = feistel_half_width(n);
+    p.d = c->d;
+    p.dp = c->dp;
+    p.r = r;
+    p.sp = tc_mrhs_sp(r);
+    p.Xc = c->Xc;
+    p.qc = c->qc;
+    p.B32 = S->B32;
+    p.XB = S->XB;
+    p.qB = S->qB;
+    p.XBhi = S->XBhi;
+    p.XBlo = S->XBlo;
+    p.v0 = S->v0;
+    p.OmN = S->OmN;
+    p.Om = S->Om;
+    p.whi = S->wsk;
+    p.wlo = S->wsk + tc_mrhs_wfloats(b, r);
+    S->prep_dev = ar.get<HeadPrepArgs>(1);
+    if (S->prep_dev && cudaMemcpy(S->prep_dev, &p, sizeof(p), cudaMemcpyHostToDevice) != cudaSuccess)
+      return ADASAP_ECUDA;
+    S->use_prep = S->prep_dev != nullptr;
+  }
   return ar.err == cudaSuccess ? ADASAP_OK : ADASAP_ENOMEM;
 }
 
@@ -659,7 +692,8 @@ cudaError_t next_omega(adasap_solver* S, int offset, cudaStream_t st) {
   } while (0)
 
 // sample, gather, sketch and Gram matrices; fork the factorisation branch to s1
-cudaError_t rec_head(adasap_solver* S, const int64_t* Bs, const float* v0s) {
+// (prep_done: the batch has already run this system's k_head_prep)
+cudaError_t rec_head(adasap_solver* S, const int64_t* Bs, const float* v0s, bool prep_done = false) {
   adasap_ctx* c = S->c;
   cudaStream_t s0 = c->s0, s1 = c->s1;
   const int64_t n = c->n, b = S->b;
@@ -668,20 +702,27 @@ cudaError_t rec_head(adasap_solver* S, const int64_t* Bs, const float* v0s) {
   const long long* tdev = &c->sc->t;
   // sample B, Omega, v0 (Alg. 2; Alg. 5)
   // (Omega_t was drawn and orthonormalised one iteration ahead, into OmN)
-  if (S->sched) {
-    KR(launch_copy_schedule(Bs, nullptr, v0s, tdev, n, b, r, S->B32, S->Om, S->v0, c->sc, s0));
+  if (S->use_prep) {
+    // B, the gathered rows and their operands, v0, Omega_t and its operand: one launch
+    if (!prep_done) KR(launch_head_prep(S->prep_dev, 1, c->kp, head_prep_work(S->prep), s0));
   } else {
-    KR(launch_sample_block(S->o.seed, tdev, 0, n, b, 1, S->B32, nullptr, s0));
-    KR(launch_normals(S->o.seed, tdev, 0, b, 3, 1.0f, S->v0, s0));
+    if (S->sched) {
+      KR(launch_copy_schedule(Bs, nullptr, v0s, tdev, n, b, r, S->B32, S->Om, S->v0, c->sc, s0));
+    } else {
+      KR(launch_sample_block(S->o.seed, tdev, 0, n, b, 1, S->B32, nullptr, s0));
+      KR(launch_normals(S->o.seed, tdev, 0, b, 3, 1.0f, S->v0, s0));
+    }
+    if (!S->identity) KR(cudaMemcpyAsync(S->Om, S->OmN, (size_t)b * r * sizeof(float), cudaMemcpyDeviceToDevice, s0));
+    KR(launch_gather(c->Xc, c->qc, S->B32, b, c->dp, S->XB, S->qB, s0));
   }
-  if (!S->identity) KR(cudaMemcpyAsync(S->Om, S->OmN, (size_t)b * r * sizeof(float), cudaMemcpyDeviceToDevice, s0));
-  KR(launch_gather(c->Xc, c->qc, S->B32, b, c->dp, S->XB, S->qB, s0));
   if (!S->identity) {
     // whole-GPU part of Steps II-III: sketch K_BB Omega and its Gram matrices
     if (S->sk_tc) {
-      KR(launch_build_tc(c->Xc, c->qc, S->B32, b, c->d, c->dp, S->XBhi, S->XBlo, s0));
       const int64_t wf = tc_mrhs_wfloats(b, r);
-      KR(launch_build_w_tc(S->Om, r, b, r, 3, S->wsk, S->wsk + wf, s0));
+      if (!S->use_prep) {
+        KR(launch_build_tc(c->Xc, c->qc, S->B32, b, c->d, c->dp, S->XBhi, S->XBlo, s0));
+        KR(launch_build_w_tc(S->Om, r, b, r, 3, S->wsk, S->wsk + wf, s0));
+      }
       KR(launch_rows_tc_mrhs(c->kern, c->d, S->XB, S->qB, nullptr, b, c->dp, S->XBhi, S->XBlo, b, 1, S->wsk,
                              S->wsk + wf, r, 3, S->part2, S->ns_sk, c->sigma2, c->err_dev, s0));
     } else {
@@ -879,7 +920,7 @@ cudaError_t capture_iteration(adasap_solver* S, const int64_t* Bs, const float* 
 // iteration graph is captured by the caller (one system, or a batch).
 adasap_status solver_prepare(adasap_ctx* c, const float* Y, int s, const adasap_opts* o, const int64_t* Bs,
                              const float* Oms, const float* v0s, const float* W0, cudaStream_t us,
-                             adasap_solver** out, int64_t T_sched, int reserve_sms) {
+                             adasap_solver** out, int64_t T_sched, int reserve_sms, int share = 1) {
   if (!c || !Y || !o || !out || s < 1 || s > kMaxRhs) return ADASAP_EINVAL;
   *out = nullptr;
   const int64_t n = c->n, b = o->b;
@@ -916,7 +957,12 @@ adasap_status solver_prepare(adasap_ctx* c, const float* Y, int s, const adasap_
   S->tc_pw = c->prec != ADASAP_PREC_FP32 && c->kp > 0;
   S->ns1 = S->plan1.nsplit;
   S->sk_tc = S->tc_pw && !identity && r >= 2;
-  S->ns_sk = identity ? 1 : (S->sk_tc ? tc_mrhs_nsplit(b, b) : rows_nsplit(b, b, r, c->dp, false));
+  // the sketch's column splits are planned for the SMs this system has: all of them
+  // alone, its share of them when `share` systems run their heads at the same time
+  // (one-tile items on every SM for each of 48 systems spread the sketches of a
+  // batch over 0.3 ms)
+  const int sk_ctas = share > 1 ? std::max(1, tc_slots() / share) : 0;
+  S->ns_sk = identity ? 1 : (S->sk_tc ? tc_mrhs_nsplit(b, b, sk_ctas) : rows_nsplit(b, b, r, c->dp, false));
   S->ns_pw = S->tc_pw ? tc_plan_nsplit(b, b) : rows_nsplit(b, b, 1, c->dp, false);
   S->ns_c = S->plan_c.nsplit;
   adasap_status st = alloc_solver(S);
@@ -1214,6 +1260,11 @@ struct Batch {
   // steps on buffer 0 / 1, the last (Rayleigh) step, the direction
   WbArgs* wb[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   int nwb = 0, wb_chunks = 1;
+  // grouped k_head_prep of the active systems that take it, one table per
+  // operand width (tc_kp 16, 32)
+  HeadPrepArgs* prep[2] = {nullptr, nullptr};
+  int nprep[2] = {0, 0};
+  int64_t prep_work[2] = {0, 0};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   void free_groups() {
@@ -1229,6 +1280,12 @@ struct Batch {
       w = nullptr;
     }
     nwb = 0;
+    for (int k = 0; k < 2; ++k) {
+      cudaFree(prep[k]);
+      prep[k] = nullptr;
+      nprep[k] = 0;
+      prep_work[k] = 0;
+    }
   }
   void free_graph() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -1332,6 +1389,24 @@ cudaError_t build_wb(Batch& bt) {
   return cudaSuccess;
 }
 
+// Tables of the grouped k_head_prep (active systems with use_prep), by operand width.
+cudaError_t build_prep(Batch& bt) {
+  std::vector<HeadPrepArgs> h[2];
+  for (size_t i = 0; i < bt.S.size(); ++i) {
+    if (!bt.active[i] || !bt.S[i]->use_prep) continue;
+    const int k = bt.S[i]->c->kp == 16 ? 0 : 1;
+    h[k].push_back(bt.S[i]->prep);
+    bt.prep_work[k] = std::max(bt.prep_work[k], head_prep_work(h[k].back()));
+  }
+  for (int k = 0; k < 2; ++k) {
+    bt.nprep[k] = (int)h[k].size();
+    if (h[k].empty()) continue;
+    KR(cudaMalloc(&bt.prep[k], h[k].size() * sizeof(HeadPrepArgs)));
+    KR(cudaMemcpy(bt.prep[k], h[k].data(), h[k].size() * sizeof(HeadPrepArgs), cudaMemcpyHostToDevice));
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_groups(const Batch& bt, const std::vector<GroupedProduct>& gs, cudaStream_t st) {
   for (const GroupedProduct& g : gs)
     KR(launch_rows_tc_grouped(g.kern, g.kp, g.grp, g.gstart, (int)g.members.size(), g.nitems,
@@ -1407,8 +1482,12 @@ cudaError_t rec_batch(Batch& bt) {
     }
     return cudaSuccess;
   };
+  // the inputs of the iteration of every system that takes k_head_prep: one launch
+  // per operand width for all of them, before the systems fork
+  for (int k = 0; k < 2; ++k)
+    if (bt.nprep[k] > 0) KR(launch_head_prep(bt.prep[k], bt.nprep[k], k == 0 ? 16 : 32, bt.prep_work[k], ms));
   KR(fork(act));
-  for (adasap_solver* S : act) KR(rec_head(S, nullptr, nullptr));
+  for (adasap_solver* S : act) KR(rec_head(S, nullptr, nullptr, S->use_prep));
   for (adasap_solver* S : act)
     if (!groupable(S)) KR(rec_step1(S));
   if (!grp.empty()) {
@@ -1455,7 +1534,7 @@ adasap_status rebuild(Batch& bt) {
   bt.free_groups();
   cudaError_t e;
   if ((e = build_groups(bt, 0, bt.tpi1, bt.step1)) || (e = build_groups(bt, 1, bt.tpipw, bt.pw[0])) ||
-      (e = build_groups(bt, 2, bt.tpipw, bt.pw[1])) || (e = build_wb(bt))) {
+      (e = build_groups(bt, 2, bt.tpipw, bt.pw[1])) || (e = build_wb(bt)) || (e = build_prep(bt))) {
     note_error(e, "grouped launch tables");
     return ADASAP_ECUDA;
   }
@@ -1499,7 +1578,7 @@ adasap_status solve_batched(int nsys, adasap_ctx* const* ctxs, const float* cons
   bt.grouped.assign(nsys, 0);
   for (int i = 0; i < nsys; ++i) {
     const adasap_status st =
-        solver_prepare(ctxs[i], Y[i], s, &opts[i], nullptr, nullptr, nullptr, W[i], us, &bt.S[i], 0, reserve);
+        solver_prepare(ctxs[i], Y[i], s, &opts[i], nullptr, nullptr, nullptr, W[i], us, &bt.S[i], 0, reserve, nsys);
     if (st != ADASAP_OK) return st;
     adasap_solver* S = bt.S[i];
     bt.grouped[i] = groupable(S);
