@@ -29,8 +29,9 @@
 //   warp 0       producer: bulk copies of the column operand tiles (1- or
 //                2-stage ring) and of the W chunks (2-slot ring), in the order the
 //                MMAs consume them
-//   warp 1       TMEM owner and MMA issuer: distance MMAs one tile ahead of
-//                the contraction MMAs of the previous tile
+//   warp 1       TMEM owner and distance MMA issuer
+//   warp 3       contraction MMA issuer (two issuing threads: one was itself the
+//                limit, at about 90 clocks an MMA)
 //   warps 4..11  epilogue: warpgroup g forms chunks 2g, 2g + 1 of every tile in
 //                its own chunk slot (one producer per slot, so that a parity wait
 //                can never alias a phase two uses back), then reads its half of
@@ -250,22 +251,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc_mrhs(MrhsArgs a) {
         }
       }
     } else if (warp == 1) {
-      // ---- MMA issuer: dist(0); per tile t: dist(t + 1), contr(t, 0..3) -------------
+      // ---- distance MMA issuer: dist(t) for every tile of the item, each once its
+      // column tile has landed and the epilogue has read that distance buffer's
+      // previous tile ------------------------------------------------------------------
       if (lane == 0) {
         bool ok = true, any = false;
-        uint32_t acc_flag[2] = {0u, 0u};
-        auto issue_dist = [&](int t) -> bool {
+        const uint32_t a_hi = smem_u32(sAhi), a_lo = smem_u32(sAlo);
+        for (int t = 0; ok && t < ntiles; ++t) {
           const uint32_t g = gt + (uint32_t)t;
           const int st = (int)(g % (uint32_t)a.nx), buf = g & 1;
           const uint32_t ph = (g >> 1) & 1u;
           if (!mbar_wait(&full[st], (g / (uint32_t)a.nx) & 1u, abort_flag) ||
               !mbar_wait(&tempty[buf], ph ^ 1u, abort_flag)) {
             tc_note_timeout(a.err, 13);
-            return false;
+            ok = false;
+            break;
           }
           tc_fence_after();
           const uint32_t dt = tbase + (uint32_t)(buf * kTcN);
-          const uint32_t a_hi = smem_u32(sAhi), a_lo = smem_u32(sAlo);
           const uint32_t b_hi = smem_u32(sX + (st * 2 + 0) * OPF), b_lo = smem_u32(sX + (st * 2 + 1) * OPF);
           uint32_t acc = 0;
 #pragma unroll
@@ -282,13 +285,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc_mrhs(MrhsArgs a) {
           tc_commit(&empty[st]);
           tc_commit(&tfull[buf]);
           any = true;
-          return true;
-        };
+        }
+        if (!ok) *abort_flag = 1;
+        if (any) {
+          // every distance MMA of this issuer completes before the row operands are
+          // rewritten (next item) or TMEM is released (end)
+          tc_commit(drain);
+          mbar_wait(drain, ndrain & 1u, nullptr);
+          ++ndrain;
+        }
+      }
+    } else if (warp == 3) {
+      // ---- contraction MMA issuer: contr(t, 0..3) for every tile.  A second issuing
+      // thread beside the distance MMAs: one thread issuing all 54 MMAs of a tile was
+      // itself the limit (its chain of waits, descriptor arithmetic and issues) -------
+      if (lane == 0) {
+        bool ok = true;
+        // accumulate flags of the even and odd tiles' accumulators, as two scalars (an
+        // array indexed by t & 1 went to local memory, in the issue chain of every MMA)
+        uint32_t acc_even = 0u, acc_odd = 0u;
         const uint32_t idesc = tc_idesc_tf32(sp);
         const uint32_t dacc = tbase + kAccCol;
-        if (ntiles > 0) ok = issue_dist(0);
         for (int t = 0; ok && t < ntiles; ++t) {
-          if (t + 1 < ntiles && !(ok = issue_dist(t + 1))) break;
           for (int j = 0; j < kChPerTile; ++j) {
             const uint32_t gg = gt + (uint32_t)t;
             const uint32_t q = gg * kChPerTile + (uint32_t)j;   // W ring: consumption index
@@ -311,30 +329,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc_mrhs(MrhsArgs a) {
             const uint32_t k_lo = k_hi + (uint32_t)(kTcM * kCh * sizeof(float));
             const uint32_t w_hi = smem_u32(sW + (wsl * 2 + 0) * sp * kCh);
             const uint32_t w_lo = smem_u32(sW + (wsl * 2 + 1) * sp * kCh);
-            for (int pass = 0; pass < a.passes; ++pass) {
-              const uint32_t A = pass == 2 ? k_lo : k_hi;
-              const uint32_t B = pass == 1 ? w_lo : w_hi;
+            // descriptors built once per chunk; K step ks starts 256 bytes further on,
+            // i.e. 16 more in the descriptor's start-address field (address >> 4, 14
+            // bits: shared addresses stay below 2^18 bytes, so the field never carries)
+            const uint64_t dkh = smem_desc(k_hi, 128u, 32u * kCh), dkl = smem_desc(k_lo, 128u, 32u * kCh);
+            const uint64_t dwh = smem_desc(w_hi, 128u, 32u * kCh), dwl = smem_desc(w_lo, 128u, 32u * kCh);
+            const uint32_t dt = dacc + (uint32_t)(t & 1) * (kAccCol2 - kAccCol);
+            uint32_t acc = (t & 1) ? acc_odd : acc_even;
 #pragma unroll
-              for (int ks = 0; ks < kCh / 8; ++ks) {
-                tc_mma_tf32(dacc + (uint32_t)(t & 1) * (kAccCol2 - kAccCol), smem_desc(A + 256u * ks, 128u, 32u * kCh),
-                            smem_desc(B + 256u * ks, 128u, 32u * kCh), idesc, acc_flag[t & 1]);
-                acc_flag[t & 1] = 1;
-              }
+            for (int ks = 0; ks < kCh / 8; ++ks) {
+              tc_mma_tf32(dt, dkh + 16u * ks, dwh + 16u * ks, idesc, acc);   // K_hi W_hi
+              acc = 1u;
             }
+            if (a.passes == 3) {
+#pragma unroll
+              for (int ks = 0; ks < kCh / 8; ++ks) tc_mma_tf32(dt, dkh + 16u * ks, dwl + 16u * ks, idesc, 1u);  // K_hi W_lo
+#pragma unroll
+              for (int ks = 0; ks < kCh / 8; ++ks) tc_mma_tf32(dt, dkl + 16u * ks, dwh + 16u * ks, idesc, 1u);  // K_lo W_hi
+            }
+            if (t & 1) acc_odd = 1u;
+            else acc_even = 1u;
             tc_commit(&kempty[ksl]);
             tc_commit(&wempty[wsl]);
           }
-          if (!ok) break;
         }
         if (!ok) *abort_flag = 1;
-        // the accumulator is complete once every MMA above has finished (items
-        // with tiles only: both roles count those in nof)
+        // the accumulator is complete once every contraction MMA above has finished
+        // (items with tiles only: both roles count those in nof); the epilogue reads it
+        // before the item's closing barrier, so this issuer needs no drain of its own
         if (ntiles > 0) tc_commit(ofull);
-        if (any) {
-          tc_commit(drain);
-          mbar_wait(drain, ndrain & 1u, nullptr);
-          ++ndrain;
-        }
       }
     } else if (warp >= 4) {
       // ---- epilogue ------------------------------------------------------------------
