@@ -12,7 +12,7 @@ from paper_2505_13723_b300 import synth
 
 pytestmark = pytest.mark.gpu
 
-# Tolerance of an FP32 kernel-row product (spec: <= 1e-5 relative):
+# Tolerance of an FP32 kernel-row product (the stated bound: <= 1e-5 relative):
 #   |out_i - ref_i| <= 1e-5 * sum_j |k_ij| |w_ij|
 # i.e. relative to the sum of absolute terms, the scale at which FP32
 # rounding of distances, exponentials and partial sums acts.

@@ -8,7 +8,7 @@ tol = max(1e-4, 4 * 2^-23 * b * sigma2 / min_t rho_t) -- the FP32 sketch
 perturbs the preconditioner by ||dP|| ~ eps32 * tr(K_BB), which moves rho and
 P^{-1} R by ||dP|| / rho -- and (2N + 1) times that for eta and W (the stepsize
 is a Rayleigh quotient after 2N + 1 products with the perturbed operator).
-The converged posterior mean is held to the benchmark spec's bound of 1e-4 relative
+The converged posterior mean is held to the stated bound of 1e-4 relative
 error on the 500 test points.
 """
 
