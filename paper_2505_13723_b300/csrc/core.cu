@@ -78,20 +78,21 @@ __host__ __device__ inline int gram_active_tiles(int nt, int rows) {
 //          the chunk sum carries a relative error of about rows x 2^-48 of sum |a b|
 //   else:  FP32 products summed in FP32 over 64 rows, those sums in double-float.
 // The chunk's partial of entry (i, j) is written as the pair (hi, lo).
+// (body for block (bx, by); the kernels below pass their own block indices)
 template <bool EXACT>
-__global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1, int64_t ld1, int c1,
-                                                   const float* __restrict__ A2, int64_t ld2, int c2,
-                                                   int64_t m, int64_t chunk_rows, int rows,
-                                                   float2* __restrict__ part) {
+__device__ __forceinline__ void gram_part_body(const float* __restrict__ A1, int64_t ld1, int c1,
+                                               const float* __restrict__ A2, int64_t ld2, int c2,
+                                               int64_t m, int64_t chunk_rows, int rows,
+                                               float2* __restrict__ part, int bx, int by) {
   constexpr int TS = 64, KR = 32, PER = KR * TS / 256;  // floats per thread per matrix and slice
   const int c = c1 + c2;
   const int nt = (c + TS - 1) / TS;
   int ti, tj;
-  gram_tile(blockIdx.y, nt, rows, ti, tj);
+  gram_tile(by, nt, rows, ti, tj);
   __shared__ __align__(16) float sa[KR][TS + 4];
   __shared__ __align__(16) float sb[KR][TS + 4];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int64_t r0 = (int64_t)blockIdx.x * chunk_rows;
+  const int64_t r0 = (int64_t)bx * chunk_rows;
   const int64_t r1 = min(m, r0 + chunk_rows);
   float hi[4][4], lo[4][4], H[4][4], L[4][4];
 #pragma unroll
@@ -175,19 +176,27 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1,
         tl = L[u][v];
         ff_add(th, tl, hi[u][v]);
       }
-      if (i < c && j < c) part[((int64_t)blockIdx.x * c + i) * c + j] = make_float2(th, tl);
+      if (i < c && j < c) part[((int64_t)bx * c + i) * c + j] = make_float2(th, tl);
     }
+}
+
+template <bool EXACT>
+__global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ A1, int64_t ld1, int c1,
+                                                   const float* __restrict__ A2, int64_t ld2, int c2,
+                                                   int64_t m, int64_t chunk_rows, int rows,
+                                                   float2* __restrict__ part) {
+  gram_part_body<EXACT>(A1, ld1, c1, A2, ld2, c2, m, chunk_rows, rows, part, blockIdx.x, blockIdx.y);
 }
 
 // G[i][j] = sum over chunks of the (hi, lo) partials, in chunk order within
 // each of 8 interleaved subsets and then in subset order (double-float);
 // block = 32 entries x 8 subsets.
-__global__ void __launch_bounds__(256) k_gram_reduce(const float2* __restrict__ part, int chunks, int c, int rows,
-                                                     double* __restrict__ G) {
+__device__ __forceinline__ void gram_reduce_body(const float2* __restrict__ part, int chunks, int c, int rows,
+                                                 double* __restrict__ G, int bx) {
   __shared__ float2 sh[8][33];
   const int x = threadIdx.x & 31, y = threadIdx.x >> 5;
   const int64_t cc = (int64_t)c * c;
-  const int e = blockIdx.x * 32 + x;
+  const int e = bx * 32 + x;
   int i = e / c, j = e % c;
   if ((i >> 6) > (j >> 6)) {
     const int t = i;
@@ -218,20 +227,61 @@ __global__ void __launch_bounds__(256) k_gram_reduce(const float2* __restrict__ 
   }
 }
 
+__global__ void __launch_bounds__(256) k_gram_reduce(const float2* __restrict__ part, int chunks, int c, int rows,
+                                                     double* __restrict__ G) {
+  gram_reduce_body(part, chunks, c, rows, G, blockIdx.x);
+}
+
+// Grouped forms (system blockIdx.z / blockIdx.y of tab); blocks past a system's
+// own grid return at once.
+template <bool EXACT>
+__global__ void __launch_bounds__(256) k_gram_part_g(const GramArgs* __restrict__ tab) {
+  const GramArgs& a = tab[blockIdx.z];
+  if ((int)blockIdx.x >= a.chunks || (int)blockIdx.y >= a.active) return;
+  gram_part_body<EXACT>(a.A1, a.ld1, a.c1, a.A2, a.ld2, a.c2, a.m, a.chunk_rows, a.rows, a.part, blockIdx.x,
+                        blockIdx.y);
+}
+
+__global__ void __launch_bounds__(256) k_gram_reduce_g(const GramArgs* __restrict__ tab) {
+  const GramArgs& a = tab[blockIdx.y];
+  if ((int)blockIdx.x >= (a.c * a.c + 31) / 32) return;
+  gram_reduce_body(a.part, a.chunks, a.c, a.rows, a.G, blockIdx.x);
+}
+
+GramArgs gram_fill_args(const float* A1, int64_t ld1, int c1, const float* A2, int64_t ld2, int c2, int64_t m,
+                        float2* part, int chunks, double* G, int rows) {
+  GramArgs a;
+  a.A1 = A1; a.ld1 = ld1; a.c1 = c1; a.A2 = A2; a.ld2 = ld2; a.c2 = c2; a.m = m; a.part = part; a.G = G;
+  a.c = c1 + c2;
+  const int nt = (a.c + 63) / 64;
+  if (rows <= 0 || rows > a.c) rows = a.c;
+  a.rows = rows;
+  // about two resident CTAs per SM over the computed tiles; fewer partials to reduce
+  a.active = gram_active_tiles(nt, rows);
+  a.chunks = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)chunks, (int64_t)(296 / a.active), (m + 31) / 32}));
+  a.chunk_rows = (m + a.chunks - 1) / a.chunks;
+  return a;
+}
+
 cudaError_t launch_gram(const float* A1, int64_t ld1, int c1, const float* A2, int64_t ld2, int c2,
                         int64_t m, float2* part, int chunks, double* G, bool exact, cudaStream_t st, int rows) {
-  const int c = c1 + c2;
-  const int nt = (c + 63) / 64;
-  if (rows <= 0 || rows > c) rows = c;
-  // about two resident CTAs per SM over the computed tiles; fewer partials to reduce
-  const int active = gram_active_tiles(nt, rows);
-  chunks = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)chunks, (int64_t)(296 / active), (m + 31) / 32}));
-  const int64_t chunk_rows = (m + chunks - 1) / chunks;
+  const GramArgs a = gram_fill_args(A1, ld1, c1, A2, ld2, c2, m, part, chunks, G, rows);
   if (exact)
-    k_gram_part<true><<<dim3(chunks, active), 256, 0, st>>>(A1, ld1, c1, A2, ld2, c2, m, chunk_rows, rows, part);
+    k_gram_part<true><<<dim3(a.chunks, a.active), 256, 0, st>>>(A1, ld1, c1, A2, ld2, c2, m, a.chunk_rows, a.rows,
+                                                                 part);
   else
-    k_gram_part<false><<<dim3(chunks, active), 256, 0, st>>>(A1, ld1, c1, A2, ld2, c2, m, chunk_rows, rows, part);
-  k_gram_reduce<<<(c * c + 31) / 32, 256, 0, st>>>(part, chunks, c, rows, G);
+    k_gram_part<false><<<dim3(a.chunks, a.active), 256, 0, st>>>(A1, ld1, c1, A2, ld2, c2, m, a.chunk_rows, a.rows,
+                                                                  part);
+  k_gram_reduce<<<(a.c * a.c + 31) / 32, 256, 0, st>>>(part, a.chunks, a.c, a.rows, G);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_grouped(const GramArgs* tab, int nsys, int max_chunks, int max_active, int max_c, bool exact,
+                                cudaStream_t st) {
+  if (nsys <= 0) return cudaSuccess;
+  if (exact) k_gram_part_g<true><<<dim3(max_chunks, max_active, nsys), 256, 0, st>>>(tab);
+  else k_gram_part_g<false><<<dim3(max_chunks, max_active, nsys), 256, 0, st>>>(tab);
+  k_gram_reduce_g<<<dim3((max_c * max_c + 31) / 32, nsys), 256, 0, st>>>(tab);
   return cudaGetLastError();
 }
 

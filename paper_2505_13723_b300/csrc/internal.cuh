@@ -164,6 +164,19 @@ int tc_mrhs_sp(int s);
 int64_t tc_mrhs_wfloats(int64_t n, int s);
 cudaError_t tc_mrhs_init();
 int tc_mrhs_nsplit(int64_t m, int64_t ncols, int max_ctas = 0);
+// Grouped multi-RHS products (several independent products in one persistent
+// launch): mrhs_fill_args writes the argument block of one product, as
+// launch_rows_tc_mrhs would launch it, into host memory (mrhs_args_size() bytes)
+// and returns its (row tile, split) items (-1 for invalid sizes); products launched
+// together need the same kernel, tc_kp and mrhs_plan_key (shared-memory plan).
+size_t mrhs_args_size();
+int64_t mrhs_fill_args(void* out, int d, const float* xr, const float* qr, const int* ridx, int64_t m, int dp,
+                       const float* bhi, const float* blo, int64_t ncols, int self_mode, const float* whi,
+                       const float* wlo, int s, int passes, float* part, int nsplit, float sigma2, int* err);
+int64_t mrhs_plan_key(const void* args);
+// first: host copy of grp[0]; grp (device, ngrp blocks), gstart (device, ngrp + 1 prefix sums of the items)
+cudaError_t launch_rows_tc_mrhs_grouped(int kern, int kp, const void* first, const void* grp, const int64_t* gstart,
+                                        int ngrp, int64_t nitems, cudaStream_t st);
 // W (n x s, row stride ldw) -> chunked canonical B operands (hi; lo when passes == 3).
 cudaError_t launch_build_w_tc(const float* W, int64_t ldw, int64_t n, int s, int passes, float* whi, float* wlo,
                               cudaStream_t st);
@@ -190,6 +203,37 @@ cudaError_t launch_wait_selftest(uint64_t limit_ns, int* err, cudaStream_t st);
 // launch_normals, tag 3; launch_gather; launch_build_tc; launch_build_w_tc,
 // three passes).  A table of these, one per system, is launched at once with
 // blockIdx.y selecting the system.
+// out (m x s) = sum over nsplit partial blocks of part (nsplit x m x s), for one
+// system of a grouped launch (launch_split_sum_grouped: blockIdx.y = system).
+struct SplitSumArgs {
+  const float* part;
+  int nsplit;
+  int64_t m;
+  int s;
+  float* out;
+};
+cudaError_t launch_split_sum_grouped(const SplitSumArgs* tab, int nsys, int64_t max_elems, cudaStream_t st);
+
+// One Gram call of launch_gram for one system of a grouped launch (the host
+// fills it with gram_fill_args; launch_gram_grouped: blockIdx.z / y = system).
+struct GramArgs {
+  const float* A1;
+  int64_t ld1;
+  int c1;
+  const float* A2;
+  int64_t ld2;
+  int c2;
+  int64_t m, chunk_rows;
+  int rows, chunks, active, c;
+  float2* part;
+  double* G;
+};
+GramArgs gram_fill_args(const float* A1, int64_t ld1, int c1, const float* A2, int64_t ld2, int c2, int64_t m,
+                        float2* part, int chunks, double* G, int rows);
+// tab: device, nsys entries; max_chunks / max_active / max_c: maxima over the table
+cudaError_t launch_gram_grouped(const GramArgs* tab, int nsys, int max_chunks, int max_active, int max_c, bool exact,
+                                cudaStream_t st);
+
 struct HeadPrepArgs {
   uint64_t seed;
   const long long* t_dev;   // iteration counter

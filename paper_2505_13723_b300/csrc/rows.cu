@@ -395,16 +395,16 @@ cudaError_t launch_rows(int kern, int dp, const RowsArgs& a, int s, int nsplit, 
 // out[i][c] = sum_p part[p][i][coff + c] + beta A[aidx i][c] + gamma B[bidx i][c],
 // summed in double-float (the products beta A, gamma B split exactly) and
 // rounded once to FP32; blocksq (optional) gets each block's sum of out^2.
-__global__ void k_reduce(const float* __restrict__ part, int nsplit, int64_t m, int na, int coff,
-                         int s, float* __restrict__ out, int64_t ldo, float beta,
-                         const float* __restrict__ A, const int* __restrict__ aidx, int64_t lda,
-                         float gamma, const float* __restrict__ B, const int* __restrict__ bidx,
-                         int64_t ldb, double* blocksq) {
+// body of k_reduce for block bx of gx (the grouped form passes its own indices)
+__device__ __forceinline__ void reduce_body(const float* __restrict__ part, int nsplit, int64_t m, int na, int coff,
+                                            int s, float* __restrict__ out, int64_t ldo, float beta,
+                                            const float* __restrict__ A, const int* __restrict__ aidx, int64_t lda,
+                                            float gamma, const float* __restrict__ B, const int* __restrict__ bidx,
+                                            int64_t ldb, double* blocksq, int bx, int gx) {
   __shared__ double red[33];
   const int64_t total = m * s;
   double sq = 0.0;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = (int64_t)bx * blockDim.x + threadIdx.x; e < total; e += (int64_t)gx * blockDim.x) {
     const int64_t i = s == 1 ? e : e / s;
     const int c = (int)(e - i * s);
     float H = 0.0f, L = 0.0f;
@@ -432,8 +432,32 @@ __global__ void k_reduce(const float* __restrict__ part, int nsplit, int64_t m, 
   }
   if (blocksq) {
     const double tot = block_sum(sq, red);
-    if (threadIdx.x == 0) blocksq[blockIdx.x] = tot;
+    if (threadIdx.x == 0) blocksq[bx] = tot;
   }
+}
+
+__global__ void k_reduce(const float* __restrict__ part, int nsplit, int64_t m, int na, int coff,
+                         int s, float* __restrict__ out, int64_t ldo, float beta,
+                         const float* __restrict__ A, const int* __restrict__ aidx, int64_t lda,
+                         float gamma, const float* __restrict__ B, const int* __restrict__ bidx,
+                         int64_t ldb, double* blocksq) {
+  reduce_body(part, nsplit, m, na, coff, s, out, ldo, beta, A, aidx, lda, gamma, B, bidx, ldb, blocksq, blockIdx.x,
+              gridDim.x);
+}
+
+// Grouped plain split sums out = sum_p part[p] (system blockIdx.y of tab), the
+// arithmetic of k_reduce with no extra terms.
+__global__ void k_split_sum_g(const SplitSumArgs* __restrict__ tab) {
+  const SplitSumArgs& a = tab[blockIdx.y];
+  reduce_body(a.part, a.nsplit, a.m, a.s, 0, a.s, a.out, a.s, 0.0f, nullptr, nullptr, 0, 0.0f, nullptr, nullptr, 0,
+              nullptr, blockIdx.x, gridDim.x);
+}
+
+cudaError_t launch_split_sum_grouped(const SplitSumArgs* tab, int nsys, int64_t max_elems, cudaStream_t st) {
+  if (nsys <= 0 || max_elems <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((max_elems + 255) / 256, 64)), (unsigned)nsys);
+  k_split_sum_g<<<grid, 256, 0, st>>>(tab);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const float* part, int nsplit, int64_t m, int na, int coff, int s,

@@ -40,6 +40,7 @@
 // [384, 384 + s_pad) the accumulators of the even and odd tiles (512 allocated).  Every wait is bounded; on a timeout the CTA
 // raises the error flag, drains its copies and MMAs, frees TMEM and writes NaN.
 #include <algorithm>
+#include <cstring>
 
 #include "prep.cuh"
 #include "tc_ptx.cuh"
@@ -101,12 +102,16 @@ struct MrhsSmem {
   }
 };
 
-template <int KERN, int KP>
-__global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc_mrhs(MrhsArgs a) {
+// GROUPED: the items of several independent products (one MrhsArgs each, item
+// ranges gstart[g] .. gstart[g + 1]) in one persistent launch; they share the
+// shared-memory plan (s padding, passes, slot and stage counts), taken from a0.
+template <int KERN, int KP, bool GROUPED>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_rows_tc_mrhs(MrhsArgs a0, const MrhsArgs* __restrict__ grp, const int64_t* __restrict__ gstart, int ngrp) {
   constexpr int OPF = kTcM * KP;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
-  const MrhsSmem L(KP, a.sp, a.passes, a.nks, a.nx);
+  const MrhsSmem L(KP, a0.sp, a0.passes, a0.nks, a0.nx);
   float* sAhi = reinterpret_cast<float*>(base + L.a);
   float* sAlo = sAhi + OPF;
   float* sX = reinterpret_cast<float*>(base + L.x);   // [st][hi, lo][OPF]
@@ -127,9 +132,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc_mrhs(MrhsArgs a) {
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int sp = a.sp;
-  const int64_t rtiles = (a.m + kTcM - 1) / kTcM;
-  const int64_t nitems = rtiles * a.nsplit;
+  const int sp = a0.sp;
+  const int64_t nitems = GROUPED ? gstart[ngrp] : (a0.m + kTcM - 1) / kTcM * a0.nsplit;
   const uint32_t wbytes = (uint32_t)(sp * kCh * sizeof(float));
 
   if (tid == 0) {
@@ -163,7 +167,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc_mrhs(MrhsArgs a) {
 
   uint32_t gt = 0, nof = 0, ndrain = 0;
   for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
-    const int64_t rtile = item % rtiles, split = item / rtiles;
+    int sys = 0;
+    if (GROUPED) {  // the product this item belongs to: last g with gstart[g] <= item
+      int hi = ngrp - 1;
+      while (sys < hi) {
+        const int mid = (sys + hi + 1) >> 1;
+        if (gstart[mid] <= item) sys = mid;
+        else hi = mid - 1;
+      }
+    }
+    const MrhsArgs& a = GROUPED ? grp[sys] : a0;
+    const int64_t li = GROUPED ? item - gstart[sys] : item;
+    const int64_t rtiles = (a.m + kTcM - 1) / kTcM;
+    const int64_t rtile = li % rtiles, split = li / rtiles;
     const int64_t row0 = rtile * kTcM;
     const int64_t c0 = split * a.cps;
     const int64_t c1 = min(a.ncols, c0 + a.cps);
@@ -479,7 +495,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc_mrhs(MrhsArgs a) {
     __syncthreads();
     tc_fence_after();
   }
-  if (warp == 0 && lane == 0 && *abort_flag) tc_note_timeout(a.err, 19);
+  if (warp == 0 && lane == 0 && *abort_flag) tc_note_timeout(a0.err, 19);
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kMrhsTmemCols)
@@ -502,8 +518,54 @@ __global__ void k_build_w_tc(const float* __restrict__ W, int64_t ldw, int64_t n
 template <int KERN, int KP>
 cudaError_t mrhs_setup(int sp_max) {
   const size_t need = MrhsSmem(KP, sp_max, 3, 1).total;   // the largest plan launched
-  return cudaFuncSetAttribute(k_rows_tc_mrhs<KERN, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)std::max(need, kMrhsSmemMax));
+  const int bytes = (int)std::max(need, kMrhsSmemMax);
+  cudaError_t e = cudaFuncSetAttribute(k_rows_tc_mrhs<KERN, KP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_rows_tc_mrhs<KERN, KP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+// The argument block of one product as launched (shared-memory plan included).
+MrhsArgs make_mrhs_args(int d, const float* xr, const float* qr, const int* ridx, int64_t m, int dp,
+                        const float* bhi, const float* blo, int64_t ncols, int self_mode, const float* whi,
+                        const float* wlo, int s, int passes, float* part, int nsplit, float sigma2, int* err) {
+  MrhsArgs a;
+  a.xr = xr; a.qr = qr; a.ridx = ridx; a.m = m; a.dp = dp; a.d = d;
+  a.bhi = bhi; a.blo = blo; a.ncols = ncols; a.self_mode = self_mode;
+  a.whi = whi; a.wlo = wlo; a.s = s; a.sp = tc_mrhs_sp(s); a.passes = passes;
+  const int kp = tc_kp(d);
+  // two K slots per warpgroup (the epilogue writes a tile's second chunk while the
+  // MMAs read the first) before a second column-operand stage (a contraction tile is
+  // long enough to reload the one stage behind the distance MMA)
+  a.nks = 2;
+  a.nx = 2;
+  if (MrhsSmem(kp, a.sp, passes, 2, 2).total > kMrhsSmemMax) a.nx = 1;
+  if (MrhsSmem(kp, a.sp, passes, 2, 1).total > kMrhsSmemMax) a.nks = 1, a.nx = 2;
+  a.part = part; a.sigma2 = sigma2; a.err = err;
+  const int64_t tiles = (ncols + kTcN - 1) / kTcN;
+  a.cps = (tiles + nsplit - 1) / nsplit * kTcN;
+  a.nsplit = nsplit;
+  return a;
+}
+
+template <bool G>
+cudaError_t launch_mrhs_any(int kern, int kp, const MrhsArgs& a, const MrhsArgs* grp, const int64_t* gstart, int ngrp,
+                            int ctas, cudaStream_t st) {
+  const size_t smem = MrhsSmem(kp, a.sp, a.passes, a.nks, a.nx).total;
+#define ADASAP_MRHS(KE, KPV) k_rows_tc_mrhs<KE, KPV, G><<<ctas, kTcThreads, smem, st>>>(a, grp, gstart, ngrp)
+  if (kp == 16) {
+    if (kern == 0) ADASAP_MRHS(0, 16);
+    else if (kern == 1) ADASAP_MRHS(1, 16);
+    else ADASAP_MRHS(2, 16);
+  } else if (kp == 32) {
+    if (kern == 0) ADASAP_MRHS(0, 32);
+    else if (kern == 1) ADASAP_MRHS(1, 32);
+    else ADASAP_MRHS(2, 32);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+#undef ADASAP_MRHS
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -558,40 +620,39 @@ cudaError_t launch_rows_tc_mrhs(int kern, int d, const float* xr, const float* q
                                 cudaStream_t st, int max_ctas) {
   if (m <= 0 || ncols <= 0) return cudaSuccess;
   if (s < 1 || s > kMaxRhs || (passes != 1 && passes != 3)) return cudaErrorInvalidValue;
-  MrhsArgs a;
-  a.xr = xr; a.qr = qr; a.ridx = ridx; a.m = m; a.dp = dp; a.d = d;
-  a.bhi = bhi; a.blo = blo; a.ncols = ncols; a.self_mode = self_mode;
-  a.whi = whi; a.wlo = wlo; a.s = s; a.sp = tc_mrhs_sp(s); a.passes = passes;
-  const int kp = tc_kp(d);
-  // two K slots per warpgroup (the epilogue writes a tile's second chunk while the
-  // MMAs read the first) before a second column-operand stage (a contraction tile is
-  // long enough to reload the one stage behind the distance MMA)
-  a.nks = 2;
-  a.nx = 2;
-  if (MrhsSmem(kp, a.sp, passes, 2, 2).total > kMrhsSmemMax) a.nx = 1;
-  if (MrhsSmem(kp, a.sp, passes, 2, 1).total > kMrhsSmemMax) a.nks = 1, a.nx = 2;
-  a.part = part; a.sigma2 = sigma2; a.err = err;
-  const int64_t tiles = (ncols + kTcN - 1) / kTcN;
-  a.cps = (tiles + nsplit - 1) / nsplit * kTcN;
-  a.nsplit = nsplit;
+  const MrhsArgs a = make_mrhs_args(d, xr, qr, ridx, m, dp, bhi, blo, ncols, self_mode, whi, wlo, s, passes, part,
+                                    nsplit, sigma2, err);
   const int64_t nitems = (m + kTcM - 1) / kTcM * (int64_t)nsplit;
   const int slots = (max_ctas > 0 && max_ctas < tc_slots()) ? max_ctas : tc_slots();
   const int ctas = (int)std::min<int64_t>(nitems, slots);
-  const size_t smem = MrhsSmem(kp, a.sp, passes, a.nks, a.nx).total;
-#define ADASAP_MRHS(KE, KPV) k_rows_tc_mrhs<KE, KPV><<<ctas, kTcThreads, smem, st>>>(a)
-  if (kp == 16) {
-    if (kern == 0) ADASAP_MRHS(0, 16);
-    else if (kern == 1) ADASAP_MRHS(1, 16);
-    else ADASAP_MRHS(2, 16);
-  } else if (kp == 32) {
-    if (kern == 0) ADASAP_MRHS(0, 32);
-    else if (kern == 1) ADASAP_MRHS(1, 32);
-    else ADASAP_MRHS(2, 32);
-  } else {
-    return cudaErrorInvalidValue;
-  }
-#undef ADASAP_MRHS
-  return cudaGetLastError();
+  return launch_mrhs_any<false>(kern, tc_kp(d), a, nullptr, nullptr, 0, ctas, st);
+}
+
+size_t mrhs_args_size() { return sizeof(MrhsArgs); }
+
+int64_t mrhs_fill_args(void* out, int d, const float* xr, const float* qr, const int* ridx, int64_t m, int dp,
+                       const float* bhi, const float* blo, int64_t ncols, int self_mode, const float* whi,
+                       const float* wlo, int s, int passes, float* part, int nsplit, float sigma2, int* err) {
+  if (m <= 0 || ncols <= 0 || s < 1 || s > kMaxRhs || (passes != 1 && passes != 3) || nsplit < 1) return -1;
+  const MrhsArgs a = make_mrhs_args(d, xr, qr, ridx, m, dp, bhi, blo, ncols, self_mode, whi, wlo, s, passes, part,
+                                    nsplit, sigma2, err);
+  std::memcpy(out, &a, sizeof(a));
+  return (m + kTcM - 1) / kTcM * (int64_t)nsplit;
+}
+
+int64_t mrhs_plan_key(const void* args) {
+  MrhsArgs a;
+  std::memcpy(&a, args, sizeof(a));
+  return (((int64_t)a.sp * 4 + a.passes) * 4 + a.nks) * 4 + a.nx;
+}
+
+cudaError_t launch_rows_tc_mrhs_grouped(int kern, int kp, const void* first, const void* grp, const int64_t* gstart,
+                                        int ngrp, int64_t nitems, cudaStream_t st) {
+  if (ngrp < 1 || nitems < 1) return cudaSuccess;
+  MrhsArgs a0;
+  std::memcpy(&a0, first, sizeof(a0));
+  const int ctas = (int)std::min<int64_t>(nitems, tc_slots());
+  return launch_mrhs_any<true>(kern, kp, a0, static_cast<const MrhsArgs*>(grp), gstart, ngrp, ctas, st);
 }
 
 }  // namespace adasap

@@ -511,6 +511,7 @@ struct adasap_solver {
   float* wop1 = nullptr;           // W operand scratch of Step I / the residual check (multi-RHS)
   float* wsk = nullptr;            // Omega operand of the sketch (hi + lo)
   bool use_prep = false;           // the inputs of an iteration come from k_head_prep (one launch)
+  bool head_grouped = false;       // the batch runs this system's sketch, split sum and Grams grouped
   HeadPrepArgs prep{};
   HeadPrepArgs* prep_dev = nullptr;
   float *XBhi = nullptr, *XBlo = nullptr;
@@ -692,8 +693,10 @@ cudaError_t next_omega(adasap_solver* S, int offset, cudaStream_t st) {
   } while (0)
 
 // sample, gather, sketch and Gram matrices; fork the factorisation branch to s1
-// (prep_done: the batch has already run this system's k_head_prep)
-cudaError_t rec_head(adasap_solver* S, const int64_t* Bs, const float* v0s, bool prep_done = false) {
+// (prep_done: the batch has already run this system's k_head_prep; head_done: and its
+// sketch, split sum and Gram matrices, in grouped launches)
+cudaError_t rec_head(adasap_solver* S, const int64_t* Bs, const float* v0s, bool prep_done = false,
+                     bool head_done = false) {
   adasap_ctx* c = S->c;
   cudaStream_t s0 = c->s0, s1 = c->s1;
   const int64_t n = c->n, b = S->b;
@@ -715,7 +718,7 @@ cudaError_t rec_head(adasap_solver* S, const int64_t* Bs, const float* v0s, bool
     if (!S->identity) KR(cudaMemcpyAsync(S->Om, S->OmN, (size_t)b * r * sizeof(float), cudaMemcpyDeviceToDevice, s0));
     KR(launch_gather(c->Xc, c->qc, S->B32, b, c->dp, S->XB, S->qB, s0));
   }
-  if (!S->identity) {
+  if (!S->identity && !head_done) {
     // whole-GPU part of Steps II-III: sketch K_BB Omega and its Gram matrices
     if (S->sk_tc) {
       const int64_t wf = tc_mrhs_wfloats(b, r);
@@ -1265,6 +1268,21 @@ struct Batch {
   HeadPrepArgs* prep[2] = {nullptr, nullptr};
   int nprep[2] = {0, 0};
   int64_t prep_work[2] = {0, 0};
+  // the rest of the head of those systems, grouped: the sketches K_BB Omega (one
+  // persistent launch per kernel, operand width and shared-memory plan), their split
+  // sums and the two Gram matrices of Alg. 4's core
+  struct SketchGroup {
+    int kern = 0, kp = 0, n = 0;
+    int64_t key = 0, nitems = 0;
+    std::vector<unsigned char> first;   // host copy of the first argument block
+    void* tab = nullptr;                // device argument blocks
+    int64_t* gstart = nullptr;          // device prefix sums of the items
+  };
+  std::vector<SketchGroup> sk;
+  SplitSumArgs* ssum = nullptr;
+  GramArgs* gram[2] = {nullptr, nullptr};
+  int nhead = 0, gram_chunks[2] = {0, 0}, gram_active[2] = {0, 0}, gram_c[2] = {0, 0};
+  int64_t ssum_elems = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   void free_groups() {
@@ -1286,6 +1304,21 @@ struct Batch {
       nprep[k] = 0;
       prep_work[k] = 0;
     }
+    for (SketchGroup& g : sk) {
+      cudaFree(g.tab);
+      cudaFree(g.gstart);
+    }
+    sk.clear();
+    cudaFree(ssum);
+    ssum = nullptr;
+    for (GramArgs*& g : gram) {
+      cudaFree(g);
+      g = nullptr;
+    }
+    nhead = 0;
+    ssum_elems = 0;
+    for (adasap_solver* x : S)
+      if (x) x->head_grouped = false;
   }
   void free_graph() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -1407,6 +1440,80 @@ cudaError_t build_prep(Batch& bt) {
   return cudaSuccess;
 }
 
+// Tables of the grouped heads: the active systems with k_head_prep and a tensor-core
+// sketch; sketches by (kernel, operand width, shared-memory plan), then one table of
+// split sums and one per Gram call of launch_nystrom_grams.
+cudaError_t build_head(Batch& bt) {
+  const size_t asz = mrhs_args_size();
+  std::vector<std::vector<unsigned char>> blocks;
+  std::vector<std::vector<int64_t>> starts;
+  std::vector<SplitSumArgs> ss;
+  std::vector<GramArgs> gr[2];
+  for (size_t i = 0; i < bt.S.size(); ++i) {
+    adasap_solver* S = bt.S[i];
+    if (!bt.active[i] || !S->use_prep || !S->sk_tc) continue;
+    adasap_ctx* c = S->c;
+    const int64_t b = S->b;
+    const int r = S->r;
+    std::vector<unsigned char> blk(asz);
+    const int64_t wf = tc_mrhs_wfloats(b, r);
+    const int64_t items = mrhs_fill_args(blk.data(), c->d, S->XB, S->qB, nullptr, b, c->dp, S->XBhi, S->XBlo, b, 1,
+                                         S->wsk, S->wsk + wf, r, 3, S->part2, S->ns_sk, c->sigma2, c->err_dev);
+    if (items < 1) continue;
+    const int64_t key = mrhs_plan_key(blk.data());
+    size_t g = 0;
+    while (g < bt.sk.size() && !(bt.sk[g].kern == c->kern && bt.sk[g].kp == c->kp && bt.sk[g].key == key)) ++g;
+    if (g == bt.sk.size()) {
+      bt.sk.emplace_back();
+      bt.sk.back().kern = c->kern;
+      bt.sk.back().kp = c->kp;
+      bt.sk.back().key = key;
+      bt.sk.back().first = blk;
+      blocks.emplace_back();
+      starts.emplace_back(1, 0);
+    }
+    blocks[g].insert(blocks[g].end(), blk.begin(), blk.end());
+    starts[g].push_back(starts[g].back() + items);
+    ++bt.sk[g].n;
+    SplitSumArgs sa;
+    sa.part = S->part2;
+    sa.nsplit = S->ns_sk;
+    sa.m = b;
+    sa.s = r;
+    sa.out = S->Ysk;
+    ss.push_back(sa);
+    bt.ssum_elems = std::max(bt.ssum_elems, b * r);
+    // launch_nystrom_grams: [Omega | M Omega] (rows r), then M Omega with exact products
+    CoreBufs& cb = S->cb;
+    gr[0].push_back(gram_fill_args(S->Om, r, r, S->Ysk, r, r, b, cb.gram_part, cb.gram_chunks, cb.G, r));
+    gr[1].push_back(gram_fill_args(S->Ysk, r, r, nullptr, 0, 0, b, cb.gram_part, cb.gram_chunks, cb.Gyy, 0));
+    for (int k = 0; k < 2; ++k) {
+      bt.gram_chunks[k] = std::max(bt.gram_chunks[k], gr[k].back().chunks);
+      bt.gram_active[k] = std::max(bt.gram_active[k], gr[k].back().active);
+      bt.gram_c[k] = std::max(bt.gram_c[k], gr[k].back().c);
+    }
+    S->head_grouped = true;
+  }
+  for (size_t g = 0; g < bt.sk.size(); ++g) {
+    Batch::SketchGroup& G = bt.sk[g];
+    G.nitems = starts[g].back();
+    KR(cudaMalloc(&G.tab, blocks[g].size()));
+    KR(cudaMalloc(&G.gstart, starts[g].size() * sizeof(int64_t)));
+    KR(cudaMemcpy(G.tab, blocks[g].data(), blocks[g].size(), cudaMemcpyHostToDevice));
+    KR(cudaMemcpy(G.gstart, starts[g].data(), starts[g].size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+  }
+  bt.nhead = (int)ss.size();
+  if (bt.nhead > 0) {
+    KR(cudaMalloc(&bt.ssum, ss.size() * sizeof(SplitSumArgs)));
+    KR(cudaMemcpy(bt.ssum, ss.data(), ss.size() * sizeof(SplitSumArgs), cudaMemcpyHostToDevice));
+    for (int k = 0; k < 2; ++k) {
+      KR(cudaMalloc(&bt.gram[k], gr[k].size() * sizeof(GramArgs)));
+      KR(cudaMemcpy(bt.gram[k], gr[k].data(), gr[k].size() * sizeof(GramArgs), cudaMemcpyHostToDevice));
+    }
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_groups(const Batch& bt, const std::vector<GroupedProduct>& gs, cudaStream_t st) {
   for (const GroupedProduct& g : gs)
     KR(launch_rows_tc_grouped(g.kern, g.kp, g.grp, g.gstart, (int)g.members.size(), g.nitems,
@@ -1486,8 +1593,17 @@ cudaError_t rec_batch(Batch& bt) {
   // per operand width for all of them, before the systems fork
   for (int k = 0; k < 2; ++k)
     if (bt.nprep[k] > 0) KR(launch_head_prep(bt.prep[k], bt.nprep[k], k == 0 ? 16 : 32, bt.prep_work[k], ms));
+  // and the rest of their heads: sketches, split sums, Gram matrices (so that every
+  // system's factorisation chain starts at the same time)
+  if (bt.nhead > 0) {
+    for (const Batch::SketchGroup& g : bt.sk)
+      KR(launch_rows_tc_mrhs_grouped(g.kern, g.kp, g.first.data(), g.tab, g.gstart, g.n, g.nitems, ms));
+    KR(launch_split_sum_grouped(bt.ssum, bt.nhead, bt.ssum_elems, ms));
+    for (int k = 0; k < 2; ++k)
+      KR(launch_gram_grouped(bt.gram[k], bt.nhead, bt.gram_chunks[k], bt.gram_active[k], bt.gram_c[k], k == 1, ms));
+  }
   KR(fork(act));
-  for (adasap_solver* S : act) KR(rec_head(S, nullptr, nullptr, S->use_prep));
+  for (adasap_solver* S : act) KR(rec_head(S, nullptr, nullptr, S->use_prep, S->head_grouped));
   for (adasap_solver* S : act)
     if (!groupable(S)) KR(rec_step1(S));
   if (!grp.empty()) {
@@ -1534,7 +1650,8 @@ adasap_status rebuild(Batch& bt) {
   bt.free_groups();
   cudaError_t e;
   if ((e = build_groups(bt, 0, bt.tpi1, bt.step1)) || (e = build_groups(bt, 1, bt.tpipw, bt.pw[0])) ||
-      (e = build_groups(bt, 2, bt.tpipw, bt.pw[1])) || (e = build_wb(bt)) || (e = build_prep(bt))) {
+      (e = build_groups(bt, 2, bt.tpipw, bt.pw[1])) || (e = build_wb(bt)) || (e = build_prep(bt)) ||
+      (e = build_head(bt))) {
     note_error(e, "grouped launch tables");
     return ADASAP_ECUDA;
   }
