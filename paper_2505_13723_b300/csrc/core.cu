@@ -293,25 +293,87 @@ cudaError_t launch_gram_grouped(const GramArgs* tab, int nsys, int max_chunks, i
 // still unscaled), and the factor L[i][k] = A[i][k] / sqrt(d_k) is formed
 // once at the end.  Returns false, uniformly over the block, if a pivot is
 // not positive.  `piv` is caller shared scratch of r entries.
+// FP64 issue is scarce on this GPU (an FP64 warp instruction holds a
+// sub-partition's pipe for 64 cycles however many lanes are active), so in
+// the FP64 instance the trailing entries are dealt to the threads densely:
+// they are numbered column by column from the right (column r - 1 first), so
+// that the entries still to update at step k (column > k) are the first
+// (r - 1 - k)(r - k) / 2 of the numbering and every warp but the last runs
+// full.  The pivot's reciprocal is taken once, by the thread that owns
+// the next pivot: it updates that entry first and starts the FP64 division
+// (about 430 cycles here) while the other warps update the rest of the step
+// (piv[k] holds 1 / d_k until the end).  Launch with kCholThreads threads.
 // ---------------------------------------------------------------------------
+constexpr int kCholThreads = 512;
+constexpr int kCholItems = (kMaxRank * (kMaxRank - 1) / 2 + kCholThreads - 1) / kCholThreads;
+
 template <typename T>
 __device__ bool chol_lower_smem(T* A, int r, int ld, T* piv) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int k = 0; k < r; ++k) {
-    __syncthreads();
-    const T d = A[k * ld + k];
-    if (!(d > T(0) && isfinite(d))) return false;
-    const T rd = T(1) / d;
-    for (int i = k + 1 + warp; i < r; i += nw) {
-      const T aik = A[i * ld + k] * rd;
-      for (int j = k + 1 + lane; j <= i; j += 32) A[i * ld + j] -= aik * A[j * ld + k];
+  if constexpr (sizeof(T) == 4) {
+    // FP32: row loops (a warp per row, lanes along it), which measured faster
+    // than the dense dealing below, the FP32 pipe being plentiful
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = 0; k < r; ++k) {
+      __syncthreads();
+      const T d = A[k * ld + k];
+      if (!(d > T(0) && isfinite(d))) return false;
+      const T rd = T(1) / d;
+      for (int i = k + 1 + warp; i < r; i += nw) {
+        const T aik = A[i * ld + k] * rd;
+        for (int j = k + 1 + lane; j <= i; j += 32) A[i * ld + j] -= aik * A[j * ld + k];
+      }
+    }
+  } else {
+    // this thread's trailing entries (i, j), j >= 1, packed as (i << 8) | j
+    int ij[kCholItems];
+    const int ntrail = (r - 1) * r / 2;
+#pragma unroll
+    for (int u = 0; u < kCholItems; ++u) {
+      const int e = threadIdx.x + kCholThreads * u;
+      int packed = 0;
+      if (e < ntrail) {
+        // the block of column r - 1 - c holds c + 1 entries and starts at c (c + 1) / 2
+        int c = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        if (c * (c + 1) / 2 > e) --c;
+        if ((c + 1) * (c + 2) / 2 <= e) ++c;
+        const int j = r - 1 - c;
+        packed = ((j + e - c * (c + 1) / 2) << 8) | j;
+      }
+      ij[u] = packed;
+    }
+    if (threadIdx.x == 0) piv[0] = T(1) / A[0];
+    for (int k = 0; k < r; ++k) {
+      __syncthreads();
+      const T d = A[k * ld + k];
+      if (!(d > T(0) && isfinite(d))) return false;
+      const T rd = piv[k];
+      const int m = r - 1 - k, active = m * (m + 1) / 2;
+      // entry (k + 1, k + 1) opens the block of column k + 1: number (m - 1) m / 2
+      const int ed = m >= 1 ? (m - 1) * m / 2 : -1;
+      if (ed >= 0 && (int)threadIdx.x == ed % kCholThreads) {
+        const int i = k + 1;
+        const T aik = A[i * ld + k] * rd;
+        A[i * ld + i] -= aik * A[i * ld + k];
+        piv[i] = T(1) / A[i * ld + i];
+      }
+#pragma unroll
+      for (int u = 0; u < kCholItems; ++u) {
+        const int e = (int)threadIdx.x + kCholThreads * u;
+        if (e < active && e != ed) {
+          const int i = ij[u] >> 8, j = ij[u] & 255;
+          const T aik = A[i * ld + k] * rd;
+          A[i * ld + j] -= aik * A[j * ld + k];
+        }
+      }
     }
   }
   __syncthreads();
   for (int k = threadIdx.x; k < r; k += blockDim.x) piv[k] = T(1) / sqrt(A[k * ld + k]);
   __syncthreads();
-  for (int i = warp; i < r; i += nw)
-    for (int j = lane; j < i; j += 32) A[i * ld + j] *= piv[j];
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e / r, j = e % r;
+    if (j < i) A[i * ld + j] *= piv[j];
+  }
   __syncthreads();
   for (int k = threadIdx.x; k < r; k += blockDim.x) A[k * ld + k] = T(1) / piv[k];
   __syncthreads();
@@ -320,7 +382,7 @@ __device__ bool chol_lower_smem(T* A, int r, int ld, T* piv) {
 
 // Alg. 4, first half: Delta, C = chol(Omega^T M Omega + Delta Omega^T Omega)
 // (stored as the lower factor L = C^T), and Y_nu^T Y_nu.
-__global__ void __launch_bounds__(512) k_nys_chol(const double* __restrict__ G, const double* __restrict__ Gyy,
+__global__ void __launch_bounds__(kCholThreads) k_nys_chol(const double* __restrict__ G, const double* __restrict__ Gyy,
                                                   int r, double eps,
                                                   double* __restrict__ Lout, double* __restrict__ Gnu,
                                                   DevScalars* sc) {
@@ -371,9 +433,11 @@ __global__ void __launch_bounds__(512) k_nys_chol(const double* __restrict__ G, 
 // (axpy) form -- lane l holds rows l, l + 32, ...; at step i the owner of row i
 // finishes x_i, broadcasts it, and every lane subtracts L[k][i] x_i (lower) or
 // L[i][k] x_i (upper) from its rows still to come, so a step needs no
-// reduction (half the FP64 instructions of the dot-product form).
+// reduction (half the FP64 instructions of the dot-product form).  A lane
+// holds KJ = ceil(r / 32) rows, so a step issues no FP64 instruction for a
+// group of 32 rows that lies wholly past r.
 constexpr int kTrsmWarps = 4;
-template <typename T>
+template <typename T, int KJ>
 __global__ void __launch_bounds__(32 * kTrsmWarps) k_trsm(const double* __restrict__ L, int r,
                                                           const double* __restrict__ R, int trans, int upper,
                                                           double* __restrict__ X) {
@@ -385,7 +449,6 @@ __global__ void __launch_bounds__(32 * kTrsmWarps) k_trsm(const double* __restri
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = blockIdx.x * kTrsmWarps + warp;
-  constexpr int KJ = kMaxRank / 32;
   T x[KJ];
 #pragma unroll
   for (int j = 0; j < KJ; ++j) {
@@ -421,7 +484,13 @@ __global__ void __launch_bounds__(32 * kTrsmWarps) k_trsm(const double* __restri
 template <typename T = double>
 static cudaError_t trsm(const double* L, int r, const double* R, int trans, int upper, double* X, cudaStream_t st) {
   const size_t smem = ((size_t)r * (r + 1) + r) * sizeof(T);
-  k_trsm<T><<<(r + kTrsmWarps - 1) / kTrsmWarps, 32 * kTrsmWarps, smem, st>>>(L, r, R, trans, upper, X);
+  const dim3 grid((r + kTrsmWarps - 1) / kTrsmWarps), block(32 * kTrsmWarps);
+  switch ((r + 31) / 32) {
+    case 1: k_trsm<T, 1><<<grid, block, smem, st>>>(L, r, R, trans, upper, X); break;
+    case 2: k_trsm<T, 2><<<grid, block, smem, st>>>(L, r, R, trans, upper, X); break;
+    case 3: k_trsm<T, 3><<<grid, block, smem, st>>>(L, r, R, trans, upper, X); break;
+    default: k_trsm<T, 4><<<grid, block, smem, st>>>(L, r, R, trans, upper, X); break;
+  }
   return cudaGetLastError();
 }
 
@@ -468,6 +537,7 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ A, i
   float4* v = shj + r2 * cs;
   __shared__ float nrm[kMaxRank];
   __shared__ float mxs[32];
+  __shared__ int rot_flag;   // set by any pair rotated in the current sweep
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int hl = lane & 15, hsel = lane >> 4;
   const unsigned full = 0xffffffffu;
@@ -477,6 +547,7 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ A, i
   for (int i = threadIdx.x; i < r; i += blockDim.x) mx = fmax(mx, fabs(A[(int64_t)i * r + i]));
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(full, mx, o));
   if (lane == 0) mxs[warp] = (float)mx;
+  if (threadIdx.x == 0) rot_flag = 0;
   __syncthreads();
   float amax = 0.f;
   for (int k = 0; k < nw; ++k) amax = fmaxf(amax, mxs[k]);
@@ -514,7 +585,6 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ A, i
       const float noise = 4.0f * 1.1920929e-7f * sqrtf(nmax);
       noise2 = noise * noise;
     }
-    int rotated = 0;
     for (int round = 0; round < r2 - 1; ++round) {
       const int m = 2 * warp + hsel;  // this half-warp's pair
       const bool act = m < half;
@@ -593,8 +663,12 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ A, i
           v[q * cs + s1] = y;
         }
       }
-      rotated |= __syncthreads_or(doit);
+      if (doit) rot_flag = 1;
+      __syncthreads();
     }
+    const int rotated = rot_flag;
+    __syncthreads();
+    if (threadIdx.x == 0) rot_flag = 0;
     if (!rotated) break;
   }
   if (threadIdx.x == 0) sc->jacobi_sweeps = sweep;
@@ -605,7 +679,9 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ A, i
   }
 }
 
-// lambda_i = v_i^T A v_i / v_i^T v_i in FP64 (one block per eigenvector)
+// lambda_i = v_i^T A v_i / v_i^T v_i in FP64 (one block per eigenvector).  Few
+// instructions by design: the blocks run beside the block-row product on its SMs,
+// and a heavier form (every lane busy on FP64 work) measured slower there.
 __global__ void k_rayleigh(const double* __restrict__ A, const float* __restrict__ V, int r, double* __restrict__ lam) {
   __shared__ double red[33];
   const int i = blockIdx.x;
@@ -622,47 +698,77 @@ __global__ void k_rayleigh(const double* __restrict__ A, const float* __restrict
   if (threadIdx.x == 0) lam[i] = num / den;
 }
 
+// Key of a double whose unsigned order is the order of the values (sign bit
+// set for non-negatives, all bits flipped for negatives), so that ranks are
+// taken with integer compares rather than on the FP64 pipe.
+__device__ __forceinline__ unsigned long long order_key(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
 // Sort eigenpairs (descending), S = max(0, Sigma^2 - Delta), rho = S_r + lambda,
-// and T' = V Sigma^{-1} (columns normalised) for U = Y_nu L^{-T} T'.
-__global__ void k_nys_finalize(const double* __restrict__ lam, const float* __restrict__ V, int r, double lam_reg,
-                               DevScalars* sc, double* __restrict__ S, double* __restrict__ keep,
-                               double* __restrict__ Tp) {
+// and T' = V Sigma^{-1} (columns normalised) for U = Y_nu L^{-T} T'.  V is staged
+// in shared memory; each column norm is summed in four parts by four groups of
+// 64 threads, and each column of T' takes one reciprocal (FP64 division and
+// square root cost about 430 and 675 cycles on this GPU).
+constexpr int kFinThreads = 256;
+__global__ void __launch_bounds__(kFinThreads) k_nys_finalize(const double* __restrict__ lam,
+                                                               const float* __restrict__ V, int r, double lam_reg,
+                                                               DevScalars* sc, double* __restrict__ S,
+                                                               double* __restrict__ keep, double* __restrict__ Tp) {
+  extern __shared__ float sV[];   // r x r
   __shared__ int perm[kMaxRank];
-  __shared__ double sig[kMaxRank];
-  __shared__ double nrm[kMaxRank];
+  __shared__ unsigned long long key[kMaxRank];
+  __shared__ double n2p[4][kMaxRank];
+  __shared__ double rcp[kMaxRank];
+  const int tid = threadIdx.x;
   const double delta = sc->delta;
-  for (int i = threadIdx.x; i < r; i += blockDim.x) perm[i] = i;  // stays a valid index even if ranks collide (NaN)
-  __syncthreads();
-  for (int i = threadIdx.x; i < r; i += blockDim.x) {
-    const double li = lam[i];
-    int rank = 0;
-    for (int j = 0; j < r; ++j) {
-      const double lj = lam[j];
-      rank += (lj > li) || (lj == li && j < i);
-    }
-    if (rank < r) perm[rank] = i;
-    double n2 = 0.0;
-    for (int k = 0; k < r; ++k) n2 += (double)V[(int64_t)k * r + i] * (double)V[(int64_t)k * r + i];
-    nrm[i] = sqrt(n2);
+  for (int e = tid; e < r * r; e += kFinThreads) sV[e] = V[e];
+  for (int i = tid; i < r; i += kFinThreads) {
+    key[i] = order_key(lam[i]);
+    perm[i] = i;   // stays a valid index even if a NaN leaves a rank unfilled
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < r; q += blockDim.x) {
-    const double li = lam[perm[q]];
+  for (int i = tid; i < r; i += kFinThreads) {
+    const unsigned long long ki = key[i];
+    int rank = 0;
+    for (int j = 0; j < r; ++j) {
+      const unsigned long long kj = key[j];
+      rank += (kj > ki) || (kj == ki && j < i);
+    }
+    perm[rank] = i;
+  }
+  {
+    const int part = tid >> 6, kq = (r + 3) / 4, k0 = part * kq, k1 = min(r, k0 + kq);
+    for (int i = tid & 63; i < r; i += 64) {
+      double n2 = 0.0;
+      for (int k = k0; k < k1; ++k) {
+        const double v = (double)sV[k * r + i];
+        n2 = fma(v, v, n2);
+      }
+      n2p[part][i] = n2;
+    }
+  }
+  __syncthreads();
+  for (int q = tid; q < r; q += kFinThreads) {
+    const int i = perm[q];
+    const double li = lam[i];
     const double sq = fmax(0.0, li - delta);
     S[q] = sq;
     keep[q] = sq > 0.0 ? 1.0 : 0.0;
-    sig[q] = li > 0.0 ? sqrt(li) : 0.0;
-    if (!isfinite(li)) set_status(sc, ADASAP_ENUMERIC, 2);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) sc->rho = S[r - 1] + lam_reg;
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-    const int k = e / r, q = e % r;
-    const int i = perm[q];
+    const double sg = li > 0.0 ? sqrt(li) : 0.0;
+    const double nr = sqrt((n2p[0][i] + n2p[1][i]) + (n2p[2][i] + n2p[3][i]));
     // a dropped eigenpair (S_q = 0) contributes exactly nothing to either Woodbury form
     // (eqs. inv_nys_woodbury and inv_sqrt_nys_woodbury), so its U column is set to 0
     // instead of V / sigma with sigma ~ 0
-    Tp[e] = (S[q] > 0.0 && sig[q] > 0.0) ? (double)V[(int64_t)k * r + i] / (nrm[i] * sig[q]) : 0.0;
+    rcp[q] = (sq > 0.0 && sg > 0.0) ? 1.0 / (nr * sg) : 0.0;
+    if (!isfinite(li)) set_status(sc, ADASAP_ENUMERIC, 2);
+    if (q == r - 1) sc->rho = sq + lam_reg;
+  }
+  __syncthreads();
+  for (int e = tid; e < r * r; e += kFinThreads) {
+    const int k = e / r, q = e % r;
+    Tp[e] = (double)sV[k * r + perm[q]] * rcp[q];
   }
 }
 
@@ -729,7 +835,7 @@ static cudaError_t make_u(const float* A1, const float* A2, int64_t b, int r, co
 // FP64 Cholesky of an r x r SPD matrix into a lower factor (identity and a
 // status on failure), one CTA.
 template <typename T>
-__global__ void __launch_bounds__(512) k_chol_plain(const double* __restrict__ G, int r, double* __restrict__ L,
+__global__ void __launch_bounds__(kCholThreads) k_chol_plain(const double* __restrict__ G, int r, double* __restrict__ L,
                                                     DevScalars* sc, int detail) {
   extern __shared__ double shd_chol[];
   T* sh = reinterpret_cast<T*>(shd_chol);
@@ -763,10 +869,10 @@ cudaError_t launch_orthonormalize(CoreBufs& cb, float* Om, float* tmp, DevScalar
     const bool wide64 = cb.b < 4 * (int64_t)r;
     if ((e = launch_gram(src, r, r, nullptr, 0, 0, cb.b, cb.gram_part, cb.gram_chunks, cb.X1, exact, st))) return e;
     if (wide64) {
-      k_chol_plain<double><<<1, 512, (size_t)r * (r + 1) * sizeof(double), st>>>(cb.X1, r, cb.Lc, sc, 6);
+      k_chol_plain<double><<<1, kCholThreads, (size_t)r * (r + 1) * sizeof(double), st>>>(cb.X1, r, cb.Lc, sc, 6);
       if ((e = trsm<double>(cb.Lc, r, cb.Ident, 0, 0, cb.A, st))) return e;      // A = L^{-1}
     } else {
-      k_chol_plain<float><<<1, 512, (size_t)r * (r + 1) * sizeof(double), st>>>(cb.X1, r, cb.Lc, sc, 6);
+      k_chol_plain<float><<<1, kCholThreads, (size_t)r * (r + 1) * sizeof(double), st>>>(cb.X1, r, cb.Lc, sc, 6);
       if ((e = trsm<float>(cb.Lc, r, cb.Ident, 0, 0, cb.A, st))) return e;
     }
     if ((e = make_u(src, nullptr, cb.b, r, cb.A, 1, sc, dst, st))) return e;
@@ -788,7 +894,7 @@ cudaError_t launch_nystrom_core(CoreBufs& cb, double eps, double lam, DevScalars
   const int r = cb.r;
   cudaError_t e;
   const size_t sm_chol = (size_t)r * (r + 1) * sizeof(double);
-  k_nys_chol<<<1, 512, sm_chol, st>>>(cb.G, cb.Gyy, r, eps, cb.Lc, cb.Gnu, sc);
+  k_nys_chol<<<1, kCholThreads, sm_chol, st>>>(cb.G, cb.Gyy, r, eps, cb.Lc, cb.Gnu, sc);
   // A = L^{-1} Gnu L^{-T}  (= C^{-T} Y_nu^T Y_nu C^{-1} = B^T B)
   if ((e = trsm(cb.Lc, r, cb.Gnu, 0, 0, cb.X1, st))) return e;
   if ((e = trsm(cb.Lc, r, cb.X1, 1, 0, cb.A, st))) return e;
@@ -796,7 +902,8 @@ cudaError_t launch_nystrom_core(CoreBufs& cb, double eps, double lam, DevScalars
   k_jacobi<<<1, 32 * ((r2 / 2 + 1) / 2), (size_t)2 * r2 * (4 * ((r2 + 3) / 4)) * sizeof(float), st>>>(
       cb.A, r, cb.V32, sc);
   k_rayleigh<<<r, 128, 0, st>>>(cb.A, cb.V32, r, cb.lam);
-  k_nys_finalize<<<1, 256, 0, st>>>(cb.lam, cb.V32, r, lam, sc, cb.S, cb.keep, cb.X1);
+  k_nys_finalize<<<1, kFinThreads, (size_t)r * r * sizeof(float), st>>>(cb.lam, cb.V32, r, lam, sc, cb.S, cb.keep,
+                                                                        cb.X1);
   // T = L^{-T} T'
   if ((e = trsm(cb.Lc, r, cb.X1, 0, 1, cb.T, st))) return e;
   return make_u(Ysk, Om, cb.b, r, cb.T, 0, sc, cb.U, st);
@@ -816,52 +923,67 @@ __device__ __forceinline__ void set4(float4& x, int c, float v) {
   else if (c == 2) x.z = v;
   else x.w = v;
 }
+// KI items (a float4 of a row each) per thread, fixed over the elimination; the
+// pivot's reciprocal is taken once per column, by the thread that finishes the
+// next pivot, and staged in shared memory.
+template <int KI>
 __global__ void __launch_bounds__(kWfThreads) k_wfactor(const double* __restrict__ UtU, int r,
                                                         const double* __restrict__ S, const double* __restrict__ keep,
                                                         DevScalars* sc, float* __restrict__ Minv,
                                                         float* __restrict__ Gu) {
   extern __shared__ float4 shw4[];
+  __shared__ double sdiag[kMaxRank];
+  __shared__ float skeep[kMaxRank];
+  __shared__ float prcp[kMaxRank];
   const int nb = (r + 3) / 4;    // float4 per row
   const int ld = 4 * nb;         // rows padded with zeros to a multiple of 4
-  float4* bufs[2] = {shw4, shw4 + r * nb};
+  float4* buf0 = shw4;
+  float4* buf1 = shw4 + r * nb;
   const double rho = sc->rho;
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    const double kp = keep[i];
+    skeep[i] = (float)kp;
+    sdiag[i] = kp > 0.0 ? rho / S[i] : 1.0;
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < r * ld; e += blockDim.x) {
     const int i = e / ld, j = e % ld;
     float val = 0.0f;
     if (j < r) {
       const double g = UtU[i * r + j];
-      Gu[i * r + j] = (float)g;
-      double v = keep[i] * keep[j] * g;
-      if (i == j) v += keep[i] > 0.0 ? rho / S[i] : 1.0;
-      val = (float)v;
+      const float gf = (float)g;
+      Gu[i * r + j] = gf;
+      // keep is 0 or 1, so keep_i keep_j g is g or a zero of g's sign
+      val = (i == j) ? (float)((double)(skeep[i] * skeep[j]) * g + sdiag[i]) : gf * (skeep[i] * skeep[j]);
     }
-    reinterpret_cast<float*>(bufs[0])[e] = val;
+    reinterpret_cast<float*>(buf0)[e] = val;
   }
-  // this thread's (row, float4 column block) items, fixed over the elimination
-  constexpr int kItems = kMaxRank * (kMaxRank / 4) / kWfThreads;
-  int it_i[kItems], it_j[kItems];
+  int it_i[KI], it_j[KI];
 #pragma unroll
-  for (int m = 0; m < kItems; ++m) {
+  for (int m = 0; m < KI; ++m) {
     const int e = threadIdx.x + m * kWfThreads;
     it_i[m] = e < r * nb ? e / nb : -1;
     it_j[m] = e < r * nb ? e % nb : 0;
   }
+  __syncthreads();
+  if (threadIdx.x == 0) prcp[0] = 1.0f / reinterpret_cast<const float*>(buf0)[0];
   bool ok = true;
   int cur = 0;
   for (int k = 0; k < r; ++k) {
     __syncthreads();
-    const float4* A4 = bufs[cur];
-    float4* B4 = bufs[cur ^ 1];
+    const float4* A4 = cur ? buf1 : buf0;
+    float4* B4 = cur ? buf0 : buf1;
     const float* Af = reinterpret_cast<const float*>(A4);
     const float pv = Af[k * ld + k];
     if (!(pv > 0.0f && isfinite(pv))) {
       ok = false;
       break;
     }
-    const float rp = 1.0f / pv;
+    const float rp = prcp[k];
     const int kb = k >> 2, kc = k & 3;
+    float4 ov[KI];
 #pragma unroll
-    for (int m = 0; m < kItems; ++m) {
+    for (int m = 0; m < KI; ++m) {
       const int i = it_i[m], jb = it_j[m];
       if (i < 0) continue;
       const float4 akj = A4[k * nb + jb];
@@ -876,13 +998,23 @@ __global__ void __launch_bounds__(kWfThreads) k_wfactor(const double* __restrict
                         fmaf(-fi, akj.w, aij.w));
         if (jb == kb) set4(o, kc, -fi);
       }
-      B4[i * nb + jb] = o;
+      ov[m] = o;
+    }
+#pragma unroll
+    for (int m = 0; m < KI; ++m) {
+      const int i = it_i[m], jb = it_j[m];
+      if (i < 0) continue;
+      B4[i * nb + jb] = ov[m];
+      if (i == k + 1 && jb == ((k + 1) >> 2)) {
+        const int c = (k + 1) & 3;
+        prcp[k + 1] = 1.0f / (c == 0 ? ov[m].x : c == 1 ? ov[m].y : c == 2 ? ov[m].z : ov[m].w);
+      }
     }
     cur ^= 1;
   }
   __syncthreads();
   if (!ok && threadIdx.x == 0) set_status(sc, ADASAP_ENUMERIC, 3);
-  const float* Mf = reinterpret_cast<const float*>(bufs[cur]);
+  const float* Mf = reinterpret_cast<const float*>(cur ? buf1 : buf0);
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
     Minv[e] = ok ? Mf[i * ld + j] : (i == j ? 1.0f : 0.0f);
@@ -902,8 +1034,11 @@ cudaError_t launch_woodbury_factor(CoreBufs& cb, double lam, DevScalars* sc, cud
   const int r = cb.r;
   cudaError_t e;
   if ((e = launch_gram(cb.U, r, r, nullptr, 0, 0, cb.b, cb.gram_part, cb.gram_chunks, cb.X1, false, st))) return e;
-  k_wfactor<<<1, kWfThreads, (size_t)2 * r * (4 * ((r + 3) / 4)) * sizeof(float), st>>>(cb.X1, r, cb.S, cb.keep,
-                                                                                        sc, cb.Minv, cb.Gu);
+  const size_t smw = (size_t)2 * r * (4 * ((r + 3) / 4)) * sizeof(float);
+  const int items = r * ((r + 3) / 4);   // float4 of the r rows
+  if (items <= 2 * kWfThreads) k_wfactor<2><<<1, kWfThreads, smw, st>>>(cb.X1, r, cb.S, cb.keep, sc, cb.Minv, cb.Gu);
+  else if (items <= 5 * kWfThreads) k_wfactor<5><<<1, kWfThreads, smw, st>>>(cb.X1, r, cb.S, cb.keep, sc, cb.Minv, cb.Gu);
+  else k_wfactor<8><<<1, kWfThreads, smw, st>>>(cb.X1, r, cb.S, cb.keep, sc, cb.Minv, cb.Gu);
   k_invsqrt_coef<<<1, 128, 0, st>>>(cb.S, r, sc, cb.cis);
   return cudaGetLastError();
 }
@@ -1675,6 +1810,15 @@ cudaError_t launch_power_step(CoreBufs& cb, int mode, const float* part, int nsp
   return launch_wb(a, cb, st);
 }
 
+template <typename T>
+static cudaError_t trsm_init(int smem) {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_trsm<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+  if ((e = cudaFuncSetAttribute(k_trsm<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+  if ((e = cudaFuncSetAttribute(k_trsm<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+  return cudaFuncSetAttribute(k_trsm<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
 cudaError_t core_init() {
   const int big = 200 * 1024;
   cudaError_t e;
@@ -1683,9 +1827,11 @@ cudaError_t core_init() {
   if ((e = cudaFuncSetAttribute(k_make_u, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_chol_plain<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_chol_plain<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-  if ((e = cudaFuncSetAttribute(k_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-  if ((e = cudaFuncSetAttribute(k_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-  if ((e = cudaFuncSetAttribute(k_wfactor, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = trsm_init<double>(big)) || (e = trsm_init<float>(big))) return e;
+  if ((e = cudaFuncSetAttribute(k_wfactor<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_wfactor<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_wfactor<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_nys_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_wapply, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   return cudaSuccess;
 }

@@ -133,7 +133,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int sp = a0.sp;
-  const int64_t nitems = GROUPED ? gstart[ngrp] : (a0.m + kTcM - 1) / kTcM * a0.nsplit;
   const uint32_t wbytes = (uint32_t)(sp * kCh * sizeof(float));
 
   if (tid == 0) {
@@ -164,6 +163,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tslot;
+  const int64_t nitems = GROUPED ? gstart[ngrp] : (a0.m + kTcM - 1) / kTcM * a0.nsplit;
 
   uint32_t gt = 0, nof = 0, ndrain = 0;
   for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
