@@ -440,7 +440,7 @@ constexpr int kTrsmWarps = 4;
 template <typename T, int KJ>
 __global__ void __launch_bounds__(32 * kTrsmWarps) k_trsm(const double* __restrict__ L, int r,
                                                           const double* __restrict__ R, int trans, int upper,
-                                                          double* __restrict__ X) {
+                                                          double* __restrict__ X, float* __restrict__ X32, int t32) {
   extern __shared__ double shd_trsm[];
   const int ld = r + 1;
   T* sL = reinterpret_cast<T*>(shd_trsm);  // r x (r + 1)
@@ -477,19 +477,24 @@ __global__ void __launch_bounds__(32 * kTrsmWarps) k_trsm(const double* __restri
 #pragma unroll
   for (int j = 0; j < KJ; ++j) {
     const int k = lane + 32 * j;
-    if (k < r) X[(int64_t)k * r + col] = (double)x[j];
+    if (k < r) {
+      X[(int64_t)k * r + col] = (double)x[j];
+      if (X32) X32[t32 ? (int64_t)col * r + k : (int64_t)k * r + col] = (float)x[j];
+    }
   }
 }
 
+// X32 (optional): an FP32 copy of X, transposed when t32 (the form k_make_u reads)
 template <typename T = double>
-static cudaError_t trsm(const double* L, int r, const double* R, int trans, int upper, double* X, cudaStream_t st) {
+static cudaError_t trsm(const double* L, int r, const double* R, int trans, int upper, double* X, cudaStream_t st,
+                        float* X32 = nullptr, int t32 = 0) {
   const size_t smem = ((size_t)r * (r + 1) + r) * sizeof(T);
   const dim3 grid((r + kTrsmWarps - 1) / kTrsmWarps), block(32 * kTrsmWarps);
   switch ((r + 31) / 32) {
-    case 1: k_trsm<T, 1><<<grid, block, smem, st>>>(L, r, R, trans, upper, X); break;
-    case 2: k_trsm<T, 2><<<grid, block, smem, st>>>(L, r, R, trans, upper, X); break;
-    case 3: k_trsm<T, 3><<<grid, block, smem, st>>>(L, r, R, trans, upper, X); break;
-    default: k_trsm<T, 4><<<grid, block, smem, st>>>(L, r, R, trans, upper, X); break;
+    case 1: k_trsm<T, 1><<<grid, block, smem, st>>>(L, r, R, trans, upper, X, X32, t32); break;
+    case 2: k_trsm<T, 2><<<grid, block, smem, st>>>(L, r, R, trans, upper, X, X32, t32); break;
+    case 3: k_trsm<T, 3><<<grid, block, smem, st>>>(L, r, R, trans, upper, X, X32, t32); break;
+    default: k_trsm<T, 4><<<grid, block, smem, st>>>(L, r, R, trans, upper, X, X32, t32); break;
   }
   return cudaGetLastError();
 }
@@ -772,19 +777,20 @@ __global__ void __launch_bounds__(kFinThreads) k_nys_finalize(const double* __re
   }
 }
 
-// U = (A1 + delta A2) T'  (b x r), T' = T or T^T (r x r FP64, staged as FP32 in
-// shared memory), delta = sc->delta or 0 when A2 is NULL.  Rows in blocks of 32.
+// U = (A1 + delta A2) T'  (b x r), T' (r x r) given in FP32 by the triangular
+// solve that forms it (an FP64 -> FP32 conversion per entry in every block would
+// run on this GPU's slow FP64 pipe), delta = sc->delta or 0 when A2 is NULL.
+// Rows in blocks of 32.
 //   Nystrom: A1 = M Omega, A2 = Omega, T' = T      (U = Y_nu T)
 //   QR:      A1 = Omega,   A2 = NULL,  T' = L^{-T} (Omega R^{-1}, R = L^T)
 __global__ void __launch_bounds__(256) k_make_u(const float* __restrict__ A1, const float* __restrict__ A2, int64_t b,
-                                                int r, const double* __restrict__ T, int transT, const DevScalars* sc,
+                                                int r, const float* __restrict__ T32, const DevScalars* sc,
                                                 float* __restrict__ U) {
   extern __shared__ float shm[];
   float* sT = shm;                  // r x r
   float* sY = shm + r * r;          // 32 x r
   const float fdelta = A2 ? (float)sc->delta : 0.0f;
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x)
-    sT[e] = (float)(transT ? T[(e % r) * r + e / r] : T[e]);
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) sT[e] = T32[e];
   const int64_t row0 = (int64_t)blockIdx.x * 32;
   for (int e = threadIdx.x; e < 32 * r; e += blockDim.x) {
     const int rr = e / r, k = e % r;
@@ -825,10 +831,10 @@ __global__ void __launch_bounds__(256) k_make_u(const float* __restrict__ A1, co
   }
 }
 
-static cudaError_t make_u(const float* A1, const float* A2, int64_t b, int r, const double* T, int transT,
-                          const DevScalars* sc, float* U, cudaStream_t st) {
-  k_make_u<<<(unsigned)((b + 31) / 32), 256, (size_t)(r * r + 32 * r) * sizeof(float), st>>>(A1, A2, b, r, T, transT,
-                                                                                            sc, U);
+static cudaError_t make_u(const float* A1, const float* A2, int64_t b, int r, const float* T32, const DevScalars* sc,
+                          float* U, cudaStream_t st) {
+  k_make_u<<<(unsigned)((b + 31) / 32), 256, (size_t)(r * r + 32 * r) * sizeof(float), st>>>(A1, A2, b, r, T32, sc,
+                                                                                            U);
   return cudaGetLastError();
 }
 
@@ -870,12 +876,12 @@ cudaError_t launch_orthonormalize(CoreBufs& cb, float* Om, float* tmp, DevScalar
     if ((e = launch_gram(src, r, r, nullptr, 0, 0, cb.b, cb.gram_part, cb.gram_chunks, cb.X1, exact, st))) return e;
     if (wide64) {
       k_chol_plain<double><<<1, kCholThreads, (size_t)r * (r + 1) * sizeof(double), st>>>(cb.X1, r, cb.Lc, sc, 6);
-      if ((e = trsm<double>(cb.Lc, r, cb.Ident, 0, 0, cb.A, st))) return e;      // A = L^{-1}
+      if ((e = trsm<double>(cb.Lc, r, cb.Ident, 0, 0, cb.A, st, cb.T32, 1))) return e;   // A = L^{-1}
     } else {
       k_chol_plain<float><<<1, kCholThreads, (size_t)r * (r + 1) * sizeof(double), st>>>(cb.X1, r, cb.Lc, sc, 6);
-      if ((e = trsm<float>(cb.Lc, r, cb.Ident, 0, 0, cb.A, st))) return e;
+      if ((e = trsm<float>(cb.Lc, r, cb.Ident, 0, 0, cb.A, st, cb.T32, 1))) return e;
     }
-    if ((e = make_u(src, nullptr, cb.b, r, cb.A, 1, sc, dst, st))) return e;
+    if ((e = make_u(src, nullptr, cb.b, r, cb.T32, sc, dst, st))) return e;   // T32 = (L^{-1})^T
   }
   return cudaGetLastError();
 }
@@ -905,8 +911,8 @@ cudaError_t launch_nystrom_core(CoreBufs& cb, double eps, double lam, DevScalars
   k_nys_finalize<<<1, kFinThreads, (size_t)r * r * sizeof(float), st>>>(cb.lam, cb.V32, r, lam, sc, cb.S, cb.keep,
                                                                         cb.X1);
   // T = L^{-T} T'
-  if ((e = trsm(cb.Lc, r, cb.X1, 0, 1, cb.T, st))) return e;
-  return make_u(Ysk, Om, cb.b, r, cb.T, 0, sc, cb.U, st);
+  if ((e = trsm(cb.Lc, r, cb.X1, 0, 1, cb.T, st, cb.T32, 0))) return e;
+  return make_u(Ysk, Om, cb.b, r, cb.T32, sc, cb.U, st);
 }
 
 // M = (rho S^{-1} + U^T U)^{-1} on the kept eigenpairs (App. C.2, stabilised

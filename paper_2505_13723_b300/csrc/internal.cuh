@@ -286,6 +286,7 @@ struct CoreBufs {
   float* V32;         // r x r  eigenvectors (FP32 Jacobi)
   double* lam;        // r      Rayleigh quotients
   double* T;          // r x r  U = Y_nu T
+  float* T32;         // r x r  FP32 right factor of the latest k_make_u (T, or (L^{-1})^T in the QR)
   double* S;          // r      Nystrom eigenvalues (descending)
   double* keep;       // r      1 if S_i > 0 else 0
   float* Minv;        // r x r  (rho S^-1 + U^T U)^-1 on the kept pairs

@@ -607,6 +607,7 @@ adasap_status alloc_solver(adasap_solver* S) {
   cb.V32 = ar.get<float>((size_t)rr * rr);
   cb.lam = ar.get<double>(rr);
   cb.T = ar.get<double>((size_t)rr * rr);
+  cb.T32 = ar.get<float>((size_t)rr * rr);
   cb.S = ar.get<double>(rr);
   cb.keep = ar.get<double>(rr);
   cb.Minv = ar.get<float>((size_t)rr * rr);

@@ -91,6 +91,16 @@ def test_scheduled_tail_average_matches_oracle(lib, T):
     PT.check("tail T=%d" % T, [("W", PT.rel(W.cpu().numpy(), Wref), sens["W"], 1e-4)])
 
 
+@pytest.mark.parametrize("r", [80, 96])
+def test_scheduled_rank_layouts(lib, r):
+    """Ranks whose r x r kernels take the layouts the other cases miss: three rows per lane
+    in the triangular solves (65 <= r <= 96) and five float4 items per thread in the
+    Woodbury factor (r ceil(r / 4) between 1025 and 2560)."""
+    P = synth.small(n=1200, d=4)
+    W, tr, Wref, rec, sens = _scheduled_case(lib, P, 3, b=300, r=r)
+    _check_case("rank layout r=%d" % r, W, tr, Wref, rec, sens, 300, P.sigma2)
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("kern", [1, 2])
 def test_scheduled_matern_regress_shape(lib, kern, prec):
