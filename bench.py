@@ -41,7 +41,7 @@ UNIT = "Gentries/s"
 
 # DRAM bytes per kernel entry of k_rows_tc (Step I shape, s = 1): dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu-captured launch at 10,000 x 262,144 entries, Matern-3/2
-TC_DRAM_BYTES_PER_ENTRY = (39.047936e6 + 46.848e3) / (10000 * 262144)
+TC_DRAM_BYTES_PER_ENTRY = (39.048704e6 + 33.792e3) / (10000 * 262144)
 
 
 def parse():
