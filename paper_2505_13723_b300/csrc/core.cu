@@ -780,48 +780,52 @@ __global__ void __launch_bounds__(kFinThreads) k_nys_finalize(const double* __re
 // U = (A1 + delta A2) T'  (b x r), T' (r x r) given in FP32 by the triangular
 // solve that forms it (an FP64 -> FP32 conversion per entry in every block would
 // run on this GPU's slow FP64 pipe), delta = sc->delta or 0 when A2 is NULL.
-// Rows in blocks of 32.
 //   Nystrom: A1 = M Omega, A2 = Omega, T' = T      (U = Y_nu T)
 //   QR:      A1 = Omega,   A2 = NULL,  T' = L^{-T} (Omega R^{-1}, R = L^T)
+// A block takes kMuRows rows of U; warp w of its 8 rows 8w .. 8w + 7 and lane l of
+// the columns l + 32 q (q < CQ = ceil(r / 32)), so that each k costs two broadcast
+// float4 loads of the (transposed) rows and CQ loads of T' for 8 CQ FMAs.
+constexpr int kMuRows = 64;
+constexpr int kMuLd = kMuRows + 4;   // transposed rows: 4-way conflicts on the staging stores
+template <int CQ>
 __global__ void __launch_bounds__(256) k_make_u(const float* __restrict__ A1, const float* __restrict__ A2, int64_t b,
                                                 int r, const float* __restrict__ T32, const DevScalars* sc,
                                                 float* __restrict__ U) {
-  extern __shared__ float shm[];
-  float* sT = shm;                  // r x r
-  float* sY = shm + r * r;          // 32 x r
+  extern __shared__ __align__(16) float shm[];
+  float* sT = shm;                          // r x r
+  float* sY = shm + ((r * r + 3) & ~3);     // [k][row], leading dimension kMuLd
   const float fdelta = A2 ? (float)sc->delta : 0.0f;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) sT[e] = T32[e];
-  const int64_t row0 = (int64_t)blockIdx.x * 32;
-  for (int e = threadIdx.x; e < 32 * r; e += blockDim.x) {
+  const int64_t row0 = (int64_t)blockIdx.x * kMuRows;
+  for (int e = threadIdx.x; e < kMuRows * r; e += blockDim.x) {
     const int rr = e / r, k = e % r;
     const int64_t row = row0 + rr;
     float v = 0.0f;
     if (row < b) v = A2 ? fmaf(fdelta, A2[row * r + k], A1[row * r + k]) : A1[row * r + k];
-    sY[e] = v;
+    sY[k * kMuLd + rr] = v;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int CQ = kMaxRank / 32;
-  float acc[4][CQ];
+  float acc[8][CQ];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < 8; ++u)
 #pragma unroll
     for (int q = 0; q < CQ; ++q) acc[u][q] = 0.0f;
   for (int k = 0; k < r; ++k) {
-    float yv[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) yv[u] = sY[(warp * 4 + u) * r + k];
+    const float4 y0 = *reinterpret_cast<const float4*>(&sY[k * kMuLd + warp * 8]);
+    const float4 y1 = *reinterpret_cast<const float4*>(&sY[k * kMuLd + warp * 8 + 4]);
+    const float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
 #pragma unroll
     for (int q = 0; q < CQ; ++q) {
       const int c = lane + 32 * q;
       const float tv = c < r ? sT[k * r + c] : 0.0f;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) acc[u][q] = fmaf(yv[u], tv, acc[u][q]);
+      for (int u = 0; u < 8; ++u) acc[u][q] = fmaf(yv[u], tv, acc[u][q]);
     }
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int64_t row = row0 + warp * 4 + u;
+  for (int u = 0; u < 8; ++u) {
+    const int64_t row = row0 + warp * 8 + u;
     if (row >= b) continue;
 #pragma unroll
     for (int q = 0; q < CQ; ++q) {
@@ -831,10 +835,18 @@ __global__ void __launch_bounds__(256) k_make_u(const float* __restrict__ A1, co
   }
 }
 
+static size_t make_u_smem(int r) { return ((size_t)((r * r + 3) & ~3) + (size_t)kMuLd * r) * sizeof(float); }
+
 static cudaError_t make_u(const float* A1, const float* A2, int64_t b, int r, const float* T32, const DevScalars* sc,
                           float* U, cudaStream_t st) {
-  k_make_u<<<(unsigned)((b + 31) / 32), 256, (size_t)(r * r + 32 * r) * sizeof(float), st>>>(A1, A2, b, r, T32, sc,
-                                                                                            U);
+  const unsigned grid = (unsigned)((b + kMuRows - 1) / kMuRows);
+  const size_t smem = make_u_smem(r);
+  switch ((r + 31) / 32) {
+    case 1: k_make_u<1><<<grid, 256, smem, st>>>(A1, A2, b, r, T32, sc, U); break;
+    case 2: k_make_u<2><<<grid, 256, smem, st>>>(A1, A2, b, r, T32, sc, U); break;
+    case 3: k_make_u<3><<<grid, 256, smem, st>>>(A1, A2, b, r, T32, sc, U); break;
+    default: k_make_u<4><<<grid, 256, smem, st>>>(A1, A2, b, r, T32, sc, U); break;
+  }
   return cudaGetLastError();
 }
 
@@ -1830,7 +1842,10 @@ cudaError_t core_init() {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_nys_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-  if ((e = cudaFuncSetAttribute(k_make_u, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_make_u<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_make_u<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_make_u<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_make_u<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_chol_plain<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_chol_plain<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = trsm_init<double>(big)) || (e = trsm_init<float>(big))) return e;
