@@ -397,6 +397,7 @@ __global__ void __launch_bounds__(kCholThreads) k_nys_chol(const double* __restr
   bool ok = false;
   int attempt = 0;
   for (; attempt < 4; ++attempt) {
+#pragma unroll 2
     for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
       const int i = e / r, j = e % r;
       const double oty = 0.5 * (G[(int64_t)i * c + r + j] + G[(int64_t)j * c + r + i]);
@@ -413,6 +414,7 @@ __global__ void __launch_bounds__(kCholThreads) k_nys_chol(const double* __restr
     if (threadIdx.x == 0) set_status(sc, ADASAP_ENUMERIC, 1);
     __syncthreads();
   }
+#pragma unroll 4
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
     Lout[e] = (j <= i) ? sh[i * ld + j] : 0.0;
@@ -445,7 +447,32 @@ __global__ void __launch_bounds__(32 * kTrsmWarps) k_trsm(const double* __restri
   const int ld = r + 1;
   T* sL = reinterpret_cast<T*>(shd_trsm);  // r x (r + 1)
   T* rinv = sL + r * ld;                  // r
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) sL[(e / r) * ld + e % r] = (T)L[e];
+  // L (FP64, 16-byte aligned) in batches of 16 double2 loads a thread, all issued
+  // before any is stored: a handful of round trips to L2 instead of one per entry
+  {
+    const int n2 = r * r / 2;
+    const double2* L2 = reinterpret_cast<const double2*>(L);
+    for (int base = threadIdx.x; base < n2; base += 16 * blockDim.x) {
+      double2 v[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int e2 = base + u * blockDim.x;
+        v[u] = e2 < n2 ? __ldg(L2 + e2) : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int e = 2 * (base + u * blockDim.x);
+        if (e < 2 * n2) {
+          sL[(e / r) * ld + e % r] = (T)v[u].x;
+          sL[((e + 1) / r) * ld + (e + 1) % r] = (T)v[u].y;
+        }
+      }
+    }
+    if ((r * r) & 1) {
+      const int e = r * r - 1;
+      if (threadIdx.x == 0) sL[(e / r) * ld + e % r] = (T)L[e];
+    }
+  }
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = blockIdx.x * kTrsmWarps + warp;
@@ -488,6 +515,7 @@ __global__ void __launch_bounds__(32 * kTrsmWarps) k_trsm(const double* __restri
 template <typename T = double>
 static cudaError_t trsm(const double* L, int r, const double* R, int trans, int upper, double* X, cudaStream_t st,
                         float* X32 = nullptr, int t32 = 0) {
+  if (reinterpret_cast<uintptr_t>(L) & 15u) return cudaErrorMisalignedAddress;   // staged by double2 loads
   const size_t smem = ((size_t)r * (r + 1) + r) * sizeof(T);
   const dim3 grid((r + kTrsmWarps - 1) / kTrsmWarps), block(32 * kTrsmWarps);
   switch ((r + 31) / 32) {
@@ -559,6 +587,7 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ A, i
   const double scale = amax > 0.f ? 1.0 / (double)amax : 1.0;
   float* wf = reinterpret_cast<float*>(w);
   float* vf = reinterpret_cast<float*>(v);
+#pragma unroll 4
   for (int e = threadIdx.x; e < r2 * ld; e += blockDim.x) {
     const int col = e / ld, row = e % ld;
     wf[e] = (row < r && col < r) ? (float)(A[(int64_t)row * r + col] * scale) : 0.0f;
@@ -693,6 +722,7 @@ __global__ void k_rayleigh(const double* __restrict__ A, const float* __restrict
   double num = 0.0, den = 0.0;
   for (int k = threadIdx.x; k < r; k += blockDim.x) {
     double w = 0.0;
+#pragma unroll 8
     for (int j = 0; j < r; ++j) w += A[(int64_t)k * r + j] * (double)V[(int64_t)j * r + i];
     const double vk = (double)V[(int64_t)k * r + i];
     num += vk * w;
@@ -728,6 +758,7 @@ __global__ void __launch_bounds__(kFinThreads) k_nys_finalize(const double* __re
   __shared__ double rcp[kMaxRank];
   const int tid = threadIdx.x;
   const double delta = sc->delta;
+#pragma unroll 8
   for (int e = tid; e < r * r; e += kFinThreads) sV[e] = V[e];
   for (int i = tid; i < r; i += kFinThreads) {
     key[i] = order_key(lam[i]);
@@ -795,14 +826,69 @@ __global__ void __launch_bounds__(256) k_make_u(const float* __restrict__ A1, co
   float* sT = shm;                          // r x r
   float* sY = shm + ((r * r + 3) & ~3);     // [k][row], leading dimension kMuLd
   const float fdelta = A2 ? (float)sc->delta : 0.0f;
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) sT[e] = T32[e];
+  // T' and the block's rows (both 16-byte aligned: row0 r is a multiple of 4) by
+  // float4 loads, each batch issued before any is stored
+  {
+    const int n4 = r * r / 4;
+    const float4* T4 = reinterpret_cast<const float4*>(T32);
+    for (int base = threadIdx.x; base < n4; base += 8 * blockDim.x) {
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e4 = base + u * blockDim.x;
+        v[u] = e4 < n4 ? __ldg(T4 + e4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e4 = base + u * blockDim.x;
+        if (e4 < n4) reinterpret_cast<float4*>(sT)[e4] = v[u];
+      }
+    }
+    for (int e = 4 * n4 + threadIdx.x; e < r * r; e += blockDim.x) sT[e] = T32[e];
+  }
   const int64_t row0 = (int64_t)blockIdx.x * kMuRows;
-  for (int e = threadIdx.x; e < kMuRows * r; e += blockDim.x) {
-    const int rr = e / r, k = e % r;
-    const int64_t row = row0 + rr;
-    float v = 0.0f;
-    if (row < b) v = A2 ? fmaf(fdelta, A2[row * r + k], A1[row * r + k]) : A1[row * r + k];
-    sY[k * kMuLd + rr] = v;
+  {
+    // rows row0 .. row0 + kMuRows - 1 are kMuRows r contiguous floats of A1 (and A2)
+    const int64_t nval = min((int64_t)kMuRows, b - row0) * r;   // valid floats
+    const int n4 = kMuRows * r / 4;
+    const float4* Y1 = reinterpret_cast<const float4*>(A1 + row0 * r);
+    const float4* Y2 = A2 ? reinterpret_cast<const float4*>(A2 + row0 * r) : nullptr;
+    for (int base = threadIdx.x; base < n4; base += 4 * blockDim.x) {
+      float4 v1[4], v2[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e4 = base + u * blockDim.x;
+        const int64_t f = 4 * (int64_t)e4;
+        v1[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        v2[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e4 < n4 && f + 3 < nval) {
+          v1[u] = __ldg(Y1 + e4);
+          if (Y2) v2[u] = __ldg(Y2 + e4);
+        } else if (e4 < n4 && f < nval) {   // the float4 that holds the last valid rows' end
+          const float* y1 = A1 + row0 * r + f;
+          const float* y2 = A2 ? A2 + row0 * r + f : nullptr;
+          v1[u].x = y1[0];
+          if (y2) v2[u].x = y2[0];
+          if (f + 1 < nval) { v1[u].y = y1[1]; if (y2) v2[u].y = y2[1]; }
+          if (f + 2 < nval) { v1[u].z = y1[2]; if (y2) v2[u].z = y2[2]; }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e4 = base + u * blockDim.x;
+        if (e4 >= n4) continue;
+        const float a1[4] = {v1[u].x, v1[u].y, v1[u].z, v1[u].w};
+        const float a2[4] = {v2[u].x, v2[u].y, v2[u].z, v2[u].w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int e = 4 * e4 + t;
+          const int rr = e / r, k = e % r;
+          float v = 0.0f;
+          if ((int64_t)e < nval) v = A2 ? fmaf(fdelta, a2[t], a1[t]) : a1[t];
+          sY[k * kMuLd + rr] = v;
+        }
+      }
+    }
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -839,6 +925,9 @@ static size_t make_u_smem(int r) { return ((size_t)((r * r + 3) & ~3) + (size_t)
 
 static cudaError_t make_u(const float* A1, const float* A2, int64_t b, int r, const float* T32, const DevScalars* sc,
                           float* U, cudaStream_t st) {
+  // the kernel stages by float4 loads (its operands are allocation bases)
+  if ((reinterpret_cast<uintptr_t>(A1) | reinterpret_cast<uintptr_t>(A2) | reinterpret_cast<uintptr_t>(T32)) & 15u)
+    return cudaErrorMisalignedAddress;
   const unsigned grid = (unsigned)((b + kMuRows - 1) / kMuRows);
   const size_t smem = make_u_smem(r);
   switch ((r + 31) / 32) {
@@ -859,6 +948,7 @@ __global__ void __launch_bounds__(kCholThreads) k_chol_plain(const double* __res
   T* sh = reinterpret_cast<T*>(shd_chol);
   __shared__ T piv[kMaxRank];
   const int ld = r + 1;
+#pragma unroll 8
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) sh[(e / r) * ld + e % r] = (T)G[e];
   __syncthreads();
   const bool ok = chol_lower_smem<T>(sh, r, ld, piv);
@@ -964,6 +1054,7 @@ __global__ void __launch_bounds__(kWfThreads) k_wfactor(const double* __restrict
     sdiag[i] = kp > 0.0 ? rho / S[i] : 1.0;
   }
   __syncthreads();
+#pragma unroll 4
   for (int e = threadIdx.x; e < r * ld; e += blockDim.x) {
     const int i = e / ld, j = e % ld;
     float val = 0.0f;
