@@ -497,8 +497,14 @@ __global__ void __launch_bounds__(32 * kTrsmWarps) k_trsm(const double* __restri
 #pragma unroll
     for (int j = 0; j < KJ; ++j) {
       const int k = lane + 32 * j;
-      if (k == i) x[j] = xi;
-      else if (!upper ? (k > i && k < r) : (k < i)) x[j] -= (upper ? sL[i * ld + k] : sL[k * ld + i]) * xi;
+      // a group of 32 rows with none left to update issues no FP64 instruction
+      // (a predicated-off one would still hold the sub-partition's FP64 pipe)
+      if (!upper ? (32 * j + 31 > i) : (32 * j < i)) {
+        if (k == i) x[j] = xi;
+        else if (!upper ? (k > i && k < r) : (k < i)) x[j] -= (upper ? sL[i * ld + k] : sL[k * ld + i]) * xi;
+      } else if (j == jo && k == i) {
+        x[j] = xi;
+      }
     }
   }
 #pragma unroll
