@@ -1857,15 +1857,30 @@ __device__ __forceinline__ void wb_apply_body(const WbArgs& a, int chunk) {
 
 __global__ void __launch_bounds__(kWbThreads) k_wb_apply(WbArgs a) { wb_apply_body(a, blockIdx.x); }
 
-// Grouped forms: system blockIdx.y of g, its chunks blockIdx.x < g[y].nchunk.
-__global__ void __launch_bounds__(kWbThreads) k_wb_partials_g(const WbArgs* __restrict__ g) {
-  const WbArgs& a = g[blockIdx.y];
-  if ((int)blockIdx.x < a.nchunk) wb_partials_body(a, blockIdx.x);
+// Grouped forms over a flat grid of the (system, chunk) pairs: block x works on
+// chunk x - start[s] of the system s with start[s] <= x < start[s + 1] (start: the
+// prefix sums of the systems' chunk counts), so no block is idle.  Three CTAs of
+// the partials fit an SM, so that the usual few hundred blocks run as one wave.
+__device__ __forceinline__ int wb_system_of(const int* __restrict__ start, int ngrp, int x) {
+  int lo = 0, hi = ngrp - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
 }
 
-__global__ void __launch_bounds__(kWbThreads) k_wb_apply_g(const WbArgs* __restrict__ g) {
-  const WbArgs& a = g[blockIdx.y];
-  if ((int)blockIdx.x < a.nchunk) wb_apply_body(a, blockIdx.x);
+__global__ void __launch_bounds__(kWbThreads, 3) k_wb_partials_g(const WbArgs* __restrict__ g,
+                                                                  const int* __restrict__ start, int ngrp) {
+  const int sys = wb_system_of(start, ngrp, (int)blockIdx.x);
+  wb_partials_body(g[sys], (int)blockIdx.x - start[sys]);
+}
+
+__global__ void __launch_bounds__(kWbThreads) k_wb_apply_g(const WbArgs* __restrict__ g, const int* __restrict__ start,
+                                                           int ngrp) {
+  const int sys = wb_system_of(start, ngrp, (int)blockIdx.x);
+  wb_apply_body(g[sys], (int)blockIdx.x - start[sys]);
 }
 
 static void fill_wb(WbArgs& a, CoreBufs& cb) {
@@ -1899,11 +1914,10 @@ WbArgs wb_args_power(CoreBufs& cb, int mode, const float* part, int nsplit, floa
   return a;
 }
 
-cudaError_t launch_wb_grouped(const WbArgs* g, int ngrp, int max_chunks, int mode, cudaStream_t st) {
-  if (ngrp < 1) return cudaSuccess;
-  const dim3 grid(max_chunks, ngrp);
-  k_wb_partials_g<<<grid, kWbThreads, 0, st>>>(g);
-  if (mode != kRayleighEta) k_wb_apply_g<<<grid, kWbThreads, 0, st>>>(g);
+cudaError_t launch_wb_grouped(const WbArgs* g, const int* start, int ngrp, int nblocks, int mode, cudaStream_t st) {
+  if (ngrp < 1 || nblocks < 1) return cudaSuccess;
+  k_wb_partials_g<<<nblocks, kWbThreads, 0, st>>>(g, start, ngrp);
+  if (mode != kRayleighEta) k_wb_apply_g<<<nblocks, kWbThreads, 0, st>>>(g, start, ngrp);
   return cudaGetLastError();
 }
 

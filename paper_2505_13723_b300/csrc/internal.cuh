@@ -359,7 +359,8 @@ struct WbArgs {
 WbArgs wb_args_single(CoreBufs& cb, int mode, const float* v, float* out, DevScalars* sc);
 WbArgs wb_args_power(CoreBufs& cb, int mode, const float* part, int nsplit, float lam, const float* acur,
                      float* hbuf, float* anext, DevScalars* sc);
-cudaError_t launch_wb_grouped(const WbArgs* g, int ngrp, int max_chunks, int mode, cudaStream_t st);
+// start: device prefix sums of the systems' chunk counts (ngrp + 1 entries, the last = nblocks)
+cudaError_t launch_wb_grouped(const WbArgs* g, const int* start, int ngrp, int nblocks, int mode, cudaStream_t st);
 // One powering step of Alg. 5 on h = sum_p part[p] + lam * acur (nsplit x b partials):
 //   kInvUnit:     anext = P^{-1} h / sqrt(h^T P^{-1} h)  (h kept in hbuf)
 //   kRayleighEta: sc->lam_hat = acur . h, sc->eta = 1 / lam_hat

@@ -1263,7 +1263,8 @@ struct Batch {
   // grouped Woodbury applies of the grouped systems: powering start, powering
   // steps on buffer 0 / 1, the last (Rayleigh) step, the direction
   WbArgs* wb[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  int nwb = 0, wb_chunks = 1;
+  int* wb_start = nullptr;   // device prefix sums of the grouped systems' chunk counts
+  int nwb = 0, wb_blocks = 0;
   // grouped k_head_prep of the active systems that take it, one table per
   // operand width (tc_kp 16, 32)
   HeadPrepArgs* prep[2] = {nullptr, nullptr};
@@ -1298,6 +1299,8 @@ struct Batch {
       cudaFree(w);
       w = nullptr;
     }
+    cudaFree(wb_start);
+    wb_start = nullptr;
     nwb = 0;
     for (int k = 0; k < 2; ++k) {
       cudaFree(prep[k]);
@@ -1398,7 +1401,7 @@ cudaError_t build_groups(Batch& bt, int which, int tpi, std::vector<GroupedProdu
 
 cudaError_t build_wb(Batch& bt) {
   std::vector<WbArgs> h[5];
-  bt.wb_chunks = 1;
+  std::vector<int> start(1, 0);
   for (size_t i = 0; i < bt.S.size(); ++i) {
     if (!bt.active[i] || !bt.grouped[i]) continue;
     adasap_solver* S = bt.S[i];
@@ -1412,14 +1415,17 @@ cudaError_t build_wb(Batch& bt) {
     h[3].push_back(wb_args_power(S->cb, kRayleighEta, S->part2, S->ns_pw, lam, power_buf(S, np - 1), S->h,
                                  power_buf(S, np), c->sc));
     h[4].push_back(wb_args_single(S->cb, kInv, S->R, S->D, c->sc));
-    bt.wb_chunks = std::max(bt.wb_chunks, h[0].back().nchunk);
+    start.push_back(start.back() + h[0].back().nchunk);   // the same chunking in all five tables
   }
   bt.nwb = (int)h[0].size();
+  bt.wb_blocks = start.back();
   if (bt.nwb == 0) return cudaSuccess;
   for (int k = 0; k < 5; ++k) {
     KR(cudaMalloc(&bt.wb[k], h[k].size() * sizeof(WbArgs)));
     KR(cudaMemcpy(bt.wb[k], h[k].data(), h[k].size() * sizeof(WbArgs), cudaMemcpyHostToDevice));
   }
+  KR(cudaMalloc(&bt.wb_start, start.size() * sizeof(int)));
+  KR(cudaMemcpy(bt.wb_start, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice));
   return cudaSuccess;
 }
 
@@ -1621,7 +1627,7 @@ cudaError_t rec_batch(Batch& bt) {
   }
   if (!grp.empty()) {
     KR(join(grp));
-    KR(launch_wb_grouped(bt.wb[0], bt.nwb, bt.wb_chunks, kInvSqrtNormalised, ms));
+    KR(launch_wb_grouped(bt.wb[0], bt.wb_start, bt.nwb, bt.wb_blocks, kInvSqrtNormalised, ms));
   }
   const int np = act.empty() ? 0 : act[0]->o.power_iters;
   for (int i = 0; i < np; ++i) {
@@ -1630,13 +1636,14 @@ cudaError_t rec_batch(Batch& bt) {
     if (!grp.empty()) {
       KR(launch_groups(bt, bt.pw[i & 1], ms));
       const bool last = i == np - 1;
-      KR(launch_wb_grouped(bt.wb[last ? 3 : 1 + (i & 1)], bt.nwb, bt.wb_chunks, last ? kRayleighEta : kInvUnit, ms));
+      KR(launch_wb_grouped(bt.wb[last ? 3 : 1 + (i & 1)], bt.wb_start, bt.nwb, bt.wb_blocks,
+                           last ? kRayleighEta : kInvUnit, ms));
     }
     for (adasap_solver* S : act)
       if (!S->identity && !groupable(S)) KR(rec_power_apply(S, i));
   }
   if (!grp.empty()) {
-    KR(launch_wb_grouped(bt.wb[4], bt.nwb, bt.wb_chunks, kInv, ms));
+    KR(launch_wb_grouped(bt.wb[4], bt.wb_start, bt.nwb, bt.wb_blocks, kInv, ms));
     KR(fork(grp));
   }
   for (adasap_solver* S : act) {
