@@ -815,8 +815,8 @@ __global__ void __launch_bounds__(kFinThreads) k_nys_finalize(const double* __re
 }
 
 // U = (A1 + delta A2) T'  (b x r), T' (r x r) given in FP32 by the triangular
-// solve that forms it (an FP64 -> FP32 conversion per entry in every block would
-// run on this GPU's slow FP64 pipe), delta = sc->delta or 0 when A2 is NULL.
+// solve that forms it (converted once, not in every block), delta = sc->delta or
+// 0 when A2 is NULL.
 //   Nystrom: A1 = M Omega, A2 = Omega, T' = T      (U = Y_nu T)
 //   QR:      A1 = Omega,   A2 = NULL,  T' = L^{-T} (Omega R^{-1}, R = L^T)
 // A block takes kMuRows rows of U; warp w of its 8 rows 8w .. 8w + 7 and lane l of
