@@ -119,6 +119,8 @@ struct TcArgs {
   int* err;          // set to 1 on a wait timeout
   int flat;          // 1: equal tile runs per CTA (one product only; nsplit = tc_flat_slots)
   const float* wp;   // w prepared per 128-column tile by launch_prep_w (NULL: the kernel stages w itself)
+  // grouped launches: {next item, CTAs done}, zero between launches (NULL: static order)
+  unsigned long long* sched;
 };
 TcArgs make_tc_args(int d, const float* xr, const float* qr, const int* ridx, int64_t m, int dp, const float* bhi,
                     const float* blo, int64_t ncols, int self_mode, const float* w, int64_t ldw, float* part,
@@ -126,8 +128,12 @@ TcArgs make_tc_args(int d, const float* xr, const float* qr, const int* ridx, in
 int64_t tc_items(const TcArgs& a);   // (row tile, split) items of one product
 // Several independent products (grp[g], device) in one persistent launch of at
 // most `ctas` CTAs; gstart (device, ngrp + 1) is the prefix sum of tc_items.
+// sched (device, 2 counters, zero; NULL: static order): the CTAs take their items
+// after the first from a shared counter, so that CTAs slowed by other work on
+// their SMs take fewer; the last CTA to finish zeroes the counters again.
 cudaError_t launch_rows_tc_grouped(int kern, int kp, const TcArgs* grp, const int64_t* gstart, int ngrp,
-                                   int64_t nitems, int* err, int ctas, cudaStream_t st);
+                                   int64_t nitems, int* err, int ctas, cudaStream_t st,
+                                   unsigned long long* sched = nullptr);
 // K of the augmented MMA operands (16 or 32; 0 if d + 2 > 32) and padded row count.
 int tc_kp(int d);
 int64_t tc_npad(int64_t n);

@@ -326,11 +326,16 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
   // the CTA that ends a row tile zeroes the slots after its own, so every slot
   // of every row is written.
   const bool flat = !GROUPED && a0.flat;
+  // grouped launches with counters: items after the first from the shared counter
+  // (the same items in the same global order, so the outputs are unchanged)
+  const bool dyn = GROUPED && a0.sched != nullptr;
+  __shared__ int64_t s_next;
   const int64_t ctiles = (a0.ncols + kTcN - 1) / kTcN;
   const int64_t ftotal = flat ? (a0.m + kTcM - 1) / kTcM * ctiles : 0;
   int64_t fpos = flat ? (int64_t)blockIdx.x * ftotal / gridDim.x : 0;
   const int64_t fend = flat ? ((int64_t)blockIdx.x + 1) * ftotal / gridDim.x : 0;
-  for (int64_t item = blockIdx.x; flat ? fpos < fend : item < nitems; item += gridDim.x) {
+  for (int64_t item = blockIdx.x; flat ? fpos < fend : item < nitems;
+       item = dyn ? s_next : item + gridDim.x) {
     int sys = 0;
     if (GROUPED) {  // the product this item belongs to: last g with gstart[g] <= item
       int hi = ngrp - 1;
@@ -594,17 +599,33 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
       red[cg * kTcM + rl] = acc - cmp;
       asm volatile("bar.sync 1, %0;" ::"r"(32 * kTcEpiWarps) : "memory");
       if (cg == 0 && ri < a.m) {
-        const float tot = (red[rl] + red[kTcM + rl]) + (red[2 * kTcM + rl] + red[3 * kTcM + rl]);
+        // group cg summed the tiles t = cg - gt (mod 4) of this item; under the shared
+        // counter the four classes are added in class order, so that the result does
+        // not depend on which CTA (and so which gt) took the item
+        static_assert(kTcBufs == 4, "four epilogue groups");
+        const int c0 = dyn ? (int)(gt % kTcBufs) : 0;
+        const float tot = (red[(c0 & 3) * kTcM + rl] + red[((c0 + 1) & 3) * kTcM + rl]) +
+                          (red[((c0 + 2) & 3) * kTcM + rl] + red[((c0 + 3) & 3) * kTcM + rl]);
         a.part[split * a.m + ri] = (bad || *abort_flag) ? __int_as_float(0x7fc00000) : a.sigma2 * tot;
         if (row_end)
           for (int64_t s2 = split + 1; s2 < a.nsplit; ++s2) a.part[s2 * a.m + ri] = 0.0f;
       }
     }
     gt += (uint32_t)ntiles;
+    if (dyn && tid == 0) s_next = (int64_t)atomicAdd(a0.sched, 1ull) + gridDim.x;
     // item boundary: the row operands, both TMEM buffers and red[] are free again
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+  }
+  if (dyn && tid == 0) {
+    // every CTA has taken its last item when the count of finished CTAs completes:
+    // the last one zeroes the counters for the next launch
+    __threadfence();
+    if (atomicAdd(a0.sched + 1, 1ull) == (unsigned long long)gridDim.x - 1ull) {
+      a0.sched[0] = 0ull;
+      a0.sched[1] = 0ull;
+    }
   }
   if (warp == 0 && lane == 0 && *abort_flag) tc_note_timeout(a0.err, 9);
   if (warp == 1) {
@@ -816,6 +837,7 @@ TcArgs make_tc_args(int d, const float* xr, const float* qr, const int* ridx, in
   a.nsplit = nsplit;
   a.flat = 0;
   a.wp = nullptr;
+  a.sched = nullptr;
   return a;
 }
 
@@ -841,10 +863,11 @@ cudaError_t launch_rows_tc(int kern, int d, const float* xr, const float* qr, co
 }
 
 cudaError_t launch_rows_tc_grouped(int kern, int kp, const TcArgs* grp, const int64_t* gstart, int ngrp,
-                                   int64_t nitems, int* err, int ctas, cudaStream_t st) {
+                                   int64_t nitems, int* err, int ctas, cudaStream_t st, unsigned long long* sched) {
   if (ngrp < 1 || nitems <= 0) return cudaSuccess;
   TcArgs a0 = {};
   a0.err = err;
+  a0.sched = sched;
   return launch_tc_any<true>(kern, kp, a0, grp, gstart, ngrp, (int)std::min<int64_t>(nitems, ctas), st);
 }
 

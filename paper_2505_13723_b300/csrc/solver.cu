@@ -1249,6 +1249,7 @@ struct GroupedProduct {
   TcArgs* grp = nullptr;         // device, one per member
   int64_t* gstart = nullptr;     // device, prefix sums of the members' items
   int64_t nitems = 0;
+  unsigned long long* sched = nullptr;   // device, the launch's item counters (zero between launches)
 };
 
 struct Batch {
@@ -1292,6 +1293,7 @@ struct Batch {
       for (GroupedProduct& g : *v) {
         cudaFree(g.grp);
         cudaFree(g.gstart);
+        cudaFree(g.sched);
       }
       v->clear();
     }
@@ -1389,6 +1391,8 @@ cudaError_t build_groups(Batch& bt, int which, int tpi, std::vector<GroupedProdu
     cudaError_t e;
     if ((e = cudaMalloc(&g.grp, args[k].size() * sizeof(TcArgs))) ||
         (e = cudaMalloc(&g.gstart, start.size() * sizeof(int64_t))) ||
+        (e = cudaMalloc(&g.sched, 2 * sizeof(unsigned long long))) ||
+        (e = cudaMemset(g.sched, 0, 2 * sizeof(unsigned long long))) ||
         (e = cudaMemcpy(g.grp, args[k].data(), args[k].size() * sizeof(TcArgs), cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(g.gstart, start.data(), start.size() * sizeof(int64_t), cudaMemcpyHostToDevice))) {
       out.insert(out.end(), cls.begin(), cls.begin() + k + 1);
@@ -1524,7 +1528,7 @@ cudaError_t build_head(Batch& bt) {
 cudaError_t launch_groups(const Batch& bt, const std::vector<GroupedProduct>& gs, cudaStream_t st) {
   for (const GroupedProduct& g : gs)
     KR(launch_rows_tc_grouped(g.kern, g.kp, g.grp, g.gstart, (int)g.members.size(), g.nitems,
-                              bt.S[g.members[0]]->c->err_dev, bt.ctas, st));
+                              bt.S[g.members[0]]->c->err_dev, bt.ctas, st, g.sched));
   return cudaSuccess;
 }
 
@@ -1561,6 +1565,7 @@ adasap_status autotune(Batch& bt) {
       for (GroupedProduct& g : gs) {
         cudaFree(g.grp);
         cudaFree(g.gstart);
+        cudaFree(g.sched);
       }
       if (e != cudaSuccess) {
         note_error(e, "autotune");
