@@ -318,7 +318,9 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
 
   // Items (row tile, column split) are taken in grid-stride order with the row
   // tile varying fastest, so the CTAs running at one time share column tiles in
-  // L2.  The pipeline phases run on across items (gt counts this CTA's tiles).
+  // L2 (grouped launches with counters: the same global order, each CTA's items
+  // after its first from the counter).  The pipeline phases run on across items
+  // (gt counts this CTA's tiles).
   uint32_t gt = 0, ndrain = 0;
   // Flat mode (one product): CTA x takes the tiles [x T / G, (x + 1) T / G) of the
   // row-tile-major sequence of all T tiles (G CTAs, T >= G), as runs within one
