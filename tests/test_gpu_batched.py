@@ -171,3 +171,22 @@ def test_batched_bo_workload_full_size(lib):
         P = Ps[k]
         Wref, rec, sens = _oracle(P, T, 40 + int(k))
         _check_w("bo full-size k=%d n=%d" % (k, P.X.shape[0]), Ws[k].cpu().numpy(), Wref, rec, sens, P)
+
+
+def test_batched_bo_workload_repeats_bit_for_bit(lib):
+    """The grouped tensor-core launches let each CTA take its next item from a shared
+    counter, so which CTA computes an item depends on timing; an item's result must
+    not (its partial sums are combined in a fixed order).  Two solves of the 48-system
+    bo workload with the same inputs and seeds give the same W, bit for bit."""
+    Ps = synth.bo_systems()
+    ctxs = [lib.Context(torch.from_numpy(P.X).cuda(), P.kernel, P.ell, P.sigma2, P.lam) for P in Ps]
+    Ys = [torch.from_numpy(P.Y).cuda() for P in Ps]
+    out = []
+    for _ in range(2):
+        opts = [lib.default_opts(P.X.shape[0], b=P.b, r=P.r, max_iters=3, check_every=0, check_rows=4096,
+                                 seed=40 + k) for k, P in enumerate(Ps)]
+        Ws, stats, status = lib.solve_batched(ctxs, Ys, opts=opts)
+        assert status == 0
+        out.append([W.cpu().numpy() for W in Ws])
+    for k, (a, b) in enumerate(zip(*out)):
+        assert np.array_equal(a, b), "system %d differs between two identical solves" % k
